@@ -1,0 +1,116 @@
+"""Generators for the synthetic workloads (no arithmetic of the method here).
+
+Workloads (shapes follow the paper's problem classes: block-angular Jacobians of
+latent-variable fits, Sec. 4.2 / Sec. 6.2, and banded matrices, Sec. 4.4):
+
+  block_angular_dense  J = [blkdiag(J_1..J_K) | S]: K blocks n x m, S dense (K n) x s,
+                       N(0,1) entries, global column j scaled by 10^(3 j / (N-1)),
+                       b ~ N(0,1).  Default K=200, n=4, m=2, s=30.
+  batched_blocks       K independent blocks, n ~ U{2..16}, m ~ U{1..min(n,6)}, N(0,1),
+                       one rhs per block; packed column-major per block.
+  curvefit_problem     points on an open uniform cubic B-spline with Kc control
+                       points plus N(0, sigma^2) noise, and a perturbed start.
+  banded_problem       J of (rows_per_col * n) x n, row i touches columns
+                       floor(i / rows_per_col) .. + w - 1 (truncated at n - 1), N(0,1).
+"""
+from __future__ import annotations
+
+import numpy as np
+
+SEED_BASE = 20180209
+
+
+def rng_for(workload: int, seed_offset: int = 0) -> np.random.Generator:
+    return np.random.Generator(np.random.Philox(SEED_BASE + workload + 1000003 * seed_offset))
+
+
+def _f32(x):
+    return np.asarray(x, dtype=np.float64).astype(np.float32)
+
+
+def block_angular_dense(K=200, n=4, m=2, s=30, seed_offset=0, scale_decades=3.0,
+                        dtype=np.float64):
+    """Block-angular J = [blkdiag(J_i) | S] with geometric column scaling.
+
+    Returns dict(blocks (K, n, m), S (K n, s), b (K n), lam).  Global column order is
+    block columns first (block i owns columns i m .. i m + m - 1), then the s shared columns.
+    """
+    g = rng_for(1, seed_offset)
+    N = K * m + s
+    scale = 10.0 ** (scale_decades * np.arange(N) / max(N - 1, 1))
+    blocks = g.standard_normal((K, n, m))
+    S = g.standard_normal((K * n, s))
+    b = g.standard_normal(K * n)
+    blocks = blocks * scale[:K * m].reshape(K, 1, m)
+    S = S * scale[K * m:][None, :]
+    if dtype == np.float32:
+        blocks, S, b = _f32(blocks), _f32(S), _f32(b)
+    return dict(blocks=blocks, S=S, b=b, lam=1e-2, K=K, n=n, m=m, s=s)
+
+
+def batched_blocks(K=1_000_000, n_lo=2, n_hi=16, m_hi=6, seed_offset=0, dtype=np.float32):
+    """K independent blocks, n ~ U{n_lo..n_hi}, m ~ U{1..min(n, m_hi)}, N(0,1) entries.
+
+    Returns dict(n (uint8 K), m (uint8 K), vals (packed column-major per block),
+    b (packed per block), val_off (int64 K+1), row_off (int64 K+1), col_off (int64 K+1)).
+    """
+    g = rng_for(2, seed_offset)
+    n = g.integers(n_lo, n_hi + 1, size=K)
+    m = (g.random(K) * np.minimum(n, m_hi)).astype(np.int64) + 1
+    m = np.minimum(m, np.minimum(n, m_hi))
+    nm = n * m
+    val_off = np.concatenate([[0], np.cumsum(nm)]).astype(np.int64)
+    row_off = np.concatenate([[0], np.cumsum(n)]).astype(np.int64)
+    col_off = np.concatenate([[0], np.cumsum(m)]).astype(np.int64)
+    vals = g.standard_normal(int(val_off[-1]))
+    b = g.standard_normal(int(row_off[-1]))
+    if dtype == np.float32:
+        vals, b = _f32(vals), _f32(b)
+    return dict(n=n.astype(np.uint8), m=m.astype(np.uint8), vals=vals, b=b,
+                val_off=val_off, row_off=row_off, col_off=col_off, K=K)
+
+
+def curvefit_problem(npoints=200_000, Kc=2048, sigma=0.01, start_sigma_t=0.05,
+                     start_sigma_p=0.01, radius_jitter=0.1, seed_offset=0, workload=3):
+    """Data for fitting an open uniform cubic B-spline (Kc control points) to 2-D points.
+
+    Control points P_k = (cos th_k, sin th_k) (1 + radius_jitter N(0,1)), th_k = 2 pi k / Kc.
+    Parameters t_i ~ U[0, Kc - 3).  The curve itself is evaluated by the model code of
+    each side; this returns only the random draws: control points, t_true, the noise to
+    add to curve(t_true), and the start perturbations.
+    """
+    g = rng_for(workload, seed_offset)
+    th = 2.0 * np.pi * np.arange(Kc) / Kc
+    rad = 1.0 + radius_jitter * g.standard_normal(Kc)
+    P_true = np.stack([np.cos(th) * rad, np.sin(th) * rad], axis=1)
+    t_true = g.random(npoints) * (Kc - 3)
+    noise = sigma * g.standard_normal((npoints, 2))
+    dt = start_sigma_t * g.standard_normal(npoints)
+    dP = start_sigma_p * g.standard_normal((Kc, 2))
+    return dict(P_true=P_true, t_true=t_true, noise=noise, dt=dt, dP=dP, Kc=Kc,
+                npoints=npoints)
+
+
+def banded_problem(n=1_000_000, rows_per_col=4, w=8, seed_offset=0, dtype=np.float32,
+                   workload=4):
+    """Banded J: row i starts at column floor(i / rows_per_col), w values, N(0,1).
+
+    Entries that would fall at columns >= n are zero (truncated band end).
+    Returns dict(start int64 (M,), vals (M, w), b (M,), n, lam).
+    """
+    g = rng_for(workload, seed_offset)
+    M = rows_per_col * n
+    start = (np.arange(M, dtype=np.int64) // rows_per_col)
+    vals = g.standard_normal((M, w))
+    cols = start[:, None] + np.arange(w)[None, :]
+    vals[cols >= n] = 0.0
+    b = g.standard_normal(M)
+    if dtype == np.float32:
+        vals, b = _f32(vals), _f32(b)
+    return dict(start=start, vals=vals, b=b, n=n, lam=1e-3, w=w, rows_per_col=rows_per_col)
+
+
+def banded_batch_shapes(count=4096, n_lo=1000, n_hi=100_000, seed_offset=0):
+    """Column counts of a batch of independent banded instances, n ~ U{n_lo..n_hi}."""
+    g = rng_for(5, seed_offset)
+    return g.integers(n_lo, n_hi + 1, size=count).astype(np.int64)
