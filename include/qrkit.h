@@ -1,0 +1,134 @@
+/*
+ * qrkit.h - C ABI of a GB300 (sm_103a) library that solves the damped least-squares
+ * problem of a Levenberg-Marquardt step by structured sparse QR.
+ *
+ * The operation (arXiv 1802.03773, Eq. 2):   min_p || [J; lambda^(1/2) D] p - [b; 0] ||_2,
+ * equivalently the normal equations Eq. 1, (J^T J + lambda D^2) p = J^T b, solved without
+ * forming J^T J.  J is given by a structure descriptor plus packed values:
+ *   QRKIT_STRUCT_BLOCKS   J = [blkdiag(J_1..J_K) | S]          (Sec. 4.1 block diagonal,
+ *                         Sec. 4.2 horizontal concatenation); S absent, dense, or windowed
+ *   QRKIT_STRUCT_BANDED   J banded: row i touches w consecutive columns from
+ *                         floor(i / rows_per_col) (Sec. 4.4 block banded)
+ * The damping rows lambda^(1/2) D are appended by the row interleave of Sec. 4.5 / Sec. 5.2
+ * ("Backtrack LM"): P_r [J; lambda^(1/2) D] = Q R, factored once.
+ *
+ * Conventions for every entry point:
+ *   - All value buffers are DEVICE pointers (memory of the context's device), owned by the
+ *     caller, on the stream given to qrkit_create; calls are asynchronous on that stream
+ *     unless stated.  Index/shape arrays inside qrkit_structure are HOST pointers, read
+ *     during qrkit_plan only.
+ *   - Value precision follows the context: float for QRKIT_FP32 / QRKIT_FP32_REFINED,
+ *     double for QRKIT_FP64.  lambda is always a double.
+ *   - Every function returns a qrkit_status; nothing throws across the ABI.  On error a
+ *     message is kept per context (qrkit_last_error).  Device-side failures (non-finite
+ *     input, zero pivot) are recorded in a device status word, read by qrkit_sync_status.
+ *   - Householder convention (Sec. 2): reflector H = I - tau v v^T with v[0] = 1,
+ *     beta = -sign(x0) ||x||, tau = (beta - x0) / beta; R may have negative diagonal.
+ */
+#ifndef QRKIT_H
+#define QRKIT_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  QRKIT_OK = 0,
+  QRKIT_EINVAL = 1,       /* bad argument or descriptor */
+  QRKIT_ENOMEM = 2,       /* device allocation failed */
+  QRKIT_ECUDA = 3,        /* a CUDA runtime call failed */
+  QRKIT_ESINGULAR = 4,    /* a diagonal entry of R is zero */
+  QRKIT_ENONFINITE = 5,   /* NaN/Inf met in the inputs or the factor */
+  QRKIT_ETIMEOUT = 6,     /* a bounded device wait expired */
+  QRKIT_ENOTCONV = 7,     /* LM stopped without converging */
+  QRKIT_EUNSUPPORTED = 8, /* structure or size outside what this build handles */
+  QRKIT_ESTATE = 9        /* call order: e.g. solve before factor, factor before plan */
+} qrkit_status;
+
+typedef enum {
+  QRKIT_FP64 = 0,          /* all arithmetic in double */
+  QRKIT_FP32_REFINED = 1,  /* float factors, high-precision residual refinement */
+  QRKIT_FP32 = 2           /* float factors, no refinement */
+} qrkit_precision;
+
+typedef enum { QRKIT_STRUCT_BLOCKS = 0, QRKIT_STRUCT_BANDED = 1 } qrkit_struct_kind;
+typedef enum {
+  QRKIT_COUPLED_NONE = 0,   /* J = blkdiag(J_i) */
+  QRKIT_COUPLED_DENSE = 1,  /* J = [blkdiag(J_i) | S], S dense (sum n_i) x s, column-major */
+  QRKIT_COUPLED_WINDOW = 2  /* block i's rows touch S columns start_i .. start_i + w - 1 */
+} qrkit_coupled_kind;
+
+/* Structure descriptor (the paper's compile-time composition, Sec. 3 / Sec. 5.1, as data). */
+typedef struct qrkit_structure {
+  int32_t kind;                 /* qrkit_struct_kind */
+  /* --- QRKIT_STRUCT_BLOCKS --- */
+  int64_t num_blocks;           /* K >= 1 */
+  const uint8_t* block_rows;    /* host, K entries: n_i (J rows of block i), 1..16 */
+  const uint8_t* block_cols;    /* host, K entries: m_i, 1..8; with the damping rows the
+                                   augmented block has n_i + m_i <= 16 rows (n_i >= m_i
+                                   when lambda = 0) */
+  int32_t coupled_kind;         /* qrkit_coupled_kind */
+  int64_t shared_cols;          /* s: columns of S (0 for QRKIT_COUPLED_NONE) */
+  int32_t window;               /* w for QRKIT_COUPLED_WINDOW */
+  const int32_t* window_start;  /* host, K entries, non-decreasing, start_i + w <= s + w - 1 */
+  /* --- QRKIT_STRUCT_BANDED --- */
+  int64_t rows, cols;           /* J is rows x cols */
+  int32_t rows_per_col;         /* row i starts at column floor(i / rows_per_col) */
+  int32_t band_window;          /* w: values per row (entries past the last column ignored) */
+} qrkit_structure;
+
+typedef struct qrkit_ctx qrkit_ctx;
+
+/* Create a context on `device` (CUDA ordinal) issuing work on `stream` (a cudaStream_t,
+ * NULL = legacy default stream).  precision: qrkit_precision.  *out receives the context. */
+qrkit_status qrkit_create(qrkit_ctx** out, int device, void* stream, int precision);
+
+/* Release the context, its plan and its device workspace.  NULL is allowed. */
+void qrkit_destroy(qrkit_ctx* ctx);
+
+/* Message of the last failed call on ctx ("" if none); valid until the next call. */
+const char* qrkit_last_error(const qrkit_ctx* ctx);
+
+/* Static name of a status code. */
+const char* qrkit_status_string(int status);
+
+/* Structure plan (Sec. 3 composition, Sec. 4.3 / 4.5 row permutation): validates the
+ * descriptor, builds offsets, the P_r interleave of the damping rows, the tile schedule of
+ * the persistent kernels, and allocates the device workspace that holds the factor.
+ * Host work, once per structure; synchronous.  Replaces any previous plan. */
+qrkit_status qrkit_plan(qrkit_ctx* ctx, const qrkit_structure* s);
+
+/* Fused factor + solve for QRKIT_STRUCT_BLOCKS with QRKIT_COUPLED_NONE (Sec. 4.1, Sec. 5.1):
+ * for every block the Householder QR of B_i = [J_i; lambda^(1/2) D_i] (damping rows only if
+ * lambda > 0), c_i = Q_i^T [b_i; 0], R_i p_i = c_i, plus `refine_steps` steps of augmented-
+ * system refinement with residuals in extended precision (FP32 modes; ignored for FP64).
+ *   J    : packed values, block i column-major n_i x m_i, blocks in order (sum n_i m_i)
+ *   b    : sum n_i values, block i's rows contiguous
+ *   D    : sum m_i diagonal values or NULL (= column norms of J, a zero norm -> 1)
+ *   p    : out, sum m_i values
+ *   qtb  : out or NULL; sum n_i (+ m_i if lambda > 0) values: Q_i^T [b_i; 0] per block
+ * The factor (reflectors below the diagonal, R on and above it, tau) stays in the context.
+ * lambda > 0 is not supported on this fused path yet (QRKIT_EUNSUPPORTED). */
+qrkit_status qrkit_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
+                                double lambda, void* p, void* qtb, int refine_steps);
+
+/* Copy the stored factor of a block structure to caller buffers (device pointers, either
+ * may be NULL): factor values in J's packing (V strictly below the diagonal, R on and above)
+ * and tau (sum m_i). */
+qrkit_status qrkit_get_factor(qrkit_ctx* ctx, void* factor_out, void* tau_out);
+
+/* Block until the stream is idle and return the device status word (QRKIT_OK if no kernel
+ * reported a failure), then clear it. */
+qrkit_status qrkit_sync_status(qrkit_ctx* ctx);
+
+/* Number of this library's kernels launched on ctx since creation (for launch accounting). */
+int64_t qrkit_launch_count(const qrkit_ctx* ctx);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* QRKIT_H */

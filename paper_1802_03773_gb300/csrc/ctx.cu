@@ -1,0 +1,269 @@
+// Context, structure plan and the C-ABI entry points.
+#include <cuda_runtime.h>
+#include <stdint.h>
+#include <string.h>
+
+#include <algorithm>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace qrkit {
+
+TileBudget block_solve_budget(size_t elem);
+int block_solve_max_rows();
+int block_solve_max_cols();
+
+qrkit_status fail(qrkit_ctx* ctx, qrkit_status st, const std::string& msg) {
+  if (ctx) ctx->last_error = msg;
+  return st;
+}
+
+qrkit_status cuda_fail(qrkit_ctx* ctx, cudaError_t e, const char* what) {
+  std::string msg = std::string(what) + ": " + cudaGetErrorString(e);
+  return fail(ctx, e == cudaErrorMemoryAllocation ? QRKIT_ENOMEM : QRKIT_ECUDA, msg);
+}
+
+void release(DevBuf& buf) {
+  if (buf.ptr) cudaFree(buf.ptr);
+  buf.ptr = nullptr;
+  buf.bytes = 0;
+}
+
+qrkit_status ensure(qrkit_ctx* ctx, DevBuf& buf, size_t bytes, const char* what) {
+  if (bytes == 0) bytes = 16;
+  if (buf.ptr && buf.bytes >= bytes) return QRKIT_OK;
+  release(buf);
+  cudaError_t e = cudaMalloc(&buf.ptr, bytes);
+  if (e != cudaSuccess) {
+    buf.ptr = nullptr;
+    return cuda_fail(ctx, e, what);
+  }
+  buf.bytes = bytes;
+  return QRKIT_OK;
+}
+
+static qrkit_status upload(qrkit_ctx* ctx, DevBuf& buf, const void* host, size_t bytes,
+                           const char* what) {
+  qrkit_status st = ensure(ctx, buf, bytes, what);
+  if (st != QRKIT_OK) return st;
+  if (bytes) QRKIT_CUDA_TRY(ctx, cudaMemcpy(buf.ptr, host, bytes, cudaMemcpyHostToDevice));
+  return QRKIT_OK;
+}
+
+static void release_plan(Plan& P) {
+  release(P.d_n);
+  release(P.d_m);
+  release(P.d_tile_block);
+  release(P.d_tile_val);
+  release(P.d_tile_row);
+  release(P.d_tile_col);
+  P = Plan();
+}
+
+// Greedy tile schedule: consecutive blocks while every budget holds.
+static void cut_tiles(Plan& P) {
+  const TileBudget& B = P.budget;
+  P.tile_block.assign(1, 0);
+  P.tile_val.assign(1, 0);
+  P.tile_row.assign(1, 0);
+  P.tile_col.assign(1, 0);
+  int64_t nb = 0, nv = 0, nr = 0, nc = 0;
+  int64_t val = 0, row = 0, col = 0;
+  for (int64_t i = 0; i < P.K; ++i) {
+    const int64_t n = P.n[i], m = P.m[i];
+    if (nb > 0 && (nb + 1 > B.blocks || nv + n * m > B.values || nr + n > B.rows ||
+                   nc + m > B.cols)) {
+      P.tile_block.push_back(i);
+      P.tile_val.push_back(val);
+      P.tile_row.push_back(row);
+      P.tile_col.push_back(col);
+      nb = nv = nr = nc = 0;
+    }
+    nb += 1; nv += n * m; nr += n; nc += m;
+    val += n * m; row += n; col += m;
+  }
+  P.tile_block.push_back(P.K);
+  P.tile_val.push_back(val);
+  P.tile_row.push_back(row);
+  P.tile_col.push_back(col);
+  P.num_tiles = (int64_t)P.tile_block.size() - 1;
+}
+
+static qrkit_status plan_blocks(qrkit_ctx* ctx, const qrkit_structure* s) {
+  Plan& P = ctx->plan;
+  if (s->num_blocks < 1) return fail(ctx, QRKIT_EINVAL, "num_blocks must be >= 1");
+  if (!s->block_rows || !s->block_cols)
+    return fail(ctx, QRKIT_EINVAL, "block_rows and block_cols are required");
+  if (s->coupled_kind != QRKIT_COUPLED_NONE)
+    return fail(ctx, QRKIT_EUNSUPPORTED, "coupled (hcat) structures are not available in this build");
+  P.K = s->num_blocks;
+  P.n.assign(s->block_rows, s->block_rows + P.K);
+  P.m.assign(s->block_cols, s->block_cols + P.K);
+  const int maxr = block_solve_max_rows(), maxc = block_solve_max_cols();
+  for (int64_t i = 0; i < P.K; ++i) {
+    const int n = P.n[i], m = P.m[i];
+    if (n < 1 || m < 1)
+      return fail(ctx, QRKIT_EINVAL, "block " + std::to_string(i) + ": empty block");
+    if (n > maxr || m > maxc)
+      return fail(ctx, QRKIT_EUNSUPPORTED,
+                  "block " + std::to_string(i) + ": " + std::to_string(n) + "x" +
+                      std::to_string(m) + " exceeds the block kernel's 16 rows x 8 columns");
+    P.rows += n;
+    P.cols += m;
+    P.values += (int64_t)n * m;
+    P.max_n = std::max(P.max_n, n);
+    P.max_m = std::max(P.max_m, m);
+  }
+  P.budget = block_solve_budget(elem_size(ctx));
+  cut_tiles(P);
+  qrkit_status st;
+  if ((st = upload(ctx, P.d_n, P.n.data(), P.K, "plan n")) != QRKIT_OK) return st;
+  if ((st = upload(ctx, P.d_m, P.m.data(), P.K, "plan m")) != QRKIT_OK) return st;
+  const size_t tb = (size_t)(P.num_tiles + 1) * sizeof(int64_t);
+  if ((st = upload(ctx, P.d_tile_block, P.tile_block.data(), tb, "plan tiles")) != QRKIT_OK) return st;
+  if ((st = upload(ctx, P.d_tile_val, P.tile_val.data(), tb, "plan tiles")) != QRKIT_OK) return st;
+  if ((st = upload(ctx, P.d_tile_row, P.tile_row.data(), tb, "plan tiles")) != QRKIT_OK) return st;
+  if ((st = upload(ctx, P.d_tile_col, P.tile_col.data(), tb, "plan tiles")) != QRKIT_OK) return st;
+  const size_t es = elem_size(ctx);
+  if ((st = ensure(ctx, ctx->ws.factor, (size_t)P.values * es, "factor workspace")) != QRKIT_OK)
+    return st;
+  if ((st = ensure(ctx, ctx->ws.tau, (size_t)P.cols * es, "tau workspace")) != QRKIT_OK) return st;
+  P.s = *s;
+  P.s.block_rows = nullptr;
+  P.s.block_cols = nullptr;
+  P.s.window_start = nullptr;
+  P.valid = true;
+  return QRKIT_OK;
+}
+
+}  // namespace qrkit
+
+using namespace qrkit;
+
+extern "C" {
+
+const char* qrkit_status_string(int st) {
+  switch (st) {
+    case QRKIT_OK: return "QRKIT_OK";
+    case QRKIT_EINVAL: return "QRKIT_EINVAL";
+    case QRKIT_ENOMEM: return "QRKIT_ENOMEM";
+    case QRKIT_ECUDA: return "QRKIT_ECUDA";
+    case QRKIT_ESINGULAR: return "QRKIT_ESINGULAR";
+    case QRKIT_ENONFINITE: return "QRKIT_ENONFINITE";
+    case QRKIT_ETIMEOUT: return "QRKIT_ETIMEOUT";
+    case QRKIT_ENOTCONV: return "QRKIT_ENOTCONV";
+    case QRKIT_EUNSUPPORTED: return "QRKIT_EUNSUPPORTED";
+    case QRKIT_ESTATE: return "QRKIT_ESTATE";
+    default: return "QRKIT_UNKNOWN";
+  }
+}
+
+qrkit_status qrkit_create(qrkit_ctx** out, int device, void* stream, int precision) {
+  if (!out) return QRKIT_EINVAL;
+  *out = nullptr;
+  if (precision < QRKIT_FP64 || precision > QRKIT_FP32) return QRKIT_EINVAL;
+  qrkit_ctx* ctx = new (std::nothrow) qrkit_ctx();
+  if (!ctx) return QRKIT_ENOMEM;
+  ctx->device = device;
+  ctx->stream = (cudaStream_t)stream;
+  ctx->precision = precision;
+  cudaError_t e = cudaSetDevice(device);
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&ctx->num_sms, cudaDevAttrMultiProcessorCount, device);
+  int optin = 0;
+  if (e == cudaSuccess) e = cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, device);
+  ctx->max_smem_optin = (size_t)optin;
+  if (e == cudaSuccess) e = cudaMalloc(&ctx->d_status, sizeof(int));
+  if (e == cudaSuccess) e = cudaMemset(ctx->d_status, 0, sizeof(int));
+  if (e != cudaSuccess) {
+    if (ctx->d_status) cudaFree(ctx->d_status);
+    delete ctx;
+    return e == cudaErrorMemoryAllocation ? QRKIT_ENOMEM : QRKIT_ECUDA;
+  }
+  *out = ctx;
+  return QRKIT_OK;
+}
+
+void qrkit_destroy(qrkit_ctx* ctx) {
+  if (!ctx) return;
+  cudaSetDevice(ctx->device);
+  if (ctx->stream) cudaStreamSynchronize(ctx->stream);
+  else cudaDeviceSynchronize();
+  Plan& P = ctx->plan;
+  release(P.d_n);
+  release(P.d_m);
+  release(P.d_tile_block);
+  release(P.d_tile_val);
+  release(P.d_tile_row);
+  release(P.d_tile_col);
+  release(ctx->ws.factor);
+  release(ctx->ws.tau);
+  if (ctx->d_status) cudaFree(ctx->d_status);
+  delete ctx;
+}
+
+const char* qrkit_last_error(const qrkit_ctx* ctx) {
+  return ctx ? ctx->last_error.c_str() : "null context";
+}
+
+qrkit_status qrkit_plan(qrkit_ctx* ctx, const qrkit_structure* s) {
+  if (!ctx) return QRKIT_EINVAL;
+  if (!s) return fail(ctx, QRKIT_EINVAL, "null structure");
+  QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  release_plan(ctx->plan);
+  ctx->factored = false;
+  if (s->kind == QRKIT_STRUCT_BLOCKS) return plan_blocks(ctx, s);
+  if (s->kind == QRKIT_STRUCT_BANDED)
+    return fail(ctx, QRKIT_EUNSUPPORTED, "banded structures are not available in this build");
+  return fail(ctx, QRKIT_EINVAL, "unknown structure kind");
+}
+
+qrkit_status qrkit_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
+                                double lambda, void* p, void* qtb, int refine_steps) {
+  if (!ctx) return QRKIT_EINVAL;
+  if (!ctx->plan.valid) return fail(ctx, QRKIT_ESTATE, "qrkit_factor_solve before qrkit_plan");
+  const Plan& P = ctx->plan;
+  if (P.s.kind != QRKIT_STRUCT_BLOCKS || P.s.coupled_kind != QRKIT_COUPLED_NONE)
+    return fail(ctx, QRKIT_EINVAL, "qrkit_factor_solve needs a block-diagonal structure");
+  if (!J || !b || !p) return fail(ctx, QRKIT_EINVAL, "J, b and p are required");
+  if (!(lambda >= 0.0)) return fail(ctx, QRKIT_EINVAL, "lambda must be >= 0");
+  if (lambda > 0.0)
+    return fail(ctx, QRKIT_EUNSUPPORTED, "damping rows on the fused block path are not available yet");
+  if (refine_steps < 0 || refine_steps > 8) return fail(ctx, QRKIT_EINVAL, "refine_steps must be in [0, 8]");
+  for (int64_t i = 0; i < P.K; ++i)
+    if (P.n[i] < P.m[i])
+      return fail(ctx, QRKIT_EINVAL, "block " + std::to_string(i) + " has fewer rows than columns and lambda = 0");
+  QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  qrkit_status st = launch_block_solve(ctx, J, b, D, p, qtb, refine_steps);
+  if (st == QRKIT_OK) ctx->factored = true;
+  return st;
+}
+
+qrkit_status qrkit_get_factor(qrkit_ctx* ctx, void* factor_out, void* tau_out) {
+  if (!ctx) return QRKIT_EINVAL;
+  if (!ctx->factored) return fail(ctx, QRKIT_ESTATE, "no factor stored");
+  const size_t es = elem_size(ctx);
+  if (factor_out)
+    QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(factor_out, ctx->ws.factor.ptr, (size_t)ctx->plan.values * es,
+                                        cudaMemcpyDeviceToDevice, ctx->stream));
+  if (tau_out)
+    QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(tau_out, ctx->ws.tau.ptr, (size_t)ctx->plan.cols * es,
+                                        cudaMemcpyDeviceToDevice, ctx->stream));
+  return QRKIT_OK;
+}
+
+qrkit_status qrkit_sync_status(qrkit_ctx* ctx) {
+  if (!ctx) return QRKIT_EINVAL;
+  QRKIT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  int h = 0;
+  QRKIT_CUDA_TRY(ctx, cudaMemcpy(&h, ctx->d_status, sizeof(int), cudaMemcpyDeviceToHost));
+  QRKIT_CUDA_TRY(ctx, cudaMemset(ctx->d_status, 0, sizeof(int)));
+  if (h != 0) return fail(ctx, (qrkit_status)h, std::string("device reported ") + qrkit_status_string(h));
+  return QRKIT_OK;
+}
+
+int64_t qrkit_launch_count(const qrkit_ctx* ctx) { return ctx ? ctx->launches : 0; }
+
+}  // extern "C"

@@ -1,0 +1,164 @@
+"""Python binding of the C-ABI library libqrkit.so (argument marshalling only).
+
+Every numerical step runs in the library's CUDA kernels; this module only checks tensor
+dtypes/devices, passes raw device pointers and the CUDA stream, and turns status codes
+into exceptions.  If the library is missing it raises: there is no fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_PKG, "libqrkit.so")
+
+FP64, FP32_REFINED, FP32 = 0, 1, 2
+PRECISION = {"fp64": FP64, "fp32_refined": FP32_REFINED, "fp32": FP32}
+STRUCT_BLOCKS, STRUCT_BANDED = 0, 1
+COUPLED_NONE, COUPLED_DENSE, COUPLED_WINDOW = 0, 1, 2
+
+STATUS = {0: "QRKIT_OK", 1: "QRKIT_EINVAL", 2: "QRKIT_ENOMEM", 3: "QRKIT_ECUDA",
+          4: "QRKIT_ESINGULAR", 5: "QRKIT_ENONFINITE", 6: "QRKIT_ETIMEOUT",
+          7: "QRKIT_ENOTCONV", 8: "QRKIT_EUNSUPPORTED", 9: "QRKIT_ESTATE"}
+
+
+class QRKitError(RuntimeError):
+    def __init__(self, status, msg):
+        super().__init__(f"{STATUS.get(status, status)}: {msg}")
+        self.status = status
+
+
+class Structure(ctypes.Structure):
+    _fields_ = [
+        ("kind", ctypes.c_int32),
+        ("num_blocks", ctypes.c_int64),
+        ("block_rows", ctypes.c_void_p),
+        ("block_cols", ctypes.c_void_p),
+        ("coupled_kind", ctypes.c_int32),
+        ("shared_cols", ctypes.c_int64),
+        ("window", ctypes.c_int32),
+        ("window_start", ctypes.c_void_p),
+        ("rows", ctypes.c_int64),
+        ("cols", ctypes.c_int64),
+        ("rows_per_col", ctypes.c_int32),
+        ("band_window", ctypes.c_int32),
+    ]
+
+
+_VP = ctypes.c_void_p
+_SIGS = {
+    "qrkit_create": (ctypes.c_int, [ctypes.POINTER(_VP), ctypes.c_int, _VP, ctypes.c_int]),
+    "qrkit_destroy": (None, [_VP]),
+    "qrkit_last_error": (ctypes.c_char_p, [_VP]),
+    "qrkit_status_string": (ctypes.c_char_p, [ctypes.c_int]),
+    "qrkit_plan": (ctypes.c_int, [_VP, ctypes.POINTER(Structure)]),
+    "qrkit_factor_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP, ctypes.c_int]),
+    "qrkit_get_factor": (ctypes.c_int, [_VP, _VP, _VP]),
+    "qrkit_sync_status": (ctypes.c_int, [_VP]),
+    "qrkit_launch_count": (ctypes.c_int64, [_VP]),
+}
+
+_lib = None
+
+
+def load(path: str = LIB_PATH):
+    """Load libqrkit.so (raises if it is missing: build it with __graft_entry__.build())."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise ImportError(f"libqrkit.so not found at {path}; build it first (the library has no "
+                          "fallback implementation)")
+    lib = ctypes.CDLL(path)
+    for name, (res, args) in _SIGS.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+def declared_symbols():
+    return list(_SIGS)
+
+
+def _ptr(t):
+    if t is None:
+        return None
+    return ctypes.c_void_p(t.data_ptr())
+
+
+class Context:
+    """A qrkit context bound to one CUDA device and stream."""
+
+    def __init__(self, device: int = 0, stream=None, precision="fp32_refined"):
+        import torch
+        self._torch = torch
+        self.lib = load()
+        self.precision = PRECISION[precision] if isinstance(precision, str) else int(precision)
+        self.dtype = torch.float64 if self.precision == FP64 else torch.float32
+        self.device = torch.device("cuda", device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        self.stream = stream
+        h = _VP()
+        st = self.lib.qrkit_create(ctypes.byref(h), device, _VP(stream.cuda_stream), self.precision)
+        if st != 0:
+            raise QRKitError(st, "qrkit_create failed")
+        self.h = h
+        self._keep = []
+
+    def close(self):
+        if getattr(self, "h", None):
+            self.lib.qrkit_destroy(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st):
+        if st != 0:
+            raise QRKitError(st, self.lib.qrkit_last_error(self.h).decode())
+
+    def _t(self, t, name, allow_none=False):
+        if t is None:
+            if allow_none:
+                return None
+            raise ValueError(f"{name} is required")
+        if t.device != self.device or t.dtype != self.dtype or not t.is_contiguous():
+            raise ValueError(f"{name}: expected a contiguous {self.dtype} tensor on {self.device}")
+        return _ptr(t)
+
+    # ---- structure plan ----
+    def plan_blocks(self, n, m):
+        n = np.ascontiguousarray(n, dtype=np.uint8)
+        m = np.ascontiguousarray(m, dtype=np.uint8)
+        s = Structure()
+        s.kind = STRUCT_BLOCKS
+        s.num_blocks = n.shape[0]
+        s.block_rows = n.ctypes.data
+        s.block_cols = m.ctypes.data
+        s.coupled_kind = COUPLED_NONE
+        self._check(self.lib.qrkit_plan(self.h, ctypes.byref(s)))
+
+    # ---- solves ----
+    def factor_solve(self, J, b, p, qtb=None, D=None, lam=0.0, refine_steps=1):
+        self._check(self.lib.qrkit_factor_solve(
+            self.h, self._t(J, "J"), self._t(b, "b"), self._t(D, "D", True), float(lam),
+            self._t(p, "p"), self._t(qtb, "qtb", True), int(refine_steps)))
+
+    def get_factor(self, factor=None, tau=None):
+        self._check(self.lib.qrkit_get_factor(self.h, self._t(factor, "factor", True),
+                                              self._t(tau, "tau", True)))
+
+    def sync_status(self):
+        self._check(self.lib.qrkit_sync_status(self.h))
+
+    @property
+    def launch_count(self):
+        return int(self.lib.qrkit_launch_count(self.h))
