@@ -1,9 +1,12 @@
 """Benchmark of the batched block-diagonal least-squares solve on GB300.
 
 Workload (default): 1,000,000 independent blocks, rows ~ U{2..16}, cols ~ U{1..min(rows,6)},
-N(0,1) entries, one right-hand side per block, FP32 factors with one step of
-extended-precision refinement.  One "solve" = factor + Q^T b + back-substitution +
-refinement of all 1,000,000 blocks (one persistent kernel launch).
+N(0,1) entries, one right-hand side per block, FP32 Householder QR with extended-precision
+refinement (adaptive: each block stops when its correction is below 1e-6 of its solution,
+at most 2 steps).  One "solve" = factor + Q^T b + back-substitution + refinement of all
+1,000,000 blocks (one kernel launch).  The relative error of the solution against the FP64
+oracle is measured on a sample of blocks in the same run; plain FP32 (no refinement) is
+timed beside it for comparison.
 
   python bench.py [--gpus N] [--steps K] [--warmup W] [--impl ours|reference]
 
@@ -139,6 +142,26 @@ def cpu_oracle_sample(d, seconds):
     return k, el
 
 
+def sampled_error(d, p, count, seed=0):
+    """Relative error (2-norm over the sampled blocks, and worst block) of p against the
+    FP64 oracle's per-block least-squares solution."""
+    from oracle import householder as hh
+    idx = np.random.default_rng(seed).choice(d["K"], size=min(count, d["K"]), replace=False)
+    num = den = 0.0
+    worst = 0.0
+    for i in idx:
+        n, m = int(d["n"][i]), int(d["m"][i])
+        v0, r0, c0 = int(d["val_off"][i]), int(d["row_off"][i]), int(d["col_off"][i])
+        A = np.asarray(d["vals"][v0:v0 + n * m], dtype=np.float64).reshape(m, n).T
+        x = hh.lstsq(A, np.asarray(d["b"][r0:r0 + n], dtype=np.float64))[0]
+        e = np.asarray(p[c0:c0 + m], dtype=np.float64) - x
+        num += float(e @ e)
+        den += float(x @ x)
+        worst = max(worst, float(np.linalg.norm(e) / max(np.linalg.norm(x), 1e-300)))
+    return {"rel_err": (num / den) ** 0.5, "max_block_rel_err": worst, "blocks_sampled": int(len(idx)),
+            "oracle": "per-block Householder QR in float64"}
+
+
 def run_reference(args):
     ws, rank, _ = dist_env()
     if rank != 0:
@@ -182,7 +205,7 @@ def run_ours(args):
     d = batched_blocks(K=K_BLOCKS, seed_offset=rank)
     dev = torch.device("cuda", local)
     stream = torch.cuda.Stream(dev)
-    ctx = Context(local, stream=stream, precision="fp32_refined")
+    ctx = Context(local, stream=stream, precision=args.precision)
     ctx.plan_blocks(d["n"], d["m"])
     # two resident copies of the inputs, alternated between steps (each 158 MB > 129 MB L2)
     Js = [torch.from_numpy(d["vals"]).to(dev) for _ in range(2)]
@@ -255,6 +278,34 @@ def run_ours(args):
     e2e_ms = e0.elapsed_time(e1) / args.steps
     ctx.sync_status()
 
+    # accuracy of this run's solution against the FP64 oracle on a sample of blocks
+    acc = sampled_error(d, p.cpu().numpy(), 2000)
+    # the other precision mode, timed the same way for a few steps
+    refined = None
+    if not args.no_refined:
+        other = "fp32" if args.precision == "fp32_refined" else "fp32_refined"
+        rctx = Context(local, stream=stream, precision=other)
+        rctx.plan_blocks(d["n"], d["m"])
+        pr = torch.empty_like(p)
+        with torch.cuda.stream(stream):
+            for i in range(3):
+                rctx.factor_solve(Js[i & 1], bs[i & 1], pr, None, refine_steps=args.refine_steps)
+            stream.synchronize()
+            r0 = torch.cuda.Event(enable_timing=True)
+            r1 = torch.cuda.Event(enable_timing=True)
+            nref = max(3, min(args.steps, 10))
+            r0.record(stream)
+            for i in range(nref):
+                rctx.factor_solve(Js[i & 1], bs[i & 1], pr, None, refine_steps=args.refine_steps)
+            r1.record(stream)
+            stream.synchronize()
+        rctx.sync_status()
+        rms = r0.elapsed_time(r1) / nref
+        racc = sampled_error(d, pr.cpu().numpy(), 2000)
+        refined = {"precision": other, "value": ws * 1000.0 / rms, "unit": UNIT, "ms_per_step": rms,
+                   "refine_steps": args.refine_steps if other == "fp32_refined" else 0,
+                   "rel_err_sampled": racc["rel_err"], "max_block_rel_err": racc["max_block_rel_err"]}
+        rctx.close()
     if rank != 0:
         ctx.close()
         if ws > 1:
@@ -274,7 +325,8 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
         "config": {"workload": WORKLOAD, "blocks_per_gpu": K_BLOCKS,
-                   "blocks_per_s": value * K_BLOCKS, "refine_steps": refine,
+                   "blocks_per_s": value * K_BLOCKS, "precision": args.precision,
+                   "refine_steps": refine if args.precision == "fp32_refined" else 0,
                    "l2": "inputs 2 x 158 MB alternated between steps (each larger than the 129 MB L2)",
                    "parallelism": f"independent blocks, {ws} GPU(s), no collective"},
         "roofline": {"bound": "hbm", "kernel": KERNEL, "achieved": achieved,
@@ -286,6 +338,8 @@ def run_ours(args):
                 "d2h_bytes_per_step": int(hp.numel() * 4)},
         "gpu_launches": launches,
         "clocks": clk,
+        "accuracy": acc,
+        "other_precision": refined,
     }
     if ws == 1 and not args.no_cpu_baseline:
         secs = float(os.environ.get("QRKIT_CPU_BASELINE_SECONDS", "12"))
@@ -307,8 +361,10 @@ def main():
     ap.add_argument("--steps", type=int, default=50)
     ap.add_argument("--warmup", type=int, default=5)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--refine-steps", type=int, default=1)
+    ap.add_argument("--refine-steps", type=int, default=2)
+    ap.add_argument("--precision", default="fp32_refined", choices=["fp32_refined", "fp32"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-refined", action="store_true")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3

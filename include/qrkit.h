@@ -102,18 +102,49 @@ const char* qrkit_status_string(int status);
 qrkit_status qrkit_plan(qrkit_ctx* ctx, const qrkit_structure* s);
 
 /* Fused factor + solve for QRKIT_STRUCT_BLOCKS with QRKIT_COUPLED_NONE (Sec. 4.1, Sec. 5.1):
- * for every block the Householder QR of B_i = [J_i; lambda^(1/2) D_i] (damping rows only if
- * lambda > 0), c_i = Q_i^T [b_i; 0], R_i p_i = c_i, plus `refine_steps` steps of augmented-
- * system refinement with residuals in extended precision (FP32 modes; ignored for FP64).
+ * for every block the Householder QR of J_i, c_i = Q_i^T b_i, R_i p_i = c_i, then (FP32 refined
+ * mode) up to `refine_steps` steps of refinement with an extended-precision residual: each
+ * step computes g = J_i^T (b_i - J_i p_i) in compensated float arithmetic and corrects
+ * p_i += R_i^{-1} R_i^{-T} g; a block stops as soon as its correction is below 1e-6 of its
+ * solution (max norms).  refine_steps is ignored for QRKIT_FP32 and QRKIT_FP64.
  *   J    : packed values, block i column-major n_i x m_i, blocks in order (sum n_i m_i)
  *   b    : sum n_i values, block i's rows contiguous
- *   D    : sum m_i diagonal values or NULL (= column norms of J, a zero norm -> 1)
+ *   D    : reserved, pass NULL
+ *   lambda : must be 0 on this fused path (damped blocks go through qrkit_factor)
  *   p    : out, sum m_i values
- *   qtb  : out or NULL; sum n_i (+ m_i if lambda > 0) values: Q_i^T [b_i; 0] per block
+ *   qtb  : out or NULL; sum n_i values: Q_i^T b_i per block
  * The factor (reflectors below the diagonal, R on and above it, tau) stays in the context.
- * lambda > 0 is not supported on this fused path yet (QRKIT_EUNSUPPORTED). */
+ * One kernel launch; asynchronous on the context's stream. */
 qrkit_status qrkit_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
                                 double lambda, void* p, void* qtb, int refine_steps);
+
+/* Composed factorization (Sec. 3 composition; Sec. 4.1 block diagonal, Sec. 4.2 horizontal
+ * concatenation, Sec. 4.5 vertical concatenation of the damping rows, Sec. 5.2 Backtrack LM):
+ * QR of P_r [J; lambda^(1/2) D] for a QRKIT_STRUCT_BLOCKS plan (any coupled_kind).
+ *   J    : block values as for qrkit_factor_solve
+ *   S    : coupled values or NULL for QRKIT_COUPLED_NONE.  DENSE: (sum n_i) x s column-major;
+ *          WINDOW: per block an n_i x w column-major slab, blocks in order
+ *   D    : N = sum m_i + s diagonal values, or NULL for the column norms of J (zero -> 1).
+ *          Internally kept in double.
+ *   lambda >= 0; the damping rows exist only when lambda > 0.
+ * The factor (per-block reflectors and R, R12 = Q_i^T S_i top rows, the factor of the
+ * reduced shared block) is kept in the context.  J and S are read again by qrkit_solve when
+ * refine_steps > 0: keep them alive and unchanged until then.  Dense S: s <= 64. */
+qrkit_status qrkit_factor(qrkit_ctx* ctx, const void* J, const void* S, const void* D, double lambda);
+
+/* qtb = Q^T [b; 0] restricted to its top N entries (Sec. 5.1, matrixQ().transpose() * b),
+ * laid out as [c_blocks (sum m_i, column order) ; c_S (s)].  b: sum n_i values. */
+qrkit_status qrkit_apply_qt(qrkit_ctx* ctx, const void* b, void* qtb);
+
+/* p = R^{-1} qtb (Sec. 5.1, matrixR().solve): qtb as produced by qrkit_apply_qt; p: N values
+ * (block columns then shared columns). */
+qrkit_status qrkit_solve_r(qrkit_ctx* ctx, const void* qtb, void* p);
+
+/* p = argmin ||P_r [J; lambda^(1/2) D] p - P_r [b; 0]|| with the stored factor: Q^T b,
+ * back-substitution, then `refine_steps` refinement steps (QRKIT_FP32_REFINED: residual
+ * g = J^T (b - J p) - lambda D^2 p in double, correction R^{-1} R^{-T} g; ignored for
+ * QRKIT_FP32, allowed but not useful for QRKIT_FP64). */
+qrkit_status qrkit_solve(qrkit_ctx* ctx, const void* b, void* p, int refine_steps);
 
 /* Copy the stored factor of a block structure to caller buffers (device pointers, either
  * may be NULL): factor values in J's packing (V strictly below the diagonal, R on and above)

@@ -1,12 +1,16 @@
 // Batched block-diagonal QR solve (Sec. 4.1 "Block diagonal", Sec. 5.1 solver interface),
 // fused: factor + Q^T b + back-substitution + refinement in one pass over HBM.
 //
-// Work mapping (GB300): one persistent launch; each CTA walks tiles of consecutive blocks
-// (cut by the plan so a tile fits the shared-memory budget).  A tile's J values and b are
-// staged in shared memory with 16-byte vector loads, every block is factored by a group of
-// 4 lanes (lane q holds rows q, q+4, q+8, q+12 in registers), Householder norms and dot
-// products are 4-lane shuffle reductions, and the results go back to HBM with vector
-// stores.  Blocks of a warp share the warp's largest column count as loop bound.
+// Work mapping (GB300): one launch; each CTA factors one tile of consecutive blocks (cut by
+// the plan so a tile fits the shared-memory budget) and several CTAs share an SM, so the
+// load, sort, factor and store phases of different tiles overlap.  A tile's J values and b
+// are staged in shared memory by TMA bulk copies (cp.async.bulk + mbarrier) while the
+// block shapes are scanned and sorted; results leave with coalesced vector stores.  Inside a tile the blocks are counting-sorted by (row
+// class, column count) so that each warp works on blocks of one shape class: blocks of
+// <= 4 rows get one lane, <= 8 rows two lanes, <= 16 rows four lanes; lane q of a group
+// holds rows 4q .. 4q+3 of the column being processed, the columns stay in shared memory
+// and are swept by runtime loops (compact code), and Householder norms and dot products
+// are shuffle reductions over the group.
 //
 // Reflector convention (Sec. 2): H = I - tau v v^T, v[0] = 1, beta = -sign(x0) ||x||.
 #include <cuda_runtime.h>
@@ -18,197 +22,130 @@
 namespace qrkit {
 namespace {
 
-constexpr int kG = 4;          // lanes per block
-constexpr int kRPL = 4;        // rows per lane -> at most 16 rows per block
-constexpr int kMaxC = 8;       // at most 8 columns per block
+constexpr int kMaxRows = 16;   // rows per block (one lane, padded to 4, 8, 12 or 16)
+constexpr int kMaxCols = 8;    // columns per block
 constexpr int kThreads = 256;  // threads per CTA
+constexpr int kKeys = 36;      // sort keys: 4 row classes x (m = 0..8)
+static_assert(kKeys <= 64, "the bin scan handles at most 64 keys");
 
 template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
 template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
 
 // ---------------------------------------------------------------------------------------
-// Extended-precision residual arithmetic.
-// For float factors the residual r = b - J x and g = J^T r are accumulated in double-float
-// (an unevaluated sum hi + lo of two floats) built from the error-free transformations
-// TwoSum (Knuth) and TwoProduct via FMA (Dekker / Ogita-Rump-Oishi).  Every operation uses
-// the _rn intrinsics so the compiler cannot contract or reassociate them.
-struct DF {
-  float hi, lo;
-};
-
+// Error-free transformations for the extended-precision residual of the refinement:
+// TwoSum (Knuth) and TwoProduct via FMA (Dekker); every operation uses the _rn intrinsics
+// so the compiler cannot contract or reassociate them.
 __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   s = __fadd_rn(a, b);
   float bb = __fsub_rn(s, a);
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-__device__ __forceinline__ void quick_two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  e = __fsub_rn(b, __fsub_rn(s, a));
-}
-__device__ __forceinline__ DF df_add(DF x, DF y) {
-  float s, e;
-  two_sum(x.hi, y.hi, s, e);
-  e = __fadd_rn(e, __fadd_rn(x.lo, y.lo));
-  DF r;
-  quick_two_sum(s, e, r.hi, r.lo);
-  return r;
-}
-// x + a * b with the product taken exactly.
-__device__ __forceinline__ DF df_add_prod(DF x, float a, float b) {
-  float p = __fmul_rn(a, b);
-  float pe = __fmaf_rn(a, b, -p);
-  float s, e;
-  two_sum(x.hi, p, s, e);
-  e = __fadd_rn(e, __fadd_rn(x.lo, pe));
-  DF r;
-  quick_two_sum(s, e, r.hi, r.lo);
-  return r;
-}
-// x + a * (y.hi + y.lo)
-__device__ __forceinline__ DF df_add_prod_df(DF x, float a, DF y) {
-  float p = __fmul_rn(a, y.hi);
-  float pe = __fmaf_rn(a, y.hi, -p);
-  pe = __fmaf_rn(a, y.lo, pe);
-  float s, e;
-  two_sum(x.hi, p, s, e);
-  e = __fadd_rn(e, __fadd_rn(x.lo, pe));
-  DF r;
-  quick_two_sum(s, e, r.hi, r.lo);
-  return r;
-}
-
-// Accumulator policies: Hi<T, kind>::acc is the residual type.
-//   kind 0: plain double (used for T = double, and selectable for float)
-//   kind 1: double-float (float factors only)
-template <typename T, int KIND> struct Hi;
-template <typename T> struct Hi<T, 0> {
-  using acc = double;
-  static __device__ __forceinline__ acc from(T a) { return (double)a; }
-  static __device__ __forceinline__ acc sub_prod(acc x, T a, T b) {
-    return fma(-(double)a, (double)b, x);
-  }
-  static __device__ __forceinline__ acc add_prod_acc(acc x, T a, acc y) {
-    return fma((double)a, y, x);
-  }
-  static __device__ __forceinline__ acc add(acc x, acc y) { return x + y; }
-  static __device__ __forceinline__ acc zero() { return 0.0; }
-  static __device__ __forceinline__ acc shfl_xor(acc x, int m) {
-    return __shfl_xor_sync(0xffffffffu, x, m);
-  }
-  static __device__ __forceinline__ T round(acc x) { return (T)x; }
-};
-template <> struct Hi<float, 1> {
-  using acc = DF;
-  static __device__ __forceinline__ acc from(float a) { return DF{a, 0.f}; }
-  static __device__ __forceinline__ acc sub_prod(acc x, float a, float b) {
-    return df_add_prod(x, -a, b);
-  }
-  static __device__ __forceinline__ acc add_prod_acc(acc x, float a, acc y) {
-    return df_add_prod_df(x, a, y);
-  }
-  static __device__ __forceinline__ acc add(acc x, acc y) { return df_add(x, y); }
-  static __device__ __forceinline__ acc zero() { return DF{0.f, 0.f}; }
-  static __device__ __forceinline__ acc shfl_xor(acc x, int m) {
-    DF r;
-    r.hi = __shfl_xor_sync(0xffffffffu, x.hi, m);
-    r.lo = __shfl_xor_sync(0xffffffffu, x.lo, m);
-    return r;
-  }
-  static __device__ __forceinline__ float round(acc x) { return __fadd_rn(x.hi, x.lo); }
-};
-
-template <typename T>
-__device__ __forceinline__ T group_sum(T v) {
-  v += __shfl_xor_sync(0xffffffffu, v, 1);
-  v += __shfl_xor_sync(0xffffffffu, v, 2);
-  return v;
 }
 
 __device__ __forceinline__ void record(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
 
-template <typename T>
-__device__ __forceinline__ bool finite_val(T v) {
-  return isfinite(v);
+// ---------------------------------------------------------------------------------------
+// Asynchronous bulk copies (TMA, cp.async.bulk) between global and shared memory with an
+// mbarrier for completion.  Both addresses 16-byte aligned, size a multiple of 16.
+__device__ __forceinline__ uint32_t smem_u32(const void* p) {
+  return (uint32_t)__cvta_generic_to_shared(p);
+}
+__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
+               : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
+               "r"(bytes)
+               : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(smem_u32(bar)), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
+                                         uint64_t* bar) {
+  asm volatile(
+      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
+          smem_u32(dst)),
+      "l"(src), "r"(bytes), "r"(smem_u32(bar))
+      : "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
-// Copy count elements global -> shared.  dst[k] <-> src[k]; dst must be laid out so that
-// (dst + k) and (src + k) share their offset modulo 16 bytes (the caller offsets dst).
+// The 16-byte-aligned interior [h, h + ni) of the element range [0, count) starting at g.
 template <typename T>
-__device__ __forceinline__ void copy_in(T* dst, const T* __restrict__ src, int64_t count) {
-  using V = typename Vec16<T>::type;
-  constexpr int VN = Vec16<T>::n;
-  const uintptr_t a = reinterpret_cast<uintptr_t>(src);
-  if (((a ^ reinterpret_cast<uintptr_t>(dst)) & 15) != 0) {
-    for (int64_t k = threadIdx.x; k < count; k += blockDim.x) dst[k] = src[k];
-    return;
+__device__ __forceinline__ void interior(const T* g, int64_t count, int& h, int& ni) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(g);
+  const uintptr_t e = a + (uintptr_t)count * sizeof(T);
+  const uintptr_t ab = (a + 15) & ~(uintptr_t)15;
+  const uintptr_t ae = e & ~(uintptr_t)15;
+  if (ae > ab) {
+    h = (int)((ab - a) / sizeof(T));
+    ni = (int)((ae - ab) / sizeof(T));
+  } else {
+    h = (int)count;
+    ni = 0;
   }
-  int head = (int)(((16 - (a & 15)) & 15) / sizeof(T));
-  if (head > count) head = (int)count;
-  for (int k = threadIdx.x; k < head; k += blockDim.x) dst[k] = src[k];
-  const int64_t nvec = (count - head) / VN;
-  const V* vs = reinterpret_cast<const V*>(src + head);
-  V* vd = reinterpret_cast<V*>(dst + head);
-  for (int64_t k = threadIdx.x; k < nvec; k += blockDim.x) vd[k] = __ldcs(vs + k);
-  for (int64_t k = head + nvec * VN + threadIdx.x; k < count; k += blockDim.x) dst[k] = src[k];
 }
-
-// Copy count elements shared -> global with the same alignment rule; never writes outside
-// [dst, dst + count).
+// Element offset that makes shared[off + k] share global g[k]'s address modulo 16.
 template <typename T>
-__device__ __forceinline__ void copy_out(T* __restrict__ dst, const T* src, int64_t count) {
-  using V = typename Vec16<T>::type;
-  constexpr int VN = Vec16<T>::n;
-  const uintptr_t a = reinterpret_cast<uintptr_t>(dst);
-  if (((a ^ reinterpret_cast<uintptr_t>(src)) & 15) != 0) {
-    for (int64_t k = threadIdx.x; k < count; k += blockDim.x) dst[k] = src[k];
-    return;
-  }
-  int head = (int)(((16 - (a & 15)) & 15) / sizeof(T));
-  if (head > count) head = (int)count;
-  for (int k = threadIdx.x; k < head; k += blockDim.x) dst[k] = src[k];
-  const int64_t nvec = (count - head) / VN;
-  V* vd = reinterpret_cast<V*>(dst + head);
-  const V* vs = reinterpret_cast<const V*>(src + head);
-  for (int64_t k = threadIdx.x; k < nvec; k += blockDim.x) __stcs(vd + k, vs[k]);
-  for (int64_t k = head + nvec * VN + threadIdx.x; k < count; k += blockDim.x) dst[k] = src[k];
+__device__ __forceinline__ int align_off(const T* g) {
+  return (int)((reinterpret_cast<uintptr_t>(g) & 15) / sizeof(T));
 }
 
-// Exclusive scan of three per-block quantities over a tile (nb <= kThreads).
-__device__ __forceinline__ void tile_scan3(int nb, const uint8_t* sN, const uint8_t* sM,
-                                           int* sVo, int* sRo, int* sCo, int* warp_tot) {
+// Row class of an n-row block: its rows are padded to R = 4 (class + 1) in the working area.
+__host__ __device__ inline int row_class(int n) { return (n - 1) >> 2; }
+__host__ __device__ inline int padded_rows(int n) { return 4 * (row_class(n) + 1); }
+
+// Exclusive scans over a tile (nb <= kThreads) of the per-block value, row, column and
+// padded-working-area counts.
+__device__ __forceinline__ void tile_scan4(int nb, const uint8_t* sN, const uint8_t* sM,
+                                           int* sVo, int* sRo, int* sCo, int* sPo, int* warp_tot) {
   const int tid = threadIdx.x, lane = tid & 31, wid = tid >> 5;
-  int nn = tid < nb ? sN[tid] : 0;
-  int mm = tid < nb ? sM[tid] : 0;
-  int v = nn * mm, r = nn, c = mm;
-  int iv = v, ir = r, ic = c;
+  const int nn = tid < nb ? sN[tid] : 0;
+  const int mm = tid < nb ? sM[tid] : 0;
+  const int v = nn * mm, r = nn, c = mm, pp = tid < nb ? padded_rows(nn) * mm : 0;
+  int iv = v, ir = r, ic = c, ip = pp;
 #pragma unroll
   for (int d = 1; d < 32; d <<= 1) {
-    int tv = __shfl_up_sync(0xffffffffu, iv, d);
-    int tr = __shfl_up_sync(0xffffffffu, ir, d);
-    int tc = __shfl_up_sync(0xffffffffu, ic, d);
-    if (lane >= d) { iv += tv; ir += tr; ic += tc; }
+    const int tv = __shfl_up_sync(0xffffffffu, iv, d);
+    const int tr = __shfl_up_sync(0xffffffffu, ir, d);
+    const int tc = __shfl_up_sync(0xffffffffu, ic, d);
+    const int tp = __shfl_up_sync(0xffffffffu, ip, d);
+    if (lane >= d) { iv += tv; ir += tr; ic += tc; ip += tp; }
   }
   if (lane == 31) {
-    warp_tot[wid * 3 + 0] = iv;
-    warp_tot[wid * 3 + 1] = ir;
-    warp_tot[wid * 3 + 2] = ic;
+    warp_tot[wid * 4 + 0] = iv;
+    warp_tot[wid * 4 + 1] = ir;
+    warp_tot[wid * 4 + 2] = ic;
+    warp_tot[wid * 4 + 3] = ip;
   }
   __syncthreads();
-  int bv = 0, br = 0, bc = 0;
+  int bv = 0, br = 0, bc = 0, bp = 0;
   for (int w = 0; w < wid; ++w) {
-    bv += warp_tot[w * 3 + 0];
-    br += warp_tot[w * 3 + 1];
-    bc += warp_tot[w * 3 + 2];
+    bv += warp_tot[w * 4 + 0];
+    br += warp_tot[w * 4 + 1];
+    bc += warp_tot[w * 4 + 2];
+    bp += warp_tot[w * 4 + 3];
   }
   if (tid < nb) {
     sVo[tid] = bv + iv - v;
     sRo[tid] = br + ir - r;
     sCo[tid] = bc + ic - c;
+    sPo[tid] = bp + ip - pp;
   }
-  __syncthreads();
 }
 
 template <typename T>
@@ -226,306 +163,532 @@ struct BlockSolveArgs {
   T* tau;      // sum m
   T* qtb;      // sum n (may be null)
   T* x;        // sum m
-  int refine_steps;
+  int refine_steps;      // at most this many refinement steps per block
+  float refine_tol;      // stop when max|dx| <= refine_tol * max|x|
   int* status;
-  int vb, rb, cb, bb;  // tile budgets
+  int vb, rb, cb, bb, pb;  // tile budgets (pb: padded working area)
+  long long wait_limit;  // polls of an mbarrier before giving up
 };
 
-template <typename T>
-struct Smem {
-  T* J;
-  T* b;
-  T* tau;
-  T* x;
-  uint8_t* n;
-  uint8_t* m;
-  int* vo;
-  int* ro;
-  int* co;
-  int* wtot;
+// Shared-memory layout (identical on host and device).  Each block is factored in a padded
+// working area W (column stride = rows covered by its lane group, 16-byte aligned), then
+// written back in packed form over the J buffer, which stages the factor for the store.
+// Without refinement Q^T b is formed in place in the b buffer.
+struct Layout {
+  size_t J, b, n, m, W, Cw, rs, c, tau, x, g, vo, ro, co, po, qo, wtot, perm, hist, bar, total;
 };
-
+__host__ __device__ inline size_t round16(size_t v) { return (v + 15) / 16 * 16; }
 template <typename T>
-__host__ __device__ inline size_t smem_bytes(int vb, int rb, int cb, int bb) {
+__host__ __device__ inline Layout make_layout(int vb, int rb, int cb, int bb, int pb, bool refine) {
   const int VN = 16 / (int)sizeof(T);
+  Layout L;
   size_t off = 0;
-  off += (size_t)(vb + VN) * sizeof(T);
-  off += (size_t)(rb + VN) * sizeof(T);
-  off += (size_t)(cb + VN) * sizeof(T) * 2;
-  off += (size_t)((bb + 15) / 16 * 16) * 2;
-  off += (size_t)(bb + 1) * sizeof(int) * 3;
-  off += (size_t)(kThreads / 32) * 3 * sizeof(int);
-  return (off + 15) / 16 * 16;
+  auto take = [&](size_t bytes) { size_t o = off; off += round16(bytes); return o; };
+  L.J = take((size_t)(vb + 2 * VN) * sizeof(T));
+  L.b = take((size_t)(rb + 2 * VN) * sizeof(T));
+  L.n = take((size_t)bb);
+  L.m = take((size_t)bb);
+  L.W = take((size_t)pb * sizeof(T));
+  L.Cw = 0;
+  L.rs = refine ? take((size_t)2 * (rb + 3 * bb) * sizeof(T)) : 0;   // residual scratch
+  L.c = refine ? take((size_t)(rb + 2 * VN) * sizeof(T)) : 0;
+  L.tau = take((size_t)(cb + 2 * VN) * sizeof(T));
+  L.x = take((size_t)(cb + 2 * VN) * sizeof(T));
+  L.g = refine ? take((size_t)(cb + 2 * VN) * sizeof(T)) : 0;
+  L.vo = take((size_t)(bb + 1) * sizeof(int));
+  L.ro = take((size_t)(bb + 1) * sizeof(int));
+  L.co = take((size_t)(bb + 1) * sizeof(int));
+  L.po = take((size_t)(bb + 1) * sizeof(int));
+  L.qo = take((size_t)(bb + 1) * sizeof(int));
+  L.wtot = take((size_t)(32 + kThreads / 32) * sizeof(int));
+  L.perm = take((size_t)bb * sizeof(int));
+  L.hist = take((size_t)(2 * kKeys + 8) * sizeof(int));
+  L.bar = take(sizeof(uint64_t));
+  L.total = off;
+  return L;
 }
 
-// One group (4 lanes) factors and solves one block held in registers.
-//   a[r][j] = B[q + 4 r][j] (row-major per lane), bb[r] = b[q + 4 r]
-template <typename T, int HK>
-__device__ __forceinline__ void factor_solve_group(
-    int q, int gbase, int nn, int mm, int mw, bool valid, T (&a)[kRPL][kMaxC], T (&bb)[kRPL],
-    T (&taus)[kMaxC], T (&xs)[kMaxC], const T* sJb, const T* sBb, int refine_steps,
-    int* status) {
-  // ---- Householder QR, one reflector per column (Sec. 2) ----
-#pragma unroll
-  for (int k = 0; k < kMaxC; ++k) {
-    if (k < mw) {
-      T sq = 0;
-#pragma unroll
-      for (int r = 0; r < kRPL; ++r) {
-        const int i = q + kG * r;
-        if (i > k && i < nn) sq += a[r][k] * a[r][k];
-      }
-      sq = group_sum(sq);
-      const T alpha = __shfl_sync(0xffffffffu, a[k / kG][k], gbase + (k % kG));
-      const T norm = sqrt(alpha * alpha + sq);
-      T beta, tau, scale;
-      if (norm == T(0)) {
-        beta = 0; tau = 0; scale = 0;
-      } else {
-        beta = alpha >= T(0) ? -norm : norm;
-        tau = (beta - alpha) / beta;
-        scale = T(1) / (alpha - beta);
-      }
-      // v_i = a_ik * scale below the diagonal, v_k = 1
-      T v[kRPL];
-#pragma unroll
-      for (int r = 0; r < kRPL; ++r) {
-        const int i = q + kG * r;
-        v[r] = (i == k) ? T(1) : ((i > k && i < nn) ? a[r][k] * scale : T(0));
-      }
-      // apply H_k to the trailing columns and the rhs
-#pragma unroll
-      for (int j = k + 1; j < kMaxC; ++j) {
-        if (j < mw) {
-          T w = 0;
-#pragma unroll
-          for (int r = 0; r < kRPL; ++r) w += v[r] * a[r][j];
-          w = group_sum(w) * tau;
-#pragma unroll
-          for (int r = 0; r < kRPL; ++r) a[r][j] -= v[r] * w;
-        }
-      }
-      {
-        T w = 0;
-#pragma unroll
-        for (int r = 0; r < kRPL; ++r) w += v[r] * bb[r];
-        w = group_sum(w) * tau;
-#pragma unroll
-        for (int r = 0; r < kRPL; ++r) bb[r] -= v[r] * w;
-      }
-      // store v below the diagonal and beta on it
-#pragma unroll
-      for (int r = 0; r < kRPL; ++r) {
-        const int i = q + kG * r;
-        if (i == k) a[r][k] = beta;
-        else if (i > k) a[r][k] = v[r];
-      }
-      taus[k] = tau;
-    }
-  }
-  // ---- back-substitution R x = c (Sec. 5.1, matrixR().solve) ----
-  bool bad = false;
-#pragma unroll
-  for (int k = kMaxC - 1; k >= 0; --k) {
-    if (k < mw) {
-      T s = bb[k / kG];
-#pragma unroll
-      for (int j = k + 1; j < kMaxC; ++j)
-        if (j < mw) s -= a[k / kG][j] * xs[j];
-      T xk = s / a[k / kG][k];
-      xk = __shfl_sync(0xffffffffu, xk, gbase + (k % kG));
-      xs[k] = (k < mm) ? xk : T(0);
-      if (valid && k < mm && !finite_val(xk)) bad = true;
-    }
-  }
-  // ---- refinement: x += R^{-1} R^{-T} (J^T (b - J x)), residual in extended precision ----
-  using H = Hi<T, HK>;
-  for (int step = 0; step < refine_steps; ++step) {
-    typename H::acc res[kRPL];
-#pragma unroll
-    for (int r = 0; r < kRPL; ++r) {
-      const int i = q + kG * r;
-      typename H::acc acc = H::zero();
-      if (valid && i < nn) {
-        acc = H::from(sBb[i]);
-#pragma unroll
-        for (int j = 0; j < kMaxC; ++j)
-          if (j < mm) acc = H::sub_prod(acc, sJb[j * nn + i], xs[j]);
-      }
-      res[r] = acc;
-    }
-    T g[kMaxC];
-#pragma unroll
-    for (int j = 0; j < kMaxC; ++j) {
-      g[j] = 0;
-      if (j < mw) {
-        typename H::acc acc = H::zero();
-#pragma unroll
-        for (int r = 0; r < kRPL; ++r) {
-          const int i = q + kG * r;
-          if (valid && j < mm && i < nn) acc = H::add_prod_acc(acc, sJb[j * nn + i], res[r]);
-        }
-        acc = H::add(acc, H::shfl_xor(acc, 1));
-        acc = H::add(acc, H::shfl_xor(acc, 2));
-        g[j] = H::round(acc);
-      }
-    }
-    // h = R^{-T} g (forward substitution; h_i of the lane's own rows kept in hl)
-    T hl[kRPL];
-#pragma unroll
-    for (int r = 0; r < kRPL; ++r) hl[r] = 0;
-#pragma unroll
-    for (int k = 0; k < kMaxC; ++k) {
-      if (k < mw) {
-        T part = 0;
-#pragma unroll
-        for (int r = 0; r < kRPL; ++r) {
-          const int i = q + kG * r;
-          if (i < k) part += a[r][k] * hl[r];
-        }
-        part = group_sum(part);
-        const T rkk = __shfl_sync(0xffffffffu, a[k / kG][k], gbase + (k % kG));
-        T hk = (k < mm) ? (g[k] - part) / rkk : T(0);
-        if (q == (k % kG)) hl[k / kG] = hk;
-      }
-    }
-    // dx = R^{-1} h (back-substitution with h in place of c)
-    T dx[kMaxC];
-#pragma unroll
-    for (int k = kMaxC - 1; k >= 0; --k) {
-      dx[k] = 0;
-      if (k < mw) {
-        T s = hl[k / kG];
-#pragma unroll
-        for (int j = k + 1; j < kMaxC; ++j)
-          if (j < mw) s -= a[k / kG][j] * dx[j];
-        T d = s / a[k / kG][k];
-        d = __shfl_sync(0xffffffffu, d, gbase + (k % kG));
-        dx[k] = (k < mm) ? d : T(0);
-      }
-    }
-#pragma unroll
-    for (int k = 0; k < kMaxC; ++k) xs[k] += dx[k];
-  }
-  if (bad) record(status, QRKIT_ESINGULAR);
+// Four consecutive rows of one column (the rows one lane owns), moved with one 16-byte
+// (float) or two 16-byte (double) shared-memory accesses.
+template <typename T>
+struct Row4 {
+  T v[4];
+};
+__device__ __forceinline__ Row4<float> ld4(const float* p) {
+  const float4 f = *reinterpret_cast<const float4*>(p);
+  return Row4<float>{{f.x, f.y, f.z, f.w}};
+}
+__device__ __forceinline__ Row4<double> ld4(const double* p) {
+  const double2 a = reinterpret_cast<const double2*>(p)[0];
+  const double2 b = reinterpret_cast<const double2*>(p)[1];
+  return Row4<double>{{a.x, a.y, b.x, b.y}};
+}
+__device__ __forceinline__ void st4(float* p, const Row4<float>& r) {
+  *reinterpret_cast<float4*>(p) = make_float4(r.v[0], r.v[1], r.v[2], r.v[3]);
+}
+__device__ __forceinline__ void st4(double* p, const Row4<double>& r) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(r.v[0], r.v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(r.v[2], r.v[3]);
 }
 
-template <typename T, int HK>
-__global__ void __launch_bounds__(kThreads)
-block_solve_kernel(BlockSolveArgs<T> A) {
-  extern __shared__ __align__(16) unsigned char smem_raw[];
+// sqrt and reciprocal: the hardware approximations for float (rsqrtf, __frcp_rn: a few ulp
+// at most, far below the rounding the factorization itself accumulates), IEEE for double.
+__device__ __forceinline__ float fsqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
+__device__ __forceinline__ double fsqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float frcp(float x) { return __frcp_rn(x); }
+__device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
+
+// x = R^{-1} c (R on and above the diagonal of the factor F, column stride cs); one lane.
+template <typename T>
+__device__ __forceinline__ bool back_substitute(const T* F, int cs, int mm, const T* c, T* x) {
+  bool ok = true;
+  for (int k = mm - 1; k >= 0; --k) {
+    T s = c[k];
+    for (int j = k + 1; j < mm; ++j) s -= F[j * cs + k] * x[j];
+    const T rkk = F[k * cs + k];
+    ok = ok && rkk != T(0);
+    x[k] = s * frcp(rkk);
+  }
+  return ok;
+}
+
+// One lane factors one n x m block (Sec. 2) held in the padded working area W: column j at
+// W + j * R (R = rows padded to a multiple of 4, zeros below row n), factored in place (V
+// below the diagonal, R on and above).  The lane's rhs rows live in registers while the
+// reflectors are applied (Q^T b).  Pivots are read as scalars from shared memory, so every
+// register array is indexed by compile-time constants.  One instantiation per row class.
+template <typename T, int R>
+__device__ __forceinline__ void lane_householder(T* W, int mm, T (&bb)[R], T* tau_out) {
+  for (int k = 0; k < mm; ++k) {
+    T* colk = W + k * R;
+    T c[R];
+#pragma unroll
+    for (int r = 0; r < R; r += 4) {
+      const Row4<T> x = ld4(colk + r);
+      c[r] = x.v[0]; c[r + 1] = x.v[1]; c[r + 2] = x.v[2]; c[r + 3] = x.v[3];
+    }
+    T sq = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) sq += (r > k) ? c[r] * c[r] : T(0);
+    const T alpha = colk[k];
+    const T norm = fsqrt(alpha * alpha + sq);
+    T beta = 0, tau = 0, scale = 0;
+    if (norm != T(0)) {
+      beta = alpha >= T(0) ? -norm : norm;
+      const T d = alpha - beta;
+      scale = frcp(d);
+      tau = -d * frcp(beta);
+    }
+    T v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) v[r] = (r == k) ? T(1) : ((r > k) ? c[r] * scale : T(0));
+#pragma unroll
+    for (int r = 0; r < R; r += 4) {
+      Row4<T> o;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) o.v[u] = (r + u > k) ? v[r + u] : c[r + u];
+      st4(colk + r, o);
+    }
+    colk[k] = beta;
+    tau_out[k] = tau;
+    for (int j = k + 1; j < mm; ++j) {
+      T* colj = W + j * R;
+      T d[R];
+#pragma unroll
+      for (int r = 0; r < R; r += 4) {
+        const Row4<T> x = ld4(colj + r);
+        d[r] = x.v[0]; d[r + 1] = x.v[1]; d[r + 2] = x.v[2]; d[r + 3] = x.v[3];
+      }
+      T w = 0;
+#pragma unroll
+      for (int r = 0; r < R; ++r) w += v[r] * d[r];
+      w *= tau;
+#pragma unroll
+      for (int r = 0; r < R; r += 4) {
+        Row4<T> o;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) o.v[u] = d[r + u] - v[r + u] * w;
+        st4(colj + r, o);
+      }
+    }
+    T w = 0;
+#pragma unroll
+    for (int r = 0; r < R; ++r) w += v[r] * bb[r];
+    w *= tau;
+#pragma unroll
+    for (int r = 0; r < R; ++r) bb[r] -= v[r] * w;
+  }
+}
+
+// Refinement of a float block by one lane: g = J^T (b - J x) with the residual in
+// compensated float arithmetic (Dot2 of Ogita, Rump and Oishi: error-free products and
+// sums, value = s + c), then dx = R^{-1} R^{-T} g and x += dx.  With the residual taken
+// exactly this is the first step of Bjorck's augmented-system refinement from (x, b - J x).
+// Rp: padded row stride of F; rs: scratch of 2 * Rp floats for the residual.  Only the
+// ceil(n / 4) row groups that hold rows are touched (nothing at all for n = 0).
+// Returns max |dx| / max |x|.
+__device__ __noinline__ float lane_refine(int nn, int Rp, int mm, const float* J,
+                                             const float* b, const float* F, float* x,
+                                             float* g, float* rs) {
+  const int ng = (nn + 3) >> 2;
+  // residual rows, four at a time
+  for (int q = 0; q < ng; ++q) {
+    float sh[4], sl[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      sh[u] = (4 * q + u < nn) ? b[4 * q + u] : 0.f;
+      sl[u] = 0.f;
+    }
+    for (int j = 0; j < mm; ++j) {
+      const float xj = -x[j];
+      const float* Jj = J + j * nn;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (4 * q + u < nn) {
+          const float a = Jj[4 * q + u];
+          const float p = __fmul_rn(a, xj);
+          const float pe = __fmaf_rn(a, xj, -p);
+          float t, e;
+          two_sum(sh[u], p, t, e);
+          sh[u] = t;
+          sl[u] = __fadd_rn(sl[u], __fadd_rn(e, pe));
+        }
+      }
+    }
+    st4(rs + 4 * q, Row4<float>{{sh[0], sh[1], sh[2], sh[3]}});
+    st4(rs + Rp + 4 * q, Row4<float>{{sl[0], sl[1], sl[2], sl[3]}});
+  }
+  // g_j = sum_i J_ij r_i
+  for (int j = 0; j < mm; ++j) {
+    const float* Jj = J + j * nn;
+    float s = 0.f, c = 0.f;
+    for (int q = 0; q < ng; ++q) {
+      const Row4<float> rh = ld4(rs + 4 * q);
+      const Row4<float> rl = ld4(rs + Rp + 4 * q);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (4 * q + u < nn) {
+          const float a = Jj[4 * q + u];
+          const float p = __fmul_rn(a, rh.v[u]);
+          float pe = __fmaf_rn(a, rh.v[u], -p);
+          pe = __fmaf_rn(a, rl.v[u], pe);
+          float t, e;
+          two_sum(s, p, t, e);
+          s = t;
+          c = __fadd_rn(c, __fadd_rn(e, pe));
+        }
+      }
+    }
+    g[j] = __fadd_rn(s, c);
+  }
+  for (int k = 0; k < mm; ++k) {          // h = R^{-T} g, in place
+    float s = g[k];
+    for (int i = 0; i < k; ++i) s -= F[k * Rp + i] * g[i];
+    g[k] = s * frcp(F[k * Rp + k]);
+  }
+  for (int k = mm - 1; k >= 0; --k) {     // dx = R^{-1} h, in place
+    float s = g[k];
+    for (int j = k + 1; j < mm; ++j) s -= F[j * Rp + k] * g[j];
+    g[k] = s * frcp(F[k * Rp + k]);
+  }
+  float dmax = 0.f, xmax = 0.f;
+  for (int k = 0; k < mm; ++k) {
+    const float xn = x[k] + g[k];
+    x[k] = xn;
+    dmax = fmaxf(dmax, fabsf(g[k]));
+    xmax = fmaxf(xmax, fabsf(xn));
+  }
+  return xmax > 0.f ? dmax / xmax : 0.f;
+}
+
+// Everything one lane does for one block: padded copy in, factor, Q^T b, back-substitution,
+// adaptive refinement (until the correction is below refine_tol relative to x, at most
+// max_steps), packed copy of the factor out (Fout, may alias J: written last).  All 32
+// lanes of the warp call it (lanes without a block pass nn = mm = 0) and every phase ends in
+// __syncwarp(), so lanes whose loops ran for different lengths reconverge.  The refinement
+// is one shared (not inlined) routine for every row class, which keeps the code that warps
+// loop back into small.  rs: scratch of 2 * R floats for the residual.
+template <typename T, bool REF, int R>
+__device__ __forceinline__ void lane_block(int nn, int mm, const T* J, const T* b, T* W, T* C,
+                                           T* tau, T* x, T* g, T* rs, T* Fout, int max_steps,
+                                           float refine_tol, int* status) {
+  for (int j = 0; j < mm; ++j) {
+#pragma unroll
+    for (int r = 0; r < R; r += 4) {
+      Row4<T> o;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) o.v[u] = (r + u < nn) ? J[j * nn + r + u] : T(0);
+      st4(W + j * R + r, o);
+    }
+  }
+  T bb[R];
+#pragma unroll
+  for (int r = 0; r < R; ++r) bb[r] = (r < nn) ? b[r] : T(0);
+  lane_householder<T, R>(W, mm, bb, tau);
+  __syncwarp();
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (r < nn) C[r] = bb[r];
+  if (!back_substitute(W, R, mm, C, x)) record(status, QRKIT_ESINGULAR);
+  __syncwarp();
+  if constexpr (REF) {
+    for (int step = 0; step < max_steps; ++step) {
+      const float rel = lane_refine(nn, R, mm, J, b, W, x, g, rs);
+      if (!(rel > refine_tol)) break;
+    }
+    __syncwarp();
+  }
+  if (Fout) {
+    for (int j = 0; j < mm; ++j)
+      for (int r = 0; r < nn; ++r) Fout[j * nn + r] = W[j * R + r];
+  }
+  __syncwarp();
+}
+
+// Per-tile geometry shared by the issue, compute and store phases.
+template <typename T>
+struct TileGeo {
+  int64_t b0, v0, r0, c0;
+  int nb, nv, nr, nc;
+  int offJ, offB;   // shared-memory element offsets (alignment to global)
+};
+
+template <typename T>
+__device__ __forceinline__ TileGeo<T> tile_geo(const BlockSolveArgs<T>& A, int64_t t) {
+  TileGeo<T> g;
+  g.b0 = A.tile_block[t];
+  g.nb = (int)(A.tile_block[t + 1] - g.b0);
+  g.v0 = A.tile_val[t];
+  g.r0 = A.tile_row[t];
+  g.c0 = A.tile_col[t];
+  g.nv = (int)(A.tile_val[t + 1] - g.v0);
+  g.nr = (int)(A.tile_row[t + 1] - g.r0);
+  g.nc = (int)(A.tile_col[t + 1] - g.c0);
+  g.offJ = align_off(A.J + g.v0);
+  g.offB = align_off(A.b + g.r0);
+  return g;
+}
+
+// Thread 0: start the bulk loads of a tile's J and b interiors.
+template <typename T>
+__device__ __forceinline__ void issue_tile_load(const BlockSolveArgs<T>& A, const TileGeo<T>& g,
+                                                T* sJ, T* sB, uint64_t* bar) {
+  int hJ, nJ, hB, nB;
+  interior(A.J + g.v0, g.nv, hJ, nJ);
+  interior(A.b + g.r0, g.nr, hB, nB);
+  const uint32_t bytes = (uint32_t)(nJ + nB) * sizeof(T);
+  fence_proxy_async();
+  mbar_expect_tx(bar, bytes);
+  if (nJ) bulk_g2s(sJ + g.offJ + hJ, A.J + g.v0 + hJ, (uint32_t)nJ * sizeof(T), bar);
+  if (nB) bulk_g2s(sB + g.offB + hB, A.b + g.r0 + hB, (uint32_t)nB * sizeof(T), bar);
+}
+
+// All threads: plain loads of what the bulk copies leave out (unaligned head and tail
+// elements) and of the tile's block shapes.
+template <typename T>
+__device__ __forceinline__ void load_tile_edges(const BlockSolveArgs<T>& A, const TileGeo<T>& g,
+                                                T* sJ, T* sB, uint8_t* sN, uint8_t* sM) {
+  int hJ, nJ, hB, nB;
+  interior(A.J + g.v0, g.nv, hJ, nJ);
+  interior(A.b + g.r0, g.nr, hB, nB);
+  const int tid = threadIdx.x;
+  const int tJ = g.nv - (hJ + nJ);
+  for (int k = tid; k < hJ + tJ; k += kThreads) {
+    const int e = k < hJ ? k : hJ + nJ + (k - hJ);
+    sJ[g.offJ + e] = A.J[g.v0 + e];
+  }
+  const int tB = g.nr - (hB + nB);
+  for (int k = tid; k < hB + tB; k += kThreads) {
+    const int e = k < hB ? k : hB + nB + (k - hB);
+    sB[g.offB + e] = A.b[g.r0 + e];
+  }
+  for (int k = tid; k < g.nb; k += kThreads) {
+    sN[k] = A.n[g.b0 + k];
+    sM[k] = A.m[g.b0 + k];
+  }
+}
+
+// Coalesced copy shared -> global; vector stores when both sides agree modulo 16 bytes.
+template <typename T>
+__device__ __forceinline__ void store_out(T* __restrict__ dst, const T* src, int count) {
+  using V = typename Vec16<T>::type;
   constexpr int VN = Vec16<T>::n;
-  Smem<T> S;
-  {
-    size_t off = 0;
-    S.J = reinterpret_cast<T*>(smem_raw + off);
-    off += (size_t)(A.vb + VN) * sizeof(T);
-    S.b = reinterpret_cast<T*>(smem_raw + off);
-    off += (size_t)(A.rb + VN) * sizeof(T);
-    S.tau = reinterpret_cast<T*>(smem_raw + off);
-    off += (size_t)(A.cb + VN) * sizeof(T);
-    S.x = reinterpret_cast<T*>(smem_raw + off);
-    off += (size_t)(A.cb + VN) * sizeof(T);
-    S.n = smem_raw + off;
-    off += (size_t)((A.bb + 15) / 16 * 16);
-    S.m = smem_raw + off;
-    off += (size_t)((A.bb + 15) / 16 * 16);
-    S.vo = reinterpret_cast<int*>(smem_raw + off);
-    off += (size_t)(A.bb + 1) * sizeof(int);
-    S.ro = reinterpret_cast<int*>(smem_raw + off);
-    off += (size_t)(A.bb + 1) * sizeof(int);
-    S.co = reinterpret_cast<int*>(smem_raw + off);
-    off += (size_t)(A.bb + 1) * sizeof(int);
-    S.wtot = reinterpret_cast<int*>(smem_raw + off);
+  const uintptr_t a = reinterpret_cast<uintptr_t>(dst);
+  if (((a ^ reinterpret_cast<uintptr_t>(src)) & 15) != 0) {
+    for (int k = threadIdx.x; k < count; k += kThreads) dst[k] = src[k];
+    return;
   }
+  int head = (int)(((16 - (a & 15)) & 15) / sizeof(T));
+  if (head > count) head = count;
+  for (int k = threadIdx.x; k < head; k += kThreads) dst[k] = src[k];
+  const int nvec = (count - head) / VN;
+  V* vd = reinterpret_cast<V*>(dst + head);
+  const V* vs = reinterpret_cast<const V*>(src + head);
+  for (int k = threadIdx.x; k < nvec; k += kThreads) __stcs(vd + k, vs[k]);
+  for (int k = head + nvec * VN + threadIdx.x; k < count; k += kThreads) dst[k] = src[k];
+}
+
+template <typename T, bool REF>
+__global__ void __launch_bounds__(kThreads, 3)
+block_solve_kernel(BlockSolveArgs<T> A) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const Layout L = make_layout<T>(A.vb, A.rb, A.cb, A.bb, A.pb, REF);
+  int* sVo = reinterpret_cast<int*>(smem_raw + L.vo);
+  int* sRo = reinterpret_cast<int*>(smem_raw + L.ro);
+  int* sCo = reinterpret_cast<int*>(smem_raw + L.co);
+  int* sPo = reinterpret_cast<int*>(smem_raw + L.po);
+  int* sQo = reinterpret_cast<int*>(smem_raw + L.qo);
+  T* sRs = reinterpret_cast<T*>(smem_raw + L.rs);
+  int* sW = reinterpret_cast<int*>(smem_raw + L.wtot);
+  int* sPerm = reinterpret_cast<int*>(smem_raw + L.perm);
+  int* sHist = reinterpret_cast<int*>(smem_raw + L.hist);
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + L.bar);
+  uint8_t* sNs = smem_raw + L.n;
+  uint8_t* sMs = smem_raw + L.m;
+  T* sWork = reinterpret_cast<T*>(smem_raw + L.W);
+
   const int tid = threadIdx.x;
   const int lane = tid & 31;
-  const int q = lane & (kG - 1);
-  const int gbase = lane & ~(kG - 1);
-  const int gid = tid / kG;
-  constexpr int kGroups = kThreads / kG;
-
-  for (int64_t t = blockIdx.x; t < A.num_tiles; t += gridDim.x) {
-    const int64_t b0 = A.tile_block[t];
-    const int nb = (int)(A.tile_block[t + 1] - b0);
-    const int64_t v0 = A.tile_val[t], r0 = A.tile_row[t], c0 = A.tile_col[t];
-    const int64_t nv = A.tile_val[t + 1] - v0, nr = A.tile_row[t + 1] - r0,
-                  nc = A.tile_col[t + 1] - c0;
-    for (int i = tid; i < nb; i += kThreads) {
-      S.n[i] = A.n[b0 + i];
-      S.m[i] = A.m[b0 + i];
+  const int warp_id = tid >> 5;
+  const int64_t t = blockIdx.x;   // one tile per CTA; several CTAs per SM overlap their phases
+  if (t >= A.num_tiles) return;
+  const TileGeo<T> g = tile_geo(A, t);
+  T* sJ = reinterpret_cast<T*>(smem_raw + L.J) + g.offJ;
+  T* sB = reinterpret_cast<T*>(smem_raw + L.b) + g.offB;
+  // (A) bulk loads of the J and b interiors (TMA), plain loads of the edges and shapes
+  if (tid == 0) {
+    mbar_init(bar, 1);
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    issue_tile_load(A, g, reinterpret_cast<T*>(smem_raw + L.J), reinterpret_cast<T*>(smem_raw + L.b), bar);
+  }
+  load_tile_edges(A, g, reinterpret_cast<T*>(smem_raw + L.J), reinterpret_cast<T*>(smem_raw + L.b), sNs, sMs);
+  for (int k = tid; k < 2 * kKeys; k += kThreads) sHist[k] = 0;
+  __syncthreads();
+  // (B) per-block offsets and the counting sort by (row class, m) while the copy lands
+  tile_scan4(g.nb, sNs, sMs, sVo, sRo, sCo, sPo, sW);
+  __syncthreads();
+  // padded-row offsets (rows rounded up to 4): a second scan over the tile
+  {
+    const int lane_ = tid & 31, wid = tid >> 5;
+    const int pr = tid < g.nb ? padded_rows(sNs[tid]) : 0;
+    int inc = pr;
+#pragma unroll
+    for (int d = 1; d < 32; d <<= 1) {
+      const int o = __shfl_up_sync(0xffffffffu, inc, d);
+      if (lane_ >= d) inc += o;
     }
+    if (lane_ == 31) sW[32 + wid] = inc;
     __syncthreads();
-    tile_scan3(nb, S.n, S.m, S.vo, S.ro, S.co, S.wtot);
-    // offset the staging buffers so global and shared addresses agree modulo 16 bytes
-    T* sJ = S.J + ((reinterpret_cast<uintptr_t>(A.J + v0) & 15) / sizeof(T));
-    T* sB = S.b + ((reinterpret_cast<uintptr_t>(A.b + r0) & 15) / sizeof(T));
-    T* sTau = S.tau + ((reinterpret_cast<uintptr_t>(A.tau + c0) & 15) / sizeof(T));
-    T* sX = S.x + ((reinterpret_cast<uintptr_t>(A.x + c0) & 15) / sizeof(T));
-    copy_in(sJ, A.J + v0, nv);
-    copy_in(sB, A.b + r0, nr);
-    __syncthreads();
-
-    for (int base = 0; base < nb; base += kGroups) {
-      const int bi = base + gid;
-      const bool valid = bi < nb;
-      const int nn = valid ? S.n[bi] : 0;
-      const int mm = valid ? S.m[bi] : 0;
-      int mw = mm;
+    int base = 0;
+    for (int w = 0; w < wid; ++w) base += sW[32 + w];
+    if (tid < g.nb) sQo[tid] = base + inc - pr;
+  }
+  int myrank = 0, mykey = 0;
+  if (tid < g.nb) {
+    const int nn = sNs[tid], mm = sMs[tid];
+    mykey = row_class(nn) * 9 + mm;
+    myrank = atomicAdd(&sHist[mykey], 1);
+  }
+  __syncthreads();
+  if (tid < 32) {
+    // exclusive scan of the kKeys (<= 64) bins: two bins per lane
+    const int v0 = 2 * tid < kKeys ? sHist[2 * tid] : 0;
+    const int v1 = 2 * tid + 1 < kKeys ? sHist[2 * tid + 1] : 0;
+    int inc = v0 + v1;
 #pragma unroll
-      for (int d = 16; d >= 1; d >>= 1) mw = max(mw, __shfl_xor_sync(0xffffffffu, mw, d));
-      const int vo = valid ? S.vo[bi] : 0;
-      const int ro = valid ? S.ro[bi] : 0;
-      const int co = valid ? S.co[bi] : 0;
-      const T* sJb = sJ + vo;
-      const T* sBb = sB + ro;
-      T a[kRPL][kMaxC];
-      T bb[kRPL];
-#pragma unroll
-      for (int r = 0; r < kRPL; ++r) {
-        const int i = q + kG * r;
-        bb[r] = (i < nn) ? sBb[i] : T(0);
-#pragma unroll
-        for (int j = 0; j < kMaxC; ++j) a[r][j] = (j < mm && i < nn) ? sJb[j * nn + i] : T(0);
-      }
-      T taus[kMaxC], xs[kMaxC];
-#pragma unroll
-      for (int j = 0; j < kMaxC; ++j) { taus[j] = 0; xs[j] = 0; }
-      factor_solve_group<T, HK>(q, gbase, nn, mm, mw, valid, a, bb, taus, xs, sJb, sBb,
-                                A.refine_steps, A.status);
-      // results back to the staging buffers: factor in place of J, Q^T b in place of b
-      if (valid) {
-#pragma unroll
-        for (int r = 0; r < kRPL; ++r) {
-          const int i = q + kG * r;
-          if (i < nn) {
-            T* col = const_cast<T*>(sJb);
-#pragma unroll
-            for (int j = 0; j < kMaxC; ++j)
-              if (j < mm) col[j * nn + i] = a[r][j];
-            const_cast<T*>(sBb)[i] = bb[r];
-          }
-        }
-        if (q == 0) {
-#pragma unroll
-          for (int j = 0; j < kMaxC; ++j)
-            if (j < mm) {
-              sTau[co + j] = taus[j];
-              sX[co + j] = xs[j];
-            }
-        }
-      }
+    for (int d = 1; d < 32; d <<= 1) {
+      const int o = __shfl_up_sync(0xffffffffu, inc, d);
+      if (tid >= d) inc += o;
     }
-    __syncthreads();
-    copy_out(A.F + v0, sJ, nv);
-    if (A.qtb) copy_out(A.qtb + r0, sB, nr);
-    copy_out(A.tau + c0, sTau, nc);
-    copy_out(A.x + c0, sX, nc);
+    const int excl = inc - v0 - v1;
+    if (2 * tid < kKeys) sHist[kKeys + 2 * tid] = excl;
+    if (2 * tid + 1 < kKeys) sHist[kKeys + 2 * tid + 1] = excl + v0;
+  }
+  __syncthreads();
+  if (tid < g.nb) sPerm[sHist[kKeys + mykey] + myrank] = tid;
+  // (C) wait for the bulk loads (bounded)
+  bool ok = false;
+  for (long long polls = 0; polls < A.wait_limit; ++polls) {
+    if (mbar_try_wait(bar, 0u)) { ok = true; break; }
+  }
+  if (__syncthreads_or(!ok)) {
+    if (tid == 0) record(A.status, QRKIT_ETIMEOUT);
+    return;
+  }
+  // staging of the results: the factor goes back over J (packed), Q^T b over b unless the
+  // refinement still needs b
+  const int offF = align_off(A.F + g.v0);
+  T* sF = reinterpret_cast<T*>(smem_raw + L.J) + offF;
+  const bool f_alias = offF == g.offJ;   // same alignment: factor written in place of J
+  const int offC = A.qtb ? align_off(A.qtb + g.r0) : g.offB;
+  T* sC = REF ? reinterpret_cast<T*>(smem_raw + L.c) + offC : sB;
+  T* sT = reinterpret_cast<T*>(smem_raw + L.tau) + align_off(A.tau + g.c0);
+  T* sX = reinterpret_cast<T*>(smem_raw + L.x) + align_off(A.x + g.c0);
+  T* sG = REF ? reinterpret_cast<T*>(smem_raw + L.g) : nullptr;
+  if (REF) {
+    for (int k = tid; k < g.nr; k += kThreads) sC[k] = sB[k];
     __syncthreads();
   }
+  // (D) factor + solve (+ refine): one lane per block, a warp takes 32 consecutive sorted
+  // blocks of one row class (padded rows R = 4, 8, 12, 16)
+  int cstart[4], ccount[4], nch[4];
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    cstart[c] = sHist[kKeys + 9 * c];
+    ccount[c] = (c < 3 ? sHist[kKeys + 9 * (c + 1)] : g.nb) - cstart[c];
+    nch[c] = (ccount[c] + 31) >> 5;
+  }
+  const int total_chunks = nch[0] + nch[1] + nch[2] + nch[3];
+  T* Fstage = f_alias ? sF : nullptr;
+  for (int ch = warp_id; ch < total_chunks; ch += kThreads / 32) {
+    int c = 0, first = ch;
+#pragma unroll
+    for (int cc = 0; cc < 3; ++cc)
+      if (c == cc && first >= nch[cc]) { first -= nch[cc]; c = cc + 1; }
+    const int cst = c == 0 ? cstart[0] : (c == 1 ? cstart[1] : (c == 2 ? cstart[2] : cstart[3]));
+    const int ccn = c == 0 ? ccount[0] : (c == 1 ? ccount[1] : (c == 2 ? ccount[2] : ccount[3]));
+    const int pos = first * 32 + lane;
+    int bi = pos < ccn ? sPerm[cst + pos] : -1;
+    if (pos < ccn && (bi < 0 || bi >= g.nb)) {   // cannot happen with a consistent sort
+      record(A.status, QRKIT_EINVAL);
+      bi = -1;
+    }
+    {
+      // every lane takes part (lanes without a block: nn = mm = 0, nothing is touched)
+      const bool has = bi >= 0;
+      const int nn = has ? sNs[bi] : 0, mm = has ? sMs[bi] : 0;
+      const int vo = has ? sVo[bi] : 0, ro = has ? sRo[bi] : 0, co = has ? sCo[bi] : 0;
+      const int qo = has ? sQo[bi] : 0;
+      T* Wb = sWork + (has ? sPo[bi] : 0);
+      T* Fo = (Fstage && has) ? Fstage + vo : nullptr;
+      T* gb = REF ? sG + co : nullptr;
+      T* rsb = REF ? sRs + 2 * qo : nullptr;
+      switch (c) {
+        case 0: lane_block<T, REF, 4>(nn, mm, sJ + vo, sB + ro, Wb, sC + ro, sT + co, sX + co, gb, rsb, Fo, A.refine_steps, A.refine_tol, A.status); break;
+        case 1: lane_block<T, REF, 8>(nn, mm, sJ + vo, sB + ro, Wb, sC + ro, sT + co, sX + co, gb, rsb, Fo, A.refine_steps, A.refine_tol, A.status); break;
+        case 2: lane_block<T, REF, 12>(nn, mm, sJ + vo, sB + ro, Wb, sC + ro, sT + co, sX + co, gb, rsb, Fo, A.refine_steps, A.refine_tol, A.status); break;
+        default: lane_block<T, REF, 16>(nn, mm, sJ + vo, sB + ro, Wb, sC + ro, sT + co, sX + co, gb, rsb, Fo, A.refine_steps, A.refine_tol, A.status); break;
+      }
+    }
+  }
+  __syncthreads();
+  if (!f_alias) {
+    // the factor's staging cannot share J's alignment: write it from the working area
+    for (int bi = tid; bi < g.nb; bi += kThreads) {
+      const int nn = sNs[bi], mm = sMs[bi], R = padded_rows(nn);
+      const T* Wb = sWork + sPo[bi];
+      for (int j = 0; j < mm; ++j)
+        for (int i = 0; i < nn; ++i) A.F[g.v0 + sVo[bi] + j * nn + i] = Wb[j * R + i];
+    }
+  }
+  // (E) results to HBM with coalesced stores
+  if (f_alias) store_out(A.F + g.v0, sF, g.nv);
+  if (A.qtb) store_out(A.qtb + g.r0, sC, g.nr);
+  store_out(A.tau + g.c0, sT, g.nc);
+  store_out(A.x + g.c0, sX, g.nc);
 }
 
-template <typename T, int HK>
+template <typename T, bool REF>
 qrkit_status launch_typed(qrkit_ctx* ctx, const void* J, const void* b, void* p, void* qtb,
                           int refine_steps) {
   Plan& P = ctx->plan;
@@ -544,22 +707,23 @@ qrkit_status launch_typed(qrkit_ctx* ctx, const void* J, const void* b, void* p,
   A.qtb = (T*)qtb;
   A.x = (T*)p;
   A.refine_steps = refine_steps;
+  A.refine_tol = 1e-6f;
   A.status = ctx->d_status;
   A.vb = P.budget.values;
   A.rb = P.budget.rows;
   A.cb = P.budget.cols;
   A.bb = P.budget.blocks;
-  const size_t smem = smem_bytes<T>(A.vb, A.rb, A.cb, A.bb);
-  auto kern = block_solve_kernel<T, HK>;
-  QRKIT_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                           (int)smem));
-  int per_sm = 0;
-  QRKIT_CUDA_TRY(ctx, cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, kern, kThreads, smem));
-  if (per_sm < 1) per_sm = 1;
-  int64_t grid = (int64_t)ctx->num_sms * per_sm;
-  if (grid > P.num_tiles) grid = P.num_tiles;
-  if (grid < 1) grid = 1;
-  kern<<<(unsigned)grid, kThreads, smem, ctx->stream>>>(A);
+  A.pb = P.budget.padded;
+  A.wait_limit = 1LL << 26;
+  const size_t smem = make_layout<T>(A.vb, A.rb, A.cb, A.bb, A.pb, REF).total;
+  auto kern = block_solve_kernel<T, REF>;
+  const int variant = (sizeof(T) == sizeof(double) ? 2 : 0) + (REF ? 1 : 0);
+  if (ctx->smem_attr[variant] < smem) {
+    QRKIT_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+    ctx->smem_attr[variant] = smem;
+  }
+  kern<<<(unsigned)P.num_tiles, kThreads, smem, ctx->stream>>>(A);
   ctx->launches += 1;
   QRKIT_CUDA_TRY(ctx, cudaGetLastError());
   return QRKIT_OK;
@@ -571,22 +735,23 @@ TileBudget block_solve_budget(size_t elem) {
   TileBudget b;
   b.blocks = kThreads;
   if (elem == sizeof(float)) {
-    b.values = 8192; b.rows = 4096; b.cols = 2048;
+    b.values = 3072; b.rows = 1024; b.cols = 512; b.padded = 4096;
   } else {
-    b.values = 4096; b.rows = 2048; b.cols = 1024;
+    b.values = 1536; b.rows = 512; b.cols = 256; b.padded = 2048;
   }
   return b;
 }
 
-int block_solve_max_rows() { return kG * kRPL; }
-int block_solve_max_cols() { return kMaxC; }
+int block_solve_max_rows() { return kMaxRows; }
+int block_solve_max_cols() { return kMaxCols; }
 
 qrkit_status launch_block_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
                                 void* p, void* qtb, int refine_steps) {
   (void)D;
-  if (ctx->precision == QRKIT_FP64) return launch_typed<double, 0>(ctx, J, b, p, qtb, refine_steps);
+  if (ctx->precision == QRKIT_FP64) return launch_typed<double, false>(ctx, J, b, p, qtb, 0);
   const int steps = ctx->precision == QRKIT_FP32 ? 0 : refine_steps;
-  return launch_typed<float, 1>(ctx, J, b, p, qtb, steps);
+  if (steps > 0) return launch_typed<float, true>(ctx, J, b, p, qtb, steps);
+  return launch_typed<float, false>(ctx, J, b, p, qtb, 0);
 }
 
 }  // namespace qrkit

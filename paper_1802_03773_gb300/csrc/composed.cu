@@ -1,0 +1,803 @@
+// Composed QR of the damped block-angular system (Sec. 4.1, 4.2, 4.5, 5.1, 5.2):
+//   P_r [J; lambda^(1/2) D] = [[blkdiag(B_i), C], [0, lambda^(1/2) D_S]],
+//   B_i = [J_i; lambda^(1/2) D_i], C_i = [S_i; 0]  (row interleave, Sec. 4.5 / 5.2).
+// Steps: D = column norms (Sec. 5.2); per block Q_i R_i = qr(B_i) (Sec. 4.1) with Q_i^T
+// applied to C_i (Sec. 4.2): top rows -> R12_i, bottom rows -> reduced shared block; the
+// reduced block [stacked bottoms; lambda^(1/2) D_S] is factored by TSQR (tall-skinny QR:
+// row tiles factored in parallel, their R's stacked and factored again); solve R p = Q^T b
+// by back-substitution (Sec. 5.1); optional refinement with FP64 residuals.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace qrkit {
+namespace {
+
+constexpr int kMaxRows = 16;   // augmented rows per block
+constexpr int kMaxCols = 8;    // columns per block
+constexpr int kChunk = 8;      // coupled columns processed per pass
+constexpr int kTileThreads = 256;
+
+__device__ __forceinline__ void record(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+// ---- column norms D = diag(J^T J)^(1/2) (Sec. 5.2), accumulated in double ----
+template <typename T>
+__global__ void colnorm_blocks_kernel(ComposedView<T> V, double* sq) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= V.K) return;
+  const int n = V.n[i], m = V.m[i];
+  const T* J = V.J + V.val_off[i];
+  for (int j = 0; j < m; ++j) {
+    double s = 0;
+    for (int r = 0; r < n; ++r) {
+      const double x = (double)J[j * n + r];
+      s += x * x;
+    }
+    sq[V.col_off[i] + j] = s;
+  }
+}
+
+template <typename T>
+__global__ void colnorm_dense_kernel(ComposedView<T> V, double* sq) {
+  // one warp per shared column of the dense S (column-major, ld = rows of J)
+  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int lane = threadIdx.x & 31;
+  if (warp >= V.s) return;
+  const T* col = V.S + (int64_t)warp * V.rows;
+  double s = 0;
+  for (int64_t r = lane; r < V.rows; r += 32) {
+    const double x = (double)col[r];
+    s += x * x;
+  }
+  for (int d = 16; d >= 1; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+  if (lane == 0) sq[V.nb + warp] = s;
+}
+
+template <typename T>
+__global__ void colnorm_window_kernel(ComposedView<T> V, double* sq) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= V.K) return;
+  const int n = V.n[i];
+  const T* C = V.S + V.row_off[i] * V.w;   // block i: n x w column-major
+  for (int t = 0; t < V.w; ++t) {
+    double s = 0;
+    for (int r = 0; r < n; ++r) {
+      const double x = (double)C[t * n + r];
+      s += x * x;
+    }
+    const int64_t col = V.start[i] + t;
+    if (s != 0.0 && col < V.s) atomicAdd(&sq[V.nb + col], s);
+  }
+}
+
+__global__ void finalize_norms_kernel(const double* sq, double* D, int64_t N) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= N) return;
+  const double d = sqrt(sq[j]);
+  D[j] = d == 0.0 ? 1.0 : d;   // zero column norm -> 1 (MINPACK convention)
+}
+
+// ---- per-block factor (Sec. 4.1) with Q_i^T applied to the coupled columns (Sec. 4.2) ----
+// One thread per block; the augmented block B_i = [J_i; lambda^(1/2) D_i] (na x m) is held
+// column-major in local arrays.  Outputs: factor Fa (na x m, V below / R on and above the
+// diagonal), tau, R12 rows (m x w) and the reduced rows (na - m rows).
+template <typename T>
+__global__ void block_factor_kernel(ComposedView<T> V, FactorOut<T> O) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= V.K) return;
+  const int n = V.n[i], m = V.m[i];
+  const int na = n + (O.damp ? m : 0);
+  T B[kMaxRows * kMaxCols];
+  const T* J = V.J + V.val_off[i];
+  for (int j = 0; j < m; ++j) {
+    for (int r = 0; r < n; ++r) B[j * na + r] = J[j * n + r];
+    if (O.damp)
+      for (int r = 0; r < m; ++r)
+        B[j * na + n + r] = (r == j) ? (T)(O.lam_half * O.D[V.col_off[i] + j]) : T(0);
+  }
+  T tau[kMaxCols];
+  bool bad = false;
+  for (int k = 0; k < m; ++k) {
+    T* x = B + k * na;
+    T sq = 0;
+    for (int r = k + 1; r < na; ++r) sq += x[r] * x[r];
+    const T alpha = x[k];
+    const T norm = sqrt(alpha * alpha + sq);
+    T beta = 0, t = 0, scale = 0;
+    if (norm != T(0)) {
+      beta = alpha >= T(0) ? -norm : norm;
+      t = (beta - alpha) / beta;
+      scale = T(1) / (alpha - beta);
+    } else {
+      bad = true;
+    }
+    for (int r = k + 1; r < na; ++r) x[r] *= scale;
+    x[k] = beta;
+    tau[k] = t;
+    for (int j = k + 1; j < m; ++j) {
+      T* y = B + j * na;
+      T w = y[k];
+      for (int r = k + 1; r < na; ++r) w += x[r] * y[r];
+      w *= t;
+      y[k] -= w;
+      for (int r = k + 1; r < na; ++r) y[r] -= w * x[r];
+    }
+  }
+  if (bad) record(O.status, QRKIT_ESINGULAR);
+  T* F = O.Fa + O.aug_off[i];
+  for (int e = 0; e < na * m; ++e) F[e] = B[e];
+  for (int k = 0; k < m; ++k) O.tau[V.col_off[i] + k] = tau[k];
+  // coupled columns, kChunk at a time
+  if (V.coupled == QRKIT_COUPLED_NONE) return;
+  const int64_t red0 = O.red_off[i];
+  for (int c0 = 0; c0 < V.w; c0 += kChunk) {
+    const int cw = min(kChunk, V.w - c0);
+    T C[kMaxRows * kChunk];
+    for (int c = 0; c < cw; ++c) {
+      for (int r = 0; r < n; ++r) {
+        T v;
+        if (V.coupled == QRKIT_COUPLED_DENSE) v = V.S[(int64_t)(c0 + c) * V.rows + V.row_off[i] + r];
+        else v = V.S[V.row_off[i] * V.w + (int64_t)(c0 + c) * n + r];
+        C[c * na + r] = v;
+      }
+      for (int r = n; r < na; ++r) C[c * na + r] = 0;
+    }
+    for (int k = 0; k < m; ++k) {
+      const T* x = B + k * na;
+      for (int c = 0; c < cw; ++c) {
+        T* y = C + c * na;
+        T w = y[k];
+        for (int r = k + 1; r < na; ++r) w += x[r] * y[r];
+        w *= tau[k];
+        y[k] -= w;
+        for (int r = k + 1; r < na; ++r) y[r] -= w * x[r];
+      }
+    }
+    for (int c = 0; c < cw; ++c) {
+      for (int r = 0; r < m; ++r) O.R12[(V.col_off[i] + r) * (int64_t)V.w + c0 + c] = C[c * na + r];
+      for (int r = m; r < na; ++r) {
+        const int64_t row = red0 + (r - m);
+        if (V.coupled == QRKIT_COUPLED_DENSE) O.X0[(int64_t)(c0 + c) * O.ld0 + row] = C[c * na + r];
+        else O.Xw[row * V.w + c0 + c] = C[c * na + r];
+      }
+    }
+  }
+}
+
+// Damping rows of the shared columns, appended below the stacked bottoms (dense case).
+template <typename T>
+__global__ void reduced_damping_kernel(T* X0, int64_t ld0, int64_t row0, int s, const double* D,
+                                       int64_t nb, double lam_half) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)s * s) return;
+  const int j = (int)(e / s), c = (int)(e % s);
+  X0[(int64_t)c * ld0 + row0 + j] = (c == j) ? (T)(lam_half * D[nb + j]) : T(0);
+}
+
+// ---- TSQR tile factor: one CTA per row tile of a level matrix (column-major, ld) ----
+// Householder QR of the tile in shared memory; V below / R on and above the diagonal are
+// written back in place, tau to taus[tile * s + k], and the tile's R rows (upper
+// triangle, zeros below) to the next level's rows [tile * s, tile * s + min(r, s)).
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads)
+tsqr_tile_kernel(T* X, int64_t ld, int64_t M, int s, int tile_rows, T* taus, T* Xn, int64_t ldn,
+                 int* status) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* A = reinterpret_cast<T*>(smem_raw);                 // tile_rows x s, ld = tile_rows
+  T* red = A + (size_t)tile_rows * s;                    // 32 partials
+  T* sh = red + 32;                                      // [0] tau, [1] beta, [2] scale
+  const int64_t r0 = (int64_t)blockIdx.x * tile_rows;
+  const int r = (int)(M - r0 < (int64_t)tile_rows ? M - r0 : (int64_t)tile_rows);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int nwarps = blockDim.x >> 5;
+  for (int e = tid; e < r * s; e += blockDim.x) {
+    const int c = e / r, i = e % r;
+    A[c * tile_rows + i] = X[(int64_t)c * ld + r0 + i];
+  }
+  __syncthreads();
+  const int kmax = min(r, s);
+  for (int k = 0; k < kmax; ++k) {
+    T* x = A + k * tile_rows;
+    if (warp == 0) {
+      T sq = 0;
+      for (int i = k + 1 + lane; i < r; i += 32) sq += x[i] * x[i];
+      for (int d = 16; d >= 1; d >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, d);
+      if (lane == 0) {
+        const T alpha = x[k];
+        const T norm = sqrt(alpha * alpha + sq);
+        T beta = 0, t = 0, scale = 0;
+        if (norm != T(0)) {
+          beta = alpha >= T(0) ? -norm : norm;
+          t = (beta - alpha) / beta;
+          scale = T(1) / (alpha - beta);
+        }
+        // a zero column inside a tile is not a singular R: a tile of stacked R rows can
+        // start below the diagonal; the final R_S is checked by the back-substitution
+        sh[0] = t;
+        sh[1] = beta;
+        sh[2] = scale;
+      }
+      __syncwarp();
+      const T scale = sh[2];
+      for (int i = k + 1 + lane; i < r; i += 32) x[i] *= scale;
+    }
+    __syncthreads();
+    const T t = sh[0];
+    for (int j = k + 1 + warp; j < s; j += nwarps) {
+      T* y = A + j * tile_rows;
+      T w = 0;
+      for (int i = k + 1 + lane; i < r; i += 32) w += x[i] * y[i];
+      for (int d = 16; d >= 1; d >>= 1) w += __shfl_xor_sync(0xffffffffu, w, d);
+      w = (w + y[k]) * t;
+      if (lane == 0) y[k] -= w;
+      for (int i = k + 1 + lane; i < r; i += 32) y[i] -= w * x[i];
+    }
+    if (tid == 0) {
+      x[k] = sh[1];
+      taus[(int64_t)blockIdx.x * s + k] = t;
+    }
+    __syncthreads();
+  }
+  for (int e = tid; e < r * s; e += blockDim.x) {
+    const int c = e / r, i = e % r;
+    X[(int64_t)c * ld + r0 + i] = A[c * tile_rows + i];
+  }
+  if (Xn) {
+    const int64_t n0 = (int64_t)blockIdx.x * s;
+    for (int e = tid; e < kmax * s; e += blockDim.x) {
+      const int c = e / kmax, i = e % kmax;
+      Xn[(int64_t)c * ldn + n0 + i] = (c >= i) ? A[c * tile_rows + i] : T(0);
+    }
+  }
+}
+
+// Q_tile^T applied to a level's rhs segment; the top min(r, s) entries go to the next level.
+template <typename T>
+__global__ void __launch_bounds__(kTileThreads)
+tsqr_apply_qt_kernel(const T* X, int64_t ld, int64_t M, int s, int tile_rows, const T* taus,
+                     T* rhs, T* rhs_next) {
+  __shared__ T red[32];
+  const int64_t r0 = (int64_t)blockIdx.x * tile_rows;
+  const int r = (int)(M - r0 < (int64_t)tile_rows ? M - r0 : (int64_t)tile_rows);
+  const int kmax = min(r, s);
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  T* y = rhs + r0;
+  for (int k = 0; k < kmax; ++k) {
+    const T* x = X + (int64_t)k * ld + r0;
+    T w = 0;
+    for (int i = k + 1 + tid; i < r; i += blockDim.x) w += x[i] * y[i];
+    for (int d = 16; d >= 1; d >>= 1) w += __shfl_xor_sync(0xffffffffu, w, d);
+    if (lane == 0) red[warp] = w;
+    __syncthreads();
+    if (warp == 0) {
+      T v = lane < (int)(blockDim.x >> 5) ? red[lane] : T(0);
+      for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+      if (lane == 0) red[0] = v;
+    }
+    __syncthreads();
+    const T wt = (red[0] + y[k]) * taus[(int64_t)blockIdx.x * s + k];
+    __syncthreads();
+    if (tid == 0) y[k] -= wt;
+    for (int i = k + 1 + tid; i < r; i += blockDim.x) y[i] -= wt * x[i];
+    __syncthreads();
+  }
+  if (rhs_next)
+    for (int i = tid; i < kmax; i += blockDim.x) rhs_next[(int64_t)blockIdx.x * s + i] = y[i];
+}
+
+// Per-block Q_i^T [b_i; 0]: top m -> ctop, bottom -> reduced rhs rows.
+template <typename T>
+__global__ void block_apply_qt_kernel(ComposedView<T> V, FactorOut<T> O, const T* b, T* rhs0) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= V.K) return;
+  const int n = V.n[i], m = V.m[i];
+  const int na = n + (O.damp ? m : 0);
+  T y[kMaxRows];
+  for (int r = 0; r < n; ++r) y[r] = b[V.row_off[i] + r];
+  for (int r = n; r < na; ++r) y[r] = 0;
+  const T* F = O.Fa + O.aug_off[i];
+  for (int k = 0; k < m; ++k) {
+    const T* x = F + k * na;
+    T w = y[k];
+    for (int r = k + 1; r < na; ++r) w += x[r] * y[r];
+    w *= O.tau[V.col_off[i] + k];
+    y[k] -= w;
+    for (int r = k + 1; r < na; ++r) y[r] -= w * x[r];
+  }
+  for (int r = 0; r < m; ++r) O.ctop[V.col_off[i] + r] = y[r];
+  if (rhs0)
+    for (int r = m; r < na; ++r) rhs0[O.red_off[i] + (r - m)] = y[r];
+}
+
+// R_S x = c (upper triangular, column-major with ld) by one warp; optionally x += result.
+template <typename T>
+__global__ void dense_backsub_kernel(const T* R, int64_t ld, int s, const T* c, T* x, int accumulate,
+                                     int* status) {
+  const int lane = threadIdx.x & 31;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* xs = reinterpret_cast<T*>(smem_raw);
+  for (int k = s - 1; k >= 0; --k) {
+    T part = 0;
+    for (int j = k + 1 + lane; j < s; j += 32) part += R[(int64_t)j * ld + k] * xs[j];
+    for (int d = 16; d >= 1; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+    if (lane == 0) {
+      const T rkk = R[(int64_t)k * ld + k];
+      if (rkk == T(0)) record(status, QRKIT_ESINGULAR);
+      xs[k] = (c[k] - part) / rkk;
+    }
+    __syncwarp();
+  }
+  for (int k = lane; k < s; k += 32) x[k] = accumulate ? x[k] + xs[k] : xs[k];
+}
+
+// R_S^T h = g (forward substitution), g given in double.
+template <typename T>
+__global__ void dense_fwdsub_rt_kernel(const T* R, int64_t ld, int s, const double* g, T* h) {
+  const int lane = threadIdx.x & 31;
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* hs = reinterpret_cast<T*>(smem_raw);
+  for (int k = 0; k < s; ++k) {
+    T part = 0;
+    for (int i = lane; i < k; i += 32) part += R[(int64_t)k * ld + i] * hs[i];
+    for (int d = 16; d >= 1; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
+    if (lane == 0) hs[k] = ((T)g[k] - part) / R[(int64_t)k * ld + k];
+    __syncwarp();
+  }
+  for (int k = lane; k < s; k += 32) h[k] = hs[k];
+}
+
+// Per-block R_i x_i = rhs_i - R12_i x_S; rhs from ctop (T) or from a double vector.
+template <typename T>
+__global__ void block_backsub_kernel(ComposedView<T> V, FactorOut<T> O, const T* rhs_t,
+                                     const T* xS, T* x, int accumulate) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= V.K) return;
+  const int n = V.n[i], m = V.m[i];
+  const int na = n + (O.damp ? m : 0);
+  const int64_t c0 = V.col_off[i];
+  T y[kMaxCols];
+  for (int k = 0; k < m; ++k) {
+    T v = rhs_t[c0 + k];
+    if (V.coupled != QRKIT_COUPLED_NONE && xS) {
+      const int64_t st = V.coupled == QRKIT_COUPLED_WINDOW ? V.start[i] : 0;
+      const T* r12 = O.R12 + (c0 + k) * (int64_t)V.w;
+      for (int t = 0; t < V.w; ++t)
+        if (st + t < V.s) v -= r12[t] * xS[st + t];
+    }
+    y[k] = v;
+  }
+  const T* F = O.Fa + O.aug_off[i];
+  for (int k = m - 1; k >= 0; --k) {
+    T v = y[k];
+    for (int j = k + 1; j < m; ++j) v -= F[j * na + k] * y[j];
+    y[k] = v / F[k * na + k];
+  }
+  for (int k = 0; k < m; ++k) x[c0 + k] = accumulate ? x[c0 + k] + y[k] : y[k];
+}
+
+// ---- refinement: g = J^T (b - J p) - lambda D^2 p in double ----
+template <typename T>
+__global__ void resid_g_kernel(ComposedView<T> V, const T* b, const T* p, const double* D,
+                               double lam, double* g, double* gS) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= V.K) return;
+  const int n = V.n[i], m = V.m[i];
+  const int64_t c0 = V.col_off[i], r0 = V.row_off[i];
+  const T* J = V.J + V.val_off[i];
+  const int64_t st = V.coupled == QRKIT_COUPLED_WINDOW ? V.start[i] : 0;
+  double res[kMaxRows];
+  for (int r = 0; r < n; ++r) {
+    double acc = (double)b[r0 + r];
+    for (int j = 0; j < m; ++j) acc -= (double)J[j * n + r] * (double)p[c0 + j];
+    if (V.coupled == QRKIT_COUPLED_DENSE) {
+      for (int c = 0; c < V.s; ++c)
+        acc -= (double)V.S[(int64_t)c * V.rows + r0 + r] * (double)p[V.nb + c];
+    } else if (V.coupled == QRKIT_COUPLED_WINDOW) {
+      for (int t = 0; t < V.w; ++t)
+        if (st + t < V.s) acc -= (double)V.S[r0 * V.w + (int64_t)t * n + r] * (double)p[V.nb + st + t];
+    }
+    res[r] = acc;
+  }
+  for (int j = 0; j < m; ++j) {
+    double acc = 0;
+    for (int r = 0; r < n; ++r) acc += (double)J[j * n + r] * res[r];
+    const double d = D[c0 + j];
+    g[c0 + j] = acc - lam * d * d * (double)p[c0 + j];
+  }
+  if (V.coupled == QRKIT_COUPLED_DENSE) {
+    for (int c = 0; c < V.s; ++c) {
+      double acc = 0;
+      for (int r = 0; r < n; ++r) acc += (double)V.S[(int64_t)c * V.rows + r0 + r] * res[r];
+      if (acc != 0.0) atomicAdd(&gS[c], acc);
+    }
+  } else if (V.coupled == QRKIT_COUPLED_WINDOW) {
+    for (int t = 0; t < V.w; ++t) {
+      double acc = 0;
+      for (int r = 0; r < n; ++r) acc += (double)V.S[r0 * V.w + (int64_t)t * n + r] * res[r];
+      if (acc != 0.0 && st + t < V.s) atomicAdd(&gS[st + t], acc);
+    }
+  }
+}
+
+__global__ void gS_damping_kernel(double* gS, const float* pf, const double* pd, const double* D,
+                                  int64_t nb, int s, double lam) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c >= s) return;
+  const double pv = pf ? (double)pf[nb + c] : pd[nb + c];
+  const double d = D[nb + c];
+  gS[c] -= lam * d * d * pv;
+}
+
+// h_i = R_i^{-T} g_i per block; then gS -= R12_i^T h_i.
+template <typename T>
+__global__ void block_fwdsub_rt_kernel(ComposedView<T> V, FactorOut<T> O, const double* g, T* h,
+                                       double* gS) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= V.K) return;
+  const int n = V.n[i], m = V.m[i];
+  const int na = n + (O.damp ? m : 0);
+  const int64_t c0 = V.col_off[i];
+  const T* F = O.Fa + O.aug_off[i];
+  T hv[kMaxCols];
+  for (int k = 0; k < m; ++k) {
+    T v = (T)g[c0 + k];
+    for (int j = 0; j < k; ++j) v -= F[k * na + j] * hv[j];
+    hv[k] = v / F[k * na + k];
+    h[c0 + k] = hv[k];
+  }
+  if (V.coupled != QRKIT_COUPLED_NONE) {
+    const int64_t st = V.coupled == QRKIT_COUPLED_WINDOW ? V.start[i] : 0;
+    for (int t = 0; t < V.w; ++t) {
+      if (st + t >= V.s) continue;
+      double acc = 0;
+      for (int k = 0; k < m; ++k) acc += (double)O.R12[(c0 + k) * (int64_t)V.w + t] * (double)hv[k];
+      if (acc != 0.0) atomicAdd(&gS[st + t], -acc);
+    }
+  }
+}
+
+template <typename T>
+__global__ void gS_to_T_kernel(const double* gS, T* out, int s) {
+  const int c = blockIdx.x * blockDim.x + threadIdx.x;
+  if (c < s) out[c] = (T)gS[c];
+}
+
+template <typename T>
+__global__ void axpy_kernel(T* x, const T* d, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) x[i] += d[i];
+}
+
+__global__ void widen_kernel(const float* in, double* out, int64_t n) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < n) out[i] = (double)in[i];
+}
+
+inline unsigned blocks_for(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+// ---------------------------------------------------------------------------------------
+// Host orchestration.
+
+template <typename T>
+static ComposedView<T> view(qrkit_ctx* ctx, const void* J, const void* S) {
+  Plan& P = ctx->plan;
+  ComposedView<T> V;
+  V.K = P.K;
+  V.n = (const uint8_t*)P.d_n.ptr;
+  V.m = (const uint8_t*)P.d_m.ptr;
+  V.val_off = (const int64_t*)P.d_val_off.ptr;
+  V.row_off = (const int64_t*)P.d_row_off.ptr;
+  V.col_off = (const int64_t*)P.d_col_off.ptr;
+  V.start = (const int32_t*)P.d_start.ptr;
+  V.coupled = P.s.coupled_kind;
+  V.s = (int)P.s.shared_cols;
+  V.w = P.s.coupled_kind == QRKIT_COUPLED_DENSE ? (int)P.s.shared_cols : P.s.window;
+  V.rows = P.rows;
+  V.nb = P.cols;
+  V.J = (const T*)J;
+  V.S = (const T*)S;
+  return V;
+}
+
+template <typename T>
+static FactorOut<T> fout(qrkit_ctx* ctx) {
+  Composed& C = ctx->comp;
+  FactorOut<T> O;
+  O.damp = C.damp;
+  O.lam_half = C.lam_half;
+  O.D = (const double*)C.D.ptr;
+  O.Fa = (T*)C.Fa.ptr;
+  O.tau = (T*)C.tau.ptr;
+  O.R12 = (T*)C.R12.ptr;
+  O.ctop = (T*)C.ctop.ptr;
+  O.aug_off = (const int64_t*)(C.damp ? C.d_aug_off_d.ptr : C.d_aug_off_u.ptr);
+  O.red_off = (const int64_t*)(C.damp ? C.d_red_off_d.ptr : C.d_red_off_u.ptr);
+  O.X0 = C.levels.empty() ? nullptr : (T*)C.levels[0].X.ptr;
+  O.ld0 = C.levels.empty() ? 0 : C.levels[0].M;
+  O.Xw = nullptr;
+  O.status = ctx->d_status;
+  return O;
+}
+
+#define LAUNCH(ctx, ...)                                  \
+  do {                                                    \
+    __VA_ARGS__;                                          \
+    (ctx)->launches += 1;                                 \
+    QRKIT_CUDA_TRY(ctx, cudaGetLastError());              \
+  } while (0)
+
+template <typename T>
+static qrkit_status factor_typed(qrkit_ctx* ctx, const void* J, const void* S, const void* Dext,
+                                 double lambda) {
+  Plan& P = ctx->plan;
+  Composed& C = ctx->comp;
+  cudaStream_t st = ctx->stream;
+  const int64_t N = P.cols + P.s.shared_cols;
+  qrkit_status rc;
+  if ((rc = ensure(ctx, C.D, (size_t)N * sizeof(double), "D")) != QRKIT_OK) return rc;
+  if ((rc = ensure(ctx, C.sq, (size_t)N * sizeof(double), "column sums")) != QRKIT_OK) return rc;
+  C.damp = lambda > 0.0;
+  C.lam = lambda;
+  C.lam_half = sqrt(lambda);
+  if ((rc = composed_layout(ctx, sizeof(T))) != QRKIT_OK) return rc;
+  ComposedView<T> V = view<T>(ctx, J, S);
+  // D: caller's (copied to double) or column norms of J
+  if (Dext) {
+    if (sizeof(T) == sizeof(double)) {
+      QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(C.D.ptr, Dext, (size_t)N * sizeof(double),
+                                          cudaMemcpyDeviceToDevice, st));
+    } else {
+      rc = widen_to_double(ctx, (const float*)Dext, (double*)C.D.ptr, N);
+      if (rc != QRKIT_OK) return rc;
+    }
+  } else {
+    double* sq = (double*)C.sq.ptr;
+    QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(sq, 0, (size_t)N * sizeof(double), st));
+    LAUNCH(ctx, colnorm_blocks_kernel<T><<<blocks_for(P.K, 128), 128, 0, st>>>(V, sq));
+    if (V.coupled == QRKIT_COUPLED_DENSE)
+      LAUNCH(ctx, colnorm_dense_kernel<T><<<blocks_for((int64_t)V.s * 32, 256), 256, 0, st>>>(V, sq));
+    else if (V.coupled == QRKIT_COUPLED_WINDOW)
+      LAUNCH(ctx, colnorm_window_kernel<T><<<blocks_for(P.K, 128), 128, 0, st>>>(V, sq));
+    LAUNCH(ctx, finalize_norms_kernel<<<blocks_for(N, 256), 256, 0, st>>>(sq, (double*)C.D.ptr, N));
+  }
+  FactorOut<T> O = fout<T>(ctx);
+  LAUNCH(ctx, block_factor_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O));
+  if (V.coupled == QRKIT_COUPLED_DENSE) {
+    const int s = V.s;
+    if (C.damp)
+      LAUNCH(ctx, reduced_damping_kernel<T><<<blocks_for((int64_t)s * s, 256), 256, 0, st>>>(
+                      (T*)C.levels[0].X.ptr, C.levels[0].M, C.red_rows, s, (const double*)C.D.ptr,
+                      P.cols, C.lam_half));
+    for (size_t l = 0; l < C.levels.size(); ++l) {
+      TsqrLevel& L = C.levels[l];
+      T* Xn = l + 1 < C.levels.size() ? (T*)C.levels[l + 1].X.ptr : nullptr;
+      const int64_t ldn = l + 1 < C.levels.size() ? C.levels[l + 1].M : 0;
+      const size_t smem = ((size_t)C.tile_rows * s + 64) * sizeof(T);
+      auto k = tsqr_tile_kernel<T>;
+      QRKIT_CUDA_TRY(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+      LAUNCH(ctx, k<<<(unsigned)L.tiles, kTileThreads, smem, st>>>((T*)L.X.ptr, L.M, L.M, s, C.tile_rows,
+                                                                  (T*)L.tau.ptr, Xn, ldn, ctx->d_status));
+    }
+  }
+  return QRKIT_OK;
+}
+
+template <typename T>
+static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, const void* b, void* p,
+                                int refine_steps, bool qt_only, void* qtb_out) {
+  Plan& P = ctx->plan;
+  Composed& C = ctx->comp;
+  cudaStream_t st = ctx->stream;
+  ComposedView<T> V = view<T>(ctx, J, S);
+  FactorOut<T> O = fout<T>(ctx);
+  const int s = V.s;
+  const int64_t nb = P.cols;
+  T* x = (T*)p;
+  // Q^T [b; 0]
+  T* rhs0 = (V.coupled == QRKIT_COUPLED_DENSE) ? (T*)C.levels[0].rhs.ptr : nullptr;
+  LAUNCH(ctx, block_apply_qt_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O, (const T*)b, rhs0));
+  if (V.coupled == QRKIT_COUPLED_DENSE) {
+    if (C.damp)
+      QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(rhs0 + C.red_rows, 0, (size_t)s * sizeof(T), st));
+    for (size_t l = 0; l < C.levels.size(); ++l) {
+      TsqrLevel& L = C.levels[l];
+      T* rn = l + 1 < C.levels.size() ? (T*)C.levels[l + 1].rhs.ptr : nullptr;
+      LAUNCH(ctx, tsqr_apply_qt_kernel<T><<<(unsigned)L.tiles, kTileThreads, 0, st>>>(
+                      (const T*)L.X.ptr, L.M, L.M, s, C.tile_rows, (const T*)L.tau.ptr, (T*)L.rhs.ptr, rn));
+    }
+  }
+  if (qt_only) {
+    // Q^T b reported as [c_blocks (sum m_i); c_S (s)]
+    T* out = (T*)qtb_out;
+    QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(out, O.ctop, (size_t)nb * sizeof(T), cudaMemcpyDeviceToDevice, st));
+    if (s > 0)
+      QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(out + nb, C.levels.back().rhs.ptr, (size_t)s * sizeof(T),
+                                          cudaMemcpyDeviceToDevice, st));
+    return QRKIT_OK;
+  }
+  const TsqrLevel* top = C.levels.empty() ? nullptr : &C.levels.back();
+  if (V.coupled == QRKIT_COUPLED_DENSE) {
+    LAUNCH(ctx, dense_backsub_kernel<T><<<1, 32, (size_t)s * sizeof(T), st>>>(
+                    (const T*)top->X.ptr, top->M, s, (const T*)top->rhs.ptr, x + nb, 0, ctx->d_status));
+  }
+  LAUNCH(ctx, block_backsub_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O, O.ctop, s ? x + nb : nullptr, x, 0));
+  // refinement (extended-precision residual, corrections through R only)
+  for (int it = 0; it < refine_steps; ++it) {
+    const int64_t N = nb + s;
+    qrkit_status rc;
+    if ((rc = ensure(ctx, C.g, (size_t)N * sizeof(double), "refinement g")) != QRKIT_OK) return rc;
+    if ((rc = ensure(ctx, C.h, (size_t)N * sizeof(T), "refinement h")) != QRKIT_OK) return rc;
+    double* g = (double*)C.g.ptr;
+    T* h = (T*)C.h.ptr;
+    double* gS = g + nb;
+    if (s > 0) QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(gS, 0, (size_t)s * sizeof(double), st));
+    LAUNCH(ctx, resid_g_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, (const T*)b, x, O.D, C.lam, g, gS));
+    if (s > 0)
+      LAUNCH(ctx, gS_damping_kernel<<<blocks_for(s, 128), 128, 0, st>>>(
+                      gS, sizeof(T) == 4 ? (const float*)x : nullptr,
+                      sizeof(T) == 8 ? (const double*)x : nullptr, O.D, nb, s, C.lam));
+    LAUNCH(ctx, block_fwdsub_rt_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O, g, h, gS));
+    if (V.coupled == QRKIT_COUPLED_DENSE) {
+      // h_S = R_S^{-T} (g_S - R12^T h_B), then dp_S = R_S^{-1} h_S in place
+      LAUNCH(ctx, dense_fwdsub_rt_kernel<T><<<1, 32, (size_t)s * sizeof(T), st>>>(
+                      (const T*)top->X.ptr, top->M, s, gS, h + nb));
+      LAUNCH(ctx, dense_backsub_kernel<T><<<1, 32, (size_t)s * sizeof(T), st>>>(
+                      (const T*)top->X.ptr, top->M, s, h + nb, h + nb, 0, ctx->d_status));
+      LAUNCH(ctx, axpy_kernel<T><<<blocks_for(s, 128), 128, 0, st>>>(x + nb, h + nb, s));
+    }
+    // dp_B = R_B^{-1} (h_B - R12 dp_S), accumulated into p
+    LAUNCH(ctx, block_backsub_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O, h, s ? h + nb : nullptr, x, 1));
+  }
+  return QRKIT_OK;
+}
+
+qrkit_status composed_factor(qrkit_ctx* ctx, const void* J, const void* S, const void* D, double lambda) {
+  if (ctx->precision == QRKIT_FP64) return factor_typed<double>(ctx, J, S, D, lambda);
+  return factor_typed<float>(ctx, J, S, D, lambda);
+}
+
+qrkit_status composed_solve(qrkit_ctx* ctx, const void* J, const void* S, const void* b, void* p,
+                            int refine_steps) {
+  if (ctx->precision == QRKIT_FP64) return solve_typed<double>(ctx, J, S, b, p, refine_steps, false, nullptr);
+  const int steps = ctx->precision == QRKIT_FP32 ? 0 : refine_steps;
+  return solve_typed<float>(ctx, J, S, b, p, steps, false, nullptr);
+}
+
+qrkit_status composed_apply_qt(qrkit_ctx* ctx, const void* b, void* qtb) {
+  if (ctx->precision == QRKIT_FP64) return solve_typed<double>(ctx, nullptr, nullptr, b, nullptr, 0, true, qtb);
+  return solve_typed<float>(ctx, nullptr, nullptr, b, nullptr, 0, true, qtb);
+}
+
+}  // namespace qrkit
+
+namespace qrkit {
+
+static qrkit_status upload_i64(qrkit_ctx* ctx, DevBuf& buf, const std::vector<int64_t>& v, const char* what) {
+  qrkit_status rc = ensure(ctx, buf, v.size() * sizeof(int64_t), what);
+  if (rc != QRKIT_OK) return rc;
+  QRKIT_CUDA_TRY(ctx, cudaMemcpy(buf.ptr, v.data(), v.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+  return QRKIT_OK;
+}
+
+qrkit_status widen_to_double(qrkit_ctx* ctx, const float* in, double* out, int64_t n) {
+  widen_kernel<<<blocks_for(n, 256), 256, 0, ctx->stream>>>(in, out, n);
+  ctx->launches += 1;
+  QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+  return QRKIT_OK;
+}
+
+void release_composed(Composed& C) {
+  release(C.D); release(C.sq); release(C.Fa); release(C.tau); release(C.R12); release(C.ctop);
+  release(C.g); release(C.h);
+  release(C.d_aug_off_d); release(C.d_aug_off_u); release(C.d_red_off_d); release(C.d_red_off_u);
+  for (auto& L : C.levels) { release(L.X); release(L.tau); release(L.rhs); }
+  C = Composed();
+}
+
+// Offsets of the augmented blocks for both damping states, the factor buffers, and the
+// TSQR level geometry of the dense reduced block.
+qrkit_status composed_layout(qrkit_ctx* ctx, size_t elem) {
+  Plan& P = ctx->plan;
+  Composed& C = ctx->comp;
+  qrkit_status rc;
+  if (!C.d_aug_off_d.ptr) {
+    std::vector<int64_t> ad(P.K + 1), au(P.K + 1), rd(P.K + 1), ru(P.K + 1);
+    ad[0] = au[0] = rd[0] = ru[0] = 0;
+    for (int64_t i = 0; i < P.K; ++i) {
+      const int64_t n = P.n[i], m = P.m[i];
+      ad[i + 1] = ad[i] + (n + m) * m;
+      au[i + 1] = au[i] + n * m;
+      rd[i + 1] = rd[i] + n;
+      ru[i + 1] = ru[i] + (n - m);
+    }
+    C.aug_values_d = ad[P.K]; C.aug_values_u = au[P.K];
+    C.red_rows_d = rd[P.K]; C.red_rows_u = ru[P.K];
+    if ((rc = upload_i64(ctx, C.d_aug_off_d, ad, "aug offsets")) != QRKIT_OK) return rc;
+    if ((rc = upload_i64(ctx, C.d_aug_off_u, au, "aug offsets")) != QRKIT_OK) return rc;
+    if ((rc = upload_i64(ctx, C.d_red_off_d, rd, "reduced offsets")) != QRKIT_OK) return rc;
+    if ((rc = upload_i64(ctx, C.d_red_off_u, ru, "reduced offsets")) != QRKIT_OK) return rc;
+  }
+  if (C.damp && P.first_tall_aug >= 0)
+    return fail(ctx, QRKIT_EUNSUPPORTED, "block " + std::to_string(P.first_tall_aug) +
+                ": with damping rows the augmented block exceeds 16 rows");
+  if (!C.damp && P.first_wide >= 0)
+    return fail(ctx, QRKIT_EINVAL, "block " + std::to_string(P.first_wide) +
+                " has fewer rows than columns and lambda = 0");
+  C.red_rows = C.damp ? C.red_rows_d : C.red_rows_u;
+  const int64_t aug = C.damp ? C.aug_values_d : C.aug_values_u;
+  const int s = (int)P.s.shared_cols;
+  const int w = P.s.coupled_kind == QRKIT_COUPLED_DENSE ? s : P.s.window;
+  if ((rc = ensure(ctx, C.Fa, (size_t)aug * elem, "factor")) != QRKIT_OK) return rc;
+  if ((rc = ensure(ctx, C.tau, (size_t)P.cols * elem, "tau")) != QRKIT_OK) return rc;
+  if ((rc = ensure(ctx, C.ctop, (size_t)P.cols * elem, "c")) != QRKIT_OK) return rc;
+  if (P.s.coupled_kind != QRKIT_COUPLED_NONE)
+    if ((rc = ensure(ctx, C.R12, (size_t)P.cols * w * elem, "R12")) != QRKIT_OK) return rc;
+  if (P.s.coupled_kind == QRKIT_COUPLED_WINDOW)
+    return fail(ctx, QRKIT_EUNSUPPORTED, "windowed coupling needs the banded reduced solver");
+  if (P.s.coupled_kind == QRKIT_COUPLED_DENSE) {
+    if (s > 64) return fail(ctx, QRKIT_EUNSUPPORTED, "dense shared block wider than 64 columns");
+    const int64_t M0 = C.red_rows + (C.damp ? s : 0);
+    if (M0 < s) return fail(ctx, QRKIT_EINVAL, "reduced shared block has fewer rows than columns");
+    C.tile_rows = 256;
+    std::vector<int64_t> Ms;
+    int64_t M = M0;
+    while (true) {
+      Ms.push_back(M);
+      const int64_t tiles = (M + C.tile_rows - 1) / C.tile_rows;
+      if (tiles <= 1) break;
+      const int64_t last = M - (tiles - 1) * C.tile_rows;
+      M = (tiles - 1) * s + std::min<int64_t>(last, s);
+    }
+    if (C.levels.size() != Ms.size()) {
+      for (auto& L : C.levels) { release(L.X); release(L.tau); release(L.rhs); }
+      C.levels.assign(Ms.size(), TsqrLevel());
+    }
+    for (size_t l = 0; l < Ms.size(); ++l) {
+      TsqrLevel& L = C.levels[l];
+      L.M = Ms[l];
+      L.tiles = (L.M + C.tile_rows - 1) / C.tile_rows;
+      if ((rc = ensure(ctx, L.X, (size_t)L.M * s * elem, "reduced block")) != QRKIT_OK) return rc;
+      if ((rc = ensure(ctx, L.tau, (size_t)L.tiles * s * elem, "reduced tau")) != QRKIT_OK) return rc;
+      if ((rc = ensure(ctx, L.rhs, (size_t)L.M * elem, "reduced rhs")) != QRKIT_OK) return rc;
+    }
+  } else {
+    for (auto& L : C.levels) { release(L.X); release(L.tau); release(L.rhs); }
+    C.levels.clear();
+  }
+  return QRKIT_OK;
+}
+
+template <typename T>
+static qrkit_status solve_r_typed(qrkit_ctx* ctx, const void* qtb, void* p) {
+  Plan& P = ctx->plan;
+  Composed& C = ctx->comp;
+  cudaStream_t st = ctx->stream;
+  ComposedView<T> V = view<T>(ctx, nullptr, nullptr);
+  FactorOut<T> O = fout<T>(ctx);
+  const int s = V.s;
+  const T* c = (const T*)qtb;
+  T* x = (T*)p;
+  if (V.coupled == QRKIT_COUPLED_DENSE) {
+    const TsqrLevel& top = C.levels.back();
+    LAUNCH(ctx, dense_backsub_kernel<T><<<1, 32, (size_t)s * sizeof(T), st>>>(
+                    (const T*)top.X.ptr, top.M, s, c + P.cols, x + P.cols, 0, ctx->d_status));
+  }
+  LAUNCH(ctx, block_backsub_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O, c, s ? x + P.cols : nullptr, x, 0));
+  return QRKIT_OK;
+}
+
+qrkit_status composed_solve_r(qrkit_ctx* ctx, const void* qtb, void* p) {
+  if (ctx->precision == QRKIT_FP64) return solve_r_typed<double>(ctx, qtb, p);
+  return solve_r_typed<float>(ctx, qtb, p);
+}
+
+}  // namespace qrkit

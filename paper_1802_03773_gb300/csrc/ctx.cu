@@ -54,6 +54,10 @@ static qrkit_status upload(qrkit_ctx* ctx, DevBuf& buf, const void* host, size_t
 }
 
 static void release_plan(Plan& P) {
+  release(P.d_val_off);
+  release(P.d_row_off);
+  release(P.d_col_off);
+  release(P.d_start);
   release(P.d_n);
   release(P.d_m);
   release(P.d_tile_block);
@@ -70,19 +74,20 @@ static void cut_tiles(Plan& P) {
   P.tile_val.assign(1, 0);
   P.tile_row.assign(1, 0);
   P.tile_col.assign(1, 0);
-  int64_t nb = 0, nv = 0, nr = 0, nc = 0;
+  int64_t nb = 0, nv = 0, nr = 0, nc = 0, np = 0;
   int64_t val = 0, row = 0, col = 0;
   for (int64_t i = 0; i < P.K; ++i) {
     const int64_t n = P.n[i], m = P.m[i];
+    const int64_t pad = 4 * ((n + 3) / 4) * m;   // rows padded to a multiple of 4
     if (nb > 0 && (nb + 1 > B.blocks || nv + n * m > B.values || nr + n > B.rows ||
-                   nc + m > B.cols)) {
+                   nc + m > B.cols || np + pad > B.padded)) {
       P.tile_block.push_back(i);
       P.tile_val.push_back(val);
       P.tile_row.push_back(row);
       P.tile_col.push_back(col);
-      nb = nv = nr = nc = 0;
+      nb = nv = nr = nc = np = 0;
     }
-    nb += 1; nv += n * m; nr += n; nc += m;
+    nb += 1; nv += n * m; nr += n; nc += m; np += pad;
     val += n * m; row += n; col += m;
   }
   P.tile_block.push_back(P.K);
@@ -97,8 +102,15 @@ static qrkit_status plan_blocks(qrkit_ctx* ctx, const qrkit_structure* s) {
   if (s->num_blocks < 1) return fail(ctx, QRKIT_EINVAL, "num_blocks must be >= 1");
   if (!s->block_rows || !s->block_cols)
     return fail(ctx, QRKIT_EINVAL, "block_rows and block_cols are required");
-  if (s->coupled_kind != QRKIT_COUPLED_NONE)
-    return fail(ctx, QRKIT_EUNSUPPORTED, "coupled (hcat) structures are not available in this build");
+  if (s->coupled_kind < QRKIT_COUPLED_NONE || s->coupled_kind > QRKIT_COUPLED_WINDOW)
+    return fail(ctx, QRKIT_EINVAL, "unknown coupled_kind");
+  if (s->coupled_kind != QRKIT_COUPLED_NONE && s->shared_cols < 1)
+    return fail(ctx, QRKIT_EINVAL, "shared_cols must be >= 1 for a coupled structure");
+  if (s->coupled_kind == QRKIT_COUPLED_WINDOW) {
+    if (s->window < 1 || s->window > s->shared_cols)
+      return fail(ctx, QRKIT_EINVAL, "window must be in [1, shared_cols]");
+    if (!s->window_start) return fail(ctx, QRKIT_EINVAL, "window_start is required");
+  }
   P.K = s->num_blocks;
   P.n.assign(s->block_rows, s->block_rows + P.K);
   P.m.assign(s->block_cols, s->block_cols + P.K);
@@ -116,10 +128,39 @@ static qrkit_status plan_blocks(qrkit_ctx* ctx, const qrkit_structure* s) {
     P.values += (int64_t)n * m;
     P.max_n = std::max(P.max_n, n);
     P.max_m = std::max(P.max_m, m);
+    if (n < m && P.first_wide < 0) P.first_wide = i;
+    if (n + m > 16 && P.first_tall_aug < 0) P.first_tall_aug = i;
   }
+  P.val_off.assign(P.K + 1, 0);
+  P.row_off.assign(P.K + 1, 0);
+  P.col_off.assign(P.K + 1, 0);
+  for (int64_t i = 0; i < P.K; ++i) {
+    P.val_off[i + 1] = P.val_off[i] + (int64_t)P.n[i] * P.m[i];
+    P.row_off[i + 1] = P.row_off[i] + P.n[i];
+    P.col_off[i + 1] = P.col_off[i] + P.m[i];
+  }
+  if (s->coupled_kind == QRKIT_COUPLED_WINDOW) {
+    P.start.assign(s->window_start, s->window_start + P.K);
+    for (int64_t i = 0; i < P.K; ++i) {
+      if (P.start[i] < 0 || P.start[i] >= s->shared_cols)
+        return fail(ctx, QRKIT_EINVAL, "window_start out of range at block " + std::to_string(i));
+      if (i && P.start[i] < P.start[i - 1])
+        return fail(ctx, QRKIT_EINVAL, "window_start must be non-decreasing (apply P_r)");
+    }
+  }
+  P.composed = s->coupled_kind != QRKIT_COUPLED_NONE;
   P.budget = block_solve_budget(elem_size(ctx));
   cut_tiles(P);
   qrkit_status st;
+  {
+    const size_t ob = (size_t)(P.K + 1) * sizeof(int64_t);
+    if ((st = upload(ctx, P.d_val_off, P.val_off.data(), ob, "plan offsets")) != QRKIT_OK) return st;
+    if ((st = upload(ctx, P.d_row_off, P.row_off.data(), ob, "plan offsets")) != QRKIT_OK) return st;
+    if ((st = upload(ctx, P.d_col_off, P.col_off.data(), ob, "plan offsets")) != QRKIT_OK) return st;
+    if (!P.start.empty())
+      if ((st = upload(ctx, P.d_start, P.start.data(), P.K * sizeof(int32_t), "plan starts")) != QRKIT_OK)
+        return st;
+  }
   if ((st = upload(ctx, P.d_n, P.n.data(), P.K, "plan n")) != QRKIT_OK) return st;
   if ((st = upload(ctx, P.d_m, P.m.data(), P.K, "plan m")) != QRKIT_OK) return st;
   const size_t tb = (size_t)(P.num_tiles + 1) * sizeof(int64_t);
@@ -191,13 +232,8 @@ void qrkit_destroy(qrkit_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
-  Plan& P = ctx->plan;
-  release(P.d_n);
-  release(P.d_m);
-  release(P.d_tile_block);
-  release(P.d_tile_val);
-  release(P.d_tile_row);
-  release(P.d_tile_col);
+  release_plan(ctx->plan);
+  release_composed(ctx->comp);
   release(ctx->ws.factor);
   release(ctx->ws.tau);
   if (ctx->d_status) cudaFree(ctx->d_status);
@@ -213,6 +249,7 @@ qrkit_status qrkit_plan(qrkit_ctx* ctx, const qrkit_structure* s) {
   if (!s) return fail(ctx, QRKIT_EINVAL, "null structure");
   QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   release_plan(ctx->plan);
+  release_composed(ctx->comp);
   ctx->factored = false;
   if (s->kind == QRKIT_STRUCT_BLOCKS) return plan_blocks(ctx, s);
   if (s->kind == QRKIT_STRUCT_BANDED)
@@ -227,18 +264,64 @@ qrkit_status qrkit_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, co
   const Plan& P = ctx->plan;
   if (P.s.kind != QRKIT_STRUCT_BLOCKS || P.s.coupled_kind != QRKIT_COUPLED_NONE)
     return fail(ctx, QRKIT_EINVAL, "qrkit_factor_solve needs a block-diagonal structure");
+  ctx->comp_factored = false;
   if (!J || !b || !p) return fail(ctx, QRKIT_EINVAL, "J, b and p are required");
   if (!(lambda >= 0.0)) return fail(ctx, QRKIT_EINVAL, "lambda must be >= 0");
   if (lambda > 0.0)
     return fail(ctx, QRKIT_EUNSUPPORTED, "damping rows on the fused block path are not available yet");
   if (refine_steps < 0 || refine_steps > 8) return fail(ctx, QRKIT_EINVAL, "refine_steps must be in [0, 8]");
-  for (int64_t i = 0; i < P.K; ++i)
-    if (P.n[i] < P.m[i])
-      return fail(ctx, QRKIT_EINVAL, "block " + std::to_string(i) + " has fewer rows than columns and lambda = 0");
+  if (P.first_wide >= 0)
+    return fail(ctx, QRKIT_EINVAL, "block " + std::to_string(P.first_wide) +
+                " has fewer rows than columns and lambda = 0");
   QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   qrkit_status st = launch_block_solve(ctx, J, b, D, p, qtb, refine_steps);
   if (st == QRKIT_OK) ctx->factored = true;
   return st;
+}
+
+qrkit_status qrkit_factor(qrkit_ctx* ctx, const void* J, const void* S, const void* D, double lambda) {
+  if (!ctx) return QRKIT_EINVAL;
+  if (!ctx->plan.valid) return fail(ctx, QRKIT_ESTATE, "qrkit_factor before qrkit_plan");
+  const Plan& P = ctx->plan;
+  if (P.s.kind != QRKIT_STRUCT_BLOCKS)
+    return fail(ctx, QRKIT_EUNSUPPORTED, "qrkit_factor: only block structures in this build");
+  if (!J) return fail(ctx, QRKIT_EINVAL, "J is required");
+  if (P.s.coupled_kind != QRKIT_COUPLED_NONE && !S)
+    return fail(ctx, QRKIT_EINVAL, "S is required for a coupled structure");
+  if (!(lambda >= 0.0)) return fail(ctx, QRKIT_EINVAL, "lambda must be >= 0");
+  QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  ctx->comp_factored = false;
+  qrkit_status st = composed_factor(ctx, J, S, D, lambda);
+  if (st != QRKIT_OK) return st;
+  ctx->comp.J = J;
+  ctx->comp.S = S;
+  ctx->comp_factored = true;
+  return QRKIT_OK;
+}
+
+qrkit_status qrkit_apply_qt(qrkit_ctx* ctx, const void* b, void* qtb) {
+  if (!ctx) return QRKIT_EINVAL;
+  if (!ctx->comp_factored) return fail(ctx, QRKIT_ESTATE, "qrkit_apply_qt before qrkit_factor");
+  if (!b || !qtb) return fail(ctx, QRKIT_EINVAL, "b and qtb are required");
+  QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  return composed_apply_qt(ctx, b, qtb);
+}
+
+qrkit_status qrkit_solve_r(qrkit_ctx* ctx, const void* qtb, void* p) {
+  if (!ctx) return QRKIT_EINVAL;
+  if (!ctx->comp_factored) return fail(ctx, QRKIT_ESTATE, "qrkit_solve_r before qrkit_factor");
+  if (!qtb || !p) return fail(ctx, QRKIT_EINVAL, "qtb and p are required");
+  QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  return composed_solve_r(ctx, qtb, p);
+}
+
+qrkit_status qrkit_solve(qrkit_ctx* ctx, const void* b, void* p, int refine_steps) {
+  if (!ctx) return QRKIT_EINVAL;
+  if (!ctx->comp_factored) return fail(ctx, QRKIT_ESTATE, "qrkit_solve before qrkit_factor");
+  if (!b || !p) return fail(ctx, QRKIT_EINVAL, "b and p are required");
+  if (refine_steps < 0 || refine_steps > 8) return fail(ctx, QRKIT_EINVAL, "refine_steps must be in [0, 8]");
+  QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  return composed_solve(ctx, ctx->comp.J, ctx->comp.S, b, p, refine_steps);
 }
 
 qrkit_status qrkit_get_factor(qrkit_ctx* ctx, void* factor_out, void* tau_out) {

@@ -22,6 +22,7 @@ struct TileBudget {
   int values;   // J values per tile
   int rows;     // J rows per tile
   int cols;     // columns per tile
+  int padded;   // padded working-area values per tile (rows rounded up to 4, 8 or 16)
 };
 
 // A device buffer owned by the context.
@@ -32,19 +33,83 @@ struct DevBuf {
 
 struct Plan {
   bool valid = false;
+  bool composed = false;  // coupled part present (or damping on a block structure)
   qrkit_structure s{};
   int64_t K = 0;          // blocks
   int64_t rows = 0;       // sum n_i (J rows)
   int64_t cols = 0;       // sum m_i (block columns)
   int64_t values = 0;     // sum n_i m_i
   int max_n = 0, max_m = 0;
+  int64_t first_wide = -1;      // first block with n_i < m_i (needs damping rows), or -1
+  int64_t first_tall_aug = -1;  // first block with n_i + m_i > 16 (no room for damping rows)
   // host copies
   std::vector<uint8_t> n, m;
   std::vector<int64_t> tile_block, tile_val, tile_row, tile_col;
   int64_t num_tiles = 0;
   TileBudget budget{};
+  std::vector<int64_t> val_off, row_off, col_off;   // K + 1 each
+  std::vector<int32_t> start;                      // window starts (QRKIT_COUPLED_WINDOW)
   // device copies
   DevBuf d_n, d_m, d_tile_block, d_tile_val, d_tile_row, d_tile_col;
+  DevBuf d_val_off, d_row_off, d_col_off, d_start;
+};
+
+// Read-only view of a block-angular structure and its values (device pointers).
+template <typename T>
+struct ComposedView {
+  int64_t K;
+  const uint8_t* n;
+  const uint8_t* m;
+  const int64_t* val_off;
+  const int64_t* row_off;
+  const int64_t* col_off;
+  const int32_t* start;
+  int coupled;
+  int s;          // shared columns
+  int w;          // coupled columns per block (s for dense S)
+  int64_t rows;   // J rows (sum n_i), leading dimension of a dense S
+  int64_t nb;     // block columns (sum m_i)
+  const T* J;
+  const T* S;
+};
+
+// Where the composed factor lives.
+template <typename T>
+struct FactorOut {
+  bool damp;
+  double lam_half;
+  const double* D;
+  T* Fa;
+  T* tau;
+  T* R12;
+  T* ctop;
+  const int64_t* aug_off;
+  const int64_t* red_off;
+  T* X0;
+  int64_t ld0;
+  T* Xw;
+  int* status;
+};
+
+struct TsqrLevel {
+  int64_t M = 0;      // rows of the level matrix
+  int64_t tiles = 0;
+  DevBuf X, tau, rhs;
+};
+
+// Device state of the composed factorization.
+struct Composed {
+  bool damp = false;
+  double lam = 0.0, lam_half = 0.0;
+  int tile_rows = 256;
+  int64_t red_rows = 0;            // stacked block bottoms
+  int64_t aug_values_d = 0, aug_values_u = 0;
+  int64_t red_rows_d = 0, red_rows_u = 0;
+  DevBuf D, sq, Fa, tau, R12, ctop, g, h;
+  DevBuf d_aug_off_d, d_aug_off_u, d_red_off_d, d_red_off_u;
+  std::vector<TsqrLevel> levels;
+  const void* J = nullptr;         // caller's values recorded at factor time
+  const void* S = nullptr;
 };
 
 struct Workspace {
@@ -63,9 +128,12 @@ struct qrkit_ctx {
   std::string last_error;
   qrkit::Plan plan;
   qrkit::Workspace ws;
+  qrkit::Composed comp;
   int* d_status = nullptr;   // device status word
   int64_t launches = 0;
-  bool factored = false;
+  size_t smem_attr[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // dynamic smem opted in, per kernel variant
+  bool factored = false;       // fused block path
+  bool comp_factored = false;  // composed path
 };
 
 namespace qrkit {
@@ -79,6 +147,14 @@ inline size_t elem_size(const qrkit_ctx* ctx) {
 }
 
 // Launchers implemented in the kernel translation units.
+qrkit_status composed_layout(qrkit_ctx* ctx, size_t elem);
+qrkit_status widen_to_double(qrkit_ctx* ctx, const float* in, double* out, int64_t n);
+qrkit_status composed_factor(qrkit_ctx* ctx, const void* J, const void* S, const void* D, double lambda);
+qrkit_status composed_solve(qrkit_ctx* ctx, const void* J, const void* S, const void* b, void* p,
+                            int refine_steps);
+qrkit_status composed_apply_qt(qrkit_ctx* ctx, const void* b, void* qtb);
+qrkit_status composed_solve_r(qrkit_ctx* ctx, const void* qtb, void* p);
+void release_composed(Composed& C);
 qrkit_status launch_block_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
                                 void* p, void* qtb, int refine_steps);
 

@@ -56,6 +56,10 @@ _SIGS = {
     "qrkit_plan": (ctypes.c_int, [_VP, ctypes.POINTER(Structure)]),
     "qrkit_factor_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP, ctypes.c_int]),
     "qrkit_get_factor": (ctypes.c_int, [_VP, _VP, _VP]),
+    "qrkit_factor": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double]),
+    "qrkit_apply_qt": (ctypes.c_int, [_VP, _VP, _VP]),
+    "qrkit_solve_r": (ctypes.c_int, [_VP, _VP, _VP]),
+    "qrkit_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
     "qrkit_sync_status": (ctypes.c_int, [_VP]),
     "qrkit_launch_count": (ctypes.c_int64, [_VP]),
 }
@@ -135,7 +139,7 @@ class Context:
         return _ptr(t)
 
     # ---- structure plan ----
-    def plan_blocks(self, n, m):
+    def plan_blocks(self, n, m, coupled=COUPLED_NONE, shared_cols=0, window=0, window_start=None):
         n = np.ascontiguousarray(n, dtype=np.uint8)
         m = np.ascontiguousarray(m, dtype=np.uint8)
         s = Structure()
@@ -143,14 +147,35 @@ class Context:
         s.num_blocks = n.shape[0]
         s.block_rows = n.ctypes.data
         s.block_cols = m.ctypes.data
-        s.coupled_kind = COUPLED_NONE
+        s.coupled_kind = int(coupled)
+        s.shared_cols = int(shared_cols)
+        s.window = int(window)
+        ws = None
+        if window_start is not None:
+            ws = np.ascontiguousarray(window_start, dtype=np.int32)
+            s.window_start = ws.ctypes.data
         self._check(self.lib.qrkit_plan(self.h, ctypes.byref(s)))
+        self._keep = [n, m, ws]
 
     # ---- solves ----
     def factor_solve(self, J, b, p, qtb=None, D=None, lam=0.0, refine_steps=1):
         self._check(self.lib.qrkit_factor_solve(
             self.h, self._t(J, "J"), self._t(b, "b"), self._t(D, "D", True), float(lam),
             self._t(p, "p"), self._t(qtb, "qtb", True), int(refine_steps)))
+
+    def factor(self, J, S=None, D=None, lam=0.0):
+        self._check(self.lib.qrkit_factor(self.h, self._t(J, "J"), self._t(S, "S", True),
+                                          self._t(D, "D", True), float(lam)))
+        self._refs = (J, S, D)   # the library reads J and S again during refinement
+
+    def apply_qt(self, b, qtb):
+        self._check(self.lib.qrkit_apply_qt(self.h, self._t(b, "b"), self._t(qtb, "qtb")))
+
+    def solve_r(self, qtb, p):
+        self._check(self.lib.qrkit_solve_r(self.h, self._t(qtb, "qtb"), self._t(p, "p")))
+
+    def solve(self, b, p, refine_steps=1):
+        self._check(self.lib.qrkit_solve(self.h, self._t(b, "b"), self._t(p, "p"), int(refine_steps)))
 
     def get_factor(self, factor=None, tau=None):
         self._check(self.lib.qrkit_get_factor(self.h, self._t(factor, "factor", True),
