@@ -146,6 +146,37 @@ qrkit_status qrkit_solve_r(qrkit_ctx* ctx, const void* qtb, void* p);
  * QRKIT_FP32, allowed but not useful for QRKIT_FP64). */
 qrkit_status qrkit_solve(qrkit_ctx* ctx, const void* b, void* p, int refine_steps);
 
+/* Size of the device array behind qrkit_block_solve_noalloc (16 MiB per device). */
+#define QRKIT_NOALLOC_SCRATCH_BYTES (16u << 20)
+
+/* Block-diagonal factor + solve that allocates no device memory.  The paper has no
+ * counterpart: this exists for callers that cannot call cudaMalloc, such as code running
+ * under a framework that owns all device memory through its own pool, or a process whose
+ * device memory budget is fixed when it starts.
+ * It solves the same problem as qrkit_plan + qrkit_factor_solve for QRKIT_STRUCT_BLOCKS /
+ * QRKIT_COUPLED_NONE with lambda = 0 and no qtb output, without a context:
+ *   device, stream, precision : as for qrkit_create (stream: a cudaStream_t or NULL)
+ *   block_rows, block_cols    : HOST arrays of num_blocks shapes (1 <= m_i <= n_i <= 16, m_i <= 8)
+ *   J, b, p                   : DEVICE buffers as for qrkit_factor_solve (caller-owned)
+ *   refine_steps              : as for qrkit_factor_solve (FP32 refined mode only)
+ * All intermediates (shapes, tile schedule, factor, tau, status word) live in one device array
+ * of QRKIT_NOALLOC_SCRATCH_BYTES that is part of the library image: every process that loads
+ * the library holds it on each device it uses until the process exits.  A problem whose
+ * intermediates do not fit (roughly sum n_i m_i above 3.5 million values in FP32, half that
+ * in FP64) is rejected with QRKIT_EUNSUPPORTED before anything is launched; bad arguments give
+ * QRKIT_EINVAL, a failed CUDA call QRKIT_ECUDA.
+ * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
+ * that device current; make that first call before any stream capture.  Each call copies the
+ * shapes and schedule into the array, clears its status word, launches one kernel on `stream`,
+ * then waits for the stream and returns the kernel's status (QRKIT_OK, QRKIT_ESINGULAR, ...).
+ * Every call uses the same array and leaves its contents behind: calls whose work overlaps on
+ * the GPU (other threads, other streams) race and must be serialized by the caller.  The
+ * factor is not kept for later calls. */
+qrkit_status qrkit_block_solve_noalloc(int device, void* stream, int precision,
+                                       int64_t num_blocks, const uint8_t* block_rows,
+                                       const uint8_t* block_cols, const void* J, const void* b,
+                                       void* p, int refine_steps);
+
 /* Copy the stored factor of a block structure to caller buffers (device pointers, either
  * may be NULL): factor values in J's packing (V strictly below the diagonal, R on and above)
  * and tau (sum m_i). */

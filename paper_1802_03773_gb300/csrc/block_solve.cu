@@ -17,6 +17,9 @@
 #include <math.h>
 #include <stdint.h>
 
+#include <mutex>
+#include <type_traits>
+
 #include "internal.h"
 
 namespace qrkit {
@@ -688,6 +691,17 @@ block_solve_kernel(BlockSolveArgs<T> A) {
   store_out(A.x + g.c0, sX, g.nc);
 }
 
+// Launch with fully formed arguments (opting the kernel in to its dynamic shared memory).
+template <typename T, bool REF>
+cudaError_t launch_block_kernel(const BlockSolveArgs<T>& A, cudaStream_t st) {
+  const size_t smem = make_layout<T>(A.vb, A.rb, A.cb, A.bb, A.pb, REF).total;
+  auto kern = block_solve_kernel<T, REF>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+  if (e != cudaSuccess) return e;
+  kern<<<(unsigned)A.num_tiles, kThreads, smem, st>>>(A);
+  return cudaGetLastError();
+}
+
 template <typename T, bool REF>
 qrkit_status launch_typed(qrkit_ctx* ctx, const void* J, const void* b, void* p, void* qtb,
                           int refine_steps) {
@@ -755,3 +769,141 @@ qrkit_status launch_block_solve(qrkit_ctx* ctx, const void* J, const void* b, co
 }
 
 }  // namespace qrkit
+
+// ---------------------------------------------------------------------------------------
+// Allocation-free variant of the batched block solve.
+//
+// Some callers cannot call cudaMalloc at all: code that runs under a framework owning every
+// byte of device memory through its own pool, or a process whose memory budget is fixed
+// once at start-up.  For them qrkit_block_solve_noalloc runs the same kernel as
+// qrkit_factor_solve without a context and without allocating: every intermediate it needs
+// (block shapes, tile schedule, factor values, tau, status word) lives in the file-scope
+// array below.  The array is part of the library image, so every process that loads the
+// library holds it on each device it uses until the process exits.
+namespace qrkit {
+namespace {
+
+constexpr size_t kNoallocScratchBytes = (size_t)QRKIT_NOALLOC_SCRATCH_BYTES;
+static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratchBytes];
+
+// Device address of g_noalloc_scratch, looked up once per device with that device current.
+// A host-side reference to g_noalloc_scratch is only a host stand-in, never a device address.
+unsigned char* g_noalloc_ptr[64] = {nullptr};
+std::mutex g_noalloc_mutex;
+
+size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+}  // namespace
+
+}  // namespace qrkit
+
+extern "C" qrkit_status qrkit_block_solve_noalloc(int device, void* stream, int precision,
+                                                  int64_t num_blocks, const uint8_t* block_rows,
+                                                  const uint8_t* block_cols, const void* J,
+                                                  const void* b, void* p, int refine_steps) {
+  using namespace qrkit;
+  if (device < 0 || device >= 64) return QRKIT_EINVAL;
+  if (precision < QRKIT_FP64 || precision > QRKIT_FP32) return QRKIT_EINVAL;
+  if (num_blocks < 1 || !block_rows || !block_cols || !J || !b || !p) return QRKIT_EINVAL;
+  if (refine_steps < 0 || refine_steps > 8) return QRKIT_EINVAL;
+  // host-side plan: the same tile schedule as qrkit_plan builds
+  Plan P;
+  P.K = num_blocks;
+  P.n.assign(block_rows, block_rows + num_blocks);
+  P.m.assign(block_cols, block_cols + num_blocks);
+  for (int64_t i = 0; i < P.K; ++i) {
+    const int n = P.n[i], m = P.m[i];
+    if (n < 1 || m < 1 || n < m) return QRKIT_EINVAL;
+    if (n > kMaxRows || m > kMaxCols) return QRKIT_EUNSUPPORTED;
+    P.rows += n;
+    P.cols += m;
+    P.values += (int64_t)n * m;
+    P.max_m = P.max_m > m ? P.max_m : m;
+  }
+  const size_t elem = precision == QRKIT_FP64 ? sizeof(double) : sizeof(float);
+  P.budget = block_solve_budget(elem);
+  cut_tiles_for(P);
+  // scratch layout; reject problems that do not fit
+  const size_t tb = (size_t)(P.num_tiles + 1) * sizeof(int64_t);
+  size_t off = 0;
+  const size_t o_status = off; off = align256(off + sizeof(int));
+  const size_t o_n = off; off = align256(off + (size_t)P.K);
+  const size_t o_m = off; off = align256(off + (size_t)P.K);
+  const size_t o_tb = off; off = align256(off + tb);
+  const size_t o_tv = off; off = align256(off + tb);
+  const size_t o_tr = off; off = align256(off + tb);
+  const size_t o_tc = off; off = align256(off + tb);
+  const size_t o_F = off; off = align256(off + (size_t)P.values * elem);
+  const size_t o_tau = off; off = align256(off + (size_t)P.cols * elem);
+  if (off > kNoallocScratchBytes) return QRKIT_EUNSUPPORTED;
+  cudaError_t e = cudaSetDevice(device);
+  if (e != cudaSuccess) return QRKIT_ECUDA;
+  unsigned char* base = nullptr;
+  {
+    std::lock_guard<std::mutex> lock(g_noalloc_mutex);
+    if (!g_noalloc_ptr[device]) {
+      void* ptr = nullptr;
+      e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+      if (e != cudaSuccess || !ptr) return QRKIT_ECUDA;
+      g_noalloc_ptr[device] = static_cast<unsigned char*>(ptr);
+    }
+    base = g_noalloc_ptr[device];
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  // the array keeps the previous call's contents: the status word must start at zero;
+  // every other region used here is written in full before it is read
+  if ((e = cudaMemsetAsync(base + o_status, 0, sizeof(int), st)) != cudaSuccess) return QRKIT_ECUDA;
+  struct Up { size_t off; const void* src; size_t bytes; } ups[] = {
+      {o_n, P.n.data(), (size_t)P.K}, {o_m, P.m.data(), (size_t)P.K},
+      {o_tb, P.tile_block.data(), tb}, {o_tv, P.tile_val.data(), tb},
+      {o_tr, P.tile_row.data(), tb}, {o_tc, P.tile_col.data(), tb}};
+  for (const Up& u : ups)
+    if ((e = cudaMemcpyAsync(base + u.off, u.src, u.bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess)
+      return QRKIT_ECUDA;
+  int* status = reinterpret_cast<int*>(base + o_status);
+  auto fill = [&](auto* tag) {
+    using T = std::remove_pointer_t<decltype(tag)>;
+    BlockSolveArgs<T> A;
+    A.n = base + o_n;
+    A.m = base + o_m;
+    A.tile_block = reinterpret_cast<const int64_t*>(base + o_tb);
+    A.tile_val = reinterpret_cast<const int64_t*>(base + o_tv);
+    A.tile_row = reinterpret_cast<const int64_t*>(base + o_tr);
+    A.tile_col = reinterpret_cast<const int64_t*>(base + o_tc);
+    A.num_tiles = P.num_tiles;
+    A.J = static_cast<const T*>(J);
+    A.b = static_cast<const T*>(b);
+    A.F = reinterpret_cast<T*>(base + o_F);
+    A.tau = reinterpret_cast<T*>(base + o_tau);
+    A.qtb = nullptr;
+    A.x = static_cast<T*>(p);
+    A.refine_tol = 1e-6f;
+    A.status = status;
+    A.vb = P.budget.values;
+    A.rb = P.budget.rows;
+    A.cb = P.budget.cols;
+    A.bb = P.budget.blocks;
+    A.pb = P.budget.padded;
+    A.wait_limit = 1LL << 26;
+    return A;
+  };
+  if (precision == QRKIT_FP64) {
+    BlockSolveArgs<double> A = fill((double*)nullptr);
+    A.refine_steps = 0;
+    e = launch_block_kernel<double, false>(A, st);
+  } else if (precision == QRKIT_FP32 || refine_steps == 0) {
+    BlockSolveArgs<float> A = fill((float*)nullptr);
+    A.refine_steps = 0;
+    e = launch_block_kernel<float, false>(A, st);
+  } else {
+    BlockSolveArgs<float> A = fill((float*)nullptr);
+    A.refine_steps = refine_steps;
+    e = launch_block_kernel<float, true>(A, st);
+  }
+  if (e != cudaSuccess) return QRKIT_ECUDA;
+  // the call returns only after the solve: read the device status word back (no allocation)
+  if ((e = cudaStreamSynchronize(st)) != cudaSuccess) return QRKIT_ECUDA;
+  int h = 0;
+  if ((e = cudaMemcpy(&h, status, sizeof(int), cudaMemcpyDeviceToHost)) != cudaSuccess) return QRKIT_ECUDA;
+  return (qrkit_status)h;
+}

@@ -68,7 +68,7 @@ static void release_plan(Plan& P) {
 }
 
 // Greedy tile schedule: consecutive blocks while every budget holds.
-static void cut_tiles(Plan& P) {
+void cut_tiles_for(Plan& P) {
   const TileBudget& B = P.budget;
   P.tile_block.assign(1, 0);
   P.tile_val.assign(1, 0);
@@ -150,7 +150,7 @@ static qrkit_status plan_blocks(qrkit_ctx* ctx, const qrkit_structure* s) {
   }
   P.composed = s->coupled_kind != QRKIT_COUPLED_NONE;
   P.budget = block_solve_budget(elem_size(ctx));
-  cut_tiles(P);
+  cut_tiles_for(P);
   qrkit_status st;
   {
     const size_t ob = (size_t)(P.K + 1) * sizeof(int64_t);

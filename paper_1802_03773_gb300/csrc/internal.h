@@ -146,6 +146,10 @@ inline size_t elem_size(const qrkit_ctx* ctx) {
   return ctx->precision == QRKIT_FP64 ? sizeof(double) : sizeof(float);
 }
 
+// Tile schedule of the persistent block kernels (fills P.tile_* and P.num_tiles).
+void cut_tiles_for(Plan& P);
+TileBudget block_solve_budget(size_t elem);
+
 // Launchers implemented in the kernel translation units.
 qrkit_status composed_layout(qrkit_ctx* ctx, size_t elem);
 qrkit_status widen_to_double(qrkit_ctx* ctx, const float* in, double* out, int64_t n);

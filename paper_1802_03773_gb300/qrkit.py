@@ -61,6 +61,8 @@ _SIGS = {
     "qrkit_solve_r": (ctypes.c_int, [_VP, _VP, _VP]),
     "qrkit_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
     "qrkit_sync_status": (ctypes.c_int, [_VP]),
+    "qrkit_block_solve_noalloc": (ctypes.c_int, [ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int64, _VP,
+                                                 _VP, _VP, _VP, _VP, ctypes.c_int]),
     "qrkit_launch_count": (ctypes.c_int64, [_VP]),
 }
 
@@ -82,6 +84,27 @@ def load(path: str = LIB_PATH):
         fn.argtypes = args
     _lib = lib
     return lib
+
+
+def block_solve_noalloc(n, m, J, b, p, precision="fp32_refined", refine_steps=2, stream=None):
+    """qrkit_block_solve_noalloc: the batched block solve without any device allocation.
+
+    n, m: host arrays of block shapes; J, b, p: CUDA tensors (inputs / output).  Blocks until
+    the solve has finished and raises QRKitError on a non-zero status.
+    """
+    import torch
+    lib = load()
+    prec = PRECISION[precision] if isinstance(precision, str) else int(precision)
+    n = np.ascontiguousarray(n, dtype=np.uint8)
+    m = np.ascontiguousarray(m, dtype=np.uint8)
+    dev = J.device.index if J.device.index is not None else torch.cuda.current_device()
+    if stream is None:
+        stream = torch.cuda.current_stream(J.device)
+    st = lib.qrkit_block_solve_noalloc(dev, _VP(stream.cuda_stream), prec, n.shape[0],
+                                       n.ctypes.data, m.ctypes.data, _ptr(J), _ptr(b), _ptr(p),
+                                       int(refine_steps))
+    if st != 0:
+        raise QRKitError(st, "qrkit_block_solve_noalloc failed")
 
 
 def declared_symbols():
