@@ -75,9 +75,13 @@ typedef struct qrkit_structure {
   int32_t window;               /* w for QRKIT_COUPLED_WINDOW */
   const int32_t* window_start;  /* host, K entries, non-decreasing, start_i + w <= s + w - 1 */
   /* --- QRKIT_STRUCT_BANDED --- */
-  int64_t rows, cols;           /* J is rows x cols */
+  int64_t rows, cols;           /* one instance: J is (rows_per_col * cols) x cols */
   int32_t rows_per_col;         /* row i starts at column floor(i / rows_per_col) */
-  int32_t band_window;          /* w: values per row (entries past the last column ignored) */
+  int32_t band_window;          /* w: values per row, 1..16 (entries past the last column
+                                   are ignored) */
+  const int64_t* instance_cols; /* host, num_blocks entries: a batch of independent banded
+                                   instances with these column counts (NULL: one instance
+                                   of `cols` columns) */
 } qrkit_structure;
 
 typedef struct qrkit_ctx qrkit_ctx;
@@ -117,6 +121,13 @@ qrkit_status qrkit_plan(qrkit_ctx* ctx, const qrkit_structure* s);
  * One kernel launch; asynchronous on the context's stream. */
 qrkit_status qrkit_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
                                 double lambda, void* p, void* qtb, int refine_steps);
+
+/* For a QRKIT_STRUCT_BANDED plan, qrkit_factor_solve factors and solves every instance of
+ * the batch (Sec. 4.4 block-banded QR, damping rows interleaved per column as in Sec. 4.5 /
+ * Sec. 5.2): J holds the instances' rows back to back, row-major with band_window values per
+ * row; b one value per row; D (total columns, or NULL for column norms, zero -> 1) as above;
+ * lambda >= 0; p one value per column; qtb must be NULL; refine_steps: steps of refinement
+ * with a double residual (FP32 refined mode).  Q is not kept. */
 
 /* Composed factorization (Sec. 3 composition; Sec. 4.1 block diagonal, Sec. 4.2 horizontal
  * concatenation, Sec. 4.5 vertical concatenation of the damping rows, Sec. 5.2 Backtrack LM):
@@ -176,6 +187,11 @@ qrkit_status qrkit_block_solve_noalloc(int device, void* stream, int precision,
                                        int64_t num_blocks, const uint8_t* block_rows,
                                        const uint8_t* block_cols, const void* J, const void* b,
                                        void* p, int refine_steps);
+
+/* Banded factor of the last qrkit_factor_solve on a QRKIT_STRUCT_BANDED plan (device pointers,
+ * any may be NULL): Rw[j * w + t] = R[j, j + t] per global column j, c = top of Q^T [b; 0] per
+ * column; res2 (HOST, one double per instance) = squared residual norm.  Synchronous. */
+qrkit_status qrkit_get_band_factor(qrkit_ctx* ctx, void* Rw, void* c, double* res2);
 
 /* Copy the stored factor of a block structure to caller buffers (device pointers, either
  * may be NULL): factor values in J's packing (V strictly below the diagonal, R on and above)

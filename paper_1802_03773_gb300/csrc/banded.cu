@@ -1,0 +1,467 @@
+// Block-banded QR of P_r [J; lambda^(1/2) D] (Sec. 4.4 "Block banded", Sec. 4.5 / Sec. 5.2
+// row interleave of the damping rows) and the banded solve, for batches of independent
+// banded instances.
+//
+// J row i of an instance touches columns floor(i / rows_per_col) .. + w - 1 (entries past the
+// last column are ignored); values are stored row-major, w per row.  The damping row of
+// column j has the single value lambda^(1/2) D_j at column j.
+//
+// Work mapping: one warp per instance, several instances per CTA.  The warp sweeps column
+// groups [c0, c0 + 8): the front holds the rows carried from the previous group (at most
+// w - 1, non-zero only from column c0 on) plus the J rows and damping rows whose first column
+// lies in the group; rows are appended in batches to a shared-memory front and reduced by
+// Householder reflections (Sec. 2) with lanes over columns, so the front never holds more
+// than (group + w - 1) + batch rows however dense the rows are.  After the last batch the
+// group's R rows are final (written as windows R[j, j .. j + w - 1]) and the next w - 1 rows
+// are carried.  Every Householder vector is as long as its front, never as long as the
+// matrix (Sec. 4.4).  Q is not kept: the right-hand side is reflected along with the front.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "internal.h"
+
+namespace qrkit {
+namespace {
+
+constexpr int kBG = 8;          // columns per group
+constexpr int kBW = 16;         // largest band window
+constexpr int kBatch = 48;      // new rows appended per front reduction
+constexpr int kFCols = kBG + kBW - 1 + 1;      // front columns incl. the rhs column
+constexpr int kFStride = kFCols + 1;           // padded row stride (bank spread)
+constexpr int kFRows = kBG + kBW - 1 + kBatch; // kept rows + one batch
+constexpr int kWarps = 4;                      // instances per CTA (float)
+template <typename T> constexpr int warps_for() { return sizeof(T) == sizeof(double) ? 2 : kWarps; }
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+  return v;
+}
+
+__device__ __forceinline__ void brecord(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+template <typename T>
+struct BandArgs {
+  int64_t num_inst;
+  const int64_t* inst_cols;   // columns per instance
+  const int64_t* inst_col0;   // first global column of each instance
+  const int64_t* inst_row0;   // first J row of each instance
+  int rows_per_col;
+  int w;                      // band window (<= kBW)
+  const T* J;                 // rows x w, row-major
+  const T* b;                 // rows
+  const double* D;            // global columns (may be null when !damp)
+  double lam;                 // lambda (damping rows present iff lam > 0)
+  T* Rw;                      // global columns x w: R[j, j + t] at Rw[j * w + t]
+  T* c;                       // global columns: top of Q^T [b; 0]
+  T* x;                       // global columns: solution
+  double* res2;               // per instance: squared norm of the rest of Q^T [b; 0]
+  int refine_steps;
+  int* status;
+};
+
+// One reduction of the front F (nr rows x fc columns + rhs column fc) by Householder
+// reflections, column by column; lanes over columns for the dot products and updates.
+template <typename T>
+__device__ __forceinline__ void front_qr(T* F, int nr, int fc, int lane) {
+  const int kmax = nr < fc ? nr : fc;
+  for (int k = 0; k < kmax; ++k) {
+    T s = 0;
+    for (int r = k + 1 + lane; r < nr; r += 32) {
+      const T a = F[r * kFStride + k];
+      s += a * a;
+    }
+    s = warp_sum(s);
+    const T alpha = F[k * kFStride + k];
+    const T norm = sqrt(alpha * alpha + s);
+    T beta = 0, tau = 0, scale = 0;
+    if (norm != T(0)) {
+      beta = alpha >= T(0) ? -norm : norm;
+      tau = (beta - alpha) / beta;
+      scale = T(1) / (alpha - beta);
+    }
+    for (int r = k + 1 + lane; r < nr; r += 32) F[r * kFStride + k] *= scale;
+    __syncwarp();
+    const int j = k + 1 + lane;   // one lane per trailing column (incl. the rhs column fc)
+    if (j <= fc) {
+      T wv = F[k * kFStride + j];
+      for (int r = k + 1; r < nr; ++r) wv += F[r * kFStride + k] * F[r * kFStride + j];
+      wv *= tau;
+      F[k * kFStride + j] -= wv;
+      for (int r = k + 1; r < nr; ++r) F[r * kFStride + j] -= wv * F[r * kFStride + k];
+    }
+    __syncwarp();
+    if (lane == 0) F[k * kFStride + k] = beta;
+    for (int r = k + 1 + lane; r < nr; r += 32) F[r * kFStride + k] = T(0);
+    __syncwarp();
+  }
+}
+
+template <typename T>
+__global__ void __launch_bounds__(32 * kWarps)
+banded_factor_solve_kernel(BandArgs<T> A) {
+  constexpr int NW = warps_for<T>();   // static shared memory stays under 48 KB
+  __shared__ __align__(16) T sF[NW][kFRows * kFStride];
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  const int64_t inst = (int64_t)blockIdx.x * NW + wid;
+  if (inst >= A.num_inst) return;
+  T* F = sF[wid];
+  const int w = A.w;
+  const int64_t N = A.inst_cols[inst];
+  const int64_t col0 = A.inst_col0[inst];
+  const int64_t row0 = A.inst_row0[inst];
+  const int64_t nrows = (int64_t)A.rows_per_col * N;
+  const bool damp = A.lam > 0.0;
+  const double lam_half = sqrt(A.lam);
+  double res2 = 0.0;
+  int carried = 0;   // rows 0 .. carried-1 of F hold the carried rows (columns from c0 on)
+  for (int e = lane; e < kFRows * kFStride; e += 32) F[e] = T(0);
+  __syncwarp();
+  for (int64_t c0 = 0; c0 < N; c0 += kBG) {
+    const int64_t c1 = c0 + kBG < N ? c0 + kBG : N;
+    const int g = (int)(c1 - c0);
+    const int64_t hi = c1 + w - 1 < N ? c1 + w - 1 : N;
+    const int fc = (int)(hi - c0);            // front columns; the rhs sits in column fc
+    // the rhs column index changes with fc: move the carried rows' rhs into place
+    // (carried rows were written with the rhs at column kFCols - 1, see below)
+    for (int r = lane; r < carried; r += 32) {
+      const T rhs = F[r * kFStride + (kFCols - 1)];
+      F[r * kFStride + (kFCols - 1)] = T(0);
+      F[r * kFStride + fc] = rhs;
+    }
+    __syncwarp();
+    int nr = carried;
+    // stream of new rows: J rows starting in [c0, c1), then the damping rows of c0 .. c1-1
+    int64_t jr = (int64_t)A.rows_per_col * c0;
+    const int64_t jr_end = (int64_t)A.rows_per_col * c1 < nrows ? (int64_t)A.rows_per_col * c1 : nrows;
+    int64_t dr = damp ? c0 : c1;
+    while (jr < jr_end || dr < c1) {
+      const int room = kFRows - nr;
+      const int64_t take_j = jr_end - jr < room ? jr_end - jr : room;
+      const int64_t take_d = (c1 - dr) < (room - take_j) ? (c1 - dr) : (room - take_j);
+      // append (lanes over new rows); each row is cleared first
+      for (int t = lane; t < (int)(take_j + take_d); t += 32) {
+        T* row = F + (nr + t) * kFStride;
+        for (int q = 0; q < kFStride; ++q) row[q] = T(0);
+        if (t < take_j) {
+          const int64_t i = jr + t;
+          const int64_t start = i / A.rows_per_col;
+          const T* src = A.J + (row0 + i) * w;
+          for (int q = 0; q < w; ++q) {
+            const int64_t col = start + q;
+            if (col < N) row[col - c0] = src[q];
+          }
+          row[fc] = A.b[row0 + i];
+        } else {
+          const int64_t j = dr + (t - take_j);
+          row[j - c0] = (T)(lam_half * A.D[col0 + j]);
+        }
+      }
+      __syncwarp();
+      nr += (int)(take_j + take_d);
+      jr += take_j;
+      dr += take_d;
+      front_qr(F, nr, fc, lane);
+      // rows beyond the triangle are now zero: their rhs is residual
+      double part = 0.0;
+      for (int r = fc + lane; r < nr; r += 32) {
+        const double v = (double)F[r * kFStride + fc];
+        part += v * v;
+        F[r * kFStride + fc] = T(0);
+      }
+      res2 += warp_sum(part);
+      nr = nr < fc ? nr : fc;
+      __syncwarp();
+    }
+    if (nr < g) {
+      brecord(A.status, QRKIT_ESINGULAR);   // fewer rows than columns in this group
+    }
+    // final R rows of the group
+    for (int i = lane; i < g; i += 32) {
+      const int64_t gj = col0 + c0 + i;
+      for (int t = 0; t < w; ++t) {
+        const int colf = i + t;
+        A.Rw[gj * w + t] = (colf < fc && i < nr) ? F[i * kFStride + colf] : T(0);
+      }
+      A.c[gj] = i < nr ? F[i * kFStride + fc] : T(0);
+    }
+    __syncwarp();
+    // carry rows g .. nr-1, shifted left by g columns; rhs parked in column kFCols - 1
+    const int nc = nr - g > 0 ? nr - g : 0;
+    if (c1 < N) {
+      // ascending rows: the source row g + r is read before any later row overwrites it
+      for (int r = 0; r < nc; ++r) {
+        const T* src = F + (g + r) * kFStride;
+        T v = T(0);
+        if (lane < kFCols - 1 && lane + g < fc) v = src[lane + g];
+        const T rhs = src[fc];
+        __syncwarp();
+        T* dst = F + r * kFStride;
+        if (lane < kFCols - 1) dst[lane] = v;
+        if (lane == 0) dst[kFCols - 1] = rhs;
+        __syncwarp();
+      }
+      // clear the rows above the carried ones
+      for (int e = nc * kFStride + lane; e < kFRows * kFStride; e += 32) F[e] = T(0);
+      __syncwarp();
+    }
+    carried = nc;
+  }
+  if (lane == 0) A.res2[inst] = res2;
+  // back-substitution R x = c on the banded R (one lane; the recurrence is sequential)
+  if (lane == 0) {
+    bool bad = false;
+    for (int64_t j = N - 1; j >= 0; --j) {
+      const int64_t gj = col0 + j;
+      T s = A.c[gj];
+      for (int t = 1; t < w && j + t < N; ++t) s -= A.Rw[gj * w + t] * A.x[gj + t];
+      const T rjj = A.Rw[gj * w];
+      if (rjj == T(0)) bad = true;
+      A.x[gj] = s / rjj;
+    }
+    if (bad) brecord(A.status, QRKIT_ESINGULAR);
+  }
+}
+
+// ---- refinement for float instances: r = b - J x in double (one lane per row), then
+// g = J^T r - lambda D^2 x (one lane per column), then x += R^{-1} R^{-T} g by banded
+// triangular solves; one warp per instance ----
+__global__ void __launch_bounds__(32 * kWarps)
+banded_refine_kernel(BandArgs<float> A, double* rbuf, double* gbuf, float* hbuf) {
+  const int lane = threadIdx.x & 31;
+  const int wid = threadIdx.x >> 5;
+  const int64_t inst = (int64_t)blockIdx.x * kWarps + wid;
+  if (inst >= A.num_inst) return;
+  const int w = A.w;
+  const int rpc = A.rows_per_col;
+  const int64_t N = A.inst_cols[inst];
+  const int64_t col0 = A.inst_col0[inst];
+  const int64_t row0 = A.inst_row0[inst];
+  const int64_t nrows = (int64_t)rpc * N;
+  for (int64_t i = lane; i < nrows; i += 32) {
+    const int64_t s = i / rpc;
+    const float* row = A.J + (row0 + i) * w;
+    double r = (double)A.b[row0 + i];
+    for (int t = 0; t < w && s + t < N; ++t) r -= (double)row[t] * (double)A.x[col0 + s + t];
+    rbuf[row0 + i] = r;
+  }
+  __syncwarp();
+  for (int64_t j = lane; j < N; j += 32) {
+    double acc = 0.0;
+    const int64_t s_lo = j - w + 1 > 0 ? j - w + 1 : 0;
+    for (int64_t s = s_lo; s <= j; ++s)
+      for (int q = 0; q < rpc; ++q) {
+        const int64_t i = s * rpc + q;
+        if (i >= nrows) break;
+        acc += (double)A.J[(row0 + i) * w + (j - s)] * rbuf[row0 + i];
+      }
+    if (A.lam > 0.0) {
+      const double d = A.D[col0 + j];
+      acc -= A.lam * d * d * (double)A.x[col0 + j];
+    }
+    gbuf[col0 + j] = acc;
+  }
+  __syncwarp();
+  if (lane == 0) {
+    // R^T h = g (forward): h_j = (g_j - sum_{t=1}^{w-1} R[j-t, j] h_{j-t}) / R[j, j]
+    for (int64_t j = 0; j < N; ++j) {
+      const int64_t gj = col0 + j;
+      float s = (float)gbuf[gj];
+      for (int t = 1; t < w && j - t >= 0; ++t) s -= A.Rw[(gj - t) * w + t] * hbuf[gj - t];
+      hbuf[gj] = s / A.Rw[gj * w];
+    }
+    // R dx = h (backward), x += dx
+    for (int64_t j = N - 1; j >= 0; --j) {
+      const int64_t gj = col0 + j;
+      float s = hbuf[gj];
+      for (int t = 1; t < w && j + t < N; ++t) s -= A.Rw[gj * w + t] * hbuf[gj + t];
+      hbuf[gj] = s / A.Rw[gj * w];
+    }
+    for (int64_t j = 0; j < N; ++j) A.x[col0 + j] += hbuf[col0 + j];
+  }
+}
+
+__global__ void band_colnorm_kernel(const float* Jf, const double* Jd, const int64_t* inst_cols,
+                                    const int64_t* inst_col0, const int64_t* inst_row0,
+                                    int64_t num_inst, int rpc, int w, double* D) {
+  // one thread per global column: rows touching column j start in [j - w + 1, j]
+  const int64_t total = inst_col0[num_inst - 1] + inst_cols[num_inst - 1];
+  const int64_t gj = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (gj >= total) return;
+  int64_t lo = 0, hi = num_inst - 1;
+  while (lo < hi) {   // instance of column gj
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (inst_col0[mid] <= gj) lo = mid; else hi = mid - 1;
+  }
+  const int64_t inst = lo, j = gj - inst_col0[inst], N = inst_cols[inst];
+  const int64_t nrows = (int64_t)rpc * N;
+  double acc = 0.0;
+  const int64_t s_lo = j - w + 1 > 0 ? j - w + 1 : 0;
+  for (int64_t s = s_lo; s <= j; ++s)
+    for (int q = 0; q < rpc; ++q) {
+      const int64_t i = s * rpc + q;
+      if (i >= nrows) break;
+      const int64_t e = (inst_row0[inst] + i) * w + (j - s);
+      const double v = Jf ? (double)Jf[e] : Jd[e];
+      acc += v * v;
+    }
+  const double d = sqrt(acc);
+  D[gj] = d == 0.0 ? 1.0 : d;
+}
+
+inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
+
+}  // namespace
+
+qrkit_status banded_plan(qrkit_ctx* ctx, const qrkit_structure* s) {
+  Plan& P = ctx->plan;
+  if (s->rows_per_col < 1) return fail(ctx, QRKIT_EINVAL, "rows_per_col must be >= 1");
+  if (s->band_window < 1 || s->band_window > kBW)
+    return fail(ctx, QRKIT_EUNSUPPORTED, "band_window must be in [1, 16]");
+  std::vector<int64_t> cols;
+  if (s->num_blocks > 0 && s->instance_cols) {
+    cols.assign(s->instance_cols, s->instance_cols + s->num_blocks);
+  } else {
+    if (s->cols < 1) return fail(ctx, QRKIT_EINVAL, "cols must be >= 1");
+    cols.assign(1, s->cols);
+  }
+  for (size_t i = 0; i < cols.size(); ++i)
+    if (cols[i] < 1) return fail(ctx, QRKIT_EINVAL, "instance " + std::to_string(i) + " has no columns");
+  std::vector<int64_t> c0(cols.size()), r0(cols.size());
+  int64_t cc = 0, rr = 0;
+  for (size_t i = 0; i < cols.size(); ++i) {
+    c0[i] = cc;
+    r0[i] = rr;
+    cc += cols[i];
+    rr += cols[i] * s->rows_per_col;
+  }
+  Band& B = ctx->band;
+  B.num_inst = (int64_t)cols.size();
+  B.total_cols = cc;
+  B.total_rows = rr;
+  B.rows_per_col = s->rows_per_col;
+  B.w = s->band_window;
+  qrkit_status st;
+  auto up = [&](DevBuf& buf, const std::vector<int64_t>& v) -> qrkit_status {
+    qrkit_status r = ensure(ctx, buf, v.size() * sizeof(int64_t), "band plan");
+    if (r != QRKIT_OK) return r;
+    QRKIT_CUDA_TRY(ctx, cudaMemcpy(buf.ptr, v.data(), v.size() * sizeof(int64_t), cudaMemcpyHostToDevice));
+    return QRKIT_OK;
+  };
+  if ((st = up(B.d_cols, cols)) != QRKIT_OK) return st;
+  if ((st = up(B.d_col0, c0)) != QRKIT_OK) return st;
+  if ((st = up(B.d_row0, r0)) != QRKIT_OK) return st;
+  const size_t es = elem_size(ctx);
+  if ((st = ensure(ctx, B.Rw, (size_t)cc * B.w * es, "banded R")) != QRKIT_OK) return st;
+  if ((st = ensure(ctx, B.c, (size_t)cc * es, "banded c")) != QRKIT_OK) return st;
+  if ((st = ensure(ctx, B.D, (size_t)cc * sizeof(double), "banded D")) != QRKIT_OK) return st;
+  if ((st = ensure(ctx, B.res2, (size_t)B.num_inst * sizeof(double), "banded residual")) != QRKIT_OK) return st;
+  P.s = *s;
+  P.s.block_rows = nullptr;
+  P.s.block_cols = nullptr;
+  P.s.window_start = nullptr;
+  P.s.instance_cols = nullptr;
+  P.valid = true;
+  return QRKIT_OK;
+}
+
+template <typename T>
+static qrkit_status banded_run(qrkit_ctx* ctx, const void* J, const void* b, const void* Dext,
+                               double lambda, void* p, int refine_steps) {
+  Band& B = ctx->band;
+  cudaStream_t st = ctx->stream;
+  const int64_t* dcols = (const int64_t*)B.d_cols.ptr;
+  const int64_t* dc0 = (const int64_t*)B.d_col0.ptr;
+  const int64_t* dr0 = (const int64_t*)B.d_row0.ptr;
+  double* D = (double*)B.D.ptr;
+  if (lambda > 0.0) {
+    if (Dext) {
+      if (sizeof(T) == sizeof(double)) {
+        QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(D, Dext, (size_t)B.total_cols * sizeof(double),
+                                            cudaMemcpyDeviceToDevice, st));
+      } else {
+        qrkit_status rc = widen_to_double(ctx, (const float*)Dext, D, B.total_cols);
+        if (rc != QRKIT_OK) return rc;
+      }
+    } else {
+      band_colnorm_kernel<<<nblk(B.total_cols, 256), 256, 0, st>>>(
+          sizeof(T) == 4 ? (const float*)J : nullptr, sizeof(T) == 8 ? (const double*)J : nullptr,
+          dcols, dc0, dr0, B.num_inst, B.rows_per_col, B.w, D);
+      ctx->launches += 1;
+      QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+    }
+  }
+  BandArgs<T> A;
+  A.num_inst = B.num_inst;
+  A.inst_cols = dcols;
+  A.inst_col0 = dc0;
+  A.inst_row0 = dr0;
+  A.rows_per_col = B.rows_per_col;
+  A.w = B.w;
+  A.J = (const T*)J;
+  A.b = (const T*)b;
+  A.D = D;
+  A.lam = lambda;
+  A.Rw = (T*)B.Rw.ptr;
+  A.c = (T*)B.c.ptr;
+  A.x = (T*)p;
+  A.res2 = (double*)B.res2.ptr;
+  A.refine_steps = refine_steps;
+  A.status = ctx->d_status;
+  banded_factor_solve_kernel<T><<<nblk(B.num_inst, warps_for<T>()), 32 * warps_for<T>(), 0, st>>>(A);
+  ctx->launches += 1;
+  QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+  if constexpr (sizeof(T) == sizeof(float)) {
+    if (refine_steps > 0) {
+      qrkit_status rc;
+      if ((rc = ensure(ctx, B.g, (size_t)B.total_cols * sizeof(double), "banded g")) != QRKIT_OK) return rc;
+      if ((rc = ensure(ctx, B.h, (size_t)B.total_cols * sizeof(float), "banded h")) != QRKIT_OK) return rc;
+      if ((rc = ensure(ctx, B.r, (size_t)B.total_rows * sizeof(double), "banded r")) != QRKIT_OK) return rc;
+      for (int it = 0; it < refine_steps; ++it) {
+        banded_refine_kernel<<<nblk(B.num_inst, kWarps), 32 * kWarps, 0, st>>>(
+            A, (double*)B.r.ptr, (double*)B.g.ptr, (float*)B.h.ptr);
+        ctx->launches += 1;
+        QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+      }
+    }
+  }
+  return QRKIT_OK;
+}
+
+qrkit_status banded_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
+                                 double lambda, void* p, int refine_steps) {
+  if (ctx->precision == QRKIT_FP64) return banded_run<double>(ctx, J, b, D, lambda, p, 0);
+  const int steps = ctx->precision == QRKIT_FP32 ? 0 : refine_steps;
+  return banded_run<float>(ctx, J, b, D, lambda, p, steps);
+}
+
+qrkit_status banded_get_factor(qrkit_ctx* ctx, void* Rw_out, void* c_out, double* res2_out) {
+  Band& B = ctx->band;
+  const size_t es = elem_size(ctx);
+  if (Rw_out)
+    QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(Rw_out, B.Rw.ptr, (size_t)B.total_cols * B.w * es,
+                                        cudaMemcpyDeviceToDevice, ctx->stream));
+  if (c_out)
+    QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(c_out, B.c.ptr, (size_t)B.total_cols * es,
+                                        cudaMemcpyDeviceToDevice, ctx->stream));
+  if (res2_out)
+    QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(res2_out, B.res2.ptr, (size_t)B.num_inst * sizeof(double),
+                                        cudaMemcpyDeviceToHost, ctx->stream));
+  return QRKIT_OK;
+}
+
+void release_band(Band& B) {
+  release(B.d_cols); release(B.d_col0); release(B.d_row0); release(B.Rw); release(B.c);
+  release(B.D); release(B.res2); release(B.g); release(B.h); release(B.r);
+  B = Band();
+}
+
+}  // namespace qrkit

@@ -234,6 +234,7 @@ void qrkit_destroy(qrkit_ctx* ctx) {
   else cudaDeviceSynchronize();
   release_plan(ctx->plan);
   release_composed(ctx->comp);
+  release_band(ctx->band);
   release(ctx->ws.factor);
   release(ctx->ws.tau);
   if (ctx->d_status) cudaFree(ctx->d_status);
@@ -250,10 +251,10 @@ qrkit_status qrkit_plan(qrkit_ctx* ctx, const qrkit_structure* s) {
   QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   release_plan(ctx->plan);
   release_composed(ctx->comp);
+  release_band(ctx->band);
   ctx->factored = false;
   if (s->kind == QRKIT_STRUCT_BLOCKS) return plan_blocks(ctx, s);
-  if (s->kind == QRKIT_STRUCT_BANDED)
-    return fail(ctx, QRKIT_EUNSUPPORTED, "banded structures are not available in this build");
+  if (s->kind == QRKIT_STRUCT_BANDED) return banded_plan(ctx, s);
   return fail(ctx, QRKIT_EINVAL, "unknown structure kind");
 }
 
@@ -262,8 +263,18 @@ qrkit_status qrkit_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, co
   if (!ctx) return QRKIT_EINVAL;
   if (!ctx->plan.valid) return fail(ctx, QRKIT_ESTATE, "qrkit_factor_solve before qrkit_plan");
   const Plan& P = ctx->plan;
+  if (P.s.kind == QRKIT_STRUCT_BANDED) {
+    if (!J || !b || !p) return fail(ctx, QRKIT_EINVAL, "J, b and p are required");
+    if (qtb) return fail(ctx, QRKIT_EINVAL, "qtb is not available for banded structures");
+    if (!(lambda >= 0.0)) return fail(ctx, QRKIT_EINVAL, "lambda must be >= 0");
+    if (refine_steps < 0 || refine_steps > 8) return fail(ctx, QRKIT_EINVAL, "refine_steps must be in [0, 8]");
+    QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+    qrkit_status st = banded_factor_solve(ctx, J, b, D, lambda, p, refine_steps);
+    if (st == QRKIT_OK) ctx->band_factored = true;
+    return st;
+  }
   if (P.s.kind != QRKIT_STRUCT_BLOCKS || P.s.coupled_kind != QRKIT_COUPLED_NONE)
-    return fail(ctx, QRKIT_EINVAL, "qrkit_factor_solve needs a block-diagonal structure");
+    return fail(ctx, QRKIT_EINVAL, "qrkit_factor_solve needs a block-diagonal or banded structure");
   ctx->comp_factored = false;
   if (!J || !b || !p) return fail(ctx, QRKIT_EINVAL, "J, b and p are required");
   if (!(lambda >= 0.0)) return fail(ctx, QRKIT_EINVAL, "lambda must be >= 0");
@@ -322,6 +333,15 @@ qrkit_status qrkit_solve(qrkit_ctx* ctx, const void* b, void* p, int refine_step
   if (refine_steps < 0 || refine_steps > 8) return fail(ctx, QRKIT_EINVAL, "refine_steps must be in [0, 8]");
   QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   return composed_solve(ctx, ctx->comp.J, ctx->comp.S, b, p, refine_steps);
+}
+
+qrkit_status qrkit_get_band_factor(qrkit_ctx* ctx, void* Rw, void* c, double* res2) {
+  if (!ctx) return QRKIT_EINVAL;
+  if (!ctx->band_factored) return fail(ctx, QRKIT_ESTATE, "no banded factor stored");
+  qrkit_status st = banded_get_factor(ctx, Rw, c, res2);
+  if (st != QRKIT_OK) return st;
+  QRKIT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+  return QRKIT_OK;
 }
 
 qrkit_status qrkit_get_factor(qrkit_ctx* ctx, void* factor_out, void* tau_out) {

@@ -91,6 +91,13 @@ struct FactorOut {
   int* status;
 };
 
+// Device state of a batch of banded instances (Sec. 4.4).
+struct Band {
+  int64_t num_inst = 0, total_cols = 0, total_rows = 0;
+  int rows_per_col = 1, w = 1;
+  DevBuf d_cols, d_col0, d_row0, Rw, c, D, res2, g, h, r;
+};
+
 struct TsqrLevel {
   int64_t M = 0;      // rows of the level matrix
   int64_t tiles = 0;
@@ -129,11 +136,13 @@ struct qrkit_ctx {
   qrkit::Plan plan;
   qrkit::Workspace ws;
   qrkit::Composed comp;
+  qrkit::Band band;
   int* d_status = nullptr;   // device status word
   int64_t launches = 0;
   size_t smem_attr[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // dynamic smem opted in, per kernel variant
   bool factored = false;       // fused block path
   bool comp_factored = false;  // composed path
+  bool band_factored = false;  // banded path
 };
 
 namespace qrkit {
@@ -159,6 +168,11 @@ qrkit_status composed_solve(qrkit_ctx* ctx, const void* J, const void* S, const 
 qrkit_status composed_apply_qt(qrkit_ctx* ctx, const void* b, void* qtb);
 qrkit_status composed_solve_r(qrkit_ctx* ctx, const void* qtb, void* p);
 void release_composed(Composed& C);
+qrkit_status banded_plan(qrkit_ctx* ctx, const qrkit_structure* s);
+qrkit_status banded_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
+                                 double lambda, void* p, int refine_steps);
+qrkit_status banded_get_factor(qrkit_ctx* ctx, void* Rw_out, void* c_out, double* res2_out);
+void release_band(Band& B);
 qrkit_status launch_block_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
                                 void* p, void* qtb, int refine_steps);
 

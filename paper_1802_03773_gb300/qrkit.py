@@ -44,6 +44,7 @@ class Structure(ctypes.Structure):
         ("cols", ctypes.c_int64),
         ("rows_per_col", ctypes.c_int32),
         ("band_window", ctypes.c_int32),
+        ("instance_cols", ctypes.c_void_p),
     ]
 
 
@@ -56,6 +57,7 @@ _SIGS = {
     "qrkit_plan": (ctypes.c_int, [_VP, ctypes.POINTER(Structure)]),
     "qrkit_factor_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP, ctypes.c_int]),
     "qrkit_get_factor": (ctypes.c_int, [_VP, _VP, _VP]),
+    "qrkit_get_band_factor": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "qrkit_factor": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double]),
     "qrkit_apply_qt": (ctypes.c_int, [_VP, _VP, _VP]),
     "qrkit_solve_r": (ctypes.c_int, [_VP, _VP, _VP]),
@@ -179,6 +181,24 @@ class Context:
             s.window_start = ws.ctypes.data
         self._check(self.lib.qrkit_plan(self.h, ctypes.byref(s)))
         self._keep = [n, m, ws]
+
+    def plan_banded(self, instance_cols, rows_per_col=4, window=8):
+        cols = np.ascontiguousarray(np.atleast_1d(instance_cols), dtype=np.int64)
+        s = Structure()
+        s.kind = STRUCT_BANDED
+        s.num_blocks = cols.shape[0]
+        s.instance_cols = cols.ctypes.data
+        s.cols = int(cols[0])
+        s.rows_per_col = int(rows_per_col)
+        s.band_window = int(window)
+        self._check(self.lib.qrkit_plan(self.h, ctypes.byref(s)))
+        self._keep = [cols]
+
+    def get_band_factor(self, Rw=None, c=None, res2=None):
+        """res2: a numpy float64 array (one entry per instance) or None."""
+        rp = None if res2 is None else res2.ctypes.data_as(ctypes.c_void_p)
+        self._check(self.lib.qrkit_get_band_factor(self.h, self._t(Rw, "Rw", True),
+                                                   self._t(c, "c", True), rp))
 
     # ---- solves ----
     def factor_solve(self, J, b, p, qtb=None, D=None, lam=0.0, refine_steps=1):

@@ -1,0 +1,114 @@
+"""GPU parity of the batched block-banded QR solve (Sec. 4.4, damping rows per Sec. 4.5 / 5.2)."""
+import numpy as np
+import pytest
+
+from oracle import banded as bd
+from oracle import householder as hh
+from tests.gpu_common import cuda_or_skip
+from workloads import banded_problem
+
+pytestmark = pytest.mark.gpu
+
+
+def batch(cols, rpc, w, dtype, seed=0):
+    """Concatenated instances (same generator, one seed offset per instance)."""
+    inst = [banded_problem(n=int(n), rows_per_col=rpc, w=w, seed_offset=seed + k, dtype=dtype)
+            for k, n in enumerate(cols)]
+    vals = np.concatenate([d["vals"] for d in inst])
+    b = np.concatenate([d["b"] for d in inst])
+    return inst, vals, b
+
+
+def run(cols, rpc, w, precision, lam, refine_steps=1, D=None, seed=0):
+    torch = cuda_or_skip()
+    from paper_1802_03773_gb300 import Context
+    dtype = np.float64 if precision == "fp64" else np.float32
+    inst, vals, b = batch(cols, rpc, w, dtype, seed)
+    ctx = Context(0, precision=precision)
+    ctx.plan_banded(cols, rows_per_col=rpc, window=w)
+    tJ = torch.from_numpy(np.ascontiguousarray(vals.reshape(-1))).cuda()
+    tb = torch.from_numpy(b).cuda()
+    tD = None if D is None else torch.from_numpy(D.astype(dtype)).cuda()
+    N = int(np.sum(cols))
+    p = torch.empty(N, device="cuda", dtype=ctx.dtype)
+    ctx.factor_solve(tJ, tb, p, None, D=tD, lam=lam, refine_steps=refine_steps)
+    ctx.sync_status()
+    Rw = torch.empty(N * w, device="cuda", dtype=ctx.dtype)
+    res2 = np.zeros(len(cols))
+    ctx.get_band_factor(Rw, None, res2)
+    out = dict(p=p.cpu().numpy().astype(np.float64), Rw=Rw.cpu().numpy().astype(np.float64).reshape(N, w),
+               res2=res2, inst=inst)
+    ctx.close()
+    return out
+
+
+def oracle_solutions(inst, lam, D=None):
+    xs, Rs, r2 = [], [], []
+    off = 0
+    for d in inst:
+        n = d["n"]
+        Dn = None if D is None else D[off:off + n]
+        x, Rw, c, res_sq, _ = bd.damped_solve(d["start"], d["vals"], d["b"], n, lam, Dn)
+        xs.append(x)
+        Rs.append(Rw)
+        r2.append(res_sq)
+        off += n
+    return np.concatenate(xs), np.vstack(Rs), np.array(r2)
+
+
+@pytest.mark.parametrize("cols,rpc,w", [([1, 7, 8, 9, 50, 333], 4, 8), ([40, 3, 17], 2, 3),
+                                        ([100], 4, 16), ([64] * 9, 1, 5)])
+def test_banded_fp64_matches_oracle(cols, rpc, w):
+    out = run(cols, rpc, w, "fp64", lam=1e-3)
+    x, Rw, r2 = oracle_solutions(out["inst"], 1e-3)
+    np.testing.assert_allclose(out["p"], x, rtol=1e-12, atol=1e-12 * np.abs(x).max())
+    # R up to row signs, window by window
+    s = np.sign(out["Rw"][:, :1]) * np.sign(Rw[:, :1])
+    np.testing.assert_allclose(out["Rw"] * s, Rw, atol=1e-11 * np.abs(Rw).max())
+    np.testing.assert_allclose(out["res2"], r2, rtol=1e-9)
+
+
+def test_banded_fp32_refined_matches_oracle():
+    cols = [500, 1200, 77]
+    out = run(cols, 4, 8, "fp32_refined", lam=1e-3, refine_steps=2)
+    x, _, _ = oracle_solutions(out["inst"], 1e-3)
+    assert np.linalg.norm(out["p"] - x) / np.linalg.norm(x) <= 1e-5
+
+
+def test_banded_given_D_and_no_damping():
+    cols = [30, 41]
+    g = np.random.default_rng(3)
+    D = np.abs(g.standard_normal(sum(cols))) + 0.5
+    out = run(cols, 4, 8, "fp64", lam=0.2, D=D)
+    x, _, _ = oracle_solutions(out["inst"], 0.2, D)
+    np.testing.assert_allclose(out["p"], x, rtol=1e-11, atol=1e-12)
+    out0 = run(cols, 4, 8, "fp64", lam=0.0)
+    x0, _, _ = oracle_solutions(out0["inst"], 0.0, np.ones(sum(cols)))
+    np.testing.assert_allclose(out0["p"], x0, rtol=1e-10, atol=1e-11)
+
+
+def test_banded_batch_scaled_sampled():
+    """A batch of 256 instances with n ~ U{1000..4000}: every instance's solution satisfies the
+    optimality identity; 4 sampled instances match the oracle."""
+    g = np.random.default_rng(1)
+    cols = g.integers(1000, 4001, size=256)
+    out = run(list(cols), 4, 8, "fp32_refined", lam=1e-3, refine_steps=2)
+    off = 0
+    worst = 0.0
+    for k, d in enumerate(out["inst"]):
+        n = d["n"]
+        x = out["p"][off:off + n]
+        start, vals = d["start"], d["vals"].astype(np.float64)
+        D = bd.column_norms(start, vals, n)
+        r = d["b"].astype(np.float64) - bd.matvec(start, vals, x)
+        gr = bd.rmatvec(start, vals, r, n) - 1e-3 * D * D * x
+        worst = max(worst, np.linalg.norm(gr) / (np.linalg.norm(vals) ** 2 * np.linalg.norm(x)))
+        off += n
+    assert worst < 1e-6
+    sel = [0, 77, 200, 255]
+    off = np.concatenate([[0], np.cumsum(cols)])
+    for k in sel:
+        d = out["inst"][k]
+        x, *_ = bd.damped_solve(d["start"], d["vals"], d["b"], d["n"], 1e-3)
+        got = out["p"][off[k]:off[k + 1]]
+        assert np.linalg.norm(got - x) / np.linalg.norm(x) <= 1e-5
