@@ -53,7 +53,9 @@ struct BandArgs {
   const int64_t* inst_cols;   // columns per instance
   const int64_t* inst_col0;   // first global column of each instance
   const int64_t* inst_row0;   // first J row of each instance
-  int rows_per_col;
+  int rows_per_col;           // implicit row starts: row i starts at floor(i / rows_per_col)
+  const int64_t* row_start;   // explicit, non-decreasing row starts (null: implicit)
+  const int64_t* inst_rows;   // rows per instance when row_start is given
   int w;                      // band window (<= kBW)
   const T* J;                 // rows x w, row-major
   const T* b;                 // rows
@@ -118,11 +120,12 @@ banded_factor_solve_kernel(BandArgs<T> A) {
   const int64_t N = A.inst_cols[inst];
   const int64_t col0 = A.inst_col0[inst];
   const int64_t row0 = A.inst_row0[inst];
-  const int64_t nrows = (int64_t)A.rows_per_col * N;
+  const int64_t nrows = A.row_start ? A.inst_rows[inst] : (int64_t)A.rows_per_col * N;
   const bool damp = A.lam > 0.0;
   const double lam_half = sqrt(A.lam);
   double res2 = 0.0;
   int carried = 0;   // rows 0 .. carried-1 of F hold the carried rows (columns from c0 on)
+  int64_t jr_next = 0;   // explicit starts: first row not yet consumed
   for (int e = lane; e < kFRows * kFStride; e += 32) F[e] = T(0);
   __syncwarp();
   for (int64_t c0 = 0; c0 < N; c0 += kBG) {
@@ -140,8 +143,16 @@ banded_factor_solve_kernel(BandArgs<T> A) {
     __syncwarp();
     int nr = carried;
     // stream of new rows: J rows starting in [c0, c1), then the damping rows of c0 .. c1-1
-    int64_t jr = (int64_t)A.rows_per_col * c0;
-    const int64_t jr_end = (int64_t)A.rows_per_col * c1 < nrows ? (int64_t)A.rows_per_col * c1 : nrows;
+    int64_t jr, jr_end;
+    if (A.row_start) {
+      jr = jr_next;
+      jr_end = jr;
+      while (jr_end < nrows && A.row_start[row0 + jr_end] < c1) ++jr_end;
+      jr_next = jr_end;
+    } else {
+      jr = (int64_t)A.rows_per_col * c0;
+      jr_end = (int64_t)A.rows_per_col * c1 < nrows ? (int64_t)A.rows_per_col * c1 : nrows;
+    }
     int64_t dr = damp ? c0 : c1;
     while (jr < jr_end || dr < c1) {
       const int room = kFRows - nr;
@@ -153,7 +164,7 @@ banded_factor_solve_kernel(BandArgs<T> A) {
         for (int q = 0; q < kFStride; ++q) row[q] = T(0);
         if (t < take_j) {
           const int64_t i = jr + t;
-          const int64_t start = i / A.rows_per_col;
+          const int64_t start = A.row_start ? A.row_start[row0 + i] : i / A.rows_per_col;
           const T* src = A.J + (row0 + i) * w;
           for (int q = 0; q < w; ++q) {
             const int64_t col = start + q;
@@ -289,6 +300,26 @@ banded_refine_kernel(BandArgs<float> A, double* rbuf, double* gbuf, float* hbuf)
   }
 }
 
+// R^T h = g (transpose = 0 -> forward with R^T) or R x = h (backward) for one banded R
+// (windows Rw, n columns); one thread: the recurrences are sequential.  In place on v.
+template <typename T>
+__global__ void band_tri_solve_kernel(const T* Rw, int64_t n, int w, T* v, int transpose) {
+  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+  if (transpose) {
+    for (int64_t j = 0; j < n; ++j) {
+      T s = v[j];
+      for (int t = 1; t < w && j - t >= 0; ++t) s -= Rw[(j - t) * w + t] * v[j - t];
+      v[j] = s / Rw[j * w];
+    }
+  } else {
+    for (int64_t j = n - 1; j >= 0; --j) {
+      T s = v[j];
+      for (int t = 1; t < w && j + t < n; ++t) s -= Rw[j * w + t] * v[j + t];
+      v[j] = s / Rw[j * w];
+    }
+  }
+}
+
 __global__ void band_colnorm_kernel(const float* Jf, const double* Jd, const int64_t* inst_cols,
                                     const int64_t* inst_col0, const int64_t* inst_row0,
                                     int64_t num_inst, int rpc, int w, double* D) {
@@ -405,6 +436,8 @@ static qrkit_status banded_run(qrkit_ctx* ctx, const void* J, const void* b, con
   A.inst_col0 = dc0;
   A.inst_row0 = dr0;
   A.rows_per_col = B.rows_per_col;
+  A.row_start = nullptr;
+  A.inst_rows = nullptr;
   A.w = B.w;
   A.J = (const T*)J;
   A.b = (const T*)b;
@@ -433,6 +466,63 @@ static qrkit_status banded_run(qrkit_ctx* ctx, const void* J, const void* b, con
       }
     }
   }
+  return QRKIT_OK;
+}
+
+// Factor + solve one banded instance with explicit sorted row starts (the reduced block of a
+// windowed block-angular structure): rows x w values, n columns, damping rows
+// lambda^(1/2) D_j (D in double) when lambda > 0.  Writes Rw (n x w), c (n), x (n).
+template <typename T>
+static qrkit_status explicit_run(qrkit_ctx* ctx, const T* rows, const int64_t* starts, int64_t nrows,
+                                 const T* rhs, int64_t n, int w, const double* D, double lambda,
+                                 T* Rw, T* c, T* x, double* res2, int64_t* meta) {
+  // meta: device scratch of 4 int64: cols, col0, row0, rows
+  const int64_t h[4] = {n, 0, 0, nrows};
+  QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(meta, h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
+  BandArgs<T> A;
+  A.num_inst = 1;
+  A.inst_cols = meta;
+  A.inst_col0 = meta + 1;
+  A.inst_row0 = meta + 2;
+  A.inst_rows = meta + 3;
+  A.rows_per_col = 1;
+  A.row_start = starts;
+  A.w = w;
+  A.J = rows;
+  A.b = rhs;
+  A.D = D;
+  A.lam = lambda;
+  A.Rw = Rw;
+  A.c = c;
+  A.x = x;
+  A.res2 = res2;
+  A.refine_steps = 0;
+  A.status = ctx->d_status;
+  banded_factor_solve_kernel<T><<<1, 32 * warps_for<T>(), 0, ctx->stream>>>(A);
+  ctx->launches += 1;
+  QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+  return QRKIT_OK;
+}
+
+qrkit_status banded_explicit_solve(qrkit_ctx* ctx, const void* rows, const int64_t* starts,
+                                   int64_t nrows, const void* rhs, int64_t n, int w,
+                                   const double* D, double lambda, void* Rw, void* c, void* x,
+                                   double* res2, int64_t* meta) {
+  if (w < 1 || w > kBW) return fail(ctx, QRKIT_EUNSUPPORTED, "reduced band window must be in [1, 16]");
+  if (ctx->precision == QRKIT_FP64)
+    return explicit_run<double>(ctx, (const double*)rows, starts, nrows, (const double*)rhs, n, w, D,
+                                lambda, (double*)Rw, (double*)c, (double*)x, res2, meta);
+  return explicit_run<float>(ctx, (const float*)rows, starts, nrows, (const float*)rhs, n, w, D,
+                             lambda, (float*)Rw, (float*)c, (float*)x, res2, meta);
+}
+
+qrkit_status banded_tri_solve(qrkit_ctx* ctx, const void* Rw, int64_t n, int w, void* v, bool transpose) {
+  if (ctx->precision == QRKIT_FP64)
+    band_tri_solve_kernel<double><<<1, 32, 0, ctx->stream>>>((const double*)Rw, n, w, (double*)v, transpose ? 1 : 0);
+  else
+    band_tri_solve_kernel<float><<<1, 32, 0, ctx->stream>>>((const float*)Rw, n, w, (float*)v, transpose ? 1 : 0);
+  ctx->launches += 1;
+  QRKIT_CUDA_TRY(ctx, cudaGetLastError());
   return QRKIT_OK;
 }
 

@@ -164,8 +164,12 @@ __global__ void block_factor_kernel(ComposedView<T> V, FactorOut<T> O) {
       for (int r = 0; r < m; ++r) O.R12[(V.col_off[i] + r) * (int64_t)V.w + c0 + c] = C[c * na + r];
       for (int r = m; r < na; ++r) {
         const int64_t row = red0 + (r - m);
-        if (V.coupled == QRKIT_COUPLED_DENSE) O.X0[(int64_t)(c0 + c) * O.ld0 + row] = C[c * na + r];
-        else O.Xw[row * V.w + c0 + c] = C[c * na + r];
+        if (V.coupled == QRKIT_COUPLED_DENSE) {
+          O.X0[(int64_t)(c0 + c) * O.ld0 + row] = C[c * na + r];
+        } else {
+          O.Xw[row * V.w + c0 + c] = C[c * na + r];
+          if (c0 + c == 0) O.Xstart[row] = V.start[i];
+        }
       }
     }
   }
@@ -523,7 +527,8 @@ static FactorOut<T> fout(qrkit_ctx* ctx) {
   O.red_off = (const int64_t*)(C.damp ? C.d_red_off_d.ptr : C.d_red_off_u.ptr);
   O.X0 = C.levels.empty() ? nullptr : (T*)C.levels[0].X.ptr;
   O.ld0 = C.levels.empty() ? 0 : C.levels[0].M;
-  O.Xw = nullptr;
+  O.Xw = (T*)C.Xw.ptr;
+  O.Xstart = (int64_t*)C.Xstart.ptr;
   O.status = ctx->d_status;
   return O;
 }
@@ -603,7 +608,8 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
   const int64_t nb = P.cols;
   T* x = (T*)p;
   // Q^T [b; 0]
-  T* rhs0 = (V.coupled == QRKIT_COUPLED_DENSE) ? (T*)C.levels[0].rhs.ptr : nullptr;
+  T* rhs0 = (V.coupled == QRKIT_COUPLED_DENSE) ? (T*)C.levels[0].rhs.ptr
+             : (V.coupled == QRKIT_COUPLED_WINDOW ? (T*)C.rhs_red.ptr : nullptr);
   LAUNCH(ctx, block_apply_qt_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O, (const T*)b, rhs0));
   if (V.coupled == QRKIT_COUPLED_DENSE) {
     if (C.damp)
@@ -615,6 +621,8 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
                       (const T*)L.X.ptr, L.M, L.M, s, C.tile_rows, (const T*)L.tau.ptr, (T*)L.rhs.ptr, rn));
     }
   }
+  if (V.coupled == QRKIT_COUPLED_WINDOW && qt_only)
+    return fail(ctx, QRKIT_EUNSUPPORTED, "Q^T b is not kept for windowed structures (use qrkit_solve)");
   if (qt_only) {
     // Q^T b reported as [c_blocks (sum m_i); c_S (s)]
     T* out = (T*)qtb_out;
@@ -628,6 +636,13 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
   if (V.coupled == QRKIT_COUPLED_DENSE) {
     LAUNCH(ctx, dense_backsub_kernel<T><<<1, 32, (size_t)s * sizeof(T), st>>>(
                     (const T*)top->X.ptr, top->M, s, (const T*)top->rhs.ptr, x + nb, 0, ctx->d_status));
+  } else if (V.coupled == QRKIT_COUPLED_WINDOW) {
+    // reduced banded block (Sec. 4.4) with the shared columns' damping rows interleaved
+    qrkit_status rc = banded_explicit_solve(ctx, C.Xw.ptr, (const int64_t*)C.Xstart.ptr, C.red_rows,
+                                            C.rhs_red.ptr, s, V.w, O.D + nb, C.damp ? C.lam : 0.0,
+                                            C.RwS.ptr, C.cS.ptr, x + nb, (double*)C.res2.ptr,
+                                            (int64_t*)C.meta.ptr);
+    if (rc != QRKIT_OK) return rc;
   }
   LAUNCH(ctx, block_backsub_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O, O.ctop, s ? x + nb : nullptr, x, 0));
   // refinement (extended-precision residual, corrections through R only)
@@ -646,6 +661,15 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
                       gS, sizeof(T) == 4 ? (const float*)x : nullptr,
                       sizeof(T) == 8 ? (const double*)x : nullptr, O.D, nb, s, C.lam));
     LAUNCH(ctx, block_fwdsub_rt_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O, g, h, gS));
+    if (V.coupled == QRKIT_COUPLED_WINDOW) {
+      // h_S = R_S^{-T} (g_S - R12^T h_B), then dp_S = R_S^{-1} h_S, both banded
+      LAUNCH(ctx, gS_to_T_kernel<T><<<blocks_for(s, 128), 128, 0, st>>>(gS, h + nb, s));
+      qrkit_status rc = banded_tri_solve(ctx, C.RwS.ptr, s, V.w, h + nb, true);
+      if (rc != QRKIT_OK) return rc;
+      rc = banded_tri_solve(ctx, C.RwS.ptr, s, V.w, h + nb, false);
+      if (rc != QRKIT_OK) return rc;
+      LAUNCH(ctx, axpy_kernel<T><<<blocks_for(s, 128), 128, 0, st>>>(x + nb, h + nb, s));
+    }
     if (V.coupled == QRKIT_COUPLED_DENSE) {
       // h_S = R_S^{-T} (g_S - R12^T h_B), then dp_S = R_S^{-1} h_S in place
       LAUNCH(ctx, dense_fwdsub_rt_kernel<T><<<1, 32, (size_t)s * sizeof(T), st>>>(
@@ -698,6 +722,8 @@ qrkit_status widen_to_double(qrkit_ctx* ctx, const float* in, double* out, int64
 void release_composed(Composed& C) {
   release(C.D); release(C.sq); release(C.Fa); release(C.tau); release(C.R12); release(C.ctop);
   release(C.g); release(C.h);
+  release(C.Xw); release(C.Xstart); release(C.rhs_red); release(C.RwS); release(C.cS);
+  release(C.res2); release(C.meta);
   release(C.d_aug_off_d); release(C.d_aug_off_u); release(C.d_red_off_d); release(C.d_red_off_u);
   for (auto& L : C.levels) { release(L.X); release(L.tau); release(L.rhs); }
   C = Composed();
@@ -741,8 +767,18 @@ qrkit_status composed_layout(qrkit_ctx* ctx, size_t elem) {
   if ((rc = ensure(ctx, C.ctop, (size_t)P.cols * elem, "c")) != QRKIT_OK) return rc;
   if (P.s.coupled_kind != QRKIT_COUPLED_NONE)
     if ((rc = ensure(ctx, C.R12, (size_t)P.cols * w * elem, "R12")) != QRKIT_OK) return rc;
-  if (P.s.coupled_kind == QRKIT_COUPLED_WINDOW)
-    return fail(ctx, QRKIT_EUNSUPPORTED, "windowed coupling needs the banded reduced solver");
+  if (P.s.coupled_kind == QRKIT_COUPLED_WINDOW) {
+    // the reduced rows form a banded matrix (rows sorted by window start); its QR runs with
+    // the right-hand side in qrkit_solve (the banded solver does not keep Q)
+    const int64_t Mr = C.red_rows > 0 ? C.red_rows : 1;
+    if ((rc = ensure(ctx, C.Xw, (size_t)Mr * w * elem, "reduced rows")) != QRKIT_OK) return rc;
+    if ((rc = ensure(ctx, C.Xstart, (size_t)Mr * sizeof(int64_t), "reduced row starts")) != QRKIT_OK) return rc;
+    if ((rc = ensure(ctx, C.rhs_red, (size_t)Mr * elem, "reduced rhs")) != QRKIT_OK) return rc;
+    if ((rc = ensure(ctx, C.RwS, (size_t)s * w * elem, "reduced R")) != QRKIT_OK) return rc;
+    if ((rc = ensure(ctx, C.cS, (size_t)s * elem, "reduced c")) != QRKIT_OK) return rc;
+    if ((rc = ensure(ctx, C.res2, sizeof(double) * 2, "reduced residual")) != QRKIT_OK) return rc;
+    if ((rc = ensure(ctx, C.meta, sizeof(int64_t) * 4, "reduced meta")) != QRKIT_OK) return rc;
+  }
   if (P.s.coupled_kind == QRKIT_COUPLED_DENSE) {
     if (s > 64) return fail(ctx, QRKIT_EUNSUPPORTED, "dense shared block wider than 64 columns");
     const int64_t M0 = C.red_rows + (C.damp ? s : 0);
@@ -779,6 +815,8 @@ qrkit_status composed_layout(qrkit_ctx* ctx, size_t elem) {
 template <typename T>
 static qrkit_status solve_r_typed(qrkit_ctx* ctx, const void* qtb, void* p) {
   Plan& P = ctx->plan;
+  if (P.s.coupled_kind == QRKIT_COUPLED_WINDOW)
+    return fail(ctx, QRKIT_EUNSUPPORTED, "R of a windowed structure is formed in qrkit_solve");
   Composed& C = ctx->comp;
   cudaStream_t st = ctx->stream;
   ComposedView<T> V = view<T>(ctx, nullptr, nullptr);

@@ -87,7 +87,8 @@ struct FactorOut {
   const int64_t* red_off;
   T* X0;
   int64_t ld0;
-  T* Xw;
+  T* Xw;            // windowed reduced rows (rows x w, row-major)
+  int64_t* Xstart;  // their first column
   int* status;
 };
 
@@ -113,6 +114,7 @@ struct Composed {
   int64_t aug_values_d = 0, aug_values_u = 0;
   int64_t red_rows_d = 0, red_rows_u = 0;
   DevBuf D, sq, Fa, tau, R12, ctop, g, h;
+  DevBuf Xw, Xstart, rhs_red, RwS, cS, res2, meta;   // windowed reduced block
   DevBuf d_aug_off_d, d_aug_off_u, d_red_off_d, d_red_off_u;
   std::vector<TsqrLevel> levels;
   const void* J = nullptr;         // caller's values recorded at factor time
@@ -172,6 +174,11 @@ qrkit_status banded_plan(qrkit_ctx* ctx, const qrkit_structure* s);
 qrkit_status banded_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
                                  double lambda, void* p, int refine_steps);
 qrkit_status banded_get_factor(qrkit_ctx* ctx, void* Rw_out, void* c_out, double* res2_out);
+qrkit_status banded_explicit_solve(qrkit_ctx* ctx, const void* rows, const int64_t* starts,
+                                   int64_t nrows, const void* rhs, int64_t n, int w,
+                                   const double* D, double lambda, void* Rw, void* c, void* x,
+                                   double* res2, int64_t* meta);
+qrkit_status banded_tri_solve(qrkit_ctx* ctx, const void* Rw, int64_t n, int w, void* v, bool transpose);
 void release_band(Band& B);
 qrkit_status launch_block_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
                                 void* p, void* qtb, int refine_steps);
