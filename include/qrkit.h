@@ -73,7 +73,10 @@ typedef struct qrkit_structure {
   int32_t coupled_kind;         /* qrkit_coupled_kind */
   int64_t shared_cols;          /* s: columns of S (0 for QRKIT_COUPLED_NONE) */
   int32_t window;               /* w for QRKIT_COUPLED_WINDOW */
-  const int32_t* window_start;  /* host, K entries, non-decreasing, start_i + w <= s + w - 1 */
+  const int32_t* window_start;  /* host, K entries: first S column of block i's window, inside
+                                   its segment (below).  Any order: the rows of the reduced
+                                   block are sorted by start on the device (Sec. 4.3 P_r).
+                                   Window entries past the end of the segment must be zero. */
   /* --- QRKIT_STRUCT_BANDED --- */
   int64_t rows, cols;           /* one instance: J is (rows_per_col * cols) x cols */
   int32_t rows_per_col;         /* row i starts at column floor(i / rows_per_col) */
@@ -82,6 +85,14 @@ typedef struct qrkit_structure {
   const int64_t* instance_cols; /* host, num_blocks entries: a batch of independent banded
                                    instances with these column counts (NULL: one instance
                                    of `cols` columns) */
+  /* --- QRKIT_COUPLED_WINDOW, optional: S split into independent segments --- */
+  int64_t num_segments;          /* 0 or 1: one segment of all s columns */
+  const int64_t* segment_cols;   /* host, num_segments entries >= 1 summing to s: columns of
+                                    each segment; a window never crosses a segment boundary,
+                                    so each segment's reduced block is a separate banded
+                                    matrix, solved in parallel with the others */
+  const int64_t* segment_blocks; /* host, num_segments entries summing to K: the blocks are
+                                    grouped by segment in order, this many per segment */
 } qrkit_structure;
 
 typedef struct qrkit_ctx qrkit_ctx;
@@ -197,6 +208,79 @@ qrkit_status qrkit_get_band_factor(qrkit_ctx* ctx, void* Rw, void* c, double* re
  * may be NULL): factor values in J's packing (V strictly below the diagonal, R on and above)
  * and tau (sum m_i). */
 qrkit_status qrkit_get_factor(qrkit_ctx* ctx, void* factor_out, void* tau_out);
+
+/* Replace the window starts of a QRKIT_COUPLED_WINDOW plan from DEVICE memory (K int32, same
+ * meaning as qrkit_structure.window_start), e.g. when an LM iteration moves the windows.
+ * Copied asynchronously; a start outside its block's segment is clamped into it and
+ * reported as QRKIT_EINVAL through the device status word.  Takes effect at the next
+ * qrkit_factor. */
+qrkit_status qrkit_set_window_start(qrkit_ctx* ctx, const int32_t* start);
+
+/* Row permutation P_r of the reduced shared block of the last qrkit_factor on a windowed plan
+ * (Sec. 4.3): order[k] = index of the reduced row at sorted position k (DEVICE, int64, one per
+ * reduced row).  Reduced rows are numbered block by block, rows of a block in order (n_i rows
+ * per block with damping, n_i - m_i without); the sort key is (segment, first S column,
+ * reduced-row index).  Asynchronous. */
+qrkit_status qrkit_get_row_order(qrkit_ctx* ctx, int64_t* order);
+
+/* ---- Levenberg-Marquardt on the device (Sec. 2; Backtrack LM of Sec. 5.2) ----
+ * Model QRKIT_MODEL_CURVEFIT: 2-D points fitted by an open uniform cubic B-spline; each
+ * point has one latent curve parameter t_i and the control points are shared, so J is
+ * block-angular with 2x1 blocks and, per point, a window of 8 shared columns (Sec. 4.2 with
+ * the banded reduced block of Sec. 4.4; the shape of the paper's surface fits, Sec. 6.2).
+ *   seg = clamp(floor(t), 0, Kc - 4), u = t - seg,
+ *   curve(t) = sum_{q=0..3} B_q(u) P_{seg+q} with the uniform cubic B-spline basis
+ *   B_0 = (1-u)^3/6, B_1 = (3u^3 - 6u^2 + 4)/6, B_2 = (-3u^3 + 3u^2 + 3u + 1)/6, B_3 = u^3/6,
+ *   f_i = curve(t_i) - data_i (two rows per point), cost = 1/2 ||f||^2.
+ * Several independent problems are solved together (one segment of S each). */
+typedef enum { QRKIT_MODEL_CURVEFIT = 0 } qrkit_model;
+
+typedef struct qrkit_lm_problem {
+  int32_t model;                 /* QRKIT_MODEL_CURVEFIT */
+  int64_t num_problems;          /* B >= 1 */
+  const int64_t* num_points;     /* host, B entries >= 1: P_k */
+  const int32_t* control_points; /* host, B entries >= 4: Kc_k */
+  const double* data;            /* DEVICE, (sum P_k) x 2 doubles (x, y), problems in order;
+                                    read by every step: keep it alive and unchanged */
+} qrkit_lm_problem;
+
+/* Per-problem LM state (host structs; copied to the device and back by each call). */
+typedef struct qrkit_lm_state {
+  double lambda;     /* in/out: damping, > 0 */
+  double nu;         /* in/out: Nielsen's growth factor after a rejection (start with 2) */
+  double cost;       /* out: 1/2 ||f(x)||^2 at the start of the last step */
+  double cost_new;   /* out: 1/2 ||f(x + p)||^2 of the last trial */
+  double pred;       /* out: predicted decrease 1/2 p^T (lambda D^2 p + J^T b), b = -f */
+  double rho;        /* out: gain ratio (cost - cost_new) / pred; -1 when pred <= 0 */
+  int32_t accepted;  /* out: the last trial was taken (rho > 0) */
+  int32_t done;      /* in/out: 1 = stopped; a stopped problem no longer changes */
+  int64_t iteration; /* in/out: steps tried */
+} qrkit_lm_state;
+
+/* Plan the LM model: builds the block-angular structure (2x1 blocks, windows of 8, one
+ * segment per problem, replacing the context's plan) and the device buffers.  x, passed to
+ * the calls below, is a DEVICE array of N = sum P_k + sum 2 Kc_k doubles:
+ * [t of all points, problems in order | control points of problem 0 (x0, y0, x1, y1, ...),
+ * problem 1, ...].  Synchronous. */
+qrkit_status qrkit_lm_plan(qrkit_ctx* ctx, const qrkit_lm_problem* problem);
+
+/* One LM iteration for every problem not marked done: f, J and the window starts at x;
+ * D = column norms of J (zero -> 1); QR of P_r [J; lambda^(1/2) D] by the composed path with
+ * the rows of J, S and b rounded to the context precision; p from qrkit_solve with
+ * `refine_steps`; cost at x + p; gain ratio; Nielsen update (rho > 0: accept,
+ * lambda *= max(1/3, 1 - (2 rho - 1)^3), nu = 2; else lambda *= nu, nu *= 2); x += p where
+ * accepted.  A problem whose lambda exceeds 1e16 is marked done.  states: host, B entries,
+ * read and written.  Synchronous (returns after the state is copied back). */
+qrkit_status qrkit_lm_step(qrkit_ctx* ctx, double* x, qrkit_lm_state* states, int refine_steps);
+
+/* Up to max_iter iterations as in qrkit_lm_step with the state kept on the device; a problem
+ * is marked done after an accepted step with cost - cost_new <= ftol * cost (or lambda > 1e16),
+ * and the loop ends early once every problem is done (checked every 8 iterations).  With
+ * use_graph != 0 one iteration is captured into a CUDA graph (on the first call, or when x,
+ * ftol or refine_steps change) and replayed; capture needs the context's stream to be a
+ * stream other than the legacy default stream.  Synchronous. */
+qrkit_status qrkit_lm_run(qrkit_ctx* ctx, double* x, qrkit_lm_state* states, int max_iter, double ftol,
+                          int refine_steps, int use_graph);
 
 /* Block until the stream is idle and return the device status word (QRKIT_OK if no kernel
  * reported a failure), then clear it. */

@@ -31,14 +31,23 @@ def nielsen(lam, nu, rho):
     return lam * nu, nu * 2.0, False
 
 
-def curvefit_system(x, data, lam):
-    """BlockProblem of the damped LM system at x (b = -f)."""
+def curvefit_system(x, data, lam, round32=False):
+    """BlockProblem of the damped LM system at x (b = -f).
+
+    round32: J, S and b rounded once to float32 (the system a float factorization is given);
+    the oracle still solves it in float64.  D then follows from the rounded J.
+    """
     npts = data.shape[0]
     f = curvefit.residual(x, data)
     blocks, coupled, start = curvefit.jacobian_parts(x, data)
+    b = -f
+    if round32:
+        blocks = blocks.astype(np.float32).astype(np.float64)
+        coupled = coupled.astype(np.float32).astype(np.float64)
+        b = b.astype(np.float32).astype(np.float64)
     Kc = (x.shape[0] - npts) // 2
     P = structured.BlockProblem(blocks=list(blocks), coupled=list(coupled), start=start,
-                                s=2 * Kc, b=-f, lam=lam)
+                                s=2 * Kc, b=b, lam=lam)
     return P, f
 
 
@@ -48,14 +57,15 @@ def solve_system(P, banded_reduced=True):
     return p
 
 
-def predicted_decrease(P, p, f):
-    """1/2 p^T (lambda D^2 p + J^T b) with b = -f (the model decrease of the step)."""
+def predicted_decrease(P, p, f=None):
+    """1/2 p^T (lambda D^2 p + J^T b) with the system's b (= -f) (the model decrease, Sec. 2)."""
     D = structured.damping(P)
+    b = np.asarray(P.b, dtype=np.float64) if f is None else -f
     J = structured.assemble_J(P) if P.M * P.N <= 4_000_000 else None
     if J is not None:
-        jtb = J.T @ (-f)
+        jtb = J.T @ b
     else:
-        jtb = _jt_vec(P, -f)
+        jtb = _jt_vec(P, b)
     return 0.5 * float(np.dot(p, P.lam * D * D * p + jtb))
 
 
@@ -81,16 +91,18 @@ class LMState:
     cost: float = float("nan")
     it: int = 0
     history: list = field(default_factory=list)   # (cost, lam, rho, accepted)
+    last_p: np.ndarray = None
 
 
-def lm_step(state: LMState, data, banded_reduced=True):
-    P, f = curvefit_system(state.x, data, state.lam)
+def lm_step(state: LMState, data, banded_reduced=True, round32=False):
+    P, f = curvefit_system(state.x, data, state.lam, round32)
     cost = 0.5 * float(np.dot(f, f))
     p = solve_system(P, banded_reduced)
+    state.last_p = p
     x_new = state.x + p
     f_new = curvefit.residual(x_new, data)
     cost_new = 0.5 * float(np.dot(f_new, f_new))
-    pred = predicted_decrease(P, p, f)
+    pred = predicted_decrease(P, p)
     rho = (cost - cost_new) / pred if pred > 0 else -1.0
     lam, nu, acc = nielsen(state.lam, state.nu, rho)
     state.history.append((cost, state.lam, rho, acc))

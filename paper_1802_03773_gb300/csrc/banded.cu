@@ -54,7 +54,7 @@ struct BandArgs {
   const int64_t* inst_col0;   // first global column of each instance
   const int64_t* inst_row0;   // first J row of each instance
   int rows_per_col;           // implicit row starts: row i starts at floor(i / rows_per_col)
-  const int64_t* row_start;   // explicit, non-decreasing row starts (null: implicit)
+  const int64_t* row_start;   // explicit row starts, global columns, non-decreasing per instance (null: implicit)
   const int64_t* inst_rows;   // rows per instance when row_start is given
   int w;                      // band window (<= kBW)
   const T* J;                 // rows x w, row-major
@@ -147,7 +147,7 @@ banded_factor_solve_kernel(BandArgs<T> A) {
     if (A.row_start) {
       jr = jr_next;
       jr_end = jr;
-      while (jr_end < nrows && A.row_start[row0 + jr_end] < c1) ++jr_end;
+      while (jr_end < nrows && A.row_start[row0 + jr_end] - col0 < c1) ++jr_end;
       jr_next = jr_end;
     } else {
       jr = (int64_t)A.rows_per_col * c0;
@@ -164,11 +164,11 @@ banded_factor_solve_kernel(BandArgs<T> A) {
         for (int q = 0; q < kFStride; ++q) row[q] = T(0);
         if (t < take_j) {
           const int64_t i = jr + t;
-          const int64_t start = A.row_start ? A.row_start[row0 + i] : i / A.rows_per_col;
+          const int64_t start = A.row_start ? A.row_start[row0 + i] - col0 : i / A.rows_per_col;
           const T* src = A.J + (row0 + i) * w;
           for (int q = 0; q < w; ++q) {
             const int64_t col = start + q;
-            if (col < N) row[col - c0] = src[q];
+            if (col >= c0 && col < N) row[col - c0] = src[q];
           }
           row[fc] = A.b[row0 + i];
         } else {
@@ -300,22 +300,28 @@ banded_refine_kernel(BandArgs<float> A, double* rbuf, double* gbuf, float* hbuf)
   }
 }
 
-// R^T h = g (transpose = 0 -> forward with R^T) or R x = h (backward) for one banded R
-// (windows Rw, n columns); one thread: the recurrences are sequential.  In place on v.
+// R^T h = g (transpose = 1: forward with R^T) or R x = h (backward) for the banded R of each
+// instance (windows Rw by global column); one thread per instance, the recurrences are
+// sequential.  In place on v (global columns).
 template <typename T>
-__global__ void band_tri_solve_kernel(const T* Rw, int64_t n, int w, T* v, int transpose) {
-  if (blockIdx.x != 0 || threadIdx.x != 0) return;
+__global__ void band_tri_solve_kernel(int64_t num_inst, const int64_t* inst, const T* Rw, int w, T* v,
+                                      int transpose) {
+  const int64_t k = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (k >= num_inst) return;
+  const int64_t n = inst[k], c0 = inst[num_inst + k];
+  const T* R = Rw + c0 * w;
+  T* x = v + c0;
   if (transpose) {
     for (int64_t j = 0; j < n; ++j) {
-      T s = v[j];
-      for (int t = 1; t < w && j - t >= 0; ++t) s -= Rw[(j - t) * w + t] * v[j - t];
-      v[j] = s / Rw[j * w];
+      T s = x[j];
+      for (int t = 1; t < w && j - t >= 0; ++t) s -= R[(j - t) * w + t] * x[j - t];
+      x[j] = s / R[j * w];
     }
   } else {
     for (int64_t j = n - 1; j >= 0; --j) {
-      T s = v[j];
-      for (int t = 1; t < w && j + t < n; ++t) s -= Rw[j * w + t] * v[j + t];
-      v[j] = s / Rw[j * w];
+      T s = x[j];
+      for (int t = 1; t < w && j + t < n; ++t) s -= R[j * w + t] * x[j + t];
+      x[j] = s / R[j * w];
     }
   }
 }
@@ -469,22 +475,20 @@ static qrkit_status banded_run(qrkit_ctx* ctx, const void* J, const void* b, con
   return QRKIT_OK;
 }
 
-// Factor + solve one banded instance with explicit sorted row starts (the reduced block of a
-// windowed block-angular structure): rows x w values, n columns, damping rows
-// lambda^(1/2) D_j (D in double) when lambda > 0.  Writes Rw (n x w), c (n), x (n).
+// Factor + solve banded instances whose rows carry explicit starts (the reduced blocks of a
+// windowed block-angular structure, one instance per segment of S): rows x w values, damping
+// rows lambda^(1/2) D_j (D in double, global columns) when lambda > 0.  Rw, c, x, D are
+// indexed by global column (instance col0 + j); rows, starts and rhs by global row.
 template <typename T>
-static qrkit_status explicit_run(qrkit_ctx* ctx, const T* rows, const int64_t* starts, int64_t nrows,
-                                 const T* rhs, int64_t n, int w, const double* D, double lambda,
-                                 T* Rw, T* c, T* x, double* res2, int64_t* meta) {
-  // meta: device scratch of 4 int64: cols, col0, row0, rows
-  const int64_t h[4] = {n, 0, 0, nrows};
-  QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(meta, h, sizeof(h), cudaMemcpyHostToDevice, ctx->stream));
+static qrkit_status explicit_run(qrkit_ctx* ctx, int64_t num_inst, const int64_t* inst, const T* rows,
+                                 const int64_t* starts, const T* rhs, int w, const double* D,
+                                 double lambda, T* Rw, T* c, T* x, double* res2) {
   BandArgs<T> A;
-  A.num_inst = 1;
-  A.inst_cols = meta;
-  A.inst_col0 = meta + 1;
-  A.inst_row0 = meta + 2;
-  A.inst_rows = meta + 3;
+  A.num_inst = num_inst;
+  A.inst_cols = inst;
+  A.inst_col0 = inst + num_inst;
+  A.inst_row0 = inst + 2 * num_inst;
+  A.inst_rows = inst + 3 * num_inst;
   A.rows_per_col = 1;
   A.row_start = starts;
   A.w = w;
@@ -498,29 +502,34 @@ static qrkit_status explicit_run(qrkit_ctx* ctx, const T* rows, const int64_t* s
   A.res2 = res2;
   A.refine_steps = 0;
   A.status = ctx->d_status;
-  banded_factor_solve_kernel<T><<<1, 32 * warps_for<T>(), 0, ctx->stream>>>(A);
+  banded_factor_solve_kernel<T><<<nblk(num_inst, warps_for<T>()), 32 * warps_for<T>(), 0, ctx->stream>>>(A);
   ctx->launches += 1;
   QRKIT_CUDA_TRY(ctx, cudaGetLastError());
   return QRKIT_OK;
 }
 
-qrkit_status banded_explicit_solve(qrkit_ctx* ctx, const void* rows, const int64_t* starts,
-                                   int64_t nrows, const void* rhs, int64_t n, int w,
+qrkit_status banded_explicit_solve(qrkit_ctx* ctx, int64_t num_inst, const int64_t* inst,
+                                   const void* rows, const int64_t* starts, const void* rhs, int w,
                                    const double* D, double lambda, void* Rw, void* c, void* x,
-                                   double* res2, int64_t* meta) {
+                                   double* res2) {
   if (w < 1 || w > kBW) return fail(ctx, QRKIT_EUNSUPPORTED, "reduced band window must be in [1, 16]");
+  if (num_inst < 1) return QRKIT_OK;
   if (ctx->precision == QRKIT_FP64)
-    return explicit_run<double>(ctx, (const double*)rows, starts, nrows, (const double*)rhs, n, w, D,
-                                lambda, (double*)Rw, (double*)c, (double*)x, res2, meta);
-  return explicit_run<float>(ctx, (const float*)rows, starts, nrows, (const float*)rhs, n, w, D,
-                             lambda, (float*)Rw, (float*)c, (float*)x, res2, meta);
+    return explicit_run<double>(ctx, num_inst, inst, (const double*)rows, starts, (const double*)rhs, w,
+                                D, lambda, (double*)Rw, (double*)c, (double*)x, res2);
+  return explicit_run<float>(ctx, num_inst, inst, (const float*)rows, starts, (const float*)rhs, w, D,
+                             lambda, (float*)Rw, (float*)c, (float*)x, res2);
 }
 
-qrkit_status banded_tri_solve(qrkit_ctx* ctx, const void* Rw, int64_t n, int w, void* v, bool transpose) {
+qrkit_status banded_tri_solve(qrkit_ctx* ctx, int64_t num_inst, const int64_t* inst, const void* Rw,
+                              int w, void* v, bool transpose) {
+  if (num_inst < 1) return QRKIT_OK;
   if (ctx->precision == QRKIT_FP64)
-    band_tri_solve_kernel<double><<<1, 32, 0, ctx->stream>>>((const double*)Rw, n, w, (double*)v, transpose ? 1 : 0);
+    band_tri_solve_kernel<double><<<nblk(num_inst, 64), 64, 0, ctx->stream>>>(
+        num_inst, inst, (const double*)Rw, w, (double*)v, transpose ? 1 : 0);
   else
-    band_tri_solve_kernel<float><<<1, 32, 0, ctx->stream>>>((const float*)Rw, n, w, (float*)v, transpose ? 1 : 0);
+    band_tri_solve_kernel<float><<<nblk(num_inst, 64), 64, 0, ctx->stream>>>(
+        num_inst, inst, (const float*)Rw, w, (float*)v, transpose ? 1 : 0);
   ctx->launches += 1;
   QRKIT_CUDA_TRY(ctx, cudaGetLastError());
   return QRKIT_OK;

@@ -542,7 +542,7 @@ static FactorOut<T> fout(qrkit_ctx* ctx) {
 
 template <typename T>
 static qrkit_status factor_typed(qrkit_ctx* ctx, const void* J, const void* S, const void* Dext,
-                                 double lambda) {
+                                 double lambda, bool dext_double = false) {
   Plan& P = ctx->plan;
   Composed& C = ctx->comp;
   cudaStream_t st = ctx->stream;
@@ -557,7 +557,7 @@ static qrkit_status factor_typed(qrkit_ctx* ctx, const void* J, const void* S, c
   ComposedView<T> V = view<T>(ctx, J, S);
   // D: caller's (copied to double) or column norms of J
   if (Dext) {
-    if (sizeof(T) == sizeof(double)) {
+    if (sizeof(T) == sizeof(double) || dext_double) {
       QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(C.D.ptr, Dext, (size_t)N * sizeof(double),
                                           cudaMemcpyDeviceToDevice, st));
     } else {
@@ -576,6 +576,13 @@ static qrkit_status factor_typed(qrkit_ctx* ctx, const void* J, const void* S, c
   }
   FactorOut<T> O = fout<T>(ctx);
   LAUNCH(ctx, block_factor_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O));
+  if (V.coupled == QRKIT_COUPLED_WINDOW) {
+    // P_r of the reduced block: its rows sorted by leading column per segment (Sec. 4.3)
+    rc = reduced_row_sort(ctx, C.sort, (int64_t)P.seg_cols.size(), C.sort_hist_entries,
+                          (const int64_t*)C.Xstart.ptr, C.Xw.ptr, V.w, (int*)C.hist.ptr,
+                          (int64_t*)C.spos.ptr, (int64_t*)C.order.ptr, (int64_t*)C.Xstart_s.ptr, C.Xw_s.ptr);
+    if (rc != QRKIT_OK) return rc;
+  }
   if (V.coupled == QRKIT_COUPLED_DENSE) {
     const int s = V.s;
     if (C.damp)
@@ -637,11 +644,13 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
     LAUNCH(ctx, dense_backsub_kernel<T><<<1, 32, (size_t)s * sizeof(T), st>>>(
                     (const T*)top->X.ptr, top->M, s, (const T*)top->rhs.ptr, x + nb, 0, ctx->d_status));
   } else if (V.coupled == QRKIT_COUPLED_WINDOW) {
-    // reduced banded block (Sec. 4.4) with the shared columns' damping rows interleaved
-    qrkit_status rc = banded_explicit_solve(ctx, C.Xw.ptr, (const int64_t*)C.Xstart.ptr, C.red_rows,
-                                            C.rhs_red.ptr, s, V.w, O.D + nb, C.damp ? C.lam : 0.0,
-                                            C.RwS.ptr, C.cS.ptr, x + nb, (double*)C.res2.ptr,
-                                            (int64_t*)C.meta.ptr);
+    // reduced banded block of every segment (Sec. 4.4), rows in P_r order, the shared
+    // columns' damping rows interleaved
+    qrkit_status rc = reduced_rhs_sort(ctx, (const int64_t*)C.spos.ptr, C.rhs_red.ptr, C.rhs_s.ptr, C.red_rows);
+    if (rc != QRKIT_OK) return rc;
+    rc = banded_explicit_solve(ctx, (int64_t)P.seg_cols.size(), (const int64_t*)C.seg_inst.ptr, C.Xw_s.ptr,
+                               (const int64_t*)C.Xstart_s.ptr, C.rhs_s.ptr, V.w, O.D + nb,
+                               C.damp ? C.lam : 0.0, C.RwS.ptr, C.cS.ptr, x + nb, (double*)C.res2.ptr);
     if (rc != QRKIT_OK) return rc;
   }
   LAUNCH(ctx, block_backsub_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O, O.ctop, s ? x + nb : nullptr, x, 0));
@@ -664,9 +673,11 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
     if (V.coupled == QRKIT_COUPLED_WINDOW) {
       // h_S = R_S^{-T} (g_S - R12^T h_B), then dp_S = R_S^{-1} h_S, both banded
       LAUNCH(ctx, gS_to_T_kernel<T><<<blocks_for(s, 128), 128, 0, st>>>(gS, h + nb, s));
-      qrkit_status rc = banded_tri_solve(ctx, C.RwS.ptr, s, V.w, h + nb, true);
+      const int64_t nseg = (int64_t)P.seg_cols.size();
+      const int64_t* inst = (const int64_t*)C.seg_inst.ptr;
+      qrkit_status rc = banded_tri_solve(ctx, nseg, inst, C.RwS.ptr, V.w, h + nb, true);
       if (rc != QRKIT_OK) return rc;
-      rc = banded_tri_solve(ctx, C.RwS.ptr, s, V.w, h + nb, false);
+      rc = banded_tri_solve(ctx, nseg, inst, C.RwS.ptr, V.w, h + nb, false);
       if (rc != QRKIT_OK) return rc;
       LAUNCH(ctx, axpy_kernel<T><<<blocks_for(s, 128), 128, 0, st>>>(x + nb, h + nb, s));
     }
@@ -687,6 +698,11 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
 qrkit_status composed_factor(qrkit_ctx* ctx, const void* J, const void* S, const void* D, double lambda) {
   if (ctx->precision == QRKIT_FP64) return factor_typed<double>(ctx, J, S, D, lambda);
   return factor_typed<float>(ctx, J, S, D, lambda);
+}
+
+qrkit_status composed_factor_scaled(qrkit_ctx* ctx, const void* J, const void* S, const double* E) {
+  if (ctx->precision == QRKIT_FP64) return factor_typed<double>(ctx, J, S, E, 1.0, true);
+  return factor_typed<float>(ctx, J, S, E, 1.0, true);
 }
 
 qrkit_status composed_solve(qrkit_ctx* ctx, const void* J, const void* S, const void* b, void* p,
@@ -724,9 +740,18 @@ void release_composed(Composed& C) {
   release(C.g); release(C.h);
   release(C.Xw); release(C.Xstart); release(C.rhs_red); release(C.RwS); release(C.cS);
   release(C.res2); release(C.meta);
+  release(C.sort_tab); release(C.hist); release(C.spos); release(C.order); release(C.Xw_s);
+  release(C.Xstart_s); release(C.rhs_s); release(C.seg_inst);
   release(C.d_aug_off_d); release(C.d_aug_off_u); release(C.d_red_off_d); release(C.d_red_off_u);
   for (auto& L : C.levels) { release(L.X); release(L.tau); release(L.rhs); }
   C = Composed();
+}
+
+// Reduced-row offsets per block (host) with / without damping rows.
+static std::vector<int64_t> reduced_offsets(const Plan& P, bool damp) {
+  std::vector<int64_t> r(P.K + 1, 0);
+  for (int64_t i = 0; i < P.K; ++i) r[i + 1] = r[i] + (damp ? P.n[i] : P.n[i] - P.m[i]);
+  return r;
 }
 
 // Offsets of the augmented blocks for both damping states, the factor buffers, and the
@@ -760,6 +785,11 @@ qrkit_status composed_layout(qrkit_ctx* ctx, size_t elem) {
                 " has fewer rows than columns and lambda = 0");
   C.red_rows = C.damp ? C.red_rows_d : C.red_rows_u;
   const int64_t aug = C.damp ? C.aug_values_d : C.aug_values_u;
+  {
+    const int64_t N = P.cols + P.s.shared_cols;
+    if ((rc = ensure(ctx, C.g, (size_t)N * sizeof(double), "refinement g")) != QRKIT_OK) return rc;
+    if ((rc = ensure(ctx, C.h, (size_t)N * elem, "refinement h")) != QRKIT_OK) return rc;
+  }
   const int s = (int)P.s.shared_cols;
   const int w = P.s.coupled_kind == QRKIT_COUPLED_DENSE ? s : P.s.window;
   if ((rc = ensure(ctx, C.Fa, (size_t)aug * elem, "factor")) != QRKIT_OK) return rc;
@@ -776,8 +806,64 @@ qrkit_status composed_layout(qrkit_ctx* ctx, size_t elem) {
     if ((rc = ensure(ctx, C.rhs_red, (size_t)Mr * elem, "reduced rhs")) != QRKIT_OK) return rc;
     if ((rc = ensure(ctx, C.RwS, (size_t)s * w * elem, "reduced R")) != QRKIT_OK) return rc;
     if ((rc = ensure(ctx, C.cS, (size_t)s * elem, "reduced c")) != QRKIT_OK) return rc;
-    if ((rc = ensure(ctx, C.res2, sizeof(double) * 2, "reduced residual")) != QRKIT_OK) return rc;
-    if ((rc = ensure(ctx, C.meta, sizeof(int64_t) * 4, "reduced meta")) != QRKIT_OK) return rc;
+    const int64_t nseg = (int64_t)P.seg_cols.size();
+    if ((rc = ensure(ctx, C.res2, sizeof(double) * nseg, "reduced residual")) != QRKIT_OK) return rc;
+    if ((rc = ensure(ctx, C.spos, (size_t)Mr * sizeof(int64_t), "reduced row order")) != QRKIT_OK) return rc;
+    if ((rc = ensure(ctx, C.order, (size_t)Mr * sizeof(int64_t), "reduced row order")) != QRKIT_OK) return rc;
+    if ((rc = ensure(ctx, C.Xw_s, (size_t)Mr * w * elem, "sorted reduced rows")) != QRKIT_OK) return rc;
+    if ((rc = ensure(ctx, C.Xstart_s, (size_t)Mr * sizeof(int64_t), "sorted row starts")) != QRKIT_OK) return rc;
+    if ((rc = ensure(ctx, C.rhs_s, (size_t)Mr * elem, "sorted reduced rhs")) != QRKIT_OK) return rc;
+    if (C.sort_damp != (C.damp ? 1 : 0)) {
+      // chunk tables of the device row sort and the segments' banded instances (host, once
+      // per damping state: the reduced rows per block differ with and without damping rows)
+      const std::vector<int64_t> ro = reduced_offsets(P, C.damp);
+      std::vector<int64_t> c_row0, c_rows, c_hoff, c_col0, c_cols, c_out0, seg_chunk0(nseg + 1, 0);
+      std::vector<int64_t> inst(4 * nseg);
+      int64_t hoff = 0;
+      for (int64_t k = 0; k < nseg; ++k) {
+        const int64_t r0 = ro[P.seg_blk0[k]], r1 = ro[P.seg_blk0[k + 1]];
+        const int64_t rows = r1 - r0;
+        if (rows >= ((int64_t)1 << 31))
+          return fail(ctx, QRKIT_EUNSUPPORTED, "a segment has more than 2^31 reduced rows");
+        int64_t per = std::max<int64_t>(2048, (rows + 255) / 256);
+        seg_chunk0[k] = (int64_t)c_row0.size();
+        for (int64_t q = r0; q < r1; q += per) {
+          c_row0.push_back(q);
+          c_rows.push_back(std::min(per, r1 - q));
+          c_hoff.push_back(hoff);
+          c_col0.push_back(P.seg_col0[k]);
+          c_cols.push_back(P.seg_cols[k]);
+          c_out0.push_back(r0);
+          hoff += P.seg_cols[k];
+        }
+        inst[k] = P.seg_cols[k];
+        inst[nseg + k] = P.seg_col0[k];
+        inst[2 * nseg + k] = r0;
+        inst[3 * nseg + k] = rows;
+      }
+      seg_chunk0[nseg] = (int64_t)c_row0.size();
+      if (hoff > ((int64_t)1 << 28))
+        return fail(ctx, QRKIT_EUNSUPPORTED, "segments too wide for the device row sort");
+      const int64_t nc = (int64_t)c_row0.size();
+      std::vector<int64_t> tab;
+      for (auto* v : {&c_row0, &c_rows, &c_hoff, &c_col0, &c_cols, &c_out0}) tab.insert(tab.end(), v->begin(), v->end());
+      tab.insert(tab.end(), seg_chunk0.begin(), seg_chunk0.end());
+      if ((rc = upload_i64(ctx, C.sort_tab, tab, "row sort tables")) != QRKIT_OK) return rc;
+      if ((rc = upload_i64(ctx, C.seg_inst, inst, "segment instances")) != QRKIT_OK) return rc;
+      if ((rc = ensure(ctx, C.hist, (size_t)std::max<int64_t>(hoff, 1) * sizeof(int), "row sort histograms")) != QRKIT_OK)
+        return rc;
+      const int64_t* t = (const int64_t*)C.sort_tab.ptr;
+      C.sort.num_chunks = nc;
+      C.sort.chunk_row0 = t;
+      C.sort.chunk_rows = t + nc;
+      C.sort.chunk_hoff = t + 2 * nc;
+      C.sort.chunk_col0 = t + 3 * nc;
+      C.sort.chunk_cols = t + 4 * nc;
+      C.sort.chunk_out0 = t + 5 * nc;
+      C.sort.seg_chunk0 = t + 6 * nc;
+      C.sort_hist_entries = hoff;
+      C.sort_damp = C.damp ? 1 : 0;
+    }
   }
   if (P.s.coupled_kind == QRKIT_COUPLED_DENSE) {
     if (s > 64) return fail(ctx, QRKIT_EUNSUPPORTED, "dense shared block wider than 64 columns");

@@ -58,6 +58,7 @@ static void release_plan(Plan& P) {
   release(P.d_row_off);
   release(P.d_col_off);
   release(P.d_start);
+  release(P.d_seg);
   release(P.d_n);
   release(P.d_m);
   release(P.d_tile_block);
@@ -140,13 +141,37 @@ static qrkit_status plan_blocks(qrkit_ctx* ctx, const qrkit_structure* s) {
     P.col_off[i + 1] = P.col_off[i] + P.m[i];
   }
   if (s->coupled_kind == QRKIT_COUPLED_WINDOW) {
-    P.start.assign(s->window_start, s->window_start + P.K);
-    for (int64_t i = 0; i < P.K; ++i) {
-      if (P.start[i] < 0 || P.start[i] >= s->shared_cols)
-        return fail(ctx, QRKIT_EINVAL, "window_start out of range at block " + std::to_string(i));
-      if (i && P.start[i] < P.start[i - 1])
-        return fail(ctx, QRKIT_EINVAL, "window_start must be non-decreasing (apply P_r)");
+    // segments of S (Sec. 4.2 horizontal concatenation of independent banded parts)
+    const int64_t nseg = s->num_segments > 0 ? s->num_segments : 1;
+    if (s->num_segments > 1 && (!s->segment_cols || !s->segment_blocks))
+      return fail(ctx, QRKIT_EINVAL, "segment_cols and segment_blocks are required for num_segments > 1");
+    if (s->num_segments == 1 && s->segment_cols && s->segment_blocks) {
+      P.seg_cols.assign(1, s->segment_cols[0]);
+      P.seg_blocks.assign(1, s->segment_blocks[0]);
+    } else if (s->num_segments > 1) {
+      P.seg_cols.assign(s->segment_cols, s->segment_cols + nseg);
+      P.seg_blocks.assign(s->segment_blocks, s->segment_blocks + nseg);
+    } else {
+      P.seg_cols.assign(1, s->shared_cols);
+      P.seg_blocks.assign(1, P.K);
     }
+    P.seg_col0.assign(nseg + 1, 0);
+    P.seg_blk0.assign(nseg + 1, 0);
+    for (int64_t k = 0; k < nseg; ++k) {
+      if (P.seg_cols[k] < 1 || P.seg_blocks[k] < 0)
+        return fail(ctx, QRKIT_EINVAL, "segment " + std::to_string(k) + " is empty or negative");
+      P.seg_col0[k + 1] = P.seg_col0[k] + P.seg_cols[k];
+      P.seg_blk0[k + 1] = P.seg_blk0[k] + P.seg_blocks[k];
+    }
+    if (P.seg_col0[nseg] != s->shared_cols)
+      return fail(ctx, QRKIT_EINVAL, "segment_cols must sum to shared_cols");
+    if (P.seg_blk0[nseg] != P.K) return fail(ctx, QRKIT_EINVAL, "segment_blocks must sum to num_blocks");
+    P.start.assign(s->window_start, s->window_start + P.K);
+    for (int64_t k = 0; k < nseg; ++k)
+      for (int64_t i = P.seg_blk0[k]; i < P.seg_blk0[k + 1]; ++i)
+        if (P.start[i] < P.seg_col0[k] || P.start[i] >= P.seg_col0[k + 1])
+          return fail(ctx, QRKIT_EINVAL, "window_start of block " + std::to_string(i) +
+                                             " is outside its segment");
   }
   P.composed = s->coupled_kind != QRKIT_COUPLED_NONE;
   P.budget = block_solve_budget(elem_size(ctx));
@@ -157,9 +182,14 @@ static qrkit_status plan_blocks(qrkit_ctx* ctx, const qrkit_structure* s) {
     if ((st = upload(ctx, P.d_val_off, P.val_off.data(), ob, "plan offsets")) != QRKIT_OK) return st;
     if ((st = upload(ctx, P.d_row_off, P.row_off.data(), ob, "plan offsets")) != QRKIT_OK) return st;
     if ((st = upload(ctx, P.d_col_off, P.col_off.data(), ob, "plan offsets")) != QRKIT_OK) return st;
-    if (!P.start.empty())
+    if (!P.start.empty()) {
       if ((st = upload(ctx, P.d_start, P.start.data(), P.K * sizeof(int32_t), "plan starts")) != QRKIT_OK)
         return st;
+      std::vector<int64_t> seg(P.seg_blk0);
+      seg.insert(seg.end(), P.seg_col0.begin(), P.seg_col0.end());
+      if ((st = upload(ctx, P.d_seg, seg.data(), seg.size() * sizeof(int64_t), "plan segments")) != QRKIT_OK)
+        return st;
+    }
   }
   if ((st = upload(ctx, P.d_n, P.n.data(), P.K, "plan n")) != QRKIT_OK) return st;
   if ((st = upload(ctx, P.d_m, P.m.data(), P.K, "plan m")) != QRKIT_OK) return st;
@@ -176,6 +206,8 @@ static qrkit_status plan_blocks(qrkit_ctx* ctx, const qrkit_structure* s) {
   P.s.block_rows = nullptr;
   P.s.block_cols = nullptr;
   P.s.window_start = nullptr;
+  P.s.segment_cols = nullptr;
+  P.s.segment_blocks = nullptr;
   P.valid = true;
   return QRKIT_OK;
 }
@@ -232,6 +264,7 @@ void qrkit_destroy(qrkit_ctx* ctx) {
   cudaSetDevice(ctx->device);
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
+  release_lm(ctx->lm);
   release_plan(ctx->plan);
   release_composed(ctx->comp);
   release_band(ctx->band);
@@ -252,6 +285,7 @@ qrkit_status qrkit_plan(qrkit_ctx* ctx, const qrkit_structure* s) {
   release_plan(ctx->plan);
   release_composed(ctx->comp);
   release_band(ctx->band);
+  release_lm(ctx->lm);
   ctx->factored = false;
   if (s->kind == QRKIT_STRUCT_BLOCKS) return plan_blocks(ctx, s);
   if (s->kind == QRKIT_STRUCT_BANDED) return banded_plan(ctx, s);
@@ -353,6 +387,30 @@ qrkit_status qrkit_get_factor(qrkit_ctx* ctx, void* factor_out, void* tau_out) {
                                         cudaMemcpyDeviceToDevice, ctx->stream));
   if (tau_out)
     QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(tau_out, ctx->ws.tau.ptr, (size_t)ctx->plan.cols * es,
+                                        cudaMemcpyDeviceToDevice, ctx->stream));
+  return QRKIT_OK;
+}
+
+qrkit_status qrkit_set_window_start(qrkit_ctx* ctx, const int32_t* start) {
+  if (!ctx) return QRKIT_EINVAL;
+  const Plan& P = ctx->plan;
+  if (!P.valid || P.s.kind != QRKIT_STRUCT_BLOCKS || P.s.coupled_kind != QRKIT_COUPLED_WINDOW)
+    return fail(ctx, QRKIT_ESTATE, "qrkit_set_window_start needs a windowed block plan");
+  if (!start) return fail(ctx, QRKIT_EINVAL, "start is required");
+  QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  ctx->comp_factored = false;
+  return window_start_copy(ctx, start);
+}
+
+qrkit_status qrkit_get_row_order(qrkit_ctx* ctx, int64_t* order) {
+  if (!ctx) return QRKIT_EINVAL;
+  const Plan& P = ctx->plan;
+  if (!P.valid || P.s.kind != QRKIT_STRUCT_BLOCKS || P.s.coupled_kind != QRKIT_COUPLED_WINDOW)
+    return fail(ctx, QRKIT_ESTATE, "qrkit_get_row_order needs a windowed block plan");
+  if (!ctx->comp_factored) return fail(ctx, QRKIT_ESTATE, "qrkit_get_row_order before qrkit_factor");
+  if (!order) return fail(ctx, QRKIT_EINVAL, "order is required");
+  if (ctx->comp.red_rows > 0)
+    QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(order, ctx->comp.order.ptr, (size_t)ctx->comp.red_rows * sizeof(int64_t),
                                         cudaMemcpyDeviceToDevice, ctx->stream));
   return QRKIT_OK;
 }

@@ -49,9 +49,12 @@ struct Plan {
   TileBudget budget{};
   std::vector<int64_t> val_off, row_off, col_off;   // K + 1 each
   std::vector<int32_t> start;                      // window starts (QRKIT_COUPLED_WINDOW)
+  // independent segments of the windowed S (one segment = all shared columns by default)
+  std::vector<int64_t> seg_cols, seg_col0, seg_blocks, seg_blk0;   // seg_col0 / seg_blk0: nseg + 1
   // device copies
   DevBuf d_n, d_m, d_tile_block, d_tile_val, d_tile_row, d_tile_col;
   DevBuf d_val_off, d_row_off, d_col_off, d_start;
+  DevBuf d_seg;   // 2 x (nseg + 1): seg_blk0 then seg_col0
 };
 
 // Read-only view of a block-angular structure and its values (device pointers).
@@ -92,6 +95,18 @@ struct FactorOut {
   int* status;
 };
 
+// Chunk tables of the device row sort of the windowed reduced block (Sec. 4.3 P_r).
+struct RowSortTables {
+  int64_t num_chunks;
+  const int64_t* chunk_row0;   // first reduced row of the chunk
+  const int64_t* chunk_rows;
+  const int64_t* chunk_hoff;   // offset of the chunk's histogram (its segment's column count)
+  const int64_t* chunk_col0;   // first shared column of the chunk's segment
+  const int64_t* chunk_cols;   // shared columns of that segment
+  const int64_t* chunk_out0;   // first sorted position of that segment
+  const int64_t* seg_chunk0;   // nseg + 1: first chunk of each segment
+};
+
 // Device state of a batch of banded instances (Sec. 4.4).
 struct Band {
   int64_t num_inst = 0, total_cols = 0, total_rows = 0;
@@ -115,11 +130,20 @@ struct Composed {
   int64_t red_rows_d = 0, red_rows_u = 0;
   DevBuf D, sq, Fa, tau, R12, ctop, g, h;
   DevBuf Xw, Xstart, rhs_red, RwS, cS, res2, meta;   // windowed reduced block
+  // device row sort of the windowed reduced block, per damping state (-1: not built)
+  int sort_damp = -1;
+  int64_t sort_hist_entries = 0;
+  RowSortTables sort{};
+  DevBuf sort_tab, hist, spos, order, Xw_s, Xstart_s, rhs_s;
+  DevBuf seg_inst;                 // 4 x nseg: cols, col0, row0, rows of the segments' banded solves
   DevBuf d_aug_off_d, d_aug_off_u, d_red_off_d, d_red_off_u;
   std::vector<TsqrLevel> levels;
   const void* J = nullptr;         // caller's values recorded at factor time
   const void* S = nullptr;
 };
+
+struct LM;   // Levenberg-Marquardt state of a planned model (lm.cu)
+void release_lm(LM*& lm);
 
 struct Workspace {
   DevBuf factor;   // factor values (J packing)
@@ -139,6 +163,7 @@ struct qrkit_ctx {
   qrkit::Workspace ws;
   qrkit::Composed comp;
   qrkit::Band band;
+  qrkit::LM* lm = nullptr;    // LM model plan and buffers (qrkit_lm_plan)
   int* d_status = nullptr;   // device status word
   int64_t launches = 0;
   size_t smem_attr[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // dynamic smem opted in, per kernel variant
@@ -165,6 +190,9 @@ TileBudget block_solve_budget(size_t elem);
 qrkit_status composed_layout(qrkit_ctx* ctx, size_t elem);
 qrkit_status widen_to_double(qrkit_ctx* ctx, const float* in, double* out, int64_t n);
 qrkit_status composed_factor(qrkit_ctx* ctx, const void* J, const void* S, const void* D, double lambda);
+// Composed factor with the damping diagonal given directly as E = lambda^(1/2) D (double,
+// N entries) and lambda = 1: per-column damping, e.g. one lambda per independent problem.
+qrkit_status composed_factor_scaled(qrkit_ctx* ctx, const void* J, const void* S, const double* E);
 qrkit_status composed_solve(qrkit_ctx* ctx, const void* J, const void* S, const void* b, void* p,
                             int refine_steps);
 qrkit_status composed_apply_qt(qrkit_ctx* ctx, const void* b, void* qtb);
@@ -174,11 +202,19 @@ qrkit_status banded_plan(qrkit_ctx* ctx, const qrkit_structure* s);
 qrkit_status banded_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
                                  double lambda, void* p, int refine_steps);
 qrkit_status banded_get_factor(qrkit_ctx* ctx, void* Rw_out, void* c_out, double* res2_out);
-qrkit_status banded_explicit_solve(qrkit_ctx* ctx, const void* rows, const int64_t* starts,
-                                   int64_t nrows, const void* rhs, int64_t n, int w,
+// Banded factor + solve of num_inst instances whose rows have explicit starts (grouped per
+// instance, non-decreasing within one); inst: 4 x num_inst device int64 (cols, col0, row0, rows).
+qrkit_status banded_explicit_solve(qrkit_ctx* ctx, int64_t num_inst, const int64_t* inst,
+                                   const void* rows, const int64_t* starts, const void* rhs, int w,
                                    const double* D, double lambda, void* Rw, void* c, void* x,
-                                   double* res2, int64_t* meta);
-qrkit_status banded_tri_solve(qrkit_ctx* ctx, const void* Rw, int64_t n, int w, void* v, bool transpose);
+                                   double* res2);
+qrkit_status banded_tri_solve(qrkit_ctx* ctx, int64_t num_inst, const int64_t* inst, const void* Rw,
+                              int w, void* v, bool transpose);
+qrkit_status reduced_row_sort(qrkit_ctx* ctx, const RowSortTables& t, int64_t nseg, int64_t hist_entries,
+                              const int64_t* Xstart, const void* Xw, int w, int* hist, int64_t* spos,
+                              int64_t* order, int64_t* Xstart_s, void* Xw_s);
+qrkit_status window_start_copy(qrkit_ctx* ctx, const int32_t* in);
+qrkit_status reduced_rhs_sort(qrkit_ctx* ctx, const int64_t* spos, const void* rhs, void* rhs_s, int64_t rows);
 void release_band(Band& B);
 qrkit_status launch_block_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
                                 void* p, void* qtb, int refine_steps);

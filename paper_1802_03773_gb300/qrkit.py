@@ -45,8 +45,37 @@ class Structure(ctypes.Structure):
         ("rows_per_col", ctypes.c_int32),
         ("band_window", ctypes.c_int32),
         ("instance_cols", ctypes.c_void_p),
+        ("num_segments", ctypes.c_int64),
+        ("segment_cols", ctypes.c_void_p),
+        ("segment_blocks", ctypes.c_void_p),
     ]
 
+
+class LMProblem(ctypes.Structure):
+    _fields_ = [
+        ("model", ctypes.c_int32),
+        ("num_problems", ctypes.c_int64),
+        ("num_points", ctypes.c_void_p),
+        ("control_points", ctypes.c_void_p),
+        ("data", ctypes.c_void_p),
+    ]
+
+
+class LMState(ctypes.Structure):
+    _fields_ = [
+        ("lambda_", ctypes.c_double),
+        ("nu", ctypes.c_double),
+        ("cost", ctypes.c_double),
+        ("cost_new", ctypes.c_double),
+        ("pred", ctypes.c_double),
+        ("rho", ctypes.c_double),
+        ("accepted", ctypes.c_int32),
+        ("done", ctypes.c_int32),
+        ("iteration", ctypes.c_int64),
+    ]
+
+
+MODEL_CURVEFIT = 0
 
 _VP = ctypes.c_void_p
 _SIGS = {
@@ -62,6 +91,11 @@ _SIGS = {
     "qrkit_apply_qt": (ctypes.c_int, [_VP, _VP, _VP]),
     "qrkit_solve_r": (ctypes.c_int, [_VP, _VP, _VP]),
     "qrkit_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
+    "qrkit_set_window_start": (ctypes.c_int, [_VP, _VP]),
+    "qrkit_get_row_order": (ctypes.c_int, [_VP, _VP]),
+    "qrkit_lm_plan": (ctypes.c_int, [_VP, ctypes.POINTER(LMProblem)]),
+    "qrkit_lm_step": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
+    "qrkit_lm_run": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
     "qrkit_sync_status": (ctypes.c_int, [_VP]),
     "qrkit_block_solve_noalloc": (ctypes.c_int, [ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int64, _VP,
                                                  _VP, _VP, _VP, _VP, ctypes.c_int]),
@@ -164,7 +198,8 @@ class Context:
         return _ptr(t)
 
     # ---- structure plan ----
-    def plan_blocks(self, n, m, coupled=COUPLED_NONE, shared_cols=0, window=0, window_start=None):
+    def plan_blocks(self, n, m, coupled=COUPLED_NONE, shared_cols=0, window=0, window_start=None,
+                    segment_cols=None, segment_blocks=None):
         n = np.ascontiguousarray(n, dtype=np.uint8)
         m = np.ascontiguousarray(m, dtype=np.uint8)
         s = Structure()
@@ -179,8 +214,27 @@ class Context:
         if window_start is not None:
             ws = np.ascontiguousarray(window_start, dtype=np.int32)
             s.window_start = ws.ctypes.data
+        sc = sb = None
+        if segment_cols is not None:
+            sc = np.ascontiguousarray(segment_cols, dtype=np.int64)
+            sb = np.ascontiguousarray(segment_blocks, dtype=np.int64)
+            s.num_segments = sc.shape[0]
+            s.segment_cols = sc.ctypes.data
+            s.segment_blocks = sb.ctypes.data
         self._check(self.lib.qrkit_plan(self.h, ctypes.byref(s)))
-        self._keep = [n, m, ws]
+        self._keep = [n, m, ws, sc, sb]
+
+    def set_window_start(self, start):
+        """start: int32 CUDA tensor (one entry per block)."""
+        import torch
+        if start.device != self.device or start.dtype != torch.int32 or not start.is_contiguous():
+            raise ValueError("start: expected a contiguous int32 tensor on the context's device")
+        self._check(self.lib.qrkit_set_window_start(self.h, _ptr(start)))
+        self._starts = start
+
+    def get_row_order(self, order):
+        """order: int64 CUDA tensor, one entry per reduced row."""
+        self._check(self.lib.qrkit_get_row_order(self.h, _ptr(order)))
 
     def plan_banded(self, instance_cols, rows_per_col=4, window=8):
         cols = np.ascontiguousarray(np.atleast_1d(instance_cols), dtype=np.int64)
@@ -223,6 +277,47 @@ class Context:
     def get_factor(self, factor=None, tau=None):
         self._check(self.lib.qrkit_get_factor(self.h, self._t(factor, "factor", True),
                                               self._t(tau, "tau", True)))
+
+    # ---- Levenberg-Marquardt on the device ----
+    def lm_plan(self, num_points, control_points, data):
+        """data: float64 CUDA tensor (sum P_k, 2), kept alive by the context."""
+        import torch
+        if data.device != self.device or data.dtype != torch.float64 or not data.is_contiguous():
+            raise ValueError("data: expected a contiguous float64 tensor on the context's device")
+        npts = np.ascontiguousarray(np.atleast_1d(num_points), dtype=np.int64)
+        kc = np.ascontiguousarray(np.atleast_1d(control_points), dtype=np.int32)
+        pr = LMProblem()
+        pr.model = MODEL_CURVEFIT
+        pr.num_problems = npts.shape[0]
+        pr.num_points = npts.ctypes.data
+        pr.control_points = kc.ctypes.data
+        pr.data = data.data_ptr()
+        self._check(self.lib.qrkit_lm_plan(self.h, ctypes.byref(pr)))
+        self._lm_data = data
+        self._lm_B = int(npts.shape[0])
+
+    def lm_states(self, lam=1e-3, nu=2.0):
+        st = (LMState * self._lm_B)()
+        lams = np.broadcast_to(np.asarray(lam, dtype=np.float64), (self._lm_B,))
+        for k in range(self._lm_B):
+            st[k].lambda_ = float(lams[k])
+            st[k].nu = nu
+        return st
+
+    def _lm_x(self, x):
+        import torch
+        if x.device != self.device or x.dtype != torch.float64 or not x.is_contiguous():
+            raise ValueError("x: expected a contiguous float64 tensor on the context's device")
+        return _ptr(x)
+
+    def lm_step(self, x, states, refine_steps=1):
+        self._check(self.lib.qrkit_lm_step(self.h, self._lm_x(x), ctypes.cast(states, _VP), int(refine_steps)))
+        return states
+
+    def lm_run(self, x, states, max_iter=100, ftol=1e-12, refine_steps=1, use_graph=True):
+        self._check(self.lib.qrkit_lm_run(self.h, self._lm_x(x), ctypes.cast(states, _VP), int(max_iter),
+                                          float(ftol), int(refine_steps), 1 if use_graph else 0))
+        return states
 
     def sync_status(self):
         self._check(self.lib.qrkit_sync_status(self.h))
