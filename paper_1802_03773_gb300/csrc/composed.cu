@@ -648,9 +648,13 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
     // columns' damping rows interleaved
     qrkit_status rc = reduced_rhs_sort(ctx, (const int64_t*)C.spos.ptr, C.rhs_red.ptr, C.rhs_s.ptr, C.red_rows);
     if (rc != QRKIT_OK) return rc;
-    rc = banded_explicit_solve(ctx, (int64_t)P.seg_cols.size(), (const int64_t*)C.seg_inst.ptr, C.Xw_s.ptr,
-                               (const int64_t*)C.Xstart_s.ptr, C.rhs_s.ptr, V.w, O.D + nb,
-                               C.damp ? C.lam : 0.0, C.RwS.ptr, C.cS.ptr, x + nb, (double*)C.res2.ptr);
+    if (C.cr)
+      rc = cr_solve(ctx, *C.cr, (const int64_t*)C.Xstart_s.ptr, 1, V.w, C.Xw_s.ptr, C.rhs_s.ptr, O.D + nb,
+                    C.damp ? C.lam : 0.0, x + nb, (double*)C.res2.ptr);
+    else
+      rc = banded_explicit_solve(ctx, (int64_t)P.seg_cols.size(), (const int64_t*)C.seg_inst.ptr, C.Xw_s.ptr,
+                                 (const int64_t*)C.Xstart_s.ptr, C.rhs_s.ptr, V.w, O.D + nb,
+                                 C.damp ? C.lam : 0.0, C.RwS.ptr, C.cS.ptr, x + nb, (double*)C.res2.ptr);
     if (rc != QRKIT_OK) return rc;
   }
   LAUNCH(ctx, block_backsub_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O, O.ctop, s ? x + nb : nullptr, x, 0));
@@ -670,7 +674,12 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
                       gS, sizeof(T) == 4 ? (const float*)x : nullptr,
                       sizeof(T) == 8 ? (const double*)x : nullptr, O.D, nb, s, C.lam));
     LAUNCH(ctx, block_fwdsub_rt_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O, g, h, gS));
-    if (V.coupled == QRKIT_COUPLED_WINDOW) {
+    if (V.coupled == QRKIT_COUPLED_WINDOW && C.cr) {
+      // dp_S = R_S^{-1} R_S^{-T} (g_S - R12^T h_B) with the parallel banded factor
+      qrkit_status rc = cr_normal_solve(ctx, *C.cr, gS, h + nb);
+      if (rc != QRKIT_OK) return rc;
+      LAUNCH(ctx, axpy_kernel<T><<<blocks_for(s, 128), 128, 0, st>>>(x + nb, h + nb, s));
+    } else if (V.coupled == QRKIT_COUPLED_WINDOW) {
       // h_S = R_S^{-T} (g_S - R12^T h_B), then dp_S = R_S^{-1} h_S, both banded
       LAUNCH(ctx, gS_to_T_kernel<T><<<blocks_for(s, 128), 128, 0, st>>>(gS, h + nb, s));
       const int64_t nseg = (int64_t)P.seg_cols.size();
@@ -742,6 +751,7 @@ void release_composed(Composed& C) {
   release(C.res2); release(C.meta);
   release(C.sort_tab); release(C.hist); release(C.spos); release(C.order); release(C.Xw_s);
   release(C.Xstart_s); release(C.rhs_s); release(C.seg_inst);
+  release_cr(C.cr);
   release(C.d_aug_off_d); release(C.d_aug_off_u); release(C.d_red_off_d); release(C.d_red_off_u);
   for (auto& L : C.levels) { release(L.X); release(L.tau); release(L.rhs); }
   C = Composed();
@@ -850,6 +860,11 @@ qrkit_status composed_layout(qrkit_ctx* ctx, size_t elem) {
       tab.insert(tab.end(), seg_chunk0.begin(), seg_chunk0.end());
       if ((rc = upload_i64(ctx, C.sort_tab, tab, "row sort tables")) != QRKIT_OK) return rc;
       if ((rc = upload_i64(ctx, C.seg_inst, inst, "segment instances")) != QRKIT_OK) return rc;
+      if (w <= 8) {
+        std::vector<int64_t> ic(inst.begin(), inst.begin() + nseg), i0(inst.begin() + nseg, inst.begin() + 2 * nseg),
+            r0v(inst.begin() + 2 * nseg, inst.begin() + 3 * nseg), rv(inst.begin() + 3 * nseg, inst.end());
+        if ((rc = cr_build(ctx, C.cr, ic, i0, r0v, rv)) != QRKIT_OK) return rc;
+      }
       if ((rc = ensure(ctx, C.hist, (size_t)std::max<int64_t>(hoff, 1) * sizeof(int), "row sort histograms")) != QRKIT_OK)
         return rc;
       const int64_t* t = (const int64_t*)C.sort_tab.ptr;

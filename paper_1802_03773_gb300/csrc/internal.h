@@ -95,6 +95,9 @@ struct FactorOut {
   int* status;
 };
 
+struct CRPlan;   // parallel banded QR (cr.cu)
+void release_cr(CRPlan*& p);
+
 // Chunk tables of the device row sort of the windowed reduced block (Sec. 4.3 P_r).
 struct RowSortTables {
   int64_t num_chunks;
@@ -136,11 +139,23 @@ struct Composed {
   RowSortTables sort{};
   DevBuf sort_tab, hist, spos, order, Xw_s, Xstart_s, rhs_s;
   DevBuf seg_inst;                 // 4 x nseg: cols, col0, row0, rows of the segments' banded solves
+  CRPlan* cr = nullptr;            // parallel banded QR of the segments (window <= 8)
   DevBuf d_aug_off_d, d_aug_off_u, d_red_off_d, d_red_off_u;
   std::vector<TsqrLevel> levels;
   const void* J = nullptr;         // caller's values recorded at factor time
   const void* S = nullptr;
 };
+
+// Instance tables (host) -> level work lists and work space of the parallel banded QR.
+qrkit_status cr_build(qrkit_ctx* ctx, CRPlan*& out, const std::vector<int64_t>& cols,
+                      const std::vector<int64_t>& col0, const std::vector<int64_t>& row0,
+                      const std::vector<int64_t>& rows);
+// QR + solve of every instance: rows with explicit sorted starts (global columns) or
+// implicit starts floor(i / rpc); damping rows lambda^(1/2) D_j; x and D by global column.
+qrkit_status cr_solve(qrkit_ctx* ctx, CRPlan& C, const int64_t* starts, int rpc, int w, const void* J,
+                      const void* b, const double* D, double lambda, void* x, double* res2);
+// dx = R^{-1} R^{-T} g with the factor of the last cr_solve (g double, dx by global column).
+qrkit_status cr_normal_solve(qrkit_ctx* ctx, CRPlan& C, const double* g, void* dx);
 
 struct LM;   // Levenberg-Marquardt state of a planned model (lm.cu)
 void release_lm(LM*& lm);
