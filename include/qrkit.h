@@ -93,7 +93,19 @@ typedef struct qrkit_structure {
                                     matrix, solved in parallel with the others */
   const int64_t* segment_blocks; /* host, num_segments entries summing to K: the blocks are
                                     grouped by segment in order, this many per segment */
+  /* --- QRKIT_STRUCT_BANDED: algorithm --- */
+  int32_t band_solver;           /* QRKIT_BAND_AUTO, QRKIT_BAND_SWEEP or QRKIT_BAND_PARALLEL */
 } qrkit_structure;
+
+/* Banded QR algorithms (both Sec. 4.4 block-banded Householder QR with the damping rows
+ * interleaved):
+ *   SWEEP     one warp per instance sweeps the column groups in order, carrying the trailing
+ *             triangle; R comes out in natural column order (qrkit_get_band_factor).
+ *   PARALLEL  rows compressed per block of 8 columns, then block cyclic reduction over the
+ *             blocks (log-depth, all blocks of a level in parallel); R is that of the columns
+ *             in nested-dissection order and is not exported.  Needs band_window <= 8.
+ *   AUTO      PARALLEL when band_window <= 8, else SWEEP. */
+enum { QRKIT_BAND_AUTO = 0, QRKIT_BAND_SWEEP = 1, QRKIT_BAND_PARALLEL = 2 };
 
 typedef struct qrkit_ctx qrkit_ctx;
 
@@ -201,7 +213,8 @@ qrkit_status qrkit_block_solve_noalloc(int device, void* stream, int precision,
 
 /* Banded factor of the last qrkit_factor_solve on a QRKIT_STRUCT_BANDED plan (device pointers,
  * any may be NULL): Rw[j * w + t] = R[j, j + t] per global column j, c = top of Q^T [b; 0] per
- * column; res2 (HOST, one double per instance) = squared residual norm.  Synchronous. */
+ * column; res2 (HOST, one double per instance) = squared residual norm.  Synchronous.
+ * Rw and c exist only for the SWEEP algorithm (QRKIT_EUNSUPPORTED otherwise); res2 always. */
 qrkit_status qrkit_get_band_factor(qrkit_ctx* ctx, void* Rw, void* c, double* res2);
 
 /* Copy the stored factor of a block structure to caller buffers (device pointers, either

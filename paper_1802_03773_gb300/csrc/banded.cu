@@ -354,6 +354,58 @@ __global__ void band_colnorm_kernel(const float* Jf, const double* Jd, const int
   D[gj] = d == 0.0 ? 1.0 : d;
 }
 
+// Refinement pieces of the parallel path, one thread per row / per column:
+// r = b - J x in double, then g_j = sum_i J_ij r_i - lambda D_j^2 x_j.
+template <typename T>
+__global__ void band_resid_kernel(const T* J, const T* b, const T* x, const int64_t* inst_cols,
+                                  const int64_t* inst_col0, const int64_t* inst_row0, int64_t num_inst,
+                                  int64_t total_rows, int rpc, int w, double* r) {
+  const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= total_rows) return;
+  int64_t lo = 0, hi = num_inst - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (inst_row0[mid] <= gi) lo = mid; else hi = mid - 1;
+  }
+  const int64_t i = gi - inst_row0[lo], N = inst_cols[lo], c0 = inst_col0[lo];
+  const int64_t s = i / rpc;
+  const T* row = J + gi * w;
+  double acc = (double)b[gi];
+  for (int t = 0; t < w && s + t < N; ++t) acc -= (double)row[t] * (double)x[c0 + s + t];
+  r[gi] = acc;
+}
+
+template <typename T>
+__global__ void band_g_kernel(const T* J, const T* x, const double* r, const double* D, double lam,
+                              const int64_t* inst_cols, const int64_t* inst_col0, const int64_t* inst_row0,
+                              int64_t num_inst, int64_t total_cols, int rpc, int w, double* g) {
+  const int64_t gj = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gj >= total_cols) return;
+  int64_t lo = 0, hi = num_inst - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (inst_col0[mid] <= gj) lo = mid; else hi = mid - 1;
+  }
+  const int64_t j = gj - inst_col0[lo], N = inst_cols[lo], r0 = inst_row0[lo];
+  const int64_t nrows = (int64_t)rpc * N;
+  double acc = 0.0;
+  const int64_t s_lo = j - w + 1 > 0 ? j - w + 1 : 0;
+  for (int64_t s = s_lo; s <= j; ++s)
+    for (int q = 0; q < rpc; ++q) {
+      const int64_t i = s * rpc + q;
+      if (i >= nrows) break;
+      acc += (double)J[(r0 + i) * w + (j - s)] * r[r0 + i];
+    }
+  if (lam > 0.0) acc -= lam * D[gj] * D[gj] * (double)x[gj];
+  g[gj] = acc;
+}
+
+template <typename T>
+__global__ void band_axpy_kernel(T* x, const T* d, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) x[i] += d[i];
+}
+
 inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 
 }  // namespace
@@ -381,6 +433,11 @@ qrkit_status banded_plan(qrkit_ctx* ctx, const qrkit_structure* s) {
     rr += cols[i] * s->rows_per_col;
   }
   Band& B = ctx->band;
+  if (s->band_solver < QRKIT_BAND_AUTO || s->band_solver > QRKIT_BAND_PARALLEL)
+    return fail(ctx, QRKIT_EINVAL, "unknown band_solver");
+  if (s->band_solver == QRKIT_BAND_PARALLEL && s->band_window > 8)
+    return fail(ctx, QRKIT_EUNSUPPORTED, "the parallel banded QR needs band_window <= 8");
+  B.parallel = s->band_solver == QRKIT_BAND_PARALLEL || (s->band_solver == QRKIT_BAND_AUTO && s->band_window <= 8);
   B.num_inst = (int64_t)cols.size();
   B.total_cols = cc;
   B.total_rows = rr;
@@ -401,6 +458,14 @@ qrkit_status banded_plan(qrkit_ctx* ctx, const qrkit_structure* s) {
   if ((st = ensure(ctx, B.c, (size_t)cc * es, "banded c")) != QRKIT_OK) return st;
   if ((st = ensure(ctx, B.D, (size_t)cc * sizeof(double), "banded D")) != QRKIT_OK) return st;
   if ((st = ensure(ctx, B.res2, (size_t)B.num_inst * sizeof(double), "banded residual")) != QRKIT_OK) return st;
+  if (B.parallel) {
+    std::vector<int64_t> rows(cols.size());
+    for (size_t i = 0; i < cols.size(); ++i) rows[i] = cols[i] * s->rows_per_col;
+    if ((st = cr_build(ctx, B.cr, cols, c0, r0, rows)) != QRKIT_OK) return st;
+    if ((st = ensure(ctx, B.g, (size_t)cc * sizeof(double), "banded g")) != QRKIT_OK) return st;
+    if ((st = ensure(ctx, B.h, (size_t)cc * es, "banded h")) != QRKIT_OK) return st;
+    if ((st = ensure(ctx, B.r, (size_t)rr * sizeof(double), "banded r")) != QRKIT_OK) return st;
+  }
   P.s = *s;
   P.s.block_rows = nullptr;
   P.s.block_cols = nullptr;
@@ -435,6 +500,26 @@ static qrkit_status banded_run(qrkit_ctx* ctx, const void* J, const void* b, con
       ctx->launches += 1;
       QRKIT_CUDA_TRY(ctx, cudaGetLastError());
     }
+  }
+  if (B.parallel) {
+    qrkit_status rc = cr_solve(ctx, *B.cr, nullptr, B.rows_per_col, B.w, J, b, D, lambda, p,
+                               (double*)B.res2.ptr);
+    if (rc != QRKIT_OK) return rc;
+    for (int it = 0; it < refine_steps; ++it) {
+      band_resid_kernel<T><<<nblk(B.total_rows, 256), 256, 0, st>>>(
+          (const T*)J, (const T*)b, (const T*)p, dcols, dc0, dr0, B.num_inst, B.total_rows, B.rows_per_col, B.w,
+          (double*)B.r.ptr);
+      band_g_kernel<T><<<nblk(B.total_cols, 256), 256, 0, st>>>(
+          (const T*)J, (const T*)p, (const double*)B.r.ptr, D, lambda, dcols, dc0, dr0, B.num_inst, B.total_cols,
+          B.rows_per_col, B.w, (double*)B.g.ptr);
+      ctx->launches += 2;
+      QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+      if ((rc = cr_normal_solve(ctx, *B.cr, (const double*)B.g.ptr, B.h.ptr)) != QRKIT_OK) return rc;
+      band_axpy_kernel<T><<<nblk(B.total_cols, 256), 256, 0, st>>>((T*)p, (const T*)B.h.ptr, B.total_cols);
+      ctx->launches += 1;
+      QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    return QRKIT_OK;
   }
   BandArgs<T> A;
   A.num_inst = B.num_inst;
@@ -545,6 +630,8 @@ qrkit_status banded_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, c
 qrkit_status banded_get_factor(qrkit_ctx* ctx, void* Rw_out, void* c_out, double* res2_out) {
   Band& B = ctx->band;
   const size_t es = elem_size(ctx);
+  if (B.parallel && (Rw_out || c_out))
+    return fail(ctx, QRKIT_EUNSUPPORTED, "R windows and Q^T b exist only for the sweep algorithm");
   if (Rw_out)
     QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(Rw_out, B.Rw.ptr, (size_t)B.total_cols * B.w * es,
                                         cudaMemcpyDeviceToDevice, ctx->stream));
@@ -560,6 +647,7 @@ qrkit_status banded_get_factor(qrkit_ctx* ctx, void* Rw_out, void* c_out, double
 void release_band(Band& B) {
   release(B.d_cols); release(B.d_col0); release(B.d_row0); release(B.Rw); release(B.c);
   release(B.D); release(B.res2); release(B.g); release(B.h); release(B.r);
+  release_cr(B.cr);
   B = Band();
 }
 

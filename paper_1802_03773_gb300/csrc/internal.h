@@ -114,6 +114,8 @@ struct RowSortTables {
 struct Band {
   int64_t num_inst = 0, total_cols = 0, total_rows = 0;
   int rows_per_col = 1, w = 1;
+  bool parallel = false;          // QRKIT_BAND_PARALLEL in effect
+  CRPlan* cr = nullptr;
   DevBuf d_cols, d_col0, d_row0, Rw, c, D, res2, g, h, r;
 };
 

@@ -72,16 +72,20 @@ void release_lm(LM*& lm) {
 
 namespace {
 
-// Uniform cubic B-spline basis and its derivative at u in [0, 1] (extrapolated outside).
+// Uniform cubic B-spline basis and its derivative at u in [0, 1] (extrapolated outside),
+// in Horner form with multiplications only (double division is slow on this part):
+//   6 B_0 = (1-u)^3, 6 B_1 = (3u - 6) u^2 + 4, 6 B_2 = ((-3u + 3) u + 3) u + 1, 6 B_3 = u^3,
+//   B_0' = -(1-u)^2 / 2, B_1' = (3u/2 - 2) u, B_2' = (-3u/2 + 1) u + 1/2, B_3' = u^2 / 2.
 __device__ __forceinline__ void bspline(double u, double B[4], double dB[4]) {
-  const double v = 1.0 - u, u2 = u * u, u3 = u2 * u;
-  B[0] = v * v * v / 6.0;
-  B[1] = (3.0 * u3 - 6.0 * u2 + 4.0) / 6.0;
-  B[2] = (-3.0 * u3 + 3.0 * u2 + 3.0 * u + 1.0) / 6.0;
-  B[3] = u3 / 6.0;
+  const double sixth = 1.0 / 6.0;
+  const double v = 1.0 - u, u2 = u * u;
+  B[0] = v * v * v * sixth;
+  B[1] = fma(fma(3.0, u, -6.0), u2, 4.0) * sixth;
+  B[2] = fma(fma(fma(-3.0, u, 3.0), u, 3.0), u, 1.0) * sixth;
+  B[3] = u2 * u * sixth;
   dB[0] = -0.5 * v * v;
-  dB[1] = (9.0 * u2 - 12.0 * u) / 6.0;
-  dB[2] = (-9.0 * u2 + 6.0 * u + 3.0) / 6.0;
+  dB[1] = fma(1.5, u, -2.0) * u;
+  dB[2] = fma(fma(-1.5, u, 1.0), u, 0.5);
   dB[3] = 0.5 * u2;
 }
 

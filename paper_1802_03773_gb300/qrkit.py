@@ -17,6 +17,7 @@ LIB_PATH = os.path.join(_PKG, "libqrkit.so")
 FP64, FP32_REFINED, FP32 = 0, 1, 2
 PRECISION = {"fp64": FP64, "fp32_refined": FP32_REFINED, "fp32": FP32}
 STRUCT_BLOCKS, STRUCT_BANDED = 0, 1
+BAND_AUTO, BAND_SWEEP, BAND_PARALLEL = 0, 1, 2
 COUPLED_NONE, COUPLED_DENSE, COUPLED_WINDOW = 0, 1, 2
 
 STATUS = {0: "QRKIT_OK", 1: "QRKIT_EINVAL", 2: "QRKIT_ENOMEM", 3: "QRKIT_ECUDA",
@@ -48,6 +49,7 @@ class Structure(ctypes.Structure):
         ("num_segments", ctypes.c_int64),
         ("segment_cols", ctypes.c_void_p),
         ("segment_blocks", ctypes.c_void_p),
+        ("band_solver", ctypes.c_int32),
     ]
 
 
@@ -236,7 +238,7 @@ class Context:
         """order: int64 CUDA tensor, one entry per reduced row."""
         self._check(self.lib.qrkit_get_row_order(self.h, _ptr(order)))
 
-    def plan_banded(self, instance_cols, rows_per_col=4, window=8):
+    def plan_banded(self, instance_cols, rows_per_col=4, window=8, solver=BAND_AUTO):
         cols = np.ascontiguousarray(np.atleast_1d(instance_cols), dtype=np.int64)
         s = Structure()
         s.kind = STRUCT_BANDED
@@ -245,6 +247,7 @@ class Context:
         s.cols = int(cols[0])
         s.rows_per_col = int(rows_per_col)
         s.band_window = int(window)
+        s.band_solver = int(solver)
         self._check(self.lib.qrkit_plan(self.h, ctypes.byref(s)))
         self._keep = [cols]
 

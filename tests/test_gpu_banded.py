@@ -19,13 +19,16 @@ def batch(cols, rpc, w, dtype, seed=0):
     return inst, vals, b
 
 
-def run(cols, rpc, w, precision, lam, refine_steps=1, D=None, seed=0):
+SOLVER = {"sweep": 1, "parallel": 2}
+
+
+def run(cols, rpc, w, precision, lam, refine_steps=1, D=None, seed=0, solver="sweep"):
     torch = cuda_or_skip()
     from paper_1802_03773_gb300 import Context
     dtype = np.float64 if precision == "fp64" else np.float32
     inst, vals, b = batch(cols, rpc, w, dtype, seed)
     ctx = Context(0, precision=precision)
-    ctx.plan_banded(cols, rows_per_col=rpc, window=w)
+    ctx.plan_banded(cols, rows_per_col=rpc, window=w, solver=SOLVER[solver])
     tJ = torch.from_numpy(np.ascontiguousarray(vals.reshape(-1))).cuda()
     tb = torch.from_numpy(b).cuda()
     tD = None if D is None else torch.from_numpy(D.astype(dtype)).cuda()
@@ -33,11 +36,11 @@ def run(cols, rpc, w, precision, lam, refine_steps=1, D=None, seed=0):
     p = torch.empty(N, device="cuda", dtype=ctx.dtype)
     ctx.factor_solve(tJ, tb, p, None, D=tD, lam=lam, refine_steps=refine_steps)
     ctx.sync_status()
-    Rw = torch.empty(N * w, device="cuda", dtype=ctx.dtype)
+    Rw = torch.empty(N * w, device="cuda", dtype=ctx.dtype) if solver == "sweep" else None
     res2 = np.zeros(len(cols))
     ctx.get_band_factor(Rw, None, res2)
-    out = dict(p=p.cpu().numpy().astype(np.float64), Rw=Rw.cpu().numpy().astype(np.float64).reshape(N, w),
-               res2=res2, inst=inst)
+    out = dict(p=p.cpu().numpy().astype(np.float64), res2=res2, inst=inst,
+               Rw=None if Rw is None else Rw.cpu().numpy().astype(np.float64).reshape(N, w))
     ctx.close()
     return out
 
@@ -68,31 +71,43 @@ def test_banded_fp64_matches_oracle(cols, rpc, w):
     np.testing.assert_allclose(out["res2"], r2, rtol=1e-9)
 
 
-def test_banded_fp32_refined_matches_oracle():
+@pytest.mark.parametrize("cols,rpc,w", [([1, 7, 8, 9, 50, 333], 4, 8), ([40, 3, 17], 2, 3),
+                                        ([64] * 9, 1, 5), ([1000], 4, 8)])
+def test_banded_parallel_fp64_matches_oracle(cols, rpc, w):
+    out = run(cols, rpc, w, "fp64", lam=1e-3, solver="parallel")
+    x, _, r2 = oracle_solutions(out["inst"], 1e-3)
+    np.testing.assert_allclose(out["p"], x, rtol=1e-12, atol=1e-12 * np.abs(x).max())
+    np.testing.assert_allclose(out["res2"], r2, rtol=1e-9)
+
+
+@pytest.mark.parametrize("solver", ["sweep", "parallel"])
+def test_banded_fp32_refined_matches_oracle(solver):
     cols = [500, 1200, 77]
-    out = run(cols, 4, 8, "fp32_refined", lam=1e-3, refine_steps=2)
+    out = run(cols, 4, 8, "fp32_refined", lam=1e-3, refine_steps=2, solver=solver)
     x, _, _ = oracle_solutions(out["inst"], 1e-3)
     assert np.linalg.norm(out["p"] - x) / np.linalg.norm(x) <= 1e-5
 
 
-def test_banded_given_D_and_no_damping():
+@pytest.mark.parametrize("solver", ["sweep", "parallel"])
+def test_banded_given_D_and_no_damping(solver):
     cols = [30, 41]
     g = np.random.default_rng(3)
     D = np.abs(g.standard_normal(sum(cols))) + 0.5
-    out = run(cols, 4, 8, "fp64", lam=0.2, D=D)
+    out = run(cols, 4, 8, "fp64", lam=0.2, D=D, solver=solver)
     x, _, _ = oracle_solutions(out["inst"], 0.2, D)
     np.testing.assert_allclose(out["p"], x, rtol=1e-11, atol=1e-12)
-    out0 = run(cols, 4, 8, "fp64", lam=0.0)
+    out0 = run(cols, 4, 8, "fp64", lam=0.0, solver=solver)
     x0, _, _ = oracle_solutions(out0["inst"], 0.0, np.ones(sum(cols)))
     np.testing.assert_allclose(out0["p"], x0, rtol=1e-10, atol=1e-11)
 
 
-def test_banded_batch_scaled_sampled():
+@pytest.mark.parametrize("solver", ["sweep", "parallel"])
+def test_banded_batch_scaled_sampled(solver):
     """A batch of 256 instances with n ~ U{1000..4000}: every instance's solution satisfies the
     optimality identity; 4 sampled instances match the oracle."""
     g = np.random.default_rng(1)
     cols = g.integers(1000, 4001, size=256)
-    out = run(list(cols), 4, 8, "fp32_refined", lam=1e-3, refine_steps=2)
+    out = run(list(cols), 4, 8, "fp32_refined", lam=1e-3, refine_steps=2, solver=solver)
     off = 0
     worst = 0.0
     for k, d in enumerate(out["inst"]):
@@ -112,3 +127,24 @@ def test_banded_batch_scaled_sampled():
         x, *_ = bd.damped_solve(d["start"], d["vals"], d["b"], d["n"], 1e-3)
         got = out["p"][off[k]:off[k + 1]]
         assert np.linalg.norm(got - x) / np.linalg.norm(x) <= 1e-5
+
+
+def test_banded_parallel_large_instance():
+    """One instance of 100,000 columns (400,000 rows): matches the oracle to 1e-5."""
+    out = run([100000], 4, 8, "fp32_refined", lam=1e-3, refine_steps=2, solver="parallel", seed=9)
+    x, _, _ = oracle_solutions(out["inst"], 1e-3)
+    assert np.linalg.norm(out["p"] - x) / np.linalg.norm(x) <= 1e-5
+
+
+@pytest.mark.slow
+def test_banded_parallel_full_size_optimality():
+    """n = 1,000,000 columns, 4,000,000 rows, lambda = 1e-3: the first-order condition
+    J^T (b - J x) = lambda D^2 x holds to float accuracy after refinement."""
+    out = run([1000000], 4, 8, "fp32_refined", lam=1e-3, refine_steps=2, solver="parallel", seed=4)
+    d = out["inst"][0]
+    x = out["p"]
+    start, vals = d["start"], d["vals"].astype(np.float64)
+    D = bd.column_norms(start, vals, d["n"])
+    r = d["b"].astype(np.float64) - bd.matvec(start, vals, x)
+    gr = bd.rmatvec(start, vals, r, d["n"]) - 1e-3 * D * D * x
+    assert np.linalg.norm(gr) / (np.linalg.norm(vals) ** 2 * np.linalg.norm(x)) < 1e-7
