@@ -180,6 +180,17 @@ qrkit_status qrkit_solve_r(qrkit_ctx* ctx, const void* qtb, void* p);
  * QRKIT_FP32, allowed but not useful for QRKIT_FP64). */
 qrkit_status qrkit_solve(qrkit_ctx* ctx, const void* b, void* p, int refine_steps);
 
+/* Comparison path (Sec. 1, Sec. 6.1 "QRkit+Chol"): p from the normal equations Eq. (1),
+ * (J^T J + lambda D^2) p = J^T b, by Cholesky in the context's precision (float for both float
+ * modes; no refinement), for a QRKIT_STRUCT_BLOCKS plan of any coupling.  The block unknowns
+ * are eliminated first (Schur complement onto the shared block, banded per segment for
+ * windows, dense for a dense S with s <= 64).  Its error grows with cond(A)^2, the QR path's
+ * with cond(A).  J, S, b, D, lambda, p as for qrkit_factor / qrkit_solve (D NULL: column
+ * norms, zero -> 1).  A non-positive pivot is reported as QRKIT_ESINGULAR in the device
+ * status word.  Asynchronous. */
+qrkit_status qrkit_normal_solve(qrkit_ctx* ctx, const void* J, const void* S, const void* b, const void* D,
+                                double lambda, void* p);
+
 /* Size of the device array behind qrkit_block_solve_noalloc (16 MiB per device). */
 #define QRKIT_NOALLOC_SCRATCH_BYTES (16u << 20)
 

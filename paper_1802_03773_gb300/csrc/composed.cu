@@ -540,6 +540,26 @@ static FactorOut<T> fout(qrkit_ctx* ctx) {
     QRKIT_CUDA_TRY(ctx, cudaGetLastError());              \
   } while (0)
 
+// D = column norms of J (Sec. 5.2), zero -> 1, in double; C.sq is the scratch.
+template <typename T>
+static qrkit_status norms_typed(qrkit_ctx* ctx, const ComposedView<T>& V, double* D) {
+  Plan& P = ctx->plan;
+  Composed& C = ctx->comp;
+  cudaStream_t st = ctx->stream;
+  const int64_t N = P.cols + P.s.shared_cols;
+  qrkit_status rc;
+  if ((rc = ensure(ctx, C.sq, (size_t)N * sizeof(double), "column sums")) != QRKIT_OK) return rc;
+  double* sq = (double*)C.sq.ptr;
+  QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(sq, 0, (size_t)N * sizeof(double), st));
+  LAUNCH(ctx, colnorm_blocks_kernel<T><<<blocks_for(P.K, 128), 128, 0, st>>>(V, sq));
+  if (V.coupled == QRKIT_COUPLED_DENSE)
+    LAUNCH(ctx, colnorm_dense_kernel<T><<<blocks_for((int64_t)V.s * 32, 256), 256, 0, st>>>(V, sq));
+  else if (V.coupled == QRKIT_COUPLED_WINDOW)
+    LAUNCH(ctx, colnorm_window_kernel<T><<<blocks_for(P.K, 128), 128, 0, st>>>(V, sq));
+  LAUNCH(ctx, finalize_norms_kernel<<<blocks_for(N, 256), 256, 0, st>>>(sq, D, N));
+  return QRKIT_OK;
+}
+
 template <typename T>
 static qrkit_status factor_typed(qrkit_ctx* ctx, const void* J, const void* S, const void* Dext,
                                  double lambda, bool dext_double = false) {
@@ -564,15 +584,8 @@ static qrkit_status factor_typed(qrkit_ctx* ctx, const void* J, const void* S, c
       rc = widen_to_double(ctx, (const float*)Dext, (double*)C.D.ptr, N);
       if (rc != QRKIT_OK) return rc;
     }
-  } else {
-    double* sq = (double*)C.sq.ptr;
-    QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(sq, 0, (size_t)N * sizeof(double), st));
-    LAUNCH(ctx, colnorm_blocks_kernel<T><<<blocks_for(P.K, 128), 128, 0, st>>>(V, sq));
-    if (V.coupled == QRKIT_COUPLED_DENSE)
-      LAUNCH(ctx, colnorm_dense_kernel<T><<<blocks_for((int64_t)V.s * 32, 256), 256, 0, st>>>(V, sq));
-    else if (V.coupled == QRKIT_COUPLED_WINDOW)
-      LAUNCH(ctx, colnorm_window_kernel<T><<<blocks_for(P.K, 128), 128, 0, st>>>(V, sq));
-    LAUNCH(ctx, finalize_norms_kernel<<<blocks_for(N, 256), 256, 0, st>>>(sq, (double*)C.D.ptr, N));
+  } else if ((rc = norms_typed<T>(ctx, V, (double*)C.D.ptr)) != QRKIT_OK) {
+    return rc;
   }
   FactorOut<T> O = fout<T>(ctx);
   LAUNCH(ctx, block_factor_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O));
@@ -709,6 +722,18 @@ qrkit_status composed_factor(qrkit_ctx* ctx, const void* J, const void* S, const
   return factor_typed<float>(ctx, J, S, D, lambda);
 }
 
+template <typename T>
+ComposedView<T> composed_view(qrkit_ctx* ctx, const void* J, const void* S) {
+  return view<T>(ctx, J, S);
+}
+template ComposedView<float> composed_view<float>(qrkit_ctx*, const void*, const void*);
+template ComposedView<double> composed_view<double>(qrkit_ctx*, const void*, const void*);
+
+qrkit_status composed_column_norms(qrkit_ctx* ctx, const void* J, const void* S, double* D) {
+  if (ctx->precision == QRKIT_FP64) return norms_typed<double>(ctx, view<double>(ctx, J, S), D);
+  return norms_typed<float>(ctx, view<float>(ctx, J, S), D);
+}
+
 qrkit_status composed_factor_scaled(qrkit_ctx* ctx, const void* J, const void* S, const double* E) {
   if (ctx->precision == QRKIT_FP64) return factor_typed<double>(ctx, J, S, E, 1.0, true);
   return factor_typed<float>(ctx, J, S, E, 1.0, true);
@@ -752,6 +777,8 @@ void release_composed(Composed& C) {
   release(C.sort_tab); release(C.hist); release(C.spos); release(C.order); release(C.Xw_s);
   release(C.Xstart_s); release(C.rhs_s); release(C.seg_inst);
   release_cr(C.cr);
+  release(C.nrm_D); release(C.nrm_L); release(C.nrm_W); release(C.nrm_y); release(C.nrm_As);
+  release(C.nrm_rs); release(C.nrm_seg);
   release(C.d_aug_off_d); release(C.d_aug_off_u); release(C.d_red_off_d); release(C.d_red_off_u);
   for (auto& L : C.levels) { release(L.X); release(L.tau); release(L.rhs); }
   C = Composed();

@@ -142,6 +142,8 @@ struct Composed {
   DevBuf sort_tab, hist, spos, order, Xw_s, Xstart_s, rhs_s;
   DevBuf seg_inst;                 // 4 x nseg: cols, col0, row0, rows of the segments' banded solves
   CRPlan* cr = nullptr;            // parallel banded QR of the segments (window <= 8)
+  // normal-equations (Cholesky) comparison path
+  DevBuf nrm_D, nrm_L, nrm_W, nrm_y, nrm_As, nrm_rs, nrm_seg;
   DevBuf d_aug_off_d, d_aug_off_u, d_red_off_d, d_red_off_u;
   std::vector<TsqrLevel> levels;
   const void* J = nullptr;         // caller's values recorded at factor time
@@ -210,6 +212,9 @@ qrkit_status composed_factor(qrkit_ctx* ctx, const void* J, const void* S, const
 // Composed factor with the damping diagonal given directly as E = lambda^(1/2) D (double,
 // N entries) and lambda = 1: per-column damping, e.g. one lambda per independent problem.
 qrkit_status composed_factor_scaled(qrkit_ctx* ctx, const void* J, const void* S, const double* E);
+// D = column norms of the block structure's J (zero -> 1), N doubles.
+qrkit_status composed_column_norms(qrkit_ctx* ctx, const void* J, const void* S, double* D);
+template <typename T> ComposedView<T> composed_view(qrkit_ctx* ctx, const void* J, const void* S);
 qrkit_status composed_solve(qrkit_ctx* ctx, const void* J, const void* S, const void* b, void* p,
                             int refine_steps);
 qrkit_status composed_apply_qt(qrkit_ctx* ctx, const void* b, void* qtb);

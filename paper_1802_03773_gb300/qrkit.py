@@ -93,6 +93,7 @@ _SIGS = {
     "qrkit_apply_qt": (ctypes.c_int, [_VP, _VP, _VP]),
     "qrkit_solve_r": (ctypes.c_int, [_VP, _VP, _VP]),
     "qrkit_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
+    "qrkit_normal_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double, _VP]),
     "qrkit_set_window_start": (ctypes.c_int, [_VP, _VP]),
     "qrkit_get_row_order": (ctypes.c_int, [_VP, _VP]),
     "qrkit_lm_plan": (ctypes.c_int, [_VP, ctypes.POINTER(LMProblem)]),
@@ -276,6 +277,11 @@ class Context:
 
     def solve(self, b, p, refine_steps=1):
         self._check(self.lib.qrkit_solve(self.h, self._t(b, "b"), self._t(p, "p"), int(refine_steps)))
+
+    def normal_solve(self, J, S, b, p, D=None, lam=0.0):
+        """Normal equations by Cholesky (comparison path; no refinement)."""
+        self._check(self.lib.qrkit_normal_solve(self.h, self._t(J, "J"), self._t(S, "S", True), self._t(b, "b"),
+                                                self._t(D, "D", True), float(lam), self._t(p, "p")))
 
     def get_factor(self, factor=None, tau=None):
         self._check(self.lib.qrkit_get_factor(self.h, self._t(factor, "factor", True),
