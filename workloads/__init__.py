@@ -14,5 +14,6 @@ from .gen import (  # noqa: F401
     curvefit_problem,
     banded_problem,
     banded_batch_shapes,
+    mlp_init,
     rng_for,
 )

@@ -12,6 +12,7 @@ latent-variable fits, Sec. 4.2 / Sec. 6.2, and banded matrices, Sec. 4.4):
                        points plus N(0, sigma^2) noise, and a perturbed start.
   banded_problem       J of (rows_per_col * n) x n, row i touches columns
                        floor(i / rows_per_col) .. + w - 1 (truncated at n - 1), N(0,1).
+  mlp_init             initial weights of the damping-policy MLP (He-normal, zero biases).
 """
 from __future__ import annotations
 
@@ -114,3 +115,14 @@ def banded_batch_shapes(count=4096, n_lo=1000, n_hi=100_000, seed_offset=0):
     """Column counts of a batch of independent banded instances, n ~ U{n_lo..n_hi}."""
     g = rng_for(5, seed_offset)
     return g.integers(n_lo, n_hi + 1, size=count).astype(np.int64)
+
+
+def mlp_init(seed_offset=0, F=16, H=64, C=8):
+    """Initial parameters of the damping-policy MLP (flat float32 vector, He-normal weights,
+    zero biases), [W1 (H x F) | b1 | W2 (H x H) | b2 | W3 (C x H) | b3]."""
+    g = rng_for(6, seed_offset)
+    W1 = g.standard_normal((H, F)) * np.sqrt(2.0 / F)
+    W2 = g.standard_normal((H, H)) * np.sqrt(2.0 / H)
+    W3 = g.standard_normal((C, H)) * np.sqrt(1.0 / H)
+    parts = [W1.reshape(-1), np.zeros(H), W2.reshape(-1), np.zeros(H), W3.reshape(-1), np.zeros(C)]
+    return np.concatenate(parts).astype(np.float32)
