@@ -306,6 +306,49 @@ qrkit_status qrkit_lm_step(qrkit_ctx* ctx, double* x, qrkit_lm_state* states, in
 qrkit_status qrkit_lm_run(qrkit_ctx* ctx, double* x, qrkit_lm_state* states, int max_iter, double ftol,
                           int refine_steps, int use_graph);
 
+/* Residual of the planned LM model at x: f (DEVICE, 2 sum P_k doubles) = curve(t_i) - data_i
+ * per point, (x, y) pairs.  Asynchronous. */
+qrkit_status qrkit_lm_residual(qrkit_ctx* ctx, const double* x, double* f);
+
+/* ---- Learned damping (not in the paper; Nielsen's rule stays the fallback) ----
+ * A 3-layer MLP, QRKIT_MLP_FEATURES -> 64 -> 64 -> QRKIT_MLP_CLASSES (ReLU), whose classes are
+ * lambda multipliers {1e-2, 1e-1, 1/3, 1/2, 1, 2, 4, 10}.  With the policy on, an LM step that
+ * is accepted sets lambda_next = lambda * multiplier[argmax]; a rejected step uses Nielsen's
+ * rule (lambda *= nu, nu *= 2).  Features of problem k after each step (float32, in order):
+ * log10(lambda) / 4, log10(iteration + 1) / 2, gain ratios of the last 4 steps (clamped to
+ * [-1, 2], newest first), their acceptance flags (0/1), log10(cost_new / cost) of the last 4
+ * steps clamped to [-8, 1] / 8, log10(pred / cost) clamped to [-16, 0] / 16, and 1.
+ * Parameters: QRKIT_MLP_PARAMS float32 values [W1 (64 x 16) | b1 | W2 (64 x 64) | b2 |
+ * W3 (8 x 64) | b3], row-major; the forward and backward passes use the weight matrices
+ * rounded to bfloat16 (round to nearest even) with float32 accumulation; Adam (beta1 0.9,
+ * beta2 0.999, eps 1e-8) updates the float32 copy.  The MLP belongs to the context. */
+#define QRKIT_MLP_FEATURES 16
+#define QRKIT_MLP_CLASSES 8
+#define QRKIT_MLP_PARAMS 5768
+
+/* Set the MLP parameters (HOST, QRKIT_MLP_PARAMS floats) and reset Adam.  Synchronous. */
+qrkit_status qrkit_mlp_init(qrkit_ctx* ctx, const float* params);
+
+/* Copy the current float32 parameters to HOST memory.  Synchronous. */
+qrkit_status qrkit_mlp_params(qrkit_ctx* ctx, float* params);
+
+/* logits (DEVICE, n x QRKIT_MLP_CLASSES) of the samples X (DEVICE, n x QRKIT_MLP_FEATURES). */
+qrkit_status qrkit_mlp_forward(qrkit_ctx* ctx, const float* X, int64_t n, float* logits);
+
+/* One training step on a batch: mean softmax cross-entropy of X (DEVICE, n x FEATURES) against
+ * labels (DEVICE int32, n, in [0, CLASSES)), its gradient, and (lr > 0) an Adam update.
+ * loss (HOST, may be NULL; synchronous when given), grad (DEVICE, QRKIT_MLP_PARAMS, may be
+ * NULL): the loss and gradient at the parameters before the update. */
+qrkit_status qrkit_mlp_train_step(qrkit_ctx* ctx, const float* X, const int32_t* labels, int64_t n, float lr,
+                                  float* loss, float* grad);
+
+/* Damping of the planned LM model: 0 = Nielsen's rule, 1 = the context's MLP after accepted
+ * steps (Nielsen after rejected ones). */
+qrkit_status qrkit_lm_set_policy(qrkit_ctx* ctx, int use_mlp);
+
+/* Features of every problem after the last LM step (DEVICE, B x QRKIT_MLP_FEATURES floats). */
+qrkit_status qrkit_lm_features(qrkit_ctx* ctx, float* features);
+
 /* Block until the stream is idle and return the device status word (QRKIT_OK if no kernel
  * reported a failure), then clear it. */
 qrkit_status qrkit_sync_status(qrkit_ctx* ctx);

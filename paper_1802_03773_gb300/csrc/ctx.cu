@@ -265,6 +265,7 @@ void qrkit_destroy(qrkit_ctx* ctx) {
   if (ctx->stream) cudaStreamSynchronize(ctx->stream);
   else cudaDeviceSynchronize();
   release_lm(ctx->lm);
+  release_mlp(ctx->mlp);
   release_plan(ctx->plan);
   release_composed(ctx->comp);
   release_band(ctx->band);

@@ -161,6 +161,13 @@ qrkit_status cr_solve(qrkit_ctx* ctx, CRPlan& C, const int64_t* starts, int rpc,
 // dx = R^{-1} R^{-T} g with the factor of the last cr_solve (g double, dx by global column).
 qrkit_status cr_normal_solve(qrkit_ctx* ctx, CRPlan& C, const double* g, void* dx);
 
+// Damping-policy MLP parameters and training state (mlp.cu)
+struct Mlp {
+  DevBuf theta, wbf, m, v, grad, partial, loss_part, loss;
+  int64_t step = 0;
+};
+void release_mlp(Mlp*& m);
+
 struct LM;   // Levenberg-Marquardt state of a planned model (lm.cu)
 void release_lm(LM*& lm);
 
@@ -183,6 +190,7 @@ struct qrkit_ctx {
   qrkit::Composed comp;
   qrkit::Band band;
   qrkit::LM* lm = nullptr;    // LM model plan and buffers (qrkit_lm_plan)
+  qrkit::Mlp* mlp = nullptr;  // damping-policy MLP (qrkit_mlp_init)
   int* d_status = nullptr;   // device status word
   int64_t launches = 0;
   size_t smem_attr[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // dynamic smem opted in, per kernel variant

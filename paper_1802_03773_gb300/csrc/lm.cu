@@ -30,6 +30,7 @@
 #include <vector>
 
 #include "internal.h"
+#include "mlp_policy.cuh"
 
 namespace qrkit {
 
@@ -51,6 +52,8 @@ struct LM {
   DevBuf tabs, tile_prob, col_prob;
   const double* data = nullptr;        // caller's points (device)
   DevBuf J, S, b, p, start, d2, E, xnew, tile_cost, tile_new, tile_pred, state, ndone;
+  DevBuf hist, feat;                   // per problem: step history (12) and policy features (16)
+  bool policy = false;                 // damping from the MLP after accepted steps
   bool prepared = false;
   cudaGraphExec_t graph = nullptr;
   int graph_refine = -1;
@@ -64,7 +67,7 @@ void release_lm(LM*& lm) {
   if (lm->graph) cudaGraphExecDestroy(lm->graph);
   for (DevBuf* b : {&lm->tabs, &lm->tile_prob, &lm->col_prob, &lm->J, &lm->S, &lm->b, &lm->p, &lm->start,
                     &lm->d2, &lm->E, &lm->xnew, &lm->tile_cost, &lm->tile_new, &lm->tile_pred, &lm->state,
-                    &lm->ndone})
+                    &lm->ndone, &lm->hist, &lm->feat})
     release(*b);
   delete lm;
   lm = nullptr;
@@ -173,6 +176,28 @@ __global__ void lm_damp_kernel(LMTables t, const double* d2, const qrkit_lm_stat
   E[j] = sqrt(st[t.col_prob[j]].lambda) * d;
 }
 
+// f = curve(t) - data per point (two values), double.
+__global__ void cf_residual_kernel(LMTables t, const double* x, const double* data, double* f) {
+  const int64_t tile = blockIdx.x;
+  const int64_t i = t.tile_p0[tile] + threadIdx.x;
+  if (i >= t.tile_p0[tile + 1]) return;
+  const int k = t.tile_prob[tile];
+  const int64_t Kc = (t.c0[k + 1] - t.c0[k]) / 2;
+  const double ti = x[i];
+  const int64_t seg = segment_of(ti, Kc);
+  double Bv[4], dB[4];
+  bspline(ti - (double)seg, Bv, dB);
+  const double* P = x + t.NP + t.c0[k] + 2 * seg;
+  double cx = 0, cy = 0;
+#pragma unroll
+  for (int q = 0; q < 4; ++q) {
+    cx += Bv[q] * P[2 * q];
+    cy += Bv[q] * P[2 * q + 1];
+  }
+  f[2 * i] = cx - data[2 * i];
+  f[2 * i + 1] = cy - data[2 * i + 1];
+}
+
 template <typename T>
 __global__ void lm_xnew_kernel(int64_t N, const double* x, const T* p, double* xnew) {
   const int64_t j = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -225,11 +250,17 @@ cf_trial_kernel(LMTables t, const double* xnew, const double* data, const T* J, 
   }
 }
 
-// One warp per problem: costs, predicted decrease, gain ratio, Nielsen update, stop rule.
+constexpr int kHist = 12;   // rho, accepted, log cost ratio of the last 4 steps
+
+__device__ __forceinline__ float clampf(float v, float lo, float hi) { return fminf(fmaxf(v, lo), hi); }
+
+// One warp per problem: costs, predicted decrease, gain ratio, then the damping update:
+// Nielsen's rule, or after an accepted step (when the policy is on) lambda * multiplier of the
+// MLP's class for the features of the step history; stop rule.
 template <typename T>
 __global__ void lm_update_kernel(LMTables t, const double* tile_cost, const double* tile_new,
                                  const double* tile_pred, const double* E, const T* p, qrkit_lm_state* st,
-                                 double ftol, int* ndone) {
+                                 double ftol, int* ndone, MlpDev w, float* hist, float* feat) {
   const int64_t k = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (k >= t.B) return;
@@ -249,23 +280,58 @@ __global__ void lm_update_kernel(LMTables t, const double* tile_cost, const doub
     cn += __shfl_xor_sync(0xffffffffu, cn, d);
     pr += __shfl_xor_sync(0xffffffffu, pr, d);
   }
-  if (lane != 0) return;
   qrkit_lm_state s = st[k];
   if (s.done) {
-    s.accepted = 0;
-    st[k] = s;
-    atomicAdd(ndone, 1);
+    if (lane == 0) {
+      s.accepted = 0;
+      st[k] = s;
+      atomicAdd(ndone, 1);
+    }
     return;
   }
   const double cost = 0.5 * c, cost_new = 0.5 * cn, pred = 0.5 * pr;
   const double rho = pred > 0.0 ? (cost - cost_new) / pred : -1.0;
+  const bool acc = rho > 0.0;
+  // step history and features (every lane computes the same values)
+  float* hk = hist + k * kHist;
+  float h[kHist];
+#pragma unroll
+  for (int q = 0; q < kHist; ++q) h[q] = s.iteration == 0 ? 0.f : hk[q];
+  const float ratio = cost > 0.0 ? (float)log10(fmax(cost_new / cost, 1e-30)) : 0.f;
+  const float pratio = cost > 0.0 ? (float)log10(fmax(pred / cost, 1e-30)) : -16.f;
+#pragma unroll
+  for (int q = 3; q >= 1; --q) {
+    h[q] = h[q - 1];
+    h[4 + q] = h[4 + q - 1];
+    h[8 + q] = h[8 + q - 1];
+  }
+  h[0] = clampf((float)rho, -1.f, 2.f);
+  h[4] = acc ? 1.f : 0.f;
+  h[8] = clampf(ratio, -8.f, 1.f) / 8.f;
+  float f[kMlpF];
+  f[0] = (float)log10(s.lambda) / 4.f;
+  f[1] = (float)log10((double)(s.iteration + 1)) / 2.f;
+#pragma unroll
+  for (int q = 0; q < kHist; ++q) f[2 + q] = h[q];
+  f[14] = clampf(pratio, -16.f, 0.f) / 16.f;
+  f[15] = 1.f;
+  __syncwarp();
+  if (lane < kHist) hk[lane] = h[lane];
+  if (lane < kMlpF) feat[k * kMlpF + lane] = f[lane];
+  int cls = -1;
+  if (acc && w.theta) cls = mlp_policy_warp(w, f, lane);
+  if (lane != 0) return;
   s.cost = cost;
   s.cost_new = cost_new;
   s.pred = pred;
   s.rho = rho;
-  if (rho > 0.0) {
-    const double a = 2.0 * rho - 1.0;
-    s.lambda *= fmax(1.0 / 3.0, 1.0 - a * a * a);
+  if (acc) {
+    if (cls >= 0) {
+      s.lambda *= mlp_multiplier(cls);
+    } else {
+      const double a = 2.0 * rho - 1.0;
+      s.lambda *= fmax(1.0 / 3.0, 1.0 - a * a * a);
+    }
     s.nu = 2.0;
     s.accepted = 1;
     if (ftol >= 0.0 && cost - cost_new <= ftol * cost) s.done = 1;
@@ -275,6 +341,7 @@ __global__ void lm_update_kernel(LMTables t, const double* tile_cost, const doub
     s.accepted = 0;
   }
   if (s.lambda > 1e16) s.done = 1;
+  if (s.lambda < 1e-30) s.lambda = 1e-30;
   s.iteration += 1;
   st[k] = s;
   if (s.done) atomicAdd(ndone, 1);
@@ -322,9 +389,15 @@ qrkit_status lm_iteration(qrkit_ctx* ctx, double* x, int refine_steps, double ft
   LM_LAUNCH(ctx, cf_trial_kernel<T><<<(unsigned)t.num_tiles, kTilePts, 0, st>>>(
                      t, xn, L.data, J, Sv, b, p, E, (const int32_t*)L.start.ptr, (double*)L.tile_new.ptr,
                      (double*)L.tile_pred.ptr));
+  MlpDev w{};
+  if (L.policy && ctx->mlp) {
+    w.theta = (const float*)ctx->mlp->theta.ptr;
+    w.wbf = (const __nv_bfloat16*)ctx->mlp->wbf.ptr;
+  }
   LM_LAUNCH(ctx, lm_update_kernel<T><<<nblk(t.B * 32, 128), 128, 0, st>>>(
                      t, (const double*)L.tile_cost.ptr, (const double*)L.tile_new.ptr,
-                     (const double*)L.tile_pred.ptr, E, p, S, ftol, (int*)L.ndone.ptr));
+                     (const double*)L.tile_pred.ptr, E, p, S, ftol, (int*)L.ndone.ptr, w, (float*)L.hist.ptr,
+                     (float*)L.feat.ptr));
   LM_LAUNCH(ctx, lm_accept_kernel<<<nblk(t.N, 256), 256, 0, st>>>(t, xn, x, S));
   return QRKIT_OK;
 }
@@ -478,6 +551,45 @@ qrkit_status qrkit_lm_plan(qrkit_ctx* ctx, const qrkit_lm_problem* pr) {
     if ((rc = ensure(ctx, *d, (size_t)nt * sizeof(double), "LM partial sums")) != QRKIT_OK) return rc;
   if ((rc = ensure(ctx, L.state, (size_t)B * sizeof(qrkit_lm_state), "LM state")) != QRKIT_OK) return rc;
   if ((rc = ensure(ctx, L.ndone, sizeof(int), "LM done count")) != QRKIT_OK) return rc;
+  if ((rc = ensure(ctx, L.hist, (size_t)B * kHist * sizeof(float), "LM history")) != QRKIT_OK) return rc;
+  if ((rc = ensure(ctx, L.feat, (size_t)B * kMlpF * sizeof(float), "LM features")) != QRKIT_OK) return rc;
+  QRKIT_CUDA_TRY(ctx, cudaMemset(L.hist.ptr, 0, (size_t)B * kHist * sizeof(float)));
+  QRKIT_CUDA_TRY(ctx, cudaMemset(L.feat.ptr, 0, (size_t)B * kMlpF * sizeof(float)));
+  return QRKIT_OK;
+}
+
+qrkit_status qrkit_lm_residual(qrkit_ctx* ctx, const double* x, double* f) {
+  if (!ctx) return QRKIT_EINVAL;
+  if (!ctx->lm) return fail(ctx, QRKIT_ESTATE, "no LM model planned (qrkit_lm_plan)");
+  if (!x || !f) return fail(ctx, QRKIT_EINVAL, "x and f are required");
+  QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  LM& L = *ctx->lm;
+  cf_residual_kernel<<<(unsigned)L.t.num_tiles, kTilePts, 0, ctx->stream>>>(L.t, x, L.data, f);
+  ctx->launches += 1;
+  QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+  return QRKIT_OK;
+}
+
+qrkit_status qrkit_lm_set_policy(qrkit_ctx* ctx, int use_mlp) {
+  if (!ctx) return QRKIT_EINVAL;
+  if (!ctx->lm) return fail(ctx, QRKIT_ESTATE, "no LM model planned (qrkit_lm_plan)");
+  if (use_mlp && !ctx->mlp) return fail(ctx, QRKIT_ESTATE, "no MLP (qrkit_mlp_init)");
+  LM& L = *ctx->lm;
+  if (L.policy != (use_mlp != 0) && L.graph) {
+    cudaGraphExecDestroy(L.graph);
+    L.graph = nullptr;
+  }
+  L.policy = use_mlp != 0;
+  return QRKIT_OK;
+}
+
+qrkit_status qrkit_lm_features(qrkit_ctx* ctx, float* features) {
+  if (!ctx) return QRKIT_EINVAL;
+  if (!ctx->lm) return fail(ctx, QRKIT_ESTATE, "no LM model planned (qrkit_lm_plan)");
+  if (!features) return fail(ctx, QRKIT_EINVAL, "features is required");
+  LM& L = *ctx->lm;
+  QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(features, L.feat.ptr, (size_t)L.t.B * kMlpF * sizeof(float),
+                                      cudaMemcpyDeviceToDevice, ctx->stream));
   return QRKIT_OK;
 }
 

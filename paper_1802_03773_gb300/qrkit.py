@@ -78,6 +78,8 @@ class LMState(ctypes.Structure):
 
 
 MODEL_CURVEFIT = 0
+MLP_FEATURES, MLP_CLASSES, MLP_PARAMS = 16, 8, 5768
+MLP_MULTIPLIERS = (1e-2, 1e-1, 1.0 / 3.0, 0.5, 1.0, 2.0, 4.0, 10.0)
 
 _VP = ctypes.c_void_p
 _SIGS = {
@@ -99,6 +101,13 @@ _SIGS = {
     "qrkit_lm_plan": (ctypes.c_int, [_VP, ctypes.POINTER(LMProblem)]),
     "qrkit_lm_step": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int]),
     "qrkit_lm_run": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int, ctypes.c_double, ctypes.c_int, ctypes.c_int]),
+    "qrkit_mlp_init": (ctypes.c_int, [_VP, _VP]),
+    "qrkit_mlp_params": (ctypes.c_int, [_VP, _VP]),
+    "qrkit_mlp_forward": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP]),
+    "qrkit_mlp_train_step": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_float, _VP, _VP]),
+    "qrkit_lm_set_policy": (ctypes.c_int, [_VP, ctypes.c_int]),
+    "qrkit_lm_residual": (ctypes.c_int, [_VP, _VP, _VP]),
+    "qrkit_lm_features": (ctypes.c_int, [_VP, _VP]),
     "qrkit_sync_status": (ctypes.c_int, [_VP]),
     "qrkit_block_solve_noalloc": (ctypes.c_int, [ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int64, _VP,
                                                  _VP, _VP, _VP, _VP, ctypes.c_int]),
@@ -327,6 +336,49 @@ class Context:
         self._check(self.lib.qrkit_lm_run(self.h, self._lm_x(x), ctypes.cast(states, _VP), int(max_iter),
                                           float(ftol), int(refine_steps), 1 if use_graph else 0))
         return states
+
+    # ---- damping-policy MLP ----
+    def mlp_init(self, params):
+        p = np.ascontiguousarray(params, dtype=np.float32)
+        if p.shape != (MLP_PARAMS,):
+            raise ValueError(f"params: expected {MLP_PARAMS} float32 values")
+        self._check(self.lib.qrkit_mlp_init(self.h, p.ctypes.data))
+
+    def mlp_params(self):
+        out = np.empty(MLP_PARAMS, dtype=np.float32)
+        self._check(self.lib.qrkit_mlp_params(self.h, out.ctypes.data))
+        return out
+
+    def _f32(self, t, name, cols=None):
+        import torch
+        if t.device != self.device or t.dtype != torch.float32 or not t.is_contiguous():
+            raise ValueError(f"{name}: expected a contiguous float32 tensor on the context's device")
+        return _ptr(t)
+
+    def mlp_forward(self, X, logits):
+        self._check(self.lib.qrkit_mlp_forward(self.h, self._f32(X, "X"), int(X.shape[0]), self._f32(logits, "logits")))
+
+    def mlp_train_step(self, X, labels, lr, grad=None):
+        import torch
+        if labels.device != self.device or labels.dtype != torch.int32 or not labels.is_contiguous():
+            raise ValueError("labels: expected a contiguous int32 tensor on the context's device")
+        loss = ctypes.c_float(0.0)
+        self._check(self.lib.qrkit_mlp_train_step(self.h, self._f32(X, "X"), _ptr(labels), int(X.shape[0]),
+                                                  float(lr), ctypes.byref(loss),
+                                                  None if grad is None else self._f32(grad, "grad")))
+        return float(loss.value)
+
+    def lm_residual(self, x, f):
+        import torch
+        if f.device != self.device or f.dtype != torch.float64 or not f.is_contiguous():
+            raise ValueError("f: expected a contiguous float64 tensor on the context's device")
+        self._check(self.lib.qrkit_lm_residual(self.h, self._lm_x(x), _ptr(f)))
+
+    def lm_set_policy(self, use_mlp):
+        self._check(self.lib.qrkit_lm_set_policy(self.h, 1 if use_mlp else 0))
+
+    def lm_features(self, out):
+        self._check(self.lib.qrkit_lm_features(self.h, self._f32(out, "features")))
 
     def sync_status(self):
         self._check(self.lib.qrkit_sync_status(self.h))
