@@ -306,6 +306,13 @@ qrkit_status qrkit_lm_step(qrkit_ctx* ctx, double* x, qrkit_lm_state* states, in
 qrkit_status qrkit_lm_run(qrkit_ctx* ctx, double* x, qrkit_lm_state* states, int max_iter, double ftol,
                           int refine_steps, int use_graph);
 
+/* The linearised system of the planned LM model at x (DEVICE buffers, any may be NULL), in the
+ * layout of a QRKIT_COUPLED_WINDOW block structure with window 8: J (2 x 1 block per point,
+ * 2 sum P_k values), S (per point 2 x 8 column-major, 16 sum P_k values), b = -f (2 sum P_k),
+ * all in the context precision, and the window starts (int32, sum P_k; global shared column).
+ * Asynchronous. */
+qrkit_status qrkit_lm_linearize(qrkit_ctx* ctx, const double* x, void* J, void* S, void* b, int32_t* start);
+
 /* Residual of the planned LM model at x: f (DEVICE, 2 sum P_k doubles) = curve(t_i) - data_i
  * per point, (x, y) pairs.  Asynchronous. */
 qrkit_status qrkit_lm_residual(qrkit_ctx* ctx, const double* x, double* f);

@@ -558,6 +558,35 @@ qrkit_status qrkit_lm_plan(qrkit_ctx* ctx, const qrkit_lm_problem* pr) {
   return QRKIT_OK;
 }
 
+qrkit_status qrkit_lm_linearize(qrkit_ctx* ctx, const double* x, void* J, void* S, void* b, int32_t* start) {
+  if (!ctx) return QRKIT_EINVAL;
+  if (!ctx->lm) return fail(ctx, QRKIT_ESTATE, "no LM model planned (qrkit_lm_plan)");
+  if (!x) return fail(ctx, QRKIT_EINVAL, "x is required");
+  QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  LM& L = *ctx->lm;
+  const LMTables& t = L.t;
+  cudaStream_t st = ctx->stream;
+  double* d2 = (double*)L.d2.ptr;
+  QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(d2 + t.NP, 0, (size_t)t.s * sizeof(double), st));
+  if (ctx->precision == QRKIT_FP64)
+    cf_eval_kernel<double><<<(unsigned)t.num_tiles, kTilePts, 0, st>>>(
+        t, x, L.data, (double*)L.J.ptr, (double*)L.S.ptr, (double*)L.b.ptr, (int32_t*)L.start.ptr, d2,
+        (double*)L.tile_cost.ptr);
+  else
+    cf_eval_kernel<float><<<(unsigned)t.num_tiles, kTilePts, 0, st>>>(
+        t, x, L.data, (float*)L.J.ptr, (float*)L.S.ptr, (float*)L.b.ptr, (int32_t*)L.start.ptr, d2,
+        (double*)L.tile_cost.ptr);
+  ctx->launches += 1;
+  QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+  const size_t es = elem_size(ctx);
+  if (J) QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(J, L.J.ptr, (size_t)2 * t.NP * es, cudaMemcpyDeviceToDevice, st));
+  if (S) QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(S, L.S.ptr, (size_t)16 * t.NP * es, cudaMemcpyDeviceToDevice, st));
+  if (b) QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(b, L.b.ptr, (size_t)2 * t.NP * es, cudaMemcpyDeviceToDevice, st));
+  if (start)
+    QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(start, L.start.ptr, (size_t)t.NP * sizeof(int32_t), cudaMemcpyDeviceToDevice, st));
+  return QRKIT_OK;
+}
+
 qrkit_status qrkit_lm_residual(qrkit_ctx* ctx, const double* x, double* f) {
   if (!ctx) return QRKIT_EINVAL;
   if (!ctx->lm) return fail(ctx, QRKIT_ESTATE, "no LM model planned (qrkit_lm_plan)");

@@ -107,6 +107,7 @@ _SIGS = {
     "qrkit_mlp_train_step": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_int64, ctypes.c_float, _VP, _VP]),
     "qrkit_lm_set_policy": (ctypes.c_int, [_VP, ctypes.c_int]),
     "qrkit_lm_residual": (ctypes.c_int, [_VP, _VP, _VP]),
+    "qrkit_lm_linearize": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "qrkit_lm_features": (ctypes.c_int, [_VP, _VP]),
     "qrkit_sync_status": (ctypes.c_int, [_VP]),
     "qrkit_block_solve_noalloc": (ctypes.c_int, [ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int64, _VP,
@@ -373,6 +374,13 @@ class Context:
         if f.device != self.device or f.dtype != torch.float64 or not f.is_contiguous():
             raise ValueError("f: expected a contiguous float64 tensor on the context's device")
         self._check(self.lib.qrkit_lm_residual(self.h, self._lm_x(x), _ptr(f)))
+
+    def lm_linearize(self, x, J=None, S=None, b=None, start=None):
+        import torch
+        if start is not None and (start.device != self.device or start.dtype != torch.int32):
+            raise ValueError("start: expected an int32 tensor on the context's device")
+        self._check(self.lib.qrkit_lm_linearize(self.h, self._lm_x(x), self._t(J, "J", True), self._t(S, "S", True),
+                                                self._t(b, "b", True), _ptr(start)))
 
     def lm_set_policy(self, use_mlp):
         self._check(self.lib.qrkit_lm_set_policy(self.h, 1 if use_mlp else 0))
