@@ -163,7 +163,9 @@ qrkit_status qrkit_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, co
  *   lambda >= 0; the damping rows exist only when lambda > 0.
  * The factor (per-block reflectors and R, R12 = Q_i^T S_i top rows, the factor of the
  * reduced shared block) is kept in the context.  J and S are read again by qrkit_solve when
- * refine_steps > 0: keep them alive and unchanged until then.  Dense S: s <= 64. */
+ * refine_steps > 0: keep them alive and unchanged until then.  Dense S: s <= 64, or in the
+ * float modes s = 96 or 128 (the reduced block's tile QR then runs its trailing updates on
+ * the tensor cores, 3xTF32 with float accumulation). */
 qrkit_status qrkit_factor(qrkit_ctx* ctx, const void* J, const void* S, const void* D, double lambda);
 
 /* qtb = Q^T [b; 0] restricted to its top N entries (Sec. 5.1, matrixQ().transpose() * b),

@@ -606,6 +606,12 @@ static qrkit_status factor_typed(qrkit_ctx* ctx, const void* J, const void* S, c
       TsqrLevel& L = C.levels[l];
       T* Xn = l + 1 < C.levels.size() ? (T*)C.levels[l + 1].X.ptr : nullptr;
       const int64_t ldn = l + 1 < C.levels.size() ? C.levels[l + 1].M : 0;
+      if (sizeof(T) == sizeof(float) && tsqr_tc_supported(s, C.tile_rows)) {
+        // tensor-core trailing updates (3xTF32)
+        rc = tsqr_tile_tc(ctx, (float*)L.X.ptr, L.M, L.M, s, (float*)L.tau.ptr, (float*)Xn, ldn, L.tiles);
+        if (rc != QRKIT_OK) return rc;
+        continue;
+      }
       const size_t smem = ((size_t)C.tile_rows * s + 64) * sizeof(T);
       auto k = tsqr_tile_kernel<T>;
       QRKIT_CUDA_TRY(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -908,7 +914,9 @@ qrkit_status composed_layout(qrkit_ctx* ctx, size_t elem) {
     }
   }
   if (P.s.coupled_kind == QRKIT_COUPLED_DENSE) {
-    if (s > 64) return fail(ctx, QRKIT_EUNSUPPORTED, "dense shared block wider than 64 columns");
+    if (s > 64 && !(elem == sizeof(float) && tsqr_tc_supported(s, 256)))
+      return fail(ctx, QRKIT_EUNSUPPORTED,
+                  "dense shared block: s <= 64, or (float) s in {96, 128} for the tensor-core tiles");
     const int64_t M0 = C.red_rows + (C.damp ? s : 0);
     if (M0 < s) return fail(ctx, QRKIT_EINVAL, "reduced shared block has fewer rows than columns");
     C.tile_rows = 256;

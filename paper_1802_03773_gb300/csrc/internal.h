@@ -244,6 +244,10 @@ qrkit_status reduced_row_sort(qrkit_ctx* ctx, const RowSortTables& t, int64_t ns
                               const int64_t* Xstart, const void* Xw, int w, int* hist, int64_t* spos,
                               int64_t* order, int64_t* Xstart_s, void* Xw_s);
 qrkit_status window_start_copy(qrkit_ctx* ctx, const int32_t* in);
+// TSQR tile factor with tcgen05 trailing updates (float, 256-row tiles, 64 < s <= 128, s % 32 == 0).
+bool tsqr_tc_supported(int s, int tile_rows);
+qrkit_status tsqr_tile_tc(qrkit_ctx* ctx, float* X, int64_t ld, int64_t M, int s, float* taus, float* Xn,
+                          int64_t ldn, int64_t tiles);
 qrkit_status reduced_rhs_sort(qrkit_ctx* ctx, const int64_t* spos, const void* rhs, void* rhs_s, int64_t rows);
 void release_band(Band& B);
 qrkit_status launch_block_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,

@@ -1,0 +1,343 @@
+// TSQR tile factor of the dense reduced shared block with the trailing updates on the
+// 5th-generation tensor cores (float, s in {96, 128}, 256-row tiles).
+//
+// One CTA factors one 256 x s row tile held in shared memory by blocked Householder QR
+// (Sec. 2, compact WY): for each panel of 32 columns,
+//   1. the panel is factored column by column on the CUDA cores (reflectors H = I - tau v v^T,
+//      v[0] = 1, stored below the diagonal as in the unblocked kernel);
+//   2. T (32 x 32 upper) of Q_panel = H_0 .. H_31 = I - Y T Y^T is built forward from Y^T Y;
+//   3. W = Y^T C for the trailing columns C, then Z = T^T W (CUDA cores);
+//   4. C -= Y Z on the tensor cores: tcgen05.mma kind::tf32 with the 3xTF32 split
+//      (Y = Y_hi + Y_lo, Z = Z_hi + Z_lo, Y Z ~ Y_hi Z_hi + Y_hi Z_lo + Y_lo Z_hi), FP32
+//      accumulation in TMEM, M = 128 rows per half tile, K = 32, N = trailing columns; the
+//      product is read back with tcgen05.ld and subtracted in shared memory.
+// Operands are staged in shared memory in the canonical K-major no-swizzle layout (8-row x
+// 16-byte core matrices) and described by tcgen05 shared-memory descriptors.  The outputs
+// follow the unblocked tile kernel exactly (V below / R on and above the diagonal, tau per
+// column, the tile's R rows to the next TSQR level), so Q^T b and the solves are unchanged.
+#include <cuda_runtime.h>
+#include <math.h>
+#include <stdint.h>
+
+#include "internal.h"
+
+namespace qrkit {
+namespace {
+
+constexpr int kRows = 256;      // tile rows (two MMA halves of 128)
+constexpr int kNb = 32;         // panel width = MMA K
+constexpr int kThr = 256;
+constexpr int kMaxS = 128;
+constexpr int kTmemCols = 256;  // D of half h at columns [128 h, 128 h + n)
+constexpr uint32_t kWaitLimit = 1u << 26;
+
+__device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
+
+__device__ __forceinline__ float to_tf32(float x) {
+  uint32_t r;
+  asm("cvt.rna.tf32.f32 %0, %1;" : "=r"(r) : "f"(x));
+  return __uint_as_float(r);
+}
+
+// Byte offset of (row, k) in a K-major, no-swizzle operand with K = 32: 8-row x 16-byte core
+// matrices, adjacent in K at 128 B (LBO), 8-row groups at 1024 B (SBO).
+__device__ __forceinline__ uint32_t koff(int row, int k) {
+  return (uint32_t)((row >> 3) * 1024 + (k >> 2) * 128 + (row & 7) * 16 + (k & 3) * 4);
+}
+
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  uint64_t d = (uint64_t)((addr >> 4) & 0x3FFF);
+  d |= (uint64_t)(128 >> 4) << 16;    // leading byte offset: next core matrix in K
+  d |= (uint64_t)(1024 >> 4) << 32;   // stride byte offset: next 8-row group
+  d |= (uint64_t)1 << 46;             // descriptor version
+  return d;                           // base offset 0, no swizzle
+}
+
+__device__ __forceinline__ uint32_t idesc_tf32(int m, int n) {
+  // D f32 (bits 4-5 = 1), A and B tf32 (= 2 at bits 7-9, 10-12), both K-major, N >> 3 at
+  // bits 17-22, M >> 4 at bits 24-28
+  return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
+}
+
+__device__ __forceinline__ void tc_record(int* status, int code) {
+  if (status) atomicCAS(status, 0, code);
+}
+
+__global__ void __launch_bounds__(kThr, 1)
+tsqr_tile_tc_kernel(float* X, int64_t ld, int64_t M, int s, float* taus, float* Xn, int64_t ldn, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  float* A = reinterpret_cast<float*>(smem_raw);                       // 256 x s, column-major
+  unsigned char* Yhi = smem_raw + (size_t)kRows * s * 4;               // 256 x 32 operand
+  unsigned char* Ylo = Yhi + kRows * kNb * 4;
+  unsigned char* Zhi = Ylo + kRows * kNb * 4;                          // n x 32 operand (n <= 96)
+  unsigned char* Zlo = Zhi + (kMaxS - kNb) * kNb * 4;                  // also W / Z in float
+  float* Tm = reinterpret_cast<float*>(Zlo + (kMaxS - kNb) * kNb * 4);  // 32 x 32 (row l, col k)
+  float* W = reinterpret_cast<float*>(Zlo);                            // 32 x n, row-major
+  __shared__ float sh[4];
+  __shared__ float tau_s[kNb];
+  __shared__ uint32_t tmem_slot;
+  __shared__ __align__(8) uint64_t mbar;
+  __shared__ int abort_s;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t r0 = (int64_t)blockIdx.x * kRows;
+  const int r = (int)(M - r0 < (int64_t)kRows ? M - r0 : (int64_t)kRows);
+  const int kmax = r < s ? r : s;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
+                 "r"(kTmemCols));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_s = 0;
+  }
+  for (int e = tid; e < kRows * s; e += kThr) {
+    const int c = e / kRows, i = e % kRows;
+    A[e] = i < r ? X[(int64_t)c * ld + r0 + i] : 0.f;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  uint32_t phase = 0;
+
+  for (int p0 = 0; p0 < kmax; p0 += kNb) {
+    const int kend = p0 + kNb < kmax ? p0 + kNb : kmax;
+    const int pend = p0 + kNb < s ? p0 + kNb : s;   // panel columns
+    // 1. panel factorization
+    for (int k = p0; k < kend; ++k) {
+      float* x = A + k * kRows;
+      if (warp == 0) {
+        float sq = 0.f;
+        for (int i = k + 1 + lane; i < r; i += 32) sq += x[i] * x[i];
+        for (int d = 16; d >= 1; d >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, d);
+        if (lane == 0) {
+          const float alpha = x[k];
+          const float norm = sqrtf(alpha * alpha + sq);
+          float beta = 0.f, t = 0.f, scale = 0.f;
+          if (norm != 0.f) {
+            beta = alpha >= 0.f ? -norm : norm;
+            t = (beta - alpha) / beta;
+            scale = 1.f / (alpha - beta);
+          }
+          sh[0] = t;
+          sh[1] = beta;
+          sh[2] = scale;
+        }
+        __syncwarp();
+        const float scale = sh[2];
+        for (int i = k + 1 + lane; i < r; i += 32) x[i] *= scale;
+      }
+      __syncthreads();
+      const float t = sh[0];
+      for (int j = k + 1 + warp; j < pend; j += kThr / 32) {
+        float* y = A + j * kRows;
+        float w = 0.f;
+        for (int i = k + 1 + lane; i < r; i += 32) w += x[i] * y[i];
+        for (int d = 16; d >= 1; d >>= 1) w += __shfl_xor_sync(0xffffffffu, w, d);
+        w = (w + y[k]) * t;
+        if (lane == 0) y[k] -= w;
+        for (int i = k + 1 + lane; i < r; i += 32) y[i] -= w * x[i];
+      }
+      if (tid == 0) {
+        x[k] = sh[1];
+        taus[(int64_t)blockIdx.x * s + k] = t;
+        tau_s[k - p0] = t;
+      }
+      __syncthreads();
+    }
+    const int n = s - pend;   // trailing columns
+    if (n <= 0) break;
+    const int nk = kend - p0;
+    // Y (256 x 32): Y[i][l] = 1 at i = p0 + l, the stored v below, 0 above (and 0 for l >= nk)
+    auto yval = [&](int i, int l) -> float {
+      if (l >= nk) return 0.f;
+      const int d = p0 + l;
+      return i < d ? 0.f : (i == d ? 1.f : A[d * kRows + i]);
+    };
+    // 2. T: G = Y^T Y (l < k) into W's space first, then the forward recurrence
+    for (int e = tid; e < kNb * kNb; e += kThr) {
+      const int l = e / kNb, k = e % kNb;
+      float g = 0.f;
+      if (l < k && k < nk)
+        for (int i = p0 + k; i < kRows; ++i) g += yval(i, l) * yval(i, k);
+      W[e] = g;
+    }
+    __syncthreads();
+    if (warp == 0) {
+      for (int k = 0; k < kNb; ++k) {
+        const float tk = k < nk ? tau_s[k] : 0.f;
+        // T[l][k] = -tau_k sum_{m=l}^{k-1} T[l][m] G[m][k] for l < k, T[k][k] = tau_k
+        float v = 0.f;
+        if (lane < k) {
+          for (int m = lane; m < k; ++m) v += Tm[lane * kNb + m] * W[m * kNb + k];
+          v *= -tk;
+        }
+        __syncwarp();
+        if (lane < k) Tm[lane * kNb + k] = v;
+        if (lane == k) Tm[k * kNb + k] = tk;
+        if (lane > k) Tm[lane * kNb + k] = 0.f;
+        __syncwarp();
+      }
+    }
+    __syncthreads();
+    // 3. W = Y^T C (32 x n, row-major), then Z = T^T W in place
+    for (int e = tid; e < kNb * n; e += kThr) {
+      const int l = e / n, j = e % n;
+      const float* c = A + (pend + j) * kRows;
+      float w = 0.f;
+      if (l < nk) {
+        const int d = p0 + l;
+        w = c[d];
+        for (int i = d + 1; i < kRows; ++i) w += A[d * kRows + i] * c[i];
+      }
+      W[e] = w;
+    }
+    __syncthreads();
+    for (int j = tid; j < n; j += kThr)
+      for (int i = kNb - 1; i >= 0; --i) {
+        float z = 0.f;
+        for (int l = 0; l <= i; ++l) z += Tm[l * kNb + i] * W[l * n + j];
+        W[i * n + j] = z;
+      }
+    __syncthreads();
+    // 4. operands: Z (n x 32, K-major) hi/lo; Y (256 x 32) hi/lo
+    {
+      float zv[(kMaxS - kNb) * kNb / kThr];
+      int cnt = 0;
+      for (int e = tid; e < kNb * n; e += kThr) zv[cnt++] = W[e];
+      __syncthreads();
+      cnt = 0;
+      for (int e = tid; e < kNb * n; e += kThr) {
+        const int i = e / n, j = e % n;
+        const float v = zv[cnt++], h = to_tf32(v);
+        *reinterpret_cast<float*>(Zhi + koff(j, i)) = h;
+        *reinterpret_cast<float*>(Zlo + koff(j, i)) = to_tf32(v - h);
+      }
+    }
+    const int h0 = p0 >= 128 ? 1 : 0;   // rows of the first half are zero in Y below p0
+    for (int e = tid + h0 * 128 * kNb; e < kRows * kNb; e += kThr) {
+      const int i = e / kNb, l = e % kNb;
+      const float v = yval(i, l), h = to_tf32(v);
+      const uint32_t o = (uint32_t)(i >> 7) * (128 * kNb * 4) + koff(i & 127, l);
+      *reinterpret_cast<float*>(Yhi + o) = h;
+      *reinterpret_cast<float*>(Ylo + o) = to_tf32(v - h);
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (tid == 0) {
+      const uint32_t id = idesc_tf32(128, n);
+      for (int h = h0; h < 2; ++h) {
+        const uint32_t yo = (uint32_t)h * (128 * kNb * 4);
+        int first = 1;
+        for (int ks = 0; ks < kNb / 8; ++ks) {
+          const uint32_t ko = (uint32_t)ks * 256;
+          for (int sp = 0; sp < 3; ++sp) {
+            const unsigned char* ya = sp == 2 ? Ylo : Yhi;
+            const unsigned char* zb = sp == 1 ? Zlo : Zhi;
+            const uint64_t ad = smem_desc(su32(ya) + yo + ko), bd = smem_desc(su32(zb) + ko);
+            const uint32_t acc = first ? 0u : 1u;
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)h * 128),
+                "l"(ad), "l"(bd), "r"(id), "r"(acc));
+            first = 0;
+          }
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          su32(&mbar)));
+    }
+    // wait for the MMAs (bounded)
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < kWaitLimit && !done; ++it)
+      asm volatile(
+          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+          : "=r"(done)
+          : "r"(su32(&mbar)), "r"(phase));
+    phase ^= 1u;
+    if (!done) abort_s = 1;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    __syncthreads();
+    if (abort_s) break;
+    // C -= D: warp w reads TMEM lanes 32 (w % 4) .. of half w / 4
+    {
+      const int h = warp >> 2;
+      if (h >= h0) {
+        const int row = h * 128 + (warp & 3) * 32 + lane;
+        for (int c0 = 0; c0 < n; c0 += 8) {
+          uint32_t v[8];
+          const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(h * 128 + c0);
+          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                         "=r"(v[7])
+                       : "r"(ta));
+          asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+          for (int j = 0; j < 8; ++j) A[(pend + c0 + j) * kRows + row] -= __uint_as_float(v[j]);
+        }
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+  }
+  if (abort_s) {
+    if (tid == 0) tc_record(status, QRKIT_ETIMEOUT);
+    // the MMAs of this CTA may still be running: wait once more (bounded) before freeing TMEM
+    uint32_t done = 0;
+    for (uint32_t it = 0; it < kWaitLimit && !done; ++it)
+      asm volatile(
+          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
+          : "=r"(done)
+          : "r"(su32(&mbar)), "r"(phase ^ 1u));
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+  if (abort_s) return;
+  for (int e = tid; e < r * s; e += kThr) {
+    const int c = e / r, i = e % r;
+    X[(int64_t)c * ld + r0 + i] = A[c * kRows + i];
+  }
+  if (Xn) {
+    const int64_t n0 = (int64_t)blockIdx.x * s;
+    for (int e = tid; e < kmax * s; e += kThr) {
+      const int c = e / kmax, i = e % kmax;
+      Xn[(int64_t)c * ldn + n0 + i] = (c >= i) ? A[c * kRows + i] : 0.f;
+    }
+  }
+}
+
+}  // namespace
+
+size_t tsqr_tc_smem(int s) {
+  return (size_t)kRows * s * 4 + 2 * (size_t)kRows * kNb * 4 + 2 * (size_t)(kMaxS - kNb) * kNb * 4 +
+         (size_t)kNb * kNb * 4;
+}
+
+bool tsqr_tc_supported(int s, int tile_rows) {
+  return tile_rows == kRows && s > 64 && s <= kMaxS && s % kNb == 0;
+}
+
+qrkit_status tsqr_tile_tc(qrkit_ctx* ctx, float* X, int64_t ld, int64_t M, int s, float* taus, float* Xn,
+                          int64_t ldn, int64_t tiles) {
+  const size_t smem = tsqr_tc_smem(s);
+  if (smem > ctx->max_smem_optin)
+    return fail(ctx, QRKIT_EUNSUPPORTED, "not enough shared memory for the tensor-core tile kernel");
+  if (ctx->smem_attr[7] < smem) {
+    QRKIT_CUDA_TRY(ctx, cudaFuncSetAttribute(tsqr_tile_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+    ctx->smem_attr[7] = smem;
+  }
+  tsqr_tile_tc_kernel<<<(unsigned)tiles, kThr, smem, ctx->stream>>>(X, ld, M, s, taus, Xn, ldn, ctx->d_status);
+  ctx->launches += 1;
+  QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+  return QRKIT_OK;
+}
+
+}  // namespace qrkit

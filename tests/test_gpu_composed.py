@@ -107,3 +107,20 @@ def test_dense_hcat_many_tsqr_levels():
     p_ref, _ = st.factor_and_solve(P)
     out = run(d, "fp64", refine_steps=0)
     assert rel(out["p"], p_ref) <= 1e-11
+
+
+@pytest.mark.parametrize("s,K", [(128, 300), (96, 257), (128, 2000)])
+def test_dense_tensor_core_tiles_fp32_refined(s, K):
+    """Shared block of 96 / 128 columns: the reduced block's tile QR runs its trailing updates
+    on the tensor cores (3xTF32); ragged tiles at every TSQR level.  Refined float result vs the
+    float64 oracle of the float-rounded problem <= 1e-5."""
+    d = block_angular_dense(K=K, n=4, m=2, s=s, scale_decades=2.0, seed_offset=s)
+    d32 = dict(d)
+    d32["blocks"] = np.asarray(d["blocks"], np.float32).astype(np.float64)
+    d32["S"] = np.asarray(d["S"], np.float32).astype(np.float64)
+    d32["b"] = np.asarray(d["b"], np.float32).astype(np.float64)
+    p_ref, _ = st.factor_and_solve(problem_from(d32))
+    out = run(d32, "fp32_refined", refine_steps=2)
+    assert rel(out["p"], p_ref) <= 1e-5
+    out0 = run(d32, "fp32", refine_steps=0)
+    assert rel(out0["p"], p_ref) <= 1e-3
