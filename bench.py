@@ -260,6 +260,28 @@ def other_workloads(dev, stream):
         "workload": "J = [blkdiag(200 blocks 4x2) | S 800x30], columns scaled 1..1e3, lambda 1e-2, D = norms",
         "value": 1000.0 / ms, "unit": "solves/s", "us_per_solve": 1000.0 * ms, "launches_per_solve": None}
     ctx.close()
+    # dense hcat at the tensor-core size: 100,000 blocks 4x2, S 400,000 x 128, FP32-refined
+    d = block_angular_dense(K=100_000, n=4, m=2, s=128, scale_decades=2.0, dtype=np.float32)
+    K, n, m, s = d["K"], d["n"], d["m"], d["s"]
+    ctx = Context(dev.index, stream=stream, precision="fp32_refined")
+    ctx.plan_blocks(np.full(K, n), np.full(K, m), qrkit.COUPLED_DENSE, shared_cols=s)
+    J = torch.from_numpy(np.concatenate([d["blocks"][i].T.reshape(-1) for i in range(K)])).to(dev)
+    S = torch.from_numpy(np.asarray(d["S"]).T.reshape(-1).copy()).to(dev)
+    b = torch.from_numpy(np.asarray(d["b"])).to(dev)
+    pl = torch.empty(K * m + s, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+    tf = _time(stream, lambda: ctx.factor(J, S, None, d["lam"]), 5)
+    ts = _time(stream, lambda: ctx.solve(b, pl, refine_steps=1), 5)
+    ctx.sync_status()
+    Mred = K * n + s
+    flops = 2.0 * Mred * s * s   # useful flops of the reduced block's Householder QR (leading term)
+    out["dense_hcat_100k_blocks_s128_fp32_refined"] = {
+        "workload": "J = [blkdiag(100,000 blocks 4x2) | S 400,000 x 128], lambda 1e-2, D = norms; "
+                    "reduced block TSQR with tcgen05 3xTF32 trailing updates",
+        "ms_factor": tf, "ms_solve_refined_1": ts, "value": 1000.0 / (tf + ts), "unit": "solves/s",
+        "reduced_block_tflops_useful": flops / (tf * 1e-3) / 1e12}
+    ctx.close()
+    del J, S, b
     # curve fit, 200,000 points, 2048 control points: LM iterations and fixed-lambda solves
     cf = {}
     for prec in ("fp32_refined", "fp32", "fp64"):

@@ -59,6 +59,12 @@ __device__ __forceinline__ uint32_t idesc_tf32(int m, int n) {
   return (1u << 4) | (2u << 7) | (2u << 10) | ((uint32_t)(n >> 3) << 17) | ((uint32_t)(m >> 4) << 24);
 }
 
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+  return v;
+}
+
 __device__ __forceinline__ void tc_record(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
@@ -158,13 +164,19 @@ tsqr_tile_tc_kernel(float* X, int64_t ld, int64_t M, int s, float* taus, float* 
       const int d = p0 + l;
       return i < d ? 0.f : (i == d ? 1.f : A[d * kRows + i]);
     };
-    // 2. T: G = Y^T Y (l < k) into W's space first, then the forward recurrence
-    for (int e = tid; e < kNb * kNb; e += kThr) {
+    // 2. T: G = Y^T Y (l < k) into W's space first (one warp per entry, lanes over rows,
+    // conflict-free column reads), then the forward recurrence
+    for (int e = warp; e < kNb * kNb; e += kThr / 32) {
       const int l = e / kNb, k = e % kNb;
       float g = 0.f;
-      if (l < k && k < nk)
-        for (int i = p0 + k; i < kRows; ++i) g += yval(i, l) * yval(i, k);
-      W[e] = g;
+      if (l < k && k < nk) {
+        const float* yl = A + (p0 + l) * kRows;
+        const float* yk = A + (p0 + k) * kRows;
+        for (int i = p0 + k + 1 + lane; i < kRows; i += 32) g += yl[i] * yk[i];
+        g = warp_sum(g);
+        g += yl[p0 + k];   // row p0 + k: y_k = 1 there
+      }
+      if (lane == 0) W[e] = g;
     }
     __syncthreads();
     if (warp == 0) {
@@ -184,17 +196,18 @@ tsqr_tile_tc_kernel(float* X, int64_t ld, int64_t M, int s, float* taus, float* 
       }
     }
     __syncthreads();
-    // 3. W = Y^T C (32 x n, row-major), then Z = T^T W in place
-    for (int e = tid; e < kNb * n; e += kThr) {
+    // 3. W = Y^T C (32 x n, row-major; one warp per entry, lanes over rows), then Z = T^T W
+    for (int e = warp; e < kNb * n; e += kThr / 32) {
       const int l = e / n, j = e % n;
       const float* c = A + (pend + j) * kRows;
       float w = 0.f;
       if (l < nk) {
         const int d = p0 + l;
-        w = c[d];
-        for (int i = d + 1; i < kRows; ++i) w += A[d * kRows + i] * c[i];
+        const float* y = A + d * kRows;
+        for (int i = d + 1 + lane; i < kRows; i += 32) w += y[i] * c[i];
+        w = warp_sum(w) + c[d];
       }
-      W[e] = w;
+      if (lane == 0) W[e] = w;
     }
     __syncthreads();
     for (int j = tid; j < n; j += kThr)
@@ -219,8 +232,9 @@ tsqr_tile_tc_kernel(float* X, int64_t ld, int64_t M, int s, float* taus, float* 
       }
     }
     const int h0 = p0 >= 128 ? 1 : 0;   // rows of the first half are zero in Y below p0
-    for (int e = tid + h0 * 128 * kNb; e < kRows * kNb; e += kThr) {
-      const int i = e / kNb, l = e % kNb;
+    for (int e = tid + h0 * 128; e < kRows * kNb; e += kThr) {
+      const int l = e / kRows, i = e % kRows;
+      if (i < h0 * 128) continue;
       const float v = yval(i, l), h = to_tf32(v);
       const uint32_t o = (uint32_t)(i >> 7) * (128 * kNb * 4) + koff(i & 127, l);
       *reinterpret_cast<float*>(Yhi + o) = h;
