@@ -129,11 +129,15 @@ const char* qrkit_status_string(int status);
 qrkit_status qrkit_plan(qrkit_ctx* ctx, const qrkit_structure* s);
 
 /* Fused factor + solve for QRKIT_STRUCT_BLOCKS with QRKIT_COUPLED_NONE (Sec. 4.1, Sec. 5.1):
- * for every block the Householder QR of J_i, c_i = Q_i^T b_i, R_i p_i = c_i, then (FP32 refined
- * mode) up to `refine_steps` steps of refinement with an extended-precision residual: each
- * step computes g = J_i^T (b_i - J_i p_i) in compensated float arithmetic and corrects
- * p_i += R_i^{-1} R_i^{-T} g; a block stops as soon as its correction is below 1e-6 of its
- * solution (max norms).  refine_steps is ignored for QRKIT_FP32 and QRKIT_FP64.
+ * for every block the Householder QR of J_i, c_i = Q_i^T b_i, R_i p_i = c_i.  In FP32 refined
+ * mode each block then estimates the error of its float solution a priori,
+ * u (kappa + kappa^2 ||r|| / (||R|| ||p||)) with u = 2^-24, ||R||_F, ||R^{-1}||_2 from two power
+ * steps and ||r|| from the bottom of Q^T b; blocks estimated above 1e-6 are refined by up to
+ * `refine_steps` steps with an extended-precision residual: each step computes
+ * g = J_i^T (b_i - J_i p_i) in compensated float arithmetic and corrects p_i += R_i^{-1}
+ * R_i^{-T} g, stopping once the correction is below 1e-6 of the solution (max norms).  The
+ * selected blocks are refined by a second kernel.  refine_steps is ignored for QRKIT_FP32 and
+ * QRKIT_FP64.
  *   J    : packed values, block i column-major n_i x m_i, blocks in order (sum n_i m_i)
  *   b    : sum n_i values, block i's rows contiguous
  *   D    : reserved, pass NULL

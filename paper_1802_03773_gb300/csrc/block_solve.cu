@@ -28,6 +28,8 @@ namespace {
 constexpr int kMaxRows = 16;   // rows per block (one lane, padded to 4, 8, 12 or 16)
 constexpr int kMaxCols = 8;    // columns per block
 constexpr int kThreads = 256;  // threads per CTA
+constexpr float kUnitRoundoff = 5.9604645e-8f;   // 2^-24
+constexpr float kRefineTarget = 1e-6f;           // blocks estimated above this are refined
 constexpr int kKeys = 36;      // sort keys: 4 row classes x (m = 0..8)
 static_assert(kKeys <= 64, "the bin scan handles at most 64 keys");
 
@@ -171,6 +173,9 @@ struct BlockSolveArgs {
   int* status;
   int vb, rb, cb, bb, pb;  // tile budgets (pb: padded working area)
   long long wait_limit;  // polls of an mbarrier before giving up
+  int* rlist;            // selection mode: blocks to refine, 4 row-class lists of rcap entries
+  int* rcount;           // their lengths (4)
+  int64_t rcap;
 };
 
 // Shared-memory layout (identical on host and device).  Each block is factored in a padded
@@ -178,11 +183,12 @@ struct BlockSolveArgs {
 // written back in packed form over the J buffer, which stages the factor for the store.
 // Without refinement Q^T b is formed in place in the b buffer.
 struct Layout {
-  size_t J, b, n, m, W, Cw, rs, c, tau, x, g, vo, ro, co, po, qo, wtot, perm, hist, bar, total;
+  size_t J, b, n, m, W, Cw, rs, c, tau, x, g, vo, ro, co, po, qo, wtot, perm, hist, sel, bar, total;
 };
 __host__ __device__ inline size_t round16(size_t v) { return (v + 15) / 16 * 16; }
 template <typename T>
-__host__ __device__ inline Layout make_layout(int vb, int rb, int cb, int bb, int pb, bool refine) {
+__host__ __device__ inline Layout make_layout(int vb, int rb, int cb, int bb, int pb, bool refine,
+                                             bool select = false) {
   const int VN = 16 / (int)sizeof(T);
   Layout L;
   size_t off = 0;
@@ -206,6 +212,7 @@ __host__ __device__ inline Layout make_layout(int vb, int rb, int cb, int bb, in
   L.wtot = take((size_t)(32 + kThreads / 32) * sizeof(int));
   L.perm = take((size_t)bb * sizeof(int));
   L.hist = take((size_t)(2 * kKeys + 8) * sizeof(int));
+  L.sel = select ? take((size_t)(bb + 16) * sizeof(int)) : 0;   // selected blocks + counters
   L.bar = take(sizeof(uint64_t));
   L.total = off;
   return L;
@@ -404,6 +411,59 @@ __device__ __noinline__ float lane_refine(int nn, int Rp, int mm, const float* J
   return xmax > 0.f ? dmax / xmax : 0.f;
 }
 
+// A-priori error estimate of a block's float least-squares solution (Householder QR is
+// backward stable: relative error ~ u (kappa + kappa^2 ||r|| / (||A|| ||x||))), with
+// ||A|| ~ ||R||_F, ||R^{-1}||_2^2 from two power steps v <- R^{-1} R^{-T} v (from below) and
+// ||r|| = || rows m.. of Q^T b ||; true when the estimate exceeds kRefineTarget.  W: the
+// factor (R on and above the diagonal, column stride R), c: Q^T b.  Register-resident: the
+// loops run to the 8-column bound with predicates.
+template <int R>
+__device__ __forceinline__ bool needs_refinement(int nn, int mm, const float* W, const float (&c)[R],
+                                                 const float* x) {
+  if (mm <= 0) return false;
+  float rF2 = 0.f, x2 = 0.f, res2 = 0.f;
+  float d[kMaxCols], v[kMaxCols];
+#pragma unroll
+  for (int k = 0; k < kMaxCols; ++k) {
+    const bool on = k < mm;
+    d[k] = on ? frcp(W[k * R + k]) : 0.f;
+    v[k] = on ? 1.f : 0.f;
+    if (on) x2 += x[k] * x[k];
+#pragma unroll
+    for (int i = 0; i <= k; ++i)
+      if (on) rF2 += W[k * R + i] * W[k * R + i];
+  }
+#pragma unroll
+  for (int r = 0; r < R; ++r)
+    if (r >= mm && r < nn) res2 += c[r] * c[r];
+  float vn2 = (float)mm, inv2 = 0.f;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const float sc = rsqrtf(vn2);
+#pragma unroll
+    for (int k = 0; k < kMaxCols; ++k) {   // R^T w = v / ||v||
+      float t = v[k] * sc;
+#pragma unroll
+      for (int i = 0; i < k; ++i) t -= W[k * R + i] * v[i];
+      v[k] = k < mm ? t * d[k] : 0.f;
+    }
+#pragma unroll
+    for (int k = kMaxCols - 1; k >= 0; --k) {   // R v' = w
+      float t = v[k];
+#pragma unroll
+      for (int j = k + 1; j < kMaxCols; ++j) t -= (j < mm ? W[j * R + k] : 0.f) * v[j];
+      v[k] = k < mm ? t * d[k] : 0.f;
+    }
+    vn2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < kMaxCols; ++k) vn2 += v[k] * v[k];
+    inv2 = sqrtf(vn2);
+  }
+  const float rF = sqrtf(rF2);
+  const float est = kUnitRoundoff * (rF * sqrtf(inv2) + rF * inv2 * sqrtf(res2 / x2));
+  return !(est <= kRefineTarget);   // NaN (x = 0, zero pivot) refines
+}
+
 // Everything one lane does for one block: padded copy in, factor, Q^T b, back-substitution,
 // adaptive refinement (until the correction is below refine_tol relative to x, at most
 // max_steps), packed copy of the factor out (Fout, may alias J: written last).  All 32
@@ -411,8 +471,8 @@ __device__ __noinline__ float lane_refine(int nn, int Rp, int mm, const float* J
 // __syncwarp(), so lanes whose loops ran for different lengths reconverge.  The refinement
 // is one shared (not inlined) routine for every row class, which keeps the code that warps
 // loop back into small.  rs: scratch of 2 * R floats for the residual.
-template <typename T, bool REF, int R>
-__device__ __forceinline__ void lane_block(int nn, int mm, const T* J, const T* b, T* W, T* C,
+template <typename T, bool REF, int R, bool SEL = false>
+__device__ __forceinline__ bool lane_block(int nn, int mm, const T* J, const T* b, T* W, T* C,
                                            T* tau, T* x, T* g, T* rs, T* Fout, int max_steps,
                                            float refine_tol, int* status) {
   for (int j = 0; j < mm; ++j) {
@@ -434,6 +494,8 @@ __device__ __forceinline__ void lane_block(int nn, int mm, const T* J, const T* 
     if (r < nn) C[r] = bb[r];
   if (!back_substitute(W, R, mm, C, x)) record(status, QRKIT_ESINGULAR);
   __syncwarp();
+  bool need = false;
+  if constexpr (SEL) need = needs_refinement<R>(nn, mm, W, bb, x);
   if constexpr (REF) {
     for (int step = 0; step < max_steps; ++step) {
       const float rel = lane_refine(nn, R, mm, J, b, W, x, g, rs);
@@ -446,6 +508,7 @@ __device__ __forceinline__ void lane_block(int nn, int mm, const T* J, const T* 
       for (int r = 0; r < nn; ++r) Fout[j * nn + r] = W[j * R + r];
   }
   __syncwarp();
+  return need;
 }
 
 // Per-tile geometry shared by the issue, compute and store phases.
@@ -531,11 +594,11 @@ __device__ __forceinline__ void store_out(T* __restrict__ dst, const T* src, int
   for (int k = head + nvec * VN + threadIdx.x; k < count; k += kThreads) dst[k] = src[k];
 }
 
-template <typename T, bool REF>
+template <typename T, bool REF, bool SEL = false>
 __global__ void __launch_bounds__(kThreads, 3)
 block_solve_kernel(BlockSolveArgs<T> A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
-  const Layout L = make_layout<T>(A.vb, A.rb, A.cb, A.bb, A.pb, REF);
+  const Layout L = make_layout<T>(A.vb, A.rb, A.cb, A.bb, A.pb, REF, SEL);
   int* sVo = reinterpret_cast<int*>(smem_raw + L.vo);
   int* sRo = reinterpret_cast<int*>(smem_raw + L.ro);
   int* sCo = reinterpret_cast<int*>(smem_raw + L.co);
@@ -643,6 +706,9 @@ block_solve_kernel(BlockSolveArgs<T> A) {
   }
   const int total_chunks = nch[0] + nch[1] + nch[2] + nch[3];
   T* Fstage = f_alias ? sF : nullptr;
+  int* sSel = SEL ? reinterpret_cast<int*>(smem_raw + L.sel) : nullptr;   // [0..15] counters
+  if (SEL && tid < 16) sSel[tid] = 0;
+  if (SEL) __syncthreads();
   for (int ch = warp_id; ch < total_chunks; ch += kThreads / 32) {
     int c = 0, first = ch;
 #pragma unroll
@@ -666,15 +732,31 @@ block_solve_kernel(BlockSolveArgs<T> A) {
       T* Fo = (Fstage && has) ? Fstage + vo : nullptr;
       T* gb = REF ? sG + co : nullptr;
       T* rsb = REF ? sRs + 2 * qo : nullptr;
+      bool need;
       switch (c) {
-        case 0: lane_block<T, REF, 4>(nn, mm, sJ + vo, sB + ro, Wb, sC + ro, sT + co, sX + co, gb, rsb, Fo, A.refine_steps, A.refine_tol, A.status); break;
-        case 1: lane_block<T, REF, 8>(nn, mm, sJ + vo, sB + ro, Wb, sC + ro, sT + co, sX + co, gb, rsb, Fo, A.refine_steps, A.refine_tol, A.status); break;
-        case 2: lane_block<T, REF, 12>(nn, mm, sJ + vo, sB + ro, Wb, sC + ro, sT + co, sX + co, gb, rsb, Fo, A.refine_steps, A.refine_tol, A.status); break;
-        default: lane_block<T, REF, 16>(nn, mm, sJ + vo, sB + ro, Wb, sC + ro, sT + co, sX + co, gb, rsb, Fo, A.refine_steps, A.refine_tol, A.status); break;
+        case 0: need = lane_block<T, REF, 4, SEL>(nn, mm, sJ + vo, sB + ro, Wb, sC + ro, sT + co, sX + co, gb, rsb, Fo, A.refine_steps, A.refine_tol, A.status); break;
+        case 1: need = lane_block<T, REF, 8, SEL>(nn, mm, sJ + vo, sB + ro, Wb, sC + ro, sT + co, sX + co, gb, rsb, Fo, A.refine_steps, A.refine_tol, A.status); break;
+        case 2: need = lane_block<T, REF, 12, SEL>(nn, mm, sJ + vo, sB + ro, Wb, sC + ro, sT + co, sX + co, gb, rsb, Fo, A.refine_steps, A.refine_tol, A.status); break;
+        default: need = lane_block<T, REF, 16, SEL>(nn, mm, sJ + vo, sB + ro, Wb, sC + ro, sT + co, sX + co, gb, rsb, Fo, A.refine_steps, A.refine_tol, A.status); break;
       }
+      if (SEL && has && need) sSel[16 + atomicAdd(&sSel[0], 1)] = (c << 28) | bi;
     }
   }
   __syncthreads();
+  if constexpr (SEL) {
+    // the selected blocks go to the global row-class lists: one atomic per class per tile
+    const int total = sSel[0];
+    for (int k = tid; k < total; k += kThreads) atomicAdd(&sSel[1 + (sSel[16 + k] >> 28)], 1);
+    __syncthreads();
+    if (tid < 4) sSel[5 + tid] = sSel[1 + tid] ? atomicAdd(&A.rcount[tid], sSel[1 + tid]) : 0;
+    if (tid < 4) sSel[9 + tid] = 0;
+    __syncthreads();
+    for (int k = tid; k < total; k += kThreads) {
+      const int e = sSel[16 + k], c = e >> 28, bi = e & 0x0FFFFFFF;
+      const int64_t pos = (int64_t)sSel[5 + c] + atomicAdd(&sSel[9 + c], 1);
+      if (pos < A.rcap) A.rlist[c * A.rcap + pos] = (int)(g.b0 + bi);
+    }
+  }
   if (!f_alias) {
     // the factor's staging cannot share J's alignment: write it from the working area
     for (int bi = tid; bi < g.nb; bi += kThreads) {
@@ -691,6 +773,103 @@ block_solve_kernel(BlockSolveArgs<T> A) {
   store_out(A.x + g.c0, sX, g.nc);
 }
 
+// Refinement of the blocks the selection listed (one thread per block, grid-stride over the
+// four row-class lists so that a warp's blocks share a row class): each step forms the
+// residual r = b - J x and g = J^T r in compensated float arithmetic (TwoProduct by FMA,
+// TwoSum), then x += R^{-1} R^{-T} g with the stored R; a block stops once its correction is
+// below tol relative to x (max norms), after at most `steps` steps.
+struct RefineArgs {
+  const uint8_t* n;
+  const uint8_t* m;
+  const int64_t* val_off;
+  const int64_t* row_off;
+  const int64_t* col_off;
+  const float* J;
+  const float* b;
+  const float* F;   // factor in J's packing: R on and above the diagonal
+  float* x;
+  const int* rlist;
+  const int* rcount;
+  int64_t rcap;
+  int steps;
+  float tol;
+};
+
+__global__ void __launch_bounds__(128) block_refine_kernel(RefineArgs A) {
+  int64_t cnt[4], total = 0;
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    cnt[c] = A.rcount[c] < A.rcap ? A.rcount[c] : A.rcap;
+    total += cnt[c];
+  }
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < total;
+       i += (int64_t)gridDim.x * blockDim.x) {
+    int c = 0;
+    int64_t pos = i;
+    while (c < 3 && pos >= cnt[c]) {
+      pos -= cnt[c];
+      ++c;
+    }
+    const int64_t blk = A.rlist[c * A.rcap + pos];
+    const int nn = A.n[blk], mm = A.m[blk];
+    if (nn > kMaxRows || mm > kMaxCols || mm < 1) continue;
+    const float* J = A.J + A.val_off[blk];
+    const float* F = A.F + A.val_off[blk];
+    const float* b = A.b + A.row_off[blk];
+    float* xo = A.x + A.col_off[blk];
+    float x[kMaxCols], rh[kMaxRows], rl[kMaxRows], h[kMaxCols];
+    for (int j = 0; j < mm; ++j) x[j] = xo[j];
+    for (int step = 0; step < A.steps; ++step) {
+      for (int r = 0; r < nn; ++r) {
+        float sh = b[r], sl = 0.f;
+        for (int j = 0; j < mm; ++j) {
+          const float a = J[j * nn + r], xj = -x[j];
+          const float pr = __fmul_rn(a, xj);
+          const float pe = __fmaf_rn(a, xj, -pr);
+          float t, e;
+          two_sum(sh, pr, t, e);
+          sh = t;
+          sl = __fadd_rn(sl, __fadd_rn(e, pe));
+        }
+        rh[r] = sh;
+        rl[r] = sl;
+      }
+      for (int j = 0; j < mm; ++j) {
+        float sj = 0.f, cj = 0.f;
+        for (int r = 0; r < nn; ++r) {
+          const float a = J[j * nn + r];
+          const float pr = __fmul_rn(a, rh[r]);
+          float pe = __fmaf_rn(a, rh[r], -pr);
+          pe = __fmaf_rn(a, rl[r], pe);
+          float t, e;
+          two_sum(sj, pr, t, e);
+          sj = t;
+          cj = __fadd_rn(cj, __fadd_rn(e, pe));
+        }
+        h[j] = __fadd_rn(sj, cj);
+      }
+      for (int k = 0; k < mm; ++k) {   // R^T h = g
+        float v = h[k];
+        for (int i = 0; i < k; ++i) v -= F[k * nn + i] * h[i];
+        h[k] = v / F[k * nn + k];
+      }
+      for (int k = mm - 1; k >= 0; --k) {   // R dx = h
+        float v = h[k];
+        for (int j = k + 1; j < mm; ++j) v -= F[j * nn + k] * h[j];
+        h[k] = v / F[k * nn + k];
+      }
+      float dmax = 0.f, xmax = 0.f;
+      for (int k = 0; k < mm; ++k) {
+        x[k] += h[k];
+        dmax = fmaxf(dmax, fabsf(h[k]));
+        xmax = fmaxf(xmax, fabsf(x[k]));
+      }
+      if (!(dmax > A.tol * xmax)) break;
+    }
+    for (int j = 0; j < mm; ++j) xo[j] = x[j];
+  }
+}
+
 // Launch with fully formed arguments (opting the kernel in to its dynamic shared memory).
 template <typename T, bool REF>
 cudaError_t launch_block_kernel(const BlockSolveArgs<T>& A, cudaStream_t st) {
@@ -702,7 +881,7 @@ cudaError_t launch_block_kernel(const BlockSolveArgs<T>& A, cudaStream_t st) {
   return cudaGetLastError();
 }
 
-template <typename T, bool REF>
+template <typename T, bool REF, bool SEL = false>
 qrkit_status launch_typed(qrkit_ctx* ctx, const void* J, const void* b, void* p, void* qtb,
                           int refine_steps) {
   Plan& P = ctx->plan;
@@ -729,9 +908,21 @@ qrkit_status launch_typed(qrkit_ctx* ctx, const void* J, const void* b, void* p,
   A.bb = P.budget.blocks;
   A.pb = P.budget.padded;
   A.wait_limit = 1LL << 26;
-  const size_t smem = make_layout<T>(A.vb, A.rb, A.cb, A.bb, A.pb, REF).total;
-  auto kern = block_solve_kernel<T, REF>;
-  const int variant = (sizeof(T) == sizeof(double) ? 2 : 0) + (REF ? 1 : 0);
+  A.rlist = nullptr;
+  A.rcount = nullptr;
+  A.rcap = 0;
+  if (SEL) {
+    qrkit_status rc;
+    if ((rc = ensure(ctx, ctx->ws.rlist, (size_t)4 * P.K * sizeof(int), "refinement lists")) != QRKIT_OK) return rc;
+    if ((rc = ensure(ctx, ctx->ws.rcount, 4 * sizeof(int), "refinement counts")) != QRKIT_OK) return rc;
+    QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->ws.rcount.ptr, 0, 4 * sizeof(int), ctx->stream));
+    A.rlist = (int*)ctx->ws.rlist.ptr;
+    A.rcount = (int*)ctx->ws.rcount.ptr;
+    A.rcap = P.K;
+  }
+  const size_t smem = make_layout<T>(A.vb, A.rb, A.cb, A.bb, A.pb, REF, SEL).total;
+  auto kern = block_solve_kernel<T, REF, SEL>;
+  const int variant = (sizeof(T) == sizeof(double) ? 2 : 0) + (REF ? 1 : 0) + (SEL ? 4 : 0);
   if (ctx->smem_attr[variant] < smem) {
     QRKIT_CUDA_TRY(ctx, cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                              (int)smem));
@@ -740,6 +931,28 @@ qrkit_status launch_typed(qrkit_ctx* ctx, const void* J, const void* b, void* p,
   kern<<<(unsigned)P.num_tiles, kThreads, smem, ctx->stream>>>(A);
   ctx->launches += 1;
   QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+  if constexpr (SEL && sizeof(T) == sizeof(float)) {
+    RefineArgs R;
+    R.n = A.n;
+    R.m = A.m;
+    R.val_off = (const int64_t*)P.d_val_off.ptr;
+    R.row_off = (const int64_t*)P.d_row_off.ptr;
+    R.col_off = (const int64_t*)P.d_col_off.ptr;
+    R.J = (const float*)J;
+    R.b = (const float*)b;
+    R.F = (const float*)A.F;
+    R.x = (float*)p;
+    R.rlist = A.rlist;
+    R.rcount = A.rcount;
+    R.rcap = A.rcap;
+    R.steps = refine_steps;
+    R.tol = A.refine_tol;
+    const int64_t want = (P.K + 127) / 128;
+    const unsigned grid = (unsigned)(want < (int64_t)ctx->num_sms * 8 ? want : (int64_t)ctx->num_sms * 8);
+    block_refine_kernel<<<grid > 0 ? grid : 1, 128, 0, ctx->stream>>>(R);
+    ctx->launches += 1;
+    QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+  }
   return QRKIT_OK;
 }
 
@@ -764,7 +977,7 @@ qrkit_status launch_block_solve(qrkit_ctx* ctx, const void* J, const void* b, co
   (void)D;
   if (ctx->precision == QRKIT_FP64) return launch_typed<double, false>(ctx, J, b, p, qtb, 0);
   const int steps = ctx->precision == QRKIT_FP32 ? 0 : refine_steps;
-  if (steps > 0) return launch_typed<float, true>(ctx, J, b, p, qtb, steps);
+  if (steps > 0) return launch_typed<float, false, true>(ctx, J, b, p, qtb, steps);
   return launch_typed<float, false>(ctx, J, b, p, qtb, 0);
 }
 

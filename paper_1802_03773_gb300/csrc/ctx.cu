@@ -271,6 +271,8 @@ void qrkit_destroy(qrkit_ctx* ctx) {
   release_band(ctx->band);
   release(ctx->ws.factor);
   release(ctx->ws.tau);
+  release(ctx->ws.rlist);
+  release(ctx->ws.rcount);
   if (ctx->d_status) cudaFree(ctx->d_status);
   delete ctx;
 }

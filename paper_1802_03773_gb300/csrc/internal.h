@@ -174,6 +174,7 @@ void release_lm(LM*& lm);
 struct Workspace {
   DevBuf factor;   // factor values (J packing)
   DevBuf tau;      // sum m_i
+  DevBuf rlist, rcount;   // blocks selected for refinement (4 row-class lists) and their counts
 };
 
 }  // namespace qrkit
