@@ -145,7 +145,7 @@ qrkit_status qrkit_plan(qrkit_ctx* ctx, const qrkit_structure* s);
  *   p    : out, sum m_i values
  *   qtb  : out or NULL; sum n_i values: Q_i^T b_i per block
  * The factor (reflectors below the diagonal, R on and above it, tau) stays in the context.
- * One kernel launch; asynchronous on the context's stream. */
+ * One kernel launch (two in FP32 refined mode); asynchronous on the context's stream. */
 qrkit_status qrkit_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
                                 double lambda, void* p, void* qtb, int refine_steps);
 
