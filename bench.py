@@ -234,152 +234,160 @@ def _curvefit_batch(ctx, specs, dev, stream):
     return x, x0, data, npts, kcs
 
 
-def other_workloads(dev, stream):
-    """The remaining configurations, each timed briefly (CUDA events, after warm-up)."""
+def other_workloads(dev, stream, only=None):
+    """The remaining configurations, each timed briefly (CUDA events, after warm-up); `only`
+    restricts the run to the workloads whose key starts with it."""
     import torch
     from paper_1802_03773_gb300 import Context, qrkit
     from workloads import banded_batch_shapes, banded_problem, block_angular_dense
     out = {}
     peaks, peak_kind = measured_peaks()
-    # dense horizontal concatenation, one LM-step solve in FP64
-    d = block_angular_dense()
-    K, n, m, s = d["K"], d["n"], d["m"], d["s"]
-    ctx = Context(dev.index, stream=stream, precision="fp64")
-    ctx.plan_blocks(np.full(K, n), np.full(K, m), qrkit.COUPLED_DENSE, shared_cols=s)
-    J = torch.from_numpy(np.concatenate([d["blocks"][i].T.reshape(-1) for i in range(K)])).to(dev)
-    S = torch.from_numpy(np.asarray(d["S"]).T.reshape(-1).copy()).to(dev)
-    b = torch.from_numpy(np.asarray(d["b"])).to(dev)
-    pd = torch.empty(K * m + s, dtype=torch.float64, device=dev)
-    torch.cuda.synchronize()   # inputs copied on the default stream before the context's stream reads them
+    want = lambda key: only is None or key.startswith(only) or only.startswith(key)
+    if want("dense_hcat_200x"):
+        # dense horizontal concatenation, one LM-step solve in FP64
+        d = block_angular_dense()
+        K, n, m, s = d["K"], d["n"], d["m"], d["s"]
+        ctx = Context(dev.index, stream=stream, precision="fp64")
+        ctx.plan_blocks(np.full(K, n), np.full(K, m), qrkit.COUPLED_DENSE, shared_cols=s)
+        J = torch.from_numpy(np.concatenate([d["blocks"][i].T.reshape(-1) for i in range(K)])).to(dev)
+        S = torch.from_numpy(np.asarray(d["S"]).T.reshape(-1).copy()).to(dev)
+        b = torch.from_numpy(np.asarray(d["b"])).to(dev)
+        pd = torch.empty(K * m + s, dtype=torch.float64, device=dev)
+        torch.cuda.synchronize()   # inputs copied on the default stream before the context's stream reads them
 
-    def dense_solve():
-        ctx.factor(J, S, None, d["lam"])
-        ctx.solve(b, pd, refine_steps=0)
-    ms = _time(stream, dense_solve, 100)
-    ctx.sync_status()
-    out["dense_hcat_200x(4x2)_s30_fp64"] = {
-        "workload": "J = [blkdiag(200 blocks 4x2) | S 800x30], columns scaled 1..1e3, lambda 1e-2, D = norms",
-        "value": 1000.0 / ms, "unit": "solves/s", "us_per_solve": 1000.0 * ms, "launches_per_solve": None}
-    ctx.close()
-    # dense hcat at the tensor-core size: 100,000 blocks 4x2, S 400,000 x 128, FP32-refined
-    d = block_angular_dense(K=100_000, n=4, m=2, s=128, scale_decades=2.0, dtype=np.float32)
-    K, n, m, s = d["K"], d["n"], d["m"], d["s"]
-    ctx = Context(dev.index, stream=stream, precision="fp32_refined")
-    ctx.plan_blocks(np.full(K, n), np.full(K, m), qrkit.COUPLED_DENSE, shared_cols=s)
-    J = torch.from_numpy(np.concatenate([d["blocks"][i].T.reshape(-1) for i in range(K)])).to(dev)
-    S = torch.from_numpy(np.asarray(d["S"]).T.reshape(-1).copy()).to(dev)
-    b = torch.from_numpy(np.asarray(d["b"])).to(dev)
-    pl = torch.empty(K * m + s, dtype=torch.float32, device=dev)
-    torch.cuda.synchronize()
-    tf = _time(stream, lambda: ctx.factor(J, S, None, d["lam"]), 5)
-    ts = _time(stream, lambda: ctx.solve(b, pl, refine_steps=1), 5)
-    ctx.sync_status()
-    Mred = K * n + s
-    flops = 2.0 * Mred * s * s   # useful flops of the reduced block's Householder QR (leading term)
-    out["dense_hcat_100k_blocks_s128_fp32_refined"] = {
-        "workload": "J = [blkdiag(100,000 blocks 4x2) | S 400,000 x 128], lambda 1e-2, D = norms; "
-                    "reduced block TSQR with tcgen05 3xTF32 trailing updates",
-        "ms_factor": tf, "ms_solve_refined_1": ts, "value": 1000.0 / (tf + ts), "unit": "solves/s",
-        "reduced_block_tflops_useful": flops / (tf * 1e-3) / 1e12}
-    ctx.close()
-    del J, S, b
-    # curve fit, 200,000 points, 2048 control points: LM iterations and fixed-lambda solves
-    cf = {}
-    for prec in ("fp32_refined", "fp32", "fp64"):
-        ctx = Context(dev.index, stream=stream, precision=prec)
-        x, x0, data, npts, kcs = _curvefit_batch(ctx, [(200_000, 2048, 0)], dev, stream)
+        def dense_solve():
+            ctx.factor(J, S, None, d["lam"])
+            ctx.solve(b, pd, refine_steps=0)
+        ms = _time(stream, dense_solve, 100)
+        ctx.sync_status()
+        out["dense_hcat_200x(4x2)_s30_fp64"] = {
+            "workload": "J = [blkdiag(200 blocks 4x2) | S 800x30], columns scaled 1..1e3, lambda 1e-2, D = norms",
+            "value": 1000.0 / ms, "unit": "solves/s", "us_per_solve": 1000.0 * ms, "launches_per_solve": None}
+        ctx.close()
+    if want("dense_hcat_100k"):
+        # dense hcat at the tensor-core size: 100,000 blocks 4x2, S 400,000 x 128, FP32-refined
+        d = block_angular_dense(K=100_000, n=4, m=2, s=128, scale_decades=2.0, dtype=np.float32)
+        K, n, m, s = d["K"], d["n"], d["m"], d["s"]
+        ctx = Context(dev.index, stream=stream, precision="fp32_refined")
+        ctx.plan_blocks(np.full(K, n), np.full(K, m), qrkit.COUPLED_DENSE, shared_cols=s)
+        J = torch.from_numpy(np.concatenate([d["blocks"][i].T.reshape(-1) for i in range(K)])).to(dev)
+        S = torch.from_numpy(np.asarray(d["S"]).T.reshape(-1).copy()).to(dev)
+        b = torch.from_numpy(np.asarray(d["b"])).to(dev)
+        pl = torch.empty(K * m + s, dtype=torch.float32, device=dev)
+        torch.cuda.synchronize()
+        tf = _time(stream, lambda: ctx.factor(J, S, None, d["lam"]), 5)
+        ts = _time(stream, lambda: ctx.solve(b, pl, refine_steps=1), 5)
+        ctx.sync_status()
+        Mred = K * n + s
+        flops = 2.0 * Mred * s * s   # useful flops of the reduced block's Householder QR (leading term)
+        out["dense_hcat_100k_blocks_s128_fp32_refined"] = {
+            "workload": "J = [blkdiag(100,000 blocks 4x2) | S 400,000 x 128], lambda 1e-2, D = norms; "
+                        "reduced block TSQR with tcgen05 3xTF32 trailing updates",
+            "ms_factor": tf, "ms_solve_refined_1": ts, "value": 1000.0 / (tf + ts), "unit": "solves/s",
+            "reduced_block_tflops_useful": flops / (tf * 1e-3) / 1e12}
+        ctx.close()
+        del J, S, b
+    if want("curvefit"):
+        # curve fit, 200,000 points, 2048 control points: LM iterations and fixed-lambda solves
+        cf = {}
+        for prec in ("fp32_refined", "fp32", "fp64"):
+            ctx = Context(dev.index, stream=stream, precision=prec)
+            x, x0, data, npts, kcs = _curvefit_batch(ctx, [(200_000, 2048, 0)], dev, stream)
+            st = ctx.lm_states(1e-3)
+            ctx.lm_run(x, st, max_iter=2, ftol=0.0, refine_steps=1, use_graph=True)
+            it = 10
+            st = ctx.lm_states(1e-3)
+            ms = _time(stream, lambda: ctx.lm_run(x, st, max_iter=it, ftol=0.0, refine_steps=1, use_graph=True), 1,
+                       warm=0) / it
+            cf[f"lm_iteration_{prec}"] = {"ms": ms, "iterations_per_s": 1000.0 / ms}
+            if prec == "fp32_refined":
+                # the linearised system at the start point, solved for several lambda by QR and by
+                # the normal equations (Cholesky)
+                NP = npts[0]
+                with torch.cuda.stream(stream):
+                    Jl = torch.empty(2 * NP, dtype=torch.float32, device=dev)
+                    Sl = torch.empty(16 * NP, dtype=torch.float32, device=dev)
+                    bl = torch.empty(2 * NP, dtype=torch.float32, device=dev)
+                    stl = torch.empty(NP, dtype=torch.int32, device=dev)
+                    xs = torch.from_numpy(x0).to(dev)
+                    ctx.lm_linearize(xs, Jl, Sl, bl, stl)
+                    stream.synchronize()
+                    starts = stl.cpu().numpy()
+                sctx = Context(dev.index, stream=stream, precision=prec)
+                sctx.plan_blocks(np.full(NP, 2), np.full(NP, 1), qrkit.COUPLED_WINDOW, shared_cols=2 * kcs[0], window=8,
+                                 window_start=starts)
+                pq = torch.empty(NP + 2 * kcs[0], dtype=torch.float32, device=dev)
+                per_lam = {}
+                for lam in (1e-6, 1e-3, 1.0, 1e2):
+                    def qr():
+                        sctx.factor(Jl, Sl, None, lam)
+                        sctx.solve(bl, pq, refine_steps=1)
+                    tq = _time(stream, qr, 5)
+                    tc = _time(stream, lambda: sctx.normal_solve(Jl, Sl, bl, pq, None, lam), 5)
+                    per_lam[f"{lam:g}"] = {"qr_fp32_refined_solves_per_s": 1000.0 / tq, "cholesky_fp32_solves_per_s": 1000.0 / tc}
+                sctx.sync_status()
+                sctx.close()
+                cf["fixed_lambda_solves"] = per_lam
+            ctx.sync_status()
+            ctx.close()
+        out["curvefit_200k_points_2048_control_points"] = {
+            "workload": "open uniform cubic B-spline, 200,000 points (2x1 blocks), 4096 shared columns in windows of 8",
+            **cf}
+    if want("banded_1e6"):
+        # banded + vertical concatenation: one instance of 1,000,000 columns, 4,000,000 rows
+        bp = banded_problem(n=1_000_000, rows_per_col=4, w=8, seed_offset=0)
+        ctx = Context(dev.index, stream=stream, precision="fp32_refined")
+        ctx.plan_banded([1_000_000], rows_per_col=4, window=8)
+        Jb = torch.from_numpy(np.ascontiguousarray(bp["vals"].reshape(-1))).to(dev)
+        bb = torch.from_numpy(bp["b"]).to(dev)
+        xb = torch.empty(1_000_000, dtype=torch.float32, device=dev)
+        torch.cuda.synchronize()
+        t0 = _time(stream, lambda: ctx.factor_solve(Jb, bb, xb, None, lam=1e-3, refine_steps=0), 5)
+        t2 = _time(stream, lambda: ctx.factor_solve(Jb, bb, xb, None, lam=1e-3, refine_steps=2), 5)
+        ctx.sync_status()
+        alg = 4 * (Jb.numel() + bb.numel() + xb.numel())
+        out["banded_1e6_cols_4e6_rows"] = {
+            "workload": "J 4,000,000 x 1,000,000, row i on columns floor(i/4)..+7, lambda 1e-3, D = norms",
+            "value": 1000.0 / t2, "unit": "solves/s", "ms_refined_2": t2, "ms_no_refinement": t0,
+            "roofline": {"bound": "hbm", "algorithmic_bytes": alg, "achieved": alg / (t0 * 1e-3) / 1e9,
+                         "peak": peaks["hbm_gbs"], "peak_kind": peak_kind, "unit": "GB/s",
+                         "frac": alg / (t0 * 1e-3) / 1e9 / peaks["hbm_gbs"],
+                         "note": "factor + solve without refinement; algorithmic bytes = read J and b, write x"}}
+        ctx.close()
+        del Jb, bb, xb
+    if want("banded_batch"):
+        # a batch of banded instances (scaled: 256 instances, n ~ U{1000..10000})
+        cols = banded_batch_shapes(256, 1000, 10000)
+        inst = [banded_problem(n=int(c), rows_per_col=4, w=8, seed_offset=10 + k) for k, c in enumerate(cols)]
+        ctx = Context(dev.index, stream=stream, precision="fp32_refined")
+        ctx.plan_banded(list(cols), rows_per_col=4, window=8)
+        Jv = torch.from_numpy(np.concatenate([q["vals"].reshape(-1) for q in inst])).to(dev)
+        bv = torch.from_numpy(np.concatenate([q["b"] for q in inst])).to(dev)
+        xv = torch.empty(int(np.sum(cols)), dtype=torch.float32, device=dev)
+        torch.cuda.synchronize()
+        tb = _time(stream, lambda: ctx.factor_solve(Jv, bv, xv, None, lam=1e-3, refine_steps=2), 5)
+        ctx.sync_status()
+        out["banded_batch_256_instances"] = {
+            "workload": f"256 banded instances, n ~ U{{1000..10000}} (total {int(np.sum(cols))} columns), 4n rows",
+            "value": 256 * 1000.0 / tb, "unit": "instances/s", "ms": tb}
+        ctx.close()
+    if want("batched_lm"):
+        # batched LM: 1024 curve-fit problems, points ~ U{500..20000}, control points ~ U{16..256}
+        g = np.random.default_rng(5)
+        specs = [(int(g.integers(500, 20001)), int(g.integers(16, 257)), 100 + i) for i in range(1024)]
+        ctx = Context(dev.index, stream=stream, precision="fp32_refined")
+        x, x0, data, npts, kcs = _curvefit_batch(ctx, specs, dev, stream)
         st = ctx.lm_states(1e-3)
         ctx.lm_run(x, st, max_iter=2, ftol=0.0, refine_steps=1, use_graph=True)
-        it = 10
         st = ctx.lm_states(1e-3)
+        it = 5
         ms = _time(stream, lambda: ctx.lm_run(x, st, max_iter=it, ftol=0.0, refine_steps=1, use_graph=True), 1,
                    warm=0) / it
-        cf[f"lm_iteration_{prec}"] = {"ms": ms, "iterations_per_s": 1000.0 / ms}
-        if prec == "fp32_refined":
-            # the linearised system at the start point, solved for several lambda by QR and by
-            # the normal equations (Cholesky)
-            NP = npts[0]
-            with torch.cuda.stream(stream):
-                Jl = torch.empty(2 * NP, dtype=torch.float32, device=dev)
-                Sl = torch.empty(16 * NP, dtype=torch.float32, device=dev)
-                bl = torch.empty(2 * NP, dtype=torch.float32, device=dev)
-                stl = torch.empty(NP, dtype=torch.int32, device=dev)
-                xs = torch.from_numpy(x0).to(dev)
-                ctx.lm_linearize(xs, Jl, Sl, bl, stl)
-                stream.synchronize()
-                starts = stl.cpu().numpy()
-            sctx = Context(dev.index, stream=stream, precision=prec)
-            sctx.plan_blocks(np.full(NP, 2), np.full(NP, 1), qrkit.COUPLED_WINDOW, shared_cols=2 * kcs[0], window=8,
-                             window_start=starts)
-            pq = torch.empty(NP + 2 * kcs[0], dtype=torch.float32, device=dev)
-            per_lam = {}
-            for lam in (1e-6, 1e-3, 1.0, 1e2):
-                def qr():
-                    sctx.factor(Jl, Sl, None, lam)
-                    sctx.solve(bl, pq, refine_steps=1)
-                tq = _time(stream, qr, 5)
-                tc = _time(stream, lambda: sctx.normal_solve(Jl, Sl, bl, pq, None, lam), 5)
-                per_lam[f"{lam:g}"] = {"qr_fp32_refined_solves_per_s": 1000.0 / tq, "cholesky_fp32_solves_per_s": 1000.0 / tc}
-            sctx.sync_status()
-            sctx.close()
-            cf["fixed_lambda_solves"] = per_lam
         ctx.sync_status()
+        out["batched_lm_1024_curvefit_problems"] = {
+            "workload": f"1024 problems, {sum(npts)} points in total, Nielsen damping, CUDA-graph iterations",
+            "value": 1000.0 / ms, "unit": "LM iterations/s (all problems)", "ms_per_iteration": ms}
         ctx.close()
-    out["curvefit_200k_points_2048_control_points"] = {
-        "workload": "open uniform cubic B-spline, 200,000 points (2x1 blocks), 4096 shared columns in windows of 8",
-        **cf}
-    # banded + vertical concatenation: one instance of 1,000,000 columns, 4,000,000 rows
-    bp = banded_problem(n=1_000_000, rows_per_col=4, w=8, seed_offset=0)
-    ctx = Context(dev.index, stream=stream, precision="fp32_refined")
-    ctx.plan_banded([1_000_000], rows_per_col=4, window=8)
-    Jb = torch.from_numpy(np.ascontiguousarray(bp["vals"].reshape(-1))).to(dev)
-    bb = torch.from_numpy(bp["b"]).to(dev)
-    xb = torch.empty(1_000_000, dtype=torch.float32, device=dev)
-    torch.cuda.synchronize()
-    t0 = _time(stream, lambda: ctx.factor_solve(Jb, bb, xb, None, lam=1e-3, refine_steps=0), 5)
-    t2 = _time(stream, lambda: ctx.factor_solve(Jb, bb, xb, None, lam=1e-3, refine_steps=2), 5)
-    ctx.sync_status()
-    alg = 4 * (Jb.numel() + bb.numel() + xb.numel())
-    out["banded_1e6_cols_4e6_rows"] = {
-        "workload": "J 4,000,000 x 1,000,000, row i on columns floor(i/4)..+7, lambda 1e-3, D = norms",
-        "value": 1000.0 / t2, "unit": "solves/s", "ms_refined_2": t2, "ms_no_refinement": t0,
-        "roofline": {"bound": "hbm", "algorithmic_bytes": alg, "achieved": alg / (t0 * 1e-3) / 1e9,
-                     "peak": peaks["hbm_gbs"], "peak_kind": peak_kind, "unit": "GB/s",
-                     "frac": alg / (t0 * 1e-3) / 1e9 / peaks["hbm_gbs"],
-                     "note": "factor + solve without refinement; algorithmic bytes = read J and b, write x"}}
-    ctx.close()
-    del Jb, bb, xb
-    # a batch of banded instances (scaled: 256 instances, n ~ U{1000..10000})
-    cols = banded_batch_shapes(256, 1000, 10000)
-    inst = [banded_problem(n=int(c), rows_per_col=4, w=8, seed_offset=10 + k) for k, c in enumerate(cols)]
-    ctx = Context(dev.index, stream=stream, precision="fp32_refined")
-    ctx.plan_banded(list(cols), rows_per_col=4, window=8)
-    Jv = torch.from_numpy(np.concatenate([q["vals"].reshape(-1) for q in inst])).to(dev)
-    bv = torch.from_numpy(np.concatenate([q["b"] for q in inst])).to(dev)
-    xv = torch.empty(int(np.sum(cols)), dtype=torch.float32, device=dev)
-    torch.cuda.synchronize()
-    tb = _time(stream, lambda: ctx.factor_solve(Jv, bv, xv, None, lam=1e-3, refine_steps=2), 5)
-    ctx.sync_status()
-    out["banded_batch_256_instances"] = {
-        "workload": f"256 banded instances, n ~ U{{1000..10000}} (total {int(np.sum(cols))} columns), 4n rows",
-        "value": 256 * 1000.0 / tb, "unit": "instances/s", "ms": tb}
-    ctx.close()
-    # batched LM: 1024 curve-fit problems, points ~ U{500..20000}, control points ~ U{16..256}
-    g = np.random.default_rng(5)
-    specs = [(int(g.integers(500, 20001)), int(g.integers(16, 257)), 100 + i) for i in range(1024)]
-    ctx = Context(dev.index, stream=stream, precision="fp32_refined")
-    x, x0, data, npts, kcs = _curvefit_batch(ctx, specs, dev, stream)
-    st = ctx.lm_states(1e-3)
-    ctx.lm_run(x, st, max_iter=2, ftol=0.0, refine_steps=1, use_graph=True)
-    st = ctx.lm_states(1e-3)
-    it = 5
-    ms = _time(stream, lambda: ctx.lm_run(x, st, max_iter=it, ftol=0.0, refine_steps=1, use_graph=True), 1,
-               warm=0) / it
-    ctx.sync_status()
-    out["batched_lm_1024_curvefit_problems"] = {
-        "workload": f"1024 problems, {sum(npts)} points in total, Nielsen damping, CUDA-graph iterations",
-        "value": 1000.0 / ms, "unit": "LM iterations/s (all problems)", "ms_per_iteration": ms}
-    ctx.close()
     return out
 
 
@@ -567,11 +575,17 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-refined", action="store_true")
     ap.add_argument("--no-workloads", action="store_true")
+    ap.add_argument("--only-workload", default=None,
+                    help="run only this other workload (key prefix) and print its result; for profiling")
     args = ap.parse_args()
     if args.warmup < 3:
         args.warmup = 3
     if args.impl == "reference":
         run_reference(args)
+    elif args.only_workload:
+        import torch
+        dev = torch.device("cuda", 0)
+        print(json.dumps(other_workloads(dev, torch.cuda.Stream(dev), args.only_workload)), flush=True)
     else:
         run_ours(args)
 
