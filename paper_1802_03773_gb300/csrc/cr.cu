@@ -151,9 +151,138 @@ __device__ __forceinline__ void group_rows(const CRArgs<T>& A, int64_t k, int64_
   }
 }
 
-// 1a. one warp per (block, split): partial triangle of the split's rows.
+// ---- 1. compression of blocks with few rows: one thread per block, rows merged one at a time into an
+// upper-triangular 16 x 16 (+ rhs) block row by 2 x 2 orthogonal rotations (the 2-element
+// Householder reflections of sparse row-merge QR); the triangle lives in shared memory,
+// element-major over the CTA's threads so that a warp's accesses hit distinct banks. ----
+constexpr int kTriElems = 16 * 17 - 120;   // packed upper triangle incl. rhs: rows k = 0..15, cols k..16
+constexpr int kCompThreads = 64;
+
+__host__ __device__ constexpr int tri_off(int k, int j) { return k * 17 - (k * (k - 1)) / 2 + (j - k); }
+
 template <typename T>
-__global__ void __launch_bounds__(128) cr_compress_kernel(CRArgs<T> A) {
+__device__ __forceinline__ void rot_coeffs(T alpha, T beta, T& c, T& s, T& r);
+template <>
+__device__ __forceinline__ void rot_coeffs<float>(float alpha, float beta, float& c, float& s, float& r) {
+  const float n2 = alpha * alpha + beta * beta;
+  const float rr = rsqrtf(n2);
+  c = alpha * rr;
+  s = beta * rr;
+  r = n2 * rr;
+}
+template <>
+__device__ __forceinline__ void rot_coeffs<double>(double alpha, double beta, double& c, double& s, double& r) {
+  r = sqrt(alpha * alpha + beta * beta);
+  c = alpha / r;
+  s = beta / r;
+}
+
+// Merge row a (16 columns + rhs at 16, nonzero from column o on) into the triangle Tr
+// (element e of this thread at Tr[e * kCompThreads]); returns the squared leftover rhs.
+template <typename T>
+__device__ __forceinline__ double merge_row(T* Tr, T (&a)[17], int o) {
+#pragma unroll
+  for (int k = 0; k < 16; ++k) {
+    if (k >= o && a[k] != T(0)) {
+      T c, sn, r;
+      rot_coeffs<T>(Tr[tri_off(k, k) * kCompThreads], a[k], c, sn, r);
+      Tr[tri_off(k, k) * kCompThreads] = r;
+      a[k] = T(0);
+#pragma unroll
+      for (int j = k + 1; j < 17; ++j) {
+        const T t = Tr[tri_off(k, j) * kCompThreads];
+        Tr[tri_off(k, j) * kCompThreads] = c * t + sn * a[j];
+        a[j] = c * a[j] - sn * t;
+      }
+    }
+  }
+  return (double)a[16] * (double)a[16];
+}
+
+template <typename T>
+__device__ __forceinline__ void damping_rows(const CRArgs<T>& A, T* Tr, int64_t g, int64_t N, int64_t c0,
+                                             double& res) {
+  const bool damp = A.lam > 0.0;
+  const double lam_half = sqrt(A.lam);
+#pragma unroll 1
+  for (int q = 0; q < kCB; ++q) {
+    const int64_t col = (int64_t)kCB * g + q;
+    T v = T(0);
+    if (col >= N) v = T(1);   // padding column: unit row
+    else if (damp) v = (T)(lam_half * A.D[c0 + col]);
+    T a[17];
+#pragma unroll
+    for (int j = 0; j < 17; ++j) a[j] = j == q ? v : T(0);
+    res += merge_row(Tr, a, q);
+  }
+}
+
+template <typename T>
+__device__ __forceinline__ void store_block_row(T* dst, const T* Tr) {
+  // 16 rows x (16 + rhs), zeros below the diagonal
+#pragma unroll
+  for (int k = 0; k < 16; ++k)
+#pragma unroll
+    for (int j = 0; j < 17; ++j) dst[k * kEW + j] = j >= k ? Tr[tri_off(k, j) * kCompThreads] : T(0);
+}
+
+template <typename T>
+__global__ void __launch_bounds__(kCompThreads) cr_compress_kernel(CRArgs<T> A) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  T* Tr = reinterpret_cast<T*>(smem_raw) + threadIdx.x;
+  const int64_t item = (int64_t)blockIdx.x * kCompThreads + threadIdx.x;
+  if (item >= A.total_blocks * A.splits) return;
+  const int64_t gb = item / A.splits;
+  const int s = (int)(item - gb * A.splits);
+  const int64_t k = inst_of_block(A.blk0, A.num_inst, gb);
+  const int64_t g = gb - A.blk0[k];
+  const int64_t N = A.cols[k], c0 = A.col0[k];
+  int64_t lo, hi;
+  group_rows(A, k, g, gb, lo, hi);
+  const int64_t len = hi - lo;
+  const int64_t r_begin = lo + len * s / A.splits, r_end = lo + len * (s + 1) / A.splits;
+#pragma unroll
+  for (int e = 0; e < kTriElems; ++e) Tr[e * kCompThreads] = T(0);
+  double res = 0.0;
+  bool bad = false;
+#pragma unroll 1
+  for (int64_t r = r_begin; r < r_end; ++r) {
+    const int64_t st = A.starts ? A.starts[r] - c0 : (r - A.row0[k]) / A.rpc;
+    const int64_t o = st - (int64_t)kCB * g;
+    if (o < 0 || o >= kCB) {
+      bad = true;
+      continue;
+    }
+    T a[17];
+#pragma unroll
+    for (int j = 0; j < 17; ++j) a[j] = T(0);
+    const T* src = A.J + r * A.w;
+#pragma unroll
+    for (int q = 0; q < kCB; ++q)
+      if (q < A.w && st + q < N) {
+#pragma unroll
+        for (int cc = 0; cc < 2 * kCB; ++cc)
+          if (cc == (int)o + q) a[cc] = src[q];
+      }
+    a[16] = A.b[r];
+    res += merge_row(Tr, a, (int)o);
+  }
+  if (bad) cr_record(A.status, QRKIT_EINVAL);
+  if (A.splits == 1) {
+    // the block's damping rows complete its block row
+    damping_rows(A, Tr, g, N, c0, res);
+    store_block_row(A.F0 + gb * 16 * kEW, Tr);
+  } else {
+    store_block_row(A.P + (gb * A.splits + s) * 16 * kEW, Tr);
+  }
+  if (res != 0.0) atomicAdd(A.res2 + k, res);
+}
+
+// ---- 1'. compression for row-heavy blocks: one warp per (block, split), 16 rows at a time
+// reduced by the warp-level Householder QR (one row per lane); the partial triangles of the
+// splits are merged by one warp per block, with the damping rows. ----
+template <typename T>
+__global__ void __launch_bounds__(128) cr_compress_warp_kernel(CRArgs<T> A) {
   const int64_t item = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (item >= A.total_blocks * A.splits) return;
@@ -213,7 +342,7 @@ __global__ void __launch_bounds__(128) cr_compress_kernel(CRArgs<T> A) {
 
 // 1b. one warp per block: merge the partial triangles and the damping rows into E_g.
 template <typename T>
-__global__ void __launch_bounds__(128) cr_merge_kernel(CRArgs<T> A) {
+__global__ void __launch_bounds__(128) cr_merge_warp_kernel(CRArgs<T> A) {
   const int64_t gb = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
   const int lane = threadIdx.x & 31;
   if (gb >= A.total_blocks) return;
@@ -474,6 +603,7 @@ inline unsigned nblk(int64_t n, int t) { return (unsigned)((n + t - 1) / t); }
 struct CRPlan {
   int64_t num_inst = 0, total_blocks = 0;
   int splits = 1, levels = 0;
+  bool thread_rows = true;   // compression by one thread per block (else one warp per split)
   std::vector<int64_t> lvl_off, lvl_n;     // eliminate / move / last items per level
   std::vector<int64_t> ev_off, ev_n;       // staying (even) blocks per level
   DevBuf tabs, items, evens, grp_lo, P, F0, F1, Rb, xp, hp;
@@ -510,7 +640,10 @@ qrkit_status cr_build(qrkit_ctx* ctx, CRPlan*& out, const std::vector<int64_t>& 
   C.total_blocks = blk0[ni];
   if (C.total_blocks >= ((int64_t)1 << 30)) return fail(ctx, QRKIT_EUNSUPPORTED, "too many column blocks");
   const double per = C.total_blocks ? (double)total_rows / (double)C.total_blocks : 0.0;
-  C.splits = (int)std::min<double>(8.0, std::max<double>(1.0, std::ceil(per / 192.0)));
+  // few rows per column block: one thread per block merges its rows (little work per row);
+  // row-heavy blocks: warps reduce 16 rows at a time, blocks split over several warps
+  C.thread_rows = per <= 64.0;
+  C.splits = C.thread_rows ? 1 : (int)std::min<double>(8.0, std::max<double>(1.0, std::ceil(per / 192.0)));
   // level work lists
   std::vector<std::vector<int64_t>> lv, ev;
   for (int64_t k = 0; k < ni; ++k) {
@@ -617,8 +750,17 @@ static qrkit_status cr_solve_typed(qrkit_ctx* ctx, CRPlan& C, const int64_t* sta
   A.res2 = res2;
   QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(res2, 0, (size_t)C.num_inst * sizeof(double), st));
   if (starts) CR_LAUNCH(ctx, cr_ranges_kernel<T><<<nblk(C.total_blocks, 256), 256, 0, st>>>(A));
-  CR_LAUNCH(ctx, cr_compress_kernel<T><<<nblk(C.total_blocks * C.splits * 32, 128), 128, 0, st>>>(A));
-  CR_LAUNCH(ctx, cr_merge_kernel<T><<<nblk(C.total_blocks * 32, 128), 128, 0, st>>>(A));
+  const size_t tri_smem = (size_t)kTriElems * kCompThreads * sizeof(T);
+  if (tri_smem > 48 * 1024) {
+    QRKIT_CUDA_TRY(ctx, cudaFuncSetAttribute(cr_compress_kernel<T>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)tri_smem));
+  }
+  if (C.thread_rows) {
+    CR_LAUNCH(ctx, cr_compress_kernel<T><<<nblk(C.total_blocks, kCompThreads), kCompThreads, tri_smem, st>>>(A));
+  } else {
+    CR_LAUNCH(ctx, cr_compress_warp_kernel<T><<<nblk(C.total_blocks * C.splits * 32, 128), 128, 0, st>>>(A));
+    CR_LAUNCH(ctx, cr_merge_warp_kernel<T><<<nblk(C.total_blocks * 32, 128), 128, 0, st>>>(A));
+  }
   const int64_t* items = (const int64_t*)C.items.ptr;
   T* Fc = A.F0;
   T* Fn = A.F1;
