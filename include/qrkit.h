@@ -253,6 +253,17 @@ qrkit_status qrkit_set_window_start(qrkit_ctx* ctx, const int32_t* start);
  * reduced-row index).  Asynchronous. */
 qrkit_status qrkit_get_row_order(qrkit_ctx* ctx, int64_t* order);
 
+/* Autotuning (no paper counterpart): times candidate launch configurations for the current
+ * plan on the given inputs (DEVICE buffers as for qrkit_factor_solve; p is overwritten) and
+ * keeps the fastest.  Block plans without coupling: the tile budget of the block kernel;
+ * parallel banded plans: the compression strategy (one thread per column block, or warps with
+ * 1-8 splits).  cache_path (HOST string, may be NULL): a text file with one line per
+ * structure key (GPU name, precision, shape signature) and its choice; a key found there is
+ * applied without timing, a new choice is appended.  chosen (HOST, may be NULL): receives the
+ * choice as text.  Synchronous. */
+qrkit_status qrkit_autotune(qrkit_ctx* ctx, const void* J, const void* b, void* p, int refine_steps,
+                            const char* cache_path, char* chosen, int64_t chosen_len);
+
 /* ---- Levenberg-Marquardt on the device (Sec. 2; Backtrack LM of Sec. 5.2) ----
  * Model QRKIT_MODEL_CURVEFIT: 2-D points fitted by an open uniform cubic B-spline; each
  * point has one latent curve parameter t_i and the control points are shared, so J is

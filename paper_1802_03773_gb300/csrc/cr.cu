@@ -706,6 +706,13 @@ qrkit_status cr_build(qrkit_ctx* ctx, CRPlan*& out, const std::vector<int64_t>& 
   return QRKIT_OK;
 }
 
+qrkit_status cr_set_strategy(qrkit_ctx* ctx, CRPlan& C, bool thread_rows, int splits) {
+  if (splits < 1 || splits > 64) return fail(ctx, QRKIT_EINVAL, "splits must be in [1, 64]");
+  C.thread_rows = thread_rows;
+  C.splits = thread_rows ? 1 : splits;
+  return ensure(ctx, C.P, (size_t)C.total_blocks * C.splits * 16 * kEW * elem_size(ctx), "banded partial triangles");
+}
+
 template <typename T>
 static CRArgs<T> cr_args(qrkit_ctx* ctx, CRPlan& C) {
   CRArgs<T> A{};

@@ -158,6 +158,9 @@ qrkit_status cr_build(qrkit_ctx* ctx, CRPlan*& out, const std::vector<int64_t>& 
 // implicit starts floor(i / rpc); damping rows lambda^(1/2) D_j; x and D by global column.
 qrkit_status cr_solve(qrkit_ctx* ctx, CRPlan& C, const int64_t* starts, int rpc, int w, const void* J,
                       const void* b, const double* D, double lambda, void* x, double* res2);
+// Compression strategy of the parallel banded QR: one thread per column block, or warps
+// with `splits` splits per block (autotuning).
+qrkit_status cr_set_strategy(qrkit_ctx* ctx, CRPlan& C, bool thread_rows, int splits);
 // dx = R^{-1} R^{-T} g with the factor of the last cr_solve (g double, dx by global column).
 qrkit_status cr_normal_solve(qrkit_ctx* ctx, CRPlan& C, const double* g, void* dx);
 

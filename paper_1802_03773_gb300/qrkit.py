@@ -109,6 +109,8 @@ _SIGS = {
     "qrkit_lm_residual": (ctypes.c_int, [_VP, _VP, _VP]),
     "qrkit_lm_linearize": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, _VP]),
     "qrkit_lm_features": (ctypes.c_int, [_VP, _VP]),
+    "qrkit_autotune": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_char_p, ctypes.c_char_p,
+                                       ctypes.c_int64]),
     "qrkit_sync_status": (ctypes.c_int, [_VP]),
     "qrkit_block_solve_noalloc": (ctypes.c_int, [ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int64, _VP,
                                                  _VP, _VP, _VP, _VP, ctypes.c_int]),
@@ -387,6 +389,14 @@ class Context:
 
     def lm_features(self, out):
         self._check(self.lib.qrkit_lm_features(self.h, self._f32(out, "features")))
+
+    def autotune(self, J, b, p, refine_steps=2, cache_path=None):
+        """Time candidate launch configurations for the current plan; returns the choice."""
+        buf = ctypes.create_string_buffer(256)
+        path = None if cache_path is None else os.fsencode(cache_path)
+        self._check(self.lib.qrkit_autotune(self.h, self._t(J, "J"), self._t(b, "b"), self._t(p, "p"),
+                                            int(refine_steps), path, buf, 256))
+        return buf.value.decode()
 
     def sync_status(self):
         self._check(self.lib.qrkit_sync_status(self.h))
