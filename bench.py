@@ -40,10 +40,8 @@ KERNEL_SRC = os.path.join(ROOT, "paper_1802_03773_gb300", "csrc", "block_solve.c
 
 
 def dist_env():
-    ws = int(os.environ.get("WORLD_SIZE", "1"))
-    rank = int(os.environ.get("RANK", "0"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
-    return ws, rank, local
+    from paper_1802_03773_gb300.replicas import dist_env as env
+    return env()
 
 
 def algorithmic_bytes(d, elem=4, with_qtb=False):
@@ -451,9 +449,8 @@ def run_ours(args):
     if ws > 1:
         import torch.distributed as dist
         dist.barrier()
-        t = torch.tensor([total_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
+        from paper_1802_03773_gb300.replicas import max_over_ranks
+        total_ms = max_over_ranks(total_ms, dev)
 
     # end-to-end through the public API with host buffers: pinned H2D of J and b, the solve,
     # D2H of p, all inside the timed region
