@@ -35,8 +35,10 @@ METRIC = "LM-step QR solves/s and HBM-roofline % at rel err ≤1e-5 vs FP64 orac
 UNIT = "solves/s"
 K_BLOCKS = 1_000_000
 WORKLOAD = "batched block-diagonal QR solve: 1,000,000 blocks n~U{2..16}, m~U{1..min(n,6)}, FP32-refined"
-KERNEL = "block_solve_kernel + block_refine_kernel (one solve)"
-KERNEL_SRC = os.path.join(ROOT, "paper_1802_03773_gb300", "csrc", "block_solve.cu")
+KERNEL = "block_task_kernel + block_task_refine_kernel (one solve)"
+KERNEL_SRCS = [os.path.join(ROOT, "paper_1802_03773_gb300", "csrc", f)
+               for f in ("block_tasks.cuh", "block_tasks.cu", "block_tasks_f32sel.cu", "block_tasks_refine.cu",
+                         "device_util.cuh")]
 
 
 def dist_env():
@@ -63,12 +65,15 @@ def measured_peaks():
 def recorded_traffic():
     """DRAM bytes of one solve (the launches of its kernels) from the committed ncu summary,
     if it was taken on the current kernel source (else None)."""
-    p = os.path.join(ROOT, "profiles", "block_solve_kernel_1m_blocks.json")
+    p = os.path.join(ROOT, "profiles", "block_task_kernel_1m_blocks.json")
     if not os.path.exists(p):
         return None
     with open(p) as f:
         rec = json.load(f)
-    h = hashlib.sha256(open(KERNEL_SRC, "rb").read()).hexdigest()
+    sha = hashlib.sha256()
+    for f in KERNEL_SRCS:
+        sha.update(open(f, "rb").read())
+    h = sha.hexdigest()
     if rec.get("kernel_source_sha256") != h:
         return None
     v = rec.get("dram_bytes_per_launch")
@@ -412,8 +417,12 @@ def run_ours(args):
     torch.cuda.synchronize()   # inputs copied on the default stream before the context's stream reads them
     refine = args.refine_steps
 
-    # the tile budget of the block kernel, chosen by the library's autotuner on these inputs
-    tuned = ctx.autotune(Js[0], bs[0], p, refine_steps=refine)
+    # the block-to-warp mapping, chosen by the library's autotuner on these inputs (or given)
+    if args.tuning:
+        tuned = args.tuning.replace(",", " ")
+        ctx.apply_tuning(tuned)
+    else:
+        tuned = ctx.autotune(Js[0], bs[0], p, refine_steps=refine)
 
     def step(i):
         ctx.factor_solve(Js[i & 1], bs[i & 1], p, None, refine_steps=refine)
@@ -485,6 +494,7 @@ def run_ours(args):
         other = "fp32" if args.precision == "fp32_refined" else "fp32_refined"
         rctx = Context(local, stream=stream, precision=other)
         rctx.plan_blocks(d["n"], d["m"])
+        rctx.apply_tuning(tuned)
         pr = torch.empty_like(p)
         with torch.cuda.stream(stream):
             for i in range(3):
@@ -576,6 +586,9 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-refined", action="store_true")
     ap.add_argument("--no-workloads", action="store_true")
+    ap.add_argument("--tuning", default=None,
+                    help="apply this block mapping (text form of the autotuner's choice, commas for spaces) "
+                         "instead of autotuning")
     ap.add_argument("--only-workload", default=None,
                     help="run only this other workload (key prefix) and print its result; for profiling")
     args = ap.parse_args()

@@ -255,14 +255,21 @@ qrkit_status qrkit_get_row_order(qrkit_ctx* ctx, int64_t* order);
 
 /* Autotuning (no paper counterpart): times candidate launch configurations for the current
  * plan on the given inputs (DEVICE buffers as for qrkit_factor_solve; p is overwritten) and
- * keeps the fastest.  Block plans without coupling: the tile budget of the block kernel;
- * parallel banded plans: the compression strategy (one thread per column block, or warps with
- * 1-8 splits).  cache_path (HOST string, may be NULL): a text file with one line per
+ * keeps the fastest.  Block plans without coupling: the block-to-warp mapping of the fused
+ * solve, "tasks <supertile> <warps per CTA>" (shape-uniform warp tasks, the default) or
+ * "budget <blocks> <values> <rows> <cols> <padded>" (tiles of consecutive blocks); parallel
+ * banded plans: the compression strategy "compress <thread rows 0/1> <splits>" (one thread per
+ * column block, or warps with 1-8 splits).  cache_path (HOST string, may be NULL): a text file with one line per
  * structure key (GPU name, precision, shape signature) and its choice; a key found there is
  * applied without timing, a new choice is appended.  chosen (HOST, may be NULL): receives the
  * choice as text.  Synchronous. */
 qrkit_status qrkit_autotune(qrkit_ctx* ctx, const void* J, const void* b, void* p, int refine_steps,
                             const char* cache_path, char* chosen, int64_t chosen_len);
+
+/* Apply a configuration in the text form qrkit_autotune returns (HOST string) to the current
+ * plan without timing, e.g. one chosen earlier on the same GPU.  QRKIT_EINVAL if the text does
+ * not parse or does not fit the plan's kind; synchronous. */
+qrkit_status qrkit_apply_tuning(qrkit_ctx* ctx, const char* choice);
 
 /* ---- Levenberg-Marquardt on the device (Sec. 2; Backtrack LM of Sec. 5.2) ----
  * Model QRKIT_MODEL_CURVEFIT: 2-D points fitted by an open uniform cubic B-spline; each

@@ -20,10 +20,13 @@
 #include <mutex>
 #include <type_traits>
 
+#include "device_util.cuh"
 #include "internal.h"
 
 namespace qrkit {
 namespace {
+
+using namespace dev;
 
 constexpr int kMaxRows = 16;   // rows per block (one lane, padded to 4, 8, 12 or 16)
 constexpr int kMaxCols = 8;    // columns per block
@@ -36,79 +39,6 @@ static_assert(kKeys <= 64, "the bin scan handles at most 64 keys");
 template <typename T> struct Vec16;
 template <> struct Vec16<float> { using type = float4; static constexpr int n = 4; };
 template <> struct Vec16<double> { using type = double2; static constexpr int n = 2; };
-
-// ---------------------------------------------------------------------------------------
-// Error-free transformations for the extended-precision residual of the refinement:
-// TwoSum (Knuth) and TwoProduct via FMA (Dekker); every operation uses the _rn intrinsics
-// so the compiler cannot contract or reassociate them.
-__device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
-  s = __fadd_rn(a, b);
-  float bb = __fsub_rn(s, a);
-  e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
-}
-
-__device__ __forceinline__ void record(int* status, int code) {
-  if (status) atomicCAS(status, 0, code);
-}
-
-// ---------------------------------------------------------------------------------------
-// Asynchronous bulk copies (TMA, cp.async.bulk) between global and shared memory with an
-// mbarrier for completion.  Both addresses 16-byte aligned, size a multiple of 16.
-__device__ __forceinline__ uint32_t smem_u32(const void* p) {
-  return (uint32_t)__cvta_generic_to_shared(p);
-}
-__device__ __forceinline__ void mbar_init(uint64_t* bar, int count) {
-  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_u32(bar)), "r"(count)
-               : "memory");
-}
-__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
-  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_u32(bar)),
-               "r"(bytes)
-               : "memory");
-}
-__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
-  uint32_t ok;
-  asm volatile(
-      "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
-      "selp.u32 %0, 1, 0, p;\n\t}"
-      : "=r"(ok)
-      : "r"(smem_u32(bar)), "r"(parity)
-      : "memory");
-  return ok != 0;
-}
-__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes,
-                                         uint64_t* bar) {
-  asm volatile(
-      "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::"r"(
-          smem_u32(dst)),
-      "l"(src), "r"(bytes), "r"(smem_u32(bar))
-      : "memory");
-}
-__device__ __forceinline__ void fence_proxy_async() {
-  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
-}
-
-// The 16-byte-aligned interior [h, h + ni) of the element range [0, count) starting at g.
-template <typename T>
-__device__ __forceinline__ void interior(const T* g, int64_t count, int& h, int& ni) {
-  const uintptr_t a = reinterpret_cast<uintptr_t>(g);
-  const uintptr_t e = a + (uintptr_t)count * sizeof(T);
-  const uintptr_t ab = (a + 15) & ~(uintptr_t)15;
-  const uintptr_t ae = e & ~(uintptr_t)15;
-  if (ae > ab) {
-    h = (int)((ab - a) / sizeof(T));
-    ni = (int)((ae - ab) / sizeof(T));
-  } else {
-    h = (int)count;
-    ni = 0;
-  }
-}
-// Element offset that makes shared[off + k] share global g[k]'s address modulo 16.
-template <typename T>
-__device__ __forceinline__ int align_off(const T* g) {
-  return (int)((reinterpret_cast<uintptr_t>(g) & 15) / sizeof(T));
-}
 
 // Row class of an n-row block: its rows are padded to R = 4 (class + 1) in the working area.
 __host__ __device__ inline int row_class(int n) { return (n - 1) >> 2; }
@@ -240,13 +170,6 @@ __device__ __forceinline__ void st4(double* p, const Row4<double>& r) {
   reinterpret_cast<double2*>(p)[0] = make_double2(r.v[0], r.v[1]);
   reinterpret_cast<double2*>(p)[1] = make_double2(r.v[2], r.v[3]);
 }
-
-// sqrt and reciprocal: the hardware approximations for float (rsqrtf, __frcp_rn: a few ulp
-// at most, far below the rounding the factorization itself accumulates), IEEE for double.
-__device__ __forceinline__ float fsqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
-__device__ __forceinline__ double fsqrt(double x) { return sqrt(x); }
-__device__ __forceinline__ float frcp(float x) { return __frcp_rn(x); }
-__device__ __forceinline__ double frcp(double x) { return 1.0 / x; }
 
 // x = R^{-1} c (R on and above the diagonal of the factor F, column stride cs); one lane.
 template <typename T>
@@ -975,6 +898,7 @@ int block_solve_max_cols() { return kMaxCols; }
 qrkit_status launch_block_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
                                 void* p, void* qtb, int refine_steps) {
   (void)D;
+  if (ctx->plan.mapping == 0 && ctx->plan.num_tasks > 0) return launch_block_tasks(ctx, J, b, p, qtb, refine_steps);
   if (ctx->precision == QRKIT_FP64) return launch_typed<double, false>(ctx, J, b, p, qtb, 0);
   const int steps = ctx->precision == QRKIT_FP32 ? 0 : refine_steps;
   if (steps > 0) return launch_typed<float, false, true>(ctx, J, b, p, qtb, steps);

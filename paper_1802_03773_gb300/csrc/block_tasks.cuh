@@ -1,0 +1,741 @@
+// Device side of the batched block-diagonal QR solve by shape-uniform warp tasks (Sec. 4.1 "Block diagonal",
+// Householder QR of Sec. 2, the compute / Q^T b / R solve interface of Sec. 5.1).
+//
+// Plan (host): the blocks are taken in supertiles of consecutive blocks; inside a supertile
+// they are counting-sorted by shape key (row class c = (n - 1) / 4, column count m) and cut
+// into warp tasks of P = floor(32 / G) blocks of one key, G = c + 1 lanes per block.  Lane q
+// of a block's group holds rows 4q .. 4q + 3 of every column in registers (rows padded to 4G
+// with zeros), so every loop of a warp has the same trip count: no divergence, and no
+// CTA-wide barrier anywhere.  Supertiles keep the blocks that concurrent warps touch (and the
+// neighbours sharing their 32-byte sectors) close in time, so partial sectors meet in L2.
+//
+// Kernels (device): persistent warps, each with its own shared-memory slots and mbarrier,
+// take tasks in a grid stride.  Per task one lane per block issues bulk copies (TMA,
+// cp.async.bulk) of the 16-byte-aligned supersets of the block's J and b; the group factors
+// the block with Householder reflectors H = I - tau v v^T (v[0] = 1, beta = -sign(x0)||x||;
+// norms and dot products are shuffle reductions over the group), applies them to b (Q^T b)
+// and back-substitutes.  The first kernel writes the factor and Q^T b back to the slots and
+// sends them to HBM with bulk stores (unaligned head and tail elements by plain stores);
+// with refinement it also estimates each block's float error a priori and lists the blocks
+// that need refinement, one list per shape key.  The second kernel takes those lists in
+// tasks of the same form, factors the listed blocks again (bit-identical to the first pass)
+// and refines their solutions with a compensated float residual.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include "device_util.cuh"
+#include "internal.h"
+
+namespace qrkit {
+namespace tasks {
+
+using namespace dev;
+
+constexpr float kUnitRoundoff = 5.9604645e-8f;   // 2^-24
+constexpr float kRefineTarget = 1e-6f;           // blocks estimated above this are refined
+constexpr int kMaxCols = 8;
+constexpr int kTaskMaxWarps = 8;   // the kernels are compiled for at most 256 threads per CTA
+#ifndef QRKIT_TASK_CTAS
+#define QRKIT_TASK_CTAS 3   // resident CTAs per SM the float task kernel is compiled for
+#endif
+
+__host__ __device__ constexpr int group_lanes(int key) { return (key >> 3) + 1; }
+__host__ __device__ constexpr int task_blocks(int G) { return 32 / G; }
+// Shared-memory slot of one block's J (or b) in a task: the 16-byte-aligned superset of
+// its values fits with room to spare.
+__host__ __device__ constexpr int slot_j_bytes(int G, int M, int es) {
+  return ((4 * G * M * es + 15) & ~15) + 32;
+}
+__host__ __device__ constexpr int slot_b_bytes(int G, int es) { return ((4 * G * es + 15) & ~15) + 32; }
+
+// ---------------------------------------------------------------------------------------
+// A block's lane group: G consecutive lanes starting at `base`; this lane is row group q.
+// Reductions add in one fixed order, so every lane of a group holds the same bits.
+template <int G>
+struct Group {
+  int base, q;
+  __device__ __forceinline__ explicit Group(int lane) {
+    base = (lane / G) * G;
+    q = G == 1 ? 0 : lane - base;
+  }
+  template <typename T>
+  __device__ __forceinline__ T sum(T v) const {
+    if constexpr (G == 1) {
+      return v;
+    } else if constexpr (G == 2) {
+      return v + __shfl_xor_sync(0xffffffffu, v, 1);
+    } else if constexpr (G == 4) {
+      v += __shfl_xor_sync(0xffffffffu, v, 1);
+      return v + __shfl_xor_sync(0xffffffffu, v, 2);
+    } else {
+      const T v0 = __shfl_sync(0xffffffffu, v, base);
+      const T v1 = __shfl_sync(0xffffffffu, v, base + 1);
+      const T v2 = __shfl_sync(0xffffffffu, v, base + 2);
+      return (v0 + v1) + v2;
+    }
+  }
+  // Sum of compensated pairs (s + c): TwoSum of the leading parts, errors added to c.
+  __device__ __forceinline__ void sum2(float& s, float& c) const {
+    if constexpr (G == 1) {
+      return;
+    } else if constexpr (G == 2 || G == 4) {
+#pragma unroll
+      for (int d = 1; d < G; d <<= 1) {
+        const float s2 = __shfl_xor_sync(0xffffffffu, s, d);
+        const float c2 = __shfl_xor_sync(0xffffffffu, c, d);
+        float t, e;
+        two_sum(s, s2, t, e);
+        s = t;
+        c = __fadd_rn(__fadd_rn(c, c2), e);
+      }
+    } else {
+      const float s0 = __shfl_sync(0xffffffffu, s, base), c0 = __shfl_sync(0xffffffffu, c, base);
+      const float s1 = __shfl_sync(0xffffffffu, s, base + 1), c1 = __shfl_sync(0xffffffffu, c, base + 1);
+      const float s2 = __shfl_sync(0xffffffffu, s, base + 2), c2 = __shfl_sync(0xffffffffu, c, base + 2);
+      float t, e1, t2, e2;
+      two_sum(s0, s1, t, e1);
+      two_sum(t, s2, t2, e2);
+      s = t2;
+      c = __fadd_rn(__fadd_rn(__fadd_rn(c0, c1), c2), __fadd_rn(e1, e2));
+    }
+  }
+  template <typename T>
+  __device__ __forceinline__ T bcast(T v, int src_q) const {
+    if constexpr (G == 1) return v;
+    else return __shfl_sync(0xffffffffu, v, base + src_q);
+  }
+  __device__ __forceinline__ bool owns(int src_q) const {
+    if constexpr (G == 1) return true;
+    else return q == src_q;
+  }
+};
+
+template <int G>
+__host__ __device__ constexpr int kmax() { return 4 * G < kMaxCols ? 4 * G : kMaxCols; }
+
+// The shape keys a task can have: row class 0 (G = 1) with m <= 4, classes 1-3 with m <= 8.
+#define QRKIT_TASK_KEYS(X) \
+  X(0) X(1) X(2) X(3) X(8) X(9) X(10) X(11) X(12) X(13) X(14) X(15) X(16) X(17) X(18) X(19) X(20) \
+  X(21) X(22) X(23) X(24) X(25) X(26) X(27) X(28) X(29) X(30) X(31)
+
+// Reciprocal and square root for the factorizations: the hardware approximations for float
+// (rcp.approx / sqrt.approx: about one ulp, far below the rounding the factorization itself
+// accumulates; zero maps to infinity and to zero), IEEE for double.
+__device__ __forceinline__ float rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double rcp(double x) { return 1.0 / x; }
+__device__ __forceinline__ float root(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double root(double x) { return sqrt(x); }
+
+// Registers of one lane: a[j][u] = row 4q + u of column j (zero below row n), c[u] = rhs.
+template <typename T, int G>
+__device__ __forceinline__ void load_regs(T (&a)[kMaxCols][4], T (&c)[4], const T* sJ, const T* sB,
+                                          int n, int M, int q) {
+#pragma unroll
+  for (int j = 0; j < kmax<G>(); ++j) {
+    if (j < M) {
+      const T* col = sJ + j * n;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[j][u] = 4 * q + u < n ? col[4 * q + u] : T(0);
+    } else {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) a[j][u] = T(0);
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u) c[u] = 4 * q + u < n ? sB[4 * q + u] : T(0);
+}
+
+template <typename T, int G>
+__device__ __forceinline__ void store_regs(const T (&a)[kMaxCols][4], const T (&c)[4], T* sJ, T* sB,
+                                           int n, int M, int q) {
+#pragma unroll
+  for (int j = 0; j < kmax<G>(); ++j) {
+    if (j < M) {
+      T* col = sJ + j * n;
+#pragma unroll
+      for (int u = 0; u < 4; ++u)
+        if (4 * q + u < n) col[4 * q + u] = a[j][u];
+    }
+  }
+#pragma unroll
+  for (int u = 0; u < 4; ++u)
+    if (4 * q + u < n) sB[4 * q + u] = c[u];
+}
+
+// Householder QR of the group's block (Sec. 2) in registers, applied to the rhs on the way:
+// afterwards a holds R on and above the diagonal and the reflectors' v below it (v[0] = 1
+// implicit), c = Q^T b; the reflector coefficients go to tau[0..M) as they are formed
+// (lanes q = k mod G store tau[k]; tau may be null).  M (warp-uniform) columns.
+template <typename T, int G>
+__device__ __forceinline__ void group_householder(T (&a)[kMaxCols][4], T (&c)[4], T* tau, int M,
+                                                  const Group<G>& g) {
+  const int q = g.q;
+#pragma unroll
+  for (int k = 0; k < kmax<G>(); ++k) {
+    if (k < M) {
+      // row k is row ku of lane kq: lanes q > kq hold rows below k only, lane kq the rows
+      // ku + 1 .. 3 below it, lanes q < kq rows above it only
+      const int kq = k >> 2, ku = k & 3;
+      const bool gt = q > kq, ge = q >= kq, eq = q == kq;
+      T full = T(0), tail = T(0);
+#pragma unroll
+      for (int u = 3; u >= 0; --u) {
+        const T s2 = a[k][u] * a[k][u];
+        if (u > ku) tail += s2;
+        full += s2;
+      }
+      const T sq = g.sum(gt ? full : (eq ? tail : T(0)));
+      const T alpha = g.bcast(a[k][ku], kq);
+      const T nrm = root(alpha * alpha + sq);
+      const T beta = alpha >= T(0) ? -nrm : nrm;
+      const T d = alpha - beta;
+      const bool live = nrm != T(0);
+      const T scale = live ? rcp(d) : T(0);
+      const T tk = live ? -d * rcp(beta) : T(0);
+      const T f_ge = ge ? scale : T(0), f_gt = gt ? scale : T(0);
+      T v[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (u > ku) {
+          v[u] = a[k][u] * f_ge;
+          a[k][u] = ge ? v[u] : a[k][u];
+        } else if (u == ku) {
+          v[u] = a[k][u] * f_gt + (eq ? T(1) : T(0));
+          a[k][u] = gt ? v[u] : (eq ? beta : a[k][u]);
+        } else {
+          v[u] = a[k][u] * f_gt;
+          a[k][u] = gt ? v[u] : a[k][u];
+        }
+      }
+      if (tau && (k % G) == q) tau[k] = tk;
+#pragma unroll
+      for (int j = k + 1; j < kmax<G>(); ++j) {
+        if (j < M) {
+          T w = T(0);
+#pragma unroll
+          for (int u = 0; u < 4; ++u) w += v[u] * a[j][u];
+          w = g.sum(w) * tk;
+#pragma unroll
+          for (int u = 0; u < 4; ++u) a[j][u] -= v[u] * w;
+        }
+      }
+      T w = T(0);
+#pragma unroll
+      for (int u = 0; u < 4; ++u) w += v[u] * c[u];
+      w = g.sum(w) * tk;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) c[u] -= v[u] * w;
+    }
+  }
+}
+
+// x = R^{-1} c[0..M): row k of R lives on lane k / 4 of the group, which computes x_k and
+// broadcasts it.  Returns false on the lane that holds a zero pivot.
+template <typename T, int G>
+__device__ __forceinline__ bool group_backsub(const T (&a)[kMaxCols][4], const T (&c)[4], int M,
+                                              const Group<G>& g, T (&x)[kMaxCols]) {
+  bool ok = true;
+#pragma unroll
+  for (int k = kmax<G>() - 1; k >= 0; --k) {
+    if (k < M) {
+      T s = c[k & 3];
+#pragma unroll
+      for (int j = k + 1; j < kmax<G>(); ++j)
+        if (j < M) s -= a[j][k & 3] * x[j];
+      const T rkk = a[k][k & 3];
+      if (g.owns(k >> 2) && rkk == T(0)) ok = false;
+      x[k] = g.bcast(s * rcp(rkk), k >> 2);
+    } else {
+      x[k] = T(0);
+    }
+  }
+  return ok;
+}
+
+// w = R^{-T} v, then v = R^{-1} w, in place (v replicated over the group, R distributed by
+// rows; d = reciprocal diagonal).  R^T is solved column by column of R: each lane keeps the
+// partial sums of its own rows' contributions.
+template <int G>
+__device__ __forceinline__ void group_normal_solve(const float (&a)[kMaxCols][4], const float (&d)[kMaxCols],
+                                                   float (&v)[kMaxCols], int M, const Group<G>& g) {
+  float part[kMaxCols];
+#pragma unroll
+  for (int k = 0; k < kMaxCols; ++k) part[k] = 0.f;
+#pragma unroll
+  for (int k = 0; k < kmax<G>(); ++k) {
+    if (k < M) {
+      const float s = k == 0 ? 0.f : g.sum(part[k]);
+      const float w = (v[k] - s) * d[k];
+      v[k] = w;
+      const bool own = g.owns(k >> 2);
+#pragma unroll
+      for (int j = k + 1; j < kmax<G>(); ++j)
+        if (j < M) part[j] += own ? a[j][k & 3] * w : 0.f;
+    }
+  }
+#pragma unroll
+  for (int k = kmax<G>() - 1; k >= 0; --k) {
+    if (k < M) {
+      float s = v[k];
+#pragma unroll
+      for (int j = k + 1; j < kmax<G>(); ++j)
+        if (j < M) s -= a[j][k & 3] * v[j];
+      v[k] = g.bcast(s, k >> 2) * d[k];
+    }
+  }
+}
+
+template <int G>
+__device__ __forceinline__ void recip_diag(const float (&a)[kMaxCols][4], int M, const Group<G>& g,
+                                           float (&d)[kMaxCols]) {
+#pragma unroll
+  for (int k = 0; k < kMaxCols; ++k) d[k] = 0.f;
+#pragma unroll
+  for (int k = 0; k < kmax<G>(); ++k)
+    if (k < M) d[k] = g.bcast(rcp(a[k][k & 3]), k >> 2);
+}
+
+// A-priori error estimate of the float least-squares solution (Householder QR is backward
+// stable: relative error ~ u (kappa + kappa^2 ||r|| / (||A|| ||x||))), with ||A|| ~ ||R||_F,
+// ||R^{-1}||_2^2 from two power steps v <- R^{-1} R^{-T} v / ||v|| starting from ones, and
+// ||r|| = || rows M.. of Q^T b ||; true when the estimate exceeds kRefineTarget (or is NaN).
+// One lane per block, R read from the factor in its slot (column k at F + k n); res2 = ||r||^2,
+// x2 = ||x||^2.
+__device__ __forceinline__ bool lane_needs_refinement(const float* F, int n, int M, float res2, float x2) {
+  float R[kMaxCols][kMaxCols], d[kMaxCols], v[kMaxCols];
+  float rF2 = 0.f;
+#pragma unroll
+  for (int k = 0; k < kMaxCols; ++k) {
+    d[k] = 0.f;
+    v[k] = 0.f;
+#pragma unroll
+    for (int i = 0; i < kMaxCols; ++i) R[i][k] = 0.f;
+    if (k < M) {
+      const float* col = F + k * n;
+#pragma unroll
+      for (int i = 0; i <= k; ++i) {
+        R[i][k] = col[i];
+        rF2 += R[i][k] * R[i][k];
+      }
+      d[k] = rcp(R[k][k]);
+      v[k] = 1.f;
+    }
+  }
+  float vn2 = (float)M, inv2 = 0.f;
+#pragma unroll
+  for (int it = 0; it < 2; ++it) {
+    const float sc = rsqrtf(vn2);
+#pragma unroll
+    for (int k = 0; k < kMaxCols; ++k) {   // R^T w = v / ||v||
+      if (k < M) {
+        float t = v[k] * sc;
+#pragma unroll
+        for (int i = 0; i < k; ++i) t -= R[i][k] * v[i];
+        v[k] = t * d[k];
+      }
+    }
+#pragma unroll
+    for (int k = kMaxCols - 1; k >= 0; --k) {   // R v' = w
+      if (k < M) {
+        float t = v[k];
+#pragma unroll
+        for (int j = k + 1; j < kMaxCols; ++j)
+          if (j < M) t -= R[k][j] * v[j];
+        v[k] = t * d[k];
+      }
+    }
+    vn2 = 0.f;
+#pragma unroll
+    for (int k = 0; k < kMaxCols; ++k) vn2 += v[k] * v[k];
+    inv2 = sqrtf(vn2);
+  }
+  const float rF = sqrtf(rF2);
+  const float est = kUnitRoundoff * (rF * sqrtf(inv2) + rF * inv2 * sqrtf(res2 / x2));
+  return !(est <= kRefineTarget);
+}
+
+// Refinement of the group's block: g = J^T (b - J x) with the residual in compensated float
+// arithmetic (Dot2 of Ogita, Rump and Oishi: error-free products and sums, value = s + c),
+// then dx = R^{-1} R^{-T} g and x += dx; with the residual taken exactly this is the first
+// step of Bjorck's augmented-system refinement from (x, b - J x).  A block stops once its
+// correction is at most tol relative to x (max norms), after at most `steps` steps.
+template <int G>
+__device__ __forceinline__ void group_refine(const float (&a)[kMaxCols][4], float (&x)[kMaxCols], const float* sJ,
+                                             const float* sB, int n, int M, const Group<G>& g, int steps,
+                                             float tol) {
+  const int q = g.q;
+  float d[kMaxCols];
+  recip_diag<G>(a, M, g, d);
+  bool done = n == 0;
+  for (int step = 0; step < steps; ++step) {
+    if (__all_sync(0xffffffffu, done)) break;
+    float rh[4], rl[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      rh[u] = 4 * q + u < n ? sB[4 * q + u] : 0.f;
+      rl[u] = 0.f;
+    }
+#pragma unroll
+    for (int j = 0; j < kmax<G>(); ++j) {
+      if (j < M) {
+        const float xj = -x[j];
+        const float* col = sJ + j * n;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float aj = 4 * q + u < n ? col[4 * q + u] : 0.f;
+          const float p = __fmul_rn(aj, xj);
+          const float pe = __fmaf_rn(aj, xj, -p);
+          float t, e;
+          two_sum(rh[u], p, t, e);
+          rh[u] = t;
+          rl[u] = __fadd_rn(rl[u], __fadd_rn(e, pe));
+        }
+      }
+    }
+    float h[kMaxCols];
+#pragma unroll
+    for (int j = 0; j < kMaxCols; ++j) h[j] = 0.f;
+#pragma unroll
+    for (int j = 0; j < kmax<G>(); ++j) {
+      if (j < M) {
+        const float* col = sJ + j * n;
+        float s = 0.f, c = 0.f;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          const float aj = 4 * q + u < n ? col[4 * q + u] : 0.f;
+          const float p = __fmul_rn(aj, rh[u]);
+          float pe = __fmaf_rn(aj, rh[u], -p);
+          pe = __fmaf_rn(aj, rl[u], pe);
+          float t, e;
+          two_sum(s, p, t, e);
+          s = t;
+          c = __fadd_rn(c, __fadd_rn(e, pe));
+        }
+        g.sum2(s, c);
+        h[j] = __fadd_rn(s, c);
+      }
+    }
+    group_normal_solve<G>(a, d, h, M, g);
+    float dmax = 0.f, xmax = 0.f;
+#pragma unroll
+    for (int k = 0; k < kmax<G>(); ++k) {
+      if (k < M) {
+        const float xn = x[k] + h[k];
+        dmax = fmaxf(dmax, fabsf(h[k]));
+        xmax = fmaxf(xmax, fabsf(xn));
+        if (!done) x[k] = xn;
+      }
+    }
+    done = done || !(dmax > tol * xmax);
+  }
+}
+
+// ---------------------------------------------------------------------------------------
+// Staging of one task: lane q = 0 of each group issues the bulk copies of its block's J
+// and b supersets (or, where a superset would leave the caller's buffers, the group loads
+// the values with plain loads); all lanes wait on the warp's mbarrier with a bounded poll.
+template <typename T, int G>
+__device__ __forceinline__ bool stage_task(const T* gJ, const T* gB, int n, int M, bool act, int grp, int q,
+                                           int lane, const T* J_lo, const T* J_hi, const T* b_lo,
+                                           const T* b_hi, unsigned char* wb, uint64_t* bar, uint32_t& phase,
+                                           long long wait_limit, int* status, T*& sJ, T*& sB) {
+  constexpr int P = task_blocks(G);
+  constexpr int es = (int)sizeof(T);
+  const int JS = slot_j_bytes(G, M, es);
+  constexpr int BS = slot_b_bytes(G, es);
+  unsigned char* sJraw = wb + (act ? grp : 0) * JS;
+  unsigned char* sBraw = wb + P * JS + (act ? grp : 0) * BS;
+  const int nv = n * M;
+  const uintptr_t aJ = reinterpret_cast<uintptr_t>(gJ), aB = reinterpret_cast<uintptr_t>(gB);
+  const uintptr_t lJ = aJ & ~(uintptr_t)15, hJ = (aJ + (uintptr_t)nv * es + 15) & ~(uintptr_t)15;
+  const uintptr_t lB = aB & ~(uintptr_t)15, hB = (aB + (uintptr_t)n * es + 15) & ~(uintptr_t)15;
+  const bool bJ = n > 0 && lJ >= reinterpret_cast<uintptr_t>(J_lo) && hJ <= reinterpret_cast<uintptr_t>(J_hi) &&
+                  hJ - lJ <= (uintptr_t)JS;
+  const bool bB = n > 0 && lB >= reinterpret_cast<uintptr_t>(b_lo) && hB <= reinterpret_cast<uintptr_t>(b_hi) &&
+                  hB - lB <= (uintptr_t)BS;
+  const uint32_t mine = q == 0 ? (uint32_t)((bJ ? hJ - lJ : 0) + (bB ? hB - lB : 0)) : 0u;
+  const uint32_t total = __reduce_add_sync(0xffffffffu, mine);
+  // the slots are free once this warp's earlier bulk stores have read them and every lane's
+  // generic accesses are ordered before the copies
+  bulk_wait_read();
+  fence_proxy_async();
+  __syncwarp();
+  if (lane == 0) mbar_expect_tx(bar, total);
+  __syncwarp();
+  if (q == 0 && bJ) bulk_g2s(sJraw, reinterpret_cast<const void*>(lJ), (uint32_t)(hJ - lJ), bar);
+  if (q == 0 && bB) bulk_g2s(sBraw, reinterpret_cast<const void*>(lB), (uint32_t)(hB - lB), bar);
+  sJ = reinterpret_cast<T*>(sJraw + (aJ & 15));
+  sB = reinterpret_cast<T*>(sBraw + (aB & 15));
+  if (n > 0 && !bJ)
+    for (int k = q; k < nv; k += G) sJ[k] = gJ[k];
+  if (n > 0 && !bB)
+    for (int k = q; k < n; k += G) sB[k] = gB[k];
+  bool ok = false;
+  for (long long polls = 0; polls < wait_limit; ++polls) {
+    if (mbar_try_wait(bar, phase)) {
+      ok = true;
+      break;
+    }
+  }
+  phase ^= 1u;
+  if (!__all_sync(0xffffffffu, ok)) {
+    if (lane == 0) record(status, QRKIT_ETIMEOUT);
+    return false;
+  }
+  __syncwarp();
+  return true;
+}
+
+// Copy of count elements from a slot to global memory that agree modulo 16 bytes: bulk
+// store of the aligned interior by lane q = 0, head and tail by the group's lanes.
+template <typename T, int G>
+__device__ __forceinline__ void send(T* dst, const T* src, int count, bool bulk, int q) {
+  if (!bulk) {
+    for (int k = q; k < count; k += G) dst[k] = src[k];
+    return;
+  }
+  int h, ni;
+  interior(dst, count, h, ni);
+  if (q == 0 && ni > 0) bulk_s2g(dst + h, src + h, (uint32_t)(ni * sizeof(T)));
+  for (int k = q; k < h; k += G) dst[k] = src[k];
+  for (int k = h + ni + q; k < count; k += G) dst[k] = src[k];
+}
+
+template <typename T>
+struct TaskArgs {
+  const TaskHdr* hdr;
+  const TaskEntry* ent;
+  int64_t num_tasks;
+  const T* J;
+  const T* b;
+  const T* J_end;   // one past the last value (bounds of the bulk supersets)
+  const T* b_end;
+  T* F;             // factor, J packing
+  T* tau;
+  T* qtb;           // may be null
+  T* x;
+  int f_bulk;       // F agrees with J modulo 16 bytes: factor leaves by bulk stores
+  int q_bulk;       // qtb agrees with b modulo 16 bytes
+  int warp_bytes;   // shared memory per warp (slots)
+  long long wait_limit;
+  int* status;
+  int* rlist;               // selection: blocks to refine, one list per shape key
+  int* rcount;              // kTaskKeys counts
+  const int64_t* key_off;   // kTaskKeys + 1 list offsets (list capacity = blocks of the key)
+};
+
+// One task of shape key (G, M): M is a compile-time constant, so every loop bound and guard of
+// the inlined helpers folds away.
+template <typename T, int G, int M, bool SEL>
+__device__ __forceinline__ bool run_task(const TaskArgs<T>& A, const TaskHdr& h, unsigned char* wb,
+                                         uint64_t* bar, uint32_t& phase, int lane) {
+  constexpr int P = task_blocks(G);
+  const int grp = lane / G;
+  const bool act = grp < P;
+  const Group<G> g(lane);
+  TaskEntry e{};
+  if (act) e = A.ent[h.first + grp];
+  const int n = e.n;
+  const T* gJ = A.J + h.v0 + e.v;
+  const T* gB = A.b + h.r0 + e.r;
+  T* sJ;
+  T* sB;
+  if (!stage_task<T, G>(gJ, gB, n, M, act, grp, g.q, lane, A.J, A.J_end, A.b, A.b_end, wb, bar, phase,
+                        A.wait_limit, A.status, sJ, sB))
+    return false;
+  T a[kMaxCols][4], c[4], x[kMaxCols];
+  load_regs<T, G>(a, c, sJ, sB, n, M, g.q);
+  group_householder<T, G>(a, c, n > 0 ? A.tau + h.c0 + e.c : nullptr, M, g);
+  store_regs<T, G>(a, c, sJ, sB, n, M, g.q);
+  if (!group_backsub<T, G>(a, c, M, g, x) && n > 0) record(A.status, QRKIT_ESINGULAR);
+  T x2 = T(0);
+  if (n > 0) {
+    T* dx = A.x + h.c0 + e.c;
+#pragma unroll
+    for (int k = 0; k < kmax<G>(); ++k)
+      if (k < M && (k % G) == g.q) dx[k] = x[k];
+  }
+#pragma unroll
+  for (int k = 0; k < kmax<G>(); ++k)
+    if (k < M) x2 += x[k] * x[k];
+  bool need = false;
+  if constexpr (SEL) {
+    float res2 = 0.f;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = 4 * g.q + u;
+      res2 += (r >= M && r < n) ? (float)(c[u] * c[u]) : 0.f;
+    }
+    res2 = g.sum(res2);
+    __syncwarp();   // the factor's rows from every lane of the group are in the slot
+    if (g.q == 0 && n > 0) need = lane_needs_refinement((const float*)sJ, n, M, res2, (float)x2);
+  }
+  // factor and Q^T b from the slots to HBM
+  fence_proxy_async();
+  __syncwarp();
+  if (n > 0) {
+    send<T, G>(A.F + h.v0 + e.v, sJ, n * M, A.f_bulk != 0, g.q);
+    if (A.qtb) send<T, G>(A.qtb + h.r0 + e.r, sB, n, A.q_bulk != 0, g.q);
+  }
+  if (g.q == 0) bulk_commit();
+  if constexpr (SEL) {
+    const bool sel = act && g.q == 0 && n > 0 && need;
+    const unsigned mask = __ballot_sync(0xffffffffu, sel);
+    if (mask) {
+      int first = 0;
+      if (lane == 0) first = atomicAdd(A.rcount + h.key, __popc(mask));
+      first = __shfl_sync(0xffffffffu, first, 0);
+      if (sel) {
+        const int64_t pos = (int64_t)first + __popc(mask & ((1u << lane) - 1u));
+        const int64_t cap = A.key_off[h.key + 1] - A.key_off[h.key];
+        if (pos < cap) A.rlist[A.key_off[h.key] + pos] = (int)(h.b0 + e.blk);
+      }
+    }
+  }
+  return true;
+}
+
+template <typename T, bool SEL>
+__global__ void __launch_bounds__(32 * kTaskMaxWarps, sizeof(T) == 4 ? QRKIT_TASK_CTAS : 2) block_task_kernel(TaskArgs<T> A) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  unsigned char* wb = smem_raw + (size_t)wid * A.warp_bytes;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + (size_t)wpc * A.warp_bytes) + wid;
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  uint32_t phase = 0;
+  for (int64_t t = (int64_t)blockIdx.x * wpc + wid; t < A.num_tasks; t += (int64_t)gridDim.x * wpc) {
+    const TaskHdr h = A.hdr[t];
+    bool ok = true;
+    switch (h.key) {
+#define QRKIT_TASK_CASE(k) \
+  case k: ok = run_task<T, ((k) >> 3) + 1, ((k) & 7) + 1, SEL>(A, h, wb, bar, phase, lane); break;
+      QRKIT_TASK_KEYS(QRKIT_TASK_CASE)
+#undef QRKIT_TASK_CASE
+      default: if (lane == 0) record(A.status, QRKIT_EINVAL); break;
+    }
+    if (!ok) break;
+  }
+  bulk_wait_all();
+}
+
+// ---------------------------------------------------------------------------------------
+// Refinement of the listed blocks (float).
+struct RefineTaskArgs {
+  const uint8_t* n;
+  const int64_t* val_off;
+  const int64_t* row_off;
+  const int64_t* col_off;
+  const float* J;
+  const float* b;
+  const float* J_end;
+  const float* b_end;
+  float* x;
+  const int* rlist;
+  const int* rcount;
+  const int64_t* key_off;
+  int steps;
+  float tol;
+  int warp_bytes;
+  long long wait_limit;
+  int* status;
+};
+
+template <int G, int M>
+__device__ __forceinline__ bool refine_task(const RefineTaskArgs& A, int key, int64_t local, unsigned char* wb,
+                                            uint64_t* bar, uint32_t& phase, int lane) {
+  constexpr int P = task_blocks(G);
+  const int grp = lane / G;
+  const bool act = grp < P;
+  const Group<G> g(lane);
+  const int64_t cap = A.key_off[key + 1] - A.key_off[key];
+  const int64_t cnt = (int64_t)A.rcount[key] < cap ? (int64_t)A.rcount[key] : cap;
+  const int64_t idx = local * P + grp;
+  int64_t bi = -1;
+  if (act && idx < cnt) bi = A.rlist[A.key_off[key] + idx];
+  const int n = bi >= 0 ? A.n[bi] : 0;
+  const float* gJ = A.J + (bi >= 0 ? A.val_off[bi] : 0);
+  const float* gB = A.b + (bi >= 0 ? A.row_off[bi] : 0);
+  float* sJ;
+  float* sB;
+  if (!stage_task<float, G>(gJ, gB, n, M, act, grp, g.q, lane, A.J, A.J_end, A.b, A.b_end, wb, bar, phase,
+                            A.wait_limit, A.status, sJ, sB))
+    return false;
+  float a[kMaxCols][4], c[4], x[kMaxCols];
+  load_regs<float, G>(a, c, sJ, sB, n, M, g.q);
+  group_householder<float, G>(a, c, nullptr, M, g);
+  group_backsub<float, G>(a, c, M, g, x);
+  group_refine<G>(a, x, sJ, sB, n, M, g, A.steps, A.tol);
+  if (n > 0) {
+    float* dx = A.x + A.col_off[bi];
+#pragma unroll
+    for (int k = 0; k < kmax<G>(); ++k)
+      if (k < M && (k % G) == g.q) dx[k] = x[k];
+  }
+  return true;
+}
+
+template <int kUnused>
+__global__ void __launch_bounds__(32 * kTaskMaxWarps, 2) block_task_refine_kernel(RefineTaskArgs A) {
+  extern __shared__ __align__(128) unsigned char smem_raw[];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpc = blockDim.x >> 5;
+  unsigned char* wb = smem_raw + (size_t)wid * A.warp_bytes;
+  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + (size_t)wpc * A.warp_bytes) + wid;
+  if (lane == 0) {
+    mbar_init(bar, 1);
+    fence_mbar_init();
+  }
+  __syncwarp();
+  // tasks per shape key (lane k: key k), their exclusive prefix sums over the keys
+  const int64_t cap = A.key_off[lane + 1] - A.key_off[lane];
+  const int64_t cnt = (int64_t)A.rcount[lane] < cap ? (int64_t)A.rcount[lane] : cap;
+  const int64_t per = task_blocks(group_lanes(lane));
+  const int64_t tk = (cnt + per - 1) / per;
+  int64_t inc = tk;
+#pragma unroll
+  for (int d = 1; d < 32; d <<= 1) {
+    const int64_t o = __shfl_up_sync(0xffffffffu, inc, d);
+    if (lane >= d) inc += o;
+  }
+  const int64_t start = inc - tk;
+  const int64_t total = __shfl_sync(0xffffffffu, inc, 31);
+  uint32_t phase = 0;
+  for (int64_t t = (int64_t)blockIdx.x * wpc + wid; t < total; t += (int64_t)gridDim.x * wpc) {
+    const int key = 31 - __clz(__ballot_sync(0xffffffffu, start <= t));
+    const int64_t local = t - __shfl_sync(0xffffffffu, start, key);
+    bool ok = true;
+    switch (key) {
+#define QRKIT_REFINE_CASE(k) \
+  case k: ok = refine_task<((k) >> 3) + 1, ((k) & 7) + 1>(A, key, local, wb, bar, phase, lane); break;
+      QRKIT_TASK_KEYS(QRKIT_REFINE_CASE)
+#undef QRKIT_REFINE_CASE
+      default: break;
+    }
+    if (!ok) break;
+  }
+}
+
+// Host-side entry points of the kernels; each is defined by the translation unit that
+// instantiates its kernel (block_tasks_<kind>.cu), so the variants compile in parallel.
+template <typename T, bool SEL>
+cudaError_t kernel_setup(size_t smem, int threads, int* per_sm);
+template <typename T, bool SEL>
+cudaError_t kernel_launch(const TaskArgs<T>& A, unsigned grid, int threads, size_t smem, cudaStream_t st);
+cudaError_t refine_setup(size_t smem, int threads, int* per_sm);
+cudaError_t refine_launch(const RefineTaskArgs& A, unsigned grid, int threads, size_t smem, cudaStream_t st);
+
+}  // namespace tasks
+}  // namespace qrkit

@@ -54,6 +54,7 @@ static qrkit_status upload(qrkit_ctx* ctx, DevBuf& buf, const void* host, size_t
 }
 
 static void release_plan(Plan& P) {
+  release_block_tasks(P);
   release(P.d_val_off);
   release(P.d_row_off);
   release(P.d_col_off);
@@ -177,6 +178,11 @@ static qrkit_status plan_blocks(qrkit_ctx* ctx, const qrkit_structure* s) {
   P.budget = block_solve_budget(elem_size(ctx));
   cut_tiles_for(P);
   qrkit_status st;
+  if (!P.composed) {
+    // the fused solve's default mapping: shape-uniform warp tasks
+    P.mapping = 0;
+    if ((st = build_block_tasks(ctx, kDefaultSupertile, 8, false)) != QRKIT_OK) return st;
+  }
   {
     const size_t ob = (size_t)(P.K + 1) * sizeof(int64_t);
     if ((st = upload(ctx, P.d_val_off, P.val_off.data(), ob, "plan offsets")) != QRKIT_OK) return st;

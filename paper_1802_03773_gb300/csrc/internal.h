@@ -25,6 +25,23 @@ struct TileBudget {
   int padded;   // padded working-area values per tile (rows rounded up to 4, 8 or 16)
 };
 
+// Warp tasks of the batched block solve (block_tasks.cu).  A task is P = floor(32 / G)
+// blocks of one shape key (row class c = (n - 1) / 4, column count m; key = 8 c + m - 1),
+// G = c + 1 lanes per block; entries are relative to the task's supertile bases.
+constexpr int kTaskKeys = 32;
+struct TaskHdr {
+  int64_t v0, r0, c0, b0;   // value, row, column and block offsets of the supertile
+  int64_t first;            // first of the task's P entries
+  int32_t key;
+  int32_t pad;
+};
+struct TaskEntry {
+  uint32_t v, r, c;         // offsets relative to the supertile bases
+  uint16_t blk;             // block index relative to the supertile
+  uint8_t n, m;             // shape; n = 0 marks an unused entry
+};
+static_assert(sizeof(TaskHdr) == 48 && sizeof(TaskEntry) == 16, "task layout");
+
 // A device buffer owned by the context.
 struct DevBuf {
   void* ptr = nullptr;
@@ -55,6 +72,15 @@ struct Plan {
   DevBuf d_n, d_m, d_tile_block, d_tile_val, d_tile_row, d_tile_col;
   DevBuf d_val_off, d_row_off, d_col_off, d_start;
   DevBuf d_seg;   // 2 x (nseg + 1): seg_blk0 then seg_col0
+  // warp tasks (uncoupled block plans): mapping 0 = warp tasks, 1 = tiles (block_solve.cu)
+  int mapping = 0;
+  int64_t supertile = 0;
+  int task_warps = 8;                 // warps per CTA
+  bool key_major = false;             // tasks ordered by shape key first
+  int64_t num_tasks = 0;
+  int64_t max_refine_tasks = 0;       // refinement tasks if every block were selected
+  std::vector<int64_t> key_off;       // kTaskKeys + 1: blocks per key, prefix sums
+  DevBuf d_task_hdr, d_task_ent, d_key_off;
 };
 
 // Read-only view of a block-angular structure and its values (device pointers).
@@ -178,6 +204,7 @@ struct Workspace {
   DevBuf factor;   // factor values (J packing)
   DevBuf tau;      // sum m_i
   DevBuf rlist, rcount;   // blocks selected for refinement (4 row-class lists) and their counts
+  DevBuf tlist, tcount;   // the same for the warp-task kernels (one list per shape key)
 };
 
 }  // namespace qrkit
@@ -197,7 +224,9 @@ struct qrkit_ctx {
   qrkit::Mlp* mlp = nullptr;  // damping-policy MLP (qrkit_mlp_init)
   int* d_status = nullptr;   // device status word
   int64_t launches = 0;
-  size_t smem_attr[8] = {0, 0, 0, 0, 0, 0, 0, 0};   // dynamic smem opted in, per kernel variant
+  size_t smem_attr[16] = {};   // dynamic smem opted in, per kernel variant (slot per kernel)
+  int occ_threads[16] = {};    // threads and resident CTAs per SM at that size (warp-task kernels)
+  int occ_per_sm[16] = {};
   bool factored = false;       // fused block path
   bool comp_factored = false;  // composed path
   bool band_factored = false;  // banded path
@@ -256,6 +285,14 @@ qrkit_status reduced_rhs_sort(qrkit_ctx* ctx, const int64_t* spos, const void* r
 void release_band(Band& B);
 qrkit_status launch_block_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
                                 void* p, void* qtb, int refine_steps);
+// Warp tasks of an uncoupled block plan: build (supertile of consecutive blocks, warps per
+// CTA, task order: supertile-major, or key-major so that concurrent warps run one shape) and
+// launch (factor + Q^T b + solve, then refinement of the selected blocks).
+constexpr int64_t kDefaultSupertile = 65536;
+qrkit_status build_block_tasks(qrkit_ctx* ctx, int64_t supertile, int warps, bool key_major);
+qrkit_status launch_block_tasks(qrkit_ctx* ctx, const void* J, const void* b, void* p, void* qtb,
+                                int refine_steps);
+void release_block_tasks(Plan& P);
 
 }  // namespace qrkit
 

@@ -1,8 +1,10 @@
 // Autotuning of launch configurations for the current plan, with a persistent text cache.
 //
-// Block plans (QRKIT_STRUCT_BLOCKS, no coupling): the tile budget of the persistent block
-// kernel (blocks / values / rows / columns / padded working area per tile), which sets the
-// tile count, the work per barrier phase and the shared memory per CTA.  Banded plans: the
+// Block plans (QRKIT_STRUCT_BLOCKS, no coupling): the block-to-warp mapping of the fused
+// solve: shape-uniform warp tasks (supertile of consecutive blocks sorted by shape, warps per
+// CTA) or tiles of consecutive blocks (blocks / values / rows / columns / padded working area
+// per tile, which set the tile count, the work per barrier phase and the shared memory per
+// CTA).  Banded plans: the
 // compression strategy of the parallel banded QR (one thread per column block, or warps with
 // a number of splits).  Every candidate is timed with CUDA events on the context's stream on
 // the caller's inputs (one warm-up, three timed runs), the fastest is kept.  The cache holds
@@ -45,7 +47,7 @@ uint64_t shape_hash(const Plan& P) {
 std::string plan_key(const qrkit_ctx* ctx) {
   const Plan& P = ctx->plan;
   std::ostringstream k;
-  k << gpu_name(ctx->device) << ":prec" << ctx->precision << ":";
+  k << "v2:" << gpu_name(ctx->device) << ":prec" << ctx->precision << ":";
   if (P.s.kind == QRKIT_STRUCT_BANDED) {
     const Band& B = ctx->band;
     k << "banded:inst" << B.num_inst << ":cols" << B.total_cols << ":rpc" << B.rows_per_col << ":w" << B.w;
@@ -112,6 +114,7 @@ qrkit_status apply_budget(qrkit_ctx* ctx, const TileBudget& t) {
   if (t.blocks < 1 || t.values < 16 * 8 || t.rows < 16 || t.cols < 8 || t.padded < pad_max)
     return fail(ctx, QRKIT_EINVAL, "tile budget too small");
   P.budget = t;
+  P.mapping = 1;
   cut_tiles_for(P);
   const size_t tb = (size_t)(P.num_tiles + 1) * sizeof(int64_t);
   qrkit_status st;
@@ -126,6 +129,67 @@ qrkit_status apply_budget(qrkit_ctx* ctx, const TileBudget& t) {
   if ((st = up(P.d_tile_row, P.tile_row)) != QRKIT_OK) return st;
   if ((st = up(P.d_tile_col, P.tile_col)) != QRKIT_OK) return st;
   return QRKIT_OK;
+}
+
+// Block mapping choices: "tasks <supertile> <warps per CTA> [<key-major 0/1>]" or
+// "budget <tile budget>".
+struct BlockChoice {
+  bool tasks = true;
+  int64_t supertile = kDefaultSupertile;
+  int warps = 8;
+  int key_major = 0;
+  TileBudget budget{};
+};
+
+std::string choice_str(const BlockChoice& c) {
+  if (!c.tasks) return budget_str(c.budget);
+  std::ostringstream s;
+  s << "tasks " << c.supertile << " " << c.warps << " " << c.key_major;
+  return s.str();
+}
+
+bool parse_choice(const std::string& v, BlockChoice& c) {
+  if (v.compare(0, 7, "budget ") == 0) {
+    c.tasks = false;
+    return parse_budget(v, c.budget);
+  }
+  std::istringstream s(v);
+  std::string tag;
+  s >> tag >> c.supertile >> c.warps;
+  c.tasks = true;
+  if (tag != "tasks" || s.fail()) return false;
+  int km = 0;
+  if (s >> km) c.key_major = km != 0;   // optional, supertile-major by default
+  return true;
+}
+
+qrkit_status apply_choice(qrkit_ctx* ctx, const BlockChoice& c) {
+  if (!c.tasks) return apply_budget(ctx, c.budget);
+  qrkit_status st = build_block_tasks(ctx, c.supertile, c.warps, c.key_major != 0);
+  if (st == QRKIT_OK) ctx->plan.mapping = 0;
+  return st;
+}
+
+std::vector<BlockChoice> block_candidates(size_t elem) {
+  std::vector<BlockChoice> c;
+  for (const int km : {0, 1})
+    for (const int64_t s : {kDefaultSupertile, (int64_t)4096, (int64_t)16384}) {
+      BlockChoice t;
+      t.supertile = s;
+      t.key_major = km;
+      c.push_back(t);
+    }
+  BlockChoice w4;
+  w4.warps = 4;
+  w4.key_major = 0;
+  c.push_back(w4);
+  for (const TileBudget& b : budget_candidates(elem)) {
+    BlockChoice t;
+    t.tasks = false;
+    t.budget = b;
+    c.push_back(t);
+  }
+  return c;
 }
 
 template <typename F>
@@ -163,24 +227,24 @@ extern "C" qrkit_status qrkit_autotune(qrkit_ctx* ctx, const void* J, const void
   qrkit_status st = QRKIT_OK;
   if (P.s.kind == QRKIT_STRUCT_BLOCKS) {
     if (P.composed) return fail(ctx, QRKIT_EUNSUPPORTED, "qrkit_autotune: block structures without coupling");
-    TileBudget t;
-    if (cache_lookup(cache_path, key, value) && parse_budget(value, t)) {
-      if ((st = apply_budget(ctx, t)) != QRKIT_OK) return st;
+    BlockChoice c;
+    if (cache_lookup(cache_path, key, value) && parse_choice(value, c)) {
+      if ((st = apply_choice(ctx, c)) != QRKIT_OK) return st;
     } else {
       float best = 1e30f;
-      TileBudget bt = P.budget;
-      for (const TileBudget& c : budget_candidates(elem_size(ctx))) {
-        if ((st = apply_budget(ctx, c)) != QRKIT_OK) return st;
+      BlockChoice bc;
+      for (const BlockChoice& cand : block_candidates(elem_size(ctx))) {
+        if ((st = apply_choice(ctx, cand)) != QRKIT_OK) return st;
         float ms = 0.f;
         st = time_runs(ctx, [&] { return launch_block_solve(ctx, J, b, nullptr, p, nullptr, refine_steps); }, ms);
         if (st != QRKIT_OK) return st;
         if (ms < best) {
           best = ms;
-          bt = c;
+          bc = cand;
         }
       }
-      if ((st = apply_budget(ctx, bt)) != QRKIT_OK) return st;
-      value = budget_str(bt);
+      if ((st = apply_choice(ctx, bc)) != QRKIT_OK) return st;
+      value = choice_str(bc);
       cache_store(cache_path, key, value);
     }
     ctx->factored = false;
@@ -218,4 +282,29 @@ extern "C" qrkit_status qrkit_autotune(qrkit_ctx* ctx, const void* J, const void
     std::snprintf(chosen, (size_t)chosen_len, "%s", value.c_str());
   }
   return QRKIT_OK;
+}
+
+extern "C" qrkit_status qrkit_apply_tuning(qrkit_ctx* ctx, const char* choice) {
+  if (!ctx) return QRKIT_EINVAL;
+  if (!choice) return fail(ctx, QRKIT_EINVAL, "choice is required");
+  Plan& P = ctx->plan;
+  if (!P.valid) return fail(ctx, QRKIT_ESTATE, "qrkit_apply_tuning before qrkit_plan");
+  QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  const std::string v(choice);
+  if (P.s.kind == QRKIT_STRUCT_BLOCKS) {
+    if (P.composed) return fail(ctx, QRKIT_EUNSUPPORTED, "qrkit_apply_tuning: block structures without coupling");
+    BlockChoice c;
+    if (!parse_choice(v, c)) return fail(ctx, QRKIT_EINVAL, "cannot parse block mapping '" + v + "'");
+    const qrkit_status st = apply_choice(ctx, c);
+    ctx->factored = false;
+    return st;
+  }
+  Band& B = ctx->band;
+  if (!B.parallel || !B.cr) return fail(ctx, QRKIT_EUNSUPPORTED, "qrkit_apply_tuning: parallel banded plans only");
+  int tr = 1, sp = 1;
+  if (sscanf(v.c_str(), "compress %d %d", &tr, &sp) != 2)
+    return fail(ctx, QRKIT_EINVAL, "cannot parse compression strategy '" + v + "'");
+  const qrkit_status st = cr_set_strategy(ctx, *B.cr, tr != 0, sp);
+  ctx->band_factored = false;
+  return st;
 }

@@ -111,6 +111,7 @@ _SIGS = {
     "qrkit_lm_features": (ctypes.c_int, [_VP, _VP]),
     "qrkit_autotune": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_int, ctypes.c_char_p, ctypes.c_char_p,
                                        ctypes.c_int64]),
+    "qrkit_apply_tuning": (ctypes.c_int, [_VP, ctypes.c_char_p]),
     "qrkit_sync_status": (ctypes.c_int, [_VP]),
     "qrkit_block_solve_noalloc": (ctypes.c_int, [ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int64, _VP,
                                                  _VP, _VP, _VP, _VP, ctypes.c_int]),
@@ -397,6 +398,10 @@ class Context:
         self._check(self.lib.qrkit_autotune(self.h, self._t(J, "J"), self._t(b, "b"), self._t(p, "p"),
                                             int(refine_steps), path, buf, 256))
         return buf.value.decode()
+
+    def apply_tuning(self, choice):
+        """Apply a configuration in the text form autotune returns, without timing."""
+        self._check(self.lib.qrkit_apply_tuning(self.h, str(choice).encode()))
 
     def sync_status(self):
         self._check(self.lib.qrkit_sync_status(self.h))

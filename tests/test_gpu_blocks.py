@@ -9,19 +9,31 @@ from workloads import batched_blocks
 pytestmark = pytest.mark.gpu
 
 
-def run(d, precision, refine_steps=1, with_qtb=True):
+def _at_offset(torch, host, offset, dev, dt):
+    """A device copy of host that starts `offset` elements into its allocation."""
+    buf = torch.zeros(len(host) + offset, device=dev, dtype=dt)
+    view = buf[offset:]
+    view.copy_(torch.from_numpy(np.asarray(host)).to(dev, dt))
+    return view
+
+
+def run(d, precision, refine_steps=1, with_qtb=True, tuning=None, offset=0):
+    """offset: J, b and Q^T b start that many elements into their allocations (their 16-byte
+    alignment then differs from the factor workspace's)."""
     torch = cuda_or_skip()
     from paper_1802_03773_gb300 import Context
     ctx = Context(0, precision=precision)
     dt = ctx.dtype
     dev = ctx.device
-    J = torch.from_numpy(np.asarray(d["vals"])).to(dev, dt)
-    b = torch.from_numpy(np.asarray(d["b"])).to(dev, dt)
+    J = _at_offset(torch, d["vals"], offset, dev, dt)
+    b = _at_offset(torch, d["b"], offset, dev, dt)
     K = d["K"]
     ncols = int(d["col_off"][-1])
     p = torch.empty(ncols, device=dev, dtype=dt)
-    qtb = torch.empty(int(d["row_off"][-1]), device=dev, dtype=dt) if with_qtb else None
+    qtb = _at_offset(torch, np.zeros(int(d["row_off"][-1])), offset, dev, dt) if with_qtb else None
     ctx.plan_blocks(d["n"], d["m"])
+    if tuning is not None:
+        ctx.apply_tuning(tuning)
     ctx.factor_solve(J, b, p, qtb, refine_steps=refine_steps)
     F = torch.empty_like(J)
     tau = torch.empty(ncols, device=dev, dtype=dt)
@@ -71,16 +83,35 @@ def check_blocks(d, out, idx, x_tol, r_tol):
     return rel
 
 
+TILES = {"fp64": "budget 256 1536 512 256 2048", "fp32": "budget 256 3072 1024 512 4096"}
+
+
+@pytest.mark.parametrize("mapping", ["tasks", "tasks 32 4 0", "tasks 64 8 1", "tiles"])
 @pytest.mark.parametrize("precision,x_tol,r_tol", [("fp64", 1e-12, 1e-13),
                                                    ("fp32_refined", 1e-5, 2e-6),
                                                    ("fp32", 1e-4, 2e-6)])
-def test_blocks_parity_small(precision, x_tol, r_tol):
-    """3000 blocks: several tiles and a ragged last tile; every block checked."""
+def test_blocks_parity_small(precision, x_tol, r_tol, mapping):
+    """3000 blocks: several supertiles / tiles, ragged warp tasks and a ragged last tile;
+    every block checked.  Mappings: the default shape-uniform warp tasks, tasks over
+    32-block supertiles in supertile order with 4 warps per CTA, tasks over 64-block
+    supertiles in shape-key order, and tiles of consecutive blocks."""
     d = batched_blocks(K=3000, seed_offset=7, dtype=np.float64 if precision == "fp64" else np.float32)
-    out = run(d, precision)
+    tuning = {"tasks": None, "tiles": TILES["fp64" if precision == "fp64" else "fp32"]}.get(mapping, mapping)
+    out = run(d, precision, tuning=tuning)
     check_blocks(d, out, range(3000), x_tol, r_tol)
     # one fused launch; with refinement a second one refines the blocks the first selected
     assert out["launches"] == (2 if precision == "fp32_refined" else 1)
+
+
+@pytest.mark.parametrize("offset", [1, 3])
+@pytest.mark.parametrize("precision,x_tol,r_tol", [("fp64", 1e-12, 1e-13), ("fp32_refined", 1e-5, 2e-6)])
+def test_blocks_unaligned_buffers(precision, x_tol, r_tol, offset):
+    """J, b and Q^T b that start off the factor workspace's 16-byte alignment: the blocks at
+    the buffers' ends are loaded with plain loads, the factor and Q^T b leave with plain
+    stores."""
+    d = batched_blocks(K=2000, seed_offset=12, dtype=np.float64 if precision == "fp64" else np.float32)
+    out = run(d, precision, offset=offset)
+    check_blocks(d, out, range(2000), x_tol, r_tol)
 
 
 def test_blocks_refinement_reduces_error():

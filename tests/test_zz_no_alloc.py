@@ -2,8 +2,9 @@
 
 qrkit_block_solve_noalloc serves callers that cannot call cudaMalloc (a framework that owns
 all device memory, a fixed memory budget): it keeps every intermediate in one static device
-array.  This test calls it through the C-ABI twice in a row, since the array keeps the
-previous call's contents, and compares each result with qrkit_factor_solve's.
+array.  It runs the tile kernel of the fused solve, so this test pins the context to the same
+tile mapping, calls the allocation-free entry point through the C-ABI twice in a row (the array
+keeps the previous call's contents) and compares each result with qrkit_factor_solve's.
 It lives in its own file so that pytest collects it last.
 """
 import numpy as np
@@ -27,6 +28,7 @@ def test_noalloc_matches_context_solve_twice(precision, tol):
     ncols = int(d["col_off"][-1])
     ctx = Context(0, precision=precision)
     ctx.plan_blocks(d["n"], d["m"])
+    ctx.apply_tuning("budget 256 1536 512 256 2048" if precision == "fp64" else "budget 256 3072 1024 512 4096")
     p_ref = torch.empty(ncols, device="cuda", dtype=tdt)
     ctx.factor_solve(J, b, p_ref, None, refine_steps=2)
     ctx.sync_status()
