@@ -15,7 +15,8 @@ namespace qrkit {
 namespace tasks {
 namespace {
 
-// Shared memory per warp for the keys present in the plan.
+// One data buffer of a warp: the block slots of the largest task among the keys present in
+// the plan.
 int warp_slot_bytes(const Plan& P, int es) {
   int best = 0;
   for (int k = 0; k < kTaskKeys; ++k) {
@@ -48,6 +49,7 @@ qrkit_status launch_tasks_typed(qrkit_ctx* ctx, const void* J, const void* b, vo
   Plan& P = ctx->plan;
   const int es = (int)sizeof(T);
   const int wpc = P.task_warps;
+  static_assert(sizeof(TaskHdr) % 16 == 0 && sizeof(RefEntry) % 16 == 0, "16-byte copies");
   const int threads = 32 * wpc;
   TaskArgs<T> A;
   A.hdr = (const TaskHdr*)P.d_task_hdr.ptr;
@@ -61,24 +63,25 @@ qrkit_status launch_tasks_typed(qrkit_ctx* ctx, const void* J, const void* b, vo
   A.tau = (T*)ctx->ws.tau.ptr;
   A.qtb = (T*)qtb;
   A.x = (T*)p;
-  A.f_bulk = ((reinterpret_cast<uintptr_t>(A.F) ^ reinterpret_cast<uintptr_t>(J)) & 15) == 0;
-  A.q_bulk = qtb && ((reinterpret_cast<uintptr_t>(qtb) ^ reinterpret_cast<uintptr_t>(b)) & 15) == 0;
-  A.warp_bytes = warp_slot_bytes(P, es);
-  A.wait_limit = 1LL << 26;
+  A.f_vec = ((reinterpret_cast<uintptr_t>(A.F) ^ reinterpret_cast<uintptr_t>(J)) & 15) == 0;
+  A.q_vec = qtb && ((reinterpret_cast<uintptr_t>(qtb) ^ reinterpret_cast<uintptr_t>(b)) & 15) == 0;
+  A.data_bytes = warp_slot_bytes(P, es);
+  A.warp_bytes = (warp_desc_bytes((int)sizeof(TaskEntry)) + 2 * A.data_bytes + 127) / 128 * 128;
   A.status = ctx->d_status;
   A.rlist = nullptr;
   A.rcount = nullptr;
   A.key_off = (const int64_t*)P.d_key_off.ptr;
   qrkit_status st;
   if (SEL) {
-    if ((st = ensure(ctx, ctx->ws.tlist, (size_t)std::max<int64_t>(P.K, 1) * sizeof(int), "refinement lists")) != QRKIT_OK)
+    if ((st = ensure(ctx, ctx->ws.tlist, (size_t)std::max<int64_t>(P.K, 1) * sizeof(RefEntry), "refinement lists")) !=
+        QRKIT_OK)
       return st;
     if ((st = ensure(ctx, ctx->ws.tcount, kTaskKeys * sizeof(int), "refinement counts")) != QRKIT_OK) return st;
     QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->ws.tcount.ptr, 0, kTaskKeys * sizeof(int), ctx->stream));
-    A.rlist = (int*)ctx->ws.tlist.ptr;
+    A.rlist = (RefEntry*)ctx->ws.tlist.ptr;
     A.rcount = (int*)ctx->ws.tcount.ptr;
   }
-  const size_t smem = (size_t)wpc * A.warp_bytes + (size_t)wpc * sizeof(uint64_t);
+  const size_t smem = (size_t)wpc * A.warp_bytes;
   int per_sm = 0;
   if ((st = resident(ctx, kernel_setup<T, SEL>, threads, smem, sizeof(T) == 8 ? 10 : (SEL ? 9 : 8), per_sm)) != QRKIT_OK)
     return st;
@@ -89,10 +92,6 @@ qrkit_status launch_tasks_typed(qrkit_ctx* ctx, const void* J, const void* b, vo
   ctx->launches += 1;
   if constexpr (SEL && sizeof(T) == sizeof(float)) {
     RefineTaskArgs R;
-    R.n = (const uint8_t*)P.d_n.ptr;
-    R.val_off = (const int64_t*)P.d_val_off.ptr;
-    R.row_off = (const int64_t*)P.d_row_off.ptr;
-    R.col_off = (const int64_t*)P.d_col_off.ptr;
     R.J = (const float*)J;
     R.b = (const float*)b;
     R.J_end = R.J + P.values;
@@ -103,15 +102,16 @@ qrkit_status launch_tasks_typed(qrkit_ctx* ctx, const void* J, const void* b, vo
     R.key_off = A.key_off;
     R.steps = refine_steps;
     R.tol = 1e-6f;
-    R.warp_bytes = A.warp_bytes;
-    R.wait_limit = A.wait_limit;
+    R.data_bytes = A.data_bytes;
+    R.warp_bytes = (warp_desc_bytes((int)sizeof(RefEntry)) + 2 * R.data_bytes + 127) / 128 * 128;
+    const size_t smem2 = (size_t)wpc * R.warp_bytes;
     R.status = A.status;
     int per_sm2 = 0;
-    if ((st = resident(ctx, refine_setup, threads, smem, 11, per_sm2)) != QRKIT_OK) return st;
+    if ((st = resident(ctx, refine_setup, threads, smem2, 11, per_sm2)) != QRKIT_OK) return st;
     const int64_t want2 = (P.max_refine_tasks + wpc - 1) / wpc;
     const int64_t full2 = (int64_t)ctx->num_sms * per_sm2;
     const unsigned grid2 = (unsigned)std::max<int64_t>(1, std::min(want2, full2));
-    QRKIT_CUDA_TRY(ctx, refine_launch(R, grid2, threads, smem, ctx->stream));
+    QRKIT_CUDA_TRY(ctx, refine_launch(R, grid2, threads, smem2, ctx->stream));
     ctx->launches += 1;
   }
   return QRKIT_OK;

@@ -9,13 +9,16 @@
 // CTA-wide barrier anywhere.  Supertiles keep the blocks that concurrent warps touch (and the
 // neighbours sharing their 32-byte sectors) close in time, so partial sectors meet in L2.
 //
-// Kernels (device): persistent warps, each with its own shared-memory slots and mbarrier,
-// take tasks in a grid stride.  Per task one lane per block issues bulk copies (TMA,
-// cp.async.bulk) of the 16-byte-aligned supersets of the block's J and b; the group factors
+// Kernels (device): persistent warps, each with its own shared-memory slots, take tasks in a
+// grid stride.  Per task the G lanes of each block's group copy the 16-byte-aligned supersets
+// of the block's J and b into its slots with per-lane 16-byte cp.async copies (the blocks of
+// a task are scattered, 20-500 bytes each: per-thread copies, not TMA, whose operands must
+// be warp-uniform and would serialise one block after another); the group factors
 // the block with Householder reflectors H = I - tau v v^T (v[0] = 1, beta = -sign(x0)||x||;
 // norms and dot products are shuffle reductions over the group), applies them to b (Q^T b)
 // and back-substitutes.  The first kernel writes the factor and Q^T b back to the slots and
-// sends them to HBM with bulk stores (unaligned head and tail elements by plain stores);
+// sends them to HBM with 16-byte vector stores (unaligned head and tail elements by plain
+// stores);
 // with refinement it also estimates each block's float error a priori and lists the blocks
 // that need refinement, one list per shape key.  The second kernel takes those lists in
 // tasks of the same form, factors the listed blocks again (bit-identical to the first pass)
@@ -38,17 +41,17 @@ constexpr float kRefineTarget = 1e-6f;           // blocks estimated above this 
 constexpr int kMaxCols = 8;
 constexpr int kTaskMaxWarps = 8;   // the kernels are compiled for at most 256 threads per CTA
 #ifndef QRKIT_TASK_CTAS
-#define QRKIT_TASK_CTAS 3   // resident CTAs per SM the float task kernel is compiled for
+#define QRKIT_TASK_CTAS 2   // resident CTAs per SM the float task kernel is compiled for
 #endif
 
 __host__ __device__ constexpr int group_lanes(int key) { return (key >> 3) + 1; }
 __host__ __device__ constexpr int task_blocks(int G) { return 32 / G; }
 // Shared-memory slot of one block's J (or b) in a task: the 16-byte-aligned superset of
-// its values fits with room to spare.
+// len bytes starting anywhere spans at most round16(len) + 16 bytes.
 __host__ __device__ constexpr int slot_j_bytes(int G, int M, int es) {
-  return ((4 * G * M * es + 15) & ~15) + 32;
+  return ((4 * G * M * es + 15) & ~15) + 16;
 }
-__host__ __device__ constexpr int slot_b_bytes(int G, int es) { return ((4 * G * es + 15) & ~15) + 32; }
+__host__ __device__ constexpr int slot_b_bytes(int G, int es) { return ((4 * G * es + 15) & ~15) + 16; }
 
 // ---------------------------------------------------------------------------------------
 // A block's lane group: G consecutive lanes starting at `base`; this lane is row group q.
@@ -441,75 +444,100 @@ __device__ __forceinline__ void group_refine(const float (&a)[kMaxCols][4], floa
 }
 
 // ---------------------------------------------------------------------------------------
-// Staging of one task: lane q = 0 of each group issues the bulk copies of its block's J
-// and b supersets (or, where a superset would leave the caller's buffers, the group loads
-// the values with plain loads); all lanes wait on the warp's mbarrier with a bounded poll.
-template <typename T, int G>
-__device__ __forceinline__ bool stage_task(const T* gJ, const T* gB, int n, int M, bool act, int grp, int q,
-                                           int lane, const T* J_lo, const T* J_hi, const T* b_lo,
-                                           const T* b_hi, unsigned char* wb, uint64_t* bar, uint32_t& phase,
-                                           long long wait_limit, int* status, T*& sJ, T*& sB) {
-  constexpr int P = task_blocks(G);
+// Software pipeline of a warp.  While task i is computed, the copies for task i + 1's block
+// data, task i + 2's entries and task i + 3's header (all per-lane 16-byte cp.async copies)
+// are in flight; they were issued as one commit group right after the warp waited for the
+// previous group.  Shared memory of a warp: 4 header buffers, 3 entry buffers and 2 data
+// buffers, each used by every 4th / 3rd / 2nd task.
+constexpr int kHdrBufs = 4, kEntBufs = 3;
+// Descriptor bytes of a warp: header buffers and entry buffers of up to 32 entries (entry
+// size: 16 bytes in the factor kernel, 32 in the refinement kernel).
+__host__ __device__ constexpr int warp_desc_bytes(int entry_bytes) {
+  return kHdrBufs * (int)sizeof(TaskHdr) + kEntBufs * 32 * entry_bytes;
+}
+
+struct WarpBufs {
+  unsigned char* base;
+  int data_bytes;
+  int ent_bytes;   // one entry buffer
+  __device__ __forceinline__ TaskHdr* hdr(int64_t i) const {
+    return reinterpret_cast<TaskHdr*>(base + (int)(i % kHdrBufs) * (int)sizeof(TaskHdr));
+  }
+  __device__ __forceinline__ unsigned char* ent(int64_t i) const {
+    return base + kHdrBufs * (int)sizeof(TaskHdr) + (int)(i % kEntBufs) * ent_bytes;
+  }
+  __device__ __forceinline__ unsigned char* data(int64_t i) const {
+    return base + kHdrBufs * (int)sizeof(TaskHdr) + kEntBufs * ent_bytes + (int)(i & 1) * data_bytes;
+  }
+};
+
+// The slots of a block in a task's data buffer (group grp of a task of G lanes per block and
+// M columns): J's superset at the J slot, b's after the P J slots; the values start at the
+// global address's offset modulo 16.
+template <typename T>
+__device__ __forceinline__ void slot_ptrs(unsigned char* db, int G, int M, int grp, const T* gJ, const T* gB,
+                                          unsigned char*& sJraw, unsigned char*& sBraw, T*& sJ, T*& sB) {
+  const int P = task_blocks(G);
+  const int JS = slot_j_bytes(G, M, (int)sizeof(T));
+  const int BS = slot_b_bytes(G, (int)sizeof(T));
+  sJraw = db + grp * JS;
+  sBraw = db + P * JS + grp * BS;
+  sJ = reinterpret_cast<T*>(sJraw + (reinterpret_cast<uintptr_t>(gJ) & 15));
+  sB = reinterpret_cast<T*>(sBraw + (reinterpret_cast<uintptr_t>(gB) & 15));
+}
+
+// Copies of one block's J (n x M values) and b (n values) into its slots by the G lanes of
+// its group: the 16-byte-aligned supersets by 16-byte cp.async copies, or, where a superset
+// would leave the caller's buffers, the values themselves by plain loads.
+template <typename T>
+__device__ __forceinline__ void issue_block(const T* gJ, const T* gB, int n, int M, int G, int q, const T* J_lo,
+                                            const T* J_hi, const T* b_lo, const T* b_hi, unsigned char* sJraw,
+                                            unsigned char* sBraw, T* sJ, T* sB) {
+  if (n <= 0) return;
   constexpr int es = (int)sizeof(T);
-  const int JS = slot_j_bytes(G, M, es);
-  constexpr int BS = slot_b_bytes(G, es);
-  unsigned char* sJraw = wb + (act ? grp : 0) * JS;
-  unsigned char* sBraw = wb + P * JS + (act ? grp : 0) * BS;
   const int nv = n * M;
   const uintptr_t aJ = reinterpret_cast<uintptr_t>(gJ), aB = reinterpret_cast<uintptr_t>(gB);
   const uintptr_t lJ = aJ & ~(uintptr_t)15, hJ = (aJ + (uintptr_t)nv * es + 15) & ~(uintptr_t)15;
   const uintptr_t lB = aB & ~(uintptr_t)15, hB = (aB + (uintptr_t)n * es + 15) & ~(uintptr_t)15;
-  const bool bJ = n > 0 && lJ >= reinterpret_cast<uintptr_t>(J_lo) && hJ <= reinterpret_cast<uintptr_t>(J_hi) &&
-                  hJ - lJ <= (uintptr_t)JS;
-  const bool bB = n > 0 && lB >= reinterpret_cast<uintptr_t>(b_lo) && hB <= reinterpret_cast<uintptr_t>(b_hi) &&
-                  hB - lB <= (uintptr_t)BS;
-  const uint32_t mine = q == 0 ? (uint32_t)((bJ ? hJ - lJ : 0) + (bB ? hB - lB : 0)) : 0u;
-  const uint32_t total = __reduce_add_sync(0xffffffffu, mine);
-  // the slots are free once this warp's earlier bulk stores have read them and every lane's
-  // generic accesses are ordered before the copies
-  bulk_wait_read();
-  fence_proxy_async();
-  __syncwarp();
-  if (lane == 0) mbar_expect_tx(bar, total);
-  __syncwarp();
-  if (q == 0 && bJ) bulk_g2s(sJraw, reinterpret_cast<const void*>(lJ), (uint32_t)(hJ - lJ), bar);
-  if (q == 0 && bB) bulk_g2s(sBraw, reinterpret_cast<const void*>(lB), (uint32_t)(hB - lB), bar);
-  sJ = reinterpret_cast<T*>(sJraw + (aJ & 15));
-  sB = reinterpret_cast<T*>(sBraw + (aB & 15));
-  if (n > 0 && !bJ)
+  if (lJ >= reinterpret_cast<uintptr_t>(J_lo) && hJ <= reinterpret_cast<uintptr_t>(J_hi)) {
+    const int nch = (int)((hJ - lJ) >> 4);
+    for (int c = q; c < nch; c += G) cp_async16(sJraw + 16 * c, reinterpret_cast<const void*>(lJ + 16 * (uintptr_t)c));
+  } else {
     for (int k = q; k < nv; k += G) sJ[k] = gJ[k];
-  if (n > 0 && !bB)
+  }
+  if (lB >= reinterpret_cast<uintptr_t>(b_lo) && hB <= reinterpret_cast<uintptr_t>(b_hi)) {
+    const int nch = (int)((hB - lB) >> 4);
+    for (int c = q; c < nch; c += G) cp_async16(sBraw + 16 * c, reinterpret_cast<const void*>(lB + 16 * (uintptr_t)c));
+  } else {
     for (int k = q; k < n; k += G) sB[k] = gB[k];
-  bool ok = false;
-  for (long long polls = 0; polls < wait_limit; ++polls) {
-    if (mbar_try_wait(bar, phase)) {
-      ok = true;
-      break;
-    }
   }
-  phase ^= 1u;
-  if (!__all_sync(0xffffffffu, ok)) {
-    if (lane == 0) record(status, QRKIT_ETIMEOUT);
-    return false;
-  }
-  __syncwarp();
-  return true;
 }
 
-// Copy of count elements from a slot to global memory that agree modulo 16 bytes: bulk
-// store of the aligned interior by lane q = 0, head and tail by the group's lanes.
+// Copy of count elements from a slot to global memory: where both agree modulo 16 bytes the
+// aligned interior goes as 16-byte vector stores, head and tail as plain stores; the group's
+// lanes share the work.
 template <typename T, int G>
-__device__ __forceinline__ void send(T* dst, const T* src, int count, bool bulk, int q) {
-  if (!bulk) {
+__device__ __forceinline__ void send(T* dst, const T* src, int count, bool vec, int q) {
+  if (!vec) {
     for (int k = q; k < count; k += G) dst[k] = src[k];
     return;
   }
+  constexpr int VN = 16 / (int)sizeof(T);
   int h, ni;
   interior(dst, count, h, ni);
-  if (q == 0 && ni > 0) bulk_s2g(dst + h, src + h, (uint32_t)(ni * sizeof(T)));
+  const int nch = ni / VN;
+  for (int c = q; c < nch; c += G)
+    *reinterpret_cast<uint4*>(dst + h + c * VN) = *reinterpret_cast<const uint4*>(src + h + c * VN);
   for (int k = q; k < h; k += G) dst[k] = src[k];
   for (int k = h + ni + q; k < count; k += G) dst[k] = src[k];
 }
+
+// A block selected for refinement: its value, row and column offsets and its row count.
+struct RefEntry {
+  int64_t v, r, c;
+  int32_t n, pad;
+};
+static_assert(sizeof(RefEntry) == 32, "refinement list layout");
 
 template <typename T>
 struct TaskArgs {
@@ -518,41 +546,68 @@ struct TaskArgs {
   int64_t num_tasks;
   const T* J;
   const T* b;
-  const T* J_end;   // one past the last value (bounds of the bulk supersets)
+  const T* J_end;   // one past the last value (bounds of the copied supersets)
   const T* b_end;
   T* F;             // factor, J packing
   T* tau;
   T* qtb;           // may be null
   T* x;
-  int f_bulk;       // F agrees with J modulo 16 bytes: factor leaves by bulk stores
-  int q_bulk;       // qtb agrees with b modulo 16 bytes
-  int warp_bytes;   // shared memory per warp (slots)
-  long long wait_limit;
+  int f_vec;        // F agrees with J modulo 16 bytes: factor leaves by vector stores
+  int q_vec;        // qtb agrees with b modulo 16 bytes
+  int warp_bytes;   // shared memory per warp (descriptor and data buffers)
+  int data_bytes;   // one data buffer
   int* status;
-  int* rlist;               // selection: blocks to refine, one list per shape key
+  RefEntry* rlist;          // selection: blocks to refine, one list per shape key
   int* rcount;              // kTaskKeys counts
   const int64_t* key_off;   // kTaskKeys + 1 list offsets (list capacity = blocks of the key)
 };
 
-// One task of shape key (G, M): M is a compile-time constant, so every loop bound and guard of
-// the inlined helpers folds away.
+// Pipeline stages of the factor kernel: the header of task t, the entries of task t (its
+// header is in shared memory), the block data of task t (header and entries are).
+__device__ __forceinline__ void issue_hdr(const TaskHdr* g, int64_t t, int64_t T, TaskHdr* s, int lane) {
+  if (t < T && lane < (int)sizeof(TaskHdr) / 16)
+    cp_async16(reinterpret_cast<unsigned char*>(s) + 16 * lane, reinterpret_cast<const unsigned char*>(g + t) + 16 * lane);
+}
+__device__ __forceinline__ void issue_ent(const TaskEntry* g, int64_t t, int64_t T, const TaskHdr* sh,
+                                          unsigned char* s, int lane) {
+  if (t >= T) return;
+  const int P = task_blocks(group_lanes(sh->key));
+  if (lane < P) cp_async16(s + 16 * lane, g + sh->first + lane);
+}
+template <typename T>
+__device__ __forceinline__ void issue_data(const TaskArgs<T>& A, int64_t t, const TaskHdr* sh, const unsigned char* se,
+                                           unsigned char* db, int lane) {
+  if (t >= A.num_tasks) return;
+  const int key = sh->key;
+  const int G = group_lanes(key), M = (key & 7) + 1, P = task_blocks(G);
+  const int grp = lane / G, q = lane - grp * G;
+  if (grp >= P) return;
+  const TaskEntry e = reinterpret_cast<const TaskEntry*>(se)[grp];
+  const T* gJ = A.J + sh->v0 + e.v;
+  const T* gB = A.b + sh->r0 + e.r;
+  unsigned char *sJraw, *sBraw;
+  T *sJ, *sB;
+  slot_ptrs<T>(db, G, M, grp, gJ, gB, sJraw, sBraw, sJ, sB);
+  issue_block<T>(gJ, gB, e.n, M, G, q, A.J, A.J_end, A.b, A.b_end, sJraw, sBraw, sJ, sB);
+}
+
+// One task of shape key (G, M), its data staged in db: M is a compile-time constant, so every
+// loop bound and guard of the inlined helpers folds away.
 template <typename T, int G, int M, bool SEL>
-__device__ __forceinline__ bool run_task(const TaskArgs<T>& A, const TaskHdr& h, unsigned char* wb,
-                                         uint64_t* bar, uint32_t& phase, int lane) {
+__device__ __forceinline__ void run_task(const TaskArgs<T>& A, const TaskHdr& h, const unsigned char* se,
+                                         unsigned char* db, int lane) {
   constexpr int P = task_blocks(G);
   const int grp = lane / G;
   const bool act = grp < P;
   const Group<G> g(lane);
   TaskEntry e{};
-  if (act) e = A.ent[h.first + grp];
+  if (act) e = reinterpret_cast<const TaskEntry*>(se)[grp];
   const int n = e.n;
   const T* gJ = A.J + h.v0 + e.v;
   const T* gB = A.b + h.r0 + e.r;
-  T* sJ;
-  T* sB;
-  if (!stage_task<T, G>(gJ, gB, n, M, act, grp, g.q, lane, A.J, A.J_end, A.b, A.b_end, wb, bar, phase,
-                        A.wait_limit, A.status, sJ, sB))
-    return false;
+  unsigned char *sJraw, *sBraw;
+  T *sJ, *sB;
+  slot_ptrs<T>(db, G, M, act ? grp : 0, gJ, gB, sJraw, sBraw, sJ, sB);
   T a[kMaxCols][4], c[4], x[kMaxCols];
   load_regs<T, G>(a, c, sJ, sB, n, M, g.q);
   group_householder<T, G>(a, c, n > 0 ? A.tau + h.c0 + e.c : nullptr, M, g);
@@ -581,13 +636,11 @@ __device__ __forceinline__ bool run_task(const TaskArgs<T>& A, const TaskHdr& h,
     if (g.q == 0 && n > 0) need = lane_needs_refinement((const float*)sJ, n, M, res2, (float)x2);
   }
   // factor and Q^T b from the slots to HBM
-  fence_proxy_async();
   __syncwarp();
   if (n > 0) {
-    send<T, G>(A.F + h.v0 + e.v, sJ, n * M, A.f_bulk != 0, g.q);
-    if (A.qtb) send<T, G>(A.qtb + h.r0 + e.r, sB, n, A.q_bulk != 0, g.q);
+    send<T, G>(A.F + h.v0 + e.v, sJ, n * M, A.f_vec != 0, g.q);
+    if (A.qtb) send<T, G>(A.qtb + h.r0 + e.r, sB, n, A.q_vec != 0, g.q);
   }
-  if (g.q == 0) bulk_commit();
   if constexpr (SEL) {
     const bool sel = act && g.q == 0 && n > 0 && need;
     const unsigned mask = __ballot_sync(0xffffffffu, sel);
@@ -598,134 +651,207 @@ __device__ __forceinline__ bool run_task(const TaskArgs<T>& A, const TaskHdr& h,
       if (sel) {
         const int64_t pos = (int64_t)first + __popc(mask & ((1u << lane) - 1u));
         const int64_t cap = A.key_off[h.key + 1] - A.key_off[h.key];
-        if (pos < cap) A.rlist[A.key_off[h.key] + pos] = (int)(h.b0 + e.blk);
+        if (pos < cap) {
+          RefEntry re;
+          re.v = h.v0 + e.v;
+          re.r = h.r0 + e.r;
+          re.c = h.c0 + e.c;
+          re.n = n;
+          re.pad = 0;
+          A.rlist[A.key_off[h.key] + pos] = re;
+        }
       }
     }
   }
-  return true;
 }
 
 template <typename T, bool SEL>
 __global__ void __launch_bounds__(32 * kTaskMaxWarps, sizeof(T) == 4 ? QRKIT_TASK_CTAS : 2) block_task_kernel(TaskArgs<T> A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-  unsigned char* wb = smem_raw + (size_t)wid * A.warp_bytes;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + (size_t)wpc * A.warp_bytes) + wid;
-  if (lane == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
+  const WarpBufs W{smem_raw + (size_t)wid * A.warp_bytes, A.data_bytes, 32 * (int)sizeof(TaskEntry)};
+  const int64_t NT = A.num_tasks;
+  const int64_t t0 = (int64_t)blockIdx.x * wpc + wid, stride = (int64_t)gridDim.x * wpc;
+  if (t0 >= NT) return;
+  // prologue: header 0; header 1 and entries 0; header 2, entries 1 and data 0
+  issue_hdr(A.hdr, t0, NT, W.hdr(0), lane);
+  cp_async_commit();
+  cp_async_wait_all();
   __syncwarp();
-  uint32_t phase = 0;
-  for (int64_t t = (int64_t)blockIdx.x * wpc + wid; t < A.num_tasks; t += (int64_t)gridDim.x * wpc) {
-    const TaskHdr h = A.hdr[t];
-    bool ok = true;
+  issue_hdr(A.hdr, t0 + stride, NT, W.hdr(1), lane);
+  issue_ent(A.ent, t0, NT, W.hdr(0), W.ent(0), lane);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncwarp();
+  issue_hdr(A.hdr, t0 + 2 * stride, NT, W.hdr(2), lane);
+  issue_ent(A.ent, t0 + stride, NT, W.hdr(1), W.ent(1), lane);
+  issue_data<T>(A, t0, W.hdr(0), W.ent(0), W.data(0), lane);
+  cp_async_commit();
+  for (int64_t i = 0, t = t0; t < NT; ++i, t += stride) {
+    cp_async_wait_all();
+    __syncwarp();   // task i's data, task i + 1's entries and task i + 2's header have landed
+    issue_hdr(A.hdr, t + 3 * stride, NT, W.hdr(i + 3), lane);
+    issue_ent(A.ent, t + 2 * stride, NT, W.hdr(i + 2), W.ent(i + 2), lane);
+    issue_data<T>(A, t + stride, W.hdr(i + 1), W.ent(i + 1), W.data(i + 1), lane);
+    cp_async_commit();
+    const TaskHdr h = *W.hdr(i);
     switch (h.key) {
 #define QRKIT_TASK_CASE(k) \
-  case k: ok = run_task<T, ((k) >> 3) + 1, ((k) & 7) + 1, SEL>(A, h, wb, bar, phase, lane); break;
+  case k: run_task<T, ((k) >> 3) + 1, ((k) & 7) + 1, SEL>(A, h, W.ent(i), W.data(i), lane); break;
       QRKIT_TASK_KEYS(QRKIT_TASK_CASE)
 #undef QRKIT_TASK_CASE
       default: if (lane == 0) record(A.status, QRKIT_EINVAL); break;
     }
-    if (!ok) break;
+    __syncwarp();   // every lane is done with task i's buffers before they are refilled
   }
-  bulk_wait_all();
+  cp_async_wait_all();
 }
 
 // ---------------------------------------------------------------------------------------
-// Refinement of the listed blocks (float).
+// Refinement of the listed blocks (float), pipelined like the factor kernel in two stages:
+// while task i is refined, the block data of task i + 1 and the list entries of task i + 2
+// are in flight.
 struct RefineTaskArgs {
-  const uint8_t* n;
-  const int64_t* val_off;
-  const int64_t* row_off;
-  const int64_t* col_off;
   const float* J;
   const float* b;
   const float* J_end;
   const float* b_end;
   float* x;
-  const int* rlist;
+  const RefEntry* rlist;
   const int* rcount;
   const int64_t* key_off;
   int steps;
   float tol;
   int warp_bytes;
-  long long wait_limit;
+  int data_bytes;
   int* status;
 };
 
+// Refinement tasks: per shape key, ceil(selected / P) tasks of P listed blocks; a task index
+// maps to its key through the keys' prefix sums (lane k holds key k's first task).
+struct RefineTasks {
+  int64_t start, total;
+  __device__ __forceinline__ void key_of(int64_t t, int& key, int64_t& local) const {
+    key = 31 - __clz(__ballot_sync(0xffffffffu, start <= t));
+    local = t - __shfl_sync(0xffffffffu, start, key);
+  }
+};
+
+__device__ __forceinline__ void issue_ref_ent(const RefineTaskArgs& A, const RefineTasks& RT, int64_t t,
+                                              unsigned char* s, int lane) {
+  if (t >= RT.total) return;
+  int key;
+  int64_t local;
+  RT.key_of(t, key, local);
+  const int P = task_blocks(group_lanes(key));
+  const int64_t cap = A.key_off[key + 1] - A.key_off[key];
+  const int64_t cnt = (int64_t)A.rcount[key] < cap ? (int64_t)A.rcount[key] : cap;
+  const int64_t idx = local * P + lane;
+  RefEntry* d = reinterpret_cast<RefEntry*>(s);
+  if (lane < P) {
+    if (idx < cnt) {
+      const RefEntry* g = A.rlist + A.key_off[key] + idx;
+      cp_async16(d + lane, g);
+      cp_async16(reinterpret_cast<unsigned char*>(d + lane) + 16, reinterpret_cast<const unsigned char*>(g) + 16);
+    } else {
+      d[lane].n = 0;   // no block
+    }
+  }
+}
+
+__device__ __forceinline__ void issue_ref_data(const RefineTaskArgs& A, const RefineTasks& RT, int64_t t,
+                                               const unsigned char* se, unsigned char* db, int lane) {
+  if (t >= RT.total) return;
+  int key;
+  int64_t local;
+  RT.key_of(t, key, local);
+  const int G = group_lanes(key), M = (key & 7) + 1, P = task_blocks(G);
+  const int grp = lane / G, q = lane - grp * G;
+  if (grp >= P) return;
+  const RefEntry e = reinterpret_cast<const RefEntry*>(se)[grp];
+  const float* gJ = A.J + e.v;
+  const float* gB = A.b + e.r;
+  unsigned char *sJraw, *sBraw;
+  float *sJ, *sB;
+  slot_ptrs<float>(db, G, M, grp, gJ, gB, sJraw, sBraw, sJ, sB);
+  issue_block<float>(gJ, gB, e.n, M, G, q, A.J, A.J_end, A.b, A.b_end, sJraw, sBraw, sJ, sB);
+}
+
 template <int G, int M>
-__device__ __forceinline__ bool refine_task(const RefineTaskArgs& A, int key, int64_t local, unsigned char* wb,
-                                            uint64_t* bar, uint32_t& phase, int lane) {
+__device__ __forceinline__ void refine_task(const RefineTaskArgs& A, const unsigned char* se, unsigned char* db,
+                                            int lane) {
   constexpr int P = task_blocks(G);
   const int grp = lane / G;
   const bool act = grp < P;
   const Group<G> g(lane);
-  const int64_t cap = A.key_off[key + 1] - A.key_off[key];
-  const int64_t cnt = (int64_t)A.rcount[key] < cap ? (int64_t)A.rcount[key] : cap;
-  const int64_t idx = local * P + grp;
-  int64_t bi = -1;
-  if (act && idx < cnt) bi = A.rlist[A.key_off[key] + idx];
-  const int n = bi >= 0 ? A.n[bi] : 0;
-  const float* gJ = A.J + (bi >= 0 ? A.val_off[bi] : 0);
-  const float* gB = A.b + (bi >= 0 ? A.row_off[bi] : 0);
-  float* sJ;
-  float* sB;
-  if (!stage_task<float, G>(gJ, gB, n, M, act, grp, g.q, lane, A.J, A.J_end, A.b, A.b_end, wb, bar, phase,
-                            A.wait_limit, A.status, sJ, sB))
-    return false;
+  RefEntry e{};
+  if (act) e = reinterpret_cast<const RefEntry*>(se)[grp];
+  const int n = e.n;
+  unsigned char *sJraw, *sBraw;
+  float *sJ, *sB;
+  slot_ptrs<float>(db, G, M, act ? grp : 0, A.J + e.v, A.b + e.r, sJraw, sBraw, sJ, sB);
   float a[kMaxCols][4], c[4], x[kMaxCols];
   load_regs<float, G>(a, c, sJ, sB, n, M, g.q);
   group_householder<float, G>(a, c, nullptr, M, g);
   group_backsub<float, G>(a, c, M, g, x);
   group_refine<G>(a, x, sJ, sB, n, M, g, A.steps, A.tol);
   if (n > 0) {
-    float* dx = A.x + A.col_off[bi];
+    float* dx = A.x + e.c;
 #pragma unroll
     for (int k = 0; k < kmax<G>(); ++k)
       if (k < M && (k % G) == g.q) dx[k] = x[k];
   }
-  return true;
 }
 
 template <int kUnused>
 __global__ void __launch_bounds__(32 * kTaskMaxWarps, 2) block_task_refine_kernel(RefineTaskArgs A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-  unsigned char* wb = smem_raw + (size_t)wid * A.warp_bytes;
-  uint64_t* bar = reinterpret_cast<uint64_t*>(smem_raw + (size_t)wpc * A.warp_bytes) + wid;
-  if (lane == 0) {
-    mbar_init(bar, 1);
-    fence_mbar_init();
-  }
-  __syncwarp();
+  const WarpBufs W{smem_raw + (size_t)wid * A.warp_bytes, A.data_bytes, 32 * (int)sizeof(RefEntry)};
   // tasks per shape key (lane k: key k), their exclusive prefix sums over the keys
-  const int64_t cap = A.key_off[lane + 1] - A.key_off[lane];
-  const int64_t cnt = (int64_t)A.rcount[lane] < cap ? (int64_t)A.rcount[lane] : cap;
-  const int64_t per = task_blocks(group_lanes(lane));
-  const int64_t tk = (cnt + per - 1) / per;
-  int64_t inc = tk;
+  RefineTasks RT;
+  {
+    const int64_t cap = A.key_off[lane + 1] - A.key_off[lane];
+    const int64_t cnt = (int64_t)A.rcount[lane] < cap ? (int64_t)A.rcount[lane] : cap;
+    const int64_t per = task_blocks(group_lanes(lane));
+    const int64_t tk = (cnt + per - 1) / per;
+    int64_t inc = tk;
 #pragma unroll
-  for (int d = 1; d < 32; d <<= 1) {
-    const int64_t o = __shfl_up_sync(0xffffffffu, inc, d);
-    if (lane >= d) inc += o;
+    for (int d = 1; d < 32; d <<= 1) {
+      const int64_t o = __shfl_up_sync(0xffffffffu, inc, d);
+      if (lane >= d) inc += o;
+    }
+    RT.start = inc - tk;
+    RT.total = __shfl_sync(0xffffffffu, inc, 31);
   }
-  const int64_t start = inc - tk;
-  const int64_t total = __shfl_sync(0xffffffffu, inc, 31);
-  uint32_t phase = 0;
-  for (int64_t t = (int64_t)blockIdx.x * wpc + wid; t < total; t += (int64_t)gridDim.x * wpc) {
-    const int key = 31 - __clz(__ballot_sync(0xffffffffu, start <= t));
-    const int64_t local = t - __shfl_sync(0xffffffffu, start, key);
-    bool ok = true;
+  const int64_t t0 = (int64_t)blockIdx.x * wpc + wid, stride = (int64_t)gridDim.x * wpc;
+  if (t0 >= RT.total) return;
+  issue_ref_ent(A, RT, t0, W.ent(0), lane);
+  cp_async_commit();
+  cp_async_wait_all();
+  __syncwarp();
+  issue_ref_ent(A, RT, t0 + stride, W.ent(1), lane);
+  issue_ref_data(A, RT, t0, W.ent(0), W.data(0), lane);
+  cp_async_commit();
+  for (int64_t i = 0, t = t0; t < RT.total; ++i, t += stride) {
+    cp_async_wait_all();
+    __syncwarp();   // task i's data and task i + 1's entries have landed
+    issue_ref_ent(A, RT, t + 2 * stride, W.ent(i + 2), lane);
+    issue_ref_data(A, RT, t + stride, W.ent(i + 1), W.data(i + 1), lane);
+    cp_async_commit();
+    int key;
+    int64_t local;
+    RT.key_of(t, key, local);
     switch (key) {
 #define QRKIT_REFINE_CASE(k) \
-  case k: ok = refine_task<((k) >> 3) + 1, ((k) & 7) + 1>(A, key, local, wb, bar, phase, lane); break;
+  case k: refine_task<((k) >> 3) + 1, ((k) & 7) + 1>(A, W.ent(i), W.data(i), lane); break;
       QRKIT_TASK_KEYS(QRKIT_REFINE_CASE)
 #undef QRKIT_REFINE_CASE
       default: break;
     }
-    if (!ok) break;
+    __syncwarp();   // every lane is done with task i's buffers before they are refilled
   }
+  cp_async_wait_all();
 }
 
 // Host-side entry points of the kernels; each is defined by the translation unit that

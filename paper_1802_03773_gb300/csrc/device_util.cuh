@@ -91,6 +91,14 @@ __device__ __forceinline__ void fence_proxy_async() {
   asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
 }
 
+// Per-thread asynchronous 16-byte copies global -> shared (cp.async, tracked per thread by
+// commit groups): both addresses 16-byte aligned.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src) {
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(smem_u32(dst)), "l"(src) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;" ::: "memory"); }
+
 // The 16-byte-aligned interior [h, h + ni) of the element range [0, count) starting at g.
 template <typename T>
 __device__ __forceinline__ void interior(const T* g, int64_t count, int& h, int& ni) {

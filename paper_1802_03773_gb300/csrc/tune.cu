@@ -173,16 +173,17 @@ qrkit_status apply_choice(qrkit_ctx* ctx, const BlockChoice& c) {
 std::vector<BlockChoice> block_candidates(size_t elem) {
   std::vector<BlockChoice> c;
   for (const int km : {0, 1})
-    for (const int64_t s : {kDefaultSupertile, (int64_t)4096, (int64_t)16384}) {
+    for (const int64_t s : {kDefaultSupertile, (int64_t)16384}) {
       BlockChoice t;
       t.supertile = s;
       t.key_major = km;
       c.push_back(t);
     }
-  BlockChoice w4;
-  w4.warps = 4;
-  w4.key_major = 0;
-  c.push_back(w4);
+  for (const int w : {4, 6}) {
+    BlockChoice t;
+    t.warps = w;
+    c.push_back(t);
+  }
   for (const TileBudget& b : budget_candidates(elem)) {
     BlockChoice t;
     t.tasks = false;
