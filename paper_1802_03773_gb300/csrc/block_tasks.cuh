@@ -456,20 +456,29 @@ __host__ __device__ constexpr int warp_desc_bytes(int entry_bytes) {
   return kHdrBufs * (int)sizeof(TaskHdr) + kEntBufs * 32 * entry_bytes;
 }
 
+// Buffers of a warp, addressed by slot numbers (header slot i mod 4, entry slot i mod 3, data
+// slot i mod 2 for the warp's i-th task; the loops keep the slot numbers as rotating counters).
 struct WarpBufs {
   unsigned char* base;
   int data_bytes;
   int ent_bytes;   // one entry buffer
-  __device__ __forceinline__ TaskHdr* hdr(int64_t i) const {
-    return reinterpret_cast<TaskHdr*>(base + (int)(i % kHdrBufs) * (int)sizeof(TaskHdr));
+  __device__ __forceinline__ TaskHdr* hdr(int slot) const {
+    return reinterpret_cast<TaskHdr*>(base + slot * (int)sizeof(TaskHdr));
   }
-  __device__ __forceinline__ unsigned char* ent(int64_t i) const {
-    return base + kHdrBufs * (int)sizeof(TaskHdr) + (int)(i % kEntBufs) * ent_bytes;
+  __device__ __forceinline__ unsigned char* ent(int slot) const {
+    return base + kHdrBufs * (int)sizeof(TaskHdr) + slot * ent_bytes;
   }
-  __device__ __forceinline__ unsigned char* data(int64_t i) const {
-    return base + kHdrBufs * (int)sizeof(TaskHdr) + kEntBufs * ent_bytes + (int)(i & 1) * data_bytes;
+  __device__ __forceinline__ unsigned char* data(int slot) const {
+    return base + kHdrBufs * (int)sizeof(TaskHdr) + kEntBufs * ent_bytes + slot * data_bytes;
   }
 };
+__device__ __forceinline__ int next3(int s) { return s == 2 ? 0 : s + 1; }
+
+// lane / G and 32 / G for the run-time group sizes G = 1..4 (no integer division).
+__device__ __forceinline__ int lane_group(int lane, int G) {
+  return G == 1 ? lane : (G == 2 ? lane >> 1 : (G == 3 ? (lane * 11) >> 5 : lane >> 2));
+}
+__device__ __forceinline__ int blocks_per_task(int G) { return G == 1 ? 32 : (G == 2 ? 16 : (G == 3 ? 10 : 8)); }
 
 // The slots of a block in a task's data buffer (group grp of a task of G lanes per block and
 // M columns): J's superset at the J slot, b's after the P J slots; the values start at the
@@ -571,7 +580,7 @@ __device__ __forceinline__ void issue_hdr(const TaskHdr* g, int64_t t, int64_t T
 __device__ __forceinline__ void issue_ent(const TaskEntry* g, int64_t t, int64_t T, const TaskHdr* sh,
                                           unsigned char* s, int lane) {
   if (t >= T) return;
-  const int P = task_blocks(group_lanes(sh->key));
+  const int P = blocks_per_task(group_lanes(sh->key));
   if (lane < P) cp_async16(s + 16 * lane, g + sh->first + lane);
 }
 template <typename T>
@@ -579,8 +588,8 @@ __device__ __forceinline__ void issue_data(const TaskArgs<T>& A, int64_t t, cons
                                            unsigned char* db, int lane) {
   if (t >= A.num_tasks) return;
   const int key = sh->key;
-  const int G = group_lanes(key), M = (key & 7) + 1, P = task_blocks(G);
-  const int grp = lane / G, q = lane - grp * G;
+  const int G = group_lanes(key), M = (key & 7) + 1, P = blocks_per_task(G);
+  const int grp = lane_group(lane, G), q = lane - grp * G;
   if (grp >= P) return;
   const TaskEntry e = reinterpret_cast<const TaskEntry*>(se)[grp];
   const T* gJ = A.J + sh->v0 + e.v;
@@ -687,22 +696,28 @@ __global__ void __launch_bounds__(32 * kTaskMaxWarps, sizeof(T) == 4 ? QRKIT_TAS
   issue_ent(A.ent, t0 + stride, NT, W.hdr(1), W.ent(1), lane);
   issue_data<T>(A, t0, W.hdr(0), W.ent(0), W.data(0), lane);
   cp_async_commit();
-  for (int64_t i = 0, t = t0; t < NT; ++i, t += stride) {
+  int sh = 0, se = 0, sd = 0;   // slots of task i
+  for (int64_t t = t0; t < NT; t += stride) {
     cp_async_wait_all();
     __syncwarp();   // task i's data, task i + 1's entries and task i + 2's header have landed
-    issue_hdr(A.hdr, t + 3 * stride, NT, W.hdr(i + 3), lane);
-    issue_ent(A.ent, t + 2 * stride, NT, W.hdr(i + 2), W.ent(i + 2), lane);
-    issue_data<T>(A, t + stride, W.hdr(i + 1), W.ent(i + 1), W.data(i + 1), lane);
+    const int sh1 = (sh + 1) & 3, sh2 = (sh + 2) & 3, sh3 = (sh + 3) & 3;
+    const int se1 = next3(se), se2 = next3(se1);
+    issue_hdr(A.hdr, t + 3 * stride, NT, W.hdr(sh3), lane);
+    issue_ent(A.ent, t + 2 * stride, NT, W.hdr(sh2), W.ent(se2), lane);
+    issue_data<T>(A, t + stride, W.hdr(sh1), W.ent(se1), W.data(sd ^ 1), lane);
     cp_async_commit();
-    const TaskHdr h = *W.hdr(i);
+    const TaskHdr h = *W.hdr(sh);
     switch (h.key) {
 #define QRKIT_TASK_CASE(k) \
-  case k: run_task<T, ((k) >> 3) + 1, ((k) & 7) + 1, SEL>(A, h, W.ent(i), W.data(i), lane); break;
+  case k: run_task<T, ((k) >> 3) + 1, ((k) & 7) + 1, SEL>(A, h, W.ent(se), W.data(sd), lane); break;
       QRKIT_TASK_KEYS(QRKIT_TASK_CASE)
 #undef QRKIT_TASK_CASE
       default: if (lane == 0) record(A.status, QRKIT_EINVAL); break;
     }
     __syncwarp();   // every lane is done with task i's buffers before they are refilled
+    sh = sh1;
+    se = se1;
+    sd ^= 1;
   }
   cp_async_wait_all();
 }
@@ -743,7 +758,7 @@ __device__ __forceinline__ void issue_ref_ent(const RefineTaskArgs& A, const Ref
   int key;
   int64_t local;
   RT.key_of(t, key, local);
-  const int P = task_blocks(group_lanes(key));
+  const int P = blocks_per_task(group_lanes(key));
   const int64_t cap = A.key_off[key + 1] - A.key_off[key];
   const int64_t cnt = (int64_t)A.rcount[key] < cap ? (int64_t)A.rcount[key] : cap;
   const int64_t idx = local * P + lane;
@@ -765,8 +780,8 @@ __device__ __forceinline__ void issue_ref_data(const RefineTaskArgs& A, const Re
   int key;
   int64_t local;
   RT.key_of(t, key, local);
-  const int G = group_lanes(key), M = (key & 7) + 1, P = task_blocks(G);
-  const int grp = lane / G, q = lane - grp * G;
+  const int G = group_lanes(key), M = (key & 7) + 1, P = blocks_per_task(G);
+  const int grp = lane_group(lane, G), q = lane - grp * G;
   if (grp >= P) return;
   const RefEntry e = reinterpret_cast<const RefEntry*>(se)[grp];
   const float* gJ = A.J + e.v;
@@ -833,23 +848,27 @@ __global__ void __launch_bounds__(32 * kTaskMaxWarps, 2) block_task_refine_kerne
   issue_ref_ent(A, RT, t0 + stride, W.ent(1), lane);
   issue_ref_data(A, RT, t0, W.ent(0), W.data(0), lane);
   cp_async_commit();
-  for (int64_t i = 0, t = t0; t < RT.total; ++i, t += stride) {
+  int se = 0, sd = 0;   // slots of task i
+  for (int64_t t = t0; t < RT.total; t += stride) {
     cp_async_wait_all();
     __syncwarp();   // task i's data and task i + 1's entries have landed
-    issue_ref_ent(A, RT, t + 2 * stride, W.ent(i + 2), lane);
-    issue_ref_data(A, RT, t + stride, W.ent(i + 1), W.data(i + 1), lane);
+    const int se1 = next3(se), se2 = next3(se1);
+    issue_ref_ent(A, RT, t + 2 * stride, W.ent(se2), lane);
+    issue_ref_data(A, RT, t + stride, W.ent(se1), W.data(sd ^ 1), lane);
     cp_async_commit();
     int key;
     int64_t local;
     RT.key_of(t, key, local);
     switch (key) {
 #define QRKIT_REFINE_CASE(k) \
-  case k: refine_task<((k) >> 3) + 1, ((k) & 7) + 1>(A, W.ent(i), W.data(i), lane); break;
+  case k: refine_task<((k) >> 3) + 1, ((k) & 7) + 1>(A, W.ent(se), W.data(sd), lane); break;
       QRKIT_TASK_KEYS(QRKIT_REFINE_CASE)
 #undef QRKIT_REFINE_CASE
       default: break;
     }
     __syncwarp();   // every lane is done with task i's buffers before they are refilled
+    se = se1;
+    sd ^= 1;
   }
   cp_async_wait_all();
 }
