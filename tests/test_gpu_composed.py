@@ -124,3 +124,48 @@ def test_dense_tensor_core_tiles_fp32_refined(s, K):
     assert rel(out["p"], p_ref) <= 1e-5
     out0 = run(d32, "fp32", refine_steps=0)
     assert rel(out0["p"], p_ref) <= 1e-3
+
+
+@pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_refined", 1e-5)])
+def test_dense_hcat_solve_replays_in_cuda_graph(precision, tol):
+    """factor + solve of the 200-block workload, captured once in a CUDA graph after a warm-up
+    call (no allocation, upload or host synchronisation inside) and replayed on new values of J,
+    S and b: every replay matches the oracle of its inputs."""
+    torch = cuda_or_skip()
+    from paper_1802_03773_gb300 import Context, qrkit
+    dt = np.float64 if precision == "fp64" else np.float32
+    stream = torch.cuda.Stream()
+    ctx = Context(0, stream=stream, precision=precision)
+    d0 = block_angular_dense(dtype=dt)
+    K, n, m, s = d0["K"], d0["n"], d0["m"], d0["s"]
+    ctx.plan_blocks(np.full(K, n), np.full(K, m), qrkit.COUPLED_DENSE, shared_cols=s)
+    J0, S0, b0 = (torch.from_numpy(a).cuda() for a in packed(d0, dt))
+    J, S, b = J0.clone(), S0.clone(), b0.clone()
+    p = torch.empty(K * m + s, device="cuda", dtype=ctx.dtype)
+    torch.cuda.synchronize()
+    steps = 0 if precision == "fp64" else 1
+
+    def solve():
+        ctx.factor(J, S, None, d0["lam"])
+        ctx.solve(b, p, refine_steps=steps)
+
+    with torch.cuda.stream(stream):
+        solve()   # warm-up: workspaces and tables are created here
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        solve()
+    for seed in (5, 6):
+        d = block_angular_dense(seed_offset=seed, dtype=dt)
+        Jn, Sn, bn = (torch.from_numpy(a).cuda() for a in packed(d, dt))
+        torch.cuda.synchronize()
+        with torch.cuda.stream(stream):
+            J.copy_(Jn)
+            S.copy_(Sn)
+            b.copy_(bn)
+            graph.replay()
+        stream.synchronize()
+        ctx.sync_status()
+        p_ref, _ = st.factor_and_solve(problem_from(d))
+        assert rel(p.cpu().numpy().astype(np.float64), p_ref) <= tol
+    ctx.close()
