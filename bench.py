@@ -237,6 +237,38 @@ def _curvefit_batch(ctx, specs, dev, stream):
     return x, x0, data, npts, kcs
 
 
+def _curvefit_problems(specs, dev, stream):
+    """Per-problem host arrays (data (P, 2), x0 = [t | control points]) of curve-fit problems,
+    the data synthesised on the GPU by the library's own model."""
+    from paper_1802_03773_gb300 import Context
+    ctx = Context(dev.index, stream=stream, precision="fp64")
+    _, x0, data, npts, kcs = _curvefit_batch(ctx, specs, dev, stream)
+    dh = data.cpu().numpy().reshape(-1, 2)
+    ctx.close()
+    NP = sum(npts)
+    out, p, c = [], 0, NP
+    for n, kc in zip(npts, kcs):
+        out.append((dh[p:p + n], np.concatenate([x0[p:p + n], x0[c:c + 2 * kc]])))
+        p += n
+        c += 2 * kc
+    return out
+
+
+def _convergence(h, times, target, iters):
+    """Problems whose best cost reaches target, iterations and wall-clock latency to get there."""
+    from paper_1802_03773_gb300 import learned
+    it = learned.iterations_to(h, target)
+    ok = np.isfinite(it)
+    r = {"reached": int(ok.sum()), "of": int(it.size),
+         "iterations_mean_all": float(np.where(ok, it, iters + 1).mean())}
+    if ok.any():
+        its = it[ok].astype(int)
+        lat = times[its - 1]
+        r.update({"iterations_p50": float(np.percentile(its, 50)), "iterations_p99": float(np.percentile(its, 99)),
+                  "latency_ms_p50": float(np.percentile(lat, 50)), "latency_ms_p99": float(np.percentile(lat, 99))})
+    return r
+
+
 def other_workloads(dev, stream, only=None):
     """The remaining configurations, each timed briefly (CUDA events, after warm-up); `only`
     restricts the run to the workloads whose key starts with it."""
@@ -403,6 +435,39 @@ def other_workloads(dev, stream, only=None):
             "workload": f"1024 problems, {sum(npts)} points in total, Nielsen damping, CUDA-graph iterations",
             "value": 1000.0 / ms, "unit": "LM iterations/s (all problems)", "ms_per_iteration": ms}
         ctx.close()
+    if want("batched_lm_convergence"):
+        # the same kind of batch solved towards convergence with Nielsen's rule and with the learned
+        # damping policy (trained here on 128 smaller problems); the FP64 optimum of every problem
+        # comes from FP64 LM polishing the better final point of the two runs
+        from paper_1802_03773_gb300 import learned
+        from workloads import mlp_init
+        g = np.random.default_rng(7)
+        specs = [(int(g.integers(500, 20001)), int(g.integers(16, 257)), 3000 + i) for i in range(1024)]
+        batch = learned.Batch(_curvefit_problems(specs, dev, stream))
+        tspecs = [(int(g.integers(500, 3001)), int(g.integers(16, 65)), 9000 + i) for i in range(128)]
+        t0 = time.perf_counter()
+        params, nsamples, _ = learned.train_policy(learned.Batch(_curvefit_problems(tspecs, dev, stream)),
+                                                   mlp_init(7), device=dev.index)
+        train_s = time.perf_counter() - t0
+        iters = 150
+        hn, _, tn, xn = learned.run(batch, iters=iters, with_times=True, device=dev.index)
+        hm, _, tm, xm = learned.run(batch, iters=iters, params=params, with_times=True, device=dev.index)
+        use_m = hm[-1] < hn[-1]
+        xb = xn.copy()
+        for k in np.nonzero(use_m)[0]:
+            t_sl = slice(batch.p0[k], batch.p0[k + 1])
+            c_sl = slice(batch.NP + batch.c0[k], batch.NP + batch.c0[k + 1])
+            xb[t_sl], xb[c_sl] = xm[t_sl], xm[c_sl]
+        h64, _ = learned.run(batch, iters=40, precision="fp64", x0=xb, device=dev.index)
+        opt = np.minimum(h64[-1], np.minimum(hn[-1], hm[-1]))
+        res = {"workload": f"1024 problems, {batch.NP} points, Kc ~ U{{16..256}}, FP32-refined, {iters} iterations",
+               "policy_training_s": train_s, "training_samples": int(nsamples),
+               "ms_per_iteration": {"nielsen": float(tn[-1] / iters), "mlp": float(tm[-1] / iters)}}
+        for tol in (1e-6, 1e-3):
+            res[f"within_{tol:g}_of_fp64_optimum"] = {
+                "nielsen": _convergence(hn, tn, opt * (1.0 + tol), iters),
+                "mlp": _convergence(hm, tm, opt * (1.0 + tol), iters)}
+        out["batched_lm_convergence_1024"] = res
     return out
 
 

@@ -153,32 +153,43 @@ def train_policy(batch: Batch, init_params, horizon=6, dagger_rounds=2, iters=60
     return params, X.shape[0], losses[-1]
 
 
-def run(batch: Batch, iters=60, lam0=1e-3, params=None, precision="fp32_refined", refine_steps=1, device=0):
-    """LM with Nielsen's rule (params None) or the MLP policy; returns (best cost so far per
-    iteration (iters, B), final x per problem)."""
+def run(batch: Batch, iters=60, lam0=1e-3, params=None, precision="fp32_refined", refine_steps=1, device=0,
+        x0=None, with_times=False):
+    """LM with Nielsen's rule (params None) or the MLP policy, from batch.x0 (or the packed x0
+    given); returns (best cost so far per iteration (iters, B), final x per problem) and, with
+    with_times, the wall-clock milliseconds from the start to the end of every iteration
+    (each iteration returns its states to the host, so the clock reads completed work)."""
+    import time
+
     import torch
     stream = torch.cuda.Stream(device)
     ctx = Context(device, stream=stream, precision=precision)
     dev = ctx.device
     with torch.cuda.stream(stream):
         data = torch.from_numpy(batch.data).to(dev)
-        x = torch.from_numpy(batch.x0).to(dev)
+        x = torch.from_numpy(batch.x0 if x0 is None else np.asarray(x0, np.float64)).to(dev)
     ctx.lm_plan(batch.npts, batch.kcs, data)
     if params is not None:
         ctx.mlp_init(params)
         ctx.lm_set_policy(True)
     st = ctx.lm_states(lam0)
     best = np.full(batch.B, np.inf)
-    hist = []
+    hist, times = [], []
+    stream.synchronize()
+    t0 = time.perf_counter()
     for _ in range(iters):
         ctx.lm_step(x, st, refine_steps=refine_steps)
         a = _states_to_arrays(st)
+        times.append(1000.0 * (time.perf_counter() - t0))
         now = np.where(a["acc"] == 1, a["cost_new"], a["cost"])
         best = np.minimum(best, now)
         hist.append(best.copy())
     stream.synchronize()
-    xs = batch.split(x.cpu().numpy())
+    xp = x.cpu().numpy()
+    xs = batch.split(xp)
     ctx.close()
+    if with_times:
+        return np.array(hist), xs, np.array(times), xp
     return np.array(hist), xs
 
 
