@@ -148,3 +148,109 @@ def test_banded_parallel_full_size_optimality():
     r = d["b"].astype(np.float64) - bd.matvec(start, vals, x)
     gr = bd.rmatvec(start, vals, r, d["n"]) - 1e-3 * D * D * x
     assert np.linalg.norm(gr) / (np.linalg.norm(vals) ** 2 * np.linalg.norm(x)) < 1e-7
+
+
+def banded_batch_optimality(d, p, lam, chunk=256):
+    """Worst instance of ||J^T (b - J x) - lambda D^2 x|| / (||J||_F^2 ||x||) over a batch held
+    on the device (workloads.device layout), computed on the device with plain PyTorch ops in
+    double, a chunk of instances at a time."""
+    import torch
+    vals, b = d["vals"], d["b"]
+    cols, row0, col0 = d["cols"], d["row0"], d["col0"]
+    w, rpc = d["w"], d["rows_per_col"]
+    dev = vals.device
+    x = p.double()
+    worst = 0.0
+    for k0 in range(0, cols.size, chunk):
+        k1 = min(cols.size, k0 + chunk)
+        R0, R1, C0, C1 = int(row0[k0]), int(row0[k1]), int(col0[k0]), int(col0[k1])
+        nk = k1 - k0
+        inst = torch.repeat_interleave(torch.arange(nk, device=dev), torch.from_numpy(rpc * cols[k0:k1]).to(dev))
+        rloc = torch.arange(R1 - R0, device=dev) - torch.from_numpy(row0[k0:k1] - R0).to(dev)[inst]
+        base = torch.from_numpy(col0[k0:k1] - C0).to(dev)[inst] + rloc // rpc
+        idx = base[:, None] + torch.arange(w, device=dev)[None, :]
+        end = torch.from_numpy(col0[k0 + 1:k1 + 1] - C0).to(dev)[inst][:, None]
+        idx = torch.where(idx < end, idx, torch.zeros_like(idx))   # truncated band ends hold zeros
+        V = vals[R0:R1].double()
+        xc = x[C0:C1]
+        r = b[R0:R1].double() - (V * xc[idx]).sum(1)
+        flat = idx.reshape(-1)
+        g = torch.zeros(C1 - C0, dtype=torch.float64, device=dev).index_add_(0, flat, (V * r[:, None]).reshape(-1))
+        D2 = torch.zeros(C1 - C0, dtype=torch.float64, device=dev).index_add_(0, flat, (V * V).reshape(-1))
+        D2 = torch.where(D2 > 0, D2, torch.ones_like(D2))
+        g -= lam * D2 * xc
+        cinst = torch.repeat_interleave(torch.arange(nk, device=dev), torch.from_numpy(cols[k0:k1]).to(dev))
+        g2 = torch.zeros(nk, dtype=torch.float64, device=dev).index_add_(0, cinst, g * g)
+        x2 = torch.zeros(nk, dtype=torch.float64, device=dev).index_add_(0, cinst, xc * xc)
+        J2 = torch.zeros(nk, dtype=torch.float64, device=dev).index_add_(0, inst, (V * V).sum(1))
+        worst = max(worst, float((g2.sqrt() / (J2 * x2.sqrt())).max()))
+        del inst, rloc, base, idx, end, V, r, flat, g, D2, cinst
+    return worst
+
+
+@pytest.mark.slow
+def test_banded_batch_full_size_4096_instances():
+    """The 4096-instance batch of workload 4 at full size (n ~ U{1000..100000}, 4n rows each:
+    about 2e8 columns and 8e8 rows, drawn on the device), parallel solver, FP32 refined: every
+    instance satisfies the first-order condition J^T (b - J x) = lambda D^2 x to float accuracy
+    (checked on the device); the smallest and the largest instance, copied to the host, match
+    the oracle to 1e-5."""
+    torch = cuda_or_skip()
+    from paper_1802_03773_gb300 import Context
+    from workloads import banded_batch_shapes
+    from workloads.device import banded_batch_device
+    cols = banded_batch_shapes()
+    d = banded_batch_device(cols, seed_offset=0)
+    ctx = Context(0, precision="fp32_refined")
+    ctx.plan_banded(list(cols), rows_per_col=4, window=8, solver=SOLVER["parallel"])
+    N = int(cols.sum())
+    p = torch.empty(N, device="cuda", dtype=torch.float32)
+    ctx.factor_solve(d["vals"].reshape(-1), d["b"], p, None, lam=1e-3, refine_steps=2)
+    ctx.sync_status()
+    ctx.close()
+    assert banded_batch_optimality(d, p, 1e-3) < 1e-6
+    for k in (int(np.argmin(cols)), int(np.argmax(cols))):
+        r0, r1, c0, n = int(d["row0"][k]), int(d["row0"][k + 1]), int(d["col0"][k]), int(cols[k])
+        vals = d["vals"][r0:r1].cpu().numpy()
+        b = d["b"][r0:r1].cpu().numpy()
+        start = np.arange(r1 - r0, dtype=np.int64) // 4
+        x, *_ = bd.damped_solve(start, vals, b, n, 1e-3)
+        got = p[c0:c0 + n].cpu().numpy().astype(np.float64)
+        assert np.linalg.norm(got - x) / np.linalg.norm(x) <= 1e-5
+
+
+def test_banded_batch_solve_replays_in_cuda_graph():
+    """The parallel banded factor + solve with refinement, captured once in a CUDA graph after a
+    warm-up call and replayed on new J and b, gives the eager result bit for bit."""
+    torch = cuda_or_skip()
+    from paper_1802_03773_gb300 import Context
+    from workloads.device import banded_batch_device
+    cols = np.array([1500, 3000, 2200, 4100], dtype=np.int64)
+    d0 = banded_batch_device(cols, seed_offset=1)
+    d1 = banded_batch_device(cols, seed_offset=2)
+    stream = torch.cuda.Stream()
+    ctx = Context(0, stream=stream, precision="fp32_refined")
+    ctx.plan_banded(list(cols), rows_per_col=4, window=8, solver=SOLVER["parallel"])
+    J, b = d0["vals"].reshape(-1).clone(), d0["b"].clone()
+    p = torch.empty(int(cols.sum()), device="cuda", dtype=torch.float32)
+    torch.cuda.synchronize()
+    solve = lambda: ctx.factor_solve(J, b, p, None, lam=1e-3, refine_steps=2)
+    with torch.cuda.stream(stream):
+        solve()
+    stream.synchronize()
+    graph = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(graph, stream=stream):
+        solve()
+    with torch.cuda.stream(stream):
+        J.copy_(d1["vals"].reshape(-1))
+        b.copy_(d1["b"])
+        graph.replay()
+    stream.synchronize()
+    replayed = p.clone()
+    with torch.cuda.stream(stream):
+        solve()
+    stream.synchronize()
+    ctx.sync_status()
+    assert torch.equal(replayed, p)
+    assert banded_batch_optimality(d1, p, 1e-3) < 1e-6
+    ctx.close()
