@@ -554,29 +554,41 @@ def run_ours(args):
         from paper_1802_03773_gb300.replicas import max_over_ranks
         total_ms = max_over_ranks(total_ms, dev)
 
-    # end-to-end through the public API with host buffers: pinned H2D of J and b, the solve,
-    # D2H of p, all inside the timed region
+    # end-to-end through the public API with host buffers: every step copies its J and b from
+    # pinned host memory and reads its p back, all inside the timed region; the copy of step
+    # i + 1 runs on its own stream into the other of two device input sets while step i solves
     hJ = torch.from_numpy(d["vals"]).pin_memory()
     hb = torch.from_numpy(d["b"]).pin_memory()
-    hp = torch.empty(ncols, dtype=torch.float32).pin_memory()
-    dJ, db = Js[0], bs[0]
-    with torch.cuda.stream(stream):
-        for _ in range(2):
-            dJ.copy_(hJ, non_blocking=True)
-            db.copy_(hb, non_blocking=True)
-            ctx.factor_solve(dJ, db, p, None, refine_steps=refine)
-            hp.copy_(p, non_blocking=True)
-        stream.synchronize()
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(args.steps):
-            dJ.copy_(hJ, non_blocking=True)
-            db.copy_(hb, non_blocking=True)
-            ctx.factor_solve(dJ, db, p, None, refine_steps=refine)
-            hp.copy_(p, non_blocking=True)
-        e1.record(stream)
-        stream.synchronize()
+    hps = [torch.empty(ncols, dtype=torch.float32).pin_memory() for _ in range(2)]
+    ps = [p, torch.empty_like(p)]
+    cs = torch.cuda.Stream(dev)
+    copied = [torch.cuda.Event() for _ in range(2)]
+    freed = [torch.cuda.Event() for _ in range(2)]
+
+    def e2e_step(i):
+        k = i & 1
+        cs.wait_event(freed[k])          # the solve that last read input set k is done
+        with torch.cuda.stream(cs):
+            Js[k].copy_(hJ, non_blocking=True)
+            bs[k].copy_(hb, non_blocking=True)
+        copied[k].record(cs)
+        stream.wait_event(copied[k])
+        with torch.cuda.stream(stream):
+            ctx.factor_solve(Js[k], bs[k], ps[k], None, refine_steps=refine)
+            freed[k].record(stream)
+            hps[k].copy_(ps[k], non_blocking=True)
+
+    for i in range(3):
+        e2e_step(i)
+    torch.cuda.synchronize()
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    cs.wait_event(e0)
+    for i in range(args.steps):
+        e2e_step(i)
+    e1.record(stream)
+    torch.cuda.synchronize()
     e2e_ms = e0.elapsed_time(e1) / args.steps
     ctx.sync_status()
 
@@ -640,7 +652,8 @@ def run_ours(args):
                      "algorithmic_bytes_per_launch": alg, "avg_launch_ms": kavg},
         "e2e": {"value": ws * 1000.0 / e2e_ms, "unit": UNIT,
                 "h2d_bytes_per_step": int(hJ.numel() * 4 + hb.numel() * 4),
-                "d2h_bytes_per_step": int(hp.numel() * 4)},
+                "d2h_bytes_per_step": int(hps[0].numel() * 4),
+                "overlap": "copy of step i + 1 on its own stream during the solve of step i"},
         "gpu_launches": launches,
         "clocks": clk,
         "accuracy": None,
