@@ -253,17 +253,14 @@ __global__ void __launch_bounds__(kCompThreads) cr_compress_kernel(CRArgs<T> A) 
       bad = true;
       continue;
     }
+    // the row over the block row's 16 columns: its w values start at column o
     T a[17];
-#pragma unroll
-    for (int j = 0; j < 17; ++j) a[j] = T(0);
     const T* src = A.J + r * A.w;
 #pragma unroll
-    for (int q = 0; q < kCB; ++q)
-      if (q < A.w && st + q < N) {
-#pragma unroll
-        for (int cc = 0; cc < 2 * kCB; ++cc)
-          if (cc == (int)o + q) a[cc] = src[q];
-      }
+    for (int cc = 0; cc < 2 * kCB; ++cc) {
+      const int64_t q = cc - o;
+      a[cc] = (q >= 0 && q < A.w && st + q < N) ? src[q] : T(0);
+    }
     a[16] = A.b[r];
     res += merge_row(Tr, a, (int)o);
   }
