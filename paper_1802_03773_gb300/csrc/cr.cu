@@ -51,32 +51,92 @@ __device__ __forceinline__ T wsum(T v) {
   return v;
 }
 
+// Square root and reciprocal of the front QR: the hardware approximations for float
+// (sqrt.approx / rcp.approx, about one ulp: far below the rounding the factorization itself
+// accumulates), IEEE for double.
+__device__ __forceinline__ float qr_sqrt(float x) {
+  float r;
+  asm("sqrt.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double qr_sqrt(double x) { return sqrt(x); }
+__device__ __forceinline__ float qr_rcp(float x) {
+  float r;
+  asm("rcp.approx.ftz.f32 %0, %1;" : "=f"(r) : "f"(x));
+  return r;
+}
+__device__ __forceinline__ double qr_rcp(double x) { return 1.0 / x; }
+
+__host__ __device__ constexpr int pow2_ceil(int m) { return m <= 1 ? 1 : 2 * pow2_ceil((m + 1) / 2); }
+__host__ __device__ constexpr int log2_exact(int p) { return p <= 1 ? 0 : 1 + log2_exact(p / 2); }
+
+// Sums of M per-lane values over the warp, returned in every lane (v[j] = sum over lanes).
+// Transpose reduction: with the values padded to P = 2^ceil(log2 M), each butterfly stage
+// sends half of the remaining values to the partner lane and keeps the other half, so after
+// log2 P stages each lane holds one partial sum (of value lane >> (5 - log2 P)); plain
+// butterfly stages finish the sums, and one broadcast per value returns them.  About
+// P - 1 + M shuffles instead of 5 M; every lane reads the same lane's sum, so all lanes hold
+// the same bits.
+template <typename T, int M>
+__device__ __forceinline__ void warp_allreduce_many(T (&v)[M], int lane) {
+  constexpr int P = pow2_ceil(M);
+  constexpr int S = 5 - log2_exact(P);
+  static_assert(P <= 32, "at most 32 values");
+  T w[P];
+#pragma unroll
+  for (int i = 0; i < P; ++i) w[i] = i < M ? v[i] : T(0);
+  int d = 16;
+#pragma unroll
+  for (int h = P / 2; h >= 1; h /= 2, d >>= 1) {
+    const bool up = (lane & d) != 0;
+#pragma unroll
+    for (int i = 0; i < h; ++i) {
+      const T send = up ? w[i] : w[h + i];
+      const T keep = up ? w[h + i] : w[i];
+      w[i] = keep + __shfl_xor_sync(0xffffffffu, send, d);
+    }
+  }
+#pragma unroll
+  for (int e = 0; e < S; ++e) {
+    w[0] += __shfl_xor_sync(0xffffffffu, w[0], d);
+    d >>= 1;
+  }
+#pragma unroll
+  for (int jj = 0; jj < M; ++jj) v[jj] = __shfl_sync(0xffffffffu, w[0], jj << S);
+}
+
 // Householder QR of a 32-row front held one row per lane (a[0..NC-1] columns, a[NC] the
 // right-hand side), reducing columns 0..NK-1 in order.  Row k of the result holds R's row k
-// (lane k); rows below NK are zero in the reduced columns.
+// (lane k); rows below NK are zero in the reduced columns.  Column K of the recursion: its
+// reflector, then the update of the NC - K trailing columns (and rhs), whose dot products
+// with v are summed over the warp together.
+template <typename T, int NC, int K, int NK>
+__device__ __forceinline__ void warp_qr_col(T (&a)[NC + 1], int lane) {
+  const T x = a[K];
+  const T sq = wsum(lane > K ? x * x : T(0));
+  const T alpha = __shfl_sync(0xffffffffu, x, K);
+  const T norm = qr_sqrt(alpha * alpha + sq);
+  T beta = T(0), tau = T(0), scale = T(0);
+  if (norm != T(0)) {
+    beta = alpha >= T(0) ? -norm : norm;
+    tau = (beta - alpha) * qr_rcp(beta);
+    scale = qr_rcp(alpha - beta);
+  }
+  const T v = lane > K ? x * scale : (lane == K ? T(1) : T(0));
+  T dv[NC - K];
+#pragma unroll
+  for (int jj = 0; jj < NC - K; ++jj) dv[jj] = v * a[K + 1 + jj];
+  warp_allreduce_many<T, NC - K>(dv, lane);
+#pragma unroll
+  for (int jj = 0; jj < NC - K; ++jj) a[K + 1 + jj] -= (dv[jj] * tau) * v;
+  if (lane == K) a[K] = beta;
+  else if (lane > K) a[K] = T(0);
+  if constexpr (K + 1 < NK) warp_qr_col<T, NC, K + 1, NK>(a, lane);
+}
+
 template <typename T, int NC, int NK>
 __device__ __forceinline__ void warp_qr(T (&a)[NC + 1], int lane) {
-#pragma unroll
-  for (int k = 0; k < NK; ++k) {
-    const T x = a[k];
-    const T sq = wsum(lane > k ? x * x : T(0));
-    const T alpha = __shfl_sync(0xffffffffu, x, k);
-    const T norm = sqrt(alpha * alpha + sq);
-    T beta = T(0), tau = T(0), scale = T(0);
-    if (norm != T(0)) {
-      beta = alpha >= T(0) ? -norm : norm;
-      tau = (beta - alpha) / beta;
-      scale = T(1) / (alpha - beta);
-    }
-    const T v = lane > k ? x * scale : (lane == k ? T(1) : T(0));
-#pragma unroll
-    for (int j = k + 1; j <= NC; ++j) {
-      const T d = wsum(v * a[j]) * tau;
-      a[j] -= d * v;
-    }
-    if (lane == k) a[k] = beta;
-    else if (lane > k) a[k] = T(0);
-  }
+  warp_qr_col<T, NC, 0, NK>(a, lane);
 }
 
 template <typename T>
