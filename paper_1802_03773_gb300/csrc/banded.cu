@@ -354,6 +354,66 @@ __global__ void band_colnorm_kernel(const float* Jf, const double* Jd, const int
   D[gj] = d == 0.0 ? 1.0 : d;
 }
 
+// Column norms for float J, in two phases per CTA of kColNormCols consecutive global columns.
+// Rows come in groups of rows_per_col per column (group g = rows rpc g .. rpc g + rpc - 1,
+// all starting at column g), so column j's entries are entry t of groups j - t, t < w.
+// Phase 1: one thread per group sums the squares of its rpc rows per entry t (contiguous
+// rpc x w floats, vector loads) into shared memory; phase 2: one thread per column adds its w
+// diagonal partial sums (in double) from groups of its own instance.
+constexpr int kColNormCols = 256;
+__global__ void __launch_bounds__(kColNormCols) band_colnorm_f32_kernel(const float* J, int64_t total_cols,
+                                                                        const int64_t* inst_col0, int64_t num_inst,
+                                                                        int rpc, int w, int vec, double* D) {
+  __shared__ float S[(kColNormCols + kBW - 1) * (kBW + 1)];
+  const int stride = w + 1;   // odd row stride: consecutive columns hit different banks
+  const int64_t j0 = (int64_t)blockIdx.x * kColNormCols;
+  for (int gg = threadIdx.x; gg < kColNormCols + w - 1; gg += kColNormCols) {
+    const int64_t g = j0 - (w - 1) + gg;
+    float acc[kBW];
+#pragma unroll
+    for (int t = 0; t < kBW; ++t) acc[t] = 0.f;
+    if (g >= 0 && g < total_cols) {
+      const float* rows = J + g * rpc * w;
+      if (vec) {   // rpc w a multiple of 4 and J 16-byte aligned
+        const float4* r4 = reinterpret_cast<const float4*>(rows);
+        for (int e = 0; e < rpc * w / 4; ++e) {
+          const float4 v = r4[e];
+          const int t0 = (4 * e) % w;   // w is a multiple of 4 or divides 4 here
+#pragma unroll
+          for (int u = 0; u < 4; ++u) {
+            const float x = u == 0 ? v.x : (u == 1 ? v.y : (u == 2 ? v.z : v.w));
+            const int t = (t0 + u) % w;
+#pragma unroll
+            for (int tt = 0; tt < kBW; ++tt)
+              if (tt == t) acc[tt] += x * x;
+          }
+        }
+      } else {
+        for (int q = 0; q < rpc; ++q)
+#pragma unroll
+          for (int t = 0; t < kBW; ++t)
+            if (t < w) acc[t] += rows[q * w + t] * rows[q * w + t];
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kBW; ++t)
+      if (t < w) S[gg * stride + t] = acc[t];
+  }
+  __syncthreads();
+  const int64_t gj = j0 + threadIdx.x;
+  if (gj >= total_cols) return;
+  int64_t lo = 0, hi = num_inst - 1;
+  while (lo < hi) {   // instance of column gj
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (inst_col0[mid] <= gj) lo = mid; else hi = mid - 1;
+  }
+  const int64_t j = gj - inst_col0[lo];
+  double sum = 0.0;
+  for (int t = 0; t < w && t <= j; ++t) sum += (double)S[(threadIdx.x + w - 1 - t) * stride + t];
+  const double d = sqrt(sum);
+  D[gj] = d == 0.0 ? 1.0 : d;
+}
+
 // Refinement pieces of the parallel path, one thread per row / per column:
 // r = b - J x in double, then g_j = sum_i J_ij r_i - lambda D_j^2 x_j.
 template <typename T>
@@ -494,9 +554,16 @@ static qrkit_status banded_run(qrkit_ctx* ctx, const void* J, const void* b, con
         if (rc != QRKIT_OK) return rc;
       }
     } else {
-      band_colnorm_kernel<<<nblk(B.total_cols, 256), 256, 0, st>>>(
-          sizeof(T) == 4 ? (const float*)J : nullptr, sizeof(T) == 8 ? (const double*)J : nullptr,
-          dcols, dc0, dr0, B.num_inst, B.rows_per_col, B.w, D);
+      if (sizeof(T) == sizeof(float)) {
+        const int rw = B.rows_per_col * B.w;
+        const int vec = (rw % 4 == 0) && (B.w % 4 == 0 || 4 % B.w == 0) &&
+                        (reinterpret_cast<uintptr_t>(J) & 15) == 0;
+        band_colnorm_f32_kernel<<<nblk(B.total_cols, kColNormCols), kColNormCols, 0, st>>>(
+            (const float*)J, B.total_cols, dc0, B.num_inst, B.rows_per_col, B.w, vec, D);
+      } else {
+        band_colnorm_kernel<<<nblk(B.total_cols, 256), 256, 0, st>>>(nullptr, (const double*)J, dcols, dc0, dr0,
+                                                                    B.num_inst, B.rows_per_col, B.w, D);
+      }
       ctx->launches += 1;
       QRKIT_CUDA_TRY(ctx, cudaGetLastError());
     }
