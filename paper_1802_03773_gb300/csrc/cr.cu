@@ -528,114 +528,124 @@ __global__ void __launch_bounds__(128) cr_level_kernel(CRArgs<T> A, const int64_
   if (lane == 0 && res != 0.0) atomicAdd(A.res2 + k, res);
 }
 
-// 3. back-substitution of one level: one thread per eliminated block.  rhs from the R rows'
-// own column (c) or from hp; writes xp (padded) and, for real columns, x.
+// 3. back-substitution of one level: eight threads per eliminated block, thread q owns row q
+// of the block's R (own | left | right | rhs): the couplings to the neighbours' solutions
+// are row-local, the triangular solve broadcasts each x_t to the block's threads (width-8
+// shuffles).  rhs from the R rows' own column (c) or from hp; writes xp (padded) and, for
+// real columns, x.  Threads past the last item run the shuffles with nothing to do.
+constexpr int kItemThreads = kCB;
+
 template <typename T>
 __global__ void cr_backsub_kernel(CRArgs<T> A, const int64_t* items, int64_t nitems, int level, int use_hp,
                                   T* x) {
-  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= nitems) return;
-  int64_t k, i;
-  int kind;
-  decode(items[w], k, i, kind);
-  if (kind == 1) return;
-  const int64_t b0 = A.blk0[k], N = A.cols[k];
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t w = tid / kItemThreads;
+  const int q = (int)(tid % kItemThreads);
+  int64_t k = 0, i = 0;
+  int kind = 1;
+  if (w < nitems) decode(items[w], k, i, kind);
+  const bool act = kind != 1;
+  const int64_t b0 = act ? A.blk0[k] : 0, N = act ? A.cols[k] : 0;
   const int64_t G = (N + kCB - 1) / kCB;
   const int64_t beta = i << level, step = (int64_t)1 << level;
-  const T* R = A.Rb + (b0 + beta) * kCB * kRW;
-  T y[kCB];
+  const T* Rq = A.Rb + ((b0 + beta) * kCB + q) * kRW;
+  T y = T(0), diag = T(1);
+  T rq[kCB];
 #pragma unroll
-  for (int q = 0; q < kCB; ++q) y[q] = use_hp ? A.hp[(b0 + beta) * kCB + q] : R[q * kRW + 3 * kCB];
-  if (kind == 0) {
-    const T* xl = A.xp + (b0 + beta - step) * kCB;
+  for (int t = 0; t < kCB; ++t) rq[t] = T(0);
+  if (act) {
+    y = use_hp ? A.hp[(b0 + beta) * kCB + q] : Rq[3 * kCB];
+    if (kind == 0) {
+      const T* xl = A.xp + (b0 + beta - step) * kCB;
 #pragma unroll
-    for (int q = 0; q < kCB; ++q)
+      for (int t = 0; t < kCB; ++t) y -= Rq[kCB + t] * xl[t];
+    }
+    if (beta + step < G) {
+      const T* xr = A.xp + (b0 + beta + step) * kCB;
 #pragma unroll
-      for (int t = 0; t < kCB; ++t) y[q] -= R[q * kRW + kCB + t] * xl[t];
+      for (int t = 0; t < kCB; ++t) y -= Rq[2 * kCB + t] * xr[t];
+    }
+#pragma unroll
+    for (int t = 0; t < kCB; ++t) rq[t] = t > q ? Rq[t] : T(0);
+    diag = Rq[q];
+    if (diag == T(0)) cr_record(A.status, QRKIT_ESINGULAR);
   }
-  if (beta + step < G) {
-    const T* xr = A.xp + (b0 + beta + step) * kCB;
+  T xq = T(0);
 #pragma unroll
-    for (int q = 0; q < kCB; ++q)
-#pragma unroll
-      for (int t = 0; t < kCB; ++t) y[q] -= R[q * kRW + 2 * kCB + t] * xr[t];
+  for (int t = kCB - 1; t >= 0; --t) {   // x_t = (y_t - sum_{u > t} R_tu x_u) / R_tt, bottom up
+    if (q == t) xq = y / diag;
+    const T xt = __shfl_sync(0xffffffffu, xq, t, kItemThreads);
+    y -= rq[t] * xt;                      // rq[t] = 0 unless t > q
   }
-  bool sing = false;
-#pragma unroll
-  for (int q = kCB - 1; q >= 0; --q) {
-    T v = y[q];
-#pragma unroll
-    for (int t = q + 1; t < kCB; ++t) v -= R[q * kRW + t] * y[t];
-    const T d = R[q * kRW + q];
-    if (d == T(0)) sing = true;
-    y[q] = v / d;
-  }
-  if (sing) cr_record(A.status, QRKIT_ESINGULAR);
-  T* xo = A.xp + (b0 + beta) * kCB;
-  const int64_t c0 = A.col0[k];
-#pragma unroll
-  for (int q = 0; q < kCB; ++q) {
-    xo[q] = y[q];
-    if (x && kCB * beta + q < N) x[c0 + kCB * beta + q] = y[q];
+  if (act) {
+    A.xp[(b0 + beta) * kCB + q] = xq;
+    if (x && kCB * beta + q < N) x[A.col0[k] + kCB * beta + q] = xq;
   }
 }
 
 // Refinement, R^T h = g upwards: per level, h_b = R_bb^{-T} g_b for the eliminated blocks ...
+// (eight threads per block; thread q solves for h_q after the h_t, t < q, are broadcast)
 template <typename T>
 __global__ void cr_rt_kernel(CRArgs<T> A, const int64_t* items, int64_t nitems, int level) {
-  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (w >= nitems) return;
-  int64_t k, i;
-  int kind;
-  decode(items[w], k, i, kind);
-  if (kind == 1) return;
-  const int64_t blk = A.blk0[k] + (i << level);
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t w = tid / kItemThreads;
+  const int q = (int)(tid % kItemThreads);
+  int64_t k = 0, i = 0;
+  int kind = 1;
+  if (w < nitems) decode(items[w], k, i, kind);
+  const bool act = kind != 1;
+  const int64_t blk = act ? A.blk0[k] + (i << level) : 0;
   const T* R = A.Rb + blk * kCB * kRW;
-  T* h = A.hp + blk * kCB;
-  const T* g = A.xp + blk * kCB;   // xp holds the updated g during the upward sweep
+  T v = T(0), diag = T(1);
+  T col[kCB];   // column q of R above the diagonal: R_tq, t < q
 #pragma unroll
-  for (int q = 0; q < kCB; ++q) {
-    T v = g[q];
+  for (int t = 0; t < kCB; ++t) col[t] = T(0);
+  if (act) {
+    v = A.xp[blk * kCB + q];   // xp holds the updated g during the upward sweep
 #pragma unroll
-    for (int t = 0; t < q; ++t) v -= R[t * kRW + q] * h[t];
-    h[q] = v / R[q * kRW + q];
+    for (int t = 0; t < kCB; ++t) col[t] = t < q ? R[t * kRW + q] : T(0);
+    diag = R[q * kRW + q];
   }
+  T hq = T(0);
+#pragma unroll
+  for (int t = 0; t < kCB; ++t) {   // h_t = (g_t - sum_{u < t} R_ut h_u) / R_tt, top down
+    if (q == t) hq = v / diag;
+    const T ht = __shfl_sync(0xffffffffu, hq, t, kItemThreads);
+    v -= col[t] * ht;                // col[t] = 0 unless t < q
+  }
+  if (act) A.hp[blk * kCB + q] = hq;
 }
 
 // ... then the blocks that stay (even j at level l) subtract their neighbours' couplings:
-// g_{b_j} -= R_{b_{j-1}}.right^T h_{b_{j-1}} + R_{b_{j+1}}.left^T h_{b_{j+1}}.
+// g_{b_j} -= R_{b_{j-1}}.right^T h_{b_{j-1}} + R_{b_{j+1}}.left^T h_{b_{j+1}}  (eight threads
+// per block, thread q one entry of g).
 template <typename T>
 __global__ void cr_rt_update_kernel(CRArgs<T> A, const int64_t* items, int64_t nitems, int level) {
-  const int64_t w = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t tid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int64_t w = tid / kItemThreads;
+  const int q = (int)(tid % kItemThreads);
   if (w >= nitems) return;
   const int64_t k = items[w] >> 32, j = items[w] & 0xffffffff;
   const int64_t b0 = A.blk0[k], N = A.cols[k];
   const int64_t G = (N + kCB - 1) / kCB;
   const int64_t Gl = (G + ((int64_t)1 << level) - 1) >> level;
   T* g = A.xp + (b0 + (j << level)) * kCB;
-  T acc[kCB];
-#pragma unroll
-  for (int q = 0; q < kCB; ++q) acc[q] = g[q];
+  T acc = g[q];
   if (j >= 1) {
     const int64_t nb = b0 + ((j - 1) << level);
     const T* R = A.Rb + nb * kCB * kRW;
     const T* h = A.hp + nb * kCB;
 #pragma unroll
-    for (int t = 0; t < kCB; ++t)
-#pragma unroll
-      for (int q = 0; q < kCB; ++q) acc[q] -= R[t * kRW + 2 * kCB + q] * h[t];
+    for (int t = 0; t < kCB; ++t) acc -= R[t * kRW + 2 * kCB + q] * h[t];
   }
   if (j + 1 < Gl) {
     const int64_t nb = b0 + ((j + 1) << level);
     const T* R = A.Rb + nb * kCB * kRW;
     const T* h = A.hp + nb * kCB;
 #pragma unroll
-    for (int t = 0; t < kCB; ++t)
-#pragma unroll
-      for (int q = 0; q < kCB; ++q) acc[q] -= R[t * kRW + kCB + q] * h[t];
+    for (int t = 0; t < kCB; ++t) acc -= R[t * kRW + kCB + q] * h[t];
   }
-#pragma unroll
-  for (int q = 0; q < kCB; ++q) g[q] = acc[q];
+  g[q] = acc;
 }
 
 template <typename T>
@@ -834,8 +844,8 @@ static qrkit_status cr_solve_typed(qrkit_ctx* ctx, CRPlan& C, const int64_t* sta
     std::swap(Fc, Fn);
   }
   for (int l = C.levels - 1; l >= 0; --l)
-    CR_LAUNCH(ctx, cr_backsub_kernel<T><<<nblk(C.lvl_n[l], 128), 128, 0, st>>>(A, items + C.lvl_off[l], C.lvl_n[l],
-                                                                               l, 0, x));
+    CR_LAUNCH(ctx, cr_backsub_kernel<T><<<nblk(C.lvl_n[l] * kItemThreads, 128), 128, 0, st>>>(
+                       A, items + C.lvl_off[l], C.lvl_n[l], l, 0, x));
   return QRKIT_OK;
 }
 
@@ -848,14 +858,15 @@ static qrkit_status cr_normal_typed(qrkit_ctx* ctx, CRPlan& C, const double* g, 
   const int64_t* evens = (const int64_t*)C.evens.ptr;
   CR_LAUNCH(ctx, cr_scatter_g_kernel<T><<<nblk(C.total_blocks * kCB, 256), 256, 0, st>>>(A, g));
   for (int l = 0; l < C.levels; ++l) {
-    CR_LAUNCH(ctx, cr_rt_kernel<T><<<nblk(C.lvl_n[l], 128), 128, 0, st>>>(A, items + C.lvl_off[l], C.lvl_n[l], l));
+    CR_LAUNCH(ctx, cr_rt_kernel<T><<<nblk(C.lvl_n[l] * kItemThreads, 128), 128, 0, st>>>(A, items + C.lvl_off[l],
+                                                                                          C.lvl_n[l], l));
     if (C.ev_n[l] > 0)
-      CR_LAUNCH(ctx, cr_rt_update_kernel<T><<<nblk(C.ev_n[l], 128), 128, 0, st>>>(A, evens + C.ev_off[l],
-                                                                                  C.ev_n[l], l));
+      CR_LAUNCH(ctx, cr_rt_update_kernel<T><<<nblk(C.ev_n[l] * kItemThreads, 128), 128, 0, st>>>(
+                         A, evens + C.ev_off[l], C.ev_n[l], l));
   }
   for (int l = C.levels - 1; l >= 0; --l)
-    CR_LAUNCH(ctx, cr_backsub_kernel<T><<<nblk(C.lvl_n[l], 128), 128, 0, st>>>(A, items + C.lvl_off[l], C.lvl_n[l],
-                                                                               l, 1, dx));
+    CR_LAUNCH(ctx, cr_backsub_kernel<T><<<nblk(C.lvl_n[l] * kItemThreads, 128), 128, 0, st>>>(
+                       A, items + C.lvl_off[l], C.lvl_n[l], l, 1, dx));
   return QRKIT_OK;
 }
 
