@@ -22,6 +22,7 @@
 #include <string>
 #include <vector>
 
+#include "device_util.cuh"
 #include "internal.h"
 
 namespace qrkit {
@@ -414,6 +415,96 @@ __global__ void __launch_bounds__(kColNormCols) band_colnorm_f32_kernel(const fl
   D[gj] = d == 0.0 ? 1.0 : d;
 }
 
+// Refinement pieces of the parallel path for float J: the residual r = b - J x of each row as
+// an unevaluated float pair (rh + rl, Dot2: error-free products and sums, the accuracy of a
+// double residual without GB300's slow FP64 pipe), stored in place of a double r ...
+__global__ void band_resid_f32_kernel(const float* J, const float* b, const float* x, const int64_t* inst_cols,
+                                      const int64_t* inst_col0, const int64_t* inst_row0, int64_t num_inst,
+                                      int64_t total_rows, int rpc, int w, float2* r) {
+  const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= total_rows) return;
+  int64_t lo = 0, hi = num_inst - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (inst_row0[mid] <= gi) lo = mid; else hi = mid - 1;
+  }
+  const int64_t i = gi - inst_row0[lo], N = inst_cols[lo], c0 = inst_col0[lo];
+  const int64_t s = i / rpc;
+  const float* row = J + gi * w;
+  float sh = b[gi], sl = 0.f;
+  for (int t = 0; t < w && s + t < N; ++t) {
+    const float a = row[t], xj = -x[c0 + s + t];
+    const float pr = __fmul_rn(a, xj);
+    const float pe = __fmaf_rn(a, xj, -pr);
+    float tt, e;
+    dev::two_sum(sh, pr, tt, e);
+    sh = tt;
+    sl = __fadd_rn(sl, __fadd_rn(e, pe));
+  }
+  r[gi] = make_float2(sh, sl);
+}
+
+// ... and g = J^T r - lambda D^2 x per column, in the two phases of the column norms: per row
+// group the Dot2 sums over its rows for each diagonal t (pairs in shared memory), then per
+// column the compensated sum of its w diagonal pairs; g in double.
+__global__ void __launch_bounds__(kColNormCols) band_g_f32_kernel(const float* J, const float* x, const float2* r,
+                                                                  const double* D, double lam, int64_t total_cols,
+                                                                  const int64_t* inst_col0, int64_t num_inst, int rpc,
+                                                                  int w, double* g) {
+  __shared__ float2 S[(kColNormCols + kBW - 1) * (kBW + 1)];
+  const int stride = w + 1;
+  const int64_t j0 = (int64_t)blockIdx.x * kColNormCols;
+  for (int gg = threadIdx.x; gg < kColNormCols + w - 1; gg += kColNormCols) {
+    const int64_t grp = j0 - (w - 1) + gg;
+    float hs[kBW], hc[kBW];
+#pragma unroll
+    for (int t = 0; t < kBW; ++t) hs[t] = hc[t] = 0.f;
+    if (grp >= 0 && grp < total_cols) {
+      for (int q = 0; q < rpc; ++q) {
+        const int64_t row = grp * rpc + q;
+        const float2 rr = r[row];
+        const float* jr = J + row * w;
+#pragma unroll
+        for (int t = 0; t < kBW; ++t) {
+          if (t < w) {
+            const float a = jr[t];
+            const float pr = __fmul_rn(a, rr.x);
+            float pe = __fmaf_rn(a, rr.x, -pr);
+            pe = __fmaf_rn(a, rr.y, pe);
+            float tt, e;
+            dev::two_sum(hs[t], pr, tt, e);
+            hs[t] = tt;
+            hc[t] = __fadd_rn(hc[t], __fadd_rn(e, pe));
+          }
+        }
+      }
+    }
+#pragma unroll
+    for (int t = 0; t < kBW; ++t)
+      if (t < w) S[gg * stride + t] = make_float2(hs[t], hc[t]);
+  }
+  __syncthreads();
+  const int64_t gj = j0 + threadIdx.x;
+  if (gj >= total_cols) return;
+  int64_t lo = 0, hi = num_inst - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (inst_col0[mid] <= gj) lo = mid; else hi = mid - 1;
+  }
+  const int64_t j = gj - inst_col0[lo];
+  float s = 0.f, c = 0.f;
+  for (int t = 0; t < w && t <= j; ++t) {
+    const float2 v = S[(threadIdx.x + w - 1 - t) * stride + t];
+    float tt, e;
+    dev::two_sum(s, v.x, tt, e);
+    s = tt;
+    c = __fadd_rn(c, __fadd_rn(e, v.y));
+  }
+  double acc = (double)s + (double)c;
+  if (lam > 0.0) acc -= lam * D[gj] * D[gj] * (double)x[gj];
+  g[gj] = acc;
+}
+
 // Refinement pieces of the parallel path, one thread per row / per column:
 // r = b - J x in double, then g_j = sum_i J_ij r_i - lambda D_j^2 x_j.
 template <typename T>
@@ -573,12 +664,21 @@ static qrkit_status banded_run(qrkit_ctx* ctx, const void* J, const void* b, con
                                (double*)B.res2.ptr);
     if (rc != QRKIT_OK) return rc;
     for (int it = 0; it < refine_steps; ++it) {
-      band_resid_kernel<T><<<nblk(B.total_rows, 256), 256, 0, st>>>(
-          (const T*)J, (const T*)b, (const T*)p, dcols, dc0, dr0, B.num_inst, B.total_rows, B.rows_per_col, B.w,
-          (double*)B.r.ptr);
-      band_g_kernel<T><<<nblk(B.total_cols, 256), 256, 0, st>>>(
-          (const T*)J, (const T*)p, (const double*)B.r.ptr, D, lambda, dcols, dc0, dr0, B.num_inst, B.total_cols,
-          B.rows_per_col, B.w, (double*)B.g.ptr);
+      if (sizeof(T) == sizeof(float)) {
+        band_resid_f32_kernel<<<nblk(B.total_rows, 256), 256, 0, st>>>(
+            (const float*)J, (const float*)b, (const float*)p, dcols, dc0, dr0, B.num_inst, B.total_rows,
+            B.rows_per_col, B.w, (float2*)B.r.ptr);
+        band_g_f32_kernel<<<nblk(B.total_cols, kColNormCols), kColNormCols, 0, st>>>(
+            (const float*)J, (const float*)p, (const float2*)B.r.ptr, D, lambda, B.total_cols, dc0, B.num_inst,
+            B.rows_per_col, B.w, (double*)B.g.ptr);
+      } else {
+        band_resid_kernel<T><<<nblk(B.total_rows, 256), 256, 0, st>>>(
+            (const T*)J, (const T*)b, (const T*)p, dcols, dc0, dr0, B.num_inst, B.total_rows, B.rows_per_col, B.w,
+            (double*)B.r.ptr);
+        band_g_kernel<T><<<nblk(B.total_cols, 256), 256, 0, st>>>(
+            (const T*)J, (const T*)p, (const double*)B.r.ptr, D, lambda, dcols, dc0, dr0, B.num_inst, B.total_cols,
+            B.rows_per_col, B.w, (double*)B.g.ptr);
+      }
       ctx->launches += 2;
       QRKIT_CUDA_TRY(ctx, cudaGetLastError());
       if ((rc = cr_normal_solve(ctx, *B.cr, (const double*)B.g.ptr, B.h.ptr)) != QRKIT_OK) return rc;
