@@ -387,11 +387,11 @@ __global__ void block_backsub_kernel(ComposedView<T> V, FactorOut<T> O, const T*
 }
 
 // ---- refinement: g = J^T (b - J p) - lambda D^2 p in double ----
+constexpr int kCtaSumCols = 4096;   // dense S: shared columns summed per CTA in shared memory
+
 template <typename T>
-__global__ void resid_g_kernel(ComposedView<T> V, const T* b, const T* p, const double* D,
-                               double lam, double* g, double* gS) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= V.K) return;
+__device__ __forceinline__ void resid_g_block(ComposedView<T> V, const T* b, const T* p, const double* D,
+                                              double lam, double* g, double* gS, int64_t i) {
   const int n = V.n[i], m = V.m[i];
   const int64_t c0 = V.col_off[i], r0 = V.row_off[i];
   const T* J = V.J + V.val_off[i];
@@ -430,6 +430,26 @@ __global__ void resid_g_kernel(ComposedView<T> V, const T* b, const T* p, const 
   }
 }
 
+template <typename T>
+__global__ void resid_g_kernel(ComposedView<T> V, const T* b, const T* p, const double* D,
+                               double lam, double* g, double* gS) {
+  // dense S: every block adds to all s shared columns; the CTA's sums are gathered in shared
+  // memory and leave with one global atomic per column
+  extern __shared__ double sgS[];
+  const bool cta_sum = V.coupled == QRKIT_COUPLED_DENSE && V.s <= kCtaSumCols;
+  if (cta_sum) {
+    for (int c = threadIdx.x; c < V.s; c += blockDim.x) sgS[c] = 0.0;
+    __syncthreads();
+  }
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < V.K) resid_g_block(V, b, p, D, lam, g, cta_sum ? sgS : gS, i);
+  if (cta_sum) {
+    __syncthreads();
+    for (int c = threadIdx.x; c < V.s; c += blockDim.x)
+      if (sgS[c] != 0.0) atomicAdd(&gS[c], sgS[c]);
+  }
+}
+
 __global__ void gS_damping_kernel(double* gS, const float* pf, const double* pd, const double* D,
                                   int64_t nb, int s, double lam) {
   const int c = blockIdx.x * blockDim.x + threadIdx.x;
@@ -439,12 +459,10 @@ __global__ void gS_damping_kernel(double* gS, const float* pf, const double* pd,
   gS[c] -= lam * d * d * pv;
 }
 
-// h_i = R_i^{-T} g_i per block; then gS -= R12_i^T h_i.
+// h_i = R_i^{-T} g_i per block; then gS -= R12_i^T h_i (dense S: summed per CTA first).
 template <typename T>
-__global__ void block_fwdsub_rt_kernel(ComposedView<T> V, FactorOut<T> O, const double* g, T* h,
-                                       double* gS) {
-  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i >= V.K) return;
+__device__ __forceinline__ void fwdsub_rt_block(ComposedView<T> V, FactorOut<T> O, const double* g, T* h,
+                                                double* gS, int64_t i) {
   const int n = V.n[i], m = V.m[i];
   const int na = n + (O.damp ? m : 0);
   const int64_t c0 = V.col_off[i];
@@ -464,6 +482,24 @@ __global__ void block_fwdsub_rt_kernel(ComposedView<T> V, FactorOut<T> O, const 
       for (int k = 0; k < m; ++k) acc += (double)O.R12[(c0 + k) * (int64_t)V.w + t] * (double)hv[k];
       if (acc != 0.0) atomicAdd(&gS[st + t], -acc);
     }
+  }
+}
+
+template <typename T>
+__global__ void block_fwdsub_rt_kernel(ComposedView<T> V, FactorOut<T> O, const double* g, T* h,
+                                       double* gS) {
+  extern __shared__ double sgS[];
+  const bool cta_sum = V.coupled == QRKIT_COUPLED_DENSE && V.s <= kCtaSumCols;
+  if (cta_sum) {
+    for (int c = threadIdx.x; c < V.s; c += blockDim.x) sgS[c] = 0.0;
+    __syncthreads();
+  }
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i < V.K) fwdsub_rt_block(V, O, g, h, cta_sum ? sgS : gS, i);
+  if (cta_sum) {
+    __syncthreads();
+    for (int c = threadIdx.x; c < V.s; c += blockDim.x)
+      if (sgS[c] != 0.0) atomicAdd(&gS[c], sgS[c]);
   }
 }
 
@@ -687,12 +723,13 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
     T* h = (T*)C.h.ptr;
     double* gS = g + nb;
     if (s > 0) QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(gS, 0, (size_t)s * sizeof(double), st));
-    LAUNCH(ctx, resid_g_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, (const T*)b, x, O.D, C.lam, g, gS));
+    const size_t sum_smem = (V.coupled == QRKIT_COUPLED_DENSE && s <= kCtaSumCols) ? (size_t)s * sizeof(double) : 0;
+    LAUNCH(ctx, resid_g_kernel<T><<<blocks_for(P.K, 64), 64, sum_smem, st>>>(V, (const T*)b, x, O.D, C.lam, g, gS));
     if (s > 0)
       LAUNCH(ctx, gS_damping_kernel<<<blocks_for(s, 128), 128, 0, st>>>(
                       gS, sizeof(T) == 4 ? (const float*)x : nullptr,
                       sizeof(T) == 8 ? (const double*)x : nullptr, O.D, nb, s, C.lam));
-    LAUNCH(ctx, block_fwdsub_rt_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O, g, h, gS));
+    LAUNCH(ctx, block_fwdsub_rt_kernel<T><<<blocks_for(P.K, 64), 64, sum_smem, st>>>(V, O, g, h, gS));
     if (V.coupled == QRKIT_COUPLED_WINDOW && C.cr) {
       // dp_S = R_S^{-1} R_S^{-T} (g_S - R12^T h_B) with the parallel banded factor
       qrkit_status rc = cr_normal_solve(ctx, *C.cr, gS, h + nb);
