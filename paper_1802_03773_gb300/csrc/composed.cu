@@ -935,7 +935,9 @@ qrkit_status composed_layout(qrkit_ctx* ctx, size_t elem) {
             r0v(inst.begin() + 2 * nseg, inst.begin() + 3 * nseg), rv(inst.begin() + 3 * nseg, inst.end());
         if ((rc = cr_build(ctx, C.cr, ic, i0, r0v, rv)) != QRKIT_OK) return rc;
       }
-      if ((rc = ensure(ctx, C.hist, (size_t)std::max<int64_t>(hoff, 1) * sizeof(int), "row sort histograms")) != QRKIT_OK)
+      // histograms, then one bin total per shared column (the scan's second pass)
+      if ((rc = ensure(ctx, C.hist, (size_t)std::max<int64_t>(hoff + P.s.shared_cols, 1) * sizeof(int),
+                       "row sort histograms")) != QRKIT_OK)
         return rc;
       const int64_t* t = (const int64_t*)C.sort_tab.ptr;
       C.sort.num_chunks = nc;

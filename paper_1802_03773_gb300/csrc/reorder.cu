@@ -5,7 +5,10 @@
 //
 // Segmented stable counting sort, deterministic:
 //   count   one warp per chunk of rows: per-chunk histogram over the segment's columns
-//   scan    one CTA per segment: bin-major, chunk-minor exclusive offsets (in place)
+//   scan    bin-major, chunk-minor exclusive offsets (in place), in three parallel passes: one
+//           thread per (segment, bin) turns the bin's chunk counts into chunk-minor prefixes
+//           and records the bin total; one CTA per segment scans its bin totals; one thread
+//           per (segment, bin) adds the bin's base to its chunk entries
 //   scatter one warp per chunk, its rows in order: rank among equal keys from
 //           __match_any_sync, the chunk's running offsets advanced by the key's leader lane;
 //           writes the sorted rows (values, starts) and both directions of the permutation.
@@ -47,24 +50,42 @@ __global__ void rsort_count_kernel(RowSortTables t, const int64_t* Xstart, int* 
   }
 }
 
-__global__ void __launch_bounds__(kScanThreads)
-rsort_scan_kernel(RowSortTables t, int* hist) {
+constexpr int kBinThreads = 256;
+
+// Pass 1 of the scan: bin b of segment blockIdx.x; chunk-minor exclusive prefixes in place,
+// the bin's total to tot (indexed by global shared column).
+__global__ void __launch_bounds__(kBinThreads) rsort_bin_prefix_kernel(RowSortTables t, int* hist, int* tot) {
+  const int64_t seg = blockIdx.x;
+  const int64_t c0 = t.seg_chunk0[seg], c1 = t.seg_chunk0[seg + 1];
+  if (c0 == c1) return;
+  const int64_t b = (int64_t)blockIdx.y * kBinThreads + threadIdx.x;
+  if (b >= t.chunk_cols[c0]) return;
+  int running = 0;
+  for (int64_t c = c0; c < c1; ++c) {
+    int* e = hist + t.chunk_hoff[c] + b;
+    const int v = *e;
+    *e = running;
+    running += v;
+  }
+  tot[t.chunk_col0[c0] + b] = running;
+}
+
+// Pass 2: exclusive scan of a segment's bin totals (one CTA per segment), in place.
+__global__ void __launch_bounds__(kScanThreads) rsort_bin_scan_kernel(RowSortTables t, int* tot) {
   __shared__ int warp_tot[kScanThreads / 32];
   __shared__ int carry_s;
   const int64_t seg = blockIdx.x;
   const int64_t c0 = t.seg_chunk0[seg], c1 = t.seg_chunk0[seg + 1];
   if (c0 == c1) return;
   const int64_t cols = t.chunk_cols[c0];
+  int* tt = tot + t.chunk_col0[c0];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
   if (threadIdx.x == 0) carry_s = 0;
   __syncthreads();
   for (int64_t b0 = 0; b0 < cols; b0 += kScanThreads) {
     const int64_t b = b0 + threadIdx.x;
-    int tot = 0;
-    if (b < cols)
-      for (int64_t c = c0; c < c1; ++c) tot += hist[t.chunk_hoff[c] + b];
-    // block exclusive scan of tot
-    int incl = tot;
+    const int v0 = b < cols ? tt[b] : 0;
+    int incl = v0;
 #pragma unroll
     for (int d = 1; d < 32; d <<= 1) {
       const int v = __shfl_up_sync(0xffffffffu, incl, d);
@@ -83,18 +104,22 @@ rsort_scan_kernel(RowSortTables t, int* hist) {
     }
     __syncthreads();
     const int carry = carry_s;
-    int base = carry + (wid ? warp_tot[wid - 1] : 0) + incl - tot;
-    if (b < cols)
-      for (int64_t c = c0; c < c1; ++c) {
-        int* e = hist + t.chunk_hoff[c] + b;
-        const int v = *e;
-        *e = base;
-        base += v;
-      }
+    if (b < cols) tt[b] = carry + (wid ? warp_tot[wid - 1] : 0) + incl - v0;
     __syncthreads();
     if (threadIdx.x == 0) carry_s = carry + warp_tot[kScanThreads / 32 - 1];
     __syncthreads();
   }
+}
+
+// Pass 3: the bin's base added to its chunk entries.
+__global__ void __launch_bounds__(kBinThreads) rsort_bin_add_kernel(RowSortTables t, int* hist, const int* tot) {
+  const int64_t seg = blockIdx.x;
+  const int64_t c0 = t.seg_chunk0[seg], c1 = t.seg_chunk0[seg + 1];
+  if (c0 == c1) return;
+  const int64_t b = (int64_t)blockIdx.y * kBinThreads + threadIdx.x;
+  if (b >= t.chunk_cols[c0]) return;
+  const int base = tot[t.chunk_col0[c0] + b];
+  for (int64_t c = c0; c < c1; ++c) hist[t.chunk_hoff[c] + b] += base;
 }
 
 template <typename T>
@@ -185,9 +210,18 @@ qrkit_status reduced_row_sort(qrkit_ctx* ctx, const RowSortTables& t, int64_t ns
   rsort_count_kernel<<<nblk(t.num_chunks * 32, 128), 128, 0, st>>>(t, Xstart, hist, ctx->d_status);
   ctx->launches += 1;
   QRKIT_CUDA_TRY(ctx, cudaGetLastError());
-  rsort_scan_kernel<<<(unsigned)nseg, kScanThreads, 0, st>>>(t, hist);
-  ctx->launches += 1;
-  QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+  {
+    // the three passes of the scan; bin totals after the histograms (indexed by shared column)
+    int64_t maxcols = 1;
+    for (const int64_t c : ctx->plan.seg_cols) maxcols = c > maxcols ? c : maxcols;
+    int* tot = hist + hist_entries;
+    const dim3 grid((unsigned)nseg, (unsigned)((maxcols + kBinThreads - 1) / kBinThreads));
+    rsort_bin_prefix_kernel<<<grid, kBinThreads, 0, st>>>(t, hist, tot);
+    rsort_bin_scan_kernel<<<(unsigned)nseg, kScanThreads, 0, st>>>(t, tot);
+    rsort_bin_add_kernel<<<grid, kBinThreads, 0, st>>>(t, hist, tot);
+    ctx->launches += 3;
+    QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+  }
   if (ctx->precision == QRKIT_FP64)
     rsort_scatter_kernel<double><<<nblk(t.num_chunks * 32, 128), 128, 0, st>>>(
         t, Xstart, (const double*)Xw, w, hist, spos, order, Xstart_s, (double*)Xw_s);
