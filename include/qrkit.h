@@ -123,8 +123,10 @@ const char* qrkit_last_error(const qrkit_ctx* ctx);
 const char* qrkit_status_string(int status);
 
 /* Structure plan (Sec. 3 composition, Sec. 4.3 / 4.5 row permutation): validates the
- * descriptor, builds offsets, the P_r interleave of the damping rows, the tile schedule of
- * the persistent kernels, and allocates the device workspace that holds the factor.
+ * descriptor, builds offsets, the P_r interleave of the damping rows, the work lists of the
+ * persistent kernels (for uncoupled blocks: shape-uniform warp tasks, blocks sorted by shape
+ * inside supertiles of consecutive blocks), and allocates the device workspace that holds
+ * the factor.
  * Host work, once per structure; synchronous.  Replaces any previous plan. */
 qrkit_status qrkit_plan(qrkit_ctx* ctx, const qrkit_structure* s);
 
@@ -145,7 +147,8 @@ qrkit_status qrkit_plan(qrkit_ctx* ctx, const qrkit_structure* s);
  *   p    : out, sum m_i values
  *   qtb  : out or NULL; sum n_i values: Q_i^T b_i per block
  * The factor (reflectors below the diagonal, R on and above it, tau) stays in the context.
- * One kernel launch (two in FP32 refined mode); asynchronous on the context's stream. */
+ * One kernel launch (two in FP32 refined mode; banded plans: the banded factor + solve and
+ * its refinement); asynchronous on the context's stream. */
 qrkit_status qrkit_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
                                 double lambda, void* p, void* qtb, int refine_steps);
 
