@@ -96,6 +96,7 @@ qrkit_status launch_tasks_typed(qrkit_ctx* ctx, const void* J, const void* b, vo
     R.b = (const float*)b;
     R.J_end = R.J + P.values;
     R.b_end = R.b + P.rows;
+    R.F = (const float*)A.F;
     R.x = (float*)p;
     R.rlist = A.rlist;
     R.rcount = A.rcount;

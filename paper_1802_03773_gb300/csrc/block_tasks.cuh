@@ -21,8 +21,8 @@
 // stores);
 // with refinement it also estimates each block's float error a priori and lists the blocks
 // that need refinement, one list per shape key.  The second kernel takes those lists in
-// tasks of the same form, factors the listed blocks again (bit-identical to the first pass)
-// and refines their solutions with a compensated float residual.
+// tasks of the same form, reads R (from the stored factor) and the float solution of the
+// listed blocks, and refines them with a compensated float residual.
 #pragma once
 
 #include <cuda_runtime.h>
@@ -725,13 +725,15 @@ __global__ void __launch_bounds__(32 * kTaskMaxWarps, sizeof(T) == 4 ? QRKIT_TAS
 // ---------------------------------------------------------------------------------------
 // Refinement of the listed blocks (float), pipelined like the factor kernel in two stages:
 // while task i is refined, the block data of task i + 1 and the list entries of task i + 2
-// are in flight.
+// are in flight.  R and the float solution come from the first kernel's output (the factor in
+// J's packing and p), so the blocks are not factored again.
 struct RefineTaskArgs {
   const float* J;
   const float* b;
   const float* J_end;
   const float* b_end;
-  float* x;
+  const float* F;   // factor of the first kernel (J's packing: R on and above the diagonal)
+  float* x;         // in: the first kernel's solution; out: refined
   const RefEntry* rlist;
   const int* rcount;
   const int64_t* key_off;
@@ -805,10 +807,18 @@ __device__ __forceinline__ void refine_task(const RefineTaskArgs& A, const unsig
   unsigned char *sJraw, *sBraw;
   float *sJ, *sB;
   slot_ptrs<float>(db, G, M, act ? grp : 0, A.J + e.v, A.b + e.r, sJraw, sBraw, sJ, sB);
-  float a[kMaxCols][4], c[4], x[kMaxCols];
-  load_regs<float, G>(a, c, sJ, sB, n, M, g.q);
-  group_householder<float, G>(a, c, nullptr, M, g);
-  group_backsub<float, G>(a, c, M, g, x);
+  // R (rows < M of the factor the first kernel stored, J's packing) and the float solution
+  // it stored; the lanes of a group hold the same x
+  float a[kMaxCols][4], x[kMaxCols];
+#pragma unroll
+  for (int j = 0; j < kmax<G>(); ++j) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = 4 * g.q + u;
+      a[j][u] = (j < M && r <= j && n > 0) ? A.F[e.v + (int64_t)j * n + r] : 0.f;
+    }
+    x[j] = (j < M && n > 0) ? A.x[e.c + j] : 0.f;
+  }
   group_refine<G>(a, x, sJ, sB, n, M, g, A.steps, A.tol);
   if (n > 0) {
     float* dx = A.x + e.c;
