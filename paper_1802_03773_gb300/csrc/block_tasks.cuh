@@ -1,5 +1,6 @@
-// Device side of the batched block-diagonal QR solve by shape-uniform warp tasks (Sec. 4.1 "Block diagonal",
-// Householder QR of Sec. 2, the compute / Q^T b / R solve interface of Sec. 5.1).
+// Device side of the batched block-diagonal QR solve by shape-uniform warp tasks
+// (Sec. 4.1 "Block diagonal", Householder QR of Sec. 2, the compute / Q^T b / R solve
+// interface of Sec. 5.1).
 //
 // Plan (host): the blocks are taken in supertiles of consecutive blocks; inside a supertile
 // they are counting-sorted by shape key (row class c = (n - 1) / 4, column count m) and cut
@@ -9,20 +10,21 @@
 // CTA-wide barrier anywhere.  Supertiles keep the blocks that concurrent warps touch (and the
 // neighbours sharing their 32-byte sectors) close in time, so partial sectors meet in L2.
 //
-// Kernels (device): persistent warps, each with its own shared-memory slots, take tasks in a
-// grid stride.  Per task the G lanes of each block's group copy the 16-byte-aligned supersets
-// of the block's J and b into its slots with per-lane 16-byte cp.async copies (the blocks of
-// a task are scattered, 20-500 bytes each: per-thread copies, not TMA, whose operands must
-// be warp-uniform and would serialise one block after another); the group factors
-// the block with Householder reflectors H = I - tau v v^T (v[0] = 1, beta = -sign(x0)||x||;
-// norms and dot products are shuffle reductions over the group), applies them to b (Q^T b)
-// and back-substitutes.  The first kernel writes the factor and Q^T b back to the slots and
-// sends them to HBM with 16-byte vector stores (unaligned head and tail elements by plain
-// stores);
+// Kernels (device): persistent warps, each with its own shared memory, take tasks in a grid
+// stride and run a software pipeline: while task i is computed, the copies of task i + 1's
+// block data, task i + 2's entries and task i + 3's header are in flight.  The block data are
+// the 16-byte-aligned supersets of each block's J and b, copied into the block's slots by the
+// G lanes of its group with per-lane 16-byte cp.async copies (the blocks of a task are
+// scattered, 20-500 bytes each: per-thread copies, not TMA, whose operands must be
+// warp-uniform and would serialise one block after another).  The group factors the block with
+// Householder reflectors H = I - tau v v^T (v[0] = 1, beta = -sign(x0)||x||; norms and dot
+// products are shuffle reductions over the group), applies them to b (Q^T b) and
+// back-substitutes.  The first kernel writes the factor and Q^T b back to the slots and sends
+// them to HBM with 16-byte vector stores (unaligned head and tail elements by plain stores);
 // with refinement it also estimates each block's float error a priori and lists the blocks
-// that need refinement, one list per shape key.  The second kernel takes those lists in
-// tasks of the same form, reads R (from the stored factor) and the float solution of the
-// listed blocks, and refines them with a compensated float residual.
+// that need refinement, one list per shape key.  The second kernel takes those lists in tasks
+// of the same form, reads R (from the stored factor) and the float solution of the listed
+// blocks, and refines them with a compensated float residual.
 #pragma once
 
 #include <cuda_runtime.h>

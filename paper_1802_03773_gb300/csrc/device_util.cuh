@@ -25,8 +25,8 @@ __device__ __forceinline__ void two_sum(float a, float b, float& s, float& e) {
   e = __fadd_rn(__fsub_rn(a, __fsub_rn(s, bb)), __fsub_rn(b, bb));
 }
 
-// sqrt and reciprocal: the hardware approximations for float (rsqrtf, __frcp_rn: a few ulp
-// at most, far below the rounding the factorization itself accumulates), IEEE for double.
+// sqrt and reciprocal for float: x * rsqrtf(x) (a few ulp at most, far below the rounding
+// the factorization itself accumulates) and the correctly rounded __frcp_rn; IEEE for double.
 __device__ __forceinline__ float fsqrt(float x) { return x > 0.f ? x * rsqrtf(x) : 0.f; }
 __device__ __forceinline__ double fsqrt(double x) { return sqrt(x); }
 __device__ __forceinline__ float frcp(float x) { return __frcp_rn(x); }
