@@ -259,7 +259,8 @@ qrkit_status qrkit_get_row_order(qrkit_ctx* ctx, int64_t* order);
 /* Autotuning (no paper counterpart): times candidate launch configurations for the current
  * plan on the given inputs (DEVICE buffers as for qrkit_factor_solve; p is overwritten) and
  * keeps the fastest.  Block plans without coupling: the block-to-warp mapping of the fused
- * solve, "tasks <supertile> <warps per CTA>" (shape-uniform warp tasks, the default) or
+ * solve, "tasks <supertile> <warps per CTA> [<key-major 0/1>]" (shape-uniform warp tasks, the
+ * default; see qrkit_task_layout) or
  * "budget <blocks> <values> <rows> <cols> <padded>" (tiles of consecutive blocks); parallel
  * banded plans: the compression strategy "compress <thread rows 0/1> <splits>" (one thread per
  * column block, or warps with 1-8 splits).  cache_path (HOST string, may be NULL): a text file with one line per
@@ -273,6 +274,28 @@ qrkit_status qrkit_autotune(qrkit_ctx* ctx, const void* J, const void* b, void* 
  * plan without timing, e.g. one chosen earlier on the same GPU.  QRKIT_EINVAL if the text does
  * not parse or does not fit the plan's kind; synchronous. */
 qrkit_status qrkit_apply_tuning(qrkit_ctx* ctx, const char* choice);
+
+/* The warp tasks a block plan (QRKIT_STRUCT_BLOCKS, QRKIT_COUPLED_NONE) hands to the fused
+ * solve of Sec. 4.1, computed on the host with no CUDA call and no context, for inspection
+ * and tests.  The blocks are taken in supertiles of `supertile` consecutive blocks (32..65536;
+ * qrkit_plan uses 65536); inside a supertile they are sorted, stably, by shape key
+ * 8 * ((n_i - 1) / 4) + (m_i - 1), and each key's run is cut into tasks of P blocks, where
+ * P = 32 / G and G = (n_i - 1) / 4 + 1 lanes of a warp hold one block (P = 32, 16, 10, 8); only
+ * the last task of a run has unused slots.  Tasks are in supertile order, keys ascending
+ * inside a supertile; key_major != 0 reorders them stably by key.
+ *   block_rows, block_cols : HOST, num_blocks shapes as in qrkit_structure (1..16, 1..8)
+ *   num_tasks              : HOST out: the number of tasks
+ *   task_key               : HOST out or NULL: the key of each task
+ *   task_slots             : HOST out or NULL: int64[num_tasks][32][4]: per task and slot the
+ *                            block index and its first value, row and column (offsets into
+ *                            J's packing, b and p); -1 in all four for an unused slot
+ *   capacity               : tasks the out arrays hold
+ * With task_key and task_slots both NULL only num_tasks is set.  QRKIT_EINVAL for a bad
+ * argument or a capacity below num_tasks (num_tasks is still set), QRKIT_EUNSUPPORTED for a
+ * shape outside 16 x 8. */
+qrkit_status qrkit_task_layout(int64_t num_blocks, const uint8_t* block_rows, const uint8_t* block_cols,
+                               int64_t supertile, int key_major, int64_t* num_tasks, int32_t* task_key,
+                               int64_t* task_slots, int64_t capacity);
 
 /* ---- Levenberg-Marquardt on the device (Sec. 2; Backtrack LM of Sec. 5.2) ----
  * Model QRKIT_MODEL_CURVEFIT: 2-D points fitted by an open uniform cubic B-spline; each

@@ -132,21 +132,35 @@ void release_block_tasks(Plan& P) {
   P.key_off.clear();
 }
 
-qrkit_status build_block_tasks(qrkit_ctx* ctx, int64_t supertile, int warps, bool key_major) {
-  Plan& P = ctx->plan;
-  if (supertile < 32 || supertile > 65536) return fail(ctx, QRKIT_EINVAL, "supertile must be in [32, 65536]");
-  if (warps < 1 || warps > kTaskMaxWarps) return fail(ctx, QRKIT_EINVAL, "warps per CTA must be in [1, 8]");
-  if (P.K > (int64_t)INT32_MAX) return fail(ctx, QRKIT_EUNSUPPORTED, "more than 2^31 - 1 blocks");
-  std::vector<TaskHdr> hdr;
-  std::vector<TaskEntry> ent;
-  hdr.reserve((size_t)(P.K / 8 + kTaskKeys));
-  ent.reserve((size_t)(P.K + P.K / 16 + 32 * kTaskKeys));
-  std::vector<int64_t> key_count(kTaskKeys, 0);
+namespace tasks {
+
+// The task lists of K blocks with the given shapes and offsets (K + 1 prefix sums each), no
+// CUDA call: per supertile of consecutive blocks a stable counting sort by shape key, each
+// key's run cut into tasks of task_blocks(G) entries (unused entries have n = 0); with
+// key_major the tasks are stably reordered by key.  key_count[k] = blocks of key k.  Returns
+// QRKIT_OK, or an error status with its message in err.
+qrkit_status make_task_lists(int64_t K, const uint8_t* n, const uint8_t* m, const int64_t* val_off,
+                             const int64_t* row_off, const int64_t* col_off, int64_t supertile,
+                             bool key_major, std::vector<TaskHdr>& hdr, std::vector<TaskEntry>& ent,
+                             std::vector<int64_t>& key_count, std::string& err) {
+  if (supertile < 32 || supertile > 65536) {
+    err = "supertile must be in [32, 65536]";
+    return QRKIT_EINVAL;
+  }
+  if (K > (int64_t)INT32_MAX) {
+    err = "more than 2^31 - 1 blocks";
+    return QRKIT_EUNSUPPORTED;
+  }
+  hdr.clear();
+  ent.clear();
+  hdr.reserve((size_t)(K / 8 + kTaskKeys));
+  ent.reserve((size_t)(K + K / 16 + 32 * kTaskKeys));
+  key_count.assign(kTaskKeys, 0);
   std::vector<int64_t> cnt(kTaskKeys), pos(kTaskKeys);
   std::vector<int32_t> order;
-  auto key_of = [&](int64_t i) { return ((P.n[i] - 1) >> 2) * 8 + (P.m[i] - 1); };
-  for (int64_t s0 = 0; s0 < P.K; s0 += supertile) {
-    const int64_t s1 = std::min(P.K, s0 + supertile);
+  auto key_of = [&](int64_t i) { return ((n[i] - 1) >> 2) * 8 + (m[i] - 1); };
+  for (int64_t s0 = 0; s0 < K; s0 += supertile) {
+    const int64_t s1 = std::min(K, s0 + supertile);
     std::fill(cnt.begin(), cnt.end(), 0);
     for (int64_t i = s0; i < s1; ++i) cnt[key_of(i)] += 1;
     int64_t acc = 0;
@@ -161,9 +175,9 @@ qrkit_status build_block_tasks(qrkit_ctx* ctx, int64_t supertile, int warps, boo
       const int per = task_blocks(group_lanes(k));
       for (int64_t c0 = 0; c0 < cnt[k]; c0 += per) {
         TaskHdr h{};
-        h.v0 = P.val_off[s0];
-        h.r0 = P.row_off[s0];
-        h.c0 = P.col_off[s0];
+        h.v0 = val_off[s0];
+        h.r0 = row_off[s0];
+        h.c0 = col_off[s0];
         h.b0 = s0;
         h.first = (int64_t)ent.size();
         h.key = k;
@@ -172,12 +186,12 @@ qrkit_status build_block_tasks(qrkit_ctx* ctx, int64_t supertile, int warps, boo
           TaskEntry e{};
           if (c0 + l < cnt[k]) {
             const int64_t i = s0 + order[(size_t)(at + c0 + l)];
-            e.v = (uint32_t)(P.val_off[i] - h.v0);
-            e.r = (uint32_t)(P.row_off[i] - h.r0);
-            e.c = (uint32_t)(P.col_off[i] - h.c0);
+            e.v = (uint32_t)(val_off[i] - h.v0);
+            e.r = (uint32_t)(row_off[i] - h.r0);
+            e.c = (uint32_t)(col_off[i] - h.c0);
             e.blk = (uint16_t)(i - s0);
-            e.n = P.n[i];
-            e.m = P.m[i];
+            e.n = n[i];
+            e.m = m[i];
           }
           ent.push_back(e);
         }
@@ -188,6 +202,21 @@ qrkit_status build_block_tasks(qrkit_ctx* ctx, int64_t supertile, int warps, boo
   }
   if (key_major)   // all tasks of a shape key together (supertiles in order within a key)
     std::stable_sort(hdr.begin(), hdr.end(), [](const TaskHdr& x, const TaskHdr& y) { return x.key < y.key; });
+  return QRKIT_OK;
+}
+
+}  // namespace tasks
+
+qrkit_status build_block_tasks(qrkit_ctx* ctx, int64_t supertile, int warps, bool key_major) {
+  Plan& P = ctx->plan;
+  if (warps < 1 || warps > kTaskMaxWarps) return fail(ctx, QRKIT_EINVAL, "warps per CTA must be in [1, 8]");
+  std::vector<TaskHdr> hdr;
+  std::vector<TaskEntry> ent;
+  std::vector<int64_t> key_count;
+  std::string err;
+  qrkit_status st = make_task_lists(P.K, P.n.data(), P.m.data(), P.val_off.data(), P.row_off.data(),
+                                    P.col_off.data(), supertile, key_major, hdr, ent, key_count, err);
+  if (st != QRKIT_OK) return fail(ctx, st, err);
   P.key_off.assign(kTaskKeys + 1, 0);
   P.max_refine_tasks = 0;
   for (int k = 0; k < kTaskKeys; ++k) {
@@ -195,7 +224,6 @@ qrkit_status build_block_tasks(qrkit_ctx* ctx, int64_t supertile, int warps, boo
     const int per = task_blocks(group_lanes(k));
     P.max_refine_tasks += (key_count[k] + per - 1) / per;
   }
-  qrkit_status st;
   auto up = [&](DevBuf& d, const void* src, size_t bytes, const char* what) -> qrkit_status {
     qrkit_status r = ensure(ctx, d, bytes, what);
     if (r != QRKIT_OK) return r;
@@ -223,3 +251,51 @@ qrkit_status launch_block_tasks(qrkit_ctx* ctx, const void* J, const void* b, vo
 }
 
 }  // namespace qrkit
+
+extern "C" qrkit_status qrkit_task_layout(int64_t num_blocks, const uint8_t* block_rows,
+                                          const uint8_t* block_cols, int64_t supertile, int key_major,
+                                          int64_t* num_tasks, int32_t* task_key, int64_t* task_slots,
+                                          int64_t capacity) {
+  using namespace qrkit;
+  using namespace qrkit::tasks;
+  if (num_blocks < 1 || !block_rows || !block_cols || !num_tasks || capacity < 0) return QRKIT_EINVAL;
+  std::vector<int64_t> val_off((size_t)num_blocks + 1, 0), row_off((size_t)num_blocks + 1, 0),
+      col_off((size_t)num_blocks + 1, 0);
+  for (int64_t i = 0; i < num_blocks; ++i) {
+    const int n = block_rows[i], m = block_cols[i];
+    if (n < 1 || m < 1) return QRKIT_EINVAL;
+    if (n > 16 || m > kMaxCols) return QRKIT_EUNSUPPORTED;
+    val_off[i + 1] = val_off[i] + (int64_t)n * m;
+    row_off[i + 1] = row_off[i] + n;
+    col_off[i + 1] = col_off[i] + m;
+  }
+  std::vector<TaskHdr> hdr;
+  std::vector<TaskEntry> ent;
+  std::vector<int64_t> key_count;
+  std::string err;
+  const qrkit_status st = make_task_lists(num_blocks, block_rows, block_cols, val_off.data(), row_off.data(),
+                                          col_off.data(), supertile, key_major != 0, hdr, ent, key_count, err);
+  if (st != QRKIT_OK) return st;
+  *num_tasks = (int64_t)hdr.size();
+  if (!task_key && !task_slots) return QRKIT_OK;
+  if (capacity < (int64_t)hdr.size()) return QRKIT_EINVAL;
+  for (size_t t = 0; t < hdr.size(); ++t) {
+    const TaskHdr& h = hdr[t];
+    if (task_key) task_key[t] = h.key;
+    if (!task_slots) continue;
+    const int per = task_blocks(group_lanes(h.key));
+    for (int l = 0; l < 32; ++l) {
+      int64_t* o = task_slots + ((int64_t)t * 32 + l) * 4;
+      const TaskEntry* e = l < per ? &ent[(size_t)(h.first + l)] : nullptr;
+      if (e && e->n > 0) {
+        o[0] = h.b0 + e->blk;
+        o[1] = h.v0 + e->v;
+        o[2] = h.r0 + e->r;
+        o[3] = h.c0 + e->c;
+      } else {
+        o[0] = o[1] = o[2] = o[3] = -1;
+      }
+    }
+  }
+  return QRKIT_OK;
+}

@@ -116,6 +116,8 @@ _SIGS = {
     "qrkit_block_solve_noalloc": (ctypes.c_int, [ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int64, _VP,
                                                  _VP, _VP, _VP, _VP, ctypes.c_int]),
     "qrkit_launch_count": (ctypes.c_int64, [_VP]),
+    "qrkit_task_layout": (ctypes.c_int, [ctypes.c_int64, _VP, _VP, ctypes.c_int64, ctypes.c_int, _VP, _VP, _VP,
+                                         ctypes.c_int64]),
 }
 
 _lib = None
@@ -157,6 +159,31 @@ def block_solve_noalloc(n, m, J, b, p, precision="fp32_refined", refine_steps=2,
                                        int(refine_steps))
     if st != 0:
         raise QRKitError(st, "qrkit_block_solve_noalloc failed")
+
+
+def task_layout(n, m, supertile=65536, key_major=False):
+    """qrkit_task_layout: the warp tasks a block plan builds, computed on the host.
+
+    n, m: host arrays of block shapes.  Returns (key (T,) int32, slots (T, 32, 4) int64): per
+    task its shape key and, per slot, (block, first value, first row, first column), -1 where
+    the slot is unused.  Raises QRKitError on a non-zero status.
+    """
+    lib = load()
+    n = np.ascontiguousarray(n, dtype=np.uint8)
+    m = np.ascontiguousarray(m, dtype=np.uint8)
+    count = ctypes.c_int64(0)
+    st = lib.qrkit_task_layout(n.shape[0], n.ctypes.data, m.ctypes.data, int(supertile), int(bool(key_major)),
+                               ctypes.addressof(count), None, None, 0)
+    if st != 0:
+        raise QRKitError(st, "qrkit_task_layout failed")
+    T = count.value
+    key = np.empty(T, dtype=np.int32)
+    slots = np.empty((T, 32, 4), dtype=np.int64)
+    st = lib.qrkit_task_layout(n.shape[0], n.ctypes.data, m.ctypes.data, int(supertile), int(bool(key_major)),
+                               ctypes.addressof(count), key.ctypes.data, slots.ctypes.data, T)
+    if st != 0:
+        raise QRKitError(st, "qrkit_task_layout failed")
+    return key, slots
 
 
 def declared_symbols():
