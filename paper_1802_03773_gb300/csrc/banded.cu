@@ -505,8 +505,9 @@ __global__ void __launch_bounds__(kColNormCols) band_g_f32_kernel(const float* J
   g[gj] = acc;
 }
 
-// Refinement pieces of the parallel path, one thread per row / per column:
-// r = b - J x in double, then g_j = sum_i J_ij r_i - lambda D_j^2 x_j.
+// Refinement pieces of the parallel path for double J (float J takes the Dot2 kernels
+// above), one thread per row / per column: r = b - J x in double, then
+// g_j = sum_i J_ij r_i - lambda D_j^2 x_j.
 template <typename T>
 __global__ void band_resid_kernel(const T* J, const T* b, const T* x, const int64_t* inst_cols,
                                   const int64_t* inst_col0, const int64_t* inst_row0, int64_t num_inst,
