@@ -334,6 +334,38 @@ def other_workloads(dev, stream, only=None):
             "reduced_block_tflops_useful": flops / (tf * 1e-3) / 1e12}
         ctx.close()
         del J, S, b
+    if want("ellipse_fit"):
+        # the surface fitting benchmark's shape: one LM-step system of an ellipse fit to N points
+        # (N blocks 2x1 + 5 dense shared columns), N over the paper's sweep, FP64
+        from workloads import ellipse_system
+        per_n = {}
+        for N in (500, 2000, 10_000, 100_000, 500_000):
+            d = ellipse_system(N=N)
+            ctx = Context(dev.index, stream=stream, precision="fp64")
+            ctx.plan_blocks(np.full(N, 2), np.full(N, 1), qrkit.COUPLED_DENSE, shared_cols=5)
+            J = torch.from_numpy(np.ascontiguousarray(d["blocks"].reshape(-1))).to(dev)
+            S = torch.from_numpy(np.asarray(d["S"]).T.reshape(-1).copy()).to(dev)
+            b = torch.from_numpy(np.asarray(d["b"])).to(dev)
+            pe = torch.empty(N + 5, dtype=torch.float64, device=dev)
+            torch.cuda.synchronize()
+
+            def ellipse_solve():
+                ctx.factor(J, S, None, d["lam"])
+                ctx.solve(b, pe, refine_steps=0)
+            ms = _time(stream, ellipse_solve, 20)
+            graph = torch.cuda.CUDAGraph()
+            with torch.cuda.graph(graph, stream=stream):
+                ellipse_solve()
+            ms_graph = _time(stream, graph.replay, 50)
+            ctx.sync_status()
+            per_n[str(N)] = {"us_per_solve_eager": 1000.0 * ms, "us_per_solve_graph": 1000.0 * ms_graph}
+            ctx.close()
+            del graph, J, S, b, pe
+        out["ellipse_fit_system_fp64"] = {
+            "workload": "one LM-step system of an ellipse fit: blkdiag(N blocks 2x1) | S 2N x 5, lambda 1e-3, "
+                        "D = norms, factor + solve, FP64; N = 500 .. 500,000",
+            "value": 1e6 / per_n["500000"]["us_per_solve_graph"], "unit": "solves/s at N = 500,000",
+            "per_n": per_n}
     if want("curvefit"):
         # curve fit, 200,000 points, 2048 control points: LM iterations and fixed-lambda solves
         cf = {}

@@ -12,6 +12,7 @@ from .gen import (  # noqa: F401
     block_angular_dense,
     batched_blocks,
     curvefit_problem,
+    ellipse_system,
     banded_problem,
     banded_batch_shapes,
     mlp_init,

@@ -92,6 +92,56 @@ def curvefit_problem(npoints=200_000, Kc=2048, sigma=0.01, start_sigma_t=0.05,
                 npoints=npoints)
 
 
+def ellipse_system(N=500_000, sigma=0.01, start_sigma_t=0.05, start_sigma_p=0.02, lam=1e-3,
+                   seed_offset=0, dtype=np.float64, workload=6):
+    """The linear system of one LM step of fitting an ellipse to N 2-D points (the surface
+    fitting benchmark of Sec. 6: one latent angle per point, five shared ellipse parameters,
+    J a horizontal concatenation of a block diagonal and a dense part, Sec. 4.2).
+
+    Ellipse E(t) = c + Rot(phi) (a cos t, b sin t) with c ~ N(0, 0.5^2 I), a ~ U[1.5, 2.5),
+    b = a U[0.3, 0.8), phi ~ U[0, pi); points y_i = E(t_i) + N(0, sigma^2 I), t_i ~ U[0, 2 pi).
+    The system is taken at a perturbed start (t_i + N(0, start_sigma_t^2), every parameter
+    + N(0, start_sigma_p^2)): residual r_i = E(t_i) - y_i (2 rows per point), block i = dr_i/dt_i
+    (2 x 1), S rows 2i, 2i + 1 = dr_i/d(c_x, c_y, a, b, phi) (2 x 5), right-hand side -r.  The
+    ellipse model is evaluated here, once, to lay out the input; neither side of the solve
+    evaluates it.  Returns dict(blocks (N, 2, 1), S (2N, 5), b (2N), lam, K, n, m, s, and the
+    start t0 (N), x0 (5) and points y (N, 2) the system was taken at).
+    """
+    g = rng_for(workload, seed_offset)
+    c = 0.5 * g.standard_normal(2)
+    a = 1.5 + g.random()
+    bb = a * (0.3 + 0.5 * g.random())
+    phi = np.pi * g.random()
+    t = 2.0 * np.pi * g.random(N)
+    noise = sigma * g.standard_normal((N, 2))
+    t0 = t + start_sigma_t * g.standard_normal(N)
+    x0 = np.array([c[0], c[1], a, bb, phi]) + start_sigma_p * g.standard_normal(5)
+
+    def curve(tt, x):
+        cs, sn = np.cos(x[4]), np.sin(x[4])
+        u, v = x[2] * np.cos(tt), x[3] * np.sin(tt)
+        return np.stack([x[0] + cs * u - sn * v, x[1] + sn * u + cs * v], axis=1)
+
+    y = curve(t, np.array([c[0], c[1], a, bb, phi])) + noise
+    r = curve(t0, x0) - y
+    cs, sn = np.cos(x0[4]), np.sin(x0[4])
+    ct, st = np.cos(t0), np.sin(t0)
+    u, v = x0[2] * ct, x0[3] * st
+    du, dv = -x0[2] * st, x0[3] * ct
+    blocks = np.stack([cs * du - sn * dv, sn * du + cs * dv], axis=1).reshape(N, 2, 1)
+    S = np.zeros((N, 2, 5))
+    S[:, 0, 0] = 1.0
+    S[:, 1, 1] = 1.0
+    S[:, 0, 2], S[:, 1, 2] = cs * ct, sn * ct
+    S[:, 0, 3], S[:, 1, 3] = -sn * st, cs * st
+    S[:, 0, 4], S[:, 1, 4] = -sn * u - cs * v, cs * u - sn * v
+    S = S.reshape(2 * N, 5)
+    b = -r.reshape(2 * N)
+    if dtype == np.float32:
+        blocks, S, b = _f32(blocks), _f32(S), _f32(b)
+    return dict(blocks=blocks, S=S, b=b, lam=lam, K=N, n=2, m=1, s=5, t0=t0, x0=x0, y=y)
+
+
 def banded_problem(n=1_000_000, rows_per_col=4, w=8, seed_offset=0, dtype=np.float32,
                    workload=4):
     """Banded J: row i starts at column floor(i / rows_per_col), w values, N(0,1).
