@@ -44,20 +44,44 @@ __global__ void colnorm_blocks_kernel(ComposedView<T> V, double* sq) {
   }
 }
 
+// Dense S (column-major, ld = rows of J): squared column norms in two deterministic passes.
+// Pass 1, one CTA per (chunk of kNormRows rows, shared column): strided per-thread sums, then
+// the warps' sums in warp order; pass 2, one thread per column adds its chunks in order.
+constexpr int kNormRows = 8192;
+constexpr int kNormThreads = 256;
+
 template <typename T>
-__global__ void colnorm_dense_kernel(ComposedView<T> V, double* sq) {
-  // one warp per shared column of the dense S (column-major, ld = rows of J)
-  const int warp = (blockIdx.x * blockDim.x + threadIdx.x) >> 5;
-  const int lane = threadIdx.x & 31;
-  if (warp >= V.s) return;
-  const T* col = V.S + (int64_t)warp * V.rows;
-  double s = 0;
-  for (int64_t r = lane; r < V.rows; r += 32) {
-    const double x = (double)col[r];
-    s += x * x;
+__global__ void __launch_bounds__(kNormThreads) colnorm_dense_part_kernel(ComposedView<T> V, double* part,
+                                                                          int64_t nchunk) {
+  __shared__ double ws[kNormThreads / 32];
+  const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5;
+  const int64_t r0 = (int64_t)blockIdx.x * kNormRows;
+  const int64_t r1 = r0 + kNormRows < V.rows ? r0 + kNormRows : V.rows;
+  for (int64_t col = blockIdx.y; col < V.s; col += gridDim.y) {
+    const T* c = V.S + col * V.rows;
+    double s = 0;
+    for (int64_t r = r0 + threadIdx.x; r < r1; r += kNormThreads) {
+      const double x = (double)c[r];
+      s += x * x;
+    }
+    for (int d = 16; d >= 1; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
+    if (lane == 0) ws[wid] = s;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+      double t = 0;
+      for (int w = 0; w < kNormThreads / 32; ++w) t += ws[w];
+      part[col * nchunk + blockIdx.x] = t;
+    }
+    __syncthreads();   // ws is reused by the next column
   }
-  for (int d = 16; d >= 1; d >>= 1) s += __shfl_xor_sync(0xffffffffu, s, d);
-  if (lane == 0) sq[V.nb + warp] = s;
+}
+
+__global__ void colnorm_dense_sum_kernel(const double* part, int64_t nchunk, int64_t s, double* sq) {
+  const int64_t col = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (col >= s) return;
+  double t = 0;
+  for (int64_t k = 0; k < nchunk; ++k) t += part[col * nchunk + k];
+  sq[col] = t;
 }
 
 template <typename T>
@@ -584,13 +608,19 @@ static qrkit_status norms_typed(qrkit_ctx* ctx, const ComposedView<T>& V, double
   cudaStream_t st = ctx->stream;
   const int64_t N = P.cols + P.s.shared_cols;
   qrkit_status rc;
-  if ((rc = ensure(ctx, C.sq, (size_t)N * sizeof(double), "column sums")) != QRKIT_OK) return rc;
+  // dense S: the chunk sums of pass 1 follow the N column sums in the same scratch
+  const int64_t nchunk = V.coupled == QRKIT_COUPLED_DENSE ? std::max<int64_t>(1, (V.rows + kNormRows - 1) / kNormRows) : 0;
+  const size_t sq_bytes = (size_t)(N + nchunk * (V.coupled == QRKIT_COUPLED_DENSE ? V.s : 0)) * sizeof(double);
+  if ((rc = ensure(ctx, C.sq, sq_bytes, "column sums")) != QRKIT_OK) return rc;
   double* sq = (double*)C.sq.ptr;
   QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(sq, 0, (size_t)N * sizeof(double), st));
   LAUNCH(ctx, colnorm_blocks_kernel<T><<<blocks_for(P.K, 128), 128, 0, st>>>(V, sq));
-  if (V.coupled == QRKIT_COUPLED_DENSE)
-    LAUNCH(ctx, colnorm_dense_kernel<T><<<blocks_for((int64_t)V.s * 32, 256), 256, 0, st>>>(V, sq));
-  else if (V.coupled == QRKIT_COUPLED_WINDOW)
+  if (V.coupled == QRKIT_COUPLED_DENSE) {
+    if (nchunk > (int64_t)INT32_MAX) return fail(ctx, QRKIT_EUNSUPPORTED, "too many rows for the column norms");
+    const dim3 grid((unsigned)nchunk, (unsigned)std::min<int64_t>(V.s, 65535));
+    LAUNCH(ctx, colnorm_dense_part_kernel<T><<<grid, kNormThreads, 0, st>>>(V, sq + N, nchunk));
+    LAUNCH(ctx, colnorm_dense_sum_kernel<<<blocks_for(V.s, 128), 128, 0, st>>>(sq + N, nchunk, V.s, sq + V.nb));
+  } else if (V.coupled == QRKIT_COUPLED_WINDOW)
     LAUNCH(ctx, colnorm_window_kernel<T><<<blocks_for(P.K, 128), 128, 0, st>>>(V, sq));
   LAUNCH(ctx, finalize_norms_kernel<<<blocks_for(N, 256), 256, 0, st>>>(sq, D, N));
   return QRKIT_OK;
