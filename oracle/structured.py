@@ -168,11 +168,13 @@ class ComposedFactor:
     residual_sq: float = 0.0                            # ||bottom of Q^T [b; 0]||^2
 
 
-def augmented_block(P: BlockProblem, i: int, D: np.ndarray):
-    """B_i = [J_i; lambda^(1/2) D_i], C_i = [S_i; 0], rhs [b_i; 0] (Sec. 4.5 row interleave)."""
+def augmented_block(P: BlockProblem, i: int, D: np.ndarray, co=None, ro=None):
+    """B_i = [J_i; lambda^(1/2) D_i], C_i = [S_i; 0], rhs [b_i; 0] (Sec. 4.5 row interleave).
+    co, ro: the problem's column and row offsets, if the caller already has them."""
     blk = np.asarray(P.blocks[i], dtype=np.float64)
     n, m = blk.shape
-    co, ro = P.col_offsets(), P.row_offsets()
+    if co is None or ro is None:
+        co, ro = P.col_offsets(), P.row_offsets()
     lam_half = np.sqrt(P.lam)
     rows = [blk]
     if P.lam > 0.0:
@@ -201,8 +203,9 @@ def factor_and_solve(P: BlockProblem, reduced_solver=None):
     s = P.s
     red_rows, red_rhs, red_start = [], [], []
     p_blocks = []
+    co, ro = P.col_offsets(), P.row_offsets()
     for i in range(P.K):
-        B, C, rhs = augmented_block(P, i, D)
+        B, C, rhs = augmented_block(P, i, D, co, ro)
         m = B.shape[1]
         f = hh.qr(B)                                  # Sec. 4.1: Q_i R_i = qr(B_i)
         qtb = hh.apply_qt(f, rhs)
