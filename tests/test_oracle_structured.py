@@ -121,8 +121,8 @@ def test_planted_mistake_missing_damping_is_caught(monkeypatch):
     """Dropping the damping rows of the blocks fails the optimality identity."""
     real = st.augmented_block
 
-    def bad(P, i, D):
-        B, C, rhs = real(P, i, D)
+    def bad(P, i, D, *offsets):
+        B, C, rhs = real(P, i, D, *offsets)
         n = P.blocks[i].shape[0]
         return B[:n], (None if C is None else C[:n]), rhs[:n]
     monkeypatch.setattr(st, "augmented_block", bad)
