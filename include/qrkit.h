@@ -297,6 +297,23 @@ qrkit_status qrkit_task_layout(int64_t num_blocks, const uint8_t* block_rows, co
                                int64_t supertile, int key_major, int64_t* num_tasks, int32_t* task_key,
                                int64_t* task_slots, int64_t capacity);
 
+/* Row and column permutations that expose a banded structure (Sec. 4.3), on the host with no
+ * CUDA call: P_c by reverse Cuthill-McKee on the column graph of A (columns adjacent when a row
+ * holds both; each search starts at the unvisited column of least degree, lower index first;
+ * neighbours are queued by (degree, index); the visit order is reversed), P_r by the rows'
+ * (first, last) column under P_c, ties by row index, empty rows last.
+ *   rows, cols        : shape of A (cols >= 1)
+ *   row_ptr, col_idx  : HOST, the pattern in CSR form (rows + 1 offsets from 0; column indices
+ *                       in [0, cols), any order, repeats allowed)
+ *   col_perm          : HOST out, cols entries: original column at each new position
+ *   row_perm          : HOST out, rows entries: original row at each new position
+ *   row_start         : HOST out, rows entries: first new column of that row (cols if empty)
+ *   width             : HOST out: band width w; row k of P_r A P_c lies in columns
+ *                       row_start[k] .. row_start[k] + w - 1
+ * QRKIT_EINVAL for a malformed pattern.  Synchronous; O(sum over rows of nnz(row)^2) time. */
+qrkit_status qrkit_band_order(int64_t rows, int64_t cols, const int64_t* row_ptr, const int32_t* col_idx,
+                              int32_t* col_perm, int64_t* row_perm, int32_t* row_start, int32_t* width);
+
 /* ---- Levenberg-Marquardt on the device (Sec. 2; Backtrack LM of Sec. 5.2) ----
  * Model QRKIT_MODEL_CURVEFIT: 2-D points fitted by an open uniform cubic B-spline; each
  * point has one latent curve parameter t_i and the control points are shared, so J is

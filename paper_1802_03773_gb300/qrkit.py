@@ -116,6 +116,7 @@ _SIGS = {
     "qrkit_block_solve_noalloc": (ctypes.c_int, [ctypes.c_int, _VP, ctypes.c_int, ctypes.c_int64, _VP,
                                                  _VP, _VP, _VP, _VP, ctypes.c_int]),
     "qrkit_launch_count": (ctypes.c_int64, [_VP]),
+    "qrkit_band_order": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP, _VP]),
     "qrkit_task_layout": (ctypes.c_int, [ctypes.c_int64, _VP, _VP, ctypes.c_int64, ctypes.c_int, _VP, _VP, _VP,
                                          ctypes.c_int64]),
 }
@@ -184,6 +185,27 @@ def task_layout(n, m, supertile=65536, key_major=False):
     if st != 0:
         raise QRKitError(st, "qrkit_task_layout failed")
     return key, slots
+
+
+def band_order(rows, cols, row_ptr, col_idx):
+    """qrkit_band_order: P_c, P_r, row starts and band width exposing a banded structure.
+
+    row_ptr (rows + 1), col_idx: the CSR pattern of A.  Returns (col_perm int32, row_perm
+    int64, row_start int32, width).  Raises QRKitError on a non-zero status.
+    """
+    lib = load()
+    row_ptr = np.ascontiguousarray(row_ptr, dtype=np.int64)
+    col_idx = np.ascontiguousarray(col_idx, dtype=np.int32)
+    col_perm = np.empty(int(cols), dtype=np.int32)
+    row_perm = np.empty(max(int(rows), 1), dtype=np.int64)
+    row_start = np.empty(max(int(rows), 1), dtype=np.int32)
+    width = ctypes.c_int32(0)
+    st = lib.qrkit_band_order(int(rows), int(cols), row_ptr.ctypes.data, col_idx.ctypes.data if col_idx.size else None,
+                              col_perm.ctypes.data, row_perm.ctypes.data, row_start.ctypes.data,
+                              ctypes.addressof(width))
+    if st != 0:
+        raise QRKitError(st, "qrkit_band_order failed")
+    return col_perm, row_perm[:int(rows)], row_start[:int(rows)], int(width.value)
 
 
 def declared_symbols():
