@@ -602,6 +602,10 @@ block_solve_kernel(BlockSolveArgs<T> A) {
   }
   if (__syncthreads_or(!ok)) {
     if (tid == 0) record(A.status, QRKIT_ETIMEOUT);
+    // the bulk loads may still be in flight: wait for them once more (bounded) before the
+    // CTA's shared memory is given up
+    for (long long polls = 0; polls < A.wait_limit; ++polls)
+      if (mbar_try_wait(bar, 0u)) break;
     return;
   }
   // staging of the results: the factor goes back over J (packed), Q^T b over b unless the
