@@ -22,6 +22,9 @@ Modules
   curvefit     - the cubic B-spline curve-fit model used by the LM workloads
   lm           - Levenberg-Marquardt step with the Nielsen damping rule (Sec. 2, Sec. 5.2)
   mlp          - the small damping-prediction MLP: forward, backward, Adam (not in the paper)
+  more         - More's two-factorization LM step: J = QR, then [R; lambda^(1/2) D] = Q'R'
+                 (Sec. 5.2, Eq. LMTwoStep)
+  reorder      - row and column permutations that expose a banded structure (Sec. 4.3)
 
 Parity status of each function is stated in its module header; a function with no
 independent pin says "parity unpinned".
