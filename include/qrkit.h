@@ -110,16 +110,19 @@ enum { QRKIT_BAND_AUTO = 0, QRKIT_BAND_SWEEP = 1, QRKIT_BAND_PARALLEL = 2 };
 typedef struct qrkit_ctx qrkit_ctx;
 
 /* Create a context on `device` (CUDA ordinal) issuing work on `stream` (a cudaStream_t,
- * NULL = legacy default stream).  precision: qrkit_precision.  *out receives the context. */
+ * NULL = legacy default stream).  precision: qrkit_precision.  *out receives the context.
+ * (No paper counterpart: the context owns the plan and the device workspace.) */
 qrkit_status qrkit_create(qrkit_ctx** out, int device, void* stream, int precision);
 
-/* Release the context, its plan and its device workspace.  NULL is allowed. */
+/* Release the context, its plan and its device workspace.  NULL is allowed.  (No paper
+ * counterpart.) */
 void qrkit_destroy(qrkit_ctx* ctx);
 
-/* Message of the last failed call on ctx ("" if none); valid until the next call. */
+/* Message of the last failed call on ctx ("" if none); valid until the next call.  (No paper
+ * counterpart.) */
 const char* qrkit_last_error(const qrkit_ctx* ctx);
 
-/* Static name of a status code. */
+/* Static name of a status code.  (No paper counterpart.) */
 const char* qrkit_status_string(int status);
 
 /* Structure plan (Sec. 3 composition, Sec. 4.3 / 4.5 row permutation): validates the
@@ -183,7 +186,8 @@ qrkit_status qrkit_apply_qt(qrkit_ctx* ctx, const void* b, void* qtb);
  * (block columns then shared columns). */
 qrkit_status qrkit_solve_r(qrkit_ctx* ctx, const void* qtb, void* p);
 
-/* p = argmin ||P_r [J; lambda^(1/2) D] p - P_r [b; 0]|| with the stored factor: Q^T b,
+/* Sec. 5.1 (Q^T b, then the R solve) with refinement (not in the paper):
+ * p = argmin ||P_r [J; lambda^(1/2) D] p - P_r [b; 0]|| with the stored factor: Q^T b,
  * back-substitution, then `refine_steps` refinement steps (QRKIT_FP32_REFINED: residual
  * g = J^T (b - J p) - lambda D^2 p in double, correction R^{-1} R^{-T} g; ignored for
  * QRKIT_FP32, allowed but not useful for QRKIT_FP64). */
@@ -231,18 +235,20 @@ qrkit_status qrkit_block_solve_noalloc(int device, void* stream, int precision,
                                        const uint8_t* block_cols, const void* J, const void* b,
                                        void* p, int refine_steps);
 
-/* Banded factor of the last qrkit_factor_solve on a QRKIT_STRUCT_BANDED plan (device pointers,
+/* Banded factor (Sec. 4.4) of the last qrkit_factor_solve on a QRKIT_STRUCT_BANDED plan (device pointers,
  * any may be NULL): Rw[j * w + t] = R[j, j + t] per global column j, c = top of Q^T [b; 0] per
  * column; res2 (HOST, one double per instance) = squared residual norm.  Synchronous.
  * Rw and c exist only for the SWEEP algorithm (QRKIT_EUNSUPPORTED otherwise); res2 always. */
 qrkit_status qrkit_get_band_factor(qrkit_ctx* ctx, void* Rw, void* c, double* res2);
 
-/* Copy the stored factor of a block structure to caller buffers (device pointers, either
+/* Copy the stored factor of a block structure (Sec. 4.1; reflectors as in Sec. 2) to caller
+ * buffers (device pointers, either
  * may be NULL): factor values in J's packing (V strictly below the diagonal, R on and above)
  * and tau (sum m_i). */
 qrkit_status qrkit_get_factor(qrkit_ctx* ctx, void* factor_out, void* tau_out);
 
-/* Replace the window starts of a QRKIT_COUPLED_WINDOW plan from DEVICE memory (K int32, same
+/* Replace the window starts (Sec. 4.2 windows, re-sorted by the P_r of Sec. 4.3) of a
+ * QRKIT_COUPLED_WINDOW plan from DEVICE memory (K int32, same
  * meaning as qrkit_structure.window_start), e.g. when an LM iteration moves the windows.
  * Copied asynchronously; a start outside its block's segment is clamped into it and
  * reported as QRKIT_EINVAL through the device status word.  Takes effect at the next
@@ -270,8 +276,8 @@ qrkit_status qrkit_get_row_order(qrkit_ctx* ctx, int64_t* order);
 qrkit_status qrkit_autotune(qrkit_ctx* ctx, const void* J, const void* b, void* p, int refine_steps,
                             const char* cache_path, char* chosen, int64_t chosen_len);
 
-/* Apply a configuration in the text form qrkit_autotune returns (HOST string) to the current
- * plan without timing, e.g. one chosen earlier on the same GPU.  QRKIT_EINVAL if the text does
+/* Apply a configuration in the text form qrkit_autotune returns (HOST string; no paper
+ * counterpart) to the current plan without timing, e.g. one chosen earlier on the same GPU.  QRKIT_EINVAL if the text does
  * not parse or does not fit the plan's kind; synchronous. */
 qrkit_status qrkit_apply_tuning(qrkit_ctx* ctx, const char* choice);
 
@@ -348,14 +354,14 @@ typedef struct qrkit_lm_state {
   int64_t iteration; /* in/out: steps tried */
 } qrkit_lm_state;
 
-/* Plan the LM model: builds the block-angular structure (2x1 blocks, windows of 8, one
+/* Plan the LM model (Sec. 2, Sec. 5.2; the curve-fit model is ours): builds the block-angular structure (2x1 blocks, windows of 8, one
  * segment per problem, replacing the context's plan) and the device buffers.  x, passed to
  * the calls below, is a DEVICE array of N = sum P_k + sum 2 Kc_k doubles:
  * [t of all points, problems in order | control points of problem 0 (x0, y0, x1, y1, ...),
  * problem 1, ...].  Synchronous. */
 qrkit_status qrkit_lm_plan(qrkit_ctx* ctx, const qrkit_lm_problem* problem);
 
-/* One LM iteration for every problem not marked done: f, J and the window starts at x;
+/* One LM iteration (Sec. 2; Backtrack LM of Sec. 5.2) for every problem not marked done: f, J and the window starts at x;
  * D = column norms of J (zero -> 1); QR of P_r [J; lambda^(1/2) D] by the composed path with
  * the rows of J, S and b rounded to the context precision; p from qrkit_solve with
  * `refine_steps`; cost at x + p; gain ratio; Nielsen update (rho > 0: accept,
@@ -364,7 +370,7 @@ qrkit_status qrkit_lm_plan(qrkit_ctx* ctx, const qrkit_lm_problem* problem);
  * read and written.  Synchronous (returns after the state is copied back). */
 qrkit_status qrkit_lm_step(qrkit_ctx* ctx, double* x, qrkit_lm_state* states, int refine_steps);
 
-/* Up to max_iter iterations as in qrkit_lm_step with the state kept on the device; a problem
+/* Up to max_iter iterations as in qrkit_lm_step (Sec. 2, Sec. 5.2) with the state kept on the device; a problem
  * is marked done after an accepted step with cost - cost_new <= ftol * cost (or lambda > 1e16),
  * and the loop ends early once every problem is done (checked every 8 iterations).  With
  * use_graph != 0 one iteration is captured into a CUDA graph (on the first call, or when x,
@@ -373,14 +379,15 @@ qrkit_status qrkit_lm_step(qrkit_ctx* ctx, double* x, qrkit_lm_state* states, in
 qrkit_status qrkit_lm_run(qrkit_ctx* ctx, double* x, qrkit_lm_state* states, int max_iter, double ftol,
                           int refine_steps, int use_graph);
 
-/* The linearised system of the planned LM model at x (DEVICE buffers, any may be NULL), in the
+/* The linearised system (Sec. 2; block-angular as in Sec. 4.2) of the planned LM model at x
+ * (DEVICE buffers, any may be NULL), in the
  * layout of a QRKIT_COUPLED_WINDOW block structure with window 8: J (2 x 1 block per point,
  * 2 sum P_k values), S (per point 2 x 8 column-major, 16 sum P_k values), b = -f (2 sum P_k),
  * all in the context precision, and the window starts (int32, sum P_k; global shared column).
  * Asynchronous. */
 qrkit_status qrkit_lm_linearize(qrkit_ctx* ctx, const double* x, void* J, void* S, void* b, int32_t* start);
 
-/* Residual of the planned LM model at x: f (DEVICE, 2 sum P_k doubles) = curve(t_i) - data_i
+/* Residual (Sec. 2) of the planned LM model at x: f (DEVICE, 2 sum P_k doubles) = curve(t_i) - data_i
  * per point, (x, y) pairs.  Asynchronous. */
 qrkit_status qrkit_lm_residual(qrkit_ctx* ctx, const double* x, double* f);
 
@@ -400,34 +407,38 @@ qrkit_status qrkit_lm_residual(qrkit_ctx* ctx, const double* x, double* f);
 #define QRKIT_MLP_CLASSES 8
 #define QRKIT_MLP_PARAMS 5768
 
-/* Set the MLP parameters (HOST, QRKIT_MLP_PARAMS floats) and reset Adam.  Synchronous. */
+/* Set the MLP parameters (HOST, QRKIT_MLP_PARAMS floats) and reset Adam.  Synchronous.  (Not
+ * in the paper.) */
 qrkit_status qrkit_mlp_init(qrkit_ctx* ctx, const float* params);
 
-/* Copy the current float32 parameters to HOST memory.  Synchronous. */
+/* Copy the current float32 parameters to HOST memory.  Synchronous.  (Not in the paper.) */
 qrkit_status qrkit_mlp_params(qrkit_ctx* ctx, float* params);
 
-/* logits (DEVICE, n x QRKIT_MLP_CLASSES) of the samples X (DEVICE, n x QRKIT_MLP_FEATURES). */
+/* logits (DEVICE, n x QRKIT_MLP_CLASSES) of the samples X (DEVICE, n x QRKIT_MLP_FEATURES).
+ * (Not in the paper.) */
 qrkit_status qrkit_mlp_forward(qrkit_ctx* ctx, const float* X, int64_t n, float* logits);
 
-/* One training step on a batch: mean softmax cross-entropy of X (DEVICE, n x FEATURES) against
+/* One training step on a batch (not in the paper): mean softmax cross-entropy of X (DEVICE, n x FEATURES) against
  * labels (DEVICE int32, n, in [0, CLASSES)), its gradient, and (lr > 0) an Adam update.
  * loss (HOST, may be NULL; synchronous when given), grad (DEVICE, QRKIT_MLP_PARAMS, may be
  * NULL): the loss and gradient at the parameters before the update. */
 qrkit_status qrkit_mlp_train_step(qrkit_ctx* ctx, const float* X, const int32_t* labels, int64_t n, float lr,
                                   float* loss, float* grad);
 
-/* Damping of the planned LM model: 0 = Nielsen's rule, 1 = the context's MLP after accepted
- * steps (Nielsen after rejected ones). */
+/* Damping of the planned LM model: 0 = Nielsen's rule (Sec. 2 adapting Lourakis, Sec. 5.2),
+ * 1 = the context's MLP after accepted steps (not in the paper; Nielsen after rejected ones). */
 qrkit_status qrkit_lm_set_policy(qrkit_ctx* ctx, int use_mlp);
 
-/* Features of every problem after the last LM step (DEVICE, B x QRKIT_MLP_FEATURES floats). */
+/* Features of every problem after the last LM step (DEVICE, B x QRKIT_MLP_FEATURES floats).
+ * (Not in the paper.) */
 qrkit_status qrkit_lm_features(qrkit_ctx* ctx, float* features);
 
 /* Block until the stream is idle and return the device status word (QRKIT_OK if no kernel
- * reported a failure), then clear it. */
+ * reported a failure), then clear it.  (No paper counterpart.) */
 qrkit_status qrkit_sync_status(qrkit_ctx* ctx);
 
-/* Number of this library's kernels launched on ctx since creation (for launch accounting). */
+/* Number of this library's kernels launched on ctx since creation (for launch accounting; no
+ * paper counterpart). */
 int64_t qrkit_launch_count(const qrkit_ctx* ctx);
 
 #ifdef __cplusplus

@@ -53,3 +53,21 @@ def test_create_rejects_bad_arguments(lib):
     assert f(None, 0, None, 1) == 1
     h = ctypes.c_void_p()
     assert f(ctypes.byref(h), 0, None, 7) == 1
+
+
+def test_every_entry_point_cites_its_passage():
+    """Each declaration's comment names the paper passage it implements, or says it has none."""
+    src = open(HEADER).read()
+    decls = [(m.start(), m.group(1)) for m in
+             re.finditer(r"\n(?:qrkit_status|int64_t|const char\*|void)\s+(qrkit_[a-z0-9_]+)\(", src)]
+    missing = []
+    prev = 0
+    for pos, name in decls:
+        seg = src[prev:pos]
+        comment = seg[seg.rfind("/*"):] if "/*" in seg else ""
+        comment = re.sub(r"\s*\n\s*\*\s*", " ", comment)     # join the comment's lines
+        if not re.search(r"Sec\.|Eq\.|not in the paper|no paper counterpart|paper has no counterpart",
+                         comment, flags=re.I):
+            missing.append(name)
+        prev = pos
+    assert not missing, missing
