@@ -71,3 +71,16 @@ def test_rejects_malformed_patterns():
     assert call(2, 4, [0, 2, 1], [0, 1]) == 1      # offsets decrease
     assert call(2, 4, [1, 1, 2], [0, 1]) == 1      # offsets do not start at 0
     assert call(2, 0, [0, 0, 0], [0]) == 1         # no columns
+
+
+def test_fuzz_patterns_match_oracle():
+    """Many small patterns: isolated columns, repeated entries, empty rows, dense rows."""
+    g = np.random.default_rng(2024)
+    for _ in range(150):
+        rows, cols = int(g.integers(0, 40)), int(g.integers(1, 25))
+        dens = g.uniform(0.0, 0.5)
+        rows_cols = []
+        for _ in range(rows):
+            k = int(g.binomial(cols, dens))
+            rows_cols.append(g.integers(0, cols, size=k).tolist())
+        same(rows_cols, rows, cols)
