@@ -147,3 +147,17 @@ def test_layout_rejects_bad_arguments():
     assert call(n, m, cap=1, key=key.ctypes.data) == 0 and key[0] == 1
     assert lib.qrkit_task_layout(0, n.ctypes.data, m.ctypes.data, 64, 0, ctypes.addressof(cnt),
                                  None, None, 0) == 1
+
+
+def test_layout_fuzz():
+    """Random batch sizes, supertiles and orders against the definition."""
+    g = np.random.default_rng(77)
+    for _ in range(25):
+        K = int(g.integers(1, 3000))
+        supertile = int(g.integers(32, 400))
+        key_major = bool(g.integers(0, 2))
+        n, m = shapes(K, seed=int(g.integers(0, 1 << 30)), wide=bool(g.integers(0, 2)))
+        key, slots = qrkit.task_layout(n, m, supertile, key_major)
+        ek, es = expected(n, m, supertile, key_major)
+        np.testing.assert_array_equal(key, ek)
+        np.testing.assert_array_equal(slots, es)
