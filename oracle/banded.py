@@ -31,7 +31,9 @@ Readings (the paper gives the update formula and the block sizes, not a row sche
 Pins (tests/test_oracle_banded.py): same R (up to row signs) and the same solution as
 dense Householder QR (householder.qr) of the assembled matrix and numpy.linalg.lstsq;
 the optimality identity at sizes the dense solve cannot reach; the result does not
-depend on the group size r.
+depend on the group size r.  column_norms (tests/test_oracle_damping_pins.py): a hand-worked
+example (with an entry past the last column, dropped), the norms of the assembled matrix,
+and planted mistakes (squared norms, no zero -> 1, entries past the end kept) that fail.
 """
 from __future__ import annotations
 

@@ -12,7 +12,11 @@ Readings (the paper prints no lambda formula, stopping rule or cost scale):
   * stop: accepted step with relative cost decrease < ftol, or ||J^T f||_inf <= gtol,
     or lambda > 1e16, or max_iter iterations.
 Pins (tests/test_oracle_lm.py): closed-form Nielsen values, monotone accepted costs,
-convergence on a problem with a known exact minimiser, determinism.
+convergence on a problem with a known exact minimiser, determinism.  predicted_decrease
+(tests/test_oracle_damping_pins.py): equals L(0) - L(p*) of the undamped linear model
+L(p) = 1/2 ||b - J p||^2 at the damped minimiser, computed from J p alone; the gain ratio of
+a residual that is linear in x is exactly 1; a dropped 1/2, lambda D for lambda D^2 and a
+wrong sign of J^T b fail.
 """
 from __future__ import annotations
 

@@ -29,7 +29,10 @@ P_r ordering rule (reading: the paper gives no tie rule): rows sorted stably by
 Pins (tests/test_oracle_structured.py): the composed solve equals a dense Householder
 solve of the assembled matrix and numpy.linalg.lstsq; the optimality identity
 J^T (b - J p) = lambda D^2 p; closed forms for one-column blocks and for J = I, D = I;
-R^T R = A^T A for the composed R; Parseval for Q^T [b; 0].
+R^T R = A^T A for the composed R; Parseval for Q^T [b; 0].  column_norms
+(tests/test_oracle_damping_pins.py): a hand-worked example with whole-number norms, the
+norms of the assembled J, and planted mistakes (squared norms, no zero -> 1, damping rows
+counted) that fail.
 """
 from __future__ import annotations
 
