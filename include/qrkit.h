@@ -135,14 +135,18 @@ qrkit_status qrkit_plan(qrkit_ctx* ctx, const qrkit_structure* s);
 
 /* Fused factor + solve for QRKIT_STRUCT_BLOCKS with QRKIT_COUPLED_NONE (Sec. 4.1, Sec. 5.1):
  * for every block the Householder QR of J_i, c_i = Q_i^T b_i, R_i p_i = c_i.  In FP32 refined
- * mode each block then estimates the error of its float solution a priori,
- * u (kappa + kappa^2 ||r|| / (||R|| ||p||)) with u = 2^-24, ||R||_F, ||R^{-1}||_2 from two power
- * steps and ||r|| from the bottom of Q^T b; blocks estimated above 1e-6 are refined by up to
- * `refine_steps` steps with an extended-precision residual: each step computes
- * g = J_i^T (b_i - J_i p_i) in compensated float arithmetic and corrects p_i += R_i^{-1}
- * R_i^{-T} g, stopping once the correction is below 1e-6 of the solution (max norms).  The
- * selected blocks are refined by a second kernel.  refine_steps is ignored for QRKIT_FP32 and
- * QRKIT_FP64.
+ * mode each block then bounds the error of its float solution a priori by
+ * u (kappa + kappa^2 ||r|| / (||R|| ||p||)) with u = 2^-24, kappa <= ||R||_F ||R^{-1}||_F,
+ * ||R|| kappa^2 <= ||R||_F ||R^{-1}||_F^2 and ||r|| from the bottom of Q^T b; blocks above the
+ * selection threshold
+ * (qrkit_set_refinement; 2e-6 by default) are refined by a second kernel with up to
+ * `refine_steps` steps of Bjorck's iterative refinement of the augmented system
+ * [I J_i; J_i^T 0] [r; p] = [b_i; 0] (not in the paper): from p_i and r = Q_i [0; c_i bottom],
+ * each step takes f = b_i - r - J_i p_i and g = -J_i^T r in extended precision (compensated
+ * float or double, qrkit_set_refinement), then h = R_i^{-T} g, [d1; d2] = Q_i^T f,
+ * dp = R_i^{-1} (d1 - h), dr = Q_i [h; d2], p_i += dp, r += dr; a block stops once its
+ * correction is below 1e-6 of its solution (max norms).  refine_steps is ignored for
+ * QRKIT_FP32 and QRKIT_FP64.
  *   J    : packed values, block i column-major n_i x m_i, blocks in order (sum n_i m_i)
  *   b    : sum n_i values, block i's rows contiguous
  *   D    : reserved, pass NULL
@@ -154,6 +158,19 @@ qrkit_status qrkit_plan(qrkit_ctx* ctx, const qrkit_structure* s);
  * its refinement); asynchronous on the context's stream. */
 qrkit_status qrkit_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
                                 double lambda, void* p, void* qtb, int refine_steps);
+
+/* Residual precision of the block refinement (qrkit_set_refinement). */
+enum { QRKIT_RESIDUAL_DOT2 = 0, QRKIT_RESIDUAL_FP64 = 1 };
+
+/* Settings of the FP32-refined block solve of qrkit_factor_solve (refinement is not in the
+ * paper; its goal, single precision without the accuracy loss, is that of Sec. 1 and 7):
+ *   select   : a block is refined when its a-priori error estimate exceeds this (in [0, 1];
+ *              0 refines every block; default 2e-6)
+ *   residual : QRKIT_RESIDUAL_DOT2 (default) computes the refinement's residuals as
+ *              unevaluated float pairs by error-free transformations (Dot2), about as accurate
+ *              as twice the float precision; QRKIT_RESIDUAL_FP64 computes them in double
+ * Takes effect at the next qrkit_factor_solve; QRKIT_EINVAL for values outside these. */
+qrkit_status qrkit_set_refinement(qrkit_ctx* ctx, double select, int residual);
 
 /* For a QRKIT_STRUCT_BANDED plan, qrkit_factor_solve factors and solves every instance of
  * the batch (Sec. 4.4 block-banded QR, damping rows interleaved per column as in Sec. 4.5 /
@@ -223,10 +240,15 @@ qrkit_status qrkit_normal_solve(qrkit_ctx* ctx, const void* J, const void* S, co
  * intermediates do not fit (roughly sum n_i m_i above 3.5 million values in FP32, half that
  * in FP64) is rejected with QRKIT_EUNSUPPORTED before anything is launched; bad arguments give
  * QRKIT_EINVAL, a failed CUDA call QRKIT_ECUDA.
+ * The work runs in the tile kernel (tiles of consecutive blocks, refinement inside the kernel),
+ * not in the warp-task kernels the context path uses by default; the problem solved is the same.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture.  Each call copies the
- * shapes and schedule into the array, clears its status word, launches one kernel on `stream`,
- * then waits for the stream and returns the kernel's status (QRKIT_OK, QRKIT_ESINGULAR, ...).
+ * that device current; make that first call before any stream capture begins.  The caller
+ * thread's current device is the same after the call as before it.  `stream` must belong to
+ * `device` (QRKIT_EINVAL otherwise).  Each call copies the shapes and schedule into the array,
+ * clears its status word, launches one kernel on `stream`, then waits for the stream and reads
+ * the status word back: every call, the first included, returns only after its work is done,
+ * with the kernel's status (QRKIT_OK, QRKIT_ESINGULAR, ...).
  * Every call uses the same array and leaves its contents behind: calls whose work overlaps on
  * the GPU (other threads, other streams) race and must be serialized by the caller.  The
  * factor is not kept for later calls. */

@@ -23,7 +23,9 @@ Readings of the paper (listed with the rest of the readings in the design notes)
 
 Pins (tests/test_oracle_householder.py): worked 2-vector example (tests/golden),
 Q^T Q = I, R upper triangular, Q R = A, agreement with numpy.linalg.qr up to row signs
-and with numpy.linalg.lstsq, compact WY equals the explicit reflector product.
+and with numpy.linalg.lstsq, compact WY equals the explicit reflector product;
+lstsq_stack equals lstsq block by block (zero columns included), and copies of it with a
+planted mistake (tau without its 2, b not transformed) fail.
 """
 from __future__ import annotations
 
@@ -169,3 +171,39 @@ def normalise_row_signs(R: np.ndarray) -> np.ndarray:
     R = np.array(R, dtype=np.float64, copy=True)
     s = np.where(np.diag(R) < 0.0, -1.0, 1.0)
     return R * s[:, None]
+
+
+def lstsq_stack(A: np.ndarray, b: np.ndarray) -> np.ndarray:
+    """lstsq for a stack of same-shape problems, A (K, M, N) and b (K, M); returns x (K, N).
+
+    The same steps as house / qr / apply_qt / back_substitute (Sec. 2, Sec. 5.1), each numpy
+    operation taken over the K problems at once so that a million small blocks solve in
+    seconds: for each column k the reflector of A[:, k:, k] (v[0] = 1, beta = -sign(x0)||x||,
+    tau = 2 / v^T v, tau = 0 for a zero column), applied to the trailing columns and to b,
+    then back-substitution.  Pinned against lstsq block by block.
+    """
+    A = np.array(A, dtype=np.float64, copy=True)
+    c = np.array(b, dtype=np.float64, copy=True)
+    K, M, N = A.shape
+    if M < N:
+        raise ValueError("lstsq_stack expects portrait blocks (M >= N)")
+    for k in range(N):
+        x = A[:, k:, k]
+        norm = np.sqrt(np.einsum("ki,ki->k", x, x))
+        live = norm > 0.0
+        beta = np.where(x[:, 0] >= 0.0, -norm, norm)
+        v = x.copy()
+        v[:, 0] = np.where(live, x[:, 0] - beta, 1.0)
+        v = v / v[:, :1]
+        tau = np.where(live, 2.0 / np.einsum("ki,ki->k", v, v), 0.0)
+        if k + 1 < N:
+            w = np.einsum("ki,kij->kj", v, A[:, k:, k + 1:])
+            A[:, k:, k + 1:] -= tau[:, None, None] * v[:, :, None] * w[:, None, :]
+        A[:, k, k] = np.where(live, beta, A[:, k, k])
+        wc = np.einsum("ki,ki->k", v, c[:, k:])
+        c[:, k:] -= (tau * wc)[:, None] * v
+    xs = np.zeros((K, N))
+    for i in reversed(range(N)):
+        s = c[:, i] - np.einsum("kj,kj->k", A[:, i, i + 1:N], xs[:, i + 1:])
+        xs[:, i] = s / A[:, i, i]
+    return xs

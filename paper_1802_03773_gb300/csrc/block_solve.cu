@@ -916,10 +916,12 @@ qrkit_status launch_block_solve(qrkit_ctx* ctx, const void* J, const void* b, co
 //
 // Some callers cannot call cudaMalloc at all: code that runs under a framework owning every
 // byte of device memory through its own pool, or a process whose memory budget is fixed
-// once at start-up.  For them qrkit_block_solve_noalloc runs the same kernel as
-// qrkit_factor_solve without a context and without allocating: every intermediate it needs
-// (block shapes, tile schedule, factor values, tau, status word) lives in the file-scope
-// array below.  The array is part of the library image, so every process that loads the
+// once at start-up.  For them qrkit_block_solve_noalloc solves the same problem as
+// qrkit_factor_solve, without a context and without allocating, by the tile kernel
+// (block_solve_kernel over tiles of consecutive blocks, refinement inside the kernel; the
+// context path's default is the warp-task kernels): every intermediate it needs (block
+// shapes, tile schedule, factor values, tau, status word) lives in the file-scope array
+// below.  The array is part of the library image, so every process that loads the
 // library holds it on each device it uses until the process exits.
 namespace qrkit {
 namespace {
@@ -933,6 +935,20 @@ unsigned char* g_noalloc_ptr[64] = {nullptr};
 std::mutex g_noalloc_mutex;
 
 size_t align256(size_t v) { return (v + 255) / 256 * 256; }
+
+// Makes `device` current for the lifetime of the guard and gives the caller's thread its
+// previous current device back on every return path.
+struct DeviceGuard {
+  int prev = -1;
+  bool ok = false;
+  explicit DeviceGuard(int device) {
+    if (cudaGetDevice(&prev) != cudaSuccess) return;
+    ok = prev == device || cudaSetDevice(device) == cudaSuccess;
+  }
+  ~DeviceGuard() {
+    if (ok && prev >= 0) cudaSetDevice(prev);
+  }
+};
 
 }  // namespace
 
@@ -977,8 +993,15 @@ extern "C" qrkit_status qrkit_block_solve_noalloc(int device, void* stream, int 
   const size_t o_F = off; off = align256(off + (size_t)P.values * elem);
   const size_t o_tau = off; off = align256(off + (size_t)P.cols * elem);
   if (off > kNoallocScratchBytes) return QRKIT_EUNSUPPORTED;
-  cudaError_t e = cudaSetDevice(device);
-  if (e != cudaSuccess) return QRKIT_ECUDA;
+  DeviceGuard guard(device);
+  if (!guard.ok) return QRKIT_ECUDA;
+  cudaError_t e = cudaSuccess;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (st) {   // a stream of another device would run the kernel against the wrong array
+    int sdev = -1;
+    if ((e = cudaStreamGetDevice(st, &sdev)) != cudaSuccess) return QRKIT_ECUDA;
+    if (sdev != device) return QRKIT_EINVAL;
+  }
   unsigned char* base = nullptr;
   {
     std::lock_guard<std::mutex> lock(g_noalloc_mutex);
@@ -990,7 +1013,6 @@ extern "C" qrkit_status qrkit_block_solve_noalloc(int device, void* stream, int 
     }
     base = g_noalloc_ptr[device];
   }
-  cudaStream_t st = (cudaStream_t)stream;
   // the array keeps the previous call's contents: the status word must start at zero;
   // every other region used here is written in full before it is read
   if ((e = cudaMemsetAsync(base + o_status, 0, sizeof(int), st)) != cudaSuccess) return QRKIT_ECUDA;
@@ -1004,7 +1026,10 @@ extern "C" qrkit_status qrkit_block_solve_noalloc(int device, void* stream, int 
   int* status = reinterpret_cast<int*>(base + o_status);
   auto fill = [&](auto* tag) {
     using T = std::remove_pointer_t<decltype(tag)>;
-    BlockSolveArgs<T> A;
+    BlockSolveArgs<T> A{};
+    A.rlist = nullptr;
+    A.rcount = nullptr;
+    A.rcap = 0;
     A.n = base + o_n;
     A.m = base + o_m;
     A.tile_block = reinterpret_cast<const int64_t*>(base + o_tb);

@@ -27,6 +27,17 @@ int warp_slot_bytes(const Plan& P, int es) {
   return (best + 127) / 128 * 128;
 }
 
+// One data buffer of a refinement warp: J's and the factor's supersets and b's.
+int warp_refine_slot_bytes(const Plan& P) {
+  int best = 0;
+  for (int k = 0; k < kTaskKeys; ++k) {
+    if (P.key_off[k + 1] == P.key_off[k]) continue;
+    const int G = group_lanes(k), M = (k & 7) + 1;
+    best = std::max(best, task_blocks(G) * (2 * slot_j_bytes(G, M, 4) + slot_b_bytes(G, 4)));
+  }
+  return (best + 127) / 128 * 128;
+}
+
 // Resident CTAs per SM of a kernel at this shared-memory size; the kernel's shared-memory
 // limit is raised and its occupancy queried once per (kernel, size) and cached.
 template <typename F>
@@ -68,6 +79,7 @@ qrkit_status launch_tasks_typed(qrkit_ctx* ctx, const void* J, const void* b, vo
   A.data_bytes = warp_slot_bytes(P, es);
   A.warp_bytes = (warp_desc_bytes((int)sizeof(TaskEntry)) + 2 * A.data_bytes + 127) / 128 * 128;
   A.status = ctx->d_status;
+  A.select = ctx->refine_select;
   A.rlist = nullptr;
   A.rcount = nullptr;
   A.key_off = (const int64_t*)P.d_key_off.ptr;
@@ -97,22 +109,29 @@ qrkit_status launch_tasks_typed(qrkit_ctx* ctx, const void* J, const void* b, vo
     R.J_end = R.J + P.values;
     R.b_end = R.b + P.rows;
     R.F = (const float*)A.F;
+    R.F_end = R.F + P.values;
+    R.tau = (const float*)A.tau;
     R.x = (float*)p;
     R.rlist = A.rlist;
     R.rcount = A.rcount;
     R.key_off = A.key_off;
     R.steps = refine_steps;
     R.tol = 1e-6f;
-    R.data_bytes = A.data_bytes;
+    R.data_bytes = warp_refine_slot_bytes(P);
     R.warp_bytes = (warp_desc_bytes((int)sizeof(RefEntry)) + 2 * R.data_bytes + 127) / 128 * 128;
-    const size_t smem2 = (size_t)wpc * R.warp_bytes;
+    const int wpc2 = kRefineWarps, threads2 = 32 * kRefineWarps;
+    const size_t smem2 = (size_t)wpc2 * R.warp_bytes;
     R.status = A.status;
+    const bool res64 = ctx->refine_residual != 0;
     int per_sm2 = 0;
-    if ((st = resident(ctx, refine_setup, threads, smem2, 11, per_sm2)) != QRKIT_OK) return st;
-    const int64_t want2 = (P.max_refine_tasks + wpc - 1) / wpc;
+    if ((st = resident(ctx, res64 ? refine_setup<1> : refine_setup<0>, threads2, smem2, res64 ? 12 : 11, per_sm2)) !=
+        QRKIT_OK)
+      return st;
+    const int64_t want2 = (P.max_refine_tasks + wpc2 - 1) / wpc2;
     const int64_t full2 = (int64_t)ctx->num_sms * per_sm2;
     const unsigned grid2 = (unsigned)std::max<int64_t>(1, std::min(want2, full2));
-    QRKIT_CUDA_TRY(ctx, refine_launch(R, grid2, threads, smem2, ctx->stream));
+    QRKIT_CUDA_TRY(ctx, res64 ? refine_launch<1>(R, grid2, threads2, smem2, ctx->stream)
+                              : refine_launch<0>(R, grid2, threads2, smem2, ctx->stream));
     ctx->launches += 1;
   }
   return QRKIT_OK;

@@ -39,12 +39,16 @@ namespace tasks {
 using namespace dev;
 
 constexpr float kUnitRoundoff = 5.9604645e-8f;   // 2^-24
-constexpr float kRefineTarget = 1e-6f;           // blocks estimated above this are refined
+constexpr float kRefineSelect = 2e-6f;           // default: blocks estimated above this are refined
 constexpr int kMaxCols = 8;
 constexpr int kTaskMaxWarps = 8;   // the kernels are compiled for at most 256 threads per CTA
 #ifndef QRKIT_TASK_CTAS
 #define QRKIT_TASK_CTAS 2   // resident CTAs per SM the float task kernel is compiled for
 #endif
+#ifndef QRKIT_REFINE_CTAS
+#define QRKIT_REFINE_CTAS 2   // the refinement kernel is compiled for 128 registers a thread
+#endif
+constexpr int kRefineWarps = 4;   // warps per CTA of the refinement kernel (its buffers are large)
 
 __host__ __device__ constexpr int group_lanes(int key) { return (key >> 3) + 1; }
 __host__ __device__ constexpr int task_blocks(int G) { return 32 / G; }
@@ -267,178 +271,242 @@ __device__ __forceinline__ bool group_backsub(const T (&a)[kMaxCols][4], const T
   return ok;
 }
 
-// w = R^{-T} v, then v = R^{-1} w, in place (v replicated over the group, R distributed by
-// rows; d = reciprocal diagonal).  R^T is solved column by column of R: each lane keeps the
-// partial sums of its own rows' contributions.
-template <int G>
-__device__ __forceinline__ void group_normal_solve(const float (&a)[kMaxCols][4], const float (&d)[kMaxCols],
-                                                   float (&v)[kMaxCols], int M, const Group<G>& g) {
-  float part[kMaxCols];
-#pragma unroll
-  for (int k = 0; k < kMaxCols; ++k) part[k] = 0.f;
-#pragma unroll
-  for (int k = 0; k < kmax<G>(); ++k) {
-    if (k < M) {
-      const float s = k == 0 ? 0.f : g.sum(part[k]);
-      const float w = (v[k] - s) * d[k];
-      v[k] = w;
-      const bool own = g.owns(k >> 2);
-#pragma unroll
-      for (int j = k + 1; j < kmax<G>(); ++j)
-        if (j < M) part[j] += own ? a[j][k & 3] * w : 0.f;
-    }
-  }
-#pragma unroll
-  for (int k = kmax<G>() - 1; k >= 0; --k) {
-    if (k < M) {
-      float s = v[k];
-#pragma unroll
-      for (int j = k + 1; j < kmax<G>(); ++j)
-        if (j < M) s -= a[j][k & 3] * v[j];
-      v[k] = g.bcast(s, k >> 2) * d[k];
-    }
-  }
-}
-
-template <int G>
-__device__ __forceinline__ void recip_diag(const float (&a)[kMaxCols][4], int M, const Group<G>& g,
-                                           float (&d)[kMaxCols]) {
-#pragma unroll
-  for (int k = 0; k < kMaxCols; ++k) d[k] = 0.f;
-#pragma unroll
-  for (int k = 0; k < kmax<G>(); ++k)
-    if (k < M) d[k] = g.bcast(rcp(a[k][k & 3]), k >> 2);
-}
-
-// A-priori error estimate of the float least-squares solution (Householder QR is backward
-// stable: relative error ~ u (kappa + kappa^2 ||r|| / (||A|| ||x||))), with ||A|| ~ ||R||_F,
-// ||R^{-1}||_2^2 from two power steps v <- R^{-1} R^{-T} v / ||v|| starting from ones, and
-// ||r|| = || rows M.. of Q^T b ||; true when the estimate exceeds kRefineTarget (or is NaN).
-// One lane per block, R read from the factor in its slot (column k at F + k n); res2 = ||r||^2,
-// x2 = ||x||^2.
-__device__ __forceinline__ bool lane_needs_refinement(const float* F, int n, int M, float res2, float x2) {
-  float R[kMaxCols][kMaxCols], d[kMaxCols], v[kMaxCols];
+// A-priori error estimate of the float least-squares solution.  Householder QR is backward
+// stable, so the forward error is a small multiple of u (kappa + kappa^2 ||r|| / (||A|| ||x||));
+// here kappa and ||A|| kappa^2 are replaced by upper bounds from the Frobenius norms of R and
+// R^{-1} (kappa_2 <= ||R||_F ||R^{-1}||_F, ||A||_2 <= ||R||_F), so the estimate never falls
+// below that expression: est = u (||R||_F ||R^{-1}||_F + ||R||_F ||R^{-1}||_F^2 ||r|| / ||x||)
+// with u = 2^-24 and ||r|| = || rows M.. of Q^T b ||.  R^{-1} is formed column by column (the
+// columns are independent back-substitutions).  True when the estimate exceeds `target` (or
+// is NaN: a zero pivot, x = 0).  One lane per block, R read from the factor in its slot
+// (column k at F + k n); res2 = ||r||^2, x2 = ||x||^2.
+template <int M>
+__device__ __forceinline__ bool lane_needs_refinement(const float* F, int n, float res2, float x2, float target) {
+  float R[M][M], d[M];
   float rF2 = 0.f;
 #pragma unroll
-  for (int k = 0; k < kMaxCols; ++k) {
-    d[k] = 0.f;
-    v[k] = 0.f;
+  for (int k = 0; k < M; ++k) {
+    const float* col = F + k * n;
 #pragma unroll
-    for (int i = 0; i < kMaxCols; ++i) R[i][k] = 0.f;
-    if (k < M) {
-      const float* col = F + k * n;
+    for (int i = 0; i <= k; ++i) {
+      R[i][k] = col[i];
+      rF2 += R[i][k] * R[i][k];
+    }
+    d[k] = rcp(R[k][k]);
+  }
+  float iF2 = 0.f;
 #pragma unroll
-      for (int i = 0; i <= k; ++i) {
-        R[i][k] = col[i];
-        rF2 += R[i][k] * R[i][k];
-      }
-      d[k] = rcp(R[k][k]);
-      v[k] = 1.f;
+  for (int j = 0; j < M; ++j) {   // column j of R^{-1}: y_j = 1 / R_jj, rows above by back-substitution
+    float y[M];
+    y[j] = d[j];
+    iF2 += y[j] * y[j];
+#pragma unroll
+    for (int i = j - 1; i >= 0; --i) {
+      float sm = 0.f;
+#pragma unroll
+      for (int l = i + 1; l <= j; ++l) sm += R[i][l] * y[l];
+      y[i] = -sm * d[i];
+      iF2 += y[i] * y[i];
     }
   }
-  float vn2 = (float)M, inv2 = 0.f;
-#pragma unroll
-  for (int it = 0; it < 2; ++it) {
-    const float sc = rsqrtf(vn2);
-#pragma unroll
-    for (int k = 0; k < kMaxCols; ++k) {   // R^T w = v / ||v||
-      if (k < M) {
-        float t = v[k] * sc;
-#pragma unroll
-        for (int i = 0; i < k; ++i) t -= R[i][k] * v[i];
-        v[k] = t * d[k];
-      }
-    }
-#pragma unroll
-    for (int k = kMaxCols - 1; k >= 0; --k) {   // R v' = w
-      if (k < M) {
-        float t = v[k];
-#pragma unroll
-        for (int j = k + 1; j < kMaxCols; ++j)
-          if (j < M) t -= R[k][j] * v[j];
-        v[k] = t * d[k];
-      }
-    }
-    vn2 = 0.f;
-#pragma unroll
-    for (int k = 0; k < kMaxCols; ++k) vn2 += v[k] * v[k];
-    inv2 = sqrtf(vn2);
-  }
-  const float rF = sqrtf(rF2);
-  const float est = kUnitRoundoff * (rF * sqrtf(inv2) + rF * inv2 * sqrtf(res2 / x2));
-  return !(est <= kRefineTarget);
+  const float kF = sqrtf(rF2 * iF2);
+  const float est = kUnitRoundoff * (kF + kF * sqrtf(iF2) * sqrtf(res2 / x2));
+  return !(est <= target);
 }
 
-// Refinement of the group's block: g = J^T (b - J x) with the residual in compensated float
-// arithmetic (Dot2 of Ogita, Rump and Oishi: error-free products and sums, value = s + c),
-// then dx = R^{-1} R^{-T} g and x += dx; with the residual taken exactly this is the first
-// step of Bjorck's augmented-system refinement from (x, b - J x).  A block stops once its
-// correction is at most tol relative to x (max norms), after at most `steps` steps.
-template <int G>
-__device__ __forceinline__ void group_refine(const float (&a)[kMaxCols][4], float (&x)[kMaxCols], const float* sJ,
-                                             const float* sB, int n, int M, const Group<G>& g, int steps,
-                                             float tol) {
+// The refinement's two residuals of the augmented system [I J; J^T 0] [r; x] = [b; 0] in
+// extended precision, rounded once to float: f = b - r - J x on the lane's rows and
+// g = -J^T r (replicated over the group).  RES = 0: compensated float arithmetic (Dot2 of
+// Ogita, Rump and Oishi: error-free products and sums, value = s + c); RES = 1: double.
+template <int G, int M, int RES>
+__device__ __forceinline__ void group_aug_residuals(const float* sJ, const float* sB, int n, const float (&x)[kMaxCols],
+                                                    const float (&r)[4], const Group<G>& g, float (&f)[4],
+                                                    float (&gv)[kMaxCols]) {
   const int q = g.q;
-  float d[kMaxCols];
-  recip_diag<G>(a, M, g, d);
+  if constexpr (RES == 0) {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int row = 4 * q + u;
+      float sh = row < n ? sB[row] : 0.f, sl = 0.f, t, e;
+      two_sum(sh, -r[u], t, e);
+      sh = t;
+      sl = e;
+#pragma unroll
+      for (int j = 0; j < M; ++j) {
+        const float aj = row < n ? sJ[j * n + row] : 0.f;
+        const float p = __fmul_rn(aj, -x[j]);
+        const float pe = __fmaf_rn(aj, -x[j], -p);
+        two_sum(sh, p, t, e);
+        sh = t;
+        sl = __fadd_rn(sl, __fadd_rn(e, pe));
+      }
+      f[u] = __fadd_rn(sh, sl);
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxCols; ++j) gv[j] = 0.f;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      float sh = 0.f, sl = 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int row = 4 * q + u;
+        const float aj = row < n ? sJ[j * n + row] : 0.f;
+        const float p = __fmul_rn(aj, r[u]);
+        const float pe = __fmaf_rn(aj, r[u], -p);
+        float t, e;
+        two_sum(sh, p, t, e);
+        sh = t;
+        sl = __fadd_rn(sl, __fadd_rn(e, pe));
+      }
+      g.sum2(sh, sl);
+      gv[j] = -__fadd_rn(sh, sl);
+    }
+  } else {
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int row = 4 * q + u;
+      double acc = row < n ? (double)sB[row] : 0.0;
+      acc -= (double)r[u];
+#pragma unroll
+      for (int j = 0; j < M; ++j) {
+        const double aj = row < n ? (double)sJ[j * n + row] : 0.0;
+        acc = fma(-aj, (double)x[j], acc);
+      }
+      f[u] = (float)acc;
+    }
+#pragma unroll
+    for (int j = 0; j < kMaxCols; ++j) gv[j] = 0.f;
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      double acc = 0.0;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        const int row = 4 * q + u;
+        const double aj = row < n ? (double)sJ[j * n + row] : 0.0;
+        acc = fma(aj, (double)r[u], acc);
+      }
+      gv[j] = (float)(-g.sum(acc));
+    }
+  }
+}
+
+// Refinement of the group's block by Bjorck's iterative refinement of the augmented system
+// [I J; J^T 0] [r; x] = [b; 0] with the float factor J = Q [R; 0] (a: reflectors below the
+// diagonal, R on and above it, tau).  Q_1 (the first M columns of Q) is formed explicitly in
+// the lanes' rows by applying the reflectors to [I_M; 0], and R is copied to every lane of the
+// group, so that a step needs no sequence of group reductions: only 2M independent ones.
+// Start: x from the first solve and r = Q [0; c2] = b - Q_1 Q_1^T b (the residual the
+// factorization itself gives).  One step, with the two residuals in extended precision:
+// f = b - r - J x, g = -J^T r; h = R^{-T} g; d1 = Q_1^T f; t = d1 - h; dx = R^{-1} t;
+// dr = Q [h; d2] = f - Q_1 t (d2 = Q_2^T f, so Q_2 d2 = f - Q_1 d1); x += dx, r += dr.  Its rate
+// is about u kappa(J) (not u kappa^2 as for the seminormal equations), so it converges on
+// every block with u kappa < 1.  A block stops once its correction is at most tol relative to
+// x (max norms), after at most `steps` steps.  x is replicated over the group; sR is the
+// factor in its slot (column k at sR + k n).
+template <int G, int M, int RES>
+__device__ __forceinline__ void group_refine_aug(const float (&a)[kMaxCols][4], const float (&tau)[kMaxCols],
+                                                 float (&x)[kMaxCols], const float* sJ, const float* sB,
+                                                 const float* sR, int n, const Group<G>& g, int steps, float tol) {
+  const int q = g.q;
+  // Q_1 = H_0 ... H_{M-1} [I_M; 0]: column j is changed by H_j .. H_0 only
+  float qm[M][4];
+#pragma unroll
+  for (int j = 0; j < M; ++j)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) qm[j][u] = 4 * q + u == j ? 1.f : 0.f;
+#pragma unroll
+  for (int k = M - 1; k >= 0; --k) {
+    float v[4];
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      const int r = 4 * q + u;
+      v[u] = r > k ? a[k][u] : (r == k ? 1.f : 0.f);
+    }
+#pragma unroll
+    for (int j = k; j < M; ++j) {
+      float w = 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) w += v[u] * qm[j][u];
+      w = g.sum(w) * tau[k];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) qm[j][u] -= v[u] * w;
+    }
+  }
+  // R on every lane of the group (upper triangle, row-major by pairs i <= l) and 1 / diag
+  float R[M][M], d[M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+#pragma unroll
+    for (int l = 0; l < M; ++l) R[i][l] = (l >= i && n > 0) ? sR[l * n + i] : 0.f;
+    d[i] = rcp(R[i][i]);
+  }
+  // r = b - Q_1 (Q_1^T b)
+  float r[4], bl[4];
+#pragma unroll
+  for (int u = 0; u < 4; ++u) bl[u] = 4 * q + u < n ? sB[4 * q + u] : 0.f;
+  {
+    float c1[M];
+#pragma unroll
+    for (int j = 0; j < M; ++j) {
+      float w = 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) w += qm[j][u] * bl[u];
+      c1[j] = g.sum(w);
+    }
+#pragma unroll
+    for (int u = 0; u < 4; ++u) {
+      float t = bl[u];
+#pragma unroll
+      for (int j = 0; j < M; ++j) t -= qm[j][u] * c1[j];
+      r[u] = t;
+    }
+  }
   bool done = n == 0;
   for (int step = 0; step < steps; ++step) {
     if (__all_sync(0xffffffffu, done)) break;
-    float rh[4], rl[4];
+    float f[4], gv[kMaxCols];
+    group_aug_residuals<G, M, RES>(sJ, sB, n, x, r, g, f, gv);
+    // t = Q_1^T f - R^{-T} g
+    float t[M];
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      rh[u] = 4 * q + u < n ? sB[4 * q + u] : 0.f;
-      rl[u] = 0.f;
+    for (int j = 0; j < M; ++j) {
+      float w = 0.f;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) w += qm[j][u] * f[u];
+      t[j] = g.sum(w);
     }
 #pragma unroll
-    for (int j = 0; j < kmax<G>(); ++j) {
-      if (j < M) {
-        const float xj = -x[j];
-        const float* col = sJ + j * n;
+    for (int k = 0; k < M; ++k) {
+      float hk = gv[k];
 #pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float aj = 4 * q + u < n ? col[4 * q + u] : 0.f;
-          const float p = __fmul_rn(aj, xj);
-          const float pe = __fmaf_rn(aj, xj, -p);
-          float t, e;
-          two_sum(rh[u], p, t, e);
-          rh[u] = t;
-          rl[u] = __fadd_rn(rl[u], __fadd_rn(e, pe));
-        }
-      }
+      for (int i = 0; i < k; ++i) hk -= R[i][k] * (gv[i]);
+      gv[k] = hk * d[k];   // gv becomes h = R^{-T} g in place
+      t[k] -= gv[k];
     }
-    float h[kMaxCols];
+    // dx = R^{-1} t, dr = f - Q_1 t
+    float dx[M];
 #pragma unroll
-    for (int j = 0; j < kMaxCols; ++j) h[j] = 0.f;
+    for (int k = M - 1; k >= 0; --k) {
+      float sk = t[k];
 #pragma unroll
-    for (int j = 0; j < kmax<G>(); ++j) {
-      if (j < M) {
-        const float* col = sJ + j * n;
-        float s = 0.f, c = 0.f;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          const float aj = 4 * q + u < n ? col[4 * q + u] : 0.f;
-          const float p = __fmul_rn(aj, rh[u]);
-          float pe = __fmaf_rn(aj, rh[u], -p);
-          pe = __fmaf_rn(aj, rl[u], pe);
-          float t, e;
-          two_sum(s, p, t, e);
-          s = t;
-          c = __fadd_rn(c, __fadd_rn(e, pe));
-        }
-        g.sum2(s, c);
-        h[j] = __fadd_rn(s, c);
-      }
+      for (int l = k + 1; l < M; ++l) sk -= R[k][l] * dx[l];
+      dx[k] = sk * d[k];
     }
-    group_normal_solve<G>(a, d, h, M, g);
     float dmax = 0.f, xmax = 0.f;
 #pragma unroll
-    for (int k = 0; k < kmax<G>(); ++k) {
-      if (k < M) {
-        const float xn = x[k] + h[k];
-        dmax = fmaxf(dmax, fabsf(h[k]));
-        xmax = fmaxf(xmax, fabsf(xn));
-        if (!done) x[k] = xn;
+    for (int k = 0; k < M; ++k) {
+      const float xn = x[k] + dx[k];
+      dmax = fmaxf(dmax, fabsf(dx[k]));
+      xmax = fmaxf(xmax, fabsf(xn));
+      if (!done) x[k] = xn;
+    }
+    if (!done) {
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        float dr = f[u];
+#pragma unroll
+        for (int j = 0; j < M; ++j) dr -= qm[j][u] * t[j];
+        r[u] += dr;
       }
     }
     done = done || !(dmax > tol * xmax);
@@ -497,31 +565,30 @@ __device__ __forceinline__ void slot_ptrs(unsigned char* db, int G, int M, int g
   sB = reinterpret_cast<T*>(sBraw + (reinterpret_cast<uintptr_t>(gB) & 15));
 }
 
-// Copies of one block's J (n x M values) and b (n values) into its slots by the G lanes of
-// its group: the 16-byte-aligned supersets by 16-byte cp.async copies, or, where a superset
-// would leave the caller's buffers, the values themselves by plain loads.
+// Copy of count values starting at g into a slot by the G lanes of a group: the
+// 16-byte-aligned superset by 16-byte cp.async copies, or, where the superset would leave the
+// buffer [lo, hi), the values themselves by plain loads (s = the slot's first value).
+template <typename T>
+__device__ __forceinline__ void issue_span(const T* g, int count, int G, int q, const T* lo, const T* hi,
+                                           unsigned char* sraw, T* s) {
+  const uintptr_t a = reinterpret_cast<uintptr_t>(g);
+  const uintptr_t l = a & ~(uintptr_t)15, h = (a + (uintptr_t)count * sizeof(T) + 15) & ~(uintptr_t)15;
+  if (l >= reinterpret_cast<uintptr_t>(lo) && h <= reinterpret_cast<uintptr_t>(hi)) {
+    const int nch = (int)((h - l) >> 4);
+    for (int c = q; c < nch; c += G) cp_async16(sraw + 16 * c, reinterpret_cast<const void*>(l + 16 * (uintptr_t)c));
+  } else {
+    for (int k = q; k < count; k += G) s[k] = g[k];
+  }
+}
+
+// Copies of one block's J (n x M values) and b (n values) into its slots.
 template <typename T>
 __device__ __forceinline__ void issue_block(const T* gJ, const T* gB, int n, int M, int G, int q, const T* J_lo,
                                             const T* J_hi, const T* b_lo, const T* b_hi, unsigned char* sJraw,
                                             unsigned char* sBraw, T* sJ, T* sB) {
   if (n <= 0) return;
-  constexpr int es = (int)sizeof(T);
-  const int nv = n * M;
-  const uintptr_t aJ = reinterpret_cast<uintptr_t>(gJ), aB = reinterpret_cast<uintptr_t>(gB);
-  const uintptr_t lJ = aJ & ~(uintptr_t)15, hJ = (aJ + (uintptr_t)nv * es + 15) & ~(uintptr_t)15;
-  const uintptr_t lB = aB & ~(uintptr_t)15, hB = (aB + (uintptr_t)n * es + 15) & ~(uintptr_t)15;
-  if (lJ >= reinterpret_cast<uintptr_t>(J_lo) && hJ <= reinterpret_cast<uintptr_t>(J_hi)) {
-    const int nch = (int)((hJ - lJ) >> 4);
-    for (int c = q; c < nch; c += G) cp_async16(sJraw + 16 * c, reinterpret_cast<const void*>(lJ + 16 * (uintptr_t)c));
-  } else {
-    for (int k = q; k < nv; k += G) sJ[k] = gJ[k];
-  }
-  if (lB >= reinterpret_cast<uintptr_t>(b_lo) && hB <= reinterpret_cast<uintptr_t>(b_hi)) {
-    const int nch = (int)((hB - lB) >> 4);
-    for (int c = q; c < nch; c += G) cp_async16(sBraw + 16 * c, reinterpret_cast<const void*>(lB + 16 * (uintptr_t)c));
-  } else {
-    for (int k = q; k < n; k += G) sB[k] = gB[k];
-  }
+  issue_span<T>(gJ, n * M, G, q, J_lo, J_hi, sJraw, sJ);
+  issue_span<T>(gB, n, G, q, b_lo, b_hi, sBraw, sB);
 }
 
 // Copy of count elements from a slot to global memory: where both agree modulo 16 bytes the
@@ -568,6 +635,7 @@ struct TaskArgs {
   int warp_bytes;   // shared memory per warp (descriptor and data buffers)
   int data_bytes;   // one data buffer
   int* status;
+  float select;             // selection: a-priori error estimate above which a block is refined
   RefEntry* rlist;          // selection: blocks to refine, one list per shape key
   int* rcount;              // kTaskKeys counts
   const int64_t* key_off;   // kTaskKeys + 1 list offsets (list capacity = blocks of the key)
@@ -644,7 +712,7 @@ __device__ __forceinline__ void run_task(const TaskArgs<T>& A, const TaskHdr& h,
     }
     res2 = g.sum(res2);
     __syncwarp();   // the factor's rows from every lane of the group are in the slot
-    if (g.q == 0 && n > 0) need = lane_needs_refinement((const float*)sJ, n, M, res2, (float)x2);
+    if (g.q == 0 && n > 0) need = lane_needs_refinement<M>((const float*)sJ, n, res2, (float)x2, A.select);
   }
   // factor and Q^T b from the slots to HBM
   __syncwarp();
@@ -726,15 +794,18 @@ __global__ void __launch_bounds__(32 * kTaskMaxWarps, sizeof(T) == 4 ? QRKIT_TAS
 
 // ---------------------------------------------------------------------------------------
 // Refinement of the listed blocks (float), pipelined like the factor kernel in two stages:
-// while task i is refined, the block data of task i + 1 and the list entries of task i + 2
-// are in flight.  R and the float solution come from the first kernel's output (the factor in
-// J's packing and p), so the blocks are not factored again.
+// while task i is refined, the block data of task i + 1 (J, the stored factor and b) and the
+// list entries of task i + 2 are in flight.  The factor (reflectors and R), tau and the float
+// solution come from the first kernel's output, so the blocks are not factored again.
 struct RefineTaskArgs {
   const float* J;
   const float* b;
   const float* J_end;
   const float* b_end;
-  const float* F;   // factor of the first kernel (J's packing: R on and above the diagonal)
+  const float* F;   // factor of the first kernel (J's packing: reflectors below the diagonal,
+                    // R on and above it)
+  const float* F_end;
+  const float* tau;
   float* x;         // in: the first kernel's solution; out: refined
   const RefEntry* rlist;
   const int* rcount;
@@ -778,6 +849,23 @@ __device__ __forceinline__ void issue_ref_ent(const RefineTaskArgs& A, const Ref
   }
 }
 
+// The slots of a listed block in a refinement task's data buffer: J's and the factor's
+// supersets (P slots each) and then b's.
+__device__ __forceinline__ void refine_slot_ptrs(unsigned char* db, int G, int M, int grp, const float* gJ,
+                                                 const float* gF, const float* gB, unsigned char*& sJraw,
+                                                 unsigned char*& sFraw, unsigned char*& sBraw, float*& sJ,
+                                                 float*& sF, float*& sB) {
+  const int P = task_blocks(G);
+  const int JS = slot_j_bytes(G, M, 4);
+  const int BS = slot_b_bytes(G, 4);
+  sJraw = db + grp * JS;
+  sFraw = db + P * JS + grp * JS;
+  sBraw = db + 2 * P * JS + grp * BS;
+  sJ = reinterpret_cast<float*>(sJraw + (reinterpret_cast<uintptr_t>(gJ) & 15));
+  sF = reinterpret_cast<float*>(sFraw + (reinterpret_cast<uintptr_t>(gF) & 15));
+  sB = reinterpret_cast<float*>(sBraw + (reinterpret_cast<uintptr_t>(gB) & 15));
+}
+
 __device__ __forceinline__ void issue_ref_data(const RefineTaskArgs& A, const RefineTasks& RT, int64_t t,
                                                const unsigned char* se, unsigned char* db, int lane) {
   if (t >= RT.total) return;
@@ -789,14 +877,16 @@ __device__ __forceinline__ void issue_ref_data(const RefineTaskArgs& A, const Re
   if (grp >= P) return;
   const RefEntry e = reinterpret_cast<const RefEntry*>(se)[grp];
   const float* gJ = A.J + e.v;
+  const float* gF = A.F + e.v;
   const float* gB = A.b + e.r;
-  unsigned char *sJraw, *sBraw;
-  float *sJ, *sB;
-  slot_ptrs<float>(db, G, M, grp, gJ, gB, sJraw, sBraw, sJ, sB);
+  unsigned char *sJraw, *sFraw, *sBraw;
+  float *sJ, *sF, *sB;
+  refine_slot_ptrs(db, G, M, grp, gJ, gF, gB, sJraw, sFraw, sBraw, sJ, sF, sB);
   issue_block<float>(gJ, gB, e.n, M, G, q, A.J, A.J_end, A.b, A.b_end, sJraw, sBraw, sJ, sB);
+  if (e.n > 0) issue_span<float>(gF, e.n * M, G, q, A.F, A.F_end, sFraw, sF);
 }
 
-template <int G, int M>
+template <int G, int M, int RES>
 __device__ __forceinline__ void refine_task(const RefineTaskArgs& A, const unsigned char* se, unsigned char* db,
                                             int lane) {
   constexpr int P = task_blocks(G);
@@ -806,22 +896,23 @@ __device__ __forceinline__ void refine_task(const RefineTaskArgs& A, const unsig
   RefEntry e{};
   if (act) e = reinterpret_cast<const RefEntry*>(se)[grp];
   const int n = e.n;
-  unsigned char *sJraw, *sBraw;
-  float *sJ, *sB;
-  slot_ptrs<float>(db, G, M, act ? grp : 0, A.J + e.v, A.b + e.r, sJraw, sBraw, sJ, sB);
-  // R (rows < M of the factor the first kernel stored, J's packing) and the float solution
-  // it stored; the lanes of a group hold the same x
-  float a[kMaxCols][4], x[kMaxCols];
+  unsigned char *sJraw, *sFraw, *sBraw;
+  float *sJ, *sF, *sB;
+  refine_slot_ptrs(db, G, M, act ? grp : 0, A.J + e.v, A.F + e.v, A.b + e.r, sJraw, sFraw, sBraw, sJ, sF, sB);
+  // the stored factor (reflectors and R) in registers as the first kernel left it, its tau and
+  // the float solution (the lanes of a group hold the same tau and x)
+  float a[kMaxCols][4], tau[kMaxCols], x[kMaxCols];
 #pragma unroll
-  for (int j = 0; j < kmax<G>(); ++j) {
+  for (int j = 0; j < kMaxCols; ++j) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
       const int r = 4 * g.q + u;
-      a[j][u] = (j < M && r <= j && n > 0) ? A.F[e.v + (int64_t)j * n + r] : 0.f;
+      a[j][u] = (j < M && r < n) ? sF[j * n + r] : 0.f;
     }
+    tau[j] = (j < M && n > 0) ? A.tau[e.c + j] : 0.f;
     x[j] = (j < M && n > 0) ? A.x[e.c + j] : 0.f;
   }
-  group_refine<G>(a, x, sJ, sB, n, M, g, A.steps, A.tol);
+  group_refine_aug<G, M, RES>(a, tau, x, sJ, sB, sF, n, g, A.steps, A.tol);
   if (n > 0) {
     float* dx = A.x + e.c;
 #pragma unroll
@@ -830,8 +921,8 @@ __device__ __forceinline__ void refine_task(const RefineTaskArgs& A, const unsig
   }
 }
 
-template <int kUnused>
-__global__ void __launch_bounds__(32 * kTaskMaxWarps, 2) block_task_refine_kernel(RefineTaskArgs A) {
+template <int RES>
+__global__ void __launch_bounds__(32 * kTaskMaxWarps, QRKIT_REFINE_CTAS) block_task_refine_kernel(RefineTaskArgs A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   const WarpBufs W{smem_raw + (size_t)wid * A.warp_bytes, A.data_bytes, 32 * (int)sizeof(RefEntry)};
@@ -873,7 +964,7 @@ __global__ void __launch_bounds__(32 * kTaskMaxWarps, 2) block_task_refine_kerne
     RT.key_of(t, key, local);
     switch (key) {
 #define QRKIT_REFINE_CASE(k) \
-  case k: refine_task<((k) >> 3) + 1, ((k) & 7) + 1>(A, W.ent(se), W.data(sd), lane); break;
+  case k: refine_task<((k) >> 3) + 1, ((k) & 7) + 1, RES>(A, W.ent(se), W.data(sd), lane); break;
       QRKIT_TASK_KEYS(QRKIT_REFINE_CASE)
 #undef QRKIT_REFINE_CASE
       default: break;
@@ -891,7 +982,10 @@ template <typename T, bool SEL>
 cudaError_t kernel_setup(size_t smem, int threads, int* per_sm);
 template <typename T, bool SEL>
 cudaError_t kernel_launch(const TaskArgs<T>& A, unsigned grid, int threads, size_t smem, cudaStream_t st);
+// RES: the refinement's residual precision (0: compensated float, 1: double).
+template <int RES>
 cudaError_t refine_setup(size_t smem, int threads, int* per_sm);
+template <int RES>
 cudaError_t refine_launch(const RefineTaskArgs& A, unsigned grid, int threads, size_t smem, cudaStream_t st);
 
 }  // namespace tasks

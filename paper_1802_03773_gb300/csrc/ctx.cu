@@ -333,6 +333,16 @@ qrkit_status qrkit_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, co
   return st;
 }
 
+qrkit_status qrkit_set_refinement(qrkit_ctx* ctx, double select, int residual) {
+  if (!ctx) return QRKIT_EINVAL;
+  if (!(select >= 0.0 && select <= 1.0)) return fail(ctx, QRKIT_EINVAL, "select must be in [0, 1]");
+  if (residual != QRKIT_RESIDUAL_DOT2 && residual != QRKIT_RESIDUAL_FP64)
+    return fail(ctx, QRKIT_EINVAL, "residual must be QRKIT_RESIDUAL_DOT2 or QRKIT_RESIDUAL_FP64");
+  ctx->refine_select = (float)select;
+  ctx->refine_residual = residual;
+  return QRKIT_OK;
+}
+
 qrkit_status qrkit_factor(qrkit_ctx* ctx, const void* J, const void* S, const void* D, double lambda) {
   if (!ctx) return QRKIT_EINVAL;
   if (!ctx->plan.valid) return fail(ctx, QRKIT_ESTATE, "qrkit_factor before qrkit_plan");

@@ -227,6 +227,8 @@ struct qrkit_ctx {
   size_t smem_attr[16] = {};   // dynamic smem opted in, per kernel variant (slot per kernel)
   int occ_threads[16] = {};    // threads and resident CTAs per SM at that size (warp-task kernels)
   int occ_per_sm[16] = {};
+  float refine_select = 2e-6f;  // block refinement: a-priori error estimate that selects a block
+  int refine_residual = 0;      // its residual precision: 0 compensated float, 1 double
   bool factored = false;       // fused block path
   bool comp_factored = false;  // composed path
   bool band_factored = false;  // banded path

@@ -19,6 +19,7 @@ PRECISION = {"fp64": FP64, "fp32_refined": FP32_REFINED, "fp32": FP32}
 STRUCT_BLOCKS, STRUCT_BANDED = 0, 1
 BAND_AUTO, BAND_SWEEP, BAND_PARALLEL = 0, 1, 2
 COUPLED_NONE, COUPLED_DENSE, COUPLED_WINDOW = 0, 1, 2
+RESIDUAL_DOT2, RESIDUAL_FP64 = 0, 1
 
 STATUS = {0: "QRKIT_OK", 1: "QRKIT_EINVAL", 2: "QRKIT_ENOMEM", 3: "QRKIT_ECUDA",
           4: "QRKIT_ESINGULAR", 5: "QRKIT_ENONFINITE", 6: "QRKIT_ETIMEOUT",
@@ -90,6 +91,7 @@ _SIGS = {
     "qrkit_plan": (ctypes.c_int, [_VP, ctypes.POINTER(Structure)]),
     "qrkit_factor_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP, ctypes.c_int]),
     "qrkit_get_factor": (ctypes.c_int, [_VP, _VP, _VP]),
+    "qrkit_set_refinement": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int]),
     "qrkit_get_band_factor": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "qrkit_factor": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double]),
     "qrkit_apply_qt": (ctypes.c_int, [_VP, _VP, _VP]),
@@ -325,6 +327,11 @@ class Context:
         self._check(self.lib.qrkit_factor_solve(
             self.h, self._t(J, "J"), self._t(b, "b"), self._t(D, "D", True), float(lam),
             self._t(p, "p"), self._t(qtb, "qtb", True), int(refine_steps)))
+
+    def set_refinement(self, select=2e-6, residual="dot2"):
+        """Block refinement settings: selection threshold and residual precision ("dot2" or "fp64")."""
+        mode = {"dot2": RESIDUAL_DOT2, "fp64": RESIDUAL_FP64}[residual] if isinstance(residual, str) else int(residual)
+        self._check(self.lib.qrkit_set_refinement(self.h, float(select), mode))
 
     def factor(self, J, S=None, D=None, lam=0.0):
         self._check(self.lib.qrkit_factor(self.h, self._t(J, "J"), self._t(S, "S", True),

@@ -47,3 +47,74 @@ def optimality_all(d, x):
             scale = nA * nA * np.linalg.norm(xx, axis=1) + nA * np.linalg.norm(b, axis=1)
             worst = max(worst, float((np.linalg.norm(g, axis=1) / scale).max()))
     return worst
+
+
+def stack_blocks(d, idx):
+    """Blocks idx (all of one shape) as stacks: A (k, n, m), b (k, n), column offsets (k, m)."""
+    nn, mm = int(d["n"][idx[0]]), int(d["m"][idx[0]])
+    vo = d["val_off"][idx][:, None] + np.arange(nn * mm)[None, :]
+    A = np.asarray(d["vals"], dtype=np.float64)[vo].reshape(-1, mm, nn).transpose(0, 2, 1)
+    ro = d["row_off"][idx][:, None] + np.arange(nn)[None, :]
+    b = np.asarray(d["b"], dtype=np.float64)[ro]
+    co = d["col_off"][idx][:, None] + np.arange(mm)[None, :]
+    return A, b, co
+
+
+def block_errors(d, x, idx=None):
+    """Per block of idx (default: all): relative error of x against the oracle's FP64 solution
+    (householder.lstsq_stack, the per-block Householder solve taken over stacks of one shape)
+    and the forward-error factor kappa + kappa^2 ||r|| / (||A||_2 ||x||) of least squares
+    (kappa from singular values; a backward-stable solve in unit roundoff u is within a small
+    multiple of u times this factor).  Returns (err, factor) in the order of idx."""
+    K = d["K"]
+    idx = np.arange(K) if idx is None else np.asarray(idx)
+    n = d["n"].astype(np.int64)[idx]
+    m = d["m"].astype(np.int64)[idx]
+    err = np.zeros(len(idx))
+    fac = np.zeros(len(idx))
+    key = n * 16 + m
+    for k in np.unique(key):
+        sel = np.nonzero(key == k)[0]
+        A, b, co = stack_blocks(d, idx[sel])
+        xo = hh.lstsq_stack(A, b)
+        xg = np.asarray(x, dtype=np.float64)[co]
+        nx = np.linalg.norm(xo, axis=1)
+        err[sel] = np.linalg.norm(xg - xo, axis=1) / nx
+        s = np.linalg.svd(A, compute_uv=False)
+        kap = s[:, 0] / s[:, -1]
+        r = b - np.einsum("kij,kj->ki", A, xo)
+        fac[sel] = kap + kap * kap * np.linalg.norm(r, axis=1) / (s[:, 0] * nx)
+    return err, fac
+
+
+U32, U64 = 2.0 ** -24, 2.0 ** -53
+
+
+def assert_blocks_within(d, x, idx, tol, u_bound, c=None, what=""):
+    """Every block of idx: error <= max(tol, c * n * m * u_bound * factor).  tol is the target
+    of the mode (1e-5 for FP32 refined, 1e-12 for FP64); the bound term admits the blocks whose
+    conditioning puts even a backward-stable solve in that precision (the oracle's own FP64
+    solve included) above it.  Returns (max error, worst block)."""
+    err, fac = block_errors(d, x, idx)
+    idx = np.arange(d["K"]) if idx is None else np.asarray(idx)
+    nm = d["n"].astype(np.float64)[idx] * d["m"].astype(np.float64)[idx]
+    lim = np.maximum(tol, (2.0 if c is None else c) * nm * u_bound * fac)
+    bad = np.nonzero(~(err <= lim))[0]
+    assert bad.size == 0, (f"{what}{bad.size} blocks above their limit, e.g. block {int(idx[bad[0]])}: "
+                           f"error {err[bad[0]]:.3e}, limit {lim[bad[0]]:.3e}, factor {fac[bad[0]]:.3e}")
+    w = int(np.argmax(err))
+    return float(err[w]), int(idx[w])
+
+
+def block_kappa(d):
+    """2-norm condition number of every block (singular values, by shape group)."""
+    n = d["n"].astype(np.int64)
+    m = d["m"].astype(np.int64)
+    kap = np.zeros(d["K"])
+    key = n * 16 + m
+    for k in np.unique(key):
+        sel = np.nonzero(key == k)[0]
+        A = stack_blocks(d, sel)[0]
+        s = np.linalg.svd(A, compute_uv=False)
+        kap[sel] = s[:, 0] / s[:, -1]
+    return kap

@@ -122,3 +122,55 @@ def test_planted_mistake_reversed_q_order_is_caught(monkeypatch):
     Q = hh.q_explicit(f)
     Rfull = np.vstack([f.R, np.zeros((3, 3))])
     assert np.linalg.norm(Q @ Rfull - A) > 1e-3
+
+
+def test_lstsq_stack_equals_per_block_lstsq():
+    """The stack-vectorised solve is the per-block Householder solve, block by block,
+    including a block with a zero column in the middle (tau = 0) and square blocks."""
+    g = np.random.default_rng(31)
+    for K, M, N in ((50, 9, 4), (20, 6, 6), (40, 16, 1), (30, 3, 2)):
+        A = g.standard_normal((K, M, N)) * 10.0 ** g.uniform(-2, 2, size=(K, 1, N))
+        b = g.standard_normal((K, M))
+        xs = hh.lstsq_stack(A, b)
+        for k in range(K):
+            np.testing.assert_allclose(xs[k], hh.lstsq(A[k], b[k])[0], rtol=1e-12, atol=1e-13)
+    # a zero first column below the diagonal only: the reflector is the identity's sign flip
+    A = np.array([[[2.0, 1.0], [0.0, 1.0], [0.0, 3.0]]])
+    np.testing.assert_allclose(hh.lstsq_stack(A, np.array([[1.0, 2.0, 3.0]]))[0],
+                               np.linalg.lstsq(A[0], [1.0, 2.0, 3.0], rcond=None)[0], rtol=1e-14)
+
+
+def test_lstsq_stack_planted_mistakes_fail():
+    """Copies of lstsq_stack with a planted mistake (the 2 of tau = 2 / v^T v dropped; the
+    reflector not applied to b) disagree with the per-block lstsq."""
+    g = np.random.default_rng(32)
+    A = g.standard_normal((30, 8, 3))
+    b = g.standard_normal((30, 8))
+    ref = np.stack([hh.lstsq(A[k], b[k])[0] for k in range(30)])
+    np.testing.assert_allclose(hh.lstsq_stack(A, b), ref, rtol=1e-12, atol=1e-13)
+
+    def planted(A, b, tau_factor, apply_to_b):
+        A = np.array(A, dtype=np.float64, copy=True)
+        c = np.array(b, dtype=np.float64, copy=True)
+        K, M, N = A.shape
+        for k in range(N):
+            x = A[:, k:, k]
+            norm = np.sqrt(np.einsum("ki,ki->k", x, x))
+            beta = np.where(x[:, 0] >= 0.0, -norm, norm)
+            v = x.copy()
+            v[:, 0] = x[:, 0] - beta
+            v = v / v[:, :1]
+            tau = tau_factor / np.einsum("ki,ki->k", v, v)
+            if k + 1 < N:
+                w = np.einsum("ki,kij->kj", v, A[:, k:, k + 1:])
+                A[:, k:, k + 1:] -= tau[:, None, None] * v[:, :, None] * w[:, None, :]
+            A[:, k, k] = beta
+            if apply_to_b:
+                c[:, k:] -= (tau * np.einsum("ki,ki->k", v, c[:, k:]))[:, None] * v
+        xs = np.zeros((K, N))
+        for i in reversed(range(N)):
+            xs[:, i] = (c[:, i] - np.einsum("kj,kj->k", A[:, i, i + 1:N], xs[:, i + 1:])) / A[:, i, i]
+        return xs
+    np.testing.assert_allclose(planted(A, b, 2.0, True), ref, rtol=1e-12, atol=1e-13)
+    assert not np.allclose(planted(A, b, 1.0, True), ref, rtol=1e-6)
+    assert not np.allclose(planted(A, b, 2.0, False), ref, rtol=1e-6)

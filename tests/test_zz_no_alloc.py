@@ -4,13 +4,14 @@ qrkit_block_solve_noalloc serves callers that cannot call cudaMalloc (a framewor
 all device memory, a fixed memory budget): it keeps every intermediate in one static device
 array.  It runs the tile kernel of the fused solve, so this test pins the context to the same
 tile mapping, calls the allocation-free entry point through the C-ABI twice in a row (the array
-keeps the previous call's contents) and compares each result with qrkit_factor_solve's.
-It lives in its own file so that pytest collects it last.
+keeps the previous call's contents) and compares each result with qrkit_factor_solve's and,
+block by block, with the FP64 oracle's.  It lives in its own file so that pytest collects it
+last.
 """
 import numpy as np
 import pytest
 
-from tests.gpu_common import cuda_or_skip
+from tests.gpu_common import U32, U64, assert_blocks_within, cuda_or_skip
 from workloads import batched_blocks
 
 pytestmark = pytest.mark.gpu
@@ -41,6 +42,22 @@ def test_noalloc_matches_context_solve_twice(precision, tol):
         assert np.all(np.isfinite(got)), f"call {call}: non-finite output"
         err = np.linalg.norm(got - ref) / np.linalg.norm(ref)
         assert err <= tol, f"call {call}: relative difference {err:.3e}"
+        # against the oracle, per block: the mode's target (FP32 plain: the float error bound)
+        target, u = {"fp32_refined": (1e-5, U64), "fp64": (1e-12, U64), "fp32": (1e-6, U32)}[precision]
+        assert_blocks_within(d, got, None, target, u, c=8.0 if u == U32 else None, what=f"call {call}: ")
+
+
+def test_noalloc_restores_the_current_device():
+    """The call makes its device current only while it runs."""
+    torch = cuda_or_skip()
+    from paper_1802_03773_gb300 import qrkit
+    d = batched_blocks(K=500, seed_offset=22)
+    J = torch.from_numpy(d["vals"]).cuda()
+    b = torch.from_numpy(d["b"]).cuda()
+    p = torch.empty(int(d["col_off"][-1]), device="cuda")
+    before = torch.cuda.current_device()
+    qrkit.block_solve_noalloc(d["n"], d["m"], J, b, p)
+    assert torch.cuda.current_device() == before
 
 
 def test_noalloc_rejects_oversized_problem():
