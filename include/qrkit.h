@@ -264,9 +264,10 @@ qrkit_status qrkit_block_solve_noalloc(int device, void* stream, int precision,
 qrkit_status qrkit_get_band_factor(qrkit_ctx* ctx, void* Rw, void* c, double* res2);
 
 /* Copy the stored factor of a block structure (Sec. 4.1; reflectors as in Sec. 2) to caller
- * buffers (device pointers, either
- * may be NULL): factor values in J's packing (V strictly below the diagonal, R on and above)
- * and tau (sum m_i). */
+ * buffers (device pointers, either may be NULL): factor values in J's packing (V strictly below
+ * the diagonal, R on and above) and tau (sum m_i).  The warp-task solve keeps its factor in a
+ * task-ordered layout of its own (whole 16-byte row quads, so that it is written in full
+ * sectors); this call rearranges it with one kernel.  Asynchronous. */
 qrkit_status qrkit_get_factor(qrkit_ctx* ctx, void* factor_out, void* tau_out);
 
 /* Replace the window starts (Sec. 4.2 windows, re-sorted by the P_r of Sec. 4.3) of a

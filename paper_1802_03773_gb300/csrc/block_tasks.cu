@@ -27,17 +27,6 @@ int warp_slot_bytes(const Plan& P, int es) {
   return (best + 127) / 128 * 128;
 }
 
-// One data buffer of a refinement warp: J's and the factor's supersets and b's.
-int warp_refine_slot_bytes(const Plan& P) {
-  int best = 0;
-  for (int k = 0; k < kTaskKeys; ++k) {
-    if (P.key_off[k + 1] == P.key_off[k]) continue;
-    const int G = group_lanes(k), M = (k & 7) + 1;
-    best = std::max(best, task_blocks(G) * (2 * slot_j_bytes(G, M, 4) + slot_b_bytes(G, 4)));
-  }
-  return (best + 127) / 128 * 128;
-}
-
 // Resident CTAs per SM of a kernel at this shared-memory size; the kernel's shared-memory
 // limit is raised and its occupancy queried once per (kernel, size) and cached.
 template <typename F>
@@ -70,11 +59,10 @@ qrkit_status launch_tasks_typed(qrkit_ctx* ctx, const void* J, const void* b, vo
   A.b = (const T*)b;
   A.J_end = A.J + P.values;
   A.b_end = A.b + P.rows;
-  A.F = (T*)ctx->ws.factor.ptr;
-  A.tau = (T*)ctx->ws.tau.ptr;
+  A.tF = (T*)ctx->ws.tfactor.ptr;
+  A.tTau = (T*)ctx->ws.ttau.ptr;
   A.qtb = (T*)qtb;
   A.x = (T*)p;
-  A.f_vec = ((reinterpret_cast<uintptr_t>(A.F) ^ reinterpret_cast<uintptr_t>(J)) & 15) == 0;
   A.q_vec = qtb && ((reinterpret_cast<uintptr_t>(qtb) ^ reinterpret_cast<uintptr_t>(b)) & 15) == 0;
   A.data_bytes = warp_slot_bytes(P, es);
   A.warp_bytes = (warp_desc_bytes((int)sizeof(TaskEntry)) + 2 * A.data_bytes + 127) / 128 * 128;
@@ -83,11 +71,17 @@ qrkit_status launch_tasks_typed(qrkit_ctx* ctx, const void* J, const void* b, vo
   A.rlist = nullptr;
   A.rcount = nullptr;
   A.key_off = (const int64_t*)P.d_key_off.ptr;
+  A.rec = nullptr;
+  A.rec_off = (const int64_t*)P.d_rec_off.ptr;
   qrkit_status st;
   if (SEL) {
     if ((st = ensure(ctx, ctx->ws.tlist, (size_t)std::max<int64_t>(P.K, 1) * sizeof(RefEntry), "refinement lists")) !=
         QRKIT_OK)
       return st;
+    if ((st = ensure(ctx, ctx->ws.rrec, (size_t)std::max<int64_t>(P.rec_off[kTaskKeys], 1) * sizeof(float),
+                     "refinement records")) != QRKIT_OK)
+      return st;
+    A.rec = (float*)ctx->ws.rrec.ptr;
     if ((st = ensure(ctx, ctx->ws.tcount, kTaskKeys * sizeof(int), "refinement counts")) != QRKIT_OK) return st;
     QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->ws.tcount.ptr, 0, kTaskKeys * sizeof(int), ctx->stream));
     A.rlist = (RefEntry*)ctx->ws.tlist.ptr;
@@ -104,34 +98,28 @@ qrkit_status launch_tasks_typed(qrkit_ctx* ctx, const void* J, const void* b, vo
   ctx->launches += 1;
   if constexpr (SEL && sizeof(T) == sizeof(float)) {
     RefineTaskArgs R;
-    R.J = (const float*)J;
-    R.b = (const float*)b;
-    R.J_end = R.J + P.values;
-    R.b_end = R.b + P.rows;
-    R.F = (const float*)A.F;
-    R.F_end = R.F + P.values;
-    R.tau = (const float*)A.tau;
+    R.tF = (const float*)A.tF;
+    R.tTau = (const float*)A.tTau;
+    R.rec = A.rec;
+    R.rec_off = A.rec_off;
     R.x = (float*)p;
     R.rlist = A.rlist;
     R.rcount = A.rcount;
     R.key_off = A.key_off;
     R.steps = refine_steps;
     R.tol = 1e-6f;
-    R.data_bytes = warp_refine_slot_bytes(P);
-    R.warp_bytes = (warp_desc_bytes((int)sizeof(RefEntry)) + 2 * R.data_bytes + 127) / 128 * 128;
-    const int wpc2 = kRefineWarps, threads2 = 32 * kRefineWarps;
-    const size_t smem2 = (size_t)wpc2 * R.warp_bytes;
     R.status = A.status;
+    const int threads2 = 32 * kRefineWarps;
     const bool res64 = ctx->refine_residual != 0;
     int per_sm2 = 0;
-    if ((st = resident(ctx, res64 ? refine_setup<1> : refine_setup<0>, threads2, smem2, res64 ? 12 : 11, per_sm2)) !=
+    if ((st = resident(ctx, res64 ? refine_setup<1> : refine_setup<0>, threads2, 0, res64 ? 12 : 11, per_sm2)) !=
         QRKIT_OK)
       return st;
-    const int64_t want2 = (P.max_refine_tasks + wpc2 - 1) / wpc2;
+    const int64_t want2 = (P.max_refine_tasks + kRefineWarps - 1) / kRefineWarps;
     const int64_t full2 = (int64_t)ctx->num_sms * per_sm2;
     const unsigned grid2 = (unsigned)std::max<int64_t>(1, std::min(want2, full2));
-    QRKIT_CUDA_TRY(ctx, res64 ? refine_launch<1>(R, grid2, threads2, smem2, ctx->stream)
-                              : refine_launch<0>(R, grid2, threads2, smem2, ctx->stream));
+    QRKIT_CUDA_TRY(ctx, res64 ? refine_launch<1>(R, grid2, threads2, 0, ctx->stream)
+                              : refine_launch<0>(R, grid2, threads2, 0, ctx->stream));
     ctx->launches += 1;
   }
   return QRKIT_OK;
@@ -146,6 +134,9 @@ void release_block_tasks(Plan& P) {
   release(P.d_task_hdr);
   release(P.d_task_ent);
   release(P.d_key_off);
+  release(P.d_rec_off);
+  P.factor_planes = 0;
+  P.rec_off.clear();
   P.num_tasks = 0;
   P.max_refine_tasks = 0;
   P.key_off.clear();
@@ -161,7 +152,7 @@ namespace tasks {
 qrkit_status make_task_lists(int64_t K, const uint8_t* n, const uint8_t* m, const int64_t* val_off,
                              const int64_t* row_off, const int64_t* col_off, int64_t supertile,
                              bool key_major, std::vector<TaskHdr>& hdr, std::vector<TaskEntry>& ent,
-                             std::vector<int64_t>& key_count, std::string& err) {
+                             std::vector<int64_t>& key_count, int64_t& planes, std::string& err) {
   if (supertile < 32 || supertile > 65536) {
     err = "supertile must be in [32, 65536]";
     return QRKIT_EINVAL;
@@ -177,6 +168,7 @@ qrkit_status make_task_lists(int64_t K, const uint8_t* n, const uint8_t* m, cons
   key_count.assign(kTaskKeys, 0);
   std::vector<int64_t> cnt(kTaskKeys), pos(kTaskKeys);
   std::vector<int32_t> order;
+  planes = 0;
   auto key_of = [&](int64_t i) { return ((n[i] - 1) >> 2) * 8 + (m[i] - 1); };
   for (int64_t s0 = 0; s0 < K; s0 += supertile) {
     const int64_t s1 = std::min(K, s0 + supertile);
@@ -200,6 +192,12 @@ qrkit_status make_task_lists(int64_t K, const uint8_t* n, const uint8_t* m, cons
         h.b0 = s0;
         h.first = (int64_t)ent.size();
         h.key = k;
+        if (planes > (int64_t)INT32_MAX - kMaxCols) {
+          err = "the factor needs more than 2^31 planes";
+          return QRKIT_EUNSUPPORTED;
+        }
+        h.plane = (int32_t)planes;
+        planes += (k & 7) + 1;
         hdr.push_back(h);
         for (int l = 0; l < per; ++l) {
           TaskEntry e{};
@@ -233,16 +231,20 @@ qrkit_status build_block_tasks(qrkit_ctx* ctx, int64_t supertile, int warps, boo
   std::vector<TaskEntry> ent;
   std::vector<int64_t> key_count;
   std::string err;
+  int64_t planes = 0;
   qrkit_status st = make_task_lists(P.K, P.n.data(), P.m.data(), P.val_off.data(), P.row_off.data(),
-                                    P.col_off.data(), supertile, key_major, hdr, ent, key_count, err);
+                                    P.col_off.data(), supertile, key_major, hdr, ent, key_count, planes, err);
   if (st != QRKIT_OK) return fail(ctx, st, err);
   P.key_off.assign(kTaskKeys + 1, 0);
+  P.rec_off.assign(kTaskKeys + 1, 0);
   P.max_refine_tasks = 0;
   for (int k = 0; k < kTaskKeys; ++k) {
     P.key_off[k + 1] = P.key_off[k] + key_count[k];
+    P.rec_off[k + 1] = P.rec_off[k] + key_count[k] * record_values(group_lanes(k), (k & 7) + 1);
     const int per = task_blocks(group_lanes(k));
     P.max_refine_tasks += (key_count[k] + per - 1) / per;
   }
+  P.factor_planes = planes;
   auto up = [&](DevBuf& d, const void* src, size_t bytes, const char* what) -> qrkit_status {
     qrkit_status r = ensure(ctx, d, bytes, what);
     if (r != QRKIT_OK) return r;
@@ -253,10 +255,39 @@ qrkit_status build_block_tasks(qrkit_ctx* ctx, int64_t supertile, int warps, boo
   if ((st = up(P.d_task_ent, ent.data(), ent.size() * sizeof(TaskEntry), "task entries")) != QRKIT_OK) return st;
   if ((st = up(P.d_key_off, P.key_off.data(), P.key_off.size() * sizeof(int64_t), "task key offsets")) != QRKIT_OK)
     return st;
+  if ((st = up(P.d_rec_off, P.rec_off.data(), P.rec_off.size() * sizeof(int64_t), "record offsets")) != QRKIT_OK)
+    return st;
+  const size_t es = elem_size(ctx);
+  if ((st = ensure(ctx, ctx->ws.tfactor, (size_t)std::max<int64_t>(planes, 1) * kPlaneValues * es, "factor planes")) !=
+      QRKIT_OK)
+    return st;
+  if ((st = ensure(ctx, ctx->ws.ttau, (size_t)std::max<int64_t>(planes, 1) * kTauPlane * es, "tau planes")) !=
+      QRKIT_OK)
+    return st;
   P.num_tasks = (int64_t)hdr.size();
   P.supertile = supertile;
   P.task_warps = warps;
   P.key_major = key_major;
+  return QRKIT_OK;
+}
+
+qrkit_status unpack_block_tasks_factor(qrkit_ctx* ctx, void* factor_out, void* tau_out) {
+  const Plan& P = ctx->plan;
+  if (P.num_tasks < 1) return fail(ctx, QRKIT_ESTATE, "the plan has no warp tasks");
+  const int threads = 256;
+  const int64_t blocks = std::min<int64_t>((P.num_tasks + 7) / 8, (int64_t)ctx->num_sms * 8);
+  const TaskHdr* hdr = (const TaskHdr*)P.d_task_hdr.ptr;
+  const TaskEntry* ent = (const TaskEntry*)P.d_task_ent.ptr;
+  if (ctx->precision == QRKIT_FP64)
+    unpack_factor_kernel<double><<<(unsigned)blocks, threads, 0, ctx->stream>>>(
+        hdr, ent, P.num_tasks, (const double*)ctx->ws.tfactor.ptr, (const double*)ctx->ws.ttau.ptr,
+        (double*)factor_out, (double*)tau_out);
+  else
+    unpack_factor_kernel<float><<<(unsigned)blocks, threads, 0, ctx->stream>>>(
+        hdr, ent, P.num_tasks, (const float*)ctx->ws.tfactor.ptr, (const float*)ctx->ws.ttau.ptr,
+        (float*)factor_out, (float*)tau_out);
+  QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+  ctx->launches += 1;
   return QRKIT_OK;
 }
 
@@ -292,8 +323,9 @@ extern "C" qrkit_status qrkit_task_layout(int64_t num_blocks, const uint8_t* blo
   std::vector<TaskEntry> ent;
   std::vector<int64_t> key_count;
   std::string err;
+  int64_t planes = 0;
   const qrkit_status st = make_task_lists(num_blocks, block_rows, block_cols, val_off.data(), row_off.data(),
-                                          col_off.data(), supertile, key_major != 0, hdr, ent, key_count, err);
+                                          col_off.data(), supertile, key_major != 0, hdr, ent, key_count, planes, err);
   if (st != QRKIT_OK) return st;
   *num_tasks = (int64_t)hdr.size();
   if (!task_key && !task_slots) return QRKIT_OK;

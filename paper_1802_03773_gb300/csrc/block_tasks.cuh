@@ -183,10 +183,10 @@ __device__ __forceinline__ void store_regs(const T (&a)[kMaxCols][4], const T (&
 
 // Householder QR of the group's block (Sec. 2) in registers, applied to the rhs on the way:
 // afterwards a holds R on and above the diagonal and the reflectors' v below it (v[0] = 1
-// implicit), c = Q^T b; the reflector coefficients go to tau[0..M) as they are formed
-// (lanes q = k mod G store tau[k]; tau may be null).  M (warp-uniform) columns.
+// implicit), c = Q^T b; the reflector coefficients go to tau[k * ts], k < M, as they are formed
+// (lanes q = k mod G store tau_k; tau may be null).  M (warp-uniform) columns.
 template <typename T, int G>
-__device__ __forceinline__ void group_householder(T (&a)[kMaxCols][4], T (&c)[4], T* tau, int M,
+__device__ __forceinline__ void group_householder(T (&a)[kMaxCols][4], T (&c)[4], T* tau, int ts, int M,
                                                   const Group<G>& g) {
   const int q = g.q;
 #pragma unroll
@@ -226,7 +226,7 @@ __device__ __forceinline__ void group_householder(T (&a)[kMaxCols][4], T (&c)[4]
           a[k][u] = gt ? v[u] : a[k][u];
         }
       }
-      if (tau && (k % G) == q) tau[k] = tk;
+      if (tau && (k % G) == q) tau[k * ts] = tk;
 #pragma unroll
       for (int j = k + 1; j < kmax<G>(); ++j) {
         if (j < M) {
@@ -278,20 +278,17 @@ __device__ __forceinline__ bool group_backsub(const T (&a)[kMaxCols][4], const T
 // below that expression: est = u (||R||_F ||R^{-1}||_F + ||R||_F ||R^{-1}||_F^2 ||r|| / ||x||)
 // with u = 2^-24 and ||r|| = || rows M.. of Q^T b ||.  R^{-1} is formed column by column (the
 // columns are independent back-substitutions).  True when the estimate exceeds `target` (or
-// is NaN: a zero pivot, x = 0).  One lane per block, R read from the factor in its slot
-// (column k at F + k n); res2 = ||r||^2, x2 = ||x||^2.
+// is NaN: a zero pivot, x = 0).  R: the upper triangle (R[i][k], i <= k); res2 = ||r||^2,
+// x2 = ||x||^2; kappa receives ||R||_F ||R^{-1}||_F.
 template <int M>
-__device__ __forceinline__ bool lane_needs_refinement(const float* F, int n, float res2, float x2, float target) {
-  float R[M][M], d[M];
+__device__ __forceinline__ bool needs_refinement(const float (&R)[M][M], float res2, float x2, float target,
+                                                 float& kappa) {
+  float d[M];
   float rF2 = 0.f;
 #pragma unroll
   for (int k = 0; k < M; ++k) {
-    const float* col = F + k * n;
 #pragma unroll
-    for (int i = 0; i <= k; ++i) {
-      R[i][k] = col[i];
-      rF2 += R[i][k] * R[i][k];
-    }
+    for (int i = 0; i <= k; ++i) rF2 += R[i][k] * R[i][k];
     d[k] = rcp(R[k][k]);
   }
   float iF2 = 0.f;
@@ -310,32 +307,38 @@ __device__ __forceinline__ bool lane_needs_refinement(const float* F, int n, flo
     }
   }
   const float kF = sqrtf(rF2 * iF2);
+  kappa = kF;
   const float est = kUnitRoundoff * (kF + kF * sqrtf(iF2) * sqrtf(res2 / x2));
   return !(est <= target);
+}
+
+// The upper triangle of the group's R (row i lives on lane i / 4) on every lane of the group.
+template <typename T, int G, int M>
+__device__ __forceinline__ void group_gather_r(const T (&a)[kMaxCols][4], const Group<G>& g, float (&R)[M][M]) {
+#pragma unroll
+  for (int k = 0; k < M; ++k)
+#pragma unroll
+    for (int i = 0; i < M; ++i) R[i][k] = i <= k ? (float)g.bcast(a[k][i & 3], i >> 2) : 0.f;
 }
 
 // The refinement's two residuals of the augmented system [I J; J^T 0] [r; x] = [b; 0] in
 // extended precision, rounded once to float: f = b - r - J x on the lane's rows and
 // g = -J^T r (replicated over the group).  RES = 0: compensated float arithmetic (Dot2 of
 // Ogita, Rump and Oishi: error-free products and sums, value = s + c); RES = 1: double.
+// jr, bl: the lane's rows of J and b (zero past n).
 template <int G, int M, int RES>
-__device__ __forceinline__ void group_aug_residuals(const float* sJ, const float* sB, int n, const float (&x)[kMaxCols],
-                                                    const float (&r)[4], const Group<G>& g, float (&f)[4],
-                                                    float (&gv)[kMaxCols]) {
-  const int q = g.q;
+__device__ __forceinline__ void group_aug_residuals(const float (&jr)[M][4], const float (&bl)[4],
+                                                    const float (&x)[kMaxCols], const float (&r)[4], const Group<G>& g,
+                                                    float (&f)[4], float (&gv)[kMaxCols]) {
   if constexpr (RES == 0) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int row = 4 * q + u;
-      float sh = row < n ? sB[row] : 0.f, sl = 0.f, t, e;
-      two_sum(sh, -r[u], t, e);
-      sh = t;
-      sl = e;
+      float sh, sl, t, e;
+      two_sum(bl[u], -r[u], sh, sl);
 #pragma unroll
       for (int j = 0; j < M; ++j) {
-        const float aj = row < n ? sJ[j * n + row] : 0.f;
-        const float p = __fmul_rn(aj, -x[j]);
-        const float pe = __fmaf_rn(aj, -x[j], -p);
+        const float p = __fmul_rn(jr[j][u], -x[j]);
+        const float pe = __fmaf_rn(jr[j][u], -x[j], -p);
         two_sum(sh, p, t, e);
         sh = t;
         sl = __fadd_rn(sl, __fadd_rn(e, pe));
@@ -349,10 +352,8 @@ __device__ __forceinline__ void group_aug_residuals(const float* sJ, const float
       float sh = 0.f, sl = 0.f;
 #pragma unroll
       for (int u = 0; u < 4; ++u) {
-        const int row = 4 * q + u;
-        const float aj = row < n ? sJ[j * n + row] : 0.f;
-        const float p = __fmul_rn(aj, r[u]);
-        const float pe = __fmaf_rn(aj, r[u], -p);
+        const float p = __fmul_rn(jr[j][u], r[u]);
+        const float pe = __fmaf_rn(jr[j][u], r[u], -p);
         float t, e;
         two_sum(sh, p, t, e);
         sh = t;
@@ -364,14 +365,9 @@ __device__ __forceinline__ void group_aug_residuals(const float* sJ, const float
   } else {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
-      const int row = 4 * q + u;
-      double acc = row < n ? (double)sB[row] : 0.0;
-      acc -= (double)r[u];
+      double acc = (double)bl[u] - (double)r[u];
 #pragma unroll
-      for (int j = 0; j < M; ++j) {
-        const double aj = row < n ? (double)sJ[j * n + row] : 0.0;
-        acc = fma(-aj, (double)x[j], acc);
-      }
+      for (int j = 0; j < M; ++j) acc = fma(-(double)jr[j][u], (double)x[j], acc);
       f[u] = (float)acc;
     }
 #pragma unroll
@@ -380,11 +376,7 @@ __device__ __forceinline__ void group_aug_residuals(const float* sJ, const float
     for (int j = 0; j < M; ++j) {
       double acc = 0.0;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
-        const int row = 4 * q + u;
-        const double aj = row < n ? (double)sJ[j * n + row] : 0.0;
-        acc = fma(aj, (double)r[u], acc);
-      }
+      for (int u = 0; u < 4; ++u) acc = fma((double)jr[j][u], (double)r[u], acc);
       gv[j] = (float)(-g.sum(acc));
     }
   }
@@ -400,13 +392,17 @@ __device__ __forceinline__ void group_aug_residuals(const float* sJ, const float
 // f = b - r - J x, g = -J^T r; h = R^{-T} g; d1 = Q_1^T f; t = d1 - h; dx = R^{-1} t;
 // dr = Q [h; d2] = f - Q_1 t (d2 = Q_2^T f, so Q_2 d2 = f - Q_1 d1); x += dx, r += dr.  Its rate
 // is about u kappa(J) (not u kappa^2 as for the seminormal equations), so it converges on
-// every block with u kappa < 1.  A block stops once its correction is at most tol relative to
-// x (max norms), after at most `steps` steps.  x is replicated over the group; sR is the
-// factor in its slot (column k at sR + k n).
+// every block with u kappa < 1.  A block stops, after at most `steps` steps, once a correction
+// is at most tol relative to x (max norms), or once the next one is predicted to be: the
+// error left after a step is about rate * (its correction) with rate <= c u kappa, so a step
+// whose correction is below tol / (16 u kappa) relative to x ends the block (kappa: an upper
+// bound of its condition number).  x is replicated over the group; jr and bl are the lane's
+// rows of J and b (zero past n).
 template <int G, int M, int RES>
 __device__ __forceinline__ void group_refine_aug(const float (&a)[kMaxCols][4], const float (&tau)[kMaxCols],
-                                                 float (&x)[kMaxCols], const float* sJ, const float* sB,
-                                                 const float* sR, int n, const Group<G>& g, int steps, float tol) {
+                                                 float (&x)[kMaxCols], const float (&jr)[M][4], const float (&bl)[4],
+                                                 int n, float kappa, const Group<G>& g, int steps, float tol) {
+  const float next_tol = tol / fmaxf(16.f * kUnitRoundoff * kappa, tol);
   const int q = g.q;
   // Q_1 = H_0 ... H_{M-1} [I_M; 0]: column j is changed by H_j .. H_0 only
   float qm[M][4];
@@ -432,18 +428,13 @@ __device__ __forceinline__ void group_refine_aug(const float (&a)[kMaxCols][4], 
       for (int u = 0; u < 4; ++u) qm[j][u] -= v[u] * w;
     }
   }
-  // R on every lane of the group (upper triangle, row-major by pairs i <= l) and 1 / diag
+  // R on every lane of the group (upper triangle) and 1 / diag
   float R[M][M], d[M];
+  group_gather_r<float, G, M>(a, g, R);
 #pragma unroll
-  for (int i = 0; i < M; ++i) {
-#pragma unroll
-    for (int l = 0; l < M; ++l) R[i][l] = (l >= i && n > 0) ? sR[l * n + i] : 0.f;
-    d[i] = rcp(R[i][i]);
-  }
+  for (int i = 0; i < M; ++i) d[i] = rcp(R[i][i]);
   // r = b - Q_1 (Q_1^T b)
-  float r[4], bl[4];
-#pragma unroll
-  for (int u = 0; u < 4; ++u) bl[u] = 4 * q + u < n ? sB[4 * q + u] : 0.f;
+  float r[4];
   {
     float c1[M];
 #pragma unroll
@@ -465,7 +456,7 @@ __device__ __forceinline__ void group_refine_aug(const float (&a)[kMaxCols][4], 
   for (int step = 0; step < steps; ++step) {
     if (__all_sync(0xffffffffu, done)) break;
     float f[4], gv[kMaxCols];
-    group_aug_residuals<G, M, RES>(sJ, sB, n, x, r, g, f, gv);
+    group_aug_residuals<G, M, RES>(jr, bl, x, r, g, f, gv);
     // t = Q_1^T f - R^{-T} g
     float t[M];
 #pragma unroll
@@ -509,7 +500,7 @@ __device__ __forceinline__ void group_refine_aug(const float (&a)[kMaxCols][4], 
         r[u] += dr;
       }
     }
-    done = done || !(dmax > tol * xmax);
+    done = done || !(dmax > next_tol * xmax);
   }
 }
 
@@ -610,12 +601,20 @@ __device__ __forceinline__ void send(T* dst, const T* src, int count, bool vec, 
   for (int k = h + ni + q; k < count; k += G) dst[k] = src[k];
 }
 
-// A block selected for refinement: its value, row and column offsets and its row count.
+// A block selected for refinement: its column offset (x), the offset of its first factor value
+// in the task planes, its row count and the bound ||R||_F ||R^{-1}||_F on its condition number.
+// The block's J and b are in its refinement record (same list position).
 struct RefEntry {
-  int64_t v, r, c;
-  int32_t n, pad;
+  int64_t c, f;
+  int32_t n;
+  float kappa;
+  int64_t pad;
 };
 static_assert(sizeof(RefEntry) == 32, "refinement list layout");
+
+// Refinement record of a block of shape key (G, M): its J in M planes of 4G rows (rows past n
+// zero) followed by b in 4G rows.
+__host__ __device__ constexpr int record_values(int G, int M) { return 4 * G * (M + 1); }
 
 template <typename T>
 struct TaskArgs {
@@ -626,11 +625,10 @@ struct TaskArgs {
   const T* b;
   const T* J_end;   // one past the last value (bounds of the copied supersets)
   const T* b_end;
-  T* F;             // factor, J packing
-  T* tau;
+  T* tF;            // factor in task planes (kPlaneValues per plane)
+  T* tTau;          // tau in task planes (kTauPlane per plane)
   T* qtb;           // may be null
   T* x;
-  int f_vec;        // F agrees with J modulo 16 bytes: factor leaves by vector stores
   int q_vec;        // qtb agrees with b modulo 16 bytes
   int warp_bytes;   // shared memory per warp (descriptor and data buffers)
   int data_bytes;   // one data buffer
@@ -639,7 +637,25 @@ struct TaskArgs {
   RefEntry* rlist;          // selection: blocks to refine, one list per shape key
   int* rcount;              // kTaskKeys counts
   const int64_t* key_off;   // kTaskKeys + 1 list offsets (list capacity = blocks of the key)
+  float* rec;               // refinement records, key k's at rec_off[k], in list order
+  const int64_t* rec_off;
 };
+
+// Four consecutive values of a lane's rows (16-byte aligned).
+__device__ __forceinline__ void store4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
 
 // Pipeline stages of the factor kernel: the header of task t, the entries of task t (its
 // header is in shared memory), the block data of task t (header and entries are).
@@ -671,7 +687,9 @@ __device__ __forceinline__ void issue_data(const TaskArgs<T>& A, int64_t t, cons
 }
 
 // One task of shape key (G, M), its data staged in db: M is a compile-time constant, so every
-// loop bound and guard of the inlined helpers folds away.
+// loop bound and guard of the inlined helpers folds away.  The factor leaves the registers
+// directly for the task's planes (one 16-byte store per lane and column), tau for its tau
+// planes; J and b stay in the slots (a selected block's record is copied from there).
 template <typename T, int G, int M, bool SEL>
 __device__ __forceinline__ void run_task(const TaskArgs<T>& A, const TaskHdr& h, const unsigned char* se,
                                          unsigned char* db, int lane) {
@@ -689,8 +707,8 @@ __device__ __forceinline__ void run_task(const TaskArgs<T>& A, const TaskHdr& h,
   slot_ptrs<T>(db, G, M, act ? grp : 0, gJ, gB, sJraw, sBraw, sJ, sB);
   T a[kMaxCols][4], c[4], x[kMaxCols];
   load_regs<T, G>(a, c, sJ, sB, n, M, g.q);
-  group_householder<T, G>(a, c, n > 0 ? A.tau + h.c0 + e.c : nullptr, M, g);
-  store_regs<T, G>(a, c, sJ, sB, n, M, g.q);
+  const int64_t plane = h.plane;
+  group_householder<T, G>(a, c, n > 0 ? A.tTau + plane * kTauPlane + grp : nullptr, kTauPlane, M, g);
   if (!group_backsub<T, G>(a, c, M, g, x) && n > 0) record(A.status, QRKIT_ESINGULAR);
   T x2 = T(0);
   if (n > 0) {
@@ -698,11 +716,13 @@ __device__ __forceinline__ void run_task(const TaskArgs<T>& A, const TaskHdr& h,
 #pragma unroll
     for (int k = 0; k < kmax<G>(); ++k)
       if (k < M && (k % G) == g.q) dx[k] = x[k];
+    T* f = A.tF + plane * kPlaneValues + grp * 4 * G + 4 * g.q;
+#pragma unroll
+    for (int j = 0; j < M; ++j) store4(f + j * kPlaneValues, a[j]);
   }
 #pragma unroll
   for (int k = 0; k < kmax<G>(); ++k)
     if (k < M) x2 += x[k] * x[k];
-  bool need = false;
   if constexpr (SEL) {
     float res2 = 0.f;
 #pragma unroll
@@ -711,36 +731,51 @@ __device__ __forceinline__ void run_task(const TaskArgs<T>& A, const TaskHdr& h,
       res2 += (r >= M && r < n) ? (float)(c[u] * c[u]) : 0.f;
     }
     res2 = g.sum(res2);
-    __syncwarp();   // the factor's rows from every lane of the group are in the slot
-    if (g.q == 0 && n > 0) need = lane_needs_refinement<M>((const float*)sJ, n, res2, (float)x2, A.select);
-  }
-  // factor and Q^T b from the slots to HBM
-  __syncwarp();
-  if (n > 0) {
-    send<T, G>(A.F + h.v0 + e.v, sJ, n * M, A.f_vec != 0, g.q);
-    if (A.qtb) send<T, G>(A.qtb + h.r0 + e.r, sB, n, A.q_vec != 0, g.q);
-  }
-  if constexpr (SEL) {
-    const bool sel = act && g.q == 0 && n > 0 && need;
+    float R[M][M];
+    group_gather_r<T, G, M>(a, g, R);
+    float kappa = 0.f;
+    const bool need = n > 0 && needs_refinement<M>(R, res2, (float)x2, A.select, kappa);
+    const bool sel = act && g.q == 0 && need;
     const unsigned mask = __ballot_sync(0xffffffffu, sel);
     if (mask) {
       int first = 0;
       if (lane == 0) first = atomicAdd(A.rcount + h.key, __popc(mask));
       first = __shfl_sync(0xffffffffu, first, 0);
-      if (sel) {
-        const int64_t pos = (int64_t)first + __popc(mask & ((1u << lane) - 1u));
-        const int64_t cap = A.key_off[h.key + 1] - A.key_off[h.key];
-        if (pos < cap) {
+      const int64_t pos = g.bcast((int64_t)first + __popc(mask & ((1u << lane) - 1u)), 0);
+      const bool gsel = g.bcast(sel ? 1 : 0, 0) != 0;
+      const int64_t cap = A.key_off[h.key + 1] - A.key_off[h.key];
+      if (gsel && pos < cap) {
+        // the record: J and b of the block from the slots, the lane's rows, zero past n
+        float* rec = A.rec + A.rec_off[h.key] + pos * record_values(G, M) + 4 * g.q;
+#pragma unroll
+        for (int j = 0; j < M; ++j) {
+          float v[4];
+#pragma unroll
+          for (int u = 0; u < 4; ++u) v[u] = 4 * g.q + u < n ? (float)sJ[j * n + 4 * g.q + u] : 0.f;
+          store4(rec + j * 4 * G, v);
+        }
+        float v[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) v[u] = 4 * g.q + u < n ? (float)sB[4 * g.q + u] : 0.f;
+        store4(rec + M * 4 * G, v);
+        if (g.q == 0) {
           RefEntry re;
-          re.v = h.v0 + e.v;
-          re.r = h.r0 + e.r;
           re.c = h.c0 + e.c;
+          re.f = plane * kPlaneValues + grp * 4 * G;
           re.n = n;
+          re.kappa = kappa;
           re.pad = 0;
           A.rlist[A.key_off[h.key] + pos] = re;
         }
       }
     }
+  }
+  if (A.qtb) {   // Q^T b through the b slot to HBM
+#pragma unroll
+    for (int u = 0; u < 4; ++u)
+      if (4 * g.q + u < n) sB[4 * g.q + u] = c[u];
+    __syncwarp();
+    if (n > 0) send<T, G>(A.qtb + h.r0 + e.r, sB, n, A.q_vec != 0, g.q);
   }
 }
 
@@ -793,27 +828,22 @@ __global__ void __launch_bounds__(32 * kTaskMaxWarps, sizeof(T) == 4 ? QRKIT_TAS
 }
 
 // ---------------------------------------------------------------------------------------
-// Refinement of the listed blocks (float), pipelined like the factor kernel in two stages:
-// while task i is refined, the block data of task i + 1 (J, the stored factor and b) and the
-// list entries of task i + 2 are in flight.  The factor (reflectors and R), tau and the float
-// solution come from the first kernel's output, so the blocks are not factored again.
+// Refinement of the listed blocks (float).  A task is P listed blocks of one shape key; each
+// group loads its block's record (J and b), its factor rows from the task planes, tau and the
+// float solution, all by 16-byte loads of whole row quads, and refines it.  The factor, tau and
+// the solution come from the first kernel, so the blocks are not factored again, and the
+// records it wrote are contiguous, so nothing is gathered from scattered blocks.
 struct RefineTaskArgs {
-  const float* J;
-  const float* b;
-  const float* J_end;
-  const float* b_end;
-  const float* F;   // factor of the first kernel (J's packing: reflectors below the diagonal,
-                    // R on and above it)
-  const float* F_end;
-  const float* tau;
-  float* x;         // in: the first kernel's solution; out: refined
+  const float* tF;     // factor planes of the first kernel
+  const float* tTau;   // tau planes
+  const float* rec;    // records
+  const int64_t* rec_off;
+  float* x;            // in: the first kernel's solution; out: refined
   const RefEntry* rlist;
   const int* rcount;
   const int64_t* key_off;
   int steps;
   float tol;
-  int warp_bytes;
-  int data_bytes;
   int* status;
 };
 
@@ -827,92 +857,49 @@ struct RefineTasks {
   }
 };
 
-__device__ __forceinline__ void issue_ref_ent(const RefineTaskArgs& A, const RefineTasks& RT, int64_t t,
-                                              unsigned char* s, int lane) {
-  if (t >= RT.total) return;
-  int key;
-  int64_t local;
-  RT.key_of(t, key, local);
-  const int P = blocks_per_task(group_lanes(key));
-  const int64_t cap = A.key_off[key + 1] - A.key_off[key];
-  const int64_t cnt = (int64_t)A.rcount[key] < cap ? (int64_t)A.rcount[key] : cap;
-  const int64_t idx = local * P + lane;
-  RefEntry* d = reinterpret_cast<RefEntry*>(s);
-  if (lane < P) {
-    if (idx < cnt) {
-      const RefEntry* g = A.rlist + A.key_off[key] + idx;
-      cp_async16(d + lane, g);
-      cp_async16(reinterpret_cast<unsigned char*>(d + lane) + 16, reinterpret_cast<const unsigned char*>(g) + 16);
-    } else {
-      d[lane].n = 0;   // no block
-    }
-  }
-}
-
-// The slots of a listed block in a refinement task's data buffer: J's and the factor's
-// supersets (P slots each) and then b's.
-__device__ __forceinline__ void refine_slot_ptrs(unsigned char* db, int G, int M, int grp, const float* gJ,
-                                                 const float* gF, const float* gB, unsigned char*& sJraw,
-                                                 unsigned char*& sFraw, unsigned char*& sBraw, float*& sJ,
-                                                 float*& sF, float*& sB) {
-  const int P = task_blocks(G);
-  const int JS = slot_j_bytes(G, M, 4);
-  const int BS = slot_b_bytes(G, 4);
-  sJraw = db + grp * JS;
-  sFraw = db + P * JS + grp * JS;
-  sBraw = db + 2 * P * JS + grp * BS;
-  sJ = reinterpret_cast<float*>(sJraw + (reinterpret_cast<uintptr_t>(gJ) & 15));
-  sF = reinterpret_cast<float*>(sFraw + (reinterpret_cast<uintptr_t>(gF) & 15));
-  sB = reinterpret_cast<float*>(sBraw + (reinterpret_cast<uintptr_t>(gB) & 15));
-}
-
-__device__ __forceinline__ void issue_ref_data(const RefineTaskArgs& A, const RefineTasks& RT, int64_t t,
-                                               const unsigned char* se, unsigned char* db, int lane) {
-  if (t >= RT.total) return;
-  int key;
-  int64_t local;
-  RT.key_of(t, key, local);
-  const int G = group_lanes(key), M = (key & 7) + 1, P = blocks_per_task(G);
-  const int grp = lane_group(lane, G), q = lane - grp * G;
-  if (grp >= P) return;
-  const RefEntry e = reinterpret_cast<const RefEntry*>(se)[grp];
-  const float* gJ = A.J + e.v;
-  const float* gF = A.F + e.v;
-  const float* gB = A.b + e.r;
-  unsigned char *sJraw, *sFraw, *sBraw;
-  float *sJ, *sF, *sB;
-  refine_slot_ptrs(db, G, M, grp, gJ, gF, gB, sJraw, sFraw, sBraw, sJ, sF, sB);
-  issue_block<float>(gJ, gB, e.n, M, G, q, A.J, A.J_end, A.b, A.b_end, sJraw, sBraw, sJ, sB);
-  if (e.n > 0) issue_span<float>(gF, e.n * M, G, q, A.F, A.F_end, sFraw, sF);
-}
-
 template <int G, int M, int RES>
-__device__ __forceinline__ void refine_task(const RefineTaskArgs& A, const unsigned char* se, unsigned char* db,
-                                            int lane) {
+__device__ __forceinline__ void refine_task(const RefineTaskArgs& A, int key, int64_t local, int lane) {
   constexpr int P = task_blocks(G);
   const int grp = lane / G;
-  const bool act = grp < P;
   const Group<G> g(lane);
+  const int64_t cap = A.key_off[key + 1] - A.key_off[key];
+  const int64_t cnt = (int64_t)A.rcount[key] < cap ? (int64_t)A.rcount[key] : cap;
+  const int64_t idx = local * P + grp;
+  const bool have = grp < P && idx < cnt;
   RefEntry e{};
-  if (act) e = reinterpret_cast<const RefEntry*>(se)[grp];
-  const int n = e.n;
-  unsigned char *sJraw, *sFraw, *sBraw;
-  float *sJ, *sF, *sB;
-  refine_slot_ptrs(db, G, M, act ? grp : 0, A.J + e.v, A.F + e.v, A.b + e.r, sJraw, sFraw, sBraw, sJ, sF, sB);
-  // the stored factor (reflectors and R) in registers as the first kernel left it, its tau and
-  // the float solution (the lanes of a group hold the same tau and x)
-  float a[kMaxCols][4], tau[kMaxCols], x[kMaxCols];
+  if (have) e = A.rlist[A.key_off[key] + idx];
+  const int n = have ? e.n : 0;
+  float jr[M][4], bl[4], a[kMaxCols][4], tau[kMaxCols], x[kMaxCols];
 #pragma unroll
   for (int j = 0; j < kMaxCols; ++j) {
 #pragma unroll
-    for (int u = 0; u < 4; ++u) {
-      const int r = 4 * g.q + u;
-      a[j][u] = (j < M && r < n) ? sF[j * n + r] : 0.f;
-    }
-    tau[j] = (j < M && n > 0) ? A.tau[e.c + j] : 0.f;
-    x[j] = (j < M && n > 0) ? A.x[e.c + j] : 0.f;
+    for (int u = 0; u < 4; ++u) a[j][u] = 0.f;
+    tau[j] = 0.f;
+    x[j] = 0.f;
   }
-  group_refine_aug<G, M, RES>(a, tau, x, sJ, sB, sF, n, g, A.steps, A.tol);
+#pragma unroll
+  for (int u = 0; u < 4; ++u) bl[u] = 0.f;
+#pragma unroll
+  for (int j = 0; j < M; ++j)
+#pragma unroll
+    for (int u = 0; u < 4; ++u) jr[j][u] = 0.f;
+  if (n > 0) {
+    const float* rec = A.rec + A.rec_off[key] + idx * record_values(G, M) + 4 * g.q;
+#pragma unroll
+    for (int j = 0; j < M; ++j) load4(rec + j * 4 * G, jr[j]);
+    load4(rec + M * 4 * G, bl);
+    const float* f = A.tF + e.f + 4 * g.q;
+#pragma unroll
+    for (int j = 0; j < M; ++j) load4(f + j * kPlaneValues, a[j]);
+    const int64_t plane = e.f / kPlaneValues;
+    const int slot = (int)(e.f - plane * kPlaneValues) / (4 * G);
+#pragma unroll
+    for (int k = 0; k < M; ++k) {
+      tau[k] = A.tTau[(plane + k) * kTauPlane + slot];
+      x[k] = A.x[e.c + k];
+    }
+  }
+  group_refine_aug<G, M, RES>(a, tau, x, jr, bl, n, e.kappa, g, A.steps, A.tol);
   if (n > 0) {
     float* dx = A.x + e.c;
 #pragma unroll
@@ -923,9 +910,7 @@ __device__ __forceinline__ void refine_task(const RefineTaskArgs& A, const unsig
 
 template <int RES>
 __global__ void __launch_bounds__(32 * kTaskMaxWarps, QRKIT_REFINE_CTAS) block_task_refine_kernel(RefineTaskArgs A) {
-  extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpc = blockDim.x >> 5;
-  const WarpBufs W{smem_raw + (size_t)wid * A.warp_bytes, A.data_bytes, 32 * (int)sizeof(RefEntry)};
   // tasks per shape key (lane k: key k), their exclusive prefix sums over the keys
   RefineTasks RT;
   {
@@ -942,38 +927,47 @@ __global__ void __launch_bounds__(32 * kTaskMaxWarps, QRKIT_REFINE_CTAS) block_t
     RT.start = inc - tk;
     RT.total = __shfl_sync(0xffffffffu, inc, 31);
   }
-  const int64_t t0 = (int64_t)blockIdx.x * wpc + wid, stride = (int64_t)gridDim.x * wpc;
-  if (t0 >= RT.total) return;
-  issue_ref_ent(A, RT, t0, W.ent(0), lane);
-  cp_async_commit();
-  cp_async_wait_all();
-  __syncwarp();
-  issue_ref_ent(A, RT, t0 + stride, W.ent(1), lane);
-  issue_ref_data(A, RT, t0, W.ent(0), W.data(0), lane);
-  cp_async_commit();
-  int se = 0, sd = 0;   // slots of task i
-  for (int64_t t = t0; t < RT.total; t += stride) {
-    cp_async_wait_all();
-    __syncwarp();   // task i's data and task i + 1's entries have landed
-    const int se1 = next3(se), se2 = next3(se1);
-    issue_ref_ent(A, RT, t + 2 * stride, W.ent(se2), lane);
-    issue_ref_data(A, RT, t + stride, W.ent(se1), W.data(sd ^ 1), lane);
-    cp_async_commit();
+  const int64_t stride = (int64_t)gridDim.x * wpc;
+  for (int64_t t = (int64_t)blockIdx.x * wpc + wid; t < RT.total; t += stride) {
     int key;
     int64_t local;
     RT.key_of(t, key, local);
     switch (key) {
 #define QRKIT_REFINE_CASE(k) \
-  case k: refine_task<((k) >> 3) + 1, ((k) & 7) + 1, RES>(A, W.ent(se), W.data(sd), lane); break;
+  case k: refine_task<((k) >> 3) + 1, ((k) & 7) + 1, RES>(A, key, local, lane); break;
       QRKIT_TASK_KEYS(QRKIT_REFINE_CASE)
 #undef QRKIT_REFINE_CASE
       default: break;
     }
-    __syncwarp();   // every lane is done with task i's buffers before they are refilled
-    se = se1;
-    sd ^= 1;
   }
-  cp_async_wait_all();
+}
+
+// The factor of the task planes copied into J's packing (reflectors below the diagonal, R on
+// and above it) and tau into column order: one warp per task, lanes as in the factor kernel.
+template <typename T>
+__global__ void __launch_bounds__(256) unpack_factor_kernel(const TaskHdr* hdr, const TaskEntry* ent,
+                                                             int64_t num_tasks, const T* tF, const T* tTau, T* F,
+                                                             T* tau) {
+  const int lane = threadIdx.x & 31;
+  const int64_t w0 = ((int64_t)blockIdx.x * blockDim.x + threadIdx.x) >> 5;
+  const int64_t stride = ((int64_t)gridDim.x * blockDim.x) >> 5;
+  for (int64_t t = w0; t < num_tasks; t += stride) {
+    const TaskHdr h = hdr[t];
+    const int G = group_lanes(h.key), M = (h.key & 7) + 1, P = blocks_per_task(G);
+    const int grp = lane_group(lane, G), q = lane - grp * G;
+    if (grp >= P) continue;
+    const TaskEntry e = ent[h.first + grp];
+    const int n = e.n;
+    if (n == 0) continue;
+    const int64_t plane = h.plane;
+    for (int j = 0; j < M; ++j)
+      for (int u = 0; u < 4; ++u) {
+        const int r = 4 * q + u;
+        if (F && r < n) F[h.v0 + e.v + (int64_t)j * n + r] = tF[(plane + j) * kPlaneValues + grp * 4 * G + r];
+      }
+    if (tau && q == 0)
+      for (int k = 0; k < M; ++k) tau[h.c0 + e.c + k] = tTau[(plane + k) * kTauPlane + grp];
+  }
 }
 
 // Host-side entry points of the kernels; each is defined by the translation unit that

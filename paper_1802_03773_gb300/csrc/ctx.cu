@@ -279,6 +279,11 @@ void qrkit_destroy(qrkit_ctx* ctx) {
   release(ctx->ws.tau);
   release(ctx->ws.rlist);
   release(ctx->ws.rcount);
+  release(ctx->ws.tlist);
+  release(ctx->ws.tcount);
+  release(ctx->ws.tfactor);
+  release(ctx->ws.ttau);
+  release(ctx->ws.rrec);
   if (ctx->d_status) cudaFree(ctx->d_status);
   delete ctx;
 }
@@ -329,7 +334,10 @@ qrkit_status qrkit_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, co
                 " has fewer rows than columns and lambda = 0");
   QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   qrkit_status st = launch_block_solve(ctx, J, b, D, p, qtb, refine_steps);
-  if (st == QRKIT_OK) ctx->factored = true;
+  if (st == QRKIT_OK) {
+    ctx->factored = true;
+    ctx->factor_in_planes = ctx->plan.mapping == 0 && ctx->plan.num_tasks > 0;
+  }
   return st;
 }
 
@@ -400,6 +408,8 @@ qrkit_status qrkit_get_band_factor(qrkit_ctx* ctx, void* Rw, void* c, double* re
 qrkit_status qrkit_get_factor(qrkit_ctx* ctx, void* factor_out, void* tau_out) {
   if (!ctx) return QRKIT_EINVAL;
   if (!ctx->factored) return fail(ctx, QRKIT_ESTATE, "no factor stored");
+  QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  if (ctx->factor_in_planes) return unpack_block_tasks_factor(ctx, factor_out, tau_out);
   const size_t es = elem_size(ctx);
   if (factor_out)
     QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(factor_out, ctx->ws.factor.ptr, (size_t)ctx->plan.values * es,

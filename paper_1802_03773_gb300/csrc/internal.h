@@ -33,8 +33,14 @@ struct TaskHdr {
   int64_t v0, r0, c0, b0;   // value, row, column and block offsets of the supertile
   int64_t first;            // first of the task's P entries
   int32_t key;
-  int32_t pad;
+  int32_t plane;            // first of the task's M planes of the stored factor (see below)
 };
+// The factor the warp-task kernels keep: per task M planes of kPlaneValues values, plane j =
+// column j of the task's blocks, block slot s at s * 4G, rows 4q .. 4q + 3 of lane q of its
+// group at 4q (rows past n are zero); tau in planes of kTauPlane values, tau_k of slot s at
+// plane k, entry s.  Lanes store whole 16-byte row quads, so every plane is written in full.
+constexpr int kPlaneValues = 128;
+constexpr int kTauPlane = 32;
 struct TaskEntry {
   uint32_t v, r, c;         // offsets relative to the supertile bases
   uint16_t blk;             // block index relative to the supertile
@@ -80,7 +86,9 @@ struct Plan {
   int64_t num_tasks = 0;
   int64_t max_refine_tasks = 0;       // refinement tasks if every block were selected
   std::vector<int64_t> key_off;       // kTaskKeys + 1: blocks per key, prefix sums
-  DevBuf d_task_hdr, d_task_ent, d_key_off;
+  int64_t factor_planes = 0;          // planes of the stored factor (all tasks)
+  std::vector<int64_t> rec_off;       // kTaskKeys + 1: offsets of the keys' refinement records
+  DevBuf d_task_hdr, d_task_ent, d_key_off, d_rec_off;
 };
 
 // Read-only view of a block-angular structure and its values (device pointers).
@@ -205,6 +213,8 @@ struct Workspace {
   DevBuf tau;      // sum m_i
   DevBuf rlist, rcount;   // blocks selected for refinement (4 row-class lists) and their counts
   DevBuf tlist, tcount;   // the same for the warp-task kernels (one list per shape key)
+  DevBuf tfactor, ttau;   // factor and tau of the warp-task kernels in task planes
+  DevBuf rrec;            // refinement records (J and b of the selected blocks)
 };
 
 }  // namespace qrkit
@@ -230,6 +240,7 @@ struct qrkit_ctx {
   float refine_select = 2e-6f;  // block refinement: a-priori error estimate that selects a block
   int refine_residual = 0;      // its residual precision: 0 compensated float, 1 double
   bool factored = false;       // fused block path
+  bool factor_in_planes = false;  // the fused factor is in task planes (warp-task kernels)
   bool comp_factored = false;  // composed path
   bool band_factored = false;  // banded path
 };
@@ -294,6 +305,8 @@ constexpr int64_t kDefaultSupertile = 65536;
 qrkit_status build_block_tasks(qrkit_ctx* ctx, int64_t supertile, int warps, bool key_major);
 qrkit_status launch_block_tasks(qrkit_ctx* ctx, const void* J, const void* b, void* p, void* qtb,
                                 int refine_steps);
+// The warp-task factor (task planes) copied into J's packing and tau into column order.
+qrkit_status unpack_block_tasks_factor(qrkit_ctx* ctx, void* factor_out, void* tau_out);
 void release_block_tasks(Plan& P);
 
 }  // namespace qrkit

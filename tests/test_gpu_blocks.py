@@ -39,6 +39,7 @@ def run(d, precision, refine_steps=1, with_qtb=True, tuning=None, offset=0, refi
     if refinement is not None:
         ctx.set_refinement(*refinement)
     ctx.factor_solve(J, b, p, qtb, refine_steps=refine_steps)
+    launches = ctx.launch_count
     F = torch.empty_like(J)
     tau = torch.empty(ncols, device=dev, dtype=dt)
     ctx.get_factor(F, tau)
@@ -46,7 +47,7 @@ def run(d, precision, refine_steps=1, with_qtb=True, tuning=None, offset=0, refi
     out = dict(p=p.cpu().numpy().astype(np.float64), F=F.cpu().numpy().astype(np.float64),
                tau=tau.cpu().numpy().astype(np.float64),
                qtb=None if qtb is None else qtb.cpu().numpy().astype(np.float64),
-               launches=ctx.launch_count)
+               launches=launches)
     ctx.close()
     return out
 
