@@ -99,7 +99,6 @@ qrkit_status launch_tasks_typed(qrkit_ctx* ctx, const void* J, const void* b, vo
   if constexpr (SEL && sizeof(T) == sizeof(float)) {
     RefineTaskArgs R;
     R.tF = (const float*)A.tF;
-    R.tTau = (const float*)A.tTau;
     R.rec = A.rec;
     R.rec_off = A.rec_off;
     R.x = (float*)p;

@@ -39,7 +39,6 @@ namespace tasks {
 using namespace dev;
 
 constexpr float kUnitRoundoff = 5.9604645e-8f;   // 2^-24
-constexpr float kRefineSelect = 2e-6f;           // default: blocks estimated above this are refined
 constexpr int kMaxCols = 8;
 constexpr int kTaskMaxWarps = 8;   // the kernels are compiled for at most 256 threads per CTA
 #ifndef QRKIT_TASK_CTAS
@@ -123,6 +122,22 @@ struct Group {
 
 template <int G>
 __host__ __device__ constexpr int kmax() { return 4 * G < kMaxCols ? 4 * G : kMaxCols; }
+
+// Four consecutive values of a lane's rows (16-byte aligned).
+__device__ __forceinline__ void store4(float* p, const float (&v)[4]) {
+  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
+}
+__device__ __forceinline__ void store4(double* p, const double (&v)[4]) {
+  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
+  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
+}
+__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
+  const float4 t = *reinterpret_cast<const float4*>(p);
+  v[0] = t.x;
+  v[1] = t.y;
+  v[2] = t.z;
+  v[3] = t.w;
+}
 
 // The shape keys a task can have: row class 0 (G = 1) with m <= 4, classes 1-3 with m <= 8.
 #define QRKIT_TASK_KEYS(X) \
@@ -272,64 +287,93 @@ __device__ __forceinline__ bool group_backsub(const T (&a)[kMaxCols][4], const T
 }
 
 // A-priori error estimate of the float least-squares solution.  Householder QR is backward
-// stable, so the forward error is a small multiple of u (kappa + kappa^2 ||r|| / (||A|| ||x||));
-// here kappa and ||A|| kappa^2 are replaced by upper bounds from the Frobenius norms of R and
-// R^{-1} (kappa_2 <= ||R||_F ||R^{-1}||_F, ||A||_2 <= ||R||_F), so the estimate never falls
-// below that expression: est = u (||R||_F ||R^{-1}||_F + ||R||_F ||R^{-1}||_F^2 ||r|| / ||x||)
-// with u = 2^-24 and ||r|| = || rows M.. of Q^T b ||.  R^{-1} is formed column by column (the
-// columns are independent back-substitutions).  True when the estimate exceeds `target` (or
-// is NaN: a zero pivot, x = 0).  R: the upper triangle (R[i][k], i <= k); res2 = ||r||^2,
-// x2 = ||x||^2; kappa receives ||R||_F ||R^{-1}||_F.
+// stable, so the forward error is a small multiple of u (kappa + kappa^2 ||r|| / (||A|| ||x||))
+// = u (||A|| ||A^+|| + ||A|| ||A^+||^2 ||r|| / ||x||) in 2-norms, ||A|| = ||R||, ||A^+|| = ||R^{-1}||.
+// Both norms are replaced by upper bounds, so the estimate never falls below that expression:
+// ||M||_2 <= min(||M||_F, (||M||_1 ||M||_inf)^(1/2)) (the Frobenius bound is tight for nearly
+// rank-one M, the Hoelder one for well-conditioned M).  est = u (a y + a y^2 ||r|| / ||x||) with
+// a, y those bounds for R and R^{-1}, u = 2^-24 and ||r|| = || rows M.. of Q^T b ||.  R^{-1} is
+// formed column by column (the columns are independent back-substitutions).  True when the
+// estimate exceeds `target` (or is NaN: a zero pivot, x = 0).  R: the upper triangle (R[i][k],
+// i <= k); res2 = ||r||^2, x2 = ||x||^2; kappa receives the bound a y on the condition number.
 template <int M>
 __device__ __forceinline__ bool needs_refinement(const float (&R)[M][M], float res2, float x2, float target,
                                                  float& kappa) {
   float d[M];
-  float rF2 = 0.f;
+  float rF2 = 0.f, r1 = 0.f, rI[M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) rI[i] = 0.f;
 #pragma unroll
   for (int k = 0; k < M; ++k) {
+    float cs = 0.f;
 #pragma unroll
-    for (int i = 0; i <= k; ++i) rF2 += R[i][k] * R[i][k];
+    for (int i = 0; i <= k; ++i) {
+      rF2 += R[i][k] * R[i][k];
+      cs += fabsf(R[i][k]);
+      rI[i] += fabsf(R[i][k]);
+    }
+    r1 = fmaxf(r1, cs);
     d[k] = rcp(R[k][k]);
   }
-  float iF2 = 0.f;
+  float yF2 = 0.f, y1 = 0.f, yI[M];
+#pragma unroll
+  for (int i = 0; i < M; ++i) yI[i] = 0.f;
 #pragma unroll
   for (int j = 0; j < M; ++j) {   // column j of R^{-1}: y_j = 1 / R_jj, rows above by back-substitution
     float y[M];
     y[j] = d[j];
-    iF2 += y[j] * y[j];
+    float cs = fabsf(y[j]);
+    yF2 += y[j] * y[j];
+    yI[j] += fabsf(y[j]);
 #pragma unroll
     for (int i = j - 1; i >= 0; --i) {
       float sm = 0.f;
 #pragma unroll
       for (int l = i + 1; l <= j; ++l) sm += R[i][l] * y[l];
       y[i] = -sm * d[i];
-      iF2 += y[i] * y[i];
+      yF2 += y[i] * y[i];
+      cs += fabsf(y[i]);
+      yI[i] += fabsf(y[i]);
     }
+    y1 = fmaxf(y1, cs);
   }
-  const float kF = sqrtf(rF2 * iF2);
-  kappa = kF;
-  const float est = kUnitRoundoff * (kF + kF * sqrtf(iF2) * sqrtf(res2 / x2));
+  float rInf = 0.f, yInf = 0.f;
+#pragma unroll
+  for (int i = 0; i < M; ++i) {
+    rInf = fmaxf(rInf, rI[i]);
+    yInf = fmaxf(yInf, yI[i]);
+  }
+  const float an = fminf(sqrtf(rF2), sqrtf(r1 * rInf));
+  const float yn = fminf(sqrtf(yF2), sqrtf(y1 * yInf));
+  kappa = an * yn;
+  const float est = kUnitRoundoff * (kappa + kappa * yn * sqrtf(res2 / x2));
   return !(est <= target);
 }
 
-// The upper triangle of the group's R (row i lives on lane i / 4) on every lane of the group.
-template <typename T, int G, int M>
+// The upper triangle of the group's R (row i lives on lane i / 4) on every lane of the group;
+// with LEAD only the group's lane 0 needs it, and rows 0..3 are its own.
+template <typename T, int G, int M, bool LEAD = false>
 __device__ __forceinline__ void group_gather_r(const T (&a)[kMaxCols][4], const Group<G>& g, float (&R)[M][M]) {
 #pragma unroll
   for (int k = 0; k < M; ++k)
 #pragma unroll
-    for (int i = 0; i < M; ++i) R[i][k] = i <= k ? (float)g.bcast(a[k][i & 3], i >> 2) : 0.f;
+    for (int i = 0; i < M; ++i)
+      R[i][k] = i > k ? 0.f : ((LEAD && i < 4) ? (float)a[k][i] : (float)g.bcast(a[k][i & 3], i >> 2));
 }
 
 // The refinement's two residuals of the augmented system [I J; J^T 0] [r; x] = [b; 0] in
 // extended precision, rounded once to float: f = b - r - J x on the lane's rows and
 // g = -J^T r (replicated over the group).  RES = 0: compensated float arithmetic (Dot2 of
 // Ogita, Rump and Oishi: error-free products and sums, value = s + c); RES = 1: double.
-// jr, bl: the lane's rows of J and b (zero past n).
+// jq: the lane's row quad of J's column 0 (16-byte aligned, column stride 4G values, zero past
+// n); bl: the lane's rows of b.
 template <int G, int M, int RES>
-__device__ __forceinline__ void group_aug_residuals(const float (&jr)[M][4], const float (&bl)[4],
+__device__ __forceinline__ void group_aug_residuals(const float* jq, const float (&bl)[4],
                                                     const float (&x)[kMaxCols], const float (&r)[4], const Group<G>& g,
                                                     float (&f)[4], float (&gv)[kMaxCols]) {
+  float jr[M][4];
+#pragma unroll
+  for (int j = 0; j < M; ++j) load4(jq + j * 4 * G, jr[j]);
   if constexpr (RES == 0) {
 #pragma unroll
     for (int u = 0; u < 4; ++u) {
@@ -396,11 +440,11 @@ __device__ __forceinline__ void group_aug_residuals(const float (&jr)[M][4], con
 // is at most tol relative to x (max norms), or once the next one is predicted to be: the
 // error left after a step is about rate * (its correction) with rate <= c u kappa, so a step
 // whose correction is below tol / (16 u kappa) relative to x ends the block (kappa: an upper
-// bound of its condition number).  x is replicated over the group; jr and bl are the lane's
-// rows of J and b (zero past n).
+// bound of its condition number).  x is replicated over the group; jq points to the lane's row
+// quad of J's column 0 (column stride 4G values, zero past n) and bl holds its rows of b.
 template <int G, int M, int RES>
 __device__ __forceinline__ void group_refine_aug(const float (&a)[kMaxCols][4], const float (&tau)[kMaxCols],
-                                                 float (&x)[kMaxCols], const float (&jr)[M][4], const float (&bl)[4],
+                                                 float (&x)[kMaxCols], const float* jq, const float (&bl)[4],
                                                  int n, float kappa, const Group<G>& g, int steps, float tol) {
   const float next_tol = tol / fmaxf(16.f * kUnitRoundoff * kappa, tol);
   const int q = g.q;
@@ -456,7 +500,7 @@ __device__ __forceinline__ void group_refine_aug(const float (&a)[kMaxCols][4], 
   for (int step = 0; step < steps; ++step) {
     if (__all_sync(0xffffffffu, done)) break;
     float f[4], gv[kMaxCols];
-    group_aug_residuals<G, M, RES>(jr, bl, x, r, g, f, gv);
+    group_aug_residuals<G, M, RES>(jq, bl, x, r, g, f, gv);
     // t = Q_1^T f - R^{-T} g
     float t[M];
 #pragma unroll
@@ -603,7 +647,7 @@ __device__ __forceinline__ void send(T* dst, const T* src, int count, bool vec, 
 
 // A block selected for refinement: its column offset (x), the offset of its first factor value
 // in the task planes, its row count and the bound ||R||_F ||R^{-1}||_F on its condition number.
-// The block's J and b are in its refinement record (same list position).
+// Everything else the refinement reads is in the block's record (same list position).
 struct RefEntry {
   int64_t c, f;
   int32_t n;
@@ -612,9 +656,11 @@ struct RefEntry {
 };
 static_assert(sizeof(RefEntry) == 32, "refinement list layout");
 
-// Refinement record of a block of shape key (G, M): its J in M planes of 4G rows (rows past n
-// zero) followed by b in 4G rows.
-__host__ __device__ constexpr int record_values(int G, int M) { return 4 * G * (M + 1); }
+// Refinement record of a block of shape key (G, M): its J in M columns of 4G rows (rows past n
+// zero), b in 4G rows and the float solution x (8 values).
+__host__ __device__ constexpr int record_values(int G, int M) { return 4 * G * (M + 1) + 8; }
+__host__ __device__ constexpr int record_b(int G, int M) { return 4 * G * M; }
+__host__ __device__ constexpr int record_tail(int G, int M) { return 4 * G * (M + 1); }
 
 template <typename T>
 struct TaskArgs {
@@ -640,22 +686,6 @@ struct TaskArgs {
   float* rec;               // refinement records, key k's at rec_off[k], in list order
   const int64_t* rec_off;
 };
-
-// Four consecutive values of a lane's rows (16-byte aligned).
-__device__ __forceinline__ void store4(float* p, const float (&v)[4]) {
-  *reinterpret_cast<float4*>(p) = make_float4(v[0], v[1], v[2], v[3]);
-}
-__device__ __forceinline__ void store4(double* p, const double (&v)[4]) {
-  reinterpret_cast<double2*>(p)[0] = make_double2(v[0], v[1]);
-  reinterpret_cast<double2*>(p)[1] = make_double2(v[2], v[3]);
-}
-__device__ __forceinline__ void load4(const float* p, float (&v)[4]) {
-  const float4 t = *reinterpret_cast<const float4*>(p);
-  v[0] = t.x;
-  v[1] = t.y;
-  v[2] = t.z;
-  v[3] = t.w;
-}
 
 // Pipeline stages of the factor kernel: the header of task t, the entries of task t (its
 // header is in shared memory), the block data of task t (header and entries are).
@@ -732,7 +762,7 @@ __device__ __forceinline__ void run_task(const TaskArgs<T>& A, const TaskHdr& h,
     }
     res2 = g.sum(res2);
     float R[M][M];
-    group_gather_r<T, G, M>(a, g, R);
+    group_gather_r<T, G, M, true>(a, g, R);   // valid on the group's lane 0, which decides
     float kappa = 0.f;
     const bool need = n > 0 && needs_refinement<M>(R, res2, (float)x2, A.select, kappa);
     const bool sel = act && g.q == 0 && need;
@@ -745,7 +775,7 @@ __device__ __forceinline__ void run_task(const TaskArgs<T>& A, const TaskHdr& h,
       const bool gsel = g.bcast(sel ? 1 : 0, 0) != 0;
       const int64_t cap = A.key_off[h.key + 1] - A.key_off[h.key];
       if (gsel && pos < cap) {
-        // the record: J and b of the block from the slots, the lane's rows, zero past n
+        // the record: J and b of the block from the slots (the lane's rows, zero past n) and x
         float* rec = A.rec + A.rec_off[h.key] + pos * record_values(G, M) + 4 * g.q;
 #pragma unroll
         for (int j = 0; j < M; ++j) {
@@ -757,8 +787,14 @@ __device__ __forceinline__ void run_task(const TaskArgs<T>& A, const TaskHdr& h,
         float v[4];
 #pragma unroll
         for (int u = 0; u < 4; ++u) v[u] = 4 * g.q + u < n ? (float)sB[4 * g.q + u] : 0.f;
-        store4(rec + M * 4 * G, v);
+        store4(rec + record_b(G, M), v);
         if (g.q == 0) {
+          float* tail = rec + record_tail(G, M);   // rec includes the lane offset 4q = 0 here
+          float xv[8];
+#pragma unroll
+          for (int k = 0; k < 8; ++k) xv[k] = k < M ? (float)x[k] : 0.f;
+          store4(tail, *reinterpret_cast<const float(*)[4]>(xv));
+          store4(tail + 4, *reinterpret_cast<const float(*)[4]>(xv + 4));
           RefEntry re;
           re.c = h.c0 + e.c;
           re.f = plane * kPlaneValues + grp * 4 * G;
@@ -829,13 +865,11 @@ __global__ void __launch_bounds__(32 * kTaskMaxWarps, sizeof(T) == 4 ? QRKIT_TAS
 
 // ---------------------------------------------------------------------------------------
 // Refinement of the listed blocks (float).  A task is P listed blocks of one shape key; each
-// group loads its block's record (J and b), its factor rows from the task planes, tau and the
-// float solution, all by 16-byte loads of whole row quads, and refines it.  The factor, tau and
-// the solution come from the first kernel, so the blocks are not factored again, and the
-// records it wrote are contiguous, so nothing is gathered from scattered blocks.
+// group reads its block's record (J, b and the float solution, contiguous) and its factor rows
+// from the task planes, by 16-byte loads of whole row quads, and refines it.  The factor and
+// the solution come from the first kernel, so the blocks are not factored again.
 struct RefineTaskArgs {
   const float* tF;     // factor planes of the first kernel
-  const float* tTau;   // tau planes
   const float* rec;    // records
   const int64_t* rec_off;
   float* x;            // in: the first kernel's solution; out: refined
@@ -857,19 +891,23 @@ struct RefineTasks {
   }
 };
 
+__device__ __forceinline__ int64_t ref_count(const RefineTaskArgs& A, int key) {
+  const int64_t cap = A.key_off[key + 1] - A.key_off[key];
+  return (int64_t)A.rcount[key] < cap ? (int64_t)A.rcount[key] : cap;
+}
+
 template <int G, int M, int RES>
 __device__ __forceinline__ void refine_task(const RefineTaskArgs& A, int key, int64_t local, int lane) {
   constexpr int P = task_blocks(G);
   const int grp = lane / G;
   const Group<G> g(lane);
-  const int64_t cap = A.key_off[key + 1] - A.key_off[key];
-  const int64_t cnt = (int64_t)A.rcount[key] < cap ? (int64_t)A.rcount[key] : cap;
   const int64_t idx = local * P + grp;
-  const bool have = grp < P && idx < cnt;
+  const bool have = grp < P && idx < ref_count(A, key);
   RefEntry e{};
   if (have) e = A.rlist[A.key_off[key] + idx];
   const int n = have ? e.n : 0;
-  float jr[M][4], bl[4], a[kMaxCols][4], tau[kMaxCols], x[kMaxCols];
+  const float* rec = A.rec + A.rec_off[key] + (have ? idx : 0) * record_values(G, M);
+  float bl[4], a[kMaxCols][4], tau[kMaxCols], x[kMaxCols];
 #pragma unroll
   for (int j = 0; j < kMaxCols; ++j) {
 #pragma unroll
@@ -879,27 +917,25 @@ __device__ __forceinline__ void refine_task(const RefineTaskArgs& A, int key, in
   }
 #pragma unroll
   for (int u = 0; u < 4; ++u) bl[u] = 0.f;
-#pragma unroll
-  for (int j = 0; j < M; ++j)
-#pragma unroll
-    for (int u = 0; u < 4; ++u) jr[j][u] = 0.f;
   if (n > 0) {
-    const float* rec = A.rec + A.rec_off[key] + idx * record_values(G, M) + 4 * g.q;
-#pragma unroll
-    for (int j = 0; j < M; ++j) load4(rec + j * 4 * G, jr[j]);
-    load4(rec + M * 4 * G, bl);
     const float* f = A.tF + e.f + 4 * g.q;
 #pragma unroll
     for (int j = 0; j < M; ++j) load4(f + j * kPlaneValues, a[j]);
-    const int64_t plane = e.f / kPlaneValues;
-    const int slot = (int)(e.f - plane * kPlaneValues) / (4 * G);
+    load4(rec + record_b(G, M) + 4 * g.q, bl);
 #pragma unroll
-    for (int k = 0; k < M; ++k) {
-      tau[k] = A.tTau[(plane + k) * kTauPlane + slot];
-      x[k] = A.x[e.c + k];
-    }
+    for (int k = 0; k < M; ++k) x[k] = rec[record_tail(G, M) + k];
   }
-  group_refine_aug<G, M, RES>(a, tau, x, jr, bl, n, e.kappa, g, A.steps, A.tol);
+  // tau_k = 2 / v^T v of the stored reflector (v_k = 1), equal in exact arithmetic to the
+  // (beta - alpha) / beta the factorization formed
+#pragma unroll
+  for (int k = 0; k < M; ++k) {
+    float w = 0.f;
+#pragma unroll
+    for (int u = 0; u < 4; ++u) w += 4 * g.q + u > k ? a[k][u] * a[k][u] : 0.f;
+    w = g.sum(w);   // every lane takes part in the group reduction
+    tau[k] = n > 0 ? 2.f / (1.f + w) : 0.f;
+  }
+  group_refine_aug<G, M, RES>(a, tau, x, rec + 4 * g.q, bl, n, e.kappa, g, A.steps, A.tol);
   if (n > 0) {
     float* dx = A.x + e.c;
 #pragma unroll
@@ -914,8 +950,7 @@ __global__ void __launch_bounds__(32 * kTaskMaxWarps, QRKIT_REFINE_CTAS) block_t
   // tasks per shape key (lane k: key k), their exclusive prefix sums over the keys
   RefineTasks RT;
   {
-    const int64_t cap = A.key_off[lane + 1] - A.key_off[lane];
-    const int64_t cnt = (int64_t)A.rcount[lane] < cap ? (int64_t)A.rcount[lane] : cap;
+    const int64_t cnt = ref_count(A, lane);
     const int64_t per = task_blocks(group_lanes(lane));
     const int64_t tk = (cnt + per - 1) / per;
     int64_t inc = tk;
