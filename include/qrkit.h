@@ -95,6 +95,14 @@ typedef struct qrkit_structure {
                                     grouped by segment in order, this many per segment */
   /* --- QRKIT_STRUCT_BANDED: algorithm --- */
   int32_t band_solver;           /* QRKIT_BAND_AUTO, QRKIT_BAND_SWEEP or QRKIT_BAND_PARALLEL */
+  /* --- QRKIT_STRUCT_BANDED, optional: explicit row starts (Sec. 4.3 row and column
+   *     permutations applied by the caller, e.g. those of qrkit_band_order) --- */
+  const int32_t* band_row_start; /* host, one entry per row (instances' rows back to back): the
+                                    first column of the row inside its instance, non-decreasing
+                                    within an instance; NULL: the implicit floor(i / rows_per_col)
+                                    rule (rows_per_col is then ignored) */
+  const int64_t* instance_rows;  /* host, num_blocks entries: rows of each instance when
+                                    band_row_start is given (NULL for one instance: `rows`) */
 } qrkit_structure;
 
 /* Banded QR algorithms (both Sec. 4.4 block-banded Householder QR with the damping rows
@@ -158,6 +166,15 @@ qrkit_status qrkit_plan(qrkit_ctx* ctx, const qrkit_structure* s);
  * its refinement); asynchronous on the context's stream. */
 qrkit_status qrkit_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
                                 double lambda, void* p, void* qtb, int refine_steps);
+
+/* Poll limit of the bounded device waits (no paper counterpart): the tile mapping of the block
+ * solve waits for its bulk copies on an mbarrier at most this many polls (default 2^26).  A
+ * wait that runs out records QRKIT_ETIMEOUT in the device status word (qrkit_sync_status);
+ * the kernel then waits for its own copies in flight with a limit of its own (2^26 polls)
+ * before it returns, so no kernel traps or hangs and the context stays usable.  A small limit
+ * (down to 0) makes the waits run out on purpose, which tests that failure path without a
+ * GPU fault.  QRKIT_EINVAL for polls < 0. */
+qrkit_status qrkit_set_wait_limit(qrkit_ctx* ctx, int64_t polls);
 
 /* Residual precision of the block refinement (qrkit_set_refinement). */
 enum { QRKIT_RESIDUAL_DOT2 = 0, QRKIT_RESIDUAL_FP64 = 1 };

@@ -552,6 +552,81 @@ __global__ void band_g_kernel(const T* J, const T* x, const double* r, const dou
   g[gj] = acc;
 }
 
+// Rows with explicit starts (global columns, non-decreasing within an instance): the rows of
+// instance k are row0[k] .. row0[k] + rows[k] - 1, and column j is touched by the rows whose
+// start lies in [j - w + 1, j], a contiguous run found by binary search.  inst: 4 x num_inst
+// (cols, col0, row0, rows).
+__device__ __forceinline__ int64_t inst_of_col(const int64_t* inst, int64_t num_inst, int64_t gj) {
+  const int64_t* col0 = inst + num_inst;
+  int64_t lo = 0, hi = num_inst - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (col0[mid] <= gj) lo = mid; else hi = mid - 1;
+  }
+  return lo;
+}
+// First row of [r0, r1) whose start is >= v (starts sorted in that range).
+__device__ __forceinline__ int64_t first_row_at(const int64_t* start, int64_t r0, int64_t r1, int64_t v) {
+  while (r0 < r1) {
+    const int64_t mid = r0 + (r1 - r0) / 2;
+    if (start[mid] < v) r0 = mid + 1; else r1 = mid;
+  }
+  return r0;
+}
+
+// D_j = || column j of J || (zero -> 1), one thread per global column, rows in order.
+template <typename T>
+__global__ void band_colnorm_explicit_kernel(const T* J, const int64_t* start, const int64_t* inst,
+                                             int64_t num_inst, int64_t total_cols, int w, double* D) {
+  const int64_t gj = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gj >= total_cols) return;
+  const int64_t k = inst_of_col(inst, num_inst, gj);
+  const int64_t r0 = inst[2 * num_inst + k], r1 = r0 + inst[3 * num_inst + k];
+  double acc = 0.0;
+  for (int64_t i = first_row_at(start, r0, r1, gj - w + 1); i < r1 && start[i] <= gj; ++i) {
+    const double v = (double)J[i * w + (gj - start[i])];
+    acc += v * v;
+  }
+  const double d = sqrt(acc);
+  D[gj] = d == 0.0 ? 1.0 : d;
+}
+
+// r_i = b_i - sum_t J_it x_{start_i + t} in double (entries past the instance's last column are
+// ignored), one thread per row.
+template <typename T>
+__global__ void band_resid_explicit_kernel(const T* J, const T* b, const T* x, const int64_t* start,
+                                           const int64_t* inst, int64_t num_inst, int64_t total_rows, int w,
+                                           double* r) {
+  const int64_t gi = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gi >= total_rows) return;
+  const int64_t* row0 = inst + 2 * num_inst;
+  int64_t lo = 0, hi = num_inst - 1;
+  while (lo < hi) {
+    const int64_t mid = (lo + hi + 1) / 2;
+    if (row0[mid] <= gi) lo = mid; else hi = mid - 1;
+  }
+  const int64_t end = inst[num_inst + lo] + inst[lo];   // one past the instance's last column
+  double acc = (double)b[gi];
+  for (int t = 0; t < w && start[gi] + t < end; ++t) acc -= (double)J[gi * w + t] * (double)x[start[gi] + t];
+  r[gi] = acc;
+}
+
+// g_j = sum_i J_ij r_i - lambda D_j^2 x_j, one thread per global column, rows in order.
+template <typename T>
+__global__ void band_g_explicit_kernel(const T* J, const T* x, const double* r, const double* D, double lam,
+                                       const int64_t* start, const int64_t* inst, int64_t num_inst,
+                                       int64_t total_cols, int w, double* g) {
+  const int64_t gj = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (gj >= total_cols) return;
+  const int64_t k = inst_of_col(inst, num_inst, gj);
+  const int64_t r0 = inst[2 * num_inst + k], r1 = r0 + inst[3 * num_inst + k];
+  double acc = 0.0;
+  for (int64_t i = first_row_at(start, r0, r1, gj - w + 1); i < r1 && start[i] <= gj; ++i)
+    acc += (double)J[i * w + (gj - start[i])] * r[i];
+  if (lam > 0.0) acc -= lam * D[gj] * D[gj] * (double)x[gj];
+  g[gj] = acc;
+}
+
 template <typename T>
 __global__ void band_axpy_kernel(T* x, const T* d, int64_t n) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
@@ -576,13 +651,42 @@ qrkit_status banded_plan(qrkit_ctx* ctx, const qrkit_structure* s) {
   }
   for (size_t i = 0; i < cols.size(); ++i)
     if (cols[i] < 1) return fail(ctx, QRKIT_EINVAL, "instance " + std::to_string(i) + " has no columns");
+  // rows per instance: rows_per_col * cols, or given with explicit row starts
+  const bool expl = s->band_row_start != nullptr;
+  std::vector<int64_t> nrows(cols.size());
+  for (size_t i = 0; i < cols.size(); ++i) {
+    if (!expl) {
+      nrows[i] = cols[i] * s->rows_per_col;
+    } else if (s->instance_rows) {
+      nrows[i] = s->instance_rows[i];
+    } else if (cols.size() == 1) {
+      nrows[i] = s->rows;
+    } else {
+      return fail(ctx, QRKIT_EINVAL, "instance_rows is required with band_row_start and a batch of instances");
+    }
+    if (nrows[i] < 0) return fail(ctx, QRKIT_EINVAL, "instance " + std::to_string(i) + " has a negative row count");
+  }
   std::vector<int64_t> c0(cols.size()), r0(cols.size());
   int64_t cc = 0, rr = 0;
   for (size_t i = 0; i < cols.size(); ++i) {
     c0[i] = cc;
     r0[i] = rr;
     cc += cols[i];
-    rr += cols[i] * s->rows_per_col;
+    rr += nrows[i];
+  }
+  std::vector<int64_t> gstart;
+  if (expl) {
+    gstart.resize((size_t)rr);
+    for (size_t i = 0; i < cols.size(); ++i)
+      for (int64_t k = 0; k < nrows[i]; ++k) {
+        const int64_t v = s->band_row_start[r0[i] + k];
+        if (v < 0 || v >= cols[i])
+          return fail(ctx, QRKIT_EINVAL, "row " + std::to_string(r0[i] + k) + " starts outside its instance");
+        if (k > 0 && v < s->band_row_start[r0[i] + k - 1])
+          return fail(ctx, QRKIT_EINVAL, "row starts must not decrease within an instance (row " +
+                                             std::to_string(r0[i] + k) + ")");
+        gstart[(size_t)(r0[i] + k)] = c0[i] + v;
+      }
   }
   Band& B = ctx->band;
   if (s->band_solver < QRKIT_BAND_AUTO || s->band_solver > QRKIT_BAND_PARALLEL)
@@ -595,6 +699,7 @@ qrkit_status banded_plan(qrkit_ctx* ctx, const qrkit_structure* s) {
   B.total_rows = rr;
   B.rows_per_col = s->rows_per_col;
   B.w = s->band_window;
+  B.explicit_starts = expl;
   qrkit_status st;
   auto up = [&](DevBuf& buf, const std::vector<int64_t>& v) -> qrkit_status {
     qrkit_status r = ensure(ctx, buf, v.size() * sizeof(int64_t), "band plan");
@@ -605,25 +710,52 @@ qrkit_status banded_plan(qrkit_ctx* ctx, const qrkit_structure* s) {
   if ((st = up(B.d_cols, cols)) != QRKIT_OK) return st;
   if ((st = up(B.d_col0, c0)) != QRKIT_OK) return st;
   if ((st = up(B.d_row0, r0)) != QRKIT_OK) return st;
+  if (expl) {
+    std::vector<int64_t> inst(cols);
+    inst.insert(inst.end(), c0.begin(), c0.end());
+    inst.insert(inst.end(), r0.begin(), r0.end());
+    inst.insert(inst.end(), nrows.begin(), nrows.end());
+    if ((st = up(B.d_inst, inst)) != QRKIT_OK) return st;
+    if ((st = up(B.d_rows, nrows)) != QRKIT_OK) return st;
+    if (rr > 0 && (st = up(B.d_start, gstart)) != QRKIT_OK) return st;
+  }
   const size_t es = elem_size(ctx);
   if ((st = ensure(ctx, B.Rw, (size_t)cc * B.w * es, "banded R")) != QRKIT_OK) return st;
   if ((st = ensure(ctx, B.c, (size_t)cc * es, "banded c")) != QRKIT_OK) return st;
   if ((st = ensure(ctx, B.D, (size_t)cc * sizeof(double), "banded D")) != QRKIT_OK) return st;
   if ((st = ensure(ctx, B.res2, (size_t)B.num_inst * sizeof(double), "banded residual")) != QRKIT_OK) return st;
   if (B.parallel) {
-    std::vector<int64_t> rows(cols.size());
-    for (size_t i = 0; i < cols.size(); ++i) rows[i] = cols[i] * s->rows_per_col;
-    if ((st = cr_build(ctx, B.cr, cols, c0, r0, rows)) != QRKIT_OK) return st;
+    if ((st = cr_build(ctx, B.cr, cols, c0, r0, nrows)) != QRKIT_OK) return st;
+  }
+  if (B.parallel || expl) {
     if ((st = ensure(ctx, B.g, (size_t)cc * sizeof(double), "banded g")) != QRKIT_OK) return st;
     if ((st = ensure(ctx, B.h, (size_t)cc * es, "banded h")) != QRKIT_OK) return st;
-    if ((st = ensure(ctx, B.r, (size_t)rr * sizeof(double), "banded r")) != QRKIT_OK) return st;
+    if ((st = ensure(ctx, B.r, (size_t)std::max<int64_t>(rr, 1) * sizeof(double), "banded r")) != QRKIT_OK) return st;
   }
   P.s = *s;
   P.s.block_rows = nullptr;
   P.s.block_cols = nullptr;
   P.s.window_start = nullptr;
   P.s.instance_cols = nullptr;
+  P.s.band_row_start = nullptr;
+  P.s.instance_rows = nullptr;
   P.valid = true;
+  return QRKIT_OK;
+}
+
+template <typename T>
+__global__ void band_g_to_t_kernel(const double* g, T* h, int64_t n) {
+  const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) h[i] = (T)g[i];
+}
+
+static qrkit_status widen_or_narrow_g(qrkit_ctx* ctx, const double* g, void* h, int64_t n) {
+  if (ctx->precision == QRKIT_FP64)
+    band_g_to_t_kernel<double><<<nblk(n, 256), 256, 0, ctx->stream>>>(g, (double*)h, n);
+  else
+    band_g_to_t_kernel<float><<<nblk(n, 256), 256, 0, ctx->stream>>>(g, (float*)h, n);
+  ctx->launches += 1;
+  QRKIT_CUDA_TRY(ctx, cudaGetLastError());
   return QRKIT_OK;
 }
 
@@ -645,6 +777,12 @@ static qrkit_status banded_run(qrkit_ctx* ctx, const void* J, const void* b, con
         qrkit_status rc = widen_to_double(ctx, (const float*)Dext, D, B.total_cols);
         if (rc != QRKIT_OK) return rc;
       }
+    } else if (B.explicit_starts) {
+      band_colnorm_explicit_kernel<T><<<nblk(B.total_cols, 256), 256, 0, st>>>(
+          (const T*)J, (const int64_t*)B.d_start.ptr, (const int64_t*)B.d_inst.ptr, B.num_inst, B.total_cols, B.w,
+          D);
+      ctx->launches += 1;
+      QRKIT_CUDA_TRY(ctx, cudaGetLastError());
     } else {
       if (sizeof(T) == sizeof(float)) {
         const int rw = B.rows_per_col * B.w;
@@ -659,6 +797,40 @@ static qrkit_status banded_run(qrkit_ctx* ctx, const void* J, const void* b, con
       ctx->launches += 1;
       QRKIT_CUDA_TRY(ctx, cudaGetLastError());
     }
+  }
+  if (B.explicit_starts) {
+    // rows with explicit starts (e.g. the row and column permutations of Sec. 4.3 applied):
+    // the parallel QR or the sweep, then refinement with a double residual
+    const int64_t* gs = (const int64_t*)B.d_start.ptr;
+    const int64_t* inst = (const int64_t*)B.d_inst.ptr;
+    qrkit_status rc;
+    if (B.parallel) {
+      rc = cr_solve(ctx, *B.cr, gs, 1, B.w, J, b, D, lambda, p, (double*)B.res2.ptr);
+    } else {
+      rc = banded_explicit_solve(ctx, B.num_inst, inst, J, gs, b, B.w, D, lambda, B.Rw.ptr, B.c.ptr, p,
+                                 (double*)B.res2.ptr);
+    }
+    if (rc != QRKIT_OK) return rc;
+    for (int it = 0; it < refine_steps; ++it) {
+      band_resid_explicit_kernel<T><<<nblk(std::max<int64_t>(B.total_rows, 1), 256), 256, 0, st>>>(
+          (const T*)J, (const T*)b, (const T*)p, gs, inst, B.num_inst, B.total_rows, B.w, (double*)B.r.ptr);
+      band_g_explicit_kernel<T><<<nblk(B.total_cols, 256), 256, 0, st>>>(
+          (const T*)J, (const T*)p, (const double*)B.r.ptr, D, lambda, gs, inst, B.num_inst, B.total_cols, B.w,
+          (double*)B.g.ptr);
+      ctx->launches += 2;
+      QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+      if (B.parallel) {
+        if ((rc = cr_normal_solve(ctx, *B.cr, (const double*)B.g.ptr, B.h.ptr)) != QRKIT_OK) return rc;
+      } else {
+        if ((rc = widen_or_narrow_g(ctx, (const double*)B.g.ptr, B.h.ptr, B.total_cols)) != QRKIT_OK) return rc;
+        if ((rc = banded_tri_solve(ctx, B.num_inst, inst, B.Rw.ptr, B.w, B.h.ptr, true)) != QRKIT_OK) return rc;
+        if ((rc = banded_tri_solve(ctx, B.num_inst, inst, B.Rw.ptr, B.w, B.h.ptr, false)) != QRKIT_OK) return rc;
+      }
+      band_axpy_kernel<T><<<nblk(B.total_cols, 256), 256, 0, st>>>((T*)p, (const T*)B.h.ptr, B.total_cols);
+      ctx->launches += 1;
+      QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+    }
+    return QRKIT_OK;
   }
   if (B.parallel) {
     qrkit_status rc = cr_solve(ctx, *B.cr, nullptr, B.rows_per_col, B.w, J, b, D, lambda, p,
@@ -814,6 +986,7 @@ qrkit_status banded_get_factor(qrkit_ctx* ctx, void* Rw_out, void* c_out, double
 
 void release_band(Band& B) {
   release(B.d_cols); release(B.d_col0); release(B.d_row0); release(B.Rw); release(B.c);
+  release(B.d_inst); release(B.d_rows); release(B.d_start);
   release(B.D); release(B.res2); release(B.g); release(B.h); release(B.r);
   release_cr(B.cr);
   B = Band();

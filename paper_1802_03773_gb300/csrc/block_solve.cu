@@ -34,6 +34,7 @@ constexpr int kThreads = 256;  // threads per CTA
 constexpr float kUnitRoundoff = 5.9604645e-8f;   // 2^-24
 constexpr float kRefineTarget = 1e-6f;           // blocks estimated above this are refined
 constexpr int kKeys = 36;      // sort keys: 4 row classes x (m = 0..8)
+constexpr long long kDrainPolls = 1LL << 26;   // polls of the wait for a CTA's own copies after a timeout
 static_assert(kKeys <= 64, "the bin scan handles at most 64 keys");
 
 template <typename T> struct Vec16;
@@ -602,9 +603,9 @@ block_solve_kernel(BlockSolveArgs<T> A) {
   }
   if (__syncthreads_or(!ok)) {
     if (tid == 0) record(A.status, QRKIT_ETIMEOUT);
-    // the bulk loads may still be in flight: wait for them once more (bounded) before the
-    // CTA's shared memory is given up
-    for (long long polls = 0; polls < A.wait_limit; ++polls)
+    // the bulk loads may still be in flight: wait for them once more, with a limit of its own
+    // (the first limit may be as small as zero), before the CTA's shared memory is given up
+    for (long long polls = 0; polls < kDrainPolls; ++polls)
       if (mbar_try_wait(bar, 0u)) break;
     return;
   }
@@ -834,7 +835,7 @@ qrkit_status launch_typed(qrkit_ctx* ctx, const void* J, const void* b, void* p,
   A.cb = P.budget.cols;
   A.bb = P.budget.blocks;
   A.pb = P.budget.padded;
-  A.wait_limit = 1LL << 26;
+  A.wait_limit = ctx->wait_limit;
   A.rlist = nullptr;
   A.rcount = nullptr;
   A.rcap = 0;

@@ -341,6 +341,13 @@ qrkit_status qrkit_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, co
   return st;
 }
 
+qrkit_status qrkit_set_wait_limit(qrkit_ctx* ctx, int64_t polls) {
+  if (!ctx) return QRKIT_EINVAL;
+  if (polls < 0) return fail(ctx, QRKIT_EINVAL, "polls must be >= 0");
+  ctx->wait_limit = polls;
+  return QRKIT_OK;
+}
+
 qrkit_status qrkit_set_refinement(qrkit_ctx* ctx, double select, int residual) {
   if (!ctx) return QRKIT_EINVAL;
   if (!(select >= 0.0 && select <= 1.0)) return fail(ctx, QRKIT_EINVAL, "select must be in [0, 1]");

@@ -149,8 +149,10 @@ struct Band {
   int64_t num_inst = 0, total_cols = 0, total_rows = 0;
   int rows_per_col = 1, w = 1;
   bool parallel = false;          // QRKIT_BAND_PARALLEL in effect
+  bool explicit_starts = false;   // rows carry explicit starts (band_row_start)
   CRPlan* cr = nullptr;
   DevBuf d_cols, d_col0, d_row0, Rw, c, D, res2, g, h, r;
+  DevBuf d_inst, d_rows, d_start;   // explicit starts: 4 x num_inst table, rows, global starts
 };
 
 struct TsqrLevel {
@@ -237,6 +239,7 @@ struct qrkit_ctx {
   size_t smem_attr[16] = {};   // dynamic smem opted in, per kernel variant (slot per kernel)
   int occ_threads[16] = {};    // threads and resident CTAs per SM at that size (warp-task kernels)
   int occ_per_sm[16] = {};
+  long long wait_limit = 1LL << 26;  // polls of a bounded device wait before it gives up
   float refine_select = 2e-6f;  // block refinement: a-priori error estimate that selects a block
   int refine_residual = 0;      // its residual precision: 0 compensated float, 1 double
   bool factored = false;       // fused block path

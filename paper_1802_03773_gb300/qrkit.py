@@ -51,6 +51,8 @@ class Structure(ctypes.Structure):
         ("segment_cols", ctypes.c_void_p),
         ("segment_blocks", ctypes.c_void_p),
         ("band_solver", ctypes.c_int32),
+        ("band_row_start", ctypes.c_void_p),
+        ("instance_rows", ctypes.c_void_p),
     ]
 
 
@@ -92,6 +94,7 @@ _SIGS = {
     "qrkit_factor_solve": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double, _VP, _VP, ctypes.c_int]),
     "qrkit_get_factor": (ctypes.c_int, [_VP, _VP, _VP]),
     "qrkit_set_refinement": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int]),
+    "qrkit_set_wait_limit": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "qrkit_get_band_factor": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "qrkit_factor": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double]),
     "qrkit_apply_qt": (ctypes.c_int, [_VP, _VP, _VP]),
@@ -303,7 +306,10 @@ class Context:
         """order: int64 CUDA tensor, one entry per reduced row."""
         self._check(self.lib.qrkit_get_row_order(self.h, _ptr(order)))
 
-    def plan_banded(self, instance_cols, rows_per_col=4, window=8, solver=BAND_AUTO):
+    def plan_banded(self, instance_cols, rows_per_col=4, window=8, solver=BAND_AUTO, row_start=None,
+                    instance_rows=None):
+        """row_start: optional explicit first column of every row (instances back to back, local
+        columns, non-decreasing per instance); instance_rows: rows per instance with it."""
         cols = np.ascontiguousarray(np.atleast_1d(instance_cols), dtype=np.int64)
         s = Structure()
         s.kind = STRUCT_BANDED
@@ -313,8 +319,16 @@ class Context:
         s.rows_per_col = int(rows_per_col)
         s.band_window = int(window)
         s.band_solver = int(solver)
+        rs = ir = None
+        if row_start is not None:
+            rs = np.ascontiguousarray(row_start, dtype=np.int32)
+            s.band_row_start = rs.ctypes.data if rs.size else None
+            s.rows = int(rs.shape[0])
+            if instance_rows is not None:
+                ir = np.ascontiguousarray(np.atleast_1d(instance_rows), dtype=np.int64)
+                s.instance_rows = ir.ctypes.data
         self._check(self.lib.qrkit_plan(self.h, ctypes.byref(s)))
-        self._keep = [cols]
+        self._keep = [cols, rs, ir]
 
     def get_band_factor(self, Rw=None, c=None, res2=None):
         """res2: a numpy float64 array (one entry per instance) or None."""
@@ -332,6 +346,10 @@ class Context:
         """Block refinement settings: selection threshold and residual precision ("dot2" or "fp64")."""
         mode = {"dot2": RESIDUAL_DOT2, "fp64": RESIDUAL_FP64}[residual] if isinstance(residual, str) else int(residual)
         self._check(self.lib.qrkit_set_refinement(self.h, float(select), mode))
+
+    def set_wait_limit(self, polls):
+        """Poll limit of the bounded device waits (0 makes them run out: QRKIT_ETIMEOUT)."""
+        self._check(self.lib.qrkit_set_wait_limit(self.h, int(polls)))
 
     def factor(self, J, S=None, D=None, lam=0.0):
         self._check(self.lib.qrkit_factor(self.h, self._t(J, "J"), self._t(S, "S", True),

@@ -118,3 +118,18 @@ def block_kappa(d):
         s = np.linalg.svd(A, compute_uv=False)
         kap[sel] = s[:, 0] / s[:, -1]
     return kap
+
+
+def assert_close(p, p_ref, tol, floor=1e-3, what=""):
+    """The solution p against the oracle's p_ref: relative 2-norm error <= tol, and every
+    component within tol (|p*_i| + floor ||p*||_inf), so that the small components of a
+    badly scaled solution are weighed too.  Returns the relative 2-norm error."""
+    p = np.asarray(p, dtype=np.float64)
+    p_ref = np.asarray(p_ref, dtype=np.float64)
+    e = np.linalg.norm(p - p_ref) / np.linalg.norm(p_ref)
+    assert e <= tol, f"{what}relative error {e:.3e} > {tol:.1e}"
+    lim = tol * (np.abs(p_ref) + floor * np.abs(p_ref).max())
+    bad = np.nonzero(~(np.abs(p - p_ref) <= lim))[0]
+    assert bad.size == 0, (f"{what}{bad.size} components outside tol (|p*| + {floor:g} ||p*||_inf), e.g. "
+                           f"{int(bad[0])}: {p[bad[0]]!r} vs {p_ref[bad[0]]!r}")
+    return e

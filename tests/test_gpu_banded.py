@@ -4,7 +4,7 @@ import pytest
 
 from oracle import banded as bd
 from oracle import householder as hh
-from tests.gpu_common import cuda_or_skip
+from tests.gpu_common import assert_close, cuda_or_skip
 from workloads import banded_problem
 
 pytestmark = pytest.mark.gpu
@@ -85,7 +85,7 @@ def test_banded_fp32_refined_matches_oracle(solver):
     cols = [500, 1200, 77]
     out = run(cols, 4, 8, "fp32_refined", lam=1e-3, refine_steps=2, solver=solver)
     x, _, _ = oracle_solutions(out["inst"], 1e-3)
-    assert np.linalg.norm(out["p"] - x) / np.linalg.norm(x) <= 1e-5
+    assert_close(out["p"], x, 1e-5)
 
 
 @pytest.mark.parametrize("solver", ["sweep", "parallel"])
@@ -126,14 +126,14 @@ def test_banded_batch_scaled_sampled(solver):
         d = out["inst"][k]
         x, *_ = bd.damped_solve(d["start"], d["vals"], d["b"], d["n"], 1e-3)
         got = out["p"][off[k]:off[k + 1]]
-        assert np.linalg.norm(got - x) / np.linalg.norm(x) <= 1e-5
+        assert_close(got, x, 1e-5)
 
 
 def test_banded_parallel_large_instance():
     """One instance of 100,000 columns (400,000 rows): matches the oracle to 1e-5."""
     out = run([100000], 4, 8, "fp32_refined", lam=1e-3, refine_steps=2, solver="parallel", seed=9)
     x, _, _ = oracle_solutions(out["inst"], 1e-3)
-    assert np.linalg.norm(out["p"] - x) / np.linalg.norm(x) <= 1e-5
+    assert_close(out["p"], x, 1e-5)
 
 
 @pytest.mark.slow
@@ -216,7 +216,7 @@ def test_banded_batch_full_size_4096_instances():
         start = np.arange(r1 - r0, dtype=np.int64) // 4
         x, *_ = bd.damped_solve(start, vals, b, n, 1e-3)
         got = p[c0:c0 + n].cpu().numpy().astype(np.float64)
-        assert np.linalg.norm(got - x) / np.linalg.norm(x) <= 1e-5
+        assert_close(got, x, 1e-5)
 
 
 def test_banded_batch_solve_replays_in_cuda_graph():

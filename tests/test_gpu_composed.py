@@ -4,7 +4,7 @@ import pytest
 
 from oracle import householder as hh
 from oracle import structured as st
-from tests.gpu_common import cuda_or_skip
+from tests.gpu_common import assert_close, cuda_or_skip
 from workloads import block_angular_dense
 
 pytestmark = pytest.mark.gpu
@@ -62,8 +62,8 @@ def test_dense_hcat_fp64_matches_oracle():
     P = problem_from(d)
     p_ref, F = st.factor_and_solve(P)
     out = run(d, "fp64", refine_steps=0)
-    assert rel(out["p"], p_ref) <= 1e-12
-    assert rel(out["p_norefine"], p_ref) <= 1e-12
+    assert_close(out["p"], p_ref, 1e-12)
+    assert_close(out["p_norefine"], p_ref, 1e-12)
     # Q^T b top entries equal the oracle's up to the sign of each R row
     K, m, s = d["K"], d["m"], d["s"]
     c_ref = np.concatenate(F.c_blocks + [F.c_S])
@@ -80,7 +80,7 @@ def test_dense_hcat_fp32_refined_matches_oracle():
     P = problem_from(d)
     p_ref, _ = st.factor_and_solve(P)
     out = run(d, "fp32_refined", refine_steps=2)
-    assert rel(out["p"], p_ref) <= 1e-5
+    assert_close(out["p"], p_ref, 1e-5)
     assert rel(out["p"], p_ref) < rel(out["p_norefine"], p_ref)
 
 
@@ -92,12 +92,12 @@ def test_dense_hcat_given_D_and_no_damping():
     P.D = D
     p_ref, _ = st.factor_and_solve(P)
     out = run(d, "fp64", refine_steps=0, D=D)
-    assert rel(out["p"], p_ref) <= 1e-12
+    assert_close(out["p"], p_ref, 1e-12)
     P0 = problem_from(d)
     P0.lam = 0.0
     p0, _ = st.factor_and_solve(P0)
     out0 = run(d, "fp64", refine_steps=0, lam=0.0)
-    assert rel(out0["p"], p0) <= 1e-11
+    assert_close(out0["p"], p0, 1e-11)
 
 
 def test_dense_hcat_many_tsqr_levels():
@@ -106,7 +106,7 @@ def test_dense_hcat_many_tsqr_levels():
     P = problem_from(d)
     p_ref, _ = st.factor_and_solve(P)
     out = run(d, "fp64", refine_steps=0)
-    assert rel(out["p"], p_ref) <= 1e-11
+    assert_close(out["p"], p_ref, 1e-11)
 
 
 @pytest.mark.parametrize("s,K", [(128, 300), (96, 257), (128, 2000)])
@@ -121,9 +121,9 @@ def test_dense_tensor_core_tiles_fp32_refined(s, K):
     d32["b"] = np.asarray(d["b"], np.float32).astype(np.float64)
     p_ref, _ = st.factor_and_solve(problem_from(d32))
     out = run(d32, "fp32_refined", refine_steps=2)
-    assert rel(out["p"], p_ref) <= 1e-5
+    assert_close(out["p"], p_ref, 1e-5)
     out0 = run(d32, "fp32", refine_steps=0)
-    assert rel(out0["p"], p_ref) <= 1e-3
+    assert_close(out0["p"], p_ref, 1e-3)
 
 
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_refined", 1e-5)])
@@ -167,5 +167,5 @@ def test_dense_hcat_solve_replays_in_cuda_graph(precision, tol):
         stream.synchronize()
         ctx.sync_status()
         p_ref, _ = st.factor_and_solve(problem_from(d))
-        assert rel(p.cpu().numpy().astype(np.float64), p_ref) <= tol
+        assert_close(p.cpu().numpy().astype(np.float64), p_ref, tol)
     ctx.close()

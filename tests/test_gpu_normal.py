@@ -9,7 +9,7 @@ from oracle import curvefit as cf
 from oracle import lm
 from oracle import normal as nrm
 from oracle import structured as st
-from tests.gpu_common import cuda_or_skip
+from tests.gpu_common import assert_close, cuda_or_skip
 from tests.test_gpu_composed import packed, problem_from, rel
 from workloads import block_angular_dense, curvefit_problem
 
@@ -48,7 +48,7 @@ def test_normal_dense_fp64_matches_oracle_cholesky():
     p = normal_gpu("fp64", plan, J, S, b, P.N, P.lam)
     Jd = st.assemble_J(P)
     p_ref = nrm.solve(Jd, np.asarray(P.b), st.damping(P), P.lam)
-    assert rel(p, p_ref) <= 1e-10
+    assert_close(p, p_ref, 1e-10)
 
 
 def test_normal_window_fp64_matches_oracle_cholesky():
@@ -63,7 +63,7 @@ def test_normal_window_fp64_matches_oracle_cholesky():
                                        window=8, window_start=np.asarray(Pb.start, dtype=np.int32))
     p = normal_gpu("fp64", plan, J, S, np.asarray(Pb.b), Pb.N, Pb.lam)
     p_ref = nrm.solve(st.assemble_J(Pb), np.asarray(Pb.b), st.damping(Pb), Pb.lam)
-    assert rel(p, p_ref) <= 1e-9
+    assert_close(p, p_ref, 1e-9)
 
 
 def test_normal_blocks_only_fp64():
@@ -79,7 +79,7 @@ def test_normal_blocks_only_fp64():
     plan = lambda ctx: ctx.plan_blocks(n, m)
     p = normal_gpu("fp64", plan, J, None, b, P.N, P.lam)
     p_ref = nrm.solve(st.assemble_J(P), b, st.damping(P), P.lam)
-    assert rel(p, p_ref) <= 1e-10
+    assert_close(p, p_ref, 1e-10)
 
 
 def test_normal_fp32_loses_cond_squared():
