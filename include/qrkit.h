@@ -157,13 +157,17 @@ qrkit_status qrkit_plan(qrkit_ctx* ctx, const qrkit_structure* s);
  * QRKIT_FP32 and QRKIT_FP64.
  *   J    : packed values, block i column-major n_i x m_i, blocks in order (sum n_i m_i)
  *   b    : sum n_i values, block i's rows contiguous
- *   D    : reserved, pass NULL
- *   lambda : must be 0 on this fused path (damped blocks go through qrkit_factor)
+ *   D    : with lambda > 0, sum m_i damping values or NULL for the column norms of J (zero ->
+ *          1); ignored when lambda = 0
+ *   lambda : >= 0.  lambda > 0 takes Moré's two factorizations (Sec. 5.2, Eq. LMTwoStep): the
+ *          undamped QR above (refine_steps ignored, no refinement: float accuracy in the
+ *          float modes), then qrkit_more_solve's second factorization per block; every block
+ *          needs n_i >= m_i.  (The composed path, qrkit_factor with lambda > 0, refines.)
  *   p    : out, sum m_i values
  *   qtb  : out or NULL; sum n_i values: Q_i^T b_i per block
  * The factor (reflectors below the diagonal, R on and above it, tau) stays in the context.
- * One kernel launch (two in FP32 refined mode; banded plans: the banded factor + solve and
- * its refinement); asynchronous on the context's stream. */
+ * One kernel launch (two in FP32 refined mode or with lambda > 0; banded plans: the banded
+ * factor + solve and its refinement); asynchronous on the context's stream. */
 qrkit_status qrkit_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,
                                 double lambda, void* p, void* qtb, int refine_steps);
 
@@ -175,6 +179,23 @@ qrkit_status qrkit_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, co
  * (down to 0) makes the waits run out on purpose, which tests that failure path without a
  * GPU fault.  QRKIT_EINVAL for polls < 0. */
 qrkit_status qrkit_set_wait_limit(qrkit_ctx* ctx, int64_t polls);
+
+/* Moré's second factorization (Sec. 5.2, Eq. LMTwoStep) for the block-diagonal factor of the
+ * last qrkit_factor_solve: with J_i = Q_i R_i kept, each damping value needs only, per block,
+ * the QR of [R_i; lambda^(1/2) D_i] with the damping row of column k placed after row k of
+ * R_i (the interleave of Sec. 4.5) and R'_i p_i = top of Q'_i^T [c_i; 0], c_i = the top m_i
+ * entries of Q_i^T b_i.  Since ||J_i p - b_i||^2 = ||R_i p - c_i||^2 + const, p_i minimises
+ * ||J_i p - b_i||^2 + lambda ||D_i p||^2 (Eq. 2).  Call it once per damping value of an LM
+ * iteration (rejected steps cost only this).
+ *   qtb    : DEVICE, sum n_i values: the Q^T b that qrkit_factor_solve wrote (lambda = 0)
+ *   D      : DEVICE, sum m_i values, or NULL for the column norms of J (computed as those of
+ *            R_i, equal since Q_i is orthogonal; zero -> 1)
+ *   lambda : >= 0 (0 gives the undamped solution again)
+ *   p      : DEVICE out, sum m_i values
+ * One thread per block, the stack reduced by 2 x 2 reflections of the damping row against the
+ * rows of R_i; no refinement.  A zero pivot is reported as QRKIT_ESINGULAR in the device status
+ * word.  Asynchronous. */
+qrkit_status qrkit_more_solve(qrkit_ctx* ctx, const void* qtb, const void* D, double lambda, void* p);
 
 /* Residual precision of the block refinement (qrkit_set_refinement). */
 enum { QRKIT_RESIDUAL_DOT2 = 0, QRKIT_RESIDUAL_FP64 = 1 };

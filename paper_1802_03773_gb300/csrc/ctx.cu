@@ -284,6 +284,7 @@ void qrkit_destroy(qrkit_ctx* ctx) {
   release(ctx->ws.tfactor);
   release(ctx->ws.ttau);
   release(ctx->ws.rrec);
+  release(ctx->ws.qtb);
   if (ctx->d_status) cudaFree(ctx->d_status);
   delete ctx;
 }
@@ -326,19 +327,43 @@ qrkit_status qrkit_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, co
   ctx->comp_factored = false;
   if (!J || !b || !p) return fail(ctx, QRKIT_EINVAL, "J, b and p are required");
   if (!(lambda >= 0.0)) return fail(ctx, QRKIT_EINVAL, "lambda must be >= 0");
-  if (lambda > 0.0)
-    return fail(ctx, QRKIT_EUNSUPPORTED, "damping rows on the fused block path are not available yet");
   if (refine_steps < 0 || refine_steps > 8) return fail(ctx, QRKIT_EINVAL, "refine_steps must be in [0, 8]");
   if (P.first_wide >= 0)
-    return fail(ctx, QRKIT_EINVAL, "block " + std::to_string(P.first_wide) +
-                " has fewer rows than columns and lambda = 0");
+    return fail(ctx, QRKIT_EINVAL, "block " + std::to_string(P.first_wide) + " has fewer rows than columns");
   QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  if (lambda > 0.0) {
+    // Moré's two factorizations (Sec. 5.2): the undamped fused QR (its Q^T b kept), then the
+    // QR of [R_i; lambda^(1/2) D_i] per block; no refinement on this path
+    void* q = qtb;
+    if (!q) {
+      qrkit_status r = ensure(ctx, ctx->ws.qtb, (size_t)P.rows * elem_size(ctx), "damped solve Q^T b");
+      if (r != QRKIT_OK) return r;
+      q = ctx->ws.qtb.ptr;
+    }
+    qrkit_status st = launch_block_solve(ctx, J, b, nullptr, p, q, 0);
+    if (st != QRKIT_OK) return st;
+    ctx->factored = true;
+    ctx->factor_in_planes = ctx->plan.mapping == 0 && ctx->plan.num_tasks > 0;
+    return more_stage2(ctx, q, D, lambda, p);
+  }
   qrkit_status st = launch_block_solve(ctx, J, b, D, p, qtb, refine_steps);
   if (st == QRKIT_OK) {
     ctx->factored = true;
     ctx->factor_in_planes = ctx->plan.mapping == 0 && ctx->plan.num_tasks > 0;
   }
   return st;
+}
+
+qrkit_status qrkit_more_solve(qrkit_ctx* ctx, const void* qtb, const void* D, double lambda, void* p) {
+  if (!ctx) return QRKIT_EINVAL;
+  const Plan& P = ctx->plan;
+  if (!P.valid || P.s.kind != QRKIT_STRUCT_BLOCKS || P.s.coupled_kind != QRKIT_COUPLED_NONE)
+    return fail(ctx, QRKIT_ESTATE, "qrkit_more_solve needs a block-diagonal plan");
+  if (!ctx->factored) return fail(ctx, QRKIT_ESTATE, "qrkit_more_solve before qrkit_factor_solve");
+  if (!qtb || !p) return fail(ctx, QRKIT_EINVAL, "qtb and p are required");
+  if (!(lambda >= 0.0)) return fail(ctx, QRKIT_EINVAL, "lambda must be >= 0");
+  QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  return more_stage2(ctx, qtb, D, lambda, p);
 }
 
 qrkit_status qrkit_set_wait_limit(qrkit_ctx* ctx, int64_t polls) {

@@ -217,6 +217,7 @@ struct Workspace {
   DevBuf tlist, tcount;   // the same for the warp-task kernels (one list per shape key)
   DevBuf tfactor, ttau;   // factor and tau of the warp-task kernels in task planes
   DevBuf rrec;            // refinement records (J and b of the selected blocks)
+  DevBuf qtb;             // Q^T b of a damped fused solve (Moré's stage 1)
 };
 
 }  // namespace qrkit
@@ -308,6 +309,9 @@ constexpr int64_t kDefaultSupertile = 65536;
 qrkit_status build_block_tasks(qrkit_ctx* ctx, int64_t supertile, int warps, bool key_major);
 qrkit_status launch_block_tasks(qrkit_ctx* ctx, const void* J, const void* b, void* p, void* qtb,
                                 int refine_steps);
+// Moré's stage 2 (Sec. 5.2) for the stored block factor: p from [R_i; lambda^(1/2) D_i] and the
+// top m_i entries of qtb per block (D null: column norms of R_i).
+qrkit_status more_stage2(qrkit_ctx* ctx, const void* qtb, const void* D, double lambda, void* p);
 // The warp-task factor (task planes) copied into J's packing and tau into column order.
 qrkit_status unpack_block_tasks_factor(qrkit_ctx* ctx, void* factor_out, void* tau_out);
 void release_block_tasks(Plan& P);

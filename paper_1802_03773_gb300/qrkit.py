@@ -95,6 +95,7 @@ _SIGS = {
     "qrkit_get_factor": (ctypes.c_int, [_VP, _VP, _VP]),
     "qrkit_set_refinement": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int]),
     "qrkit_set_wait_limit": (ctypes.c_int, [_VP, ctypes.c_int64]),
+    "qrkit_more_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, _VP]),
     "qrkit_get_band_factor": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "qrkit_factor": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double]),
     "qrkit_apply_qt": (ctypes.c_int, [_VP, _VP, _VP]),
@@ -346,6 +347,11 @@ class Context:
         """Block refinement settings: selection threshold and residual precision ("dot2" or "fp64")."""
         mode = {"dot2": RESIDUAL_DOT2, "fp64": RESIDUAL_FP64}[residual] if isinstance(residual, str) else int(residual)
         self._check(self.lib.qrkit_set_refinement(self.h, float(select), mode))
+
+    def more_solve(self, qtb, p, D=None, lam=0.0):
+        """Moré's second factorization for the stored block factor (qtb from factor_solve)."""
+        self._check(self.lib.qrkit_more_solve(self.h, self._t(qtb, "qtb"), self._t(D, "D", True), float(lam),
+                                              self._t(p, "p")))
 
     def set_wait_limit(self, polls):
         """Poll limit of the bounded device waits (0 makes them run out: QRKIT_ETIMEOUT)."""
