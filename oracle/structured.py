@@ -320,3 +320,72 @@ def optimality_residual(J, b, D, lam, p) -> float:
         fro = float(np.linalg.norm(J))
     scale = fro * fro * float(np.linalg.norm(p)) + fro * float(np.linalg.norm(b))
     return float(np.linalg.norm(g)) / max(scale, 1e-300)
+
+
+def structural_rows(P: BlockProblem, damped: bool):
+    """The column sets of the rows of [J; lambda^(1/2) D] from the structure alone (Sec. 3, 4.1,
+    4.2, 4.5): a J row of block i touches the block's columns and its coupled columns (all s
+    for a dense S; start_i .. start_i + w - 1 within the s shared columns for a window); the
+    damping row of column j (when damped) touches j.  Source row ids as in row_permutation."""
+    ro, co = P.row_offsets(), P.col_offsets()
+    nb = P.n_block_cols
+    rows = {}
+    for i, blk in enumerate(P.blocks):
+        cols = list(range(int(co[i]), int(co[i + 1])))
+        if P.coupled is not None and P.s > 0:
+            w = P.coupled[i].shape[1]
+            st0 = 0 if P.start is None else int(P.start[i])
+            cols += [nb + c for c in range(st0, min(st0 + w, P.s))]
+        for r in range(blk.shape[0]):
+            rows[int(ro[i]) + r] = cols
+    if damped:
+        for j in range(P.N):
+            rows[P.M + j] = [j]
+    return rows
+
+
+def r_pattern(P: BlockProblem, damped: bool):
+    """Structural non-zero pattern of R for the rows of P_r [J; lambda^(1/2) D] in natural column
+    order, by symbolic row merging (the structure of the row-merge QR of Sec. 5.2 / the oracle
+    O2 description): rows are taken in P_r order; a row whose leading column c has no R row yet
+    becomes R row c, otherwise it is merged with R row c (the 2 x 2 reflection mixes them: R
+    row c takes the union of the two patterns, and the row continues from its next column with
+    that union).  Returns (row_ptr (N + 1), col_idx) with each R row's
+    columns ascending; an R row that no row reaches stays empty."""
+    rows = structural_rows(P, damped)
+    order = [k for k in structural_row_order(P, damped)]
+    R = [None] * P.N
+    for k in order:
+        cur = sorted(set(rows[int(k)]))
+        while cur:
+            c = cur[0]
+            if R[c] is None:
+                R[c] = cur
+                break
+            # the 2 x 2 reflection mixes the two rows: both take the union of the patterns
+            R[c] = sorted(set(R[c]) | set(cur))
+            cur = [x for x in R[c] if x > c]
+    ptr = [0]
+    idx = []
+    for c in range(P.N):
+        if R[c] is not None:
+            idx += R[c]
+        ptr.append(len(idx))
+    return np.array(ptr, dtype=np.int64), np.array(idx, dtype=np.int32)
+
+
+def structural_row_order(P: BlockProblem, damped: bool):
+    """P_r from the structure alone: the J rows of block i lead at the block's first column,
+    the damping row of column j (when damped) at j; sorted stably by (leading column, J rows
+    before damping rows, source index).  Equal to row_permutation when no J row starts with a
+    zero (the tie rule of reading 7)."""
+    ro, co = P.row_offsets(), P.col_offsets()
+    keys = []
+    for i, blk in enumerate(P.blocks):
+        for r in range(blk.shape[0]):
+            keys.append((int(co[i]), 0, int(ro[i]) + r))
+    if damped:
+        for j in range(P.N):
+            keys.append((j, 1, P.M + j))
+    keys.sort()
+    return np.array([k[2] for k in keys], dtype=np.int64)

@@ -80,6 +80,25 @@ class LMState(ctypes.Structure):
     ]
 
 
+class Metadata(ctypes.Structure):
+    _fields_ = [
+        ("damped", ctypes.c_int32),
+        ("num_blocks", ctypes.c_int64),
+        ("rows", ctypes.c_int64),
+        ("cols", ctypes.c_int64),
+        ("values", ctypes.c_int64),
+        ("aug_rows", ctypes.c_int64),
+        ("val_off", ctypes.c_void_p),
+        ("row_off", ctypes.c_void_p),
+        ("col_off", ctypes.c_void_p),
+        ("row_order", ctypes.c_void_p),
+        ("r_row_ptr", ctypes.c_void_p),
+        ("r_col_idx", ctypes.c_void_p),
+        ("r_capacity", ctypes.c_int64),
+        ("r_nnz", ctypes.c_int64),
+    ]
+
+
 MODEL_CURVEFIT = 0
 MLP_FEATURES, MLP_CLASSES, MLP_PARAMS = 16, 8, 5768
 MLP_MULTIPLIERS = (1e-2, 1e-1, 1.0 / 3.0, 0.5, 1.0, 2.0, 4.0, 10.0)
@@ -123,6 +142,7 @@ _SIGS = {
                                                  _VP, _VP, _VP, _VP, ctypes.c_int]),
     "qrkit_launch_count": (ctypes.c_int64, [_VP]),
     "qrkit_band_order": (ctypes.c_int, [ctypes.c_int64, ctypes.c_int64, _VP, _VP, _VP, _VP, _VP, _VP]),
+    "qrkit_structure_metadata": (ctypes.c_int, [ctypes.POINTER(Structure), ctypes.POINTER(Metadata)]),
     "qrkit_task_layout": (ctypes.c_int, [ctypes.c_int64, _VP, _VP, ctypes.c_int64, ctypes.c_int, _VP, _VP, _VP,
                                          ctypes.c_int64]),
 }
@@ -191,6 +211,61 @@ def task_layout(n, m, supertile=65536, key_major=False):
     if st != 0:
         raise QRKitError(st, "qrkit_task_layout failed")
     return key, slots
+
+
+def block_structure(n, m, coupled=COUPLED_NONE, shared_cols=0, window=0, window_start=None,
+                    segment_cols=None, segment_blocks=None):
+    """A QRKIT_STRUCT_BLOCKS descriptor and the arrays it points to (keep them alive)."""
+    n = np.ascontiguousarray(n, dtype=np.uint8)
+    m = np.ascontiguousarray(m, dtype=np.uint8)
+    s = Structure()
+    s.kind = STRUCT_BLOCKS
+    s.num_blocks = n.shape[0]
+    s.block_rows = n.ctypes.data
+    s.block_cols = m.ctypes.data
+    s.coupled_kind = int(coupled)
+    s.shared_cols = int(shared_cols)
+    s.window = int(window)
+    keep = [n, m]
+    if window_start is not None:
+        ws = np.ascontiguousarray(window_start, dtype=np.int32)
+        s.window_start = ws.ctypes.data
+        keep.append(ws)
+    if segment_cols is not None:
+        sc = np.ascontiguousarray(segment_cols, dtype=np.int64)
+        sb = np.ascontiguousarray(segment_blocks, dtype=np.int64)
+        s.num_segments = sc.shape[0]
+        s.segment_cols = sc.ctypes.data
+        s.segment_blocks = sb.ctypes.data
+        keep += [sc, sb]
+    return s, keep
+
+
+def structure_metadata(n, m, damped, **kw):
+    """qrkit_structure_metadata: (val_off, row_off, col_off, row_order, r_row_ptr, r_col_idx)."""
+    lib = load()
+    s, keep = block_structure(n, m, **kw)
+    md = Metadata()
+    md.damped = 1 if damped else 0
+    st = lib.qrkit_structure_metadata(ctypes.byref(s), ctypes.byref(md))
+    if st != 0:
+        raise QRKitError(st, "qrkit_structure_metadata failed")
+    K, N = md.num_blocks, md.cols
+    vo, ro, co = (np.empty(K + 1, dtype=np.int64) for _ in range(3))
+    order = np.empty(max(md.aug_rows, 1), dtype=np.int64)
+    ptr = np.empty(N + 1, dtype=np.int64)
+    md.val_off, md.row_off, md.col_off = vo.ctypes.data, ro.ctypes.data, co.ctypes.data
+    md.row_order, md.r_row_ptr = order.ctypes.data, ptr.ctypes.data
+    st = lib.qrkit_structure_metadata(ctypes.byref(s), ctypes.byref(md))
+    if st != 0:
+        raise QRKitError(st, "qrkit_structure_metadata failed")
+    idx = np.empty(max(md.r_nnz, 1), dtype=np.int32)
+    md.r_col_idx, md.r_capacity = idx.ctypes.data, md.r_nnz
+    st = lib.qrkit_structure_metadata(ctypes.byref(s), ctypes.byref(md))
+    if st != 0:
+        raise QRKitError(st, "qrkit_structure_metadata failed")
+    del keep
+    return vo, ro, co, order[:md.aug_rows], ptr, idx[:md.r_nnz]
 
 
 def band_order(rows, cols, row_ptr, col_idx):

@@ -142,3 +142,44 @@ def test_planted_mistake_sign_of_coupling_is_caught():
     J = st.assemble_J(P)
     assert st.optimality_residual(J, P.b, st.damping(P), P.lam, p_bad) > 1e-6
     assert st.optimality_residual(J, P.b, st.damping(P), P.lam, p_ok) < 1e-14
+
+
+@pytest.mark.parametrize("kw,damped", [(dict(K=5, n=4, m=2, s=3), True), (dict(K=6, n=3, m=2, s=0), True),
+                                       (dict(windowed=True, s=12, w=4, K=9), True),
+                                       (dict(windowed=True, s=12, w=4, K=9, lam=0.0), False),
+                                       (dict(K=4, n=5, m=3, s=2, lam=0.0), False)])
+def test_structural_metadata_matches_the_numerical_factor(kw, damped):
+    """The structural P_r equals the value-based one on random data, and the symbolic R
+    pattern is exactly the non-zero pattern of the R that dense Householder QR of
+    P_r [J; lambda^(1/2) D] produces (random values: no cancellation)."""
+    P = small_problem(**kw)
+    order = st.structural_row_order(P, damped)
+    if damped:
+        np.testing.assert_array_equal(order, st.row_permutation(P))
+    ptr, idx = st.r_pattern(P, damped)
+    A, _ = st.assemble_augmented(P)
+    if not damped:
+        A = st.assemble_J(P)[order]
+    R = hh.qr(A).R
+    for c in range(P.N):
+        nz = np.nonzero(np.abs(R[c]) > 1e-13 * np.abs(R).max())[0]
+        assert nz.tolist() == idx[ptr[c]:ptr[c + 1]].tolist(), c
+
+
+def test_structural_pattern_planted_mistake_fails():
+    """Merging without carrying the union (a row keeps only its own columns) gives a pattern
+    that misses fill, so it differs from the numerical one."""
+    P = small_problem(windowed=True, s=12, w=4, K=9)
+    rows = st.structural_rows(P, True)
+    R = [None] * P.N
+    for k in st.structural_row_order(P, True):
+        cur = sorted(set(rows[int(k)]))
+        while cur:
+            c = cur[0]
+            if R[c] is None:
+                R[c] = cur
+                break
+            cur = cur[1:]                       # planted: no union with R row c
+    ptr, idx = st.r_pattern(P, True)
+    bad = [x for c in range(P.N) for x in (R[c] or [])]
+    assert bad != idx.tolist()
