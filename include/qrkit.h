@@ -364,20 +364,7 @@ qrkit_status qrkit_task_layout(int64_t num_blocks, const uint8_t* block_rows, co
                                int64_t supertile, int key_major, int64_t* num_tasks, int32_t* task_key,
                                int64_t* task_slots, int64_t capacity);
 
-/* Structure metadata of a QRKIT_STRUCT_BLOCKS descriptor (Sec. 3 composition, Sec. 4.5 / 5.2
- * row interleave), on the host with no CUDA call and no context.  in: damped (1: the damping
- * rows lambda^(1/2) D are present, i.e. lambda > 0).  out: the sizes; and, where the HOST
- * pointers are not NULL, the offsets of the packed values, rows and columns of each block
- * (num_blocks + 1 each), the row permutation P_r of [J; lambda^(1/2) D] (aug_rows entries: the
- * source row of each row, J rows 0 .. rows - 1, the damping row of column j = rows + j; sorted by
- * leading column, J rows before the damping row of that column, then by source index) and the
- * structural pattern of R in natural column order (block columns, then shared columns) as CSR:
- * r_row_ptr (cols + 1) and r_col_idx (r_nnz entries, columns ascending per row; r_capacity
- * entries available).  The pattern is that of the row-merge QR of the rows in P_r order (a row
- * whose leading column c already has an R row is merged with it, both taking the union of the
- * two patterns), which is the pattern of the unique R barring cancellation.  A window is cut at
- * the end of its block's segment.  QRKIT_EINVAL for a malformed descriptor or too small a
- * capacity (r_nnz is still set), QRKIT_EUNSUPPORTED for other structure kinds. */
+/* In/out record of qrkit_structure_metadata. */
 typedef struct qrkit_metadata {
   int32_t damped;       /* in */
   int64_t num_blocks;   /* out */
@@ -394,6 +381,20 @@ typedef struct qrkit_metadata {
   int64_t r_capacity;   /* in: entries r_col_idx holds */
   int64_t r_nnz;        /* out: entries of the R pattern (-1 if not asked for) */
 } qrkit_metadata;
+/* Structure metadata of a QRKIT_STRUCT_BLOCKS descriptor (Sec. 3 composition, Sec. 4.5 / 5.2
+ * row interleave), on the host with no CUDA call and no context.  in: damped (1: the damping
+ * rows lambda^(1/2) D are present, i.e. lambda > 0).  out: the sizes; and, where the HOST
+ * pointers are not NULL, the offsets of the packed values, rows and columns of each block
+ * (num_blocks + 1 each), the row permutation P_r of [J; lambda^(1/2) D] (aug_rows entries: the
+ * source row of each row, J rows 0 .. rows - 1, the damping row of column j = rows + j; sorted by
+ * leading column, J rows before the damping row of that column, then by source index) and the
+ * structural pattern of R in natural column order (block columns, then shared columns) as CSR:
+ * r_row_ptr (cols + 1) and r_col_idx (r_nnz entries, columns ascending per row; r_capacity
+ * entries available).  The pattern is that of the row-merge QR of the rows in P_r order (a row
+ * whose leading column c already has an R row is merged with it, both taking the union of the
+ * two patterns), which is the pattern of the unique R barring cancellation.  A window is cut at
+ * the end of its block's segment.  QRKIT_EINVAL for a malformed descriptor or too small a
+ * capacity (r_nnz is still set), QRKIT_EUNSUPPORTED for other structure kinds. */
 qrkit_status qrkit_structure_metadata(const qrkit_structure* s, qrkit_metadata* md);
 
 /* Row and column permutations that expose a banded structure (Sec. 4.3), on the host with no
