@@ -197,6 +197,27 @@ qrkit_status qrkit_set_wait_limit(qrkit_ctx* ctx, int64_t polls);
  * word.  Asynchronous. */
 qrkit_status qrkit_more_solve(qrkit_ctx* ctx, const void* qtb, const void* D, double lambda, void* p);
 
+/* Result record of qrkit_get_info. */
+typedef struct qrkit_info {
+  int32_t refine_steps_max;   /* most refinement steps a block took in the last FP32-refined
+                                 qrkit_factor_solve (warp-task mapping), else -1 */
+  int64_t refined_blocks;     /* blocks its a-priori estimate selected, else -1 */
+  double residual_norm;       /* ||b - J p||_2 */
+  double optimality_norm;     /* ||J^T (b - J p) - lambda D^2 p||_2 */
+  double optimality_scale;    /* ||J||_F (||J||_F ||p|| + ||b||): the size of J^T b and of
+                                 J^T J p, against which optimality_norm is small */
+} qrkit_info;
+
+/* Diagnostics of a solution p of a block-diagonal plan (no paper counterpart; the quantities
+ * are those of Eq. 1 and Eq. 2): the residual norm, the norm of the optimality residual
+ * J^T (b - J p) - lambda D^2 p, which is zero at the exact minimiser of Eq. 2 ((J^T J +
+ * lambda D^2) p = J^T b, Eq. 1), its scale, and the refinement's selection count and most steps
+ * taken in the last qrkit_factor_solve.  J, b, p: DEVICE buffers as for qrkit_factor_solve; D:
+ * DEVICE (sum m_i) or NULL for the column norms of J (zero -> 1); lambda >= 0.  Everything in
+ * double, added in a fixed order.  Synchronous. */
+qrkit_status qrkit_get_info(qrkit_ctx* ctx, const void* J, const void* b, const void* p, const void* D,
+                            double lambda, qrkit_info* out);
+
 /* Residual precision of the block refinement (qrkit_set_refinement). */
 enum { QRKIT_RESIDUAL_DOT2 = 0, QRKIT_RESIDUAL_FP64 = 1 };
 
@@ -463,6 +484,23 @@ qrkit_status qrkit_lm_plan(qrkit_ctx* ctx, const qrkit_lm_problem* problem);
  * accepted.  A problem whose lambda exceeds 1e16 is marked done.  states: host, B entries,
  * read and written.  Synchronous (returns after the state is copied back). */
 qrkit_status qrkit_lm_step(qrkit_ctx* ctx, double* x, qrkit_lm_state* states, int refine_steps);
+
+/* One LM trial step for a model of the caller's own (Sec. 2; Backtrack LM of Sec. 5.2): the
+ * caller evaluates its residual f and Jacobian at x and passes J, S (the layout of
+ * qrkit_factor for the current QRKIT_STRUCT_BLOCKS plan) and b = -f; the library factors
+ * P_r [J; lambda^(1/2) D] (D NULL: column norms of J, zero -> 1), solves with `refine_steps`
+ * refinement steps into p (DEVICE, N values) and returns in *pred (HOST) the predicted decrease
+ * 1/2 p^T (lambda D^2 p + J^T b) of the linear model, computed in double.  The caller then
+ * evaluates cost_new = 1/2 ||f(x + p)||^2 and forms the gain ratio rho = (cost - cost_new) /
+ * pred for qrkit_nielsen_update.  J and S stay in use until the call returns.  Synchronous. */
+qrkit_status qrkit_lm_trial(qrkit_ctx* ctx, const void* J, const void* S, const void* b, const void* D,
+                            double lambda, int refine_steps, void* p, double* pred);
+
+/* Nielsen's damping rule (the reading of the paper's "adapting Lourakis", Sec. 2 / Sec. 5.2):
+ * rho > 0: the step is accepted, lambda *= max(1/3, 1 - (2 rho - 1)^3), nu = 2; otherwise
+ * rejected, lambda *= nu, nu *= 2.  HOST values, read and written; accepted (may be NULL)
+ * receives 1 or 0.  QRKIT_EINVAL unless lambda > 0 and nu > 0.  No CUDA call. */
+qrkit_status qrkit_nielsen_update(double rho, double* lambda, double* nu, int32_t* accepted);
 
 /* Up to max_iter iterations as in qrkit_lm_step (Sec. 2, Sec. 5.2) with the state kept on the device; a problem
  * is marked done after an accepted step with cost - cost_new <= ftol * cost (or lambda > 1e16),

@@ -82,11 +82,13 @@ qrkit_status launch_tasks_typed(qrkit_ctx* ctx, const void* J, const void* b, vo
                      "refinement records")) != QRKIT_OK)
       return st;
     A.rec = (float*)ctx->ws.rrec.ptr;
-    if ((st = ensure(ctx, ctx->ws.tcount, kTaskKeys * sizeof(int), "refinement counts")) != QRKIT_OK) return st;
-    QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->ws.tcount.ptr, 0, kTaskKeys * sizeof(int), ctx->stream));
+    // counts per shape key, then the most steps a block took
+    if ((st = ensure(ctx, ctx->ws.tcount, (kTaskKeys + 1) * sizeof(int), "refinement counts")) != QRKIT_OK) return st;
+    QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(ctx->ws.tcount.ptr, 0, (kTaskKeys + 1) * sizeof(int), ctx->stream));
     A.rlist = (RefEntry*)ctx->ws.tlist.ptr;
     A.rcount = (int*)ctx->ws.tcount.ptr;
   }
+  ctx->refine_stats = SEL && sizeof(T) == sizeof(float);
   const size_t smem = (size_t)wpc * A.warp_bytes;
   int per_sm = 0;
   if ((st = resident(ctx, kernel_setup<T, SEL>, threads, smem, sizeof(T) == 8 ? 10 : (SEL ? 9 : 8), per_sm)) != QRKIT_OK)
@@ -107,6 +109,7 @@ qrkit_status launch_tasks_typed(qrkit_ctx* ctx, const void* J, const void* b, vo
     R.key_off = A.key_off;
     R.steps = refine_steps;
     R.tol = 1e-6f;
+    R.steps_max = A.rcount + kTaskKeys;
     R.status = A.status;
     const int threads2 = 32 * kRefineWarps;
     const bool res64 = ctx->refine_residual != 0;

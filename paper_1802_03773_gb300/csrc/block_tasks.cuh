@@ -442,10 +442,11 @@ __device__ __forceinline__ void group_aug_residuals(const float* jq, const float
 // whose correction is below tol / (16 u kappa) relative to x ends the block (kappa: an upper
 // bound of its condition number).  x is replicated over the group; jq points to the lane's row
 // quad of J's column 0 (column stride 4G values, zero past n) and bl holds its rows of b.
+// Returns the steps the block took.
 template <int G, int M, int RES>
-__device__ __forceinline__ void group_refine_aug(const float (&a)[kMaxCols][4], const float (&tau)[kMaxCols],
-                                                 float (&x)[kMaxCols], const float* jq, const float (&bl)[4],
-                                                 int n, float kappa, const Group<G>& g, int steps, float tol) {
+__device__ __forceinline__ int group_refine_aug(const float (&a)[kMaxCols][4], const float (&tau)[kMaxCols],
+                                                float (&x)[kMaxCols], const float* jq, const float (&bl)[4],
+                                                int n, float kappa, const Group<G>& g, int steps, float tol) {
   const float next_tol = tol / fmaxf(16.f * kUnitRoundoff * kappa, tol);
   const int q = g.q;
   // Q_1 = H_0 ... H_{M-1} [I_M; 0]: column j is changed by H_j .. H_0 only
@@ -497,8 +498,10 @@ __device__ __forceinline__ void group_refine_aug(const float (&a)[kMaxCols][4], 
     }
   }
   bool done = n == 0;
+  int taken = 0;
   for (int step = 0; step < steps; ++step) {
     if (__all_sync(0xffffffffu, done)) break;
+    taken += done ? 0 : 1;
     float f[4], gv[kMaxCols];
     group_aug_residuals<G, M, RES>(jq, bl, x, r, g, f, gv);
     // t = Q_1^T f - R^{-T} g
@@ -546,6 +549,7 @@ __device__ __forceinline__ void group_refine_aug(const float (&a)[kMaxCols][4], 
     }
     done = done || !(dmax > next_tol * xmax);
   }
+  return taken;
 }
 
 // ---------------------------------------------------------------------------------------
@@ -878,6 +882,7 @@ struct RefineTaskArgs {
   const int64_t* key_off;
   int steps;
   float tol;
+  int* steps_max;      // the most steps any block took (atomic maximum)
   int* status;
 };
 
@@ -935,7 +940,9 @@ __device__ __forceinline__ void refine_task(const RefineTaskArgs& A, int key, in
     w = g.sum(w);   // every lane takes part in the group reduction
     tau[k] = n > 0 ? 2.f / (1.f + w) : 0.f;
   }
-  group_refine_aug<G, M, RES>(a, tau, x, rec + 4 * g.q, bl, n, e.kappa, g, A.steps, A.tol);
+  const int taken = group_refine_aug<G, M, RES>(a, tau, x, rec + 4 * g.q, bl, n, e.kappa, g, A.steps, A.tol);
+  const int most = __reduce_max_sync(0xffffffffu, n > 0 ? taken : 0);
+  if (lane == 0 && most > 0) atomicMax(A.steps_max, most);
   if (n > 0) {
     float* dx = A.x + e.c;
 #pragma unroll

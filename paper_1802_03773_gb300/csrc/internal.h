@@ -241,6 +241,7 @@ struct qrkit_ctx {
   int occ_threads[16] = {};    // threads and resident CTAs per SM at that size (warp-task kernels)
   int occ_per_sm[16] = {};
   long long wait_limit = 1LL << 26;  // polls of a bounded device wait before it gives up
+  bool refine_stats = false;    // ws.tcount holds the last fused solve's selection counts and steps
   float refine_select = 2e-6f;  // block refinement: a-priori error estimate that selects a block
   int refine_residual = 0;      // its residual precision: 0 compensated float, 1 double
   bool factored = false;       // fused block path

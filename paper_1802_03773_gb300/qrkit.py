@@ -99,6 +99,16 @@ class Metadata(ctypes.Structure):
     ]
 
 
+class Info(ctypes.Structure):
+    _fields_ = [
+        ("refine_steps_max", ctypes.c_int32),
+        ("refined_blocks", ctypes.c_int64),
+        ("residual_norm", ctypes.c_double),
+        ("optimality_norm", ctypes.c_double),
+        ("optimality_scale", ctypes.c_double),
+    ]
+
+
 MODEL_CURVEFIT = 0
 MLP_FEATURES, MLP_CLASSES, MLP_PARAMS = 16, 8, 5768
 MLP_MULTIPLIERS = (1e-2, 1e-1, 1.0 / 3.0, 0.5, 1.0, 2.0, 4.0, 10.0)
@@ -115,6 +125,11 @@ _SIGS = {
     "qrkit_set_refinement": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int]),
     "qrkit_set_wait_limit": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "qrkit_more_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, _VP]),
+    "qrkit_get_info": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.POINTER(Info)]),
+    "qrkit_lm_trial": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int, _VP,
+                                      ctypes.POINTER(ctypes.c_double)]),
+    "qrkit_nielsen_update": (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_double),
+                                            ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     "qrkit_get_band_factor": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "qrkit_factor": (ctypes.c_int, [_VP, _VP, _VP, _VP, ctypes.c_double]),
     "qrkit_apply_qt": (ctypes.c_int, [_VP, _VP, _VP]),
@@ -211,6 +226,16 @@ def task_layout(n, m, supertile=65536, key_major=False):
     if st != 0:
         raise QRKitError(st, "qrkit_task_layout failed")
     return key, slots
+
+
+def nielsen_update(rho, lam, nu):
+    """qrkit_nielsen_update on the host: returns (lambda, nu, accepted)."""
+    lib = load()
+    l, v, a = ctypes.c_double(lam), ctypes.c_double(nu), ctypes.c_int32(0)
+    st = lib.qrkit_nielsen_update(float(rho), ctypes.byref(l), ctypes.byref(v), ctypes.byref(a))
+    if st != 0:
+        raise QRKitError(st, "qrkit_nielsen_update failed")
+    return l.value, v.value, bool(a.value)
 
 
 def block_structure(n, m, coupled=COUPLED_NONE, shared_cols=0, window=0, window_start=None,
@@ -422,6 +447,22 @@ class Context:
         """Block refinement settings: selection threshold and residual precision ("dot2" or "fp64")."""
         mode = {"dot2": RESIDUAL_DOT2, "fp64": RESIDUAL_FP64}[residual] if isinstance(residual, str) else int(residual)
         self._check(self.lib.qrkit_set_refinement(self.h, float(select), mode))
+
+    def lm_trial(self, J, S, b, p, D=None, lam=1e-3, refine_steps=1):
+        """One LM trial step for the caller's own model: solve into p, return the predicted decrease."""
+        pred = ctypes.c_double(0.0)
+        self._check(self.lib.qrkit_lm_trial(self.h, self._t(J, "J"), self._t(S, "S", True), self._t(b, "b"),
+                                            self._t(D, "D", True), float(lam), int(refine_steps), self._t(p, "p"),
+                                            ctypes.byref(pred)))
+        self._refs = (J, S, D)
+        return pred.value
+
+    def info(self, J, b, p, D=None, lam=0.0):
+        """qrkit_get_info: dict of the solution's diagnostics (block-diagonal plans)."""
+        out = Info()
+        self._check(self.lib.qrkit_get_info(self.h, self._t(J, "J"), self._t(b, "b"), self._t(p, "p"),
+                                            self._t(D, "D", True), float(lam), ctypes.byref(out)))
+        return {k: getattr(out, k) for k, _ in Info._fields_}
 
     def more_solve(self, qtb, p, D=None, lam=0.0):
         """Moré's second factorization for the stored block factor (qtb from factor_solve)."""

@@ -66,3 +66,19 @@ def test_lm_system_matches_dense_and_banded():
     np.testing.assert_allclose(p_band, p_dense, rtol=1e-10, atol=1e-12)
     J = cf.jacobian_dense(x0, data)
     np.testing.assert_allclose(J, st.assemble_J(P), atol=0)
+
+
+def test_library_nielsen_update_equals_the_oracle():
+    """The host entry point qrkit_nielsen_update against the oracle's rule, including the
+    clamp at 1/3, rho = 0 (rejected) and a negative rho."""
+    from paper_1802_03773_gb300 import build as b
+    b.build()
+    from paper_1802_03773_gb300 import qrkit
+    for lam, nu, rho in [(1.0, 2.0, 1.0), (1.0, 8.0, 0.5), (2.0, 2.0, 0.75), (2.0, 4.0, -0.1), (3e-4, 16.0, 0.0),
+                         (5.0, 2.0, 0.999), (1e-8, 2.0, 0.01)]:
+        got = qrkit.nielsen_update(rho, lam, nu)
+        ref = lm.nielsen(lam, nu, rho)
+        assert got[2] == ref[2]
+        assert got[0] == pytest.approx(ref[0], rel=1e-15) and got[1] == ref[1]
+    with pytest.raises(qrkit.QRKitError):
+        qrkit.nielsen_update(0.5, 0.0, 2.0)
