@@ -565,6 +565,14 @@ qrkit_status qrkit_lm_set_policy(qrkit_ctx* ctx, int use_mlp);
  * (Not in the paper.) */
 qrkit_status qrkit_lm_features(qrkit_ctx* ctx, float* features);
 
+/* Peak-rate probe of a device (no paper counterpart; the roofline denominators no library
+ * measures): kind 0 = FP32 fused multiply-add throughput of the CUDA cores, 1 = FP64 FMA,
+ * 2 = dense TF32 rate of the tensor cores (tcgen05.mma kind::tf32, M = 128, N = 256, FP32
+ * accumulation).  *tflops (HOST) receives the rate in TFLOP/s (2 flops per multiply-add) of
+ * the second of two timed launches over every SM.  Allocates 64 bytes and a stream of its own;
+ * the caller thread's current device is restored.  Synchronous. */
+qrkit_status qrkit_peak_probe(int device, int kind, double* tflops);
+
 /* Block until the stream is idle and return the device status word (QRKIT_OK if no kernel
  * reported a failure), then clear it.  (No paper counterpart.) */
 qrkit_status qrkit_sync_status(qrkit_ctx* ctx);

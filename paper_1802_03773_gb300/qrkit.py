@@ -128,6 +128,7 @@ _SIGS = {
     "qrkit_get_info": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.POINTER(Info)]),
     "qrkit_lm_trial": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int, _VP,
                                       ctypes.POINTER(ctypes.c_double)]),
+    "qrkit_peak_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
     "qrkit_nielsen_update": (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     "qrkit_get_band_factor": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
@@ -226,6 +227,17 @@ def task_layout(n, m, supertile=65536, key_major=False):
     if st != 0:
         raise QRKitError(st, "qrkit_task_layout failed")
     return key, slots
+
+
+def peak_probe(device=0, kind="tf32"):
+    """qrkit_peak_probe: TFLOP/s of "fp32" / "fp64" FMA or "tf32" tensor-core MMA on `device`."""
+    lib = load()
+    k = {"fp32": 0, "fp64": 1, "tf32": 2}[kind]
+    v = ctypes.c_double(0.0)
+    st = lib.qrkit_peak_probe(int(device), k, ctypes.byref(v))
+    if st != 0:
+        raise QRKitError(st, "qrkit_peak_probe failed")
+    return v.value
 
 
 def nielsen_update(rho, lam, nu):
