@@ -41,6 +41,14 @@ KERNEL_SRCS = [os.path.join(ROOT, "paper_1802_03773_gb300", "csrc", f)
                          "device_util.cuh")]
 
 
+def workload_config(args):
+    """The workload as both arms report it (identical dictionaries)."""
+    return {"workload": WORKLOAD, "blocks_per_gpu": K_BLOCKS, "precision": args.precision,
+            "refine_steps": args.refine_steps if args.precision == "fp32_refined" else 0,
+            "l2": "inputs 2 x 158 MB alternated between steps (each larger than the 129 MB L2)",
+            "parallelism": "independent blocks, one replica per GPU, no collective"}
+
+
 def dist_env():
     from paper_1802_03773_gb300.replicas import dist_env as env
     return env()
@@ -191,9 +199,10 @@ def run_reference(args):
     cores = 1
     line = {"metric": METRIC, "value": value, "unit": UNIT, "impl": "reference",
             "n_gpus": args.gpus, "steps": args.steps, "warmup": args.warmup,
-            "ms_per_step": 1000.0 / value, "higher_is_better": True, "scaling": "weak",
+            "ms_per_step": 1000.0 * el / args.steps, "blocks_per_step": blocks / args.steps,
+            "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": WORKLOAD, "blocks": K_BLOCKS},
+            "config": workload_config(args),
             "cpu_baseline": {"value": value, "unit": UNIT, "cores": cores, "kind": "oracle",
                              "sample": f"{blocks} blocks of the 1,000,000-block workload in {args.steps} "
                                        f"steps of ~{per_step:.0f} s, per-block Householder QR solve "
@@ -275,6 +284,39 @@ def _convergence(h, times, target, iters):
     return r
 
 
+def _curvefit_cond(dev, stream):
+    """cond(J) of a scaled replica of the curve fit (2,000 points, 64 control points) at its start
+    point, from the singular values of the dense Jacobian the library linearises (numpy SVD), and
+    of the damped [J; lambda^(1/2) D] over the lambda sweep."""
+    import torch
+    from paper_1802_03773_gb300 import Context
+    ctx = Context(dev.index, stream=stream, precision="fp64")
+    x, x0, data, npts, kcs = _curvefit_batch(ctx, [(2000, 64, 0)], dev, stream)
+    NP, s = npts[0], 2 * kcs[0]
+    with torch.cuda.stream(stream):
+        Jl = torch.empty(2 * NP, dtype=torch.float64, device=dev)
+        Sl = torch.empty(16 * NP, dtype=torch.float64, device=dev)
+        st = torch.empty(NP, dtype=torch.int32, device=dev)
+        ctx.lm_linearize(torch.from_numpy(x0).to(dev), Jl, Sl, None, st)
+        stream.synchronize()
+    ctx.close()
+    Jb, Sb, stt = Jl.cpu().numpy().reshape(NP, 2), Sl.cpu().numpy().reshape(NP, 8, 2), st.cpu().numpy()
+    A = np.zeros((2 * NP, NP + s))
+    for i in range(NP):
+        A[2 * i:2 * i + 2, i] = Jb[i]
+        for t in range(8):
+            if stt[i] + t < s:
+                A[2 * i:2 * i + 2, NP + stt[i] + t] = Sb[i, t]
+    sv = np.linalg.svd(A, compute_uv=False)
+    D = np.sqrt((A * A).sum(axis=0))
+    D[D == 0] = 1.0
+    damped = {}
+    for lam in (1e-6, 1e-3, 1.0, 1e2):
+        sd = np.linalg.svd(np.vstack([A, np.sqrt(lam) * np.diag(D)]), compute_uv=False)
+        damped[f"{lam:g}"] = float(sd[0] / sd[-1])
+    return {"points": NP, "control_points": kcs[0], "cond_J": float(sv[0] / sv[-1]), "cond_damped": damped}
+
+
 def other_workloads(dev, stream, only=None):
     """The remaining configurations, each timed briefly (CUDA events, after warm-up); `only`
     restricts the run to the workloads whose key starts with it."""
@@ -284,6 +326,74 @@ def other_workloads(dev, stream, only=None):
     out = {}
     peaks, peak_kind = measured_peaks()
     want = lambda key: only is None or key.startswith(only) or only.startswith(key)
+    if want("peaks_probe"):
+        # the rates no library measures: FMA throughput of the CUDA cores and the dense TF32 rate
+        # of the tensor cores, by the library's own probe kernels
+        out["peaks_probe"] = {"unit": "TFLOP/s",
+                              "fp32_fma": qrkit.peak_probe(dev.index, "fp32"),
+                              "fp64_fma": qrkit.peak_probe(dev.index, "fp64"),
+                              "tf32_tensor_dense": qrkit.peak_probe(dev.index, "tf32")}
+    if want("more_1m"):
+        # Moré's two factorizations on the 1M-block workload: stage 1 once (undamped fused QR, its
+        # Q^T b kept), then stage 2 per damping value ([R_i; lambda^(1/2) D_i] per block)
+        from workloads import batched_blocks
+        res = {}
+        for prec, dt in (("fp32", np.float32), ("fp64", np.float64)):
+            d = batched_blocks(K=K_BLOCKS, dtype=dt)
+            ctx = Context(dev.index, stream=stream, precision=prec)
+            ctx.plan_blocks(d["n"], d["m"])
+            J = torch.from_numpy(d["vals"]).to(dev)
+            b = torch.from_numpy(d["b"]).to(dev)
+            p1 = torch.empty(int(d["col_off"][-1]), dtype=J.dtype, device=dev)
+            q = torch.empty(int(d["row_off"][-1]), dtype=J.dtype, device=dev)
+            torch.cuda.synchronize()
+            t1 = _time(stream, lambda: ctx.factor_solve(J, b, p1, q, refine_steps=0), 5)
+            t2 = _time(stream, lambda: ctx.more_solve(q, p1, None, 1e-2), 10)
+            ctx.sync_status()
+            res[prec] = {"ms_stage1_factor_qtb_solve": t1, "ms_stage2_per_lambda": t2,
+                         "lambda_trials_per_s": 1000.0 / t2}
+            ctx.close()
+            del J, b, p1, q
+        out["more_two_step_1m_blocks"] = {
+            "workload": "1,000,000 blocks as the headline; stage 2 with D = column norms, lambda 1e-2", **res}
+    if want("dense_hcat_batch"):
+        # the dense horizontal concatenation over 4096 seeds: independent FP64 solves spread over
+        # 32 streams (one context each), eager launches
+        nstreams, nseeds = 32, 4096
+        ctxs, data = [], []
+        streams = [torch.cuda.Stream(dev) for _ in range(nstreams)]
+        for k in range(nstreams):
+            c = Context(dev.index, stream=streams[k], precision="fp64")
+            c.plan_blocks(np.full(200, 4), np.full(200, 2), qrkit.COUPLED_DENSE, shared_cols=30)
+            ctxs.append(c)
+        for sd in range(nseeds):
+            d = block_angular_dense(seed_offset=1000 + sd)
+            data.append((torch.from_numpy(np.ascontiguousarray(d["blocks"].transpose(0, 2, 1).reshape(-1))).to(dev),
+                         torch.from_numpy(np.asarray(d["S"]).T.reshape(-1).copy()).to(dev),
+                         torch.from_numpy(np.asarray(d["b"])).to(dev),
+                         torch.empty(430, dtype=torch.float64, device=dev)))
+        torch.cuda.synchronize()
+
+        def run_all():
+            for sd in range(nseeds):
+                k = sd % nstreams
+                J, S, b, pp = data[sd]
+                with torch.cuda.stream(streams[k]):
+                    ctxs[k].factor(J, S, None, 1e-2)
+                    ctxs[k].solve(b, pp, refine_steps=0)
+        run_all()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        run_all()
+        torch.cuda.synchronize()
+        el = time.perf_counter() - t0
+        for c in ctxs:
+            c.sync_status()
+            c.close()
+        out["dense_hcat_200x(4x2)_s30_fp64_batch_4096"] = {
+            "workload": "4096 seeds of J = [blkdiag(200 blocks 4x2) | S 800x30], lambda 1e-2, D = norms, FP64, "
+                        "32 streams", "value": nseeds / el, "unit": "solves/s", "ms_total": 1000.0 * el}
+        del data
     if want("dense_hcat_200x"):
         # dense horizontal concatenation, one LM-step solve in FP64
         d = block_angular_dense()
@@ -402,22 +512,74 @@ def other_workloads(dev, stream, only=None):
                 sctx.plan_blocks(np.full(NP, 2), np.full(NP, 1), qrkit.COUPLED_WINDOW, shared_cols=2 * kcs[0], window=8,
                                  window_start=starts)
                 pq = torch.empty(NP + 2 * kcs[0], dtype=torch.float32, device=dev)
+                # the FP64 solve of the same float-rounded system is the accuracy reference
+                dctx = Context(dev.index, stream=stream, precision="fp64")
+                dctx.plan_blocks(np.full(NP, 2), np.full(NP, 1), qrkit.COUPLED_WINDOW, shared_cols=2 * kcs[0],
+                                 window=8, window_start=starts)
+                Jd, Sd, bd = Jl.double(), Sl.double(), bl.double()
+                pd = torch.empty(NP + 2 * kcs[0], dtype=torch.float64, device=dev)
                 per_lam = {}
-                for lam in (1e-6, 1e-3, 1.0, 1e2):
+                for lam in (1e-6, 1e-5, 1e-4, 1e-3, 1e-2, 1e-1, 1.0, 1e1, 1e2):
                     def qr():
                         sctx.factor(Jl, Sl, None, lam)
                         sctx.solve(bl, pq, refine_steps=1)
                     tq = _time(stream, qr, 5)
+                    eq = pq.double()
                     tc = _time(stream, lambda: sctx.normal_solve(Jl, Sl, bl, pq, None, lam), 5)
-                    per_lam[f"{lam:g}"] = {"qr_fp32_refined_solves_per_s": 1000.0 / tq, "cholesky_fp32_solves_per_s": 1000.0 / tc}
+                    ec = pq.double()
+
+                    def f64():
+                        dctx.factor(Jd, Sd, None, lam)
+                        dctx.solve(bd, pd, refine_steps=0)
+                    td = _time(stream, f64, 3)
+                    stream.synchronize()
+                    ref = pd.clone()
+                    rel = lambda v: float(torch.linalg.norm(v - ref) / torch.linalg.norm(ref))
+                    per_lam[f"{lam:g}"] = {"qr_fp32_refined_solves_per_s": 1000.0 / tq,
+                                           "cholesky_fp32_solves_per_s": 1000.0 / tc,
+                                           "qr_fp64_solves_per_s": 1000.0 / td,
+                                           "rel_err_qr_fp32_refined": rel(eq), "rel_err_cholesky_fp32": rel(ec)}
                 sctx.sync_status()
+                dctx.sync_status()
                 sctx.close()
+                dctx.close()
                 cf["fixed_lambda_solves"] = per_lam
+                cf["fixed_lambda_note"] = ("relative errors against the FP64 QR solve of the same float-rounded "
+                                           "system (the FP64 path matches the oracle to 1e-12 in the tests)")
+                cf["cond_J_replica"] = _curvefit_cond(dev, stream)
             ctx.sync_status()
             ctx.close()
         out["curvefit_200k_points_2048_control_points"] = {
             "workload": "open uniform cubic B-spline, 200,000 points (2x1 blocks), 4096 shared columns in windows of 8",
             **cf}
+    if want("curvefit_convergence"):
+        # the same 200,000-point fit solved to convergence, FP32 QR with refinement against plain
+        # FP64 QR on the same GPU: wall-clock time (one iteration per call, the state read back each
+        # time) until the cost is within 1e-6 of the best FP64 cost
+        runs = {}
+        for prec in ("fp32_refined", "fp64"):
+            ctx = Context(dev.index, stream=stream, precision=prec)
+            x, x0, data, npts, kcs = _curvefit_batch(ctx, [(200_000, 2048, 0)], dev, stream)
+            st = ctx.lm_states(1e-3)
+            costs, times = [], []
+            t0 = time.perf_counter()
+            for it in range(120):
+                ctx.lm_run(x, st, max_iter=1, ftol=0.0, refine_steps=1, use_graph=True)
+                times.append(1000.0 * (time.perf_counter() - t0))
+                costs.append(st[0].cost_new if st[0].accepted else st[0].cost)
+            ctx.sync_status()
+            runs[prec] = (np.minimum.accumulate(np.array(costs)), np.array(times))
+            ctx.close()
+        best = runs["fp64"][0][-1]
+        res = {}
+        for prec, (c, t) in runs.items():
+            hit = np.nonzero(c <= best * (1.0 + 1e-6))[0]
+            res[prec] = {"final_cost": float(c[-1]), "ms_per_iteration": float(t[-1] / len(t)),
+                         "iterations_to_1e-6": int(hit[0] + 1) if hit.size else None,
+                         "ms_to_1e-6": float(t[hit[0]]) if hit.size else None}
+        out["curvefit_200k_convergence_fp32_refined_vs_fp64"] = {
+            "workload": "200,000-point curve fit, 2048 control points, Nielsen damping, up to 120 iterations",
+            "target": "cost <= (1 + 1e-6) x the best FP64 cost", **res}
     if want("banded_1e6"):
         # banded + vertical concatenation: one instance of 1,000,000 columns, 4,000,000 rows
         bp = banded_problem(n=1_000_000, rows_per_col=4, w=8, seed_offset=0)
@@ -521,6 +683,10 @@ def other_workloads(dev, stream, only=None):
             res[f"within_{tol:g}_of_fp64_optimum"] = {
                 "nielsen": _convergence(hn, tn, opt * (1.0 + tol), iters),
                 "mlp": _convergence(hm, tm, opt * (1.0 + tol), iters)}
+        # the two smallest problems, for the oracle's own FP64 LM in the CPU leg
+        small = np.argsort([n for n, _, _ in specs])[:2]
+        probs = _curvefit_problems([specs[k] for k in small], dev, stream)
+        res["_oracle_check"] = [(probs[j][0], probs[j][1], float(opt[k])) for j, k in enumerate(small)]
         out["batched_lm_convergence_1024"] = res
     return out
 
@@ -667,6 +833,8 @@ def run_ours(args):
             dist.destroy_process_group()
         return
 
+    if args.no_cpu_baseline and extra:
+        extra.get("batched_lm_convergence_1024", {}).pop("_oracle_check", None)
     ms_per_step = total_ms / args.steps
     value = ws * 1000.0 / ms_per_step
     peaks, peak_kind = measured_peaks()
@@ -678,12 +846,8 @@ def run_ours(args):
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
-        "config": {"workload": WORKLOAD, "blocks_per_gpu": K_BLOCKS,
-                   "blocks_per_s": value * K_BLOCKS, "precision": args.precision,
-                   "refine_steps": refine if args.precision == "fp32_refined" else 0,
-                   "autotuned": tuned,
-                   "l2": "inputs 2 x 158 MB alternated between steps (each larger than the 129 MB L2)",
-                   "parallelism": f"independent blocks, {ws} GPU(s), no collective"},
+        "config": workload_config(args),
+        "blocks_per_s": value * K_BLOCKS, "autotuned": tuned,
         "roofline": {"bound": "hbm", "kernel": KERNEL, "achieved": achieved,
                      "peak": peaks["hbm_gbs"], "peak_kind": peak_kind, "unit": "GB/s",
                      "frac": achieved / peaks["hbm_gbs"], "traffic": traffic,
@@ -708,6 +872,18 @@ def run_ours(args):
             "sample": f"first {k} blocks of the workload ({el:.1f} s), per-block Householder QR "
                       "solve in numpy float64, extrapolated to whole 1,000,000-block solves"}
         line["accuracy"] = every_block_error(d, p_host)
+        chk = (extra or {}).get("batched_lm_convergence_1024", {}).pop("_oracle_check", None)
+        if chk:
+            # the FP64 optimum of sampled problems from the oracle's own LM (Nielsen rule, FP64)
+            from oracle import lm as olm
+            rows = []
+            for data_k, x0_k, opt_k in chk:
+                t0 = time.perf_counter()
+                stt = olm.lm_run(x0_k, data_k, lam0=1e-3, max_iter=150, ftol=1e-14)
+                rows.append({"points": int(data_k.shape[0]), "oracle_cost": float(stt.cost),
+                             "library_optimum": opt_k, "rel_diff": (opt_k - stt.cost) / stt.cost,
+                             "oracle_iterations": int(stt.it), "oracle_s": time.perf_counter() - t0})
+            line["workloads"]["batched_lm_convergence_1024"]["fp64_optimum_vs_oracle"] = rows
         if refined is not None:
             racc = every_block_error(d, pr_host)
             refined["rel_err_sampled"] = racc["rel_err"]
