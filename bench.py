@@ -796,6 +796,15 @@ def run_ours(args):
     e2e_ms = e0.elapsed_time(e1) / args.steps
     ctx.sync_status()
 
+    # the host link the inputs cross: copy engine and kernel zero-copy reads of pinned memory
+    from paper_1802_03773_gb300 import qrkit as _qk
+    cg, kg = _qk.host_link_probe(local, 1 << 30)
+    link_bytes = hJ.numel() * 4 + hb.numel() * 4 + hps[0].numel() * 4
+    link = {"copy_gbs": cg, "kernel_read_gbs": kg,
+            "achieved_gbs": link_bytes / (e2e_ms * 1e-3) / 1e9,
+            "frac_of_copy_rate": link_bytes / (e2e_ms * 1e-3) / 1e9 / cg,
+            "note": "both directions' bytes per step over the time of a step; the copy rate is one direction"}
+
     p_host = p.cpu().numpy()
     # the other precision mode, timed the same way for a few steps
     refined = None
@@ -855,7 +864,8 @@ def run_ours(args):
         "e2e": {"value": ws * 1000.0 / e2e_ms, "unit": UNIT,
                 "h2d_bytes_per_step": int(hJ.numel() * 4 + hb.numel() * 4),
                 "d2h_bytes_per_step": int(hps[0].numel() * 4),
-                "overlap": "copy of step i + 1 on its own stream during the solve of step i"},
+                "overlap": "copy of step i + 1 on its own stream during the solve of step i",
+                "host_link": link},
         "gpu_launches": launches,
         "clocks": clk,
         "accuracy": None,

@@ -573,6 +573,14 @@ qrkit_status qrkit_lm_features(qrkit_ctx* ctx, float* features);
  * the caller thread's current device is restored.  Synchronous. */
 qrkit_status qrkit_peak_probe(int device, int kind, double* tflops);
 
+/* Host-link probe of a device (no paper counterpart; it explains the end-to-end rate of a solve
+ * whose inputs start in host memory): `bytes` (>= 1 MiB, a multiple of 16) of pinned host memory
+ * moved to device memory by cudaMemcpyAsync (*copy_gbs) and by a kernel that reads the pinned
+ * memory directly (*kernel_gbs), in GB/s, each the second of two timed runs.  Allocates its own
+ * host and device buffers and a stream; the caller thread's current device is restored.
+ * Synchronous. */
+qrkit_status qrkit_host_link_probe(int device, int64_t bytes, double* copy_gbs, double* kernel_gbs);
+
 /* Block until the stream is idle and return the device status word (QRKIT_OK if no kernel
  * reported a failure), then clear it.  (No paper counterpart.) */
 qrkit_status qrkit_sync_status(qrkit_ctx* ctx);

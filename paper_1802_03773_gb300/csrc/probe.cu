@@ -2,9 +2,12 @@
 // and FP64 fused multiply-add throughput of the CUDA cores, and the dense TF32 rate of the
 // 5th-generation tensor cores (tcgen05.mma kind::tf32, M = 128, N = 256, K = 8 per
 // instruction, FP32 accumulation in tensor memory).  Each probe is one launch over every SM,
-// timed with CUDA events; the rates are returned in TFLOP/s (2 flops per multiply-add).
+// timed with CUDA events; the rates are returned in TFLOP/s (2 flops per multiply-add).  The
+// host-link probe times the two ways inputs in host memory reach a kernel: a copy-engine copy
+// into device memory, and a kernel reading pinned host memory directly.
 #include <cuda_runtime.h>
 #include <stdint.h>
+#include <string.h>
 
 #include "internal.h"
 
@@ -151,4 +154,66 @@ extern "C" qrkit_status qrkit_peak_probe(int device, int kind, double* tflops) {
   if (st) cudaStreamDestroy(st);
   cudaSetDevice(prev);
   return rc;
+}
+
+namespace qrkit {
+namespace {
+
+// Streams `n16` 16-byte words from src (pinned host memory, read by the GPU over the host link)
+// into dst (device memory): the rate a kernel that reads its inputs straight from the host gets.
+__global__ void __launch_bounds__(256) host_read_kernel(const uint4* __restrict__ src, uint4* __restrict__ dst,
+                                                        int64_t n16) {
+  const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+  for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n16; i += stride) dst[i] = src[i];
+}
+
+}  // namespace
+}  // namespace qrkit
+
+extern "C" qrkit_status qrkit_host_link_probe(int device, int64_t bytes, double* copy_gbs, double* kernel_gbs) {
+  using namespace qrkit;
+  if (!copy_gbs || !kernel_gbs || bytes < (1 << 20) || (bytes & 15)) return QRKIT_EINVAL;
+  int prev = -1;
+  if (cudaGetDevice(&prev) != cudaSuccess) return QRKIT_ECUDA;
+  if (cudaSetDevice(device) != cudaSuccess) return QRKIT_ECUDA;
+  int sms = 0;
+  cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
+  void *h = nullptr, *d = nullptr;
+  cudaStream_t st = nullptr;
+  cudaEvent_t a = nullptr, b = nullptr;
+  if (e == cudaSuccess) e = cudaHostAlloc(&h, (size_t)bytes, cudaHostAllocMapped | cudaHostAllocPortable);
+  if (e == cudaSuccess) e = cudaMalloc(&d, (size_t)bytes);
+  if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&st, cudaStreamNonBlocking);
+  if (e == cudaSuccess) e = cudaEventCreate(&a);
+  if (e == cudaSuccess) e = cudaEventCreate(&b);
+  if (e == cudaSuccess) memset(h, 1, (size_t)bytes);
+  void* hd = nullptr;
+  if (e == cudaSuccess) e = cudaHostGetDevicePointer(&hd, h, 0);
+  float ms_copy = 0.f, ms_kernel = 0.f;
+  for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {   // the first of each runs warms up
+    if ((e = cudaEventRecord(a, st)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(d, h, (size_t)bytes, cudaMemcpyHostToDevice, st)) != cudaSuccess) break;
+    if ((e = cudaEventRecord(b, st)) != cudaSuccess) break;
+    if ((e = cudaEventSynchronize(b)) != cudaSuccess) break;
+    e = cudaEventElapsedTime(&ms_copy, a, b);
+  }
+  for (int rep = 0; rep < 2 && e == cudaSuccess; ++rep) {
+    if ((e = cudaEventRecord(a, st)) != cudaSuccess) break;
+    host_read_kernel<<<sms * 8, 256, 0, st>>>((const uint4*)hd, (uint4*)d, bytes / 16);
+    if ((e = cudaGetLastError()) != cudaSuccess) break;
+    if ((e = cudaEventRecord(b, st)) != cudaSuccess) break;
+    if ((e = cudaEventSynchronize(b)) != cudaSuccess) break;
+    e = cudaEventElapsedTime(&ms_kernel, a, b);
+  }
+  if (e == cudaSuccess) {
+    *copy_gbs = (double)bytes / (ms_copy * 1e-3) / 1e9;
+    *kernel_gbs = (double)bytes / (ms_kernel * 1e-3) / 1e9;
+  }
+  if (a) cudaEventDestroy(a);
+  if (b) cudaEventDestroy(b);
+  if (st) cudaStreamDestroy(st);
+  if (d) cudaFree(d);
+  if (h) cudaFreeHost(h);
+  cudaSetDevice(prev);
+  return e == cudaSuccess ? QRKIT_OK : QRKIT_ECUDA;
 }

@@ -129,6 +129,8 @@ _SIGS = {
     "qrkit_lm_trial": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int, _VP,
                                       ctypes.POINTER(ctypes.c_double)]),
     "qrkit_peak_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int, ctypes.POINTER(ctypes.c_double)]),
+    "qrkit_host_link_probe": (ctypes.c_int, [ctypes.c_int, ctypes.c_int64, ctypes.POINTER(ctypes.c_double),
+                                             ctypes.POINTER(ctypes.c_double)]),
     "qrkit_nielsen_update": (ctypes.c_int, [ctypes.c_double, ctypes.POINTER(ctypes.c_double),
                                             ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_int32)]),
     "qrkit_get_band_factor": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
@@ -238,6 +240,16 @@ def peak_probe(device=0, kind="tf32"):
     if st != 0:
         raise QRKitError(st, "qrkit_peak_probe failed")
     return v.value
+
+
+def host_link_probe(device=0, nbytes=1 << 30):
+    """qrkit_host_link_probe: (copy-engine GB/s, kernel zero-copy read GB/s) host -> device."""
+    lib = load()
+    c, k = ctypes.c_double(0.0), ctypes.c_double(0.0)
+    st = lib.qrkit_host_link_probe(int(device), int(nbytes), ctypes.byref(c), ctypes.byref(k))
+    if st != 0:
+        raise QRKitError(st, "qrkit_host_link_probe failed")
+    return c.value, k.value
 
 
 def nielsen_update(rho, lam, nu):
