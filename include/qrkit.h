@@ -269,6 +269,42 @@ qrkit_status qrkit_solve_r(qrkit_ctx* ctx, const void* qtb, void* p);
  * QRKIT_FP32, allowed but not useful for QRKIT_FP64). */
 qrkit_status qrkit_solve(qrkit_ctx* ctx, const void* b, void* p, int refine_steps);
 
+/* ---- A dense S split by rows over several contexts (one per GPU): the horizontal
+ * concatenation of Sec. 4.2 with the reduced shared block factored by TSQR across GPUs.  Each
+ * context plans its own blocks and their rows of S, factors them with the global D (the shared
+ * columns' damping entries set to zero, so that those rows enter once, at the merge), and
+ * reports its s x s triangle R_g and c_g (the last s entries of qrkit_apply_qt); the stacked
+ * [R_1; c_1 .. R_G; c_G; lambda^(1/2) D_S; 0] is solved once by qrkit_dense_lstsq, and each
+ * context finishes its block unknowns with qrkit_solve_blocks. ---- */
+
+/* Squared column sums of J = [blkdiag(J_i) | S] (DEVICE out, N doubles), added in a fixed
+ * order: summed over contexts they give the global column norms (Sec. 5.2 D = diag(J^T J)^(1/2)).
+ * Asynchronous. */
+qrkit_status qrkit_column_sumsq(qrkit_ctx* ctx, const void* J, const void* S, double* sq);
+
+/* D = sqrt(sq), zero -> 1 (Sec. 5.2, the MINPACK convention for a zero column), n values, D in
+ * the context precision (DEVICE).  Asynchronous. */
+qrkit_status qrkit_norms_from_sumsq(qrkit_ctx* ctx, const double* sq, int64_t n, void* D);
+
+/* The s x s upper triangle R_S of the reduced shared block of the last qrkit_factor on a dense-S
+ * plan (Sec. 4.2 Q_1-perp^T A_2 factored by TSQR), DEVICE out, column-major, zeros below the
+ * diagonal.  Asynchronous. */
+qrkit_status qrkit_get_reduced_r(qrkit_ctx* ctx, void* R);
+
+/* The block unknowns for given shared unknowns (Sec. 5.1 back-substitution, the reduced solve
+ * left out): qtb as from qrkit_apply_qt; p (DEVICE, N values) holds the shared unknowns in its
+ * last s entries on entry and receives the block unknowns R_i^{-1} (c_i - R12_i p_S) in its first
+ * sum m_i entries.  Asynchronous. */
+qrkit_status qrkit_solve_blocks(qrkit_ctx* ctx, const void* qtb, void* p);
+
+/* min ||A x - b|| for a dense A (DEVICE, M x N column-major, leading dimension lda, M >= N) by
+ * Householder QR (Sec. 2) in one CTA, in the context precision; A and b are not changed.
+ * res2 (HOST, may be NULL; the call then waits for the stream) receives ||b - A x||^2.  For the
+ * merge of distributed triangles: N <= 1024 and M N <= 2^24 (QRKIT_EUNSUPPORTED beyond).
+ * A zero pivot is reported as QRKIT_ESINGULAR in the device status word. */
+qrkit_status qrkit_dense_lstsq(qrkit_ctx* ctx, int64_t M, int64_t N, const void* A, int64_t lda, const void* b,
+                               void* x, double* res2);
+
 /* Comparison path (Sec. 1, Sec. 6.1 "QRkit+Chol"): p from the normal equations Eq. (1),
  * (J^T J + lambda D^2) p = J^T b, by Cholesky in the context's precision (float for both float
  * modes; no refinement), for a QRKIT_STRUCT_BLOCKS plan of any coupling.  The block unknowns

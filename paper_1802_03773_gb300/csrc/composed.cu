@@ -846,7 +846,7 @@ void release_composed(Composed& C) {
   release(C.D); release(C.sq); release(C.Fa); release(C.tau); release(C.R12); release(C.ctop);
   release(C.g); release(C.h);
   release(C.Xw); release(C.Xstart); release(C.rhs_red); release(C.RwS); release(C.cS);
-  release(C.res2); release(C.meta);
+  release(C.res2); release(C.meta); release(C.dense_ws);
   release(C.sort_tab); release(C.hist); release(C.spos); release(C.order); release(C.Xw_s);
   release(C.Xstart_s); release(C.rhs_s); release(C.seg_inst);
   release_cr(C.cr);
@@ -1041,6 +1041,72 @@ static qrkit_status solve_r_typed(qrkit_ctx* ctx, const void* qtb, void* p) {
 qrkit_status composed_solve_r(qrkit_ctx* ctx, const void* qtb, void* p) {
   if (ctx->precision == QRKIT_FP64) return solve_r_typed<double>(ctx, qtb, p);
   return solve_r_typed<float>(ctx, qtb, p);
+}
+
+// Distributed pieces (a dense S whose rows are split over several contexts): the squared column
+// sums of J, the R of the reduced shared block, and the block unknowns for given shared ones.
+qrkit_status composed_column_sumsq(qrkit_ctx* ctx, const void* J, const void* S, double* out) {
+  Composed& C = ctx->comp;
+  const int64_t N = ctx->plan.cols + ctx->plan.s.shared_cols;
+  qrkit_status rc;
+  if ((rc = ensure(ctx, C.D, (size_t)N * sizeof(double), "D")) != QRKIT_OK) return rc;
+  if ((rc = composed_column_norms(ctx, J, S, (double*)C.D.ptr)) != QRKIT_OK) return rc;
+  QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(out, C.sq.ptr, (size_t)N * sizeof(double), cudaMemcpyDeviceToDevice,
+                                      ctx->stream));
+  return QRKIT_OK;
+}
+
+template <typename T>
+__global__ void norms_from_sumsq_kernel(const double* sq, T* D, int64_t n) {
+  const int64_t j = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (j >= n) return;
+  const double d = sqrt(sq[j]);
+  D[j] = (T)(d == 0.0 ? 1.0 : d);   // zero column norm -> 1
+}
+
+qrkit_status composed_norms_from_sumsq(qrkit_ctx* ctx, const double* sq, int64_t n, void* D) {
+  if (ctx->precision == QRKIT_FP64)
+    LAUNCH(ctx, norms_from_sumsq_kernel<double><<<blocks_for(n, 256), 256, 0, ctx->stream>>>(sq, (double*)D, n));
+  else
+    LAUNCH(ctx, norms_from_sumsq_kernel<float><<<blocks_for(n, 256), 256, 0, ctx->stream>>>(sq, (float*)D, n));
+  return QRKIT_OK;
+}
+
+template <typename T>
+__global__ void copy_upper_kernel(const T* X, int64_t ld, int s, T* R) {
+  const int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (e >= (int64_t)s * s) return;
+  const int i = (int)(e % s), j = (int)(e / s);
+  R[e] = i <= j ? X[(int64_t)j * ld + i] : T(0);
+}
+
+qrkit_status composed_reduced_r(qrkit_ctx* ctx, void* R) {
+  Composed& C = ctx->comp;
+  const int s = (int)ctx->plan.s.shared_cols;
+  const TsqrLevel& top = C.levels.back();
+  if (ctx->precision == QRKIT_FP64)
+    LAUNCH(ctx, copy_upper_kernel<double><<<blocks_for((int64_t)s * s, 256), 256, 0, ctx->stream>>>(
+                    (const double*)top.X.ptr, top.M, s, (double*)R));
+  else
+    LAUNCH(ctx, copy_upper_kernel<float><<<blocks_for((int64_t)s * s, 256), 256, 0, ctx->stream>>>(
+                    (const float*)top.X.ptr, top.M, s, (float*)R));
+  return QRKIT_OK;
+}
+
+template <typename T>
+static qrkit_status solve_blocks_typed(qrkit_ctx* ctx, const void* qtb, void* p) {
+  Plan& P = ctx->plan;
+  ComposedView<T> V = view<T>(ctx, nullptr, nullptr);
+  FactorOut<T> O = fout<T>(ctx);
+  T* x = (T*)p;
+  LAUNCH(ctx, block_backsub_kernel<T><<<blocks_for(P.K, 64), 64, 0, ctx->stream>>>(
+                  V, O, (const T*)qtb, V.s ? x + P.cols : nullptr, x, 0));
+  return QRKIT_OK;
+}
+
+qrkit_status composed_solve_blocks(qrkit_ctx* ctx, const void* qtb, void* p) {
+  if (ctx->precision == QRKIT_FP64) return solve_blocks_typed<double>(ctx, qtb, p);
+  return solve_blocks_typed<float>(ctx, qtb, p);
 }
 
 }  // namespace qrkit

@@ -366,6 +366,50 @@ qrkit_status qrkit_more_solve(qrkit_ctx* ctx, const void* qtb, const void* D, do
   return more_stage2(ctx, qtb, D, lambda, p);
 }
 
+static qrkit_status need_dense_plan(qrkit_ctx* ctx, const char* what) {
+  const Plan& P = ctx->plan;
+  if (!P.valid || P.s.kind != QRKIT_STRUCT_BLOCKS || P.s.coupled_kind != QRKIT_COUPLED_DENSE)
+    return fail(ctx, QRKIT_ESTATE, std::string(what) + " needs a plan with a dense S");
+  return QRKIT_OK;
+}
+
+qrkit_status qrkit_column_sumsq(qrkit_ctx* ctx, const void* J, const void* S, double* sq) {
+  if (!ctx) return QRKIT_EINVAL;
+  const Plan& P = ctx->plan;
+  if (!P.valid || P.s.kind != QRKIT_STRUCT_BLOCKS) return fail(ctx, QRKIT_ESTATE, "qrkit_column_sumsq needs a block plan");
+  if (!J || !sq || (P.s.coupled_kind != QRKIT_COUPLED_NONE && !S)) return fail(ctx, QRKIT_EINVAL, "J, S and sq are required");
+  QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  return composed_column_sumsq(ctx, J, S, sq);
+}
+
+qrkit_status qrkit_norms_from_sumsq(qrkit_ctx* ctx, const double* sq, int64_t n, void* D) {
+  if (!ctx) return QRKIT_EINVAL;
+  if (!sq || !D || n < 1) return fail(ctx, QRKIT_EINVAL, "sq, D and n >= 1 are required");
+  QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  return composed_norms_from_sumsq(ctx, sq, n, D);
+}
+
+qrkit_status qrkit_get_reduced_r(qrkit_ctx* ctx, void* R) {
+  if (!ctx) return QRKIT_EINVAL;
+  qrkit_status st = need_dense_plan(ctx, "qrkit_get_reduced_r");
+  if (st != QRKIT_OK) return st;
+  if (!ctx->comp_factored) return fail(ctx, QRKIT_ESTATE, "qrkit_get_reduced_r before qrkit_factor");
+  if (!R) return fail(ctx, QRKIT_EINVAL, "R is required");
+  QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  return composed_reduced_r(ctx, R);
+}
+
+qrkit_status qrkit_solve_blocks(qrkit_ctx* ctx, const void* qtb, void* p) {
+  if (!ctx) return QRKIT_EINVAL;
+  const Plan& P = ctx->plan;
+  if (!P.valid || P.s.kind != QRKIT_STRUCT_BLOCKS || P.s.coupled_kind == QRKIT_COUPLED_WINDOW)
+    return fail(ctx, QRKIT_ESTATE, "qrkit_solve_blocks needs a block plan without windows");
+  if (!ctx->comp_factored) return fail(ctx, QRKIT_ESTATE, "qrkit_solve_blocks before qrkit_factor");
+  if (!qtb || !p) return fail(ctx, QRKIT_EINVAL, "qtb and p are required");
+  QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  return composed_solve_blocks(ctx, qtb, p);
+}
+
 qrkit_status qrkit_set_wait_limit(qrkit_ctx* ctx, int64_t polls) {
   if (!ctx) return QRKIT_EINVAL;
   if (polls < 0) return fail(ctx, QRKIT_EINVAL, "polls must be >= 0");

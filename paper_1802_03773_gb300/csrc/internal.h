@@ -182,6 +182,7 @@ struct Composed {
   DevBuf nrm_D, nrm_L, nrm_W, nrm_y, nrm_As, nrm_rs, nrm_seg;
   DevBuf d_aug_off_d, d_aug_off_u, d_red_off_d, d_red_off_u;
   std::vector<TsqrLevel> levels;
+  DevBuf dense_ws;                 // qrkit_dense_lstsq: the copied matrix and rhs
   const void* J = nullptr;         // caller's values recorded at factor time
   const void* S = nullptr;
 };
@@ -278,6 +279,11 @@ qrkit_status composed_solve(qrkit_ctx* ctx, const void* J, const void* S, const 
                             int refine_steps);
 qrkit_status composed_apply_qt(qrkit_ctx* ctx, const void* b, void* qtb);
 qrkit_status composed_solve_r(qrkit_ctx* ctx, const void* qtb, void* p);
+// Pieces of the dense-S solve split over several contexts (distributed TSQR).
+qrkit_status composed_column_sumsq(qrkit_ctx* ctx, const void* J, const void* S, double* out);
+qrkit_status composed_norms_from_sumsq(qrkit_ctx* ctx, const double* sq, int64_t n, void* D);
+qrkit_status composed_reduced_r(qrkit_ctx* ctx, void* R);
+qrkit_status composed_solve_blocks(qrkit_ctx* ctx, const void* qtb, void* p);
 void release_composed(Composed& C);
 qrkit_status banded_plan(qrkit_ctx* ctx, const qrkit_structure* s);
 qrkit_status banded_factor_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,

@@ -125,6 +125,12 @@ _SIGS = {
     "qrkit_set_refinement": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int]),
     "qrkit_set_wait_limit": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "qrkit_more_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, _VP]),
+    "qrkit_column_sumsq": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
+    "qrkit_norms_from_sumsq": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP]),
+    "qrkit_get_reduced_r": (ctypes.c_int, [_VP, _VP]),
+    "qrkit_solve_blocks": (ctypes.c_int, [_VP, _VP, _VP]),
+    "qrkit_dense_lstsq": (ctypes.c_int, [_VP, ctypes.c_int64, ctypes.c_int64, _VP, ctypes.c_int64, _VP, _VP,
+                                         ctypes.POINTER(ctypes.c_double)]),
     "qrkit_get_info": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.POINTER(Info)]),
     "qrkit_lm_trial": (ctypes.c_int, [_VP, _VP, _VP, _VP, _VP, ctypes.c_double, ctypes.c_int, _VP,
                                       ctypes.POINTER(ctypes.c_double)]),
@@ -487,6 +493,28 @@ class Context:
         self._check(self.lib.qrkit_get_info(self.h, self._t(J, "J"), self._t(b, "b"), self._t(p, "p"),
                                             self._t(D, "D", True), float(lam), ctypes.byref(out)))
         return {k: getattr(out, k) for k, _ in Info._fields_}
+
+    # ---- pieces of a dense-S solve split over several contexts ----
+    def column_sumsq(self, J, S, sq):
+        """sq: float64 CUDA tensor of N entries (squared column sums of J)."""
+        self._check(self.lib.qrkit_column_sumsq(self.h, self._t(J, "J"), self._t(S, "S", True), _ptr(sq)))
+
+    def norms_from_sumsq(self, sq, D):
+        self._check(self.lib.qrkit_norms_from_sumsq(self.h, _ptr(sq), int(sq.numel()), self._t(D, "D")))
+
+    def reduced_r(self, R):
+        self._check(self.lib.qrkit_get_reduced_r(self.h, self._t(R, "R")))
+
+    def solve_blocks(self, qtb, p):
+        self._check(self.lib.qrkit_solve_blocks(self.h, self._t(qtb, "qtb"), self._t(p, "p")))
+
+    def dense_lstsq(self, A, b, x):
+        """A: (N, M) contiguous tensor viewed as M x N column-major (A.T of a row-major M x N)."""
+        N, M = A.shape
+        r2 = ctypes.c_double(0.0)
+        self._check(self.lib.qrkit_dense_lstsq(self.h, int(M), int(N), self._t(A, "A"), int(M), self._t(b, "b"),
+                                               self._t(x, "x"), ctypes.byref(r2)))
+        return r2.value
 
     def more_solve(self, qtb, p, D=None, lam=0.0):
         """Moré's second factorization for the stored block factor (qtb from factor_solve)."""
