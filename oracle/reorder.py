@@ -18,7 +18,7 @@ position k, row_start[k] = first new column of that row (cols for an empty row),
 width w = max over rows of (last - first + 1) (0 without non-zeros): row k of P_r A P_c lies
 in columns row_start[k] .. row_start[k] + w - 1.
 
-Pins (tests/test_oracle_reorder.py): a hand-worked example (tests/golden/band_order_worked.json),
+Pins (tests/test_oracle_reorder.py): a hand-worked example (5 rows, 4 columns) written out in that test,
 banded patterns with scrambled rows and columns get their band width back, the permutations
 are permutations, every row lies in its band, and rows are sorted by their starts.
 """
