@@ -412,10 +412,11 @@ __global__ void block_backsub_kernel(ComposedView<T> V, FactorOut<T> O, const T*
 
 // ---- refinement: g = J^T (b - J p) - lambda D^2 p in double ----
 constexpr int kCtaSumCols = 4096;   // dense S: shared columns summed per CTA in shared memory
+constexpr int kWinSumCols = 2048;   // windowed S: the column range of a CTA summed in shared memory
 
 template <typename T>
 __device__ __forceinline__ void resid_g_block(ComposedView<T> V, const T* b, const T* p, const double* D,
-                                              double lam, double* g, double* gS, int64_t i) {
+                                              double lam, double* g, double* gS, int64_t goff, int64_t i) {
   const int n = V.n[i], m = V.m[i];
   const int64_t c0 = V.col_off[i], r0 = V.row_off[i];
   const T* J = V.J + V.val_off[i];
@@ -449,14 +450,45 @@ __device__ __forceinline__ void resid_g_block(ComposedView<T> V, const T* b, con
     for (int t = 0; t < V.w; ++t) {
       double acc = 0;
       for (int r = 0; r < n; ++r) acc += (double)V.S[r0 * V.w + (int64_t)t * n + r] * res[r];
-      if (acc != 0.0 && st + t < V.s) atomicAdd(&gS[st + t], acc);
+      if (acc != 0.0 && st + t < V.s) atomicAdd(&gS[st + t - goff], acc);
     }
   }
 }
 
+// Windowed S: the columns the CTA's blocks touch, [lo, hi) with hi = max start + w (uniform
+// over the CTA; blocks past K do not count).  The kernels sum into shared memory when the range
+// fits (consecutive blocks of one LM problem share its few hundred columns), so a column leaves
+// the CTA with one global atomic instead of one per block.
+template <typename T>
+__device__ __forceinline__ bool window_range(const ComposedView<T>& V, int64_t i, int cap, int64_t& lo, int& width) {
+  __shared__ unsigned long long rng[2];
+  if (threadIdx.x == 0) {
+    rng[0] = ~0ull;
+    rng[1] = 0ull;
+  }
+  __syncthreads();
+  unsigned long long mn = ~0ull, mx = 0ull;
+  if (i < V.K) mn = mx = (unsigned long long)V.start[i];
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    mn = min(mn, __shfl_xor_sync(0xffffffffu, mn, d));
+    mx = max(mx, __shfl_xor_sync(0xffffffffu, mx, d));
+  }
+  if ((threadIdx.x & 31) == 0 && mn != ~0ull) {
+    atomicMin(&rng[0], mn);
+    atomicMax(&rng[1], mx);
+  }
+  __syncthreads();
+  if (rng[0] == ~0ull) return false;
+  lo = (int64_t)rng[0];
+  const int64_t w = (int64_t)rng[1] + V.w - lo;
+  width = (int)(w < (int64_t)cap ? w : (int64_t)cap);
+  return w <= cap;
+}
+
 template <typename T>
 __global__ void resid_g_kernel(ComposedView<T> V, const T* b, const T* p, const double* D,
-                               double lam, double* g, double* gS) {
+                               double lam, double* g, double* gS, int win_cols) {
   // dense S: every block adds to all s shared columns; the CTA's sums are gathered in shared
   // memory and leave with one global atomic per column
   extern __shared__ double sgS[];
@@ -466,11 +498,23 @@ __global__ void resid_g_kernel(ComposedView<T> V, const T* b, const T* p, const 
     __syncthreads();
   }
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < V.K) resid_g_block(V, b, p, D, lam, g, cta_sum ? sgS : gS, i);
+  int64_t lo = 0;
+  int width = 0;
+  const bool win_sum = V.coupled == QRKIT_COUPLED_WINDOW && win_cols > 0 && window_range(V, i, win_cols, lo, width);
+  if (win_sum) {
+    for (int c = threadIdx.x; c < width; c += blockDim.x) sgS[c] = 0.0;
+    __syncthreads();
+  }
+  if (i < V.K) resid_g_block(V, b, p, D, lam, g, (cta_sum || win_sum) ? sgS : gS, win_sum ? lo : 0, i);
   if (cta_sum) {
     __syncthreads();
     for (int c = threadIdx.x; c < V.s; c += blockDim.x)
       if (sgS[c] != 0.0) atomicAdd(&gS[c], sgS[c]);
+  }
+  if (win_sum) {
+    __syncthreads();
+    for (int c = threadIdx.x; c < width; c += blockDim.x)
+      if (sgS[c] != 0.0) atomicAdd(&gS[lo + c], sgS[c]);
   }
 }
 
@@ -486,7 +530,7 @@ __global__ void gS_damping_kernel(double* gS, const float* pf, const double* pd,
 // h_i = R_i^{-T} g_i per block; then gS -= R12_i^T h_i (dense S: summed per CTA first).
 template <typename T>
 __device__ __forceinline__ void fwdsub_rt_block(ComposedView<T> V, FactorOut<T> O, const double* g, T* h,
-                                                double* gS, int64_t i) {
+                                                double* gS, int64_t goff, int64_t i) {
   const int n = V.n[i], m = V.m[i];
   const int na = n + (O.damp ? m : 0);
   const int64_t c0 = V.col_off[i];
@@ -504,14 +548,14 @@ __device__ __forceinline__ void fwdsub_rt_block(ComposedView<T> V, FactorOut<T> 
       if (st + t >= V.s) continue;
       double acc = 0;
       for (int k = 0; k < m; ++k) acc += (double)O.R12[(c0 + k) * (int64_t)V.w + t] * (double)hv[k];
-      if (acc != 0.0) atomicAdd(&gS[st + t], -acc);
+      if (acc != 0.0) atomicAdd(&gS[st + t - goff], -acc);
     }
   }
 }
 
 template <typename T>
 __global__ void block_fwdsub_rt_kernel(ComposedView<T> V, FactorOut<T> O, const double* g, T* h,
-                                       double* gS) {
+                                       double* gS, int win_cols) {
   extern __shared__ double sgS[];
   const bool cta_sum = V.coupled == QRKIT_COUPLED_DENSE && V.s <= kCtaSumCols;
   if (cta_sum) {
@@ -519,11 +563,23 @@ __global__ void block_fwdsub_rt_kernel(ComposedView<T> V, FactorOut<T> O, const 
     __syncthreads();
   }
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
-  if (i < V.K) fwdsub_rt_block(V, O, g, h, cta_sum ? sgS : gS, i);
+  int64_t lo = 0;
+  int width = 0;
+  const bool win_sum = V.coupled == QRKIT_COUPLED_WINDOW && win_cols > 0 && window_range(V, i, win_cols, lo, width);
+  if (win_sum) {
+    for (int c = threadIdx.x; c < width; c += blockDim.x) sgS[c] = 0.0;
+    __syncthreads();
+  }
+  if (i < V.K) fwdsub_rt_block(V, O, g, h, (cta_sum || win_sum) ? sgS : gS, win_sum ? lo : 0, i);
   if (cta_sum) {
     __syncthreads();
     for (int c = threadIdx.x; c < V.s; c += blockDim.x)
       if (sgS[c] != 0.0) atomicAdd(&gS[c], sgS[c]);
+  }
+  if (win_sum) {
+    __syncthreads();
+    for (int c = threadIdx.x; c < width; c += blockDim.x)
+      if (sgS[c] != 0.0) atomicAdd(&gS[lo + c], sgS[c]);
   }
 }
 
@@ -753,13 +809,21 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
     T* h = (T*)C.h.ptr;
     double* gS = g + nb;
     if (s > 0) QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(gS, 0, (size_t)s * sizeof(double), st));
-    const size_t sum_smem = (V.coupled == QRKIT_COUPLED_DENSE && s <= kCtaSumCols) ? (size_t)s * sizeof(double) : 0;
-    LAUNCH(ctx, resid_g_kernel<T><<<blocks_for(P.K, 64), 64, sum_smem, st>>>(V, (const T*)b, x, O.D, C.lam, g, gS));
+    // dense S: all s columns per CTA; windowed S: the CTA's column range (up to kWinSumCols),
+    // with larger CTAs so that more blocks share a column sum
+    const bool win = V.coupled == QRKIT_COUPLED_WINDOW;
+    const int rthreads = win ? 256 : 64;
+    const size_t sum_smem = (V.coupled == QRKIT_COUPLED_DENSE && s <= kCtaSumCols) ? (size_t)s * sizeof(double)
+                            : win ? (size_t)kWinSumCols * sizeof(double) : 0;
+    const int win_cols = win ? kWinSumCols : 0;
+    LAUNCH(ctx, resid_g_kernel<T><<<blocks_for(P.K, rthreads), rthreads, sum_smem, st>>>(
+                    V, (const T*)b, x, O.D, C.lam, g, gS, win_cols));
     if (s > 0)
       LAUNCH(ctx, gS_damping_kernel<<<blocks_for(s, 128), 128, 0, st>>>(
                       gS, sizeof(T) == 4 ? (const float*)x : nullptr,
                       sizeof(T) == 8 ? (const double*)x : nullptr, O.D, nb, s, C.lam));
-    LAUNCH(ctx, block_fwdsub_rt_kernel<T><<<blocks_for(P.K, 64), 64, sum_smem, st>>>(V, O, g, h, gS));
+    LAUNCH(ctx, block_fwdsub_rt_kernel<T><<<blocks_for(P.K, rthreads), rthreads, sum_smem, st>>>(V, O, g, h, gS,
+                                                                                               win_cols));
     if (V.coupled == QRKIT_COUPLED_WINDOW && C.cr) {
       // dp_S = R_S^{-1} R_S^{-T} (g_S - R12^T h_B) with the parallel banded factor
       qrkit_status rc = cr_normal_solve(ctx, *C.cr, gS, h + nb);

@@ -35,6 +35,7 @@
 namespace qrkit {
 
 constexpr int kTilePts = 256;   // points per reduction tile (tiles never cross problems)
+constexpr int kEvalSumCols = 2048;   // problems up to this many columns: S column sums per tile in shared memory
 
 struct LMTables {
   int64_t B = 0, NP = 0, s = 0, N = 0, num_tiles = 0;
@@ -55,6 +56,7 @@ struct LM {
   DevBuf hist, feat;                   // per problem: step history (12) and policy features (16)
   bool policy = false;                 // damping from the MLP after accepted steps
   bool prepared = false;
+  int sum_cols = 0;                    // columns of the widest problem when it fits a tile's shared sums
   cudaGraphExec_t graph = nullptr;
   int graph_refine = -1;
   int64_t graph_launches = 0;          // kernels in one captured iteration
@@ -113,16 +115,27 @@ __device__ __forceinline__ double block_sum(double v, double* red) {
 }
 
 // Residual, Jacobian blocks, windows, b = -f, squared column norms and the cost per tile.
+// A tile lies in one problem: when the problem's columns fit (sum_cols > 0), the squared
+// column sums of S are gathered in shared memory and leave the tile with one global atomic per
+// column touched, instead of eight per point.
 template <typename T>
 __global__ void __launch_bounds__(kTilePts)
 cf_eval_kernel(LMTables t, const double* x, const double* data, T* J, T* S, T* b, int32_t* start,
-               double* d2, double* tile_cost) {
+               double* d2, double* tile_cost, int sum_cols) {
   __shared__ double red[kTilePts / 32];
+  extern __shared__ double scol[];
   const int64_t tile = blockIdx.x;
   const int64_t i = t.tile_p0[tile] + threadIdx.x;
+  const int kt = t.tile_prob[tile];
+  const int ncol = (int)(t.c0[kt + 1] - t.c0[kt]);
+  const bool tile_sum = ncol <= sum_cols;
+  if (tile_sum) {
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x) scol[c] = 0.0;
+    __syncthreads();
+  }
   double fsq = 0.0;
   if (i < t.tile_p0[tile + 1]) {
-    const int k = t.tile_prob[tile];
+    const int k = kt;
     const int64_t Kc = (t.c0[k + 1] - t.c0[k]) / 2;
     const double ti = x[i];
     const int64_t seg = segment_of(ti, Kc);
@@ -158,13 +171,24 @@ cf_eval_kernel(LMTables t, const double* x, const double* data, T* J, T* S, T* b
       Si[4 * q + 3] = v;      // (row y, column 2q + 1)
       const double v2 = (double)v * (double)v;
       if (v2 != 0.0) {
-        atomicAdd(dS + 2 * q, v2);
-        atomicAdd(dS + 2 * q + 1, v2);
+        if (tile_sum) {
+          atomicAdd(&scol[2 * seg + 2 * q], v2);
+          atomicAdd(&scol[2 * seg + 2 * q + 1], v2);
+        } else {
+          atomicAdd(dS + 2 * q, v2);
+          atomicAdd(dS + 2 * q + 1, v2);
+        }
       }
     }
   }
   const double s = block_sum(fsq, red);
   if (threadIdx.x == 0) tile_cost[tile] = s;
+  if (tile_sum) {
+    __syncthreads();
+    double* dP = d2 + t.NP + t.c0[kt];
+    for (int c = threadIdx.x; c < ncol; c += blockDim.x)
+      if (scol[c] != 0.0) atomicAdd(dP + c, scol[c]);
+  }
 }
 
 // E_j = lambda_k^(1/2) D_j with D_j = ||column j of J|| (zero -> 1).
@@ -377,8 +401,8 @@ qrkit_status lm_iteration(qrkit_ctx* ctx, double* x, int refine_steps, double ft
   double* E = (double*)L.E.ptr;
   QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(d2 + t.NP, 0, (size_t)t.s * sizeof(double), st));
   QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(L.ndone.ptr, 0, sizeof(int), st));
-  LM_LAUNCH(ctx, cf_eval_kernel<T><<<(unsigned)t.num_tiles, kTilePts, 0, st>>>(
-                     t, x, L.data, J, Sv, b, (int32_t*)L.start.ptr, d2, (double*)L.tile_cost.ptr));
+  LM_LAUNCH(ctx, cf_eval_kernel<T><<<(unsigned)t.num_tiles, kTilePts, (size_t)L.sum_cols * sizeof(double), st>>>(
+                     t, x, L.data, J, Sv, b, (int32_t*)L.start.ptr, d2, (double*)L.tile_cost.ptr, L.sum_cols));
   LM_LAUNCH(ctx, lm_damp_kernel<<<nblk(t.N, 256), 256, 0, st>>>(t, d2, S, E));
   qrkit_status rc = window_start_copy(ctx, (const int32_t*)L.start.ptr);
   if (rc != QRKIT_OK) return rc;
@@ -500,6 +524,11 @@ qrkit_status qrkit_lm_plan(qrkit_ctx* ctx, const qrkit_lm_problem* pr) {
   L.t.N = NP + s;
   L.h_p0 = p0;
   L.h_c0 = c0;
+  {
+    int64_t widest = 0;
+    for (size_t k = 0; k + 1 < c0.size(); ++k) widest = std::max<int64_t>(widest, c0[k + 1] - c0[k]);
+    L.sum_cols = widest <= kEvalSumCols ? (int)widest : 0;
+  }
   L.h_tile_p0.clear();
   L.h_prob_tile0.assign(B + 1, 0);
   std::vector<int32_t> tile_prob;
@@ -569,13 +598,13 @@ qrkit_status qrkit_lm_linearize(qrkit_ctx* ctx, const double* x, void* J, void* 
   double* d2 = (double*)L.d2.ptr;
   QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(d2 + t.NP, 0, (size_t)t.s * sizeof(double), st));
   if (ctx->precision == QRKIT_FP64)
-    cf_eval_kernel<double><<<(unsigned)t.num_tiles, kTilePts, 0, st>>>(
+    cf_eval_kernel<double><<<(unsigned)t.num_tiles, kTilePts, (size_t)L.sum_cols * sizeof(double), st>>>(
         t, x, L.data, (double*)L.J.ptr, (double*)L.S.ptr, (double*)L.b.ptr, (int32_t*)L.start.ptr, d2,
-        (double*)L.tile_cost.ptr);
+        (double*)L.tile_cost.ptr, L.sum_cols);
   else
-    cf_eval_kernel<float><<<(unsigned)t.num_tiles, kTilePts, 0, st>>>(
+    cf_eval_kernel<float><<<(unsigned)t.num_tiles, kTilePts, (size_t)L.sum_cols * sizeof(double), st>>>(
         t, x, L.data, (float*)L.J.ptr, (float*)L.S.ptr, (float*)L.b.ptr, (int32_t*)L.start.ptr, d2,
-        (double*)L.tile_cost.ptr);
+        (double*)L.tile_cost.ptr, L.sum_cols);
   ctx->launches += 1;
   QRKIT_CUDA_TRY(ctx, cudaGetLastError());
   const size_t es = elem_size(ctx);
