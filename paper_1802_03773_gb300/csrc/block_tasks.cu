@@ -15,12 +15,12 @@ namespace qrkit {
 namespace tasks {
 namespace {
 
-// One data buffer of a warp: the block slots of the largest task among the keys present in
-// the plan.
-int warp_slot_bytes(const Plan& P, int es) {
+// One data buffer of a warp: the block slots of the largest task among the keys of class cls
+// present in the plan.
+int warp_slot_bytes(const Plan& P, int es, int cls) {
   int best = 0;
   for (int k = 0; k < kTaskKeys; ++k) {
-    if (P.key_off[k + 1] == P.key_off[k]) continue;
+    if (P.key_off[k + 1] == P.key_off[k] || !key_in_class(k, cls)) continue;
     const int G = group_lanes(k), M = (k & 7) + 1;
     best = std::max(best, task_blocks(G) * (slot_j_bytes(G, M, es) + slot_b_bytes(G, es)));
   }
@@ -43,14 +43,35 @@ qrkit_status resident(qrkit_ctx* ctx, F setup, int threads, size_t smem, int slo
   return QRKIT_OK;
 }
 
+// One launch of the factor kernel of class CLS over tasks [t0, t1) of the plan.
+template <typename T, bool SEL, int CLS>
+qrkit_status launch_class(qrkit_ctx* ctx, TaskArgs<T> A, int64_t t0, int64_t t1, int slot) {
+  const Plan& P = ctx->plan;
+  if (t1 <= t0) return QRKIT_OK;
+  const int es = (int)sizeof(T);
+  const int wpc = P.task_warps;
+  const int threads = 32 * wpc;
+  A.hdr += t0;
+  A.num_tasks = t1 - t0;
+  A.data_bytes = warp_slot_bytes(P, es, CLS);
+  A.warp_bytes = (warp_desc_bytes((int)sizeof(TaskEntry)) + 2 * A.data_bytes + 127) / 128 * 128;
+  const size_t smem = (size_t)wpc * A.warp_bytes;
+  int per_sm = 0;
+  qrkit_status st;
+  if ((st = resident(ctx, kernel_setup<T, SEL, CLS>, threads, smem, slot, per_sm)) != QRKIT_OK) return st;
+  const int64_t want = (A.num_tasks + wpc - 1) / wpc;
+  const int64_t full = (int64_t)ctx->num_sms * per_sm;
+  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min(want, full));
+  QRKIT_CUDA_TRY(ctx, (kernel_launch<T, SEL, CLS>(A, grid, threads, smem, ctx->stream)));
+  ctx->launches += 1;
+  return QRKIT_OK;
+}
+
 template <typename T, bool SEL>
 qrkit_status launch_tasks_typed(qrkit_ctx* ctx, const void* J, const void* b, void* p, void* qtb,
                                 int refine_steps) {
   Plan& P = ctx->plan;
-  const int es = (int)sizeof(T);
-  const int wpc = P.task_warps;
   static_assert(sizeof(TaskHdr) % 16 == 0 && sizeof(RefEntry) % 16 == 0, "16-byte copies");
-  const int threads = 32 * wpc;
   TaskArgs<T> A;
   A.hdr = (const TaskHdr*)P.d_task_hdr.ptr;
   A.ent = (const TaskEntry*)P.d_task_ent.ptr;
@@ -64,8 +85,6 @@ qrkit_status launch_tasks_typed(qrkit_ctx* ctx, const void* J, const void* b, vo
   A.qtb = (T*)qtb;
   A.x = (T*)p;
   A.q_vec = qtb && ((reinterpret_cast<uintptr_t>(qtb) ^ reinterpret_cast<uintptr_t>(b)) & 15) == 0;
-  A.data_bytes = warp_slot_bytes(P, es);
-  A.warp_bytes = (warp_desc_bytes((int)sizeof(TaskEntry)) + 2 * A.data_bytes + 127) / 128 * 128;
   A.status = ctx->d_status;
   A.select = ctx->refine_select;
   A.rlist = nullptr;
@@ -89,15 +108,14 @@ qrkit_status launch_tasks_typed(qrkit_ctx* ctx, const void* J, const void* b, vo
     A.rcount = (int*)ctx->ws.tcount.ptr;
   }
   ctx->refine_stats = SEL && sizeof(T) == sizeof(float);
-  const size_t smem = (size_t)wpc * A.warp_bytes;
-  int per_sm = 0;
-  if ((st = resident(ctx, kernel_setup<T, SEL>, threads, smem, sizeof(T) == 8 ? 10 : (SEL ? 9 : 8), per_sm)) != QRKIT_OK)
-    return st;
-  const int64_t want = (P.num_tasks + wpc - 1) / wpc;
-  const int64_t full = (int64_t)ctx->num_sms * per_sm;
-  const unsigned grid = (unsigned)std::max<int64_t>(1, std::min(want, full));
-  QRKIT_CUDA_TRY(ctx, (kernel_launch<T, SEL>(A, grid, threads, smem, ctx->stream)));
-  ctx->launches += 1;
+  if constexpr (sizeof(T) == sizeof(double)) {
+    if ((st = launch_class<T, false, 0>(ctx, A, 0, P.num_tasks, 10)) != QRKIT_OK) return st;
+  } else {
+    // float: the plan puts the tasks of blocks with at most 4 columns first; each class runs
+    // in the kernel compiled for it
+    if ((st = launch_class<T, SEL, 1>(ctx, A, 0, P.narrow_tasks, SEL ? 9 : 8)) != QRKIT_OK) return st;
+    if ((st = launch_class<T, SEL, 2>(ctx, A, P.narrow_tasks, P.num_tasks, SEL ? 14 : 13)) != QRKIT_OK) return st;
+  }
   if constexpr (SEL && sizeof(T) == sizeof(float)) {
     RefineTaskArgs R;
     R.tF = (const float*)A.tF;
@@ -140,6 +158,7 @@ void release_block_tasks(Plan& P) {
   P.factor_planes = 0;
   P.rec_off.clear();
   P.num_tasks = 0;
+  P.narrow_tasks = 0;
   P.max_refine_tasks = 0;
   P.key_off.clear();
 }
@@ -237,6 +256,13 @@ qrkit_status build_block_tasks(qrkit_ctx* ctx, int64_t supertile, int warps, boo
   qrkit_status st = make_task_lists(P.K, P.n.data(), P.m.data(), P.val_off.data(), P.row_off.data(),
                                     P.col_off.data(), supertile, key_major, hdr, ent, key_count, planes, err);
   if (st != QRKIT_OK) return fail(ctx, st, err);
+  // float plans: the tasks of blocks with at most 4 columns first (kept in order), then the
+  // others; the two runs go to the factor kernels compiled for each class
+  P.narrow_tasks = 0;
+  if (ctx->precision != QRKIT_FP64) {
+    auto mid = std::stable_partition(hdr.begin(), hdr.end(), [](const TaskHdr& h) { return key_in_class(h.key, 1); });
+    P.narrow_tasks = (int64_t)(mid - hdr.begin());
+  }
   P.key_off.assign(kTaskKeys + 1, 0);
   P.rec_off.assign(kTaskKeys + 1, 0);
   P.max_refine_tasks = 0;

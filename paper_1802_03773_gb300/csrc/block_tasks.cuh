@@ -819,8 +819,19 @@ __device__ __forceinline__ void run_task(const TaskArgs<T>& A, const TaskHdr& h,
   }
 }
 
-template <typename T, bool SEL>
-__global__ void __launch_bounds__(32 * kTaskMaxWarps, sizeof(T) == 4 ? QRKIT_TASK_CTAS : 2) block_task_kernel(TaskArgs<T> A) {
+// Key classes of the factor kernel: 0 every key; for float, 1 the keys of blocks with at most
+// 4 columns (compiled for 3 resident CTAs per SM: more warps to hide latency, and their
+// register needs fit) and 2 the wider ones (2 CTAs per SM).
+__host__ __device__ constexpr bool key_in_class(int key, int cls) {
+  return cls == 0 || ((key & 7) < 4) == (cls == 1);
+}
+template <typename T, int CLS>
+constexpr int task_ctas() {
+  return sizeof(T) == 4 ? (CLS == 1 ? 3 : QRKIT_TASK_CTAS) : 2;
+}
+
+template <typename T, bool SEL, int CLS = 0>
+__global__ void __launch_bounds__(32 * kTaskMaxWarps, task_ctas<T, CLS>()) block_task_kernel(TaskArgs<T> A) {
   extern __shared__ __align__(128) unsigned char smem_raw[];
   const int lane = threadIdx.x & 31, wid = threadIdx.x >> 5, wpc = blockDim.x >> 5;
   const WarpBufs W{smem_raw + (size_t)wid * A.warp_bytes, A.data_bytes, 32 * (int)sizeof(TaskEntry)};
@@ -853,8 +864,10 @@ __global__ void __launch_bounds__(32 * kTaskMaxWarps, sizeof(T) == 4 ? QRKIT_TAS
     cp_async_commit();
     const TaskHdr h = *W.hdr(sh);
     switch (h.key) {
-#define QRKIT_TASK_CASE(k) \
-  case k: run_task<T, ((k) >> 3) + 1, ((k) & 7) + 1, SEL>(A, h, W.ent(se), W.data(sd), lane); break;
+#define QRKIT_TASK_CASE(k)                                                                       \
+  case k:                                                                                        \
+    if constexpr (key_in_class(k, CLS)) run_task<T, ((k) >> 3) + 1, ((k) & 7) + 1, SEL>(A, h, W.ent(se), W.data(sd), lane); \
+    break;
       QRKIT_TASK_KEYS(QRKIT_TASK_CASE)
 #undef QRKIT_TASK_CASE
       default: if (lane == 0) record(A.status, QRKIT_EINVAL); break;
@@ -1014,10 +1027,26 @@ __global__ void __launch_bounds__(256) unpack_factor_kernel(const TaskHdr* hdr, 
 
 // Host-side entry points of the kernels; each is defined by the translation unit that
 // instantiates its kernel (block_tasks_<kind>.cu), so the variants compile in parallel.
-template <typename T, bool SEL>
+template <typename T, bool SEL, int CLS>
 cudaError_t kernel_setup(size_t smem, int threads, int* per_sm);
-template <typename T, bool SEL>
+template <typename T, bool SEL, int CLS>
 cudaError_t kernel_launch(const TaskArgs<T>& A, unsigned grid, int threads, size_t smem, cudaStream_t st);
+
+// The definitions an instantiating translation unit expands for its (T, SEL, CLS).
+#define QRKIT_TASK_KERNEL_ENTRIES(T, SEL, CLS)                                                            \
+  template <>                                                                                             \
+  cudaError_t kernel_setup<T, SEL, CLS>(size_t smem, int threads, int* per_sm) {                          \
+    auto k = block_task_kernel<T, SEL, CLS>;                                                              \
+    cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);     \
+    if (e != cudaSuccess) return e;                                                                       \
+    return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, threads, smem);                      \
+  }                                                                                                       \
+  template <>                                                                                             \
+  cudaError_t kernel_launch<T, SEL, CLS>(const TaskArgs<T>& A, unsigned grid, int threads, size_t smem,   \
+                                         cudaStream_t st) {                                               \
+    block_task_kernel<T, SEL, CLS><<<grid, threads, smem, st>>>(A);                                       \
+    return cudaGetLastError();                                                                            \
+  }
 // RES: the refinement's residual precision (0: compensated float, 1: double).
 template <int RES>
 cudaError_t refine_setup(size_t smem, int threads, int* per_sm);

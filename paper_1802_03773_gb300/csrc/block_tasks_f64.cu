@@ -1,24 +1,11 @@
-// Instantiation of the warp-task block solve kernel for double
-// (one kernel per translation unit, so that the variants compile in parallel).
+// Instantiation of the warp-task block solve kernel for double (every key)
+// (one or two kernels per translation unit, so that the variants compile in parallel).
 #include "block_tasks.cuh"
 
 namespace qrkit {
 namespace tasks {
 
-template <>
-cudaError_t kernel_setup<double, false>(size_t smem, int threads, int* per_sm) {
-  auto k = block_task_kernel<double, false>;
-  cudaError_t e = cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
-  if (e != cudaSuccess) return e;
-  return cudaOccupancyMaxActiveBlocksPerMultiprocessor(per_sm, k, threads, smem);
-}
-
-template <>
-cudaError_t kernel_launch<double, false>(const TaskArgs<double>& A, unsigned grid, int threads, size_t smem,
-                                  cudaStream_t st) {
-  block_task_kernel<double, false><<<grid, threads, smem, st>>>(A);
-  return cudaGetLastError();
-}
+QRKIT_TASK_KERNEL_ENTRIES(double, false, 0)
 
 }  // namespace tasks
 }  // namespace qrkit

@@ -85,6 +85,7 @@ struct Plan {
   bool key_major = false;             // tasks ordered by shape key first
   int64_t num_tasks = 0;
   int64_t max_refine_tasks = 0;       // refinement tasks if every block were selected
+  int64_t narrow_tasks = 0;           // float plans: tasks [0, narrow_tasks) hold blocks of <= 4 columns
   std::vector<int64_t> key_off;       // kTaskKeys + 1: blocks per key, prefix sums
   int64_t factor_planes = 0;          // planes of the stored factor (all tasks)
   std::vector<int64_t> rec_off;       // kTaskKeys + 1: offsets of the keys' refinement records
