@@ -37,8 +37,8 @@ K_BLOCKS = 1_000_000
 WORKLOAD = "batched block-diagonal QR solve: 1,000,000 blocks n~U{2..16}, m~U{1..min(n,6)}, FP32-refined"
 KERNEL = "block_task_kernel + block_task_refine_kernel (one solve)"
 KERNEL_SRCS = [os.path.join(ROOT, "paper_1802_03773_gb300", "csrc", f)
-               for f in ("block_tasks.cuh", "block_tasks.cu", "block_tasks_f32sel.cu", "block_tasks_refine.cu",
-                         "device_util.cuh")]
+               for f in ("block_tasks.cuh", "block_tasks.cu", "block_tasks_f32sel.cu", "block_tasks_f32selw.cu",
+                         "block_tasks_refine.cu", "device_util.cuh", "internal.h")]
 
 
 def workload_config(args):
