@@ -112,6 +112,142 @@ __global__ void finalize_norms_kernel(const double* sq, double* D, int64_t N) {
 // One thread per block; the augmented block B_i = [J_i; lambda^(1/2) D_i] (na x m) is held
 // column-major in local arrays.  Outputs: factor Fa (na x m, V below / R on and above the
 // diagonal), tau, R12 rows (m x w) and the reduced rows (na - m rows).
+// Small blocks (at most NA augmented rows and MM columns, e.g. the 2 x 1 blocks of curve and
+// ellipse fits): the same factorization as the general path below, with every loop unrolled to
+// the compile-time bounds (runtime sizes as guards), so the block, its reflectors and a chunk
+// of coupled columns stay in registers instead of local memory.
+template <typename T, int NA, int MM>
+__device__ __forceinline__ void block_factor_small(const ComposedView<T>& V, const FactorOut<T>& O, int64_t i, int n,
+                                                   int m) {
+  const int na = n + (O.damp ? m : 0);
+  const T* J = V.J + V.val_off[i];
+  T B[MM][NA];
+#pragma unroll
+  for (int j = 0; j < MM; ++j)
+#pragma unroll
+    for (int r = 0; r < NA; ++r) {
+      T v = T(0);
+      if (j < m) {
+        if (r < n) v = J[j * n + r];
+        else if (O.damp && r - n == j) v = (T)(O.lam_half * O.D[V.col_off[i] + j]);
+      }
+      B[j][r] = v;
+    }
+  T tau[MM];
+  bool bad = false;
+#pragma unroll
+  for (int k = 0; k < MM; ++k) {
+    tau[k] = T(0);
+    if (k < m) {
+      T sq = 0;
+#pragma unroll
+      for (int r = 0; r < NA; ++r)
+        if (r > k && r < na) sq += B[k][r] * B[k][r];
+      const T alpha = B[k][k];
+      const T norm = sqrt(alpha * alpha + sq);
+      T beta = 0, t = 0, scale = 0;
+      if (norm != T(0)) {
+        beta = alpha >= T(0) ? -norm : norm;
+        t = (beta - alpha) / beta;
+        scale = T(1) / (alpha - beta);
+      } else {
+        bad = true;
+      }
+#pragma unroll
+      for (int r = 0; r < NA; ++r)
+        if (r > k) B[k][r] *= scale;
+      B[k][k] = beta;
+      tau[k] = t;
+#pragma unroll
+      for (int j = k + 1; j < MM; ++j) {
+        if (j < m) {
+          T w = B[j][k];
+#pragma unroll
+          for (int r = 0; r < NA; ++r)
+            if (r > k && r < na) w += B[k][r] * B[j][r];
+          w *= t;
+          B[j][k] -= w;
+#pragma unroll
+          for (int r = 0; r < NA; ++r)
+            if (r > k && r < na) B[j][r] -= w * B[k][r];
+        }
+      }
+    }
+  }
+  if (bad) record(O.status, QRKIT_ESINGULAR);
+  T* F = O.Fa + O.aug_off[i];
+#pragma unroll
+  for (int j = 0; j < MM; ++j)
+#pragma unroll
+    for (int r = 0; r < NA; ++r)
+      if (j < m && r < na) F[j * na + r] = B[j][r];
+#pragma unroll
+  for (int k = 0; k < MM; ++k)
+    if (k < m) O.tau[V.col_off[i] + k] = tau[k];
+  if (V.coupled == QRKIT_COUPLED_NONE) return;
+  const int64_t red0 = O.red_off[i];
+  for (int c0 = 0; c0 < V.w; c0 += kChunk) {
+    const int cw = min(kChunk, V.w - c0);
+    T C[kChunk][NA];
+#pragma unroll
+    for (int c = 0; c < kChunk; ++c)
+#pragma unroll
+      for (int r = 0; r < NA; ++r) {
+        T v = T(0);
+        if (c < cw && r < n) {
+          if (V.coupled == QRKIT_COUPLED_DENSE) v = V.S[(int64_t)(c0 + c) * V.rows + V.row_off[i] + r];
+          else v = V.S[V.row_off[i] * V.w + (int64_t)(c0 + c) * n + r];
+        }
+        C[c][r] = v;
+      }
+#pragma unroll
+    for (int k = 0; k < MM; ++k) {
+      if (k < m) {
+#pragma unroll
+        for (int c = 0; c < kChunk; ++c) {
+          T w = C[c][k];
+#pragma unroll
+          for (int r = 0; r < NA; ++r)
+            if (r > k && r < na) w += B[k][r] * C[c][r];
+          w *= tau[k];
+          C[c][k] -= w;
+#pragma unroll
+          for (int r = 0; r < NA; ++r)
+            if (r > k && r < na) C[c][r] -= w * B[k][r];
+        }
+      }
+    }
+#pragma unroll
+    for (int c = 0; c < kChunk; ++c) {
+      if (c < cw) {
+#pragma unroll
+        for (int r = 0; r < NA; ++r) {
+          if (r < m) {
+            O.R12[(V.col_off[i] + r) * (int64_t)V.w + c0 + c] = C[c][r];
+          } else if (r < na) {
+            const int64_t row = red0 + (r - m);
+            if (V.coupled == QRKIT_COUPLED_DENSE) {
+              O.X0[(int64_t)(c0 + c) * O.ld0 + row] = C[c][r];
+            } else {
+              O.Xw[row * V.w + c0 + c] = C[c][r];
+              if (c0 + c == 0) O.Xstart[row] = V.start[i];
+            }
+          }
+        }
+      }
+    }
+  }
+}
+
+// Plans whose blocks all fit (NA, MM) run this kernel (its register needs are those of the
+// small blocks only).
+template <typename T, int NA, int MM>
+__global__ void block_factor_small_kernel(ComposedView<T> V, FactorOut<T> O) {
+  const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
+  if (i >= V.K) return;
+  block_factor_small<T, NA, MM>(V, O, i, V.n[i], V.m[i]);
+}
+
 template <typename T>
 __global__ void block_factor_kernel(ComposedView<T> V, FactorOut<T> O) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
@@ -320,11 +456,40 @@ tsqr_apply_qt_kernel(const T* X, int64_t ld, int64_t M, int s, int tile_rows, co
     for (int i = tid; i < kmax; i += blockDim.x) rhs_next[(int64_t)blockIdx.x * s + i] = y[i];
 }
 
-// Per-block Q_i^T [b_i; 0]: top m -> ctop, bottom -> reduced rhs rows.
-template <typename T>
+// Per-block Q_i^T [b_i; 0]: top m -> ctop, bottom -> reduced rhs rows.  NA > 0: every block has
+// at most NA augmented rows and MM columns (loops unrolled to those bounds, registers only).
+template <typename T, int NA = 0, int MM = 0>
 __global__ void block_apply_qt_kernel(ComposedView<T> V, FactorOut<T> O, const T* b, T* rhs0) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= V.K) return;
+  if constexpr (NA > 0) {
+    const int n = V.n[i], m = V.m[i];
+    const int na = n + (O.damp ? m : 0);
+    T y[NA];
+#pragma unroll
+    for (int r = 0; r < NA; ++r) y[r] = r < n ? b[V.row_off[i] + r] : T(0);
+    const T* F = O.Fa + O.aug_off[i];
+#pragma unroll
+    for (int k = 0; k < MM; ++k) {
+      if (k < m) {
+        T w = y[k];
+#pragma unroll
+        for (int r = 0; r < NA; ++r)
+          if (r > k && r < na) w += F[k * na + r] * y[r];
+        w *= O.tau[V.col_off[i] + k];
+        y[k] -= w;
+#pragma unroll
+        for (int r = 0; r < NA; ++r)
+          if (r > k && r < na) y[r] -= w * F[k * na + r];
+      }
+    }
+#pragma unroll
+    for (int r = 0; r < NA; ++r) {
+      if (r < m) O.ctop[V.col_off[i] + r] = y[r];
+      else if (rhs0 && r < na) rhs0[O.red_off[i] + (r - m)] = y[r];
+    }
+    return;
+  }
   const int n = V.n[i], m = V.m[i];
   const int na = n + (O.damp ? m : 0);
   T y[kMaxRows];
@@ -381,12 +546,48 @@ __global__ void dense_fwdsub_rt_kernel(const T* R, int64_t ld, int s, const doub
   for (int k = lane; k < s; k += 32) h[k] = hs[k];
 }
 
-// Per-block R_i x_i = rhs_i - R12_i x_S; rhs from ctop (T) or from a double vector.
-template <typename T>
+// Per-block R_i x_i = rhs_i - R12_i x_S; rhs from ctop (T) or from a double vector.  NA > 0:
+// every block has at most NA augmented rows and MM columns (registers only).
+template <typename T, int NA = 0, int MM = 0>
 __global__ void block_backsub_kernel(ComposedView<T> V, FactorOut<T> O, const T* rhs_t,
                                      const T* xS, T* x, int accumulate) {
   const int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x;
   if (i >= V.K) return;
+  if constexpr (NA > 0) {
+    const int n = V.n[i], m = V.m[i];
+    const int na = n + (O.damp ? m : 0);
+    const int64_t c0 = V.col_off[i];
+    const int64_t st = V.coupled == QRKIT_COUPLED_WINDOW ? V.start[i] : 0;
+    T y[MM];
+#pragma unroll
+    for (int k = 0; k < MM; ++k) {
+      T v = T(0);
+      if (k < m) {
+        v = rhs_t[c0 + k];
+        if (V.coupled != QRKIT_COUPLED_NONE && xS) {
+          const T* r12 = O.R12 + (c0 + k) * (int64_t)V.w;
+          for (int t = 0; t < V.w; ++t)
+            if (st + t < V.s) v -= r12[t] * xS[st + t];
+        }
+      }
+      y[k] = v;
+    }
+    const T* F = O.Fa + O.aug_off[i];
+#pragma unroll
+    for (int k = MM - 1; k >= 0; --k) {
+      if (k < m) {
+        T v = y[k];
+#pragma unroll
+        for (int j = k + 1; j < MM; ++j)
+          if (j < m) v -= F[j * na + k] * y[j];
+        y[k] = v / F[k * na + k];
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < MM; ++k)
+      if (k < m) x[c0 + k] = accumulate ? x[c0 + k] + y[k] : y[k];
+    return;
+  }
   const int n = V.n[i], m = V.m[i];
   const int na = n + (O.damp ? m : 0);
   const int64_t c0 = V.col_off[i];
@@ -455,6 +656,64 @@ __device__ __forceinline__ void resid_g_block(ComposedView<T> V, const T* b, con
   }
 }
 
+// resid_g_block for blocks of at most NR rows and MM columns, every array in registers.
+template <typename T, int NR, int MM>
+__device__ __forceinline__ void resid_g_small(const ComposedView<T>& V, const T* b, const T* p, const double* D,
+                                              double lam, double* g, double* gS, int64_t goff, int64_t i) {
+  const int n = V.n[i], m = V.m[i];
+  const int64_t c0 = V.col_off[i], r0 = V.row_off[i];
+  const T* J = V.J + V.val_off[i];
+  const int64_t st = V.coupled == QRKIT_COUPLED_WINDOW ? V.start[i] : 0;
+  double pj[MM], res[NR];
+#pragma unroll
+  for (int j = 0; j < MM; ++j) pj[j] = j < m ? (double)p[c0 + j] : 0.0;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    double acc = 0.0;
+    if (r < n) {
+      acc = (double)b[r0 + r];
+#pragma unroll
+      for (int j = 0; j < MM; ++j)
+        if (j < m) acc -= (double)J[j * n + r] * pj[j];
+      if (V.coupled == QRKIT_COUPLED_DENSE) {
+        for (int c = 0; c < V.s; ++c) acc -= (double)V.S[(int64_t)c * V.rows + r0 + r] * (double)p[V.nb + c];
+      } else if (V.coupled == QRKIT_COUPLED_WINDOW) {
+        for (int t = 0; t < V.w; ++t)
+          if (st + t < V.s) acc -= (double)V.S[r0 * V.w + (int64_t)t * n + r] * (double)p[V.nb + st + t];
+      }
+    }
+    res[r] = acc;
+  }
+#pragma unroll
+  for (int j = 0; j < MM; ++j) {
+    if (j < m) {
+      double acc = 0;
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        if (r < n) acc += (double)J[j * n + r] * res[r];
+      const double d = D[c0 + j];
+      g[c0 + j] = acc - lam * d * d * pj[j];
+    }
+  }
+  if (V.coupled == QRKIT_COUPLED_DENSE) {
+    for (int c = 0; c < V.s; ++c) {
+      double acc = 0;
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        if (r < n) acc += (double)V.S[(int64_t)c * V.rows + r0 + r] * res[r];
+      if (acc != 0.0) atomicAdd(&gS[c], acc);
+    }
+  } else if (V.coupled == QRKIT_COUPLED_WINDOW) {
+    for (int t = 0; t < V.w; ++t) {
+      double acc = 0;
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        if (r < n) acc += (double)V.S[r0 * V.w + (int64_t)t * n + r] * res[r];
+      if (acc != 0.0 && st + t < V.s) atomicAdd(&gS[st + t - goff], acc);
+    }
+  }
+}
+
 // Windowed S: the columns the CTA's blocks touch, [lo, hi) with hi = max start + w (uniform
 // over the CTA; blocks past K do not count).  The kernels sum into shared memory when the range
 // fits (consecutive blocks of one LM problem share its few hundred columns), so a column leaves
@@ -486,7 +745,7 @@ __device__ __forceinline__ bool window_range(const ComposedView<T>& V, int64_t i
   return w <= cap;
 }
 
-template <typename T>
+template <typename T, int NA = 0, int MM = 0>
 __global__ void resid_g_kernel(ComposedView<T> V, const T* b, const T* p, const double* D,
                                double lam, double* g, double* gS, int win_cols) {
   // dense S: every block adds to all s shared columns; the CTA's sums are gathered in shared
@@ -505,7 +764,12 @@ __global__ void resid_g_kernel(ComposedView<T> V, const T* b, const T* p, const 
     for (int c = threadIdx.x; c < width; c += blockDim.x) sgS[c] = 0.0;
     __syncthreads();
   }
-  if (i < V.K) resid_g_block(V, b, p, D, lam, g, (cta_sum || win_sum) ? sgS : gS, win_sum ? lo : 0, i);
+  if (i < V.K) {
+    if constexpr (NA > 0)
+      resid_g_small<T, NA, MM>(V, b, p, D, lam, g, (cta_sum || win_sum) ? sgS : gS, win_sum ? lo : 0, i);
+    else
+      resid_g_block(V, b, p, D, lam, g, (cta_sum || win_sum) ? sgS : gS, win_sum ? lo : 0, i);
+  }
   if (cta_sum) {
     __syncthreads();
     for (int c = threadIdx.x; c < V.s; c += blockDim.x)
@@ -553,7 +817,42 @@ __device__ __forceinline__ void fwdsub_rt_block(ComposedView<T> V, FactorOut<T> 
   }
 }
 
-template <typename T>
+// fwdsub_rt_block for blocks of at most NA augmented rows and MM columns (registers only).
+template <typename T, int NA, int MM>
+__device__ __forceinline__ void fwdsub_rt_small(const ComposedView<T>& V, const FactorOut<T>& O, const double* g, T* h,
+                                                double* gS, int64_t goff, int64_t i) {
+  const int n = V.n[i], m = V.m[i];
+  const int na = n + (O.damp ? m : 0);
+  const int64_t c0 = V.col_off[i];
+  const T* F = O.Fa + O.aug_off[i];
+  T hv[MM];
+#pragma unroll
+  for (int k = 0; k < MM; ++k) {
+    T v = T(0);
+    if (k < m) {
+      v = (T)g[c0 + k];
+#pragma unroll
+      for (int j = 0; j < MM; ++j)
+        if (j < k) v -= F[k * na + j] * hv[j];
+      v = v / F[k * na + k];
+      h[c0 + k] = v;
+    }
+    hv[k] = v;
+  }
+  if (V.coupled != QRKIT_COUPLED_NONE) {
+    const int64_t st = V.coupled == QRKIT_COUPLED_WINDOW ? V.start[i] : 0;
+    for (int t = 0; t < V.w; ++t) {
+      if (st + t >= V.s) continue;
+      double acc = 0;
+#pragma unroll
+      for (int k = 0; k < MM; ++k)
+        if (k < m) acc += (double)O.R12[(c0 + k) * (int64_t)V.w + t] * (double)hv[k];
+      if (acc != 0.0) atomicAdd(&gS[st + t - goff], -acc);
+    }
+  }
+}
+
+template <typename T, int NA = 0, int MM = 0>
 __global__ void block_fwdsub_rt_kernel(ComposedView<T> V, FactorOut<T> O, const double* g, T* h,
                                        double* gS, int win_cols) {
   extern __shared__ double sgS[];
@@ -570,7 +869,12 @@ __global__ void block_fwdsub_rt_kernel(ComposedView<T> V, FactorOut<T> O, const 
     for (int c = threadIdx.x; c < width; c += blockDim.x) sgS[c] = 0.0;
     __syncthreads();
   }
-  if (i < V.K) fwdsub_rt_block(V, O, g, h, (cta_sum || win_sum) ? sgS : gS, win_sum ? lo : 0, i);
+  if (i < V.K) {
+    if constexpr (NA > 0)
+      fwdsub_rt_small<T, NA, MM>(V, O, g, h, (cta_sum || win_sum) ? sgS : gS, win_sum ? lo : 0, i);
+    else
+      fwdsub_rt_block(V, O, g, h, (cta_sum || win_sum) ? sgS : gS, win_sum ? lo : 0, i);
+  }
   if (cta_sum) {
     __syncthreads();
     for (int c = threadIdx.x; c < V.s; c += blockDim.x)
@@ -656,6 +960,22 @@ static FactorOut<T> fout(qrkit_ctx* ctx) {
     QRKIT_CUDA_TRY(ctx, cudaGetLastError());              \
   } while (0)
 
+// Shape class of a plan's blocks for the per-block kernels: 1 if every augmented block is at
+// most 3 x 1, 2 if at most 6 x 2, else 0 (the general kernels with runtime loops).
+int small_class(const Plan& P, bool damp) {
+  const int na = P.max_n + (damp ? P.max_m : 0);
+  if (P.max_m == 1 && na <= 3) return 1;
+  if (P.max_m <= 2 && na <= 6) return 2;
+  return 0;
+}
+// A per-block kernel template KERNEL<T, NA, MM> launched in the instantiation of the class.
+#define LAUNCH_SHAPED(ctx, cls, KERNEL, grid, threads, smem, stream, ...)                      \
+  do {                                                                                         \
+    if ((cls) == 1) LAUNCH(ctx, (KERNEL<T, 3, 1><<<grid, threads, smem, stream>>>(__VA_ARGS__))); \
+    else if ((cls) == 2) LAUNCH(ctx, (KERNEL<T, 6, 2><<<grid, threads, smem, stream>>>(__VA_ARGS__))); \
+    else LAUNCH(ctx, (KERNEL<T><<<grid, threads, smem, stream>>>(__VA_ARGS__)));                \
+  } while (0)
+
 // D = column norms of J (Sec. 5.2), zero -> 1, in double; C.sq is the scratch.
 template <typename T>
 static qrkit_status norms_typed(qrkit_ctx* ctx, const ComposedView<T>& V, double* D) {
@@ -710,7 +1030,14 @@ static qrkit_status factor_typed(qrkit_ctx* ctx, const void* J, const void* S, c
     return rc;
   }
   FactorOut<T> O = fout<T>(ctx);
-  LAUNCH(ctx, block_factor_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O));
+  // the small-block kernels when every block fits them (e.g. 2 x 1 blocks of curve fits)
+  const int cls = small_class(P, O.damp);
+  if (cls == 1)
+    LAUNCH(ctx, (block_factor_small_kernel<T, 3, 1><<<blocks_for(P.K, 128), 128, 0, st>>>(V, O)));
+  else if (cls == 2)
+    LAUNCH(ctx, (block_factor_small_kernel<T, 6, 2><<<blocks_for(P.K, 128), 128, 0, st>>>(V, O)));
+  else
+    LAUNCH(ctx, block_factor_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O));
   if (V.coupled == QRKIT_COUPLED_WINDOW) {
     // P_r of the reduced block: its rows sorted by leading column per segment (Sec. 4.3)
     rc = reduced_row_sort(ctx, C.sort, (int64_t)P.seg_cols.size(), C.sort_hist_entries,
@@ -758,7 +1085,8 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
   // Q^T [b; 0]
   T* rhs0 = (V.coupled == QRKIT_COUPLED_DENSE) ? (T*)C.levels[0].rhs.ptr
              : (V.coupled == QRKIT_COUPLED_WINDOW ? (T*)C.rhs_red.ptr : nullptr);
-  LAUNCH(ctx, block_apply_qt_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O, (const T*)b, rhs0));
+  LAUNCH_SHAPED(ctx, small_class(P, O.damp), block_apply_qt_kernel, blocks_for(P.K, 64), 64, 0, st, V, O, (const T*)b,
+                rhs0);
   if (V.coupled == QRKIT_COUPLED_DENSE) {
     if (C.damp)
       QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(rhs0 + C.red_rows, 0, (size_t)s * sizeof(T), st));
@@ -798,7 +1126,8 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
                                  C.damp ? C.lam : 0.0, C.RwS.ptr, C.cS.ptr, x + nb, (double*)C.res2.ptr);
     if (rc != QRKIT_OK) return rc;
   }
-  LAUNCH(ctx, block_backsub_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O, O.ctop, s ? x + nb : nullptr, x, 0));
+  LAUNCH_SHAPED(ctx, small_class(P, O.damp), block_backsub_kernel, blocks_for(P.K, 64), 64, 0, st, V, O, O.ctop,
+                s ? x + nb : nullptr, x, 0);
   // refinement (extended-precision residual, corrections through R only)
   for (int it = 0; it < refine_steps; ++it) {
     const int64_t N = nb + s;
@@ -816,14 +1145,14 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
     const size_t sum_smem = (V.coupled == QRKIT_COUPLED_DENSE && s <= kCtaSumCols) ? (size_t)s * sizeof(double)
                             : win ? (size_t)kWinSumCols * sizeof(double) : 0;
     const int win_cols = win ? kWinSumCols : 0;
-    LAUNCH(ctx, resid_g_kernel<T><<<blocks_for(P.K, rthreads), rthreads, sum_smem, st>>>(
-                    V, (const T*)b, x, O.D, C.lam, g, gS, win_cols));
+    LAUNCH_SHAPED(ctx, small_class(P, O.damp), resid_g_kernel, blocks_for(P.K, rthreads), rthreads, sum_smem, st, V,
+                  (const T*)b, x, O.D, C.lam, g, gS, win_cols);
     if (s > 0)
       LAUNCH(ctx, gS_damping_kernel<<<blocks_for(s, 128), 128, 0, st>>>(
                       gS, sizeof(T) == 4 ? (const float*)x : nullptr,
                       sizeof(T) == 8 ? (const double*)x : nullptr, O.D, nb, s, C.lam));
-    LAUNCH(ctx, block_fwdsub_rt_kernel<T><<<blocks_for(P.K, rthreads), rthreads, sum_smem, st>>>(V, O, g, h, gS,
-                                                                                               win_cols));
+    LAUNCH_SHAPED(ctx, small_class(P, O.damp), block_fwdsub_rt_kernel, blocks_for(P.K, rthreads), rthreads, sum_smem,
+                  st, V, O, g, h, gS, win_cols);
     if (V.coupled == QRKIT_COUPLED_WINDOW && C.cr) {
       // dp_S = R_S^{-1} R_S^{-T} (g_S - R12^T h_B) with the parallel banded factor
       qrkit_status rc = cr_normal_solve(ctx, *C.cr, gS, h + nb);
@@ -849,7 +1178,8 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
       LAUNCH(ctx, axpy_kernel<T><<<blocks_for(s, 128), 128, 0, st>>>(x + nb, h + nb, s));
     }
     // dp_B = R_B^{-1} (h_B - R12 dp_S), accumulated into p
-    LAUNCH(ctx, block_backsub_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O, h, s ? h + nb : nullptr, x, 1));
+    LAUNCH_SHAPED(ctx, small_class(P, O.damp), block_backsub_kernel, blocks_for(P.K, 64), 64, 0, st, V, O, h,
+                  s ? h + nb : nullptr, x, 1);
   }
   return QRKIT_OK;
 }
