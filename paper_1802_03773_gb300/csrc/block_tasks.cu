@@ -108,13 +108,15 @@ qrkit_status launch_tasks_typed(qrkit_ctx* ctx, const void* J, const void* b, vo
     A.rcount = (int*)ctx->ws.tcount.ptr;
   }
   ctx->refine_stats = SEL && sizeof(T) == sizeof(float);
-  if constexpr (sizeof(T) == sizeof(double)) {
-    if ((st = launch_class<T, false, 0>(ctx, A, 0, P.num_tasks, 10)) != QRKIT_OK) return st;
+  if constexpr (sizeof(T) == sizeof(double) || !SEL) {
+    // one kernel over every task: double, and float without the refinement selection (whose
+    // register needs fit 2 CTAs per SM for every key)
+    if ((st = launch_class<T, false, 0>(ctx, A, 0, P.num_tasks, sizeof(T) == 8 ? 10 : 8)) != QRKIT_OK) return st;
   } else {
-    // float: the plan puts the tasks of blocks with at most 4 columns first; each class runs
-    // in the kernel compiled for it
-    if ((st = launch_class<T, SEL, 1>(ctx, A, 0, P.narrow_tasks, SEL ? 9 : 8)) != QRKIT_OK) return st;
-    if ((st = launch_class<T, SEL, 2>(ctx, A, P.narrow_tasks, P.num_tasks, SEL ? 14 : 13)) != QRKIT_OK) return st;
+    // float with the selection: a refined plan puts the tasks of blocks with at most 4 columns
+    // first; each class runs in the kernel compiled for it
+    if ((st = launch_class<T, SEL, 1>(ctx, A, 0, P.narrow_tasks, 9)) != QRKIT_OK) return st;
+    if ((st = launch_class<T, SEL, 2>(ctx, A, P.narrow_tasks, P.num_tasks, 14)) != QRKIT_OK) return st;
   }
   if constexpr (SEL && sizeof(T) == sizeof(float)) {
     RefineTaskArgs R;
@@ -256,10 +258,12 @@ qrkit_status build_block_tasks(qrkit_ctx* ctx, int64_t supertile, int warps, boo
   qrkit_status st = make_task_lists(P.K, P.n.data(), P.m.data(), P.val_off.data(), P.row_off.data(),
                                     P.col_off.data(), supertile, key_major, hdr, ent, key_count, planes, err);
   if (st != QRKIT_OK) return fail(ctx, st, err);
-  // float plans: the tasks of blocks with at most 4 columns first (kept in order), then the
-  // others; the two runs go to the factor kernels compiled for each class
+  // FP32-refined plans: the tasks of blocks with at most 4 columns first (kept in order), then
+  // the others; the two runs go to the factor kernels compiled for each class (the other
+  // precisions keep the supertile order, in which neighbouring blocks' shared sectors are read
+  // together)
   P.narrow_tasks = 0;
-  if (ctx->precision != QRKIT_FP64) {
+  if (ctx->precision == QRKIT_FP32_REFINED) {
     auto mid = std::stable_partition(hdr.begin(), hdr.end(), [](const TaskHdr& h) { return key_in_class(h.key, 1); });
     P.narrow_tasks = (int64_t)(mid - hdr.begin());
   }

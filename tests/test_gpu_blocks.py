@@ -106,9 +106,9 @@ def test_blocks_parity_small(precision, mapping):
     tuning = {"tasks": None, "tiles": TILES["fp64" if precision == "fp64" else "fp32"]}.get(mapping, mapping)
     out = run(d, precision, tuning=tuning, refine_steps=2)
     check_blocks(d, out, range(3000), precision)
-    # one fused launch (float warp tasks: one per key class, blocks of <= 4 and of 5-8 columns,
-    # both present here); with refinement one more refines the blocks the first selected
-    factor = 2 if (precision != "fp64" and mapping != "tiles") else 1
+    # one fused launch (FP32-refined warp tasks: one per key class, blocks of <= 4 and of 5-8
+    # columns, both present here); with refinement one more refines the blocks it selected
+    factor = 2 if (precision == "fp32_refined" and mapping != "tiles") else 1
     assert out["launches"] == factor + (1 if precision == "fp32_refined" else 0)
 
 
