@@ -338,7 +338,8 @@ qrkit_status qrkit_normal_solve(qrkit_ctx* ctx, const void* J, const void* S, co
  * The work runs in the tile kernel (tiles of consecutive blocks, refinement inside the kernel),
  * not in the warp-task kernels the context path uses by default; the problem solved is the same.
  * The first call on a device looks up the array's device address (cudaGetSymbolAddress) with
- * that device current; make that first call before any stream capture begins.  The caller
+ * that device current.  Every call is synchronous (it waits for its stream and copies the
+ * status word back), so no call may be made while any stream is being captured.  The caller
  * thread's current device is the same after the call as before it.  `stream` must belong to
  * `device` (QRKIT_EINVAL otherwise).  Each call copies the shapes and schedule into the array,
  * clears its status word, launches one kernel on `stream`, then waits for the stream and reads
