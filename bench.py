@@ -450,6 +450,29 @@ def other_workloads(dev, stream, only=None):
             "reduced_block_tflops_useful": flops / (tf * 1e-3) / 1e12}
         ctx.close()
         del J, S, b
+    if want("ba_"):
+        # BA-shaped system (bundle adjustment, Sec. 6.2): 100,000 points, each seen by 2-6 of 14
+        # cameras (9 parameters each, 126 columns padded to 128: the tensor-core tiles), damped
+        from workloads import ba_system
+        d = ba_system(P=100_000, C=14, s_pad=128, dtype=np.float32)
+        K, s = d["K"], d["s"]
+        ctx = Context(dev.index, stream=stream, precision="fp32_refined")
+        ctx.plan_blocks(d["n"], np.full(K, 3), qrkit.COUPLED_DENSE, shared_cols=s)
+        J = torch.from_numpy(np.concatenate([blk.T.reshape(-1) for blk in d["blocks"]])).to(dev)
+        S = torch.from_numpy(np.asarray(d["S"]).T.reshape(-1).copy()).to(dev)
+        b = torch.from_numpy(np.asarray(d["b"])).to(dev)
+        pl = torch.empty(3 * K + s, dtype=torch.float32, device=dev)
+        torch.cuda.synchronize()
+        tf = _time(stream, lambda: ctx.factor(J, S, None, d["lam"]), 5)
+        ts = _time(stream, lambda: ctx.solve(b, pl, refine_steps=1), 5)
+        ctx.sync_status()
+        rows = int(np.sum(d["n"]))
+        out["ba_100k_points_14_cameras_fp32_refined"] = {
+            "workload": f"BA-shaped: 100,000 points x 2-6 observations ({rows} rows) of 14 cameras "
+                        f"(9 parameters each, S {rows} x 128 dense with the camera blocks), lambda 1e-3, D = norms",
+            "ms_factor": tf, "ms_solve_refined_1": ts, "value": 1000.0 / (tf + ts), "unit": "solves/s"}
+        ctx.close()
+        del J, S, b, d
     if want("ellipse_fit"):
         # the surface fitting benchmark's shape: one LM-step system of an ellipse fit to N points
         # (N blocks 2x1 + 5 dense shared columns), N over the paper's sweep, FP64

@@ -13,6 +13,8 @@ from .gen import (  # noqa: F401
     batched_blocks,
     curvefit_problem,
     ellipse_system,
+    ba_project,
+    ba_system,
     banded_problem,
     banded_batch_shapes,
     mlp_init,

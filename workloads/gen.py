@@ -142,6 +142,111 @@ def ellipse_system(N=500_000, sigma=0.01, start_sigma_t=0.05, start_sigma_p=0.02
     return dict(blocks=blocks, S=S, b=b, lam=lam, K=N, n=2, m=1, s=5, t0=t0, x0=x0, y=y)
 
 
+def _rodrigues(w):
+    """Rotation matrices of angle-axis vectors w (..., 3)."""
+    th = np.linalg.norm(w, axis=-1)[..., None, None]
+    k = w / np.maximum(np.linalg.norm(w, axis=-1, keepdims=True), 1e-300)
+    K = np.zeros(w.shape[:-1] + (3, 3))
+    K[..., 0, 1], K[..., 0, 2] = -k[..., 2], k[..., 1]
+    K[..., 1, 0], K[..., 1, 2] = k[..., 2], -k[..., 0]
+    K[..., 2, 0], K[..., 2, 1] = -k[..., 1], k[..., 0]
+    I = np.broadcast_to(np.eye(3), K.shape)
+    return I + np.sin(th) * K + (1.0 - np.cos(th)) * (K @ K)
+
+
+def ba_project(cam, X):
+    """Projection of points X (..., 3) by cameras cam (..., 9) = [angle-axis (3), translation
+    (3), focal length, radial k1, k2]: X_c = R X + t, p = -X_c[:2] / X_c[2],
+    u = f (1 + k1 |p|^2 + k2 |p|^4) p (the camera model of the public bundle-adjustment
+    problem sets)."""
+    R = _rodrigues(cam[..., :3])
+    Xc = np.einsum("...ij,...j->...i", R, X) + cam[..., 3:6]
+    pxy = -Xc[..., :2] / Xc[..., 2:3]
+    r2 = np.sum(pxy * pxy, axis=-1, keepdims=True)
+    return cam[..., 6:7] * (1.0 + cam[..., 7:8] * r2 + cam[..., 8:9] * r2 * r2) * pxy
+
+
+def ba_system(P=2000, C=7, obs_lo=2, obs_hi=6, s_pad=None, sigma=0.5, lam=1e-3, seed_offset=0,
+              dtype=np.float64, workload=7):
+    """The linear system of one LM step of a bundle adjustment (the BA experiments of Sec. 6.2:
+    3 unknowns per point, 9 per camera; an observation gives two rows that touch its point and
+    one camera): J = [blkdiag(point blocks) | camera part] (Sec. 4.2), the camera part block-
+    sparse and stored dense with s = 9 C shared columns (zero-padded to s_pad when given).
+
+    Scene: points uniform in the unit ball; C cameras on a circle of radius 4 around the y
+    axis, looking at the origin; f ~ U[500, 800), k1 ~ N(0, 0.05^2), k2 ~ N(0, 0.01^2).  Each
+    point is observed by k ~ U{obs_lo..obs_hi} distinct cameras (its rows in camera order);
+    observations = projections + N(0, sigma^2) pixels.  The system is taken at a start with
+    points + N(0, 0.01^2), angle-axis + N(0, 0.001^2), translations + N(0, 0.01^2),
+    f (1 + N(0, 0.005^2)), k1, k2 + N(0, 0.001^2): rows r = projection - observation, J by
+    central differences of ba_project (steps 1e-6 relative), right-hand side -r.  The camera
+    model is evaluated here to lay out the input; neither side of the solve evaluates it.
+    Returns dict(blocks (list of (2 k_i, 3)), n (K), m = 3, S (rows, s), b, lam, K = P, s,
+    cam (rows / 2: camera of each observation), point (rows / 2), X0, cams0, obs).
+    """
+    if not (1 <= obs_lo <= obs_hi <= C):
+        raise ValueError("need 1 <= obs_lo <= obs_hi <= C")
+    g = rng_for(workload, seed_offset)
+    X = g.standard_normal((P, 3))
+    X *= (g.random(P) ** (1.0 / 3.0) / np.linalg.norm(X, axis=1))[:, None]
+    th = 2.0 * np.pi * (np.arange(C) + 0.5 * g.random(C)) / C
+    centers = 4.0 * np.stack([np.sin(th), 0.2 * g.standard_normal(C), np.cos(th)], axis=1)
+    cams = np.zeros((C, 9))
+    for c in range(C):
+        z = centers[c] / np.linalg.norm(centers[c])      # camera z axis in world (looks along -z)
+        x = np.cross([0.0, 1.0, 0.0], z)
+        x /= np.linalg.norm(x)
+        y = np.cross(z, x)
+        R = np.stack([x, y, z])
+        ang = np.arccos(np.clip((np.trace(R) - 1.0) / 2.0, -1.0, 1.0))
+        axis = np.array([R[2, 1] - R[1, 2], R[0, 2] - R[2, 0], R[1, 0] - R[0, 1]])
+        nrm = np.linalg.norm(axis)
+        cams[c, :3] = ang * axis / nrm if nrm > 1e-12 else 0.0
+        cams[c, 3:6] = -R @ centers[c]
+    cams[:, 6] = 500.0 + 300.0 * g.random(C)
+    cams[:, 7] = 0.05 * g.standard_normal(C)
+    cams[:, 8] = 0.01 * g.standard_normal(C)
+    k = g.integers(obs_lo, obs_hi + 1, size=P)
+    cam_of = np.concatenate([np.sort(g.choice(C, size=int(ki), replace=False)) for ki in k])
+    pt_of = np.repeat(np.arange(P), k)
+    obs = ba_project(cams[cam_of], X[pt_of]) + sigma * g.standard_normal((pt_of.size, 2))
+    X0 = X + 0.01 * g.standard_normal(X.shape)
+    cams0 = cams.copy()
+    cams0[:, :3] += 0.001 * g.standard_normal((C, 3))
+    cams0[:, 3:6] += 0.01 * g.standard_normal((C, 3))
+    cams0[:, 6] *= 1.0 + 0.005 * g.standard_normal(C)
+    cams0[:, 7:9] += 0.001 * g.standard_normal((C, 2))
+    r = ba_project(cams0[cam_of], X0[pt_of]) - obs                 # (nobs, 2)
+    nobs = pt_of.size
+    Jp = np.zeros((nobs, 2, 3))
+    Jc = np.zeros((nobs, 2, 9))
+    for j in range(3):
+        h = 1e-6 * max(1.0, float(np.max(np.abs(X0[:, j]))))
+        d = np.zeros(3)
+        d[j] = h
+        Jp[:, :, j] = (ba_project(cams0[cam_of], X0[pt_of] + d) - ba_project(cams0[cam_of], X0[pt_of] - d)) / (2 * h)
+    for j in range(9):
+        h = 1e-6 * max(1.0, float(np.max(np.abs(cams0[:, j]))))
+        d = np.zeros(9)
+        d[j] = h
+        Jc[:, :, j] = (ba_project(cams0[cam_of] + d, X0[pt_of]) - ba_project(cams0[cam_of] - d, X0[pt_of])) / (2 * h)
+    s = 9 * C if s_pad is None else int(s_pad)
+    if s < 9 * C:
+        raise ValueError("s_pad below 9 C")
+    rows = 2 * nobs
+    S = np.zeros((nobs, 2, s))
+    cols = 9 * cam_of[:, None] + np.arange(9)[None, :]
+    S[np.arange(nobs)[:, None, None], np.arange(2)[None, :, None], cols[:, None, :]] = Jc
+    S = S.reshape(rows, s)
+    starts = np.concatenate([[0], np.cumsum(k)])
+    blocks = [Jp[starts[i]:starts[i + 1]].reshape(-1, 3) for i in range(P)]
+    b = -r.reshape(rows)
+    if dtype == np.float32:
+        blocks, S, b = [_f32(x) for x in blocks], _f32(S), _f32(b)
+    return dict(blocks=blocks, n=(2 * k).astype(np.int64), m=3, S=S, b=b, lam=lam, K=P, s=s,
+                cam=cam_of, point=pt_of, X0=X0, cams0=cams0, obs=obs)
+
+
 def banded_problem(n=1_000_000, rows_per_col=4, w=8, seed_offset=0, dtype=np.float32,
                    workload=4):
     """Banded J: row i starts at column floor(i / rows_per_col), w values, N(0,1).
