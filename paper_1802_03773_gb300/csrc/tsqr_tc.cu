@@ -65,6 +65,44 @@ __device__ __forceinline__ float warp_sum(float v) {
   return v;
 }
 
+// Sum over the warp of 32 values per lane, transposed: lane l ends with the sum over all lanes
+// of v[l] (31 shuffles: at each halving a lane keeps the half of the pairs its bit selects).
+__device__ __forceinline__ float transpose_reduce(float (&v)[32], int lane) {
+#pragma unroll
+  for (int d = 16; d >= 1; d >>= 1) {
+    const bool upper = (lane & d) != 0;
+#pragma unroll
+    for (int k = 0; k < d; ++k) {
+      const float send = upper ? v[k] : v[k + d];
+      const float keep = upper ? v[k + d] : v[k];
+      v[k] = keep + __shfl_xor_sync(0xffffffffu, send, d);
+    }
+  }
+  return v[0];
+}
+
+// Row i of the panel's Y (Y[i][l] = 1 at i = p0 + l, the stored v below, 0 above and for
+// l >= nk) against a column x of the tile: acc[l] += Y[i][l] x[i] for the lane's rows
+// i = p0 + lane, p0 + lane + 32, ... (the first pass holds the triangle, the others are full).
+__device__ __forceinline__ void accumulate_yt(const float* A, int p0, int nk, const float* x, float (&acc)[32],
+                                              int lane) {
+  {
+    const int i = p0 + lane;
+    const float xv = i < kRows ? x[i] : 0.f;
+#pragma unroll
+    for (int l = 0; l < kNb; ++l) {
+      const int d = p0 + l;
+      const float y = (l < nk && i < kRows) ? (i > d ? A[d * kRows + i] : (i == d ? 1.f : 0.f)) : 0.f;
+      acc[l] += y * xv;
+    }
+  }
+  for (int i = p0 + 32 + lane; i < kRows; i += 32) {
+    const float xv = x[i];
+#pragma unroll
+    for (int l = 0; l < kNb; ++l) acc[l] += (l < nk ? A[(p0 + l) * kRows + i] : 0.f) * xv;
+  }
+}
+
 __device__ __forceinline__ void tc_record(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
@@ -164,19 +202,34 @@ tsqr_tile_tc_kernel(float* X, int64_t ld, int64_t M, int s, float* taus, float* 
       const int d = p0 + l;
       return i < d ? 0.f : (i == d ? 1.f : A[d * kRows + i]);
     };
-    // 2. T: G = Y^T Y (l < k) into W's space first (one warp per entry, lanes over rows,
-    // conflict-free column reads), then the forward recurrence
-    for (int e = warp; e < kNb * kNb; e += kThr / 32) {
-      const int l = e / kNb, k = e % kNb;
-      float g = 0.f;
-      if (l < k && k < nk) {
-        const float* yl = A + (p0 + l) * kRows;
+    // 2. T: G = Y^T Y (G[l][k], l < k) into W's space first (one warp per column k of Y, lanes
+    // over rows, the 32 sums of a column reduced together), then the forward recurrence
+    for (int k = warp; k < kNb; k += kThr / 32) {
+      float acc[32];
+#pragma unroll
+      for (int l = 0; l < 32; ++l) acc[l] = 0.f;
+      if (k < nk) {
+        // column k of Y as a vector: y_k[i] = 1 at p0 + k, A below, 0 above
         const float* yk = A + (p0 + k) * kRows;
-        for (int i = p0 + k + 1 + lane; i < kRows; i += 32) g += yl[i] * yk[i];
-        g = warp_sum(g);
-        g += yl[p0 + k];   // row p0 + k: y_k = 1 there
+        const int d = p0 + k;
+        {
+          const int i = p0 + lane;
+          const float xv = i < kRows ? (i > d ? yk[i] : (i == d ? 1.f : 0.f)) : 0.f;
+#pragma unroll
+          for (int l = 0; l < kNb; ++l) {
+            const int dl = p0 + l;
+            const float y = (l < nk && i < kRows) ? (i > dl ? A[dl * kRows + i] : (i == dl ? 1.f : 0.f)) : 0.f;
+            acc[l] += y * xv;
+          }
+        }
+        for (int i = p0 + 32 + lane; i < kRows; i += 32) {
+          const float xv = yk[i];
+#pragma unroll
+          for (int l = 0; l < kNb; ++l) acc[l] += (l < nk ? A[(p0 + l) * kRows + i] : 0.f) * xv;
+        }
       }
-      if (lane == 0) W[e] = g;
+      const float g = transpose_reduce(acc, lane);
+      W[lane * kNb + k] = (lane < k && k < nk) ? g : 0.f;
     }
     __syncthreads();
     if (warp == 0) {
@@ -196,18 +249,15 @@ tsqr_tile_tc_kernel(float* X, int64_t ld, int64_t M, int s, float* taus, float* 
       }
     }
     __syncthreads();
-    // 3. W = Y^T C (32 x n, row-major; one warp per entry, lanes over rows), then Z = T^T W
-    for (int e = warp; e < kNb * n; e += kThr / 32) {
-      const int l = e / n, j = e % n;
-      const float* c = A + (pend + j) * kRows;
-      float w = 0.f;
-      if (l < nk) {
-        const int d = p0 + l;
-        const float* y = A + d * kRows;
-        for (int i = d + 1 + lane; i < kRows; i += 32) w += y[i] * c[i];
-        w = warp_sum(w) + c[d];
-      }
-      if (lane == 0) W[e] = w;
+    // 3. W = Y^T C (32 x n, row-major; one warp per trailing column, lanes over rows, the 32
+    // sums of a column reduced together), then Z = T^T W
+    for (int j = warp; j < n; j += kThr / 32) {
+      float acc[32];
+#pragma unroll
+      for (int l = 0; l < 32; ++l) acc[l] = 0.f;
+      accumulate_yt(A, p0, nk, A + (pend + j) * kRows, acc, lane);
+      const float w = transpose_reduce(acc, lane);
+      W[lane * n + j] = lane < nk ? w : 0.f;
     }
     __syncthreads();
     for (int j = tid; j < n; j += kThr)
