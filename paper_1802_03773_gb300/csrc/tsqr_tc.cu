@@ -117,7 +117,7 @@ tsqr_tile_tc_kernel(float* X, int64_t ld, int64_t M, int s, float* taus, float* 
   unsigned char* Zlo = Zhi + (kMaxS - kNb) * kNb * 4;                  // also W / Z in float
   float* Tm = reinterpret_cast<float*>(Zlo + (kMaxS - kNb) * kNb * 4);  // 32 x 32 (row l, col k)
   float* W = reinterpret_cast<float*>(Zlo);                            // 32 x n, row-major
-  __shared__ float sh[4];
+  __shared__ float sh2[2][2];   // reflector slots: tau, beta
   __shared__ float tau_s[kNb];
   __shared__ uint32_t tmem_slot;
   __shared__ __align__(8) uint64_t mbar;
@@ -151,48 +151,94 @@ tsqr_tile_tc_kernel(float* X, int64_t ld, int64_t M, int s, float* taus, float* 
   for (int p0 = 0; p0 < kmax; p0 += kNb) {
     const int kend = p0 + kNb < kmax ? p0 + kNb : kmax;
     const int pend = p0 + kNb < s ? p0 + kNb : s;   // panel columns
-    // 1. panel factorization
-    for (int k = p0; k < kend; ++k) {
+    // 1. panel factorization.  The reflector of column k is formed by warp 0 (norm of the
+    // column below k, tau, beta, the column scaled to v with v_k = 1) before the barrier that
+    // opens step k; the trailing panel columns are then updated up to four per warp at once
+    // (one pass over the rows for their dot products), and warp 0, which holds column k + 1,
+    // forms the next reflector right after updating it (the reflectors alternate between two
+    // slots, so a warp still reading the current one is never overtaken).
+    auto reflector = [&](int k, int slot) {   // warp 0 only
       float* x = A + k * kRows;
-      if (warp == 0) {
-        float sq = 0.f;
-        for (int i = k + 1 + lane; i < r; i += 32) sq += x[i] * x[i];
-        for (int d = 16; d >= 1; d >>= 1) sq += __shfl_xor_sync(0xffffffffu, sq, d);
-        if (lane == 0) {
-          const float alpha = x[k];
-          const float norm = sqrtf(alpha * alpha + sq);
-          float beta = 0.f, t = 0.f, scale = 0.f;
-          if (norm != 0.f) {
-            beta = alpha >= 0.f ? -norm : norm;
-            t = (beta - alpha) / beta;
-            scale = 1.f / (alpha - beta);
-          }
-          sh[0] = t;
-          sh[1] = beta;
-          sh[2] = scale;
-        }
-        __syncwarp();
-        const float scale = sh[2];
-        for (int i = k + 1 + lane; i < r; i += 32) x[i] *= scale;
+      float sq = 0.f;
+#pragma unroll
+      for (int u = 0; u < kRows / 32; ++u) {   // rows k + 1 + lane + 32 u below r: loads in flight together
+        const int i = k + 1 + lane + 32 * u;
+        if (i < r) sq += x[i] * x[i];
       }
-      __syncthreads();
-      const float t = sh[0];
-      for (int j = k + 1 + warp; j < pend; j += kThr / 32) {
-        float* y = A + j * kRows;
-        float w = 0.f;
-        for (int i = k + 1 + lane; i < r; i += 32) w += x[i] * y[i];
-        for (int d = 16; d >= 1; d >>= 1) w += __shfl_xor_sync(0xffffffffu, w, d);
-        w = (w + y[k]) * t;
-        if (lane == 0) y[k] -= w;
-        for (int i = k + 1 + lane; i < r; i += 32) y[i] -= w * x[i];
+      sq = warp_sum(sq);
+      const float alpha = x[k];
+      const float norm = sqrtf(alpha * alpha + sq);
+      float beta = 0.f, t = 0.f, scale = 0.f;
+      if (norm != 0.f) {
+        beta = alpha >= 0.f ? -norm : norm;
+        t = (beta - alpha) / beta;
+        scale = 1.f / (alpha - beta);
+      }
+#pragma unroll
+      for (int u = 0; u < kRows / 32; ++u) {
+        const int i = k + 1 + lane + 32 * u;
+        if (i < r) x[i] *= scale;
+      }
+      if (lane == 0) {
+        sh2[slot][0] = t;
+        sh2[slot][1] = beta;
+      }
+    };
+    if (warp == 0 && p0 < kend) reflector(p0, p0 & 1);
+    for (int k = p0; k < kend; ++k) {
+      __syncthreads();   // reflector k formed and its column scaled; column k + 1 updated
+      const float* x = A + k * kRows;
+      const float t = sh2[k & 1][0];
+      // warp w takes columns k + 1 + w + 8 q (warp 0 first column k + 1)
+      constexpr int kQ = 4;
+      float* yq[kQ];
+      float w[kQ] = {0.f, 0.f, 0.f, 0.f};
+      const int jstep = kThr / 32;
+#pragma unroll
+      for (int q = 0; q < kQ; ++q) {
+        const int j = k + 1 + warp + q * jstep;
+        yq[q] = A + (j < pend ? j : k) * kRows;   // past the panel: a harmless stand-in, unused
+      }
+      const int left = pend - (k + 1 + warp);
+      const int cnt = left > 0 ? (left + jstep - 1) / jstep : 0;
+      if (cnt > 0) {
+        float xr[kRows / 32];   // the reflector's rows of this lane, kept for the update
+#pragma unroll
+        for (int u = 0; u < kRows / 32; ++u) {
+          const int i = k + 1 + lane + 32 * u;
+          xr[u] = i < r ? x[i] : 0.f;
+#pragma unroll
+          for (int q = 0; q < kQ; ++q)
+            if (q < cnt && i < r) w[q] += xr[u] * yq[q][i];
+        }
+#pragma unroll
+        for (int q = 0; q < kQ; ++q)
+          if (q < cnt) w[q] = (warp_sum(w[q]) + yq[q][k]) * t;
+        __syncwarp();   // every lane has read row k of its columns
+        if (lane == 0) {
+#pragma unroll
+          for (int q = 0; q < kQ; ++q)
+            if (q < cnt) yq[q][k] -= w[q];
+        }
+#pragma unroll
+        for (int u = 0; u < kRows / 32; ++u) {
+          const int i = k + 1 + lane + 32 * u;
+#pragma unroll
+          for (int q = 0; q < kQ; ++q)
+            if (q < cnt && i < r) yq[q][i] -= w[q] * xr[u];
+        }
+      }
+      if (warp == 0 && k + 1 < kend) {
+        __syncwarp();   // column k + 1 (this warp's first) is fully updated
+        reflector(k + 1, (k + 1) & 1);
       }
       if (tid == 0) {
-        x[k] = sh[1];
+        A[k * kRows + k] = sh2[k & 1][1];
         taus[(int64_t)blockIdx.x * s + k] = t;
         tau_s[k - p0] = t;
       }
-      __syncthreads();
     }
+    __syncthreads();
     const int n = s - pend;   // trailing columns
     if (n <= 0) break;
     const int nk = kend - p0;
