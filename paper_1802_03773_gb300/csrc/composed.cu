@@ -13,6 +13,7 @@
 #include <string>
 #include <vector>
 
+#include "device_util.cuh"
 #include "internal.h"
 
 namespace qrkit {
@@ -656,10 +657,103 @@ __device__ __forceinline__ void resid_g_block(ComposedView<T> V, const T* b, con
   }
 }
 
+// Compensated float accumulation (Dot2, Ogita-Rump-Oishi): (sh + sl) += a x with the product's
+// rounding error from an FMA and the sum's from TwoSum (Knuth).
+__device__ __forceinline__ void dot2_acc(float& sh, float& sl, float a, float x) {
+  const float p = __fmul_rn(a, x);
+  const float pe = __fmaf_rn(a, x, -p);
+  float t, e;
+  dev::two_sum(sh, p, t, e);
+  sh = t;
+  sl = __fadd_rn(sl, __fadd_rn(e, pe));
+}
+
+// resid_g_small for float data: the residual b - J p - S p_S and the sums J^T r, S^T r in
+// compensated float arithmetic (as if in twice the working precision) instead of FP64, whose
+// rate on this part is a small fraction of FP32's; each sum is rounded to double once, for g
+// and the column accumulation.
+template <int NR, int MM>
+__device__ __forceinline__ void resid_g_small_f32(const ComposedView<float>& V, const float* b, const float* p,
+                                                  const double* D, double lam, double* g, double* gS, int64_t goff,
+                                                  int64_t i) {
+  const int n = V.n[i], m = V.m[i];
+  const int64_t c0 = V.col_off[i], r0 = V.row_off[i];
+  const float* J = V.J + V.val_off[i];
+  const int64_t st = V.coupled == QRKIT_COUPLED_WINDOW ? V.start[i] : 0;
+  float pj[MM], rh[NR], rl[NR];
+#pragma unroll
+  for (int j = 0; j < MM; ++j) pj[j] = j < m ? p[c0 + j] : 0.f;
+#pragma unroll
+  for (int r = 0; r < NR; ++r) {
+    float sh = 0.f, sl = 0.f;
+    if (r < n) {
+      sh = b[r0 + r];
+#pragma unroll
+      for (int j = 0; j < MM; ++j)
+        if (j < m) dot2_acc(sh, sl, -J[j * n + r], pj[j]);
+      if (V.coupled == QRKIT_COUPLED_DENSE) {
+        for (int c = 0; c < V.s; ++c) dot2_acc(sh, sl, -V.S[(int64_t)c * V.rows + r0 + r], p[V.nb + c]);
+      } else if (V.coupled == QRKIT_COUPLED_WINDOW) {
+        for (int t = 0; t < V.w; ++t)
+          if (st + t < V.s) dot2_acc(sh, sl, -V.S[r0 * V.w + (int64_t)t * n + r], p[V.nb + st + t]);
+      }
+    }
+    rh[r] = sh;
+    rl[r] = sl;
+  }
+  // a sum of a x over the rows with x = rh + rl: the rh part compensated, the rl part plain
+#pragma unroll
+  for (int j = 0; j < MM; ++j) {
+    if (j < m) {
+      float ah = 0.f, al = 0.f;
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        if (r < n) {
+          const float a = J[j * n + r];
+          dot2_acc(ah, al, a, rh[r]);
+          al = __fmaf_rn(a, rl[r], al);
+        }
+      const double d = D[c0 + j];
+      g[c0 + j] = ((double)ah + (double)al) - lam * d * d * (double)pj[j];
+    }
+  }
+  if (V.coupled == QRKIT_COUPLED_DENSE) {
+    for (int c = 0; c < V.s; ++c) {
+      float ah = 0.f, al = 0.f;
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        if (r < n) {
+          const float a = V.S[(int64_t)c * V.rows + r0 + r];
+          dot2_acc(ah, al, a, rh[r]);
+          al = __fmaf_rn(a, rl[r], al);
+        }
+      const double acc = (double)ah + (double)al;
+      if (acc != 0.0) atomicAdd(&gS[c], acc);
+    }
+  } else if (V.coupled == QRKIT_COUPLED_WINDOW) {
+    for (int t = 0; t < V.w; ++t) {
+      float ah = 0.f, al = 0.f;
+#pragma unroll
+      for (int r = 0; r < NR; ++r)
+        if (r < n) {
+          const float a = V.S[r0 * V.w + (int64_t)t * n + r];
+          dot2_acc(ah, al, a, rh[r]);
+          al = __fmaf_rn(a, rl[r], al);
+        }
+      const double acc = (double)ah + (double)al;
+      if (acc != 0.0 && st + t < V.s) atomicAdd(&gS[st + t - goff], acc);
+    }
+  }
+}
+
 // resid_g_block for blocks of at most NR rows and MM columns, every array in registers.
 template <typename T, int NR, int MM>
 __device__ __forceinline__ void resid_g_small(const ComposedView<T>& V, const T* b, const T* p, const double* D,
                                               double lam, double* g, double* gS, int64_t goff, int64_t i) {
+  if constexpr (sizeof(T) == sizeof(float)) {
+    resid_g_small_f32<NR, MM>(V, b, p, D, lam, g, gS, goff, i);
+    return;
+  }
   const int n = V.n[i], m = V.m[i];
   const int64_t c0 = V.col_off[i], r0 = V.row_off[i];
   const T* J = V.J + V.val_off[i];
