@@ -94,6 +94,16 @@ __device__ __forceinline__ void bspline(double u, double B[4], double dB[4]) {
   dB[3] = 0.5 * u2;
 }
 
+// The basis alone (the trial cost needs no derivative).
+__device__ __forceinline__ void bspline_values(double u, double B[4]) {
+  const double sixth = 1.0 / 6.0;
+  const double v = 1.0 - u, u2 = u * u;
+  B[0] = v * v * v * sixth;
+  B[1] = fma(fma(3.0, u, -6.0), u2, 4.0) * sixth;
+  B[2] = fma(fma(fma(-3.0, u, 3.0), u, 3.0), u, 1.0) * sixth;
+  B[3] = u2 * u * sixth;
+}
+
 __device__ __forceinline__ int64_t segment_of(double t, int64_t Kc) {
   const double hi = (double)(Kc - 4);
   double f = floor(t);
@@ -242,8 +252,8 @@ cf_trial_kernel(LMTables t, const double* xnew, const double* data, const T* J, 
     const int64_t Kc = (t.c0[k + 1] - t.c0[k]) / 2;
     const double ti = xnew[i];
     const int64_t seg = segment_of(ti, Kc);
-    double Bv[4], dB[4];
-    bspline(ti - (double)seg, Bv, dB);
+    double Bv[4];
+    bspline_values(ti - (double)seg, Bv);
     const double* P = xnew + t.NP + t.c0[k] + 2 * seg;
     double cx = 0, cy = 0;
 #pragma unroll
@@ -253,17 +263,20 @@ cf_trial_kernel(LMTables t, const double* xnew, const double* data, const T* J, 
     }
     const double fx = cx - data[2 * i], fy = cy - data[2 * i + 1];
     fsq = fx * fx + fy * fy;
-    // (J p) at the linearisation point, with the system's own J, S and b
-    const double pt = (double)p[i];
-    double jx = (double)J[2 * i] * pt, jy = (double)J[2 * i + 1] * pt;
+    // (J p) at the linearisation point, with the system's own J, S and b; in the context
+    // precision (a relative error of the order of its rounding in the predicted decrease moves
+    // the gain ratio by as little, far below what the damping rule resolves)
+    const T pt = p[i];
+    T jx = J[2 * i] * pt, jy = J[2 * i + 1] * pt;
     const T* Si = S + 16 * i;
     const T* pS = p + t.NP + start[i];
 #pragma unroll
     for (int c = 0; c < 8; ++c) {
-      jx += (double)Si[2 * c] * (double)pS[c];
-      jy += (double)Si[2 * c + 1] * (double)pS[c];
+      jx += Si[2 * c] * pS[c];
+      jy += Si[2 * c + 1] * pS[c];
     }
-    pr = jx * (double)b[2 * i] + jy * (double)b[2 * i + 1] + E[i] * E[i] * pt * pt;
+    const T e = (T)E[i];
+    pr = (double)(jx * b[2 * i] + jy * b[2 * i + 1] + e * e * pt * pt);
   }
   const double s1 = block_sum(fsq, red);
   __syncthreads();
