@@ -153,7 +153,19 @@ __global__ void rsort_scatter_kernel(RowSortTables t, const int64_t* Xstart, con
       spos[row0 + r] = pos;
       order[pos] = row0 + r;
       Xstart_s[pos] = col0 + k;   // clamped: every start lies in its segment
-      for (int q = 0; q < w; ++q) Xw_s[pos * w + q] = Xw[(row0 + r) * w + q];
+      bool moved = false;
+      if constexpr (sizeof(T) == 4) {
+        if (w == 8) {   // a row of 8 floats: two 16-byte moves (rows are 32-byte aligned)
+          const float4* src = reinterpret_cast<const float4*>(Xw + (row0 + r) * 8);
+          float4* dst = reinterpret_cast<float4*>(Xw_s + pos * 8);
+          const float4 v0 = src[0], v1 = src[1];
+          dst[0] = v0;
+          dst[1] = v1;
+          moved = true;
+        }
+      }
+      if (!moved)
+        for (int q = 0; q < w; ++q) Xw_s[pos * w + q] = Xw[(row0 + r) * w + q];
     }
     __syncwarp();
   }
