@@ -187,6 +187,45 @@ __device__ __forceinline__ void block_factor_small(const ComposedView<T>& V, con
     if (k < m) O.tau[V.col_off[i] + k] = tau[k];
   if (V.coupled == QRKIT_COUPLED_NONE) return;
   const int64_t red0 = O.red_off[i];
+  if constexpr (sizeof(T) == 4 && NA == 3 && MM == 1) {
+    // the 2 x 1 point blocks of curve fits with windows of 8 (damped): the window, R12 and
+    // the two reduced rows are moved by 16-byte loads and stores (all 32-byte aligned)
+    if (V.coupled == QRKIT_COUPLED_WINDOW && V.w == 8 && n == 2 && m == 1 && na == 3 &&
+        (reinterpret_cast<uintptr_t>(V.S) & 15) == 0) {   // the caller's S 16-byte aligned
+      const float4* src = reinterpret_cast<const float4*>(V.S + V.row_off[i] * 8);   // 2 x 8 column-major
+      float sv[16];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 v = src[q];
+        sv[4 * q] = v.x;
+        sv[4 * q + 1] = v.y;
+        sv[4 * q + 2] = v.z;
+        sv[4 * q + 3] = v.w;
+      }
+      float r12[8], x1[8], x2[8];
+#pragma unroll
+      for (int c = 0; c < 8; ++c) {
+        // column c of the augmented window: rows (S[0][c], S[1][c], 0); reflector k = 0
+        const float y0 = sv[2 * c], y1 = sv[2 * c + 1];
+        float w = y0 + B[0][1] * y1;   // row 2 of the column is 0
+        w *= tau[0];
+        r12[c] = y0 - w;
+        x1[c] = y1 - w * B[0][1];
+        x2[c] = -w * B[0][2];
+      }
+      float4* dr = reinterpret_cast<float4*>(O.R12 + V.col_off[i] * 8);
+      dr[0] = make_float4(r12[0], r12[1], r12[2], r12[3]);
+      dr[1] = make_float4(r12[4], r12[5], r12[6], r12[7]);
+      float4* dx = reinterpret_cast<float4*>(O.Xw + red0 * 8);
+      dx[0] = make_float4(x1[0], x1[1], x1[2], x1[3]);
+      dx[1] = make_float4(x1[4], x1[5], x1[6], x1[7]);
+      dx[2] = make_float4(x2[0], x2[1], x2[2], x2[3]);
+      dx[3] = make_float4(x2[4], x2[5], x2[6], x2[7]);
+      O.Xstart[red0] = V.start[i];
+      O.Xstart[red0 + 1] = V.start[i];
+      return;
+    }
+  }
   for (int c0 = 0; c0 < V.w; c0 += kChunk) {
     const int cw = min(kChunk, V.w - c0);
     T C[kChunk][NA];
