@@ -719,6 +719,59 @@ __device__ __forceinline__ void resid_g_small_f32(const ComposedView<float>& V, 
   const int64_t c0 = V.col_off[i], r0 = V.row_off[i];
   const float* J = V.J + V.val_off[i];
   const int64_t st = V.coupled == QRKIT_COUPLED_WINDOW ? V.start[i] : 0;
+  if constexpr (MM == 1 && NR >= 2) {
+    // the 2 x 1 point blocks of curve fits with windows of 8: the window (2 x 8 column-major,
+    // 32-byte aligned in a 16-byte aligned S) by four 16-byte loads
+    if (V.coupled == QRKIT_COUPLED_WINDOW && V.w == 8 && n == 2 && m == 1 &&
+        (reinterpret_cast<uintptr_t>(V.S) & 15) == 0) {
+      const float4* s4 = reinterpret_cast<const float4*>(V.S + r0 * 8);
+      float sv[16];
+#pragma unroll
+      for (int q = 0; q < 4; ++q) {
+        const float4 v = s4[q];
+        sv[4 * q] = v.x;
+        sv[4 * q + 1] = v.y;
+        sv[4 * q + 2] = v.z;
+        sv[4 * q + 3] = v.w;
+      }
+      const float p0 = p[c0];
+      float ps[8];
+#pragma unroll
+      for (int t = 0; t < 8; ++t) ps[t] = st + t < V.s ? p[V.nb + st + t] : 0.f;
+      float rh2[2], rl2[2];
+#pragma unroll
+      for (int r = 0; r < 2; ++r) {
+        float sh = b[r0 + r], sl = 0.f;
+        dot2_acc(sh, sl, -J[r], p0);
+#pragma unroll
+        for (int t = 0; t < 8; ++t) dot2_acc(sh, sl, -sv[2 * t + r], ps[t]);
+        rh2[r] = sh;
+        rl2[r] = sl;
+      }
+      {
+        float ah = 0.f, al = 0.f;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          dot2_acc(ah, al, J[r], rh2[r]);
+          al = __fmaf_rn(J[r], rl2[r], al);
+        }
+        const double d = D[c0];
+        g[c0] = ((double)ah + (double)al) - lam * d * d * (double)p0;
+      }
+#pragma unroll
+      for (int t = 0; t < 8; ++t) {
+        float ah = 0.f, al = 0.f;
+#pragma unroll
+        for (int r = 0; r < 2; ++r) {
+          dot2_acc(ah, al, sv[2 * t + r], rh2[r]);
+          al = __fmaf_rn(sv[2 * t + r], rl2[r], al);
+        }
+        const double acc = (double)ah + (double)al;
+        if (acc != 0.0 && st + t < V.s) atomicAdd(&gS[st + t - goff], acc);
+      }
+      return;
+    }
+  }
   float pj[MM], rh[NR], rl[NR];
 #pragma unroll
   for (int j = 0; j < MM; ++j) pj[j] = j < m ? p[c0 + j] : 0.f;
@@ -974,6 +1027,21 @@ __device__ __forceinline__ void fwdsub_rt_small(const ComposedView<T>& V, const 
   }
   if (V.coupled != QRKIT_COUPLED_NONE) {
     const int64_t st = V.coupled == QRKIT_COUPLED_WINDOW ? V.start[i] : 0;
+    if constexpr (sizeof(T) == 4 && MM == 1) {
+      if (V.coupled == QRKIT_COUPLED_WINDOW && V.w == 8 && m == 1) {
+        // one column: R12 row by two 16-byte loads (32-byte aligned), the products in float
+        // (h is itself a float correction), each rounded to double once for the sum
+        const float4* r4 = reinterpret_cast<const float4*>(O.R12 + c0 * 8);
+        const float4 a = r4[0], bq = r4[1];
+        const float rv[8] = {a.x, a.y, a.z, a.w, bq.x, bq.y, bq.z, bq.w};
+#pragma unroll
+        for (int t = 0; t < 8; ++t) {
+          const float prod = rv[t] * hv[0];
+          if (prod != 0.f && st + t < V.s) atomicAdd(&gS[st + t - goff], -(double)prod);
+        }
+        return;
+      }
+    }
     for (int t = 0; t < V.w; ++t) {
       if (st + t >= V.s) continue;
       double acc = 0;
