@@ -26,7 +26,7 @@ namespace {
 
 constexpr int kRows = 256;      // tile rows (two MMA halves of 128)
 constexpr int kNb = 32;         // panel width = MMA K
-constexpr int kThr = 256;
+constexpr int kThr = 512;     // 16 warps: more of them to hide the panel's latency
 constexpr int kMaxS = 128;
 constexpr int kTmemCols = 256;  // D of half h at columns [128 h, 128 h + n)
 constexpr uint32_t kWaitLimit = 1u << 26;
@@ -375,14 +375,15 @@ tsqr_tile_tc_kernel(float* X, int64_t ld, int64_t M, int s, float* taus, float* 
     asm volatile("tcgen05.fence::after_thread_sync;");
     __syncthreads();
     if (abort_s) break;
-    // C -= D: warp w reads TMEM lanes 32 (w % 4) .. of half w / 4
+    // C -= D: warp w reads TMEM lanes 32 (w % 4) .. of half (w / 4) % 2, columns 8-wide groups
+    // (w / 8), (w / 8) + 2, ... (the lane quarter a warp may read is fixed by w % 4)
     {
-      const int h = warp >> 2;
+      const int qd = warp & 3, h = (warp >> 2) & 1, part = warp >> 3;
       if (h >= h0) {
-        const int row = h * 128 + (warp & 3) * 32 + lane;
-        for (int c0 = 0; c0 < n; c0 += 8) {
+        const int row = h * 128 + qd * 32 + lane;
+        for (int c0 = part * 8; c0 < n; c0 += 8 * (kThr / 256)) {
           uint32_t v[8];
-          const uint32_t ta = tmem + ((uint32_t)((warp & 3) * 32) << 16) + (uint32_t)(h * 128 + c0);
+          const uint32_t ta = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(h * 128 + c0);
           asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
                        : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
                          "=r"(v[7])
