@@ -17,7 +17,11 @@ Pins (tests/test_oracle_more.py): the damped least-squares solution of numpy.lin
 [J; lambda^(1/2) D], R'^T R' = J^T J + lambda D^2, lambda = 0 gives the plain least-squares
 solution, the one-column closed form a^T b / (a^T a + lambda d^2), the minimum value of the
 damped objective from the two residual norms, the block version against the composed solve of
-Sec. 4.1, and a planted mistake (lambda instead of lambda^(1/2)) that fails them.
+Sec. 4.1, and a planted mistake (lambda instead of lambda^(1/2)) that fails them.  The
+trust-region lambda: its step's scaled length within sigma Delta of Delta, the lambda inside
+the bracket an independent bisection on the assembled problem gives, the step equal to
+numpy's damped least squares there, lambda = 0 when the Gauss-Newton step is shorter, and the
+derivative of the length against central differences (a planted mistake in z fails it).
 """
 from __future__ import annotations
 
@@ -88,3 +92,61 @@ def block_steps(blocks, b: np.ndarray, d: np.ndarray, lam: float) -> np.ndarray:
         r0 += n
         c0 += m
     return np.concatenate(p)
+
+
+# ---- Moré's trust-region choice of lambda (Sec. 5.2: the damping of the two-factorization LM
+# step chosen so that the step has a given scaled length; Moré 1977, Hebden's iteration) ----
+
+def tr_parts(s1_list, d_list, lam: float):
+    """For the block-diagonal step p(lam): ||q|| with q = D p, ||z|| with z = R'^{-T} D q
+    (R'^T R' = J^T J + lam D^2), and p.  d/dlam ||q|| = -||z||^2 / ||q||."""
+    ps, q2, z2 = [], 0.0, 0.0
+    for s1, d in zip(s1_list, d_list):
+        p, Rp, _ = stage2(s1, d, lam)
+        q = d * p
+        # R'^T z = D q by forward substitution (R' upper triangular)
+        z = hh.forward_substitute_rt(Rp, d * q)
+        ps.append(p)
+        q2 += float(q @ q)
+        z2 += float(z @ z)
+    return np.concatenate(ps), np.sqrt(q2), np.sqrt(z2)
+
+
+def trust_region_lambda(blocks, b, d, delta: float, sigma: float = 0.1, max_iter: int = 30):
+    """The lambda >= 0 whose damped step has scaled length ||D p(lambda)|| within sigma Delta of
+    Delta, or lambda = 0 when the Gauss-Newton step is already that short (the trust-region
+    subproblem).  Newton's method on 1/||D p|| - 1/Delta (nearly linear in lambda), kept inside
+    a bracket [lo, hi] that every iterate narrows: lo from a Newton step of ||D p|| - Delta at 0
+    (that function is convex and decreasing), hi = ||D^{-1} J^T b|| / Delta.  Returns
+    (lambda, p, iterations)."""
+    s1s, ds, r0, c0 = [], [], 0, 0
+    g2 = 0.0
+    for Ji in blocks:
+        n, m = Ji.shape
+        s1 = stage1(Ji, b[r0:r0 + n])
+        di = np.asarray(d[c0:c0 + m], dtype=np.float64)
+        gi = s1.R.T @ s1.c            # J_i^T b_i
+        g2 += float(np.sum((gi / di) ** 2))
+        s1s.append(s1)
+        ds.append(di)
+        r0 += n
+        c0 += m
+    p, qn, zn = tr_parts(s1s, ds, 0.0)
+    phi = qn - delta
+    if phi <= sigma * delta:
+        return 0.0, p, 0
+    lo = phi * qn / (zn * zn) if zn > 0 else 0.0
+    hi = np.sqrt(g2) / delta
+    lam = max(0.001 * hi, np.sqrt(lo * hi))
+    for it in range(1, max_iter + 1):
+        p, qn, zn = tr_parts(s1s, ds, lam)
+        phi = qn - delta
+        if abs(phi) <= sigma * delta:
+            return lam, p, it
+        if phi > 0:
+            lo = max(lo, lam)
+        else:
+            hi = min(hi, lam)
+        lam_new = lam + (qn / zn) ** 2 * (phi / delta)
+        lam = lam_new if lo < lam_new < hi else max(0.001 * hi, np.sqrt(lo * hi))
+    return lam, p, max_iter
