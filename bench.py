@@ -350,8 +350,22 @@ def other_workloads(dev, stream, only=None):
             t1 = _time(stream, lambda: ctx.factor_solve(J, b, p1, q, refine_steps=0), 5)
             t2 = _time(stream, lambda: ctx.more_solve(q, p1, None, 1e-2), 10)
             ctx.sync_status()
+            # the trust-region lambda for a radius a tenth of the undamped step's scaled length
+            # (host clock: the iteration reads three sums back per pass)
+            ctx.more_solve(q, p1, None, 0.0)
+            gn = float(torch.linalg.vector_norm(p1.double()).item())
+            ctx.more_trust_region(q, p1, 0.1 * gn)   # warm
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            reps = 5
+            for _ in range(reps):
+                lam_tr, it_tr = ctx.more_trust_region(q, p1, 0.1 * gn)
+            t_tr = (time.perf_counter() - t0) / reps * 1e3
+            ctx.sync_status()
             res[prec] = {"ms_stage1_factor_qtb_solve": t1, "ms_stage2_per_lambda": t2,
-                         "lambda_trials_per_s": 1000.0 / t2}
+                         "lambda_trials_per_s": 1000.0 / t2,
+                         "trust_region": {"radius": "0.1 ||p_GN||_2, inside the undamped step's scaled length ||D p_GN||",
+                                          "ms": t_tr, "passes": it_tr + 1, "lambda": lam_tr}}
             ctx.close()
             del J, b, p1, q
         out["more_two_step_1m_blocks"] = {

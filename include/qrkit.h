@@ -197,6 +197,25 @@ qrkit_status qrkit_set_wait_limit(qrkit_ctx* ctx, int64_t polls);
  * word.  Asynchronous. */
 qrkit_status qrkit_more_solve(qrkit_ctx* ctx, const void* qtb, const void* D, double lambda, void* p);
 
+/* Moré's trust-region choice of the damping for the two-factorization step (Sec. 5.2, after
+ * Moré 1977): the lambda >= 0 whose step p(lambda) (qrkit_more_solve's) has scaled length
+ * ||D p|| within sigma delta of delta, or lambda = 0 when the undamped step is already that
+ * short.  Each iteration is one stage 2 over all blocks that also sums ||D p||^2 and ||z||^2
+ * (R'^T z = D^2 p, so d||D p||/dlambda = -||z||^2 / ||D p||); lambda moves by Newton's step on
+ * 1/||D p|| - 1/delta inside a bracket that each iterate narrows (upper end
+ * ||D^{-1} J^T b|| / delta).
+ *   qtb, D, p     : as for qrkit_more_solve (D NULL: the column norms of J)
+ *   delta         : > 0, the trust-region radius in the scaled norm
+ *   sigma         : in (0, 1), the accepted relative deviation (0.1 is customary)
+ *   max_iter      : >= 1
+ *   lambda        : HOST out, the damping found
+ *   iterations    : HOST out or NULL, stage-2 passes after the undamped one
+ * p holds the step for the returned lambda.  QRKIT_ENOTCONV when max_iter passes do not
+ * reach the tolerance (p and lambda then hold the last iterate); QRKIT_ESTATE without a
+ * block-diagonal factor.  Synchronous (three sums are read back per iteration). */
+qrkit_status qrkit_more_trust_region(qrkit_ctx* ctx, const void* qtb, const void* D, double delta, double sigma,
+                                     int max_iter, double* lambda, void* p, int* iterations);
+
 /* Result record of qrkit_get_info. */
 typedef struct qrkit_info {
   int32_t refine_steps_max;   /* most refinement steps a block took in the last FP32-refined

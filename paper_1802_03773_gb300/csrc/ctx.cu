@@ -281,6 +281,7 @@ void qrkit_destroy(qrkit_ctx* ctx) {
   release(ctx->ws.rcount);
   release(ctx->ws.tlist);
   release(ctx->ws.tcount);
+  release(ctx->more_sums);
   release(ctx->ws.tfactor);
   release(ctx->ws.ttau);
   release(ctx->ws.rrec);
@@ -364,6 +365,20 @@ qrkit_status qrkit_more_solve(qrkit_ctx* ctx, const void* qtb, const void* D, do
   if (!(lambda >= 0.0)) return fail(ctx, QRKIT_EINVAL, "lambda must be >= 0");
   QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
   return more_stage2(ctx, qtb, D, lambda, p);
+}
+
+qrkit_status qrkit_more_trust_region(qrkit_ctx* ctx, const void* qtb, const void* D, double delta, double sigma,
+                                     int max_iter, double* lambda, void* p, int* iterations) {
+  if (!ctx) return QRKIT_EINVAL;
+  const Plan& P = ctx->plan;
+  if (!P.valid || P.s.kind != QRKIT_STRUCT_BLOCKS || P.s.coupled_kind != QRKIT_COUPLED_NONE)
+    return fail(ctx, QRKIT_ESTATE, "qrkit_more_trust_region needs a block-diagonal plan");
+  if (!ctx->factored) return fail(ctx, QRKIT_ESTATE, "qrkit_more_trust_region before qrkit_factor_solve");
+  if (!qtb || !p || !lambda) return fail(ctx, QRKIT_EINVAL, "qtb, p and lambda are required");
+  if (!(delta > 0.0) || !(sigma > 0.0 && sigma < 1.0) || max_iter < 1)
+    return fail(ctx, QRKIT_EINVAL, "need delta > 0, 0 < sigma < 1, max_iter >= 1");
+  QRKIT_CUDA_TRY(ctx, cudaSetDevice(ctx->device));
+  return more_trust_region(ctx, qtb, D, delta, sigma, max_iter, lambda, p, iterations);
 }
 
 static qrkit_status need_dense_plan(qrkit_ctx* ctx, const char* what) {

@@ -244,6 +244,7 @@ struct qrkit_ctx {
   int occ_per_sm[16] = {};
   long long wait_limit = 1LL << 26;  // polls of a bounded device wait before it gives up
   bool refine_stats = false;    // ws.tcount holds the last fused solve's selection counts and steps
+  qrkit::DevBuf more_sums;      // trust-region lambda: the three block sums of an iteration
   float refine_select = 2e-6f;  // block refinement: a-priori error estimate that selects a block
   int refine_residual = 0;      // its residual precision: 0 compensated float, 1 double
   bool factored = false;       // fused block path
@@ -320,6 +321,8 @@ qrkit_status launch_block_tasks(qrkit_ctx* ctx, const void* J, const void* b, vo
 // Moré's stage 2 (Sec. 5.2) for the stored block factor: p from [R_i; lambda^(1/2) D_i] and the
 // top m_i entries of qtb per block (D null: column norms of R_i).
 qrkit_status more_stage2(qrkit_ctx* ctx, const void* qtb, const void* D, double lambda, void* p);
+qrkit_status more_trust_region(qrkit_ctx* ctx, const void* qtb, const void* D, double delta, double sigma,
+                               int max_iter, double* lambda, void* p, int* iterations);
 // The warp-task factor (task planes) copied into J's packing and tau into column order.
 qrkit_status unpack_block_tasks_factor(qrkit_ctx* ctx, void* factor_out, void* tau_out);
 void release_block_tasks(Plan& P);

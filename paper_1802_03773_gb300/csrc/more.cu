@@ -44,12 +44,26 @@ struct MoreArgs {
   double lambda;
   T* p;
   int* status;
+  double* sums;          // or null: ||D p||^2, ||R'^{-T} D^2 p||^2, ||D^{-1} J^T b||^2 summed over blocks
 };
 
-// Stage 2 for one block: R (upper, m x m), c (m), d (m) -> p.
+// Stage 2 for one block: R (upper, m x m), c (m), d (m) -> p.  With sums, also the block's
+// parts of the trust-region iteration (Moré 1977): ||D_i J_i^T b_i||-type term
+// g2 = ||D_i^{-1} R_i^T c_i||^2 (= ||D_i^{-1} J_i^T b_i||^2, from stage 1's R and c),
+// q2 = ||D_i p_i||^2 and z2 = ||z_i||^2 with R'_i^T z_i = D_i^2 p_i.
 template <typename T>
 __device__ __forceinline__ void more_block(T (&R)[kM][kM], T (&c)[kM], const T (&d)[kM], int m, double lambda,
-                                           T* p, int* status) {
+                                           T* p, int* status, double* part) {
+  if (part) {   // in the context precision (the bracket needs no more), squares summed in double
+    double g2 = 0.0;
+    for (int k = 0; k < m; ++k) {
+      T gk = T(0);
+      for (int i = 0; i <= k; ++i) gk += R[i][k] * c[i];
+      gk /= d[k];
+      g2 += (double)gk * (double)gk;
+    }
+    part[2] = g2;
+  }
   const T lh = (T)sqrt(lambda);
   for (int k = 0; k < m; ++k) {
     // the damping row of column k: one entry lambda^(1/2) d_k at column k, rhs 0
@@ -88,6 +102,33 @@ __device__ __forceinline__ void more_block(T (&R)[kM][kM], T (&c)[kM], const T (
   }
   for (int k = 0; k < m; ++k) p[k] = c[k];
   if (!ok && status) atomicCAS(status, 0, (int)QRKIT_ESINGULAR);
+  if (part) {
+    // q = D p; R'^T z = D q by forward substitution (R' upper triangular, now in R); z only
+    // steers Newton's step, so it is formed in the context precision
+    double q2 = 0.0, z2 = 0.0;
+    T z[kM];
+    for (int k = 0; k < m; ++k) {
+      const T q = d[k] * c[k];
+      q2 += (double)q * (double)q;
+      T v = d[k] * q;
+      for (int i = 0; i < k; ++i) v -= R[i][k] * z[i];
+      z[k] = v / R[k][k];
+      z2 += (double)z[k] * (double)z[k];
+    }
+    part[0] = q2;
+    part[1] = z2;
+  }
+}
+
+// The three sums of the trust-region iteration over a warp, then one atomic each.
+__device__ __forceinline__ void more_sums_add(double* sums, double (&part)[3]) {
+#pragma unroll
+  for (int j = 0; j < 3; ++j) {
+    double v = part[j];
+#pragma unroll
+    for (int o = 16; o >= 1; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0 && v != 0.0) atomicAdd(sums + j, v);
+  }
 }
 
 template <typename T>
@@ -107,51 +148,58 @@ __device__ __forceinline__ void load_d(const MoreArgs<T>& A, const T (&R)[kM][kM
 }
 
 // Warp-task factor: one thread per task slot.
-template <typename T>
+template <typename T, bool SUMS>
 __global__ void __launch_bounds__(128) more_planes_kernel(MoreArgs<T> A) {
   const int64_t gid = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
   const int64_t t = gid >> 5;
   const int slot = (int)(gid & 31);
-  if (t >= A.num_tasks) return;
+  if (t >= A.num_tasks) return;   // warp-uniform: a warp is one task's slots
   const TaskHdr h = A.hdr[t];
   const int G = tasks::group_lanes(h.key), m = (h.key & 7) + 1;
-  if (slot >= tasks::task_blocks(G)) return;
-  const TaskEntry e = A.ent[h.first + slot];
-  if (e.n == 0) return;
-  T R[kM][kM], c[kM], d[kM];
+  double part[3] = {0.0, 0.0, 0.0};
+  if (slot < tasks::task_blocks(G)) {
+    const TaskEntry e = A.ent[h.first + slot];
+    if (e.n != 0) {
+      T R[kM][kM], c[kM], d[kM];
 #pragma unroll
-  for (int i = 0; i < kM; ++i)
+      for (int i = 0; i < kM; ++i)
 #pragma unroll
-    for (int j = 0; j < kM; ++j)
-      R[i][j] = (i <= j && j < m) ? A.tF[((int64_t)h.plane + j) * kPlaneValues + slot * 4 * G + i] : T(0);
-  const int64_t r0 = h.r0 + e.r, c0 = h.c0 + e.c;
+        for (int j = 0; j < kM; ++j)
+          R[i][j] = (i <= j && j < m) ? A.tF[((int64_t)h.plane + j) * kPlaneValues + slot * 4 * G + i] : T(0);
+      const int64_t r0 = h.r0 + e.r, c0 = h.c0 + e.c;
 #pragma unroll
-  for (int k = 0; k < kM; ++k) c[k] = k < m ? A.qtb[r0 + k] : T(0);
-  load_d<T>(A, R, c0, m, d);
-  more_block<T>(R, c, d, m, A.lambda, A.p + c0, A.status);
+      for (int k = 0; k < kM; ++k) c[k] = k < m ? A.qtb[r0 + k] : T(0);
+      load_d<T>(A, R, c0, m, d);
+      more_block<T>(R, c, d, m, A.lambda, A.p + c0, A.status, SUMS ? part : nullptr);
+    }
+  }
+  if constexpr (SUMS) more_sums_add(A.sums, part);
 }
 
 // Tile-mapping factor (J's packing): one thread per block.
-template <typename T>
+template <typename T, bool SUMS>
 __global__ void __launch_bounds__(128) more_packed_kernel(MoreArgs<T> A) {
   const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-  if (i >= A.K) return;
-  const int n = A.n[i], m = A.m[i];
-  const T* F = A.F + A.val_off[i];
-  T R[kM][kM], c[kM], d[kM];
+  double part[3] = {0.0, 0.0, 0.0};
+  if (i < A.K) {
+    const int n = A.n[i], m = A.m[i];
+    const T* F = A.F + A.val_off[i];
+    T R[kM][kM], c[kM], d[kM];
 #pragma unroll
-  for (int r = 0; r < kM; ++r)
+    for (int r = 0; r < kM; ++r)
 #pragma unroll
-    for (int j = 0; j < kM; ++j) R[r][j] = (r <= j && j < m) ? F[(int64_t)j * n + r] : T(0);
-  const int64_t r0 = A.row_off[i], c0 = A.col_off[i];
+      for (int j = 0; j < kM; ++j) R[r][j] = (r <= j && j < m) ? F[(int64_t)j * n + r] : T(0);
+    const int64_t r0 = A.row_off[i], c0 = A.col_off[i];
 #pragma unroll
-  for (int k = 0; k < kM; ++k) c[k] = k < m ? A.qtb[r0 + k] : T(0);
-  load_d<T>(A, R, c0, m, d);
-  more_block<T>(R, c, d, m, A.lambda, A.p + c0, A.status);
+    for (int k = 0; k < kM; ++k) c[k] = k < m ? A.qtb[r0 + k] : T(0);
+    load_d<T>(A, R, c0, m, d);
+    more_block<T>(R, c, d, m, A.lambda, A.p + c0, A.status, SUMS ? part : nullptr);
+  }
+  if constexpr (SUMS) more_sums_add(A.sums, part);
 }
 
 template <typename T>
-qrkit_status more_typed(qrkit_ctx* ctx, const void* qtb, const void* D, double lambda, void* p) {
+qrkit_status more_typed(qrkit_ctx* ctx, const void* qtb, const void* D, double lambda, void* p, double* sums) {
   const Plan& P = ctx->plan;
   MoreArgs<T> A{};
   A.qtb = (const T*)qtb;
@@ -159,13 +207,17 @@ qrkit_status more_typed(qrkit_ctx* ctx, const void* qtb, const void* D, double l
   A.lambda = lambda;
   A.p = (T*)p;
   A.status = ctx->d_status;
+  A.sums = sums;
   if (ctx->factor_in_planes) {
     A.hdr = (const TaskHdr*)P.d_task_hdr.ptr;
     A.ent = (const TaskEntry*)P.d_task_ent.ptr;
     A.num_tasks = P.num_tasks;
     A.tF = (const T*)ctx->ws.tfactor.ptr;
     const int64_t threads = P.num_tasks * 32;
-    more_planes_kernel<T><<<(unsigned)((threads + 127) / 128), 128, 0, ctx->stream>>>(A);
+    if (sums)
+      more_planes_kernel<T, true><<<(unsigned)((threads + 127) / 128), 128, 0, ctx->stream>>>(A);
+    else
+      more_planes_kernel<T, false><<<(unsigned)((threads + 127) / 128), 128, 0, ctx->stream>>>(A);
   } else {
     A.F = (const T*)ctx->ws.factor.ptr;
     A.val_off = (const int64_t*)P.d_val_off.ptr;
@@ -174,7 +226,10 @@ qrkit_status more_typed(qrkit_ctx* ctx, const void* qtb, const void* D, double l
     A.n = (const uint8_t*)P.d_n.ptr;
     A.m = (const uint8_t*)P.d_m.ptr;
     A.K = P.K;
-    more_packed_kernel<T><<<(unsigned)((P.K + 127) / 128), 128, 0, ctx->stream>>>(A);
+    if (sums)
+      more_packed_kernel<T, true><<<(unsigned)((P.K + 127) / 128), 128, 0, ctx->stream>>>(A);
+    else
+      more_packed_kernel<T, false><<<(unsigned)((P.K + 127) / 128), 128, 0, ctx->stream>>>(A);
   }
   ctx->launches += 1;
   QRKIT_CUDA_TRY(ctx, cudaGetLastError());
@@ -184,8 +239,64 @@ qrkit_status more_typed(qrkit_ctx* ctx, const void* qtb, const void* D, double l
 }  // namespace
 
 qrkit_status more_stage2(qrkit_ctx* ctx, const void* qtb, const void* D, double lambda, void* p) {
-  if (ctx->precision == QRKIT_FP64) return more_typed<double>(ctx, qtb, D, lambda, p);
-  return more_typed<float>(ctx, qtb, D, lambda, p);
+  if (ctx->precision == QRKIT_FP64) return more_typed<double>(ctx, qtb, D, lambda, p, nullptr);
+  return more_typed<float>(ctx, qtb, D, lambda, p, nullptr);
+}
+
+// Moré's choice of lambda for a trust region of scaled radius delta (Moré 1977): stage 2 at
+// lambda gives p, ||q|| = ||D p|| and ||z|| (R'^T z = D q), whose ratio fixes the derivative
+// of the length, d||q||/dlambda = -||z||^2 / ||q||.  Newton's method on 1/||q|| - 1/delta,
+// which is nearly linear in lambda: lambda += (||q|| / ||z||)^2 (||q|| - delta) / delta,
+// kept inside a bracket [lo, hi] that each iterate narrows (lo from a Newton step of the
+// convex, decreasing ||q|| - delta at 0, hi = ||D^{-1} J^T b|| / delta), until ||q|| is within
+// sigma delta of delta; lambda = 0 when the Gauss-Newton step is already that short.  The three
+// block sums come back to the host once per iteration (synchronous).
+qrkit_status more_trust_region(qrkit_ctx* ctx, const void* qtb, const void* D, double delta, double sigma,
+                               int max_iter, double* lambda, void* p, int* iterations) {
+  DevBuf& S = ctx->more_sums;
+  qrkit_status st = ensure(ctx, S, 3 * sizeof(double), "trust-region sums");
+  if (st != QRKIT_OK) return st;
+  double* sums = (double*)S.ptr;
+  double h[3];
+  auto eval = [&](double lam) -> qrkit_status {
+    QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(sums, 0, 3 * sizeof(double), ctx->stream));
+    qrkit_status r = ctx->precision == QRKIT_FP64 ? more_typed<double>(ctx, qtb, D, lam, p, sums)
+                                                  : more_typed<float>(ctx, qtb, D, lam, p, sums);
+    if (r != QRKIT_OK) return r;
+    QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(h, sums, sizeof(h), cudaMemcpyDeviceToHost, ctx->stream));
+    QRKIT_CUDA_TRY(ctx, cudaStreamSynchronize(ctx->stream));
+    return QRKIT_OK;
+  };
+  if ((st = eval(0.0)) != QRKIT_OK) return st;
+  double qn = sqrt(h[0]), zn = sqrt(h[1]);
+  const double gn = sqrt(h[2]);
+  double phi = qn - delta;
+  if (phi <= sigma * delta) {
+    *lambda = 0.0;
+    if (iterations) *iterations = 0;
+    return QRKIT_OK;
+  }
+  double lo = zn > 0.0 ? phi * qn / (zn * zn) : 0.0;
+  double hi = gn / delta;
+  double lam = std::max(0.001 * hi, sqrt(lo * hi));
+  for (int it = 1; it <= max_iter; ++it) {
+    if ((st = eval(lam)) != QRKIT_OK) return st;
+    qn = sqrt(h[0]);
+    zn = sqrt(h[1]);
+    phi = qn - delta;
+    if (fabs(phi) <= sigma * delta || !(zn > 0.0)) {
+      *lambda = lam;
+      if (iterations) *iterations = it;
+      return QRKIT_OK;
+    }
+    if (phi > 0.0) lo = std::max(lo, lam);
+    else hi = std::min(hi, lam);
+    const double next = lam + (qn / zn) * (qn / zn) * (phi / delta);
+    lam = (lo < next && next < hi) ? next : std::max(0.001 * hi, sqrt(lo * hi));
+  }
+  *lambda = lam;
+  if (iterations) *iterations = max_iter;
+  return fail(ctx, QRKIT_ENOTCONV, "trust-region lambda: no convergence within max_iter iterations");
 }
 
 }  // namespace qrkit

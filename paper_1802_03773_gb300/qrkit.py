@@ -125,6 +125,8 @@ _SIGS = {
     "qrkit_set_refinement": (ctypes.c_int, [_VP, ctypes.c_double, ctypes.c_int]),
     "qrkit_set_wait_limit": (ctypes.c_int, [_VP, ctypes.c_int64]),
     "qrkit_more_solve": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, _VP]),
+    "qrkit_more_trust_region": (ctypes.c_int, [_VP, _VP, _VP, ctypes.c_double, ctypes.c_double, ctypes.c_int,
+                                               ctypes.POINTER(ctypes.c_double), _VP, ctypes.POINTER(ctypes.c_int)]),
     "qrkit_column_sumsq": (ctypes.c_int, [_VP, _VP, _VP, _VP]),
     "qrkit_norms_from_sumsq": (ctypes.c_int, [_VP, _VP, ctypes.c_int64, _VP]),
     "qrkit_get_reduced_r": (ctypes.c_int, [_VP, _VP]),
@@ -520,6 +522,16 @@ class Context:
         """Moré's second factorization for the stored block factor (qtb from factor_solve)."""
         self._check(self.lib.qrkit_more_solve(self.h, self._t(qtb, "qtb"), self._t(D, "D", True), float(lam),
                                               self._t(p, "p")))
+
+    def more_trust_region(self, qtb, p, delta, D=None, sigma=0.1, max_iter=30):
+        """Moré's trust-region lambda for the stored block factor (qrkit_more_trust_region):
+        returns (lambda, iterations); p receives the step."""
+        lam = ctypes.c_double(0.0)
+        it = ctypes.c_int(0)
+        self._check(self.lib.qrkit_more_trust_region(self.h, self._t(qtb, "qtb"), self._t(D, "D", True), float(delta),
+                                                     float(sigma), int(max_iter), ctypes.byref(lam),
+                                                     self._t(p, "p"), ctypes.byref(it)))
+        return lam.value, it.value
 
     def set_wait_limit(self, polls):
         """Poll limit of the bounded device waits (0 makes them run out: QRKIT_ETIMEOUT)."""

@@ -139,3 +139,68 @@ def test_more_needs_a_factor():
         ctx.more_solve(q, p, None, 1.0)
     assert e.value.status == 9
     ctx.close()
+
+
+def oracle_blocks_and_d(d):
+    P = blocks_problem(d)
+    dcol = np.concatenate([np.sqrt(np.sum(B * B, axis=0)) for B in P.blocks])
+    dcol[dcol == 0.0] = 1.0
+    return P, dcol
+
+
+@pytest.mark.parametrize("precision,mapping", [("fp64", None), ("fp64", "budget 256 1536 512 256 2048"),
+                                               ("fp32", None)])
+def test_trust_region_lambda_equals_oracle(precision, mapping):
+    """Moré's trust-region lambda (qrkit_more_trust_region) against the oracle's iteration on the
+    same blocks: lambda to the iteration's rounding, the step as the damped solution there, and
+    the scaled length within sigma of the radius."""
+    torch = cuda_or_skip()
+    from paper_1802_03773_gb300 import Context
+    d = batched_blocks(K=3000, seed_offset=31, dtype=np.float64 if precision == "fp64" else np.float32)
+    P, dcol = oracle_blocks_and_d(d)
+    p_gn = np.concatenate([np.linalg.lstsq(B, P.b[int(d["row_off"][i]):int(d["row_off"][i + 1])], rcond=None)[0]
+                           for i, B in enumerate(P.blocks)])
+    gn_len = float(np.linalg.norm(dcol * p_gn))
+    ctx = Context(0, precision=precision)
+    J, b, p0, qtb = stage1(torch, ctx, d)
+    if mapping:
+        ctx.apply_tuning(mapping)
+        ctx.factor_solve(J, b, p0, qtb, refine_steps=0)
+    p = torch.empty_like(p0)
+    for frac in (0.02, 0.3):
+        delta = frac * gn_len
+        lam, it = ctx.more_trust_region(qtb, p, delta, sigma=0.1)
+        ctx.sync_status()
+        lam_o, p_o, it_o = more.trust_region_lambda(P.blocks, P.b, dcol, delta, sigma=0.1)
+        pg = p.cpu().numpy().astype(np.float64)
+        length = float(np.linalg.norm(dcol * pg))
+        assert abs(length - delta) <= 0.1 * delta * (1 + 1e-3)
+        if precision == "fp64":
+            assert it == it_o
+            assert lam == pytest.approx(lam_o, rel=1e-8)
+            assert_close(pg, p_o, 1e-10)
+        else:
+            # float stage 2: the same iteration on slightly different sums
+            assert lam == pytest.approx(lam_o, rel=1e-3)
+            p_ref = more.block_steps(P.blocks, P.b, dcol, lam)
+            assert_close(pg, p_ref, 2e-4)
+    # a radius the undamped step already fits: lambda = 0 and the undamped step
+    lam, it = ctx.more_trust_region(qtb, p, 2.0 * gn_len)
+    assert lam == 0.0 and it == 0
+    if precision == "fp64":
+        assert_close(p.cpu().numpy().astype(np.float64), p_gn, 1e-10)
+    else:   # the same back-substitution as stage 1's
+        assert_close(p.cpu().numpy().astype(np.float64), p0.cpu().numpy().astype(np.float64), 1e-5)
+    ctx.close()
+
+
+def test_trust_region_rejects_bad_arguments():
+    torch = cuda_or_skip()
+    from paper_1802_03773_gb300 import Context, qrkit
+    d = batched_blocks(K=100, seed_offset=32, dtype=np.float64)
+    ctx = Context(0, precision="fp64")
+    J, b, p0, qtb = stage1(torch, ctx, d)
+    for delta, sigma, iters in ((0.0, 0.1, 10), (1.0, 0.0, 10), (1.0, 1.0, 10), (1.0, 0.1, 0)):
+        with pytest.raises(qrkit.QRKitError):
+            ctx.more_trust_region(qtb, p0, delta, sigma=sigma, max_iter=iters)
+    ctx.close()
