@@ -462,11 +462,12 @@ tsqr_tile_kernel(T* X, int64_t ld, int64_t M, int s, int tile_rows, T* taus, T* 
   }
 }
 
-// Q_tile^T applied to a level's rhs segment; the top min(r, s) entries go to the next level.
+// Q_tile^T applied to a level's rhs segment; the top min(r, s) entries go to the next level, and
+// with column panels the others to the next panel's first level (row down0 + tile (tile_rows - s)).
 template <typename T>
 __global__ void __launch_bounds__(kTileThreads)
 tsqr_apply_qt_kernel(const T* X, int64_t ld, int64_t M, int s, int tile_rows, const T* taus,
-                     T* rhs, T* rhs_next) {
+                     T* rhs, T* rhs_next, T* rhs_down, int64_t down0) {
   __shared__ T red[32];
   const int64_t r0 = (int64_t)blockIdx.x * tile_rows;
   const int r = (int)(M - r0 < (int64_t)tile_rows ? M - r0 : (int64_t)tile_rows);
@@ -494,6 +495,9 @@ tsqr_apply_qt_kernel(const T* X, int64_t ld, int64_t M, int s, int tile_rows, co
   }
   if (rhs_next)
     for (int i = tid; i < kmax; i += blockDim.x) rhs_next[(int64_t)blockIdx.x * s + i] = y[i];
+  if (rhs_down)   // column panels: the rows below the tile's R rows, for the next panel
+    for (int i = kmax + tid; i < r; i += blockDim.x)
+      rhs_down[down0 + (int64_t)blockIdx.x * (tile_rows - s) + (i - kmax)] = y[i];
 }
 
 // Per-block Q_i^T [b_i; 0]: top m -> ctop, bottom -> reduced rhs rows.  NA > 0: every block has
@@ -1147,7 +1151,7 @@ static FactorOut<T> fout(qrkit_ctx* ctx) {
   O.aug_off = (const int64_t*)(C.damp ? C.d_aug_off_d.ptr : C.d_aug_off_u.ptr);
   O.red_off = (const int64_t*)(C.damp ? C.d_red_off_d.ptr : C.d_red_off_u.ptr);
   O.X0 = C.levels.empty() ? nullptr : (T*)C.levels[0].X.ptr;
-  O.ld0 = C.levels.empty() ? 0 : C.levels[0].M;
+  O.ld0 = C.levels.empty() ? 0 : C.levels[0].ld;
   O.Xw = (T*)C.Xw.ptr;
   O.Xstart = (int64_t*)C.Xstart.ptr;
   O.status = ctx->d_status;
@@ -1203,6 +1207,50 @@ static qrkit_status norms_typed(qrkit_ctx* ctx, const ComposedView<T>& V, double
   return QRKIT_OK;
 }
 
+// Column-panel TSQR of a float dense reduced block wider than one tile.  Panel j (columns
+// c0 = 128 j ..): its levels are factored tile by tile (R rows up; the top level's into R_S), and
+// after each level the tiles' Q^T is applied to the panel's trailing columns, whose rows move up
+// with the R rows or down into the next panel's first level.
+static qrkit_status factor_panels(qrkit_ctx* ctx, int s) {
+  Composed& C = ctx->comp;
+  cudaStream_t st = ctx->stream;
+  float* Rs = (float*)C.Rs.ptr;
+  const int np = 1 + (int)C.panels.size();
+  for (int j = 0; j < np; ++j) {
+    std::vector<TsqrLevel>& LV = j == 0 ? C.levels : C.panels[j - 1].levels;
+    const int c0 = j * kPanelCols;
+    const int pw = std::min(kPanelCols, s - c0);
+    const int n = s - c0 - pw;   // trailing columns
+    for (size_t l = 0; l < LV.size(); ++l) {
+      TsqrLevel& L = LV[l];
+      const bool top = l + 1 == LV.size();
+      float* X = (float*)L.X.ptr;
+      float* Xn = top ? Rs + (int64_t)c0 * s + c0 : (float*)LV[l + 1].X.ptr;
+      const int64_t ldn = top ? s : LV[l + 1].ld;
+      qrkit_status rc;
+      if (tsqr_tc_supported(pw, C.tile_rows)) {
+        rc = tsqr_tile_tc(ctx, X, L.ld, L.M, pw, (float*)L.tau.ptr, Xn, ldn, L.tiles, n > 0 ? (float*)L.T.ptr : nullptr);
+        if (rc != QRKIT_OK) return rc;
+      } else {   // a last panel of at most 64 columns
+        const size_t smem = ((size_t)C.tile_rows * pw + 64) * sizeof(float);
+        auto k = tsqr_tile_kernel<float>;
+        QRKIT_CUDA_TRY(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+        LAUNCH(ctx, k<<<(unsigned)L.tiles, kTileThreads, smem, st>>>(X, L.ld, L.M, pw, C.tile_rows,
+                                                                    (float*)L.tau.ptr, Xn, ldn, ctx->d_status));
+      }
+      if (n > 0) {
+        float* upp = top ? Rs + (int64_t)(c0 + pw) * s + c0 : (float*)LV[l + 1].X.ptr + (int64_t)pw * LV[l + 1].ld;
+        const int64_t ldu = top ? s : LV[l + 1].ld;
+        TsqrLevel& N0 = C.panels[j].levels[0];
+        rc = tsqr_panel_apply(ctx, X, L.ld, L.M, pw, (const float*)L.T.ptr, n, upp, ldu, (float*)N0.X.ptr, N0.ld,
+                              L.down0, L.tiles);
+        if (rc != QRKIT_OK) return rc;
+      }
+    }
+  }
+  return QRKIT_OK;
+}
+
 template <typename T>
 static qrkit_status factor_typed(qrkit_ctx* ctx, const void* J, const void* S, const void* Dext,
                                  double lambda, bool dext_double = false) {
@@ -1250,22 +1298,23 @@ static qrkit_status factor_typed(qrkit_ctx* ctx, const void* J, const void* S, c
     const int s = V.s;
     if (C.damp)
       LAUNCH(ctx, reduced_damping_kernel<T><<<blocks_for((int64_t)s * s, 256), 256, 0, st>>>(
-                      (T*)C.levels[0].X.ptr, C.levels[0].M, C.red_rows, s, (const double*)C.D.ptr,
+                      (T*)C.levels[0].X.ptr, C.levels[0].ld, C.red_rows, s, (const double*)C.D.ptr,
                       P.cols, C.lam_half));
+    if (!C.panels.empty()) return factor_panels(ctx, s);
     for (size_t l = 0; l < C.levels.size(); ++l) {
       TsqrLevel& L = C.levels[l];
       T* Xn = l + 1 < C.levels.size() ? (T*)C.levels[l + 1].X.ptr : nullptr;
-      const int64_t ldn = l + 1 < C.levels.size() ? C.levels[l + 1].M : 0;
+      const int64_t ldn = l + 1 < C.levels.size() ? C.levels[l + 1].ld : 0;
       if (sizeof(T) == sizeof(float) && tsqr_tc_supported(s, C.tile_rows)) {
         // tensor-core trailing updates (3xTF32)
-        rc = tsqr_tile_tc(ctx, (float*)L.X.ptr, L.M, L.M, s, (float*)L.tau.ptr, (float*)Xn, ldn, L.tiles);
+        rc = tsqr_tile_tc(ctx, (float*)L.X.ptr, L.ld, L.M, s, (float*)L.tau.ptr, (float*)Xn, ldn, L.tiles);
         if (rc != QRKIT_OK) return rc;
         continue;
       }
       const size_t smem = ((size_t)C.tile_rows * s + 64) * sizeof(T);
       auto k = tsqr_tile_kernel<T>;
       QRKIT_CUDA_TRY(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-      LAUNCH(ctx, k<<<(unsigned)L.tiles, kTileThreads, smem, st>>>((T*)L.X.ptr, L.M, L.M, s, C.tile_rows,
+      LAUNCH(ctx, k<<<(unsigned)L.tiles, kTileThreads, smem, st>>>((T*)L.X.ptr, L.ld, L.M, s, C.tile_rows,
                                                                   (T*)L.tau.ptr, Xn, ldn, ctx->d_status));
     }
   }
@@ -1291,11 +1340,22 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
   if (V.coupled == QRKIT_COUPLED_DENSE) {
     if (C.damp)
       QRKIT_CUDA_TRY(ctx, cudaMemsetAsync(rhs0 + C.red_rows, 0, (size_t)s * sizeof(T), st));
-    for (size_t l = 0; l < C.levels.size(); ++l) {
-      TsqrLevel& L = C.levels[l];
-      T* rn = l + 1 < C.levels.size() ? (T*)C.levels[l + 1].rhs.ptr : nullptr;
-      LAUNCH(ctx, tsqr_apply_qt_kernel<T><<<(unsigned)L.tiles, kTileThreads, 0, st>>>(
-                      (const T*)L.X.ptr, L.M, L.M, s, C.tile_rows, (const T*)L.tau.ptr, (T*)L.rhs.ptr, rn));
+    // Q^T of every panel's levels: the top rows of a level go up (the last level's into c_S),
+    // the others, with column panels, into the next panel's first level
+    const int np = 1 + (int)C.panels.size();
+    for (int j = 0; j < np; ++j) {
+      std::vector<TsqrLevel>& LV = j == 0 ? C.levels : C.panels[j - 1].levels;
+      const int c0 = j == 0 ? 0 : C.panels[j - 1].c0;
+      const int pw = j == 0 ? C.panel0_w : C.panels[j - 1].pw;
+      T* down = j + 1 < np ? (T*)C.panels[j].levels[0].rhs.ptr : nullptr;
+      for (size_t l = 0; l < LV.size(); ++l) {
+        TsqrLevel& L = LV[l];
+        const bool top = l + 1 == LV.size();
+        T* rn = !top ? (T*)LV[l + 1].rhs.ptr : (np > 1 ? (T*)C.cs.ptr + c0 : nullptr);
+        LAUNCH(ctx, tsqr_apply_qt_kernel<T><<<(unsigned)L.tiles, kTileThreads, 0, st>>>(
+                        (const T*)L.X.ptr, L.ld, L.M, pw, C.tile_rows, (const T*)L.tau.ptr, (T*)L.rhs.ptr, rn, down,
+                        L.down0));
+      }
     }
   }
   if (V.coupled == QRKIT_COUPLED_WINDOW && qt_only)
@@ -1305,14 +1365,18 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
     T* out = (T*)qtb_out;
     QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(out, O.ctop, (size_t)nb * sizeof(T), cudaMemcpyDeviceToDevice, st));
     if (s > 0)
-      QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(out + nb, C.levels.back().rhs.ptr, (size_t)s * sizeof(T),
-                                          cudaMemcpyDeviceToDevice, st));
+      QRKIT_CUDA_TRY(ctx, cudaMemcpyAsync(out + nb, C.panels.empty() ? C.levels.back().rhs.ptr : C.cs.ptr,
+                                          (size_t)s * sizeof(T), cudaMemcpyDeviceToDevice, st));
     return QRKIT_OK;
   }
+  // R_S and c_S: the top level's rows, or the panels' R rows gathered in Rs and cs
   const TsqrLevel* top = C.levels.empty() ? nullptr : &C.levels.back();
+  const bool pan = !C.panels.empty();
+  const T* RS = pan ? (const T*)C.Rs.ptr : (top ? (const T*)top->X.ptr : nullptr);
+  const int64_t ldRS = pan ? s : (top ? top->ld : 0);
   if (V.coupled == QRKIT_COUPLED_DENSE) {
     LAUNCH(ctx, dense_backsub_kernel<T><<<1, 32, (size_t)s * sizeof(T), st>>>(
-                    (const T*)top->X.ptr, top->M, s, (const T*)top->rhs.ptr, x + nb, 0, ctx->d_status));
+                    RS, ldRS, s, pan ? (const T*)C.cs.ptr : (const T*)top->rhs.ptr, x + nb, 0, ctx->d_status));
   } else if (V.coupled == QRKIT_COUPLED_WINDOW) {
     // reduced banded block of every segment (Sec. 4.4), rows in P_r order, the shared
     // columns' damping rows interleaved
@@ -1372,10 +1436,9 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
     }
     if (V.coupled == QRKIT_COUPLED_DENSE) {
       // h_S = R_S^{-T} (g_S - R12^T h_B), then dp_S = R_S^{-1} h_S in place
-      LAUNCH(ctx, dense_fwdsub_rt_kernel<T><<<1, 32, (size_t)s * sizeof(T), st>>>(
-                      (const T*)top->X.ptr, top->M, s, gS, h + nb));
-      LAUNCH(ctx, dense_backsub_kernel<T><<<1, 32, (size_t)s * sizeof(T), st>>>(
-                      (const T*)top->X.ptr, top->M, s, h + nb, h + nb, 0, ctx->d_status));
+      LAUNCH(ctx, dense_fwdsub_rt_kernel<T><<<1, 32, (size_t)s * sizeof(T), st>>>(RS, ldRS, s, gS, h + nb));
+      LAUNCH(ctx, dense_backsub_kernel<T><<<1, 32, (size_t)s * sizeof(T), st>>>(RS, ldRS, s, h + nb, h + nb, 0,
+                                                                                 ctx->d_status));
       LAUNCH(ctx, axpy_kernel<T><<<blocks_for(s, 128), 128, 0, st>>>(x + nb, h + nb, s));
     }
     // dp_B = R_B^{-1} (h_B - R12 dp_S), accumulated into p
@@ -1437,6 +1500,11 @@ qrkit_status widen_to_double(qrkit_ctx* ctx, const float* in, double* out, int64
   return QRKIT_OK;
 }
 
+static void release_levels(std::vector<TsqrLevel>& LV) {
+  for (auto& L : LV) { release(L.X); release(L.tau); release(L.rhs); release(L.T); }
+  LV.clear();
+}
+
 void release_composed(Composed& C) {
   release(C.D); release(C.sq); release(C.Fa); release(C.tau); release(C.R12); release(C.ctop);
   release(C.g); release(C.h);
@@ -1448,7 +1516,9 @@ void release_composed(Composed& C) {
   release(C.nrm_D); release(C.nrm_L); release(C.nrm_W); release(C.nrm_y); release(C.nrm_As);
   release(C.nrm_rs); release(C.nrm_seg);
   release(C.d_aug_off_d); release(C.d_aug_off_u); release(C.d_red_off_d); release(C.d_red_off_u);
-  for (auto& L : C.levels) { release(L.X); release(L.tau); release(L.rhs); }
+  release_levels(C.levels);
+  for (auto& Pn : C.panels) release_levels(Pn.levels);
+  release(C.Rs); release(C.cs);
   C = Composed();
 }
 
@@ -1578,36 +1648,72 @@ qrkit_status composed_layout(qrkit_ctx* ctx, size_t elem) {
     }
   }
   if (P.s.coupled_kind == QRKIT_COUPLED_DENSE) {
-    if (s > 64 && !(elem == sizeof(float) && tsqr_tc_supported(s, 256)))
+    // wider than one tile (float): column panels of kPanelCols, each a TSQR of its own
+    const bool panels = elem == sizeof(float) && s > kPanelCols && s <= kMaxDenseS && s % 32 == 0;
+    if (s > 64 && !(elem == sizeof(float) && tsqr_tc_supported(s, 256)) && !panels)
       return fail(ctx, QRKIT_EUNSUPPORTED,
-                  "dense shared block: s <= 64, or (float) s in {96, 128} for the tensor-core tiles");
+                  "dense shared block: s <= 64, or (float) s a multiple of 32 up to 512 for the tensor-core tiles");
     const int64_t M0 = C.red_rows + (C.damp ? s : 0);
     if (M0 < s) return fail(ctx, QRKIT_EINVAL, "reduced shared block has fewer rows than columns");
     C.tile_rows = 256;
-    std::vector<int64_t> Ms;
-    int64_t M = M0;
-    while (true) {
-      Ms.push_back(M);
-      const int64_t tiles = (M + C.tile_rows - 1) / C.tile_rows;
-      if (tiles <= 1) break;
-      const int64_t last = M - (tiles - 1) * C.tile_rows;
-      M = (tiles - 1) * s + std::min<int64_t>(last, s);
-    }
-    if (C.levels.size() != Ms.size()) {
-      for (auto& L : C.levels) { release(L.X); release(L.tau); release(L.rhs); }
-      C.levels.assign(Ms.size(), TsqrLevel());
-    }
-    for (size_t l = 0; l < Ms.size(); ++l) {
-      TsqrLevel& L = C.levels[l];
-      L.M = Ms[l];
-      L.tiles = (L.M + C.tile_rows - 1) / C.tile_rows;
-      if ((rc = ensure(ctx, L.X, (size_t)L.M * s * elem, "reduced block")) != QRKIT_OK) return rc;
-      if ((rc = ensure(ctx, L.tau, (size_t)L.tiles * s * elem, "reduced tau")) != QRKIT_OK) return rc;
-      if ((rc = ensure(ctx, L.rhs, (size_t)L.M * elem, "reduced rhs")) != QRKIT_OK) return rc;
+    // the TSQR levels of a panel of pw columns over M rows, w columns wide (panel + trailing);
+    // each level's leading dimension is padded to 16 bytes, and the rows that leave a panel
+    // (all but its R rows) are laid out level by level, tile by tile, for the next panel
+    auto build_levels = [&](std::vector<TsqrLevel>& LV, int64_t M, int pw, int w, bool need_T) -> qrkit_status {
+      std::vector<int64_t> Ms;
+      while (true) {
+        Ms.push_back(M);
+        const int64_t tiles = (M + C.tile_rows - 1) / C.tile_rows;
+        if (tiles <= 1) break;
+        const int64_t last = M - (tiles - 1) * C.tile_rows;
+        M = (tiles - 1) * pw + std::min<int64_t>(last, pw);
+      }
+      if (LV.size() != Ms.size()) {
+        release_levels(LV);
+        LV.assign(Ms.size(), TsqrLevel());
+      }
+      int64_t down = 0;
+      qrkit_status rc2;
+      for (size_t l = 0; l < Ms.size(); ++l) {
+        TsqrLevel& L = LV[l];
+        L.M = Ms[l];
+        L.ld = (L.M + 3) & ~int64_t(3);
+        L.tiles = (L.M + C.tile_rows - 1) / C.tile_rows;
+        L.down0 = down;
+        down += L.M - (l + 1 < Ms.size() ? Ms[l + 1] : (int64_t)pw);
+        if ((rc2 = ensure(ctx, L.X, (size_t)L.ld * w * elem, "reduced block")) != QRKIT_OK) return rc2;
+        if ((rc2 = ensure(ctx, L.tau, (size_t)L.tiles * pw * elem, "reduced tau")) != QRKIT_OK) return rc2;
+        if ((rc2 = ensure(ctx, L.rhs, (size_t)L.ld * elem, "reduced rhs")) != QRKIT_OK) return rc2;
+        if (need_T && (rc2 = ensure(ctx, L.T, (size_t)L.tiles * pw * 32 * elem, "reduced T")) != QRKIT_OK)
+          return rc2;
+      }
+      return QRKIT_OK;
+    };
+    C.panel0_w = panels ? kPanelCols : s;
+    if ((rc = build_levels(C.levels, M0, C.panel0_w, s, panels)) != QRKIT_OK) return rc;
+    if (panels) {
+      const int np = (s + kPanelCols - 1) / kPanelCols;
+      if ((int)C.panels.size() != np - 1) {
+        for (auto& Pn : C.panels) release_levels(Pn.levels);
+        C.panels.assign(np - 1, TsqrPanel());
+      }
+      for (int j = 1; j < np; ++j) {
+        TsqrPanel& Pn = C.panels[j - 1];
+        Pn.c0 = j * kPanelCols;
+        Pn.pw = std::min(kPanelCols, s - Pn.c0);
+        Pn.w = s - Pn.c0;
+        if ((rc = build_levels(Pn.levels, M0 - Pn.c0, Pn.pw, Pn.w, j + 1 < np)) != QRKIT_OK) return rc;
+      }
+      if ((rc = ensure(ctx, C.Rs, (size_t)s * s * elem, "R_S")) != QRKIT_OK) return rc;
+      if ((rc = ensure(ctx, C.cs, (size_t)s * elem, "R_S rhs")) != QRKIT_OK) return rc;
+    } else {
+      for (auto& Pn : C.panels) release_levels(Pn.levels);
+      C.panels.clear();
     }
   } else {
-    for (auto& L : C.levels) { release(L.X); release(L.tau); release(L.rhs); }
-    C.levels.clear();
+    release_levels(C.levels);
+    for (auto& Pn : C.panels) release_levels(Pn.levels);
+    C.panels.clear();
   }
   return QRKIT_OK;
 }
@@ -1626,8 +1732,10 @@ static qrkit_status solve_r_typed(qrkit_ctx* ctx, const void* qtb, void* p) {
   T* x = (T*)p;
   if (V.coupled == QRKIT_COUPLED_DENSE) {
     const TsqrLevel& top = C.levels.back();
+    const bool pan = !C.panels.empty();
     LAUNCH(ctx, dense_backsub_kernel<T><<<1, 32, (size_t)s * sizeof(T), st>>>(
-                    (const T*)top.X.ptr, top.M, s, c + P.cols, x + P.cols, 0, ctx->d_status));
+                    pan ? (const T*)C.Rs.ptr : (const T*)top.X.ptr, pan ? s : top.ld, s, c + P.cols, x + P.cols, 0,
+                    ctx->d_status));
   }
   LAUNCH(ctx, block_backsub_kernel<T><<<blocks_for(P.K, 64), 64, 0, st>>>(V, O, c, s ? x + P.cols : nullptr, x, 0));
   return QRKIT_OK;
@@ -1679,12 +1787,14 @@ qrkit_status composed_reduced_r(qrkit_ctx* ctx, void* R) {
   Composed& C = ctx->comp;
   const int s = (int)ctx->plan.s.shared_cols;
   const TsqrLevel& top = C.levels.back();
+  const void* src = C.panels.empty() ? top.X.ptr : C.Rs.ptr;
+  const int64_t ld = C.panels.empty() ? top.ld : s;
   if (ctx->precision == QRKIT_FP64)
     LAUNCH(ctx, copy_upper_kernel<double><<<blocks_for((int64_t)s * s, 256), 256, 0, ctx->stream>>>(
-                    (const double*)top.X.ptr, top.M, s, (double*)R));
+                    (const double*)src, ld, s, (double*)R));
   else
     LAUNCH(ctx, copy_upper_kernel<float><<<blocks_for((int64_t)s * s, 256), 256, 0, ctx->stream>>>(
-                    (const float*)top.X.ptr, top.M, s, (float*)R));
+                    (const float*)src, ld, s, (float*)R));
   return QRKIT_OK;
 }
 

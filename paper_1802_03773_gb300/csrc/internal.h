@@ -158,8 +158,19 @@ struct Band {
 
 struct TsqrLevel {
   int64_t M = 0;      // rows of the level matrix
+  int64_t ld = 0;     // its leading dimension: M rounded up to a multiple of 4 (16-byte columns)
   int64_t tiles = 0;
+  int64_t down0 = 0;  // column panels: first row of this level's retired rows in the next panel
   DevBuf X, tau, rhs;
+  DevBuf T;           // column panels: the tiles' compact-WY T factors (32 x 32 per 32 columns)
+};
+
+// One column panel of a dense reduced block wider than one tile: columns [c0, c0 + pw) are
+// factored by TSQR over the rows the earlier panels left, and the panel's Q^T is applied to
+// the w - pw columns after it.
+struct TsqrPanel {
+  int c0 = 0, pw = 0, w = 0;
+  std::vector<TsqrLevel> levels;
 };
 
 // Device state of the composed factorization.
@@ -182,7 +193,10 @@ struct Composed {
   // normal-equations (Cholesky) comparison path
   DevBuf nrm_D, nrm_L, nrm_W, nrm_y, nrm_As, nrm_rs, nrm_seg;
   DevBuf d_aug_off_d, d_aug_off_u, d_red_off_d, d_red_off_u;
-  std::vector<TsqrLevel> levels;
+  std::vector<TsqrLevel> levels;   // TSQR levels of the first (or only) column panel
+  std::vector<TsqrPanel> panels;   // s > 128: the column panels after the first
+  int panel0_w = 0;                // columns of the first panel's factor (s, or 128 with panels)
+  DevBuf Rs, cs;                   // with panels: R_S (s x s, column-major) and its rhs
   DevBuf dense_ws;                 // qrkit_dense_lstsq: the copied matrix and rhs
   const void* J = nullptr;         // caller's values recorded at factor time
   const void* S = nullptr;
@@ -304,9 +318,19 @@ qrkit_status reduced_row_sort(qrkit_ctx* ctx, const RowSortTables& t, int64_t ns
                               int64_t* order, int64_t* Xstart_s, void* Xw_s);
 qrkit_status window_start_copy(qrkit_ctx* ctx, const int32_t* in);
 // TSQR tile factor with tcgen05 trailing updates (float, 256-row tiles, 64 < s <= 128, s % 32 == 0).
+// Tout (optional): each tile's T factors, (s / 32) blocks of 32 x 32 per tile.
 bool tsqr_tc_supported(int s, int tile_rows);
 qrkit_status tsqr_tile_tc(qrkit_ctx* ctx, float* X, int64_t ld, int64_t M, int s, float* taus, float* Xn,
-                          int64_t ldn, int64_t tiles);
+                          int64_t ldn, int64_t tiles, float* Tout = nullptr);
+// Column-panel TSQR (float): the Q^T of every 256-row tile of a factored 128-column panel
+// (reflectors in X's first pw columns, T factors from tsqr_tile_tc) applied to the n trailing
+// columns X[:, pw .. pw + n); the tile's top pw rows go to `up` (row tile * pw), the rest to
+// `down` (row down0 + tile * (256 - pw)).  ld, ldu and ldd are multiples of 4.
+qrkit_status tsqr_panel_apply(qrkit_ctx* ctx, const float* X, int64_t ld, int64_t M, int pw, const float* T,
+                              int n, float* up, int64_t ldu, float* down, int64_t ldd, int64_t down0,
+                              int64_t tiles);
+constexpr int kPanelCols = 128;   // column panel width of a dense reduced block wider than that
+constexpr int kMaxDenseS = 512;   // widest dense reduced block (float, column panels)
 qrkit_status reduced_rhs_sort(qrkit_ctx* ctx, const int64_t* spos, const void* rhs, void* rhs_s, int64_t rows);
 void release_band(Band& B);
 qrkit_status launch_block_solve(qrkit_ctx* ctx, const void* J, const void* b, const void* D,

@@ -19,6 +19,7 @@
 #include <math.h>
 #include <stdint.h>
 
+#include "device_util.cuh"
 #include "internal.h"
 
 namespace qrkit {
@@ -107,8 +108,27 @@ __device__ __forceinline__ void tc_record(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
 
+// Rows [r0, r0 + r) of `cols` columns of a column-major matrix (ld a multiple of 4, 16-byte
+// aligned base) into shared memory at a column stride of kRows, by bulk copies (TMA) on one
+// mbarrier; issued by one thread.  Each copy takes the rows rounded up to a multiple of 4 (inside
+// the padded column), so the caller zeroes rows r .. kRows - 1 after the wait.
+__device__ __forceinline__ uint32_t column_bytes(int r) { return (uint32_t)((r + 3) & ~3) * 4u; }
+__device__ __forceinline__ void stage_columns(float* dst, const float* src, int64_t ld, int64_t r0, int r,
+                                              int cols, uint64_t* bar) {
+  const uint32_t cb = column_bytes(r);
+  for (int c = 0; c < cols; ++c) dev::bulk_g2s(dst + (size_t)c * kRows, src + (int64_t)c * ld + r0, cb, bar);
+}
+
+// Bounded wait for the mbarrier's phase `parity`; false if the limit ran out.
+__device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity) {
+  for (uint32_t it = 0; it < kWaitLimit; ++it)
+    if (dev::mbar_try_wait(bar, parity)) return true;
+  return false;
+}
+
 __global__ void __launch_bounds__(kThr, 1)
-tsqr_tile_tc_kernel(float* X, int64_t ld, int64_t M, int s, float* taus, float* Xn, int64_t ldn, int* status) {
+tsqr_tile_tc_kernel(float* X, int64_t ld, int64_t M, int s, float* taus, float* Xn, int64_t ldn, float* Tout,
+                    int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float* A = reinterpret_cast<float*>(smem_raw);                       // 256 x s, column-major
   unsigned char* Yhi = smem_raw + (size_t)kRows * s * 4;               // 256 x 32 operand
@@ -121,12 +141,15 @@ tsqr_tile_tc_kernel(float* X, int64_t ld, int64_t M, int s, float* taus, float* 
   __shared__ float tau_s[kNb];
   __shared__ uint32_t tmem_slot;
   __shared__ __align__(8) uint64_t mbar;
+  __shared__ __align__(8) uint64_t mbar_ld;
   __shared__ int abort_s;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t r0 = (int64_t)blockIdx.x * kRows;
   const int r = (int)(M - r0 < (int64_t)kRows ? M - r0 : (int64_t)kRows);
   const int kmax = r < s ? r : s;
+  // the tile's columns by bulk copies when every column starts on a 16-byte boundary
+  const bool bulk = (ld & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
 
   if (warp == 0) {
     asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
@@ -135,18 +158,40 @@ tsqr_tile_tc_kernel(float* X, int64_t ld, int64_t M, int s, float* taus, float* 
   }
   if (tid == 0) {
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar_ld)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
     abort_s = 0;
+    if (bulk) {
+      dev::mbar_expect_tx(&mbar_ld, column_bytes(r) * (uint32_t)s);
+      stage_columns(A, X, ld, r0, r, s, &mbar_ld);
+    }
   }
-  for (int e = tid; e < kRows * s; e += kThr) {
-    const int c = e / kRows, i = e % kRows;
-    A[e] = i < r ? X[(int64_t)c * ld + r0 + i] : 0.f;
-  }
+  if (!bulk)
+    for (int e = tid; e < kRows * s; e += kThr) {
+      const int c = e / kRows, i = e % kRows;
+      A[e] = i < r ? X[(int64_t)c * ld + r0 + i] : 0.f;
+    }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
   asm volatile("tcgen05.fence::after_thread_sync;");
   const uint32_t tmem = tmem_slot;
   uint32_t phase = 0;
+  if (bulk) {
+    const bool ok = wait_phase(&mbar_ld, 0u);
+    if (__syncthreads_or(!ok)) {
+      // the copies may still be in flight: one more bounded wait before the CTA exits
+      if (tid == 0) tc_record(status, QRKIT_ETIMEOUT);
+      wait_phase(&mbar_ld, 0u);
+      __syncthreads();
+      if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
+      return;
+    }
+    for (int e = tid; e < (kRows - r) * s; e += kThr) {   // rows past the tile's end
+      const int c = e / (kRows - r), i = r + e % (kRows - r);
+      A[c * kRows + i] = 0.f;
+    }
+    __syncthreads();
+  }
 
   for (int p0 = 0; p0 < kmax; p0 += kNb) {
     const int kend = p0 + kNb < kmax ? p0 + kNb : kmax;
@@ -240,7 +285,7 @@ tsqr_tile_tc_kernel(float* X, int64_t ld, int64_t M, int s, float* taus, float* 
     }
     __syncthreads();
     const int n = s - pend;   // trailing columns
-    if (n <= 0) break;
+    if (n <= 0 && !Tout) break;
     const int nk = kend - p0;
     // Y (256 x 32): Y[i][l] = 1 at i = p0 + l, the stored v below, 0 above (and 0 for l >= nk)
     auto yval = [&](int i, int l) -> float {
@@ -295,6 +340,10 @@ tsqr_tile_tc_kernel(float* X, int64_t ld, int64_t M, int s, float* taus, float* 
       }
     }
     __syncthreads();
+    if (Tout)
+      for (int e = tid; e < kNb * kNb; e += kThr)
+        Tout[((int64_t)blockIdx.x * (s / kNb) + p0 / kNb) * (kNb * kNb) + e] = Tm[e];
+    if (n <= 0) break;
     // 3. W = Y^T C (32 x n, row-major; one warp per trailing column, lanes over rows, the 32
     // sums of a column reduced together), then Z = T^T W
     for (int j = warp; j < n; j += kThr / 32) {
@@ -424,6 +473,203 @@ tsqr_tile_tc_kernel(float* X, int64_t ld, int64_t M, int s, float* taus, float* 
   }
 }
 
+// ---- Column-panel TSQR: a factored panel's tile reflectors applied to the columns after it ----
+//
+// One CTA takes one 256-row tile of a TSQR level and kCw of the trailing columns C (staged by
+// bulk copies).  For each group of 32 reflectors of the tile's panel (Y, with the tile kernel's T),
+// Q_group^T C = C - Y (T^T (Y^T C)): W = Y^T C and Z = T^T W on the CUDA cores, C -= Y Z on the
+// tensor cores (kind::tf32, 3xTF32, FP32 accumulation in TMEM), as in the tile kernel.  The
+// transformed tile's top rows (R rows of the panel) go up to the next level, the others down to
+// the next panel.
+constexpr int kCw = 64;   // trailing columns per CTA
+
+size_t panel_apply_smem() {
+  return (size_t)kRows * kCw * 4 + (size_t)kRows * kNb * 4 + 2 * (size_t)kRows * kNb * 4 + 2 * (size_t)kCw * kNb * 4 +
+         (size_t)kNb * kNb * 4 + (size_t)kNb * kCw * 4;
+}
+
+__global__ void __launch_bounds__(kThr, 1)
+tsqr_panel_apply_kernel(const float* X, int64_t ld, int64_t M, int pw, const float* Tin, int n, float* up,
+                        int64_t ldu, float* down, int64_t ldd, int64_t down0, int* status) {
+  extern __shared__ __align__(1024) unsigned char smem_raw[];
+  float* Cs = reinterpret_cast<float*>(smem_raw);                          // 256 x kCw, column-major
+  float* Yf = Cs + kRows * kCw;                                            // 256 x 32, column-major
+  unsigned char* Yhi = reinterpret_cast<unsigned char*>(Yf + kRows * kNb);  // 256 x 32 operand
+  unsigned char* Ylo = Yhi + kRows * kNb * 4;
+  unsigned char* Zhi = Ylo + kRows * kNb * 4;                              // kCw x 32 operand
+  unsigned char* Zlo = Zhi + kCw * kNb * 4;
+  float* Tm = reinterpret_cast<float*>(Zlo + kCw * kNb * 4);               // 32 x 32 (row l, col k)
+  float* W = Tm + kNb * kNb;                                               // 32 x kCw, row-major
+  __shared__ uint32_t tmem_slot;
+  __shared__ __align__(8) uint64_t mbar_ld, mbar_mma;
+  __shared__ int abort_s;
+
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int64_t tile = blockIdx.x;
+  const int64_t r0 = tile * kRows;
+  const int r = (int)(M - r0 < (int64_t)kRows ? M - r0 : (int64_t)kRows);
+  const int kmax = r < pw ? r : pw;
+  const int j0 = blockIdx.y * kCw;
+  const int nc = n - j0 < kCw ? n - j0 : kCw;   // a multiple of 32
+  const float* Cg = X + (int64_t)(pw + j0) * ld;
+
+  if (warp == 0) {
+    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
+                 "r"(2 * kCw));
+    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
+  }
+  if (tid == 0) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar_ld)), "r"(1));
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar_mma)), "r"(1));
+    asm volatile("fence.mbarrier_init.release.cluster;");
+    abort_s = 0;
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  asm volatile("tcgen05.fence::after_thread_sync;");
+  const uint32_t tmem = tmem_slot;
+  uint32_t ph_ld = 0, ph_mma = 0;
+  int pending = 0;   // 1: a bulk load, 2: the MMAs still outstanding after a timeout
+
+  for (int p0 = 0; p0 < kmax; p0 += kNb) {
+    const int nk = kmax - p0 < kNb ? kmax - p0 : kNb;
+    // (a) Y of this group of reflectors (and, the first time, the tile's trailing columns)
+    dev::fence_proxy_async();
+    __syncthreads();   // every earlier read of Yf and Cs is done
+    if (tid == 0) {
+      dev::mbar_expect_tx(&mbar_ld, column_bytes(r) * (uint32_t)(nk + (p0 == 0 ? nc : 0)));
+      stage_columns(Yf, X + (int64_t)p0 * ld, ld, r0, r, nk, &mbar_ld);
+      if (p0 == 0) stage_columns(Cs, Cg, ld, r0, r, nc, &mbar_ld);
+    }
+    for (int e = tid; e < kNb * kNb; e += kThr) Tm[e] = Tin[(tile * (pw / kNb) + p0 / kNb) * (kNb * kNb) + e];
+    const bool ok = wait_phase(&mbar_ld, ph_ld);
+    ph_ld ^= 1u;
+    if (__syncthreads_or(!ok)) {
+      pending = 1;
+      break;
+    }
+    // Y[i][l]: 1 at i = p0 + l, the stored v below, 0 above, past the tile and for l >= nk
+    for (int e = tid; e < kRows * kNb; e += kThr) {
+      const int l = e / kRows, i = e % kRows, d = p0 + l;
+      if (l >= nk || i <= d || i >= r) Yf[e] = (l < nk && i == d) ? 1.f : 0.f;
+    }
+    if (p0 == 0)
+      for (int e = tid; e < (kRows - r) * nc; e += kThr) {
+        const int c = e / (kRows - r), i = r + e % (kRows - r);
+        Cs[c * kRows + i] = 0.f;
+      }
+    __syncthreads();
+    // (b) W = Y^T C (32 x nc): a warp per column, lanes over rows p0.., the 32 sums reduced together
+    for (int j = warp; j < nc; j += kThr / 32) {
+      float acc[32];
+#pragma unroll
+      for (int l = 0; l < 32; ++l) acc[l] = 0.f;
+      const float* x = Cs + j * kRows;
+      for (int i = p0 + lane; i < kRows; i += 32) {
+        const float xv = x[i];
+#pragma unroll
+        for (int l = 0; l < kNb; ++l) acc[l] += Yf[l * kRows + i] * xv;
+      }
+      W[lane * kCw + j] = transpose_reduce(acc, lane);
+    }
+    __syncthreads();
+    // (c) Z = T^T W in place (row i of Z from rows l <= i of W)
+    for (int j = tid; j < nc; j += kThr)
+      for (int i = kNb - 1; i >= 0; --i) {
+        float z = 0.f;
+        for (int l = 0; l <= i; ++l) z += Tm[l * kNb + i] * W[l * kCw + j];
+        W[i * kCw + j] = z;
+      }
+    __syncthreads();
+    // (d) operands: Z (nc x 32, K-major) and Y (256 x 32), each split into TF32 hi + lo
+    for (int e = tid; e < kNb * nc; e += kThr) {
+      const int i = e / nc, j = e % nc;
+      const float v = W[i * kCw + j], h = to_tf32(v);
+      *reinterpret_cast<float*>(Zhi + koff(j, i)) = h;
+      *reinterpret_cast<float*>(Zlo + koff(j, i)) = to_tf32(v - h);
+    }
+    for (int e = tid; e < kRows * kNb; e += kThr) {
+      const int l = e / kRows, i = e % kRows;
+      const float v = Yf[e], h = to_tf32(v);
+      const uint32_t o = (uint32_t)(i >> 7) * (128 * kNb * 4) + koff(i & 127, l);
+      *reinterpret_cast<float*>(Yhi + o) = h;
+      *reinterpret_cast<float*>(Ylo + o) = to_tf32(v - h);
+    }
+    asm volatile("fence.proxy.async.shared::cta;");
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    // (e) D_h = Y_h Z for the two 128-row halves (3 products each: hi hi, hi lo, lo hi)
+    if (tid == 0) {
+      const uint32_t id = idesc_tf32(128, nc);
+      for (int h = 0; h < 2; ++h) {
+        const uint32_t yo = (uint32_t)h * (128 * kNb * 4);
+        int first = 1;
+        for (int ks = 0; ks < kNb / 8; ++ks) {
+          const uint32_t ko = (uint32_t)ks * 256;
+          for (int sp = 0; sp < 3; ++sp) {
+            const unsigned char* ya = sp == 2 ? Ylo : Yhi;
+            const unsigned char* zb = sp == 1 ? Zlo : Zhi;
+            const uint64_t ad = smem_desc(su32(ya) + yo + ko), bd = smem_desc(su32(zb) + ko);
+            const uint32_t acc = first ? 0u : 1u;
+            asm volatile(
+                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
+                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)(h * kCw)),
+                "l"(ad), "l"(bd), "r"(id), "r"(acc));
+            first = 0;
+          }
+        }
+      }
+      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
+          su32(&mbar_mma)));
+    }
+    const bool mma_ok = wait_phase(&mbar_mma, ph_mma);
+    ph_mma ^= 1u;
+    asm volatile("tcgen05.fence::after_thread_sync;");
+    if (__syncthreads_or(!mma_ok)) {
+      pending = 2;
+      break;
+    }
+    // (f) C -= D: warp w reads TMEM lanes 32 (w % 4) .. of half (w / 4) % 2, 8-column groups
+    // (w / 8), (w / 8) + 2, ...
+    {
+      const int qd = warp & 3, h = (warp >> 2) & 1, part = warp >> 3;
+      const int row = h * 128 + qd * 32 + lane;
+      for (int c0 = part * 8; c0 < nc; c0 += 8 * (kThr / 256)) {
+        uint32_t v[8];
+        const uint32_t ta = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(h * kCw + c0);
+        asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
+                     : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
+                       "=r"(v[7])
+                     : "r"(ta));
+        asm volatile("tcgen05.wait::ld.sync.aligned;");
+#pragma unroll
+        for (int j = 0; j < 8; ++j) Cs[(c0 + j) * kRows + row] -= __uint_as_float(v[j]);
+      }
+    }
+    asm volatile("tcgen05.fence::before_thread_sync;");
+    __syncthreads();
+  }
+  if (pending) {
+    if (tid == 0) tc_record(status, QRKIT_ETIMEOUT);
+    // what timed out may still be running: wait once more (bounded) before TMEM and shared
+    // memory are given up
+    if (pending == 1) wait_phase(&mbar_ld, ph_ld ^ 1u);
+    else wait_phase(&mbar_mma, ph_mma ^ 1u);
+  }
+  asm volatile("tcgen05.fence::before_thread_sync;");
+  __syncthreads();
+  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(2 * kCw));
+  if (pending) return;
+  // the tile's top kmax rows up (the next level, or R_S), the others down (the next panel)
+  for (int e = tid; e < r * nc; e += kThr) {
+    const int c = e / r, i = e % r;
+    const float v = Cs[c * kRows + i];
+    if (i < kmax) up[(int64_t)(j0 + c) * ldu + tile * pw + i] = v;
+    else down[(int64_t)(j0 + c) * ldd + down0 + tile * (kRows - pw) + (i - kmax)] = v;
+  }
+}
+
 }  // namespace
 
 size_t tsqr_tc_smem(int s) {
@@ -436,7 +682,7 @@ bool tsqr_tc_supported(int s, int tile_rows) {
 }
 
 qrkit_status tsqr_tile_tc(qrkit_ctx* ctx, float* X, int64_t ld, int64_t M, int s, float* taus, float* Xn,
-                          int64_t ldn, int64_t tiles) {
+                          int64_t ldn, int64_t tiles, float* Tout) {
   const size_t smem = tsqr_tc_smem(s);
   if (smem > ctx->max_smem_optin)
     return fail(ctx, QRKIT_EUNSUPPORTED, "not enough shared memory for the tensor-core tile kernel");
@@ -445,7 +691,31 @@ qrkit_status tsqr_tile_tc(qrkit_ctx* ctx, float* X, int64_t ld, int64_t M, int s
                                              (int)smem));
     ctx->smem_attr[7] = smem;
   }
-  tsqr_tile_tc_kernel<<<(unsigned)tiles, kThr, smem, ctx->stream>>>(X, ld, M, s, taus, Xn, ldn, ctx->d_status);
+  tsqr_tile_tc_kernel<<<(unsigned)tiles, kThr, smem, ctx->stream>>>(X, ld, M, s, taus, Xn, ldn, Tout,
+                                                                    ctx->d_status);
+  ctx->launches += 1;
+  QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+  return QRKIT_OK;
+}
+
+qrkit_status tsqr_panel_apply(qrkit_ctx* ctx, const float* X, int64_t ld, int64_t M, int pw, const float* T,
+                              int n, float* up, int64_t ldu, float* down, int64_t ldd, int64_t down0,
+                              int64_t tiles) {
+  if (n <= 0 || tiles <= 0) return QRKIT_OK;
+  if ((ld & 3) != 0 || (reinterpret_cast<uintptr_t>(X) & 15) != 0 || pw % kNb != 0 || n % kNb != 0 ||
+      pw > kRows / 2)
+    return fail(ctx, QRKIT_EINVAL, "column-panel TSQR: unaligned level matrix or panel shape");
+  const size_t smem = panel_apply_smem();
+  if (smem > ctx->max_smem_optin)
+    return fail(ctx, QRKIT_EUNSUPPORTED, "not enough shared memory for the column-panel TSQR kernel");
+  if (ctx->smem_attr[15] < smem) {
+    QRKIT_CUDA_TRY(ctx, cudaFuncSetAttribute(tsqr_panel_apply_kernel,
+                                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
+    ctx->smem_attr[15] = smem;
+  }
+  const dim3 grid((unsigned)tiles, (unsigned)((n + kCw - 1) / kCw));
+  tsqr_panel_apply_kernel<<<grid, kThr, smem, ctx->stream>>>(X, ld, M, pw, T, n, up, ldu, down, ldd, down0,
+                                                             ctx->d_status);
   ctx->launches += 1;
   QRKIT_CUDA_TRY(ctx, cudaGetLastError());
   return QRKIT_OK;

@@ -126,6 +126,42 @@ def test_dense_tensor_core_tiles_fp32_refined(s, K):
     assert_close(out0["p"], p_ref, 1e-3)
 
 
+@pytest.mark.parametrize("s,K", [(160, 400), (224, 300), (256, 1029), (512, 700)])
+def test_dense_column_panels_fp32_refined(s, K):
+    """Shared blocks wider than one tile (Sec. 2, blocked Householder by column panels): each
+    128-column panel is a TSQR over the rows the earlier panels left, its tiles' Q^T applied to
+    the trailing columns on the tensor cores; a last panel of 96 columns uses the tensor-core
+    tile, one of 32 the CUDA-core tile.  Several levels and ragged tiles per panel.  The refined
+    float solution within 1e-5 of the float64 oracle of the float-rounded problem, plain float
+    within 1e-3, and R_S^T R_S (free of the rows' signs) within 1e-5 of the oracle's."""
+    torch = cuda_or_skip()
+    from paper_1802_03773_gb300 import Context, qrkit
+    d = block_angular_dense(K=K, n=4, m=2, s=s, scale_decades=2.0, seed_offset=s + 1)
+    d32 = dict(d)
+    d32["blocks"] = np.asarray(d["blocks"], np.float32).astype(np.float64)
+    d32["S"] = np.asarray(d["S"], np.float32).astype(np.float64)
+    d32["b"] = np.asarray(d["b"], np.float32).astype(np.float64)
+    p_ref, F = st.factor_and_solve(problem_from(d32))
+    out = run(d32, "fp32_refined", refine_steps=2)
+    assert_close(out["p"], p_ref, 1e-5)
+    out0 = run(d32, "fp32", refine_steps=0)
+    assert_close(out0["p"], p_ref, 1e-3)
+    # the reduced R itself
+    ctx = Context(0, precision="fp32_refined")
+    J, S, _ = packed(d32, np.float32)
+    ctx.plan_blocks(np.full(K, 4), np.full(K, 2), qrkit.COUPLED_DENSE, shared_cols=s)
+    ctx.factor(torch.from_numpy(J).cuda(), torch.from_numpy(S).cuda(), None, d["lam"])
+    R = torch.empty(s * s, device="cuda", dtype=torch.float32)
+    ctx.reduced_r(R)
+    ctx.sync_status()
+    ctx.close()
+    Rg = R.cpu().numpy().astype(np.float64).reshape(s, s).T   # column-major
+    Rr = F.reduced_factor.R[:s, :s]
+    assert np.allclose(np.tril(Rg, -1), 0.0)
+    G, Gr = Rg.T @ Rg, Rr.T @ Rr
+    assert np.abs(G - Gr).max() <= 1e-5 * np.abs(Gr).max()
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_refined", 1e-5)])
 def test_dense_hcat_solve_replays_in_cuda_graph(precision, tol):
     """factor + solve of the 200-block workload, captured once in a CUDA graph after a warm-up
