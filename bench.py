@@ -464,6 +464,40 @@ def other_workloads(dev, stream, only=None):
             "reduced_block_tflops_useful": flops / (tf * 1e-3) / 1e12}
         ctx.close()
         del J, S, b
+    if want("dense_wide") or only == "dense_wide_small":
+        # the reduced block wider than one tile: s = 256 and 512 by 128-column panels, each a TSQR
+        # whose tiles' Q^T reaches the later columns through the tensor cores (tcgen05, 3xTF32).
+        # "dense_wide_small" (20,000 blocks, s = 512, asked for by name only) is the profiling case.
+        small = only == "dense_wide_small"
+        for s in ((512,) if small else (256, 512)):
+            K = 20_000 if small else 100_000
+            d = block_angular_dense(K=K, n=4, m=2, s=s, scale_decades=2.0, dtype=np.float32)
+            n, m = d["n"], d["m"]
+            ctx = Context(dev.index, stream=stream, precision="fp32_refined")
+            ctx.plan_blocks(np.full(K, n), np.full(K, m), qrkit.COUPLED_DENSE, shared_cols=s)
+            J = torch.from_numpy(np.concatenate([d["blocks"][i].T.reshape(-1) for i in range(K)])).to(dev)
+            S = torch.from_numpy(np.asarray(d["S"]).T.reshape(-1).copy()).to(dev)
+            b = torch.from_numpy(np.asarray(d["b"])).to(dev)
+            pl = torch.empty(K * m + s, dtype=torch.float32, device=dev)
+            del d
+            torch.cuda.synchronize()
+            tf = _time(stream, lambda: ctx.factor(J, S, None, 1e-2), 2 if small else 5)
+            ts = _time(stream, lambda: ctx.solve(b, pl, refine_steps=1), 2 if small else 5)
+            ctx.sync_status()
+            l0 = ctx.launch_count
+            with torch.cuda.stream(stream):
+                ctx.factor(J, S, None, 1e-2)
+            launches = ctx.launch_count - l0
+            Mred = K * n + s
+            flops = 2.0 * Mred * s * s - 2.0 * s ** 3 / 3.0   # Householder QR of the Mred x s reduced block
+            out[f"dense_wide_{K // 1000}k_blocks_s{s}_fp32_refined"] = {
+                "workload": f"J = [blkdiag({K:,} blocks 4x2) | S {K * n:,} x {s}], lambda 1e-2, D = norms; reduced "
+                            f"block by {(s + 127) // 128} column panels of 128 (TSQR each, tcgen05 3xTF32 updates)",
+                "ms_factor": tf, "ms_solve_refined_1": ts, "value": 1000.0 / (tf + ts), "unit": "solves/s",
+                "reduced_block_tflops_useful": flops / (tf * 1e-3) / 1e12, "launches_per_factor": launches}
+            ctx.close()
+            del J, S, b
+            torch.cuda.empty_cache()
     if want("ba_"):
         # BA-shaped system (bundle adjustment, Sec. 6.2): 100,000 points, each seen by 2-6 of 14
         # cameras (9 parameters each, 126 columns padded to 128: the tensor-core tiles), damped

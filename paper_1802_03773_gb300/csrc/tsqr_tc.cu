@@ -480,12 +480,15 @@ tsqr_tile_tc_kernel(float* X, int64_t ld, int64_t M, int s, float* taus, float* 
 // Q_group^T C = C - Y (T^T (Y^T C)): W = Y^T C and Z = T^T W on the CUDA cores, C -= Y Z on the
 // tensor cores (kind::tf32, 3xTF32, FP32 accumulation in TMEM), as in the tile kernel.  The
 // transformed tile's top rows (R rows of the panel) go up to the next level, the others down to
-// the next panel.
+// the next panel.  Y arrives column by column in the space of its low operand half and is kept
+// row-major (rows padded to kYr floats), so that a lane reads four reflectors of its row in one
+// 16-byte load.
 constexpr int kCw = 64;   // trailing columns per CTA
+constexpr int kYr = 36;   // row stride of the row-major Y: 16-byte rows, conflict-free quarter warps
 
 size_t panel_apply_smem() {
-  return (size_t)kRows * kCw * 4 + (size_t)kRows * kNb * 4 + 2 * (size_t)kRows * kNb * 4 + 2 * (size_t)kCw * kNb * 4 +
-         (size_t)kNb * kNb * 4 + (size_t)kNb * kCw * 4;
+  return (size_t)kRows * kCw * 4 + (size_t)kRows * kYr * 4 + 2 * (size_t)kRows * kNb * 4 +
+         2 * (size_t)kCw * kNb * 4 + (size_t)kNb * kNb * 4 + (size_t)kNb * kCw * 4;
 }
 
 __global__ void __launch_bounds__(kThr, 1)
@@ -493,9 +496,10 @@ tsqr_panel_apply_kernel(const float* X, int64_t ld, int64_t M, int pw, const flo
                         int64_t ldu, float* down, int64_t ldd, int64_t down0, int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
   float* Cs = reinterpret_cast<float*>(smem_raw);                          // 256 x kCw, column-major
-  float* Yf = Cs + kRows * kCw;                                            // 256 x 32, column-major
-  unsigned char* Yhi = reinterpret_cast<unsigned char*>(Yf + kRows * kNb);  // 256 x 32 operand
+  float* Yr = Cs + kRows * kCw;                                            // 256 x 32, row-major (kYr)
+  unsigned char* Yhi = reinterpret_cast<unsigned char*>(Yr + kRows * kYr);  // 256 x 32 operand
   unsigned char* Ylo = Yhi + kRows * kNb * 4;
+  float* Yf = reinterpret_cast<float*>(Ylo);   // Y as copied (256 x 32, column-major), until Yr is formed
   unsigned char* Zhi = Ylo + kRows * kNb * 4;                              // kCw x 32 operand
   unsigned char* Zlo = Zhi + kCw * kNb * 4;
   float* Tm = reinterpret_cast<float*>(Zlo + kCw * kNb * 4);               // 32 x 32 (row l, col k)
@@ -551,7 +555,7 @@ tsqr_panel_apply_kernel(const float* X, int64_t ld, int64_t M, int pw, const flo
     // Y[i][l]: 1 at i = p0 + l, the stored v below, 0 above, past the tile and for l >= nk
     for (int e = tid; e < kRows * kNb; e += kThr) {
       const int l = e / kRows, i = e % kRows, d = p0 + l;
-      if (l >= nk || i <= d || i >= r) Yf[e] = (l < nk && i == d) ? 1.f : 0.f;
+      Yr[i * kYr + l] = (l >= nk || i < d || i >= r) ? 0.f : (i == d ? 1.f : Yf[e]);
     }
     if (p0 == 0)
       for (int e = tid; e < (kRows - r) * nc; e += kThr) {
@@ -559,18 +563,32 @@ tsqr_panel_apply_kernel(const float* X, int64_t ld, int64_t M, int pw, const flo
         Cs[c * kRows + i] = 0.f;
       }
     __syncthreads();
-    // (b) W = Y^T C (32 x nc): a warp per column, lanes over rows p0.., the 32 sums reduced together
-    for (int j = warp; j < nc; j += kThr / 32) {
-      float acc[32];
+    // (b) W = Y^T C (32 x nc): a warp per pair of columns, lanes over rows p0.., each row's 32
+    // reflector values in eight 16-byte loads; the 32 sums of a column reduced together
+    for (int j = 2 * warp; j < nc; j += 2 * (kThr / 32)) {
+      float acc0[32], acc1[32];
 #pragma unroll
-      for (int l = 0; l < 32; ++l) acc[l] = 0.f;
-      const float* x = Cs + j * kRows;
+      for (int l = 0; l < 32; ++l) acc0[l] = acc1[l] = 0.f;
+      const float* x0 = Cs + j * kRows;
+      const float* x1 = x0 + kRows;
       for (int i = p0 + lane; i < kRows; i += 32) {
-        const float xv = x[i];
+        const float c0 = x0[i], c1 = x1[i];
+        const float4* yrow = reinterpret_cast<const float4*>(Yr + i * kYr);
 #pragma unroll
-        for (int l = 0; l < kNb; ++l) acc[l] += Yf[l * kRows + i] * xv;
+        for (int q = 0; q < kNb / 4; ++q) {
+          const float4 y = yrow[q];
+          acc0[4 * q] += y.x * c0;
+          acc0[4 * q + 1] += y.y * c0;
+          acc0[4 * q + 2] += y.z * c0;
+          acc0[4 * q + 3] += y.w * c0;
+          acc1[4 * q] += y.x * c1;
+          acc1[4 * q + 1] += y.y * c1;
+          acc1[4 * q + 2] += y.z * c1;
+          acc1[4 * q + 3] += y.w * c1;
+        }
       }
-      W[lane * kCw + j] = transpose_reduce(acc, lane);
+      W[lane * kCw + j] = transpose_reduce(acc0, lane);
+      W[lane * kCw + j + 1] = transpose_reduce(acc1, lane);
     }
     __syncthreads();
     // (c) Z = T^T W in place (row i of Z from rows l <= i of W)
@@ -590,7 +608,7 @@ tsqr_panel_apply_kernel(const float* X, int64_t ld, int64_t M, int pw, const flo
     }
     for (int e = tid; e < kRows * kNb; e += kThr) {
       const int l = e / kRows, i = e % kRows;
-      const float v = Yf[e], h = to_tf32(v);
+      const float v = Yr[i * kYr + l], h = to_tf32(v);
       const uint32_t o = (uint32_t)(i >> 7) * (128 * kNb * 4) + koff(i & 127, l);
       *reinterpret_cast<float*>(Yhi + o) = h;
       *reinterpret_cast<float*>(Ylo + o) = to_tf32(v - h);
