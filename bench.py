@@ -459,13 +459,13 @@ def other_workloads(dev, stream, only=None):
         flops = 2.0 * Mred * s * s   # useful flops of the reduced block's Householder QR (leading term)
         out["dense_hcat_100k_blocks_s128_fp32_refined"] = {
             "workload": "J = [blkdiag(100,000 blocks 4x2) | S 400,000 x 128], lambda 1e-2, D = norms; "
-                        "reduced block TSQR with tcgen05 3xTF32 trailing updates",
+                        "reduced block by 4 column panels of 32 (TSQR each, tcgen05 3xTF32 updates)",
             "ms_factor": tf, "ms_solve_refined_1": ts, "value": 1000.0 / (tf + ts), "unit": "solves/s",
             "reduced_block_tflops_useful": flops / (tf * 1e-3) / 1e12}
         ctx.close()
         del J, S, b
     if want("dense_wide") or only == "dense_wide_small":
-        # the reduced block wider than one tile: s = 256 and 512 by 128-column panels, each a TSQR
+        # wider reduced blocks: s = 256 and 512 by 32-column panels, each a TSQR
         # whose tiles' Q^T reaches the later columns through the tensor cores (tcgen05, 3xTF32).
         # "dense_wide_small" (20,000 blocks, s = 512, asked for by name only) is the profiling case.
         small = only == "dense_wide_small"
@@ -492,7 +492,7 @@ def other_workloads(dev, stream, only=None):
             flops = 2.0 * Mred * s * s - 2.0 * s ** 3 / 3.0   # Householder QR of the Mred x s reduced block
             out[f"dense_wide_{K // 1000}k_blocks_s{s}_fp32_refined"] = {
                 "workload": f"J = [blkdiag({K:,} blocks 4x2) | S {K * n:,} x {s}], lambda 1e-2, D = norms; reduced "
-                            f"block by {(s + 127) // 128} column panels of 128 (TSQR each, tcgen05 3xTF32 updates)",
+                            f"block by {s // 32} column panels of 32 (TSQR each, tcgen05 3xTF32 updates)",
                 "ms_factor": tf, "ms_solve_refined_1": ts, "value": 1000.0 / (tf + ts), "unit": "solves/s",
                 "reduced_block_tflops_useful": flops / (tf * 1e-3) / 1e12, "launches_per_factor": launches}
             ctx.close()
@@ -500,7 +500,7 @@ def other_workloads(dev, stream, only=None):
             torch.cuda.empty_cache()
     if want("ba_"):
         # BA-shaped system (bundle adjustment, Sec. 6.2): 100,000 points, each seen by 2-6 of 14
-        # cameras (9 parameters each, 126 columns padded to 128: the tensor-core tiles), damped
+        # cameras (9 parameters each, 126 columns padded to 128, a multiple of the panel width), damped
         from workloads import ba_system
         d = ba_system(P=100_000, C=14, s_pad=128, dtype=np.float32)
         K, s = d["K"], d["s"]

@@ -269,10 +269,9 @@ qrkit_status qrkit_set_refinement(qrkit_ctx* ctx, double select, int residual);
  * The factor (per-block reflectors and R, R12 = Q_i^T S_i top rows, the factor of the
  * reduced shared block) is kept in the context.  J and S are read again by qrkit_solve when
  * refine_steps > 0: keep them alive and unchanged until then.  Dense S: s <= 64, or in the
- * float modes s = 96 or 128 (the reduced block's tile QR then runs its trailing updates on
- * the tensor cores, 3xTF32 with float accumulation), or a multiple of 32 up to 512 (blocked
- * by column panels of 128, Sec. 2: each panel a TSQR of its own, its Q^T applied to the later
- * columns on the tensor cores).  QRKIT_EUNSUPPORTED otherwise. */
+ * float modes any multiple of 32 up to 512 (the reduced block is then blocked by column panels
+ * of 32, Sec. 2: each panel a TSQR of its own, its Q^T applied to the later columns on the
+ * tensor cores, 3xTF32 with float accumulation).  QRKIT_EUNSUPPORTED otherwise. */
 qrkit_status qrkit_factor(qrkit_ctx* ctx, const void* J, const void* S, const void* D, double lambda);
 
 /* qtb = Q^T [b; 0] restricted to its top N entries (Sec. 5.1, matrixQ().transpose() * b),

@@ -1207,10 +1207,12 @@ static qrkit_status norms_typed(qrkit_ctx* ctx, const ComposedView<T>& V, double
   return QRKIT_OK;
 }
 
-// Column-panel TSQR of a float dense reduced block wider than one tile.  Panel j (columns
-// c0 = 128 j ..): its levels are factored tile by tile (R rows up; the top level's into R_S), and
-// after each level the tiles' Q^T is applied to the panel's trailing columns, whose rows move up
-// with the R rows or down into the next panel's first level.
+// Column-panel TSQR of a float dense reduced block (s a multiple of 32 above 32).  Panel j
+// (columns c0 = 32 j ..): its levels are factored tile by tile (R rows up; the top level's into
+// R_S), and after each level the tiles' Q^T is applied to the panel's trailing columns on the
+// tensor cores, whose rows move up with the R rows or down into the next panel's first level.
+// Narrow panels keep the column-by-column part of the work (the tile QR) small: it grows with the
+// panel width, while the trailing updates do the rest of the arithmetic.
 static qrkit_status factor_panels(qrkit_ctx* ctx, int s) {
   Composed& C = ctx->comp;
   cudaStream_t st = ctx->stream;
@@ -1227,17 +1229,9 @@ static qrkit_status factor_panels(qrkit_ctx* ctx, int s) {
       float* X = (float*)L.X.ptr;
       float* Xn = top ? Rs + (int64_t)c0 * s + c0 : (float*)LV[l + 1].X.ptr;
       const int64_t ldn = top ? s : LV[l + 1].ld;
-      qrkit_status rc;
-      if (tsqr_tc_supported(pw, C.tile_rows)) {
-        rc = tsqr_tile_tc(ctx, X, L.ld, L.M, pw, (float*)L.tau.ptr, Xn, ldn, L.tiles, n > 0 ? (float*)L.T.ptr : nullptr);
-        if (rc != QRKIT_OK) return rc;
-      } else {   // a last panel of at most 64 columns
-        const size_t smem = ((size_t)C.tile_rows * pw + 64) * sizeof(float);
-        auto k = tsqr_tile_kernel<float>;
-        QRKIT_CUDA_TRY(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
-        LAUNCH(ctx, k<<<(unsigned)L.tiles, kTileThreads, smem, st>>>(X, L.ld, L.M, pw, C.tile_rows,
-                                                                    (float*)L.tau.ptr, Xn, ldn, ctx->d_status));
-      }
+      qrkit_status rc =
+          tsqr_tile_tc(ctx, X, L.ld, L.M, pw, (float*)L.tau.ptr, Xn, ldn, L.tiles, n > 0 ? (float*)L.T.ptr : nullptr);
+      if (rc != QRKIT_OK) return rc;
       if (n > 0) {
         float* upp = top ? Rs + (int64_t)(c0 + pw) * s + c0 : (float*)LV[l + 1].X.ptr + (int64_t)pw * LV[l + 1].ld;
         const int64_t ldu = top ? s : LV[l + 1].ld;
@@ -1305,12 +1299,6 @@ static qrkit_status factor_typed(qrkit_ctx* ctx, const void* J, const void* S, c
       TsqrLevel& L = C.levels[l];
       T* Xn = l + 1 < C.levels.size() ? (T*)C.levels[l + 1].X.ptr : nullptr;
       const int64_t ldn = l + 1 < C.levels.size() ? C.levels[l + 1].ld : 0;
-      if (sizeof(T) == sizeof(float) && tsqr_tc_supported(s, C.tile_rows)) {
-        // tensor-core trailing updates (3xTF32)
-        rc = tsqr_tile_tc(ctx, (float*)L.X.ptr, L.ld, L.M, s, (float*)L.tau.ptr, (float*)Xn, ldn, L.tiles);
-        if (rc != QRKIT_OK) return rc;
-        continue;
-      }
       const size_t smem = ((size_t)C.tile_rows * s + 64) * sizeof(T);
       auto k = tsqr_tile_kernel<T>;
       QRKIT_CUDA_TRY(ctx, cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem));
@@ -1648,11 +1636,12 @@ qrkit_status composed_layout(qrkit_ctx* ctx, size_t elem) {
     }
   }
   if (P.s.coupled_kind == QRKIT_COUPLED_DENSE) {
-    // wider than one tile (float): column panels of kPanelCols, each a TSQR of its own
+    // float, s a multiple of 32 above 32: column panels of kPanelCols, each a TSQR of its own,
+    // their trailing updates on the tensor cores; otherwise one TSQR of CUDA-core tiles (s <= 64)
     const bool panels = elem == sizeof(float) && s > kPanelCols && s <= kMaxDenseS && s % 32 == 0;
-    if (s > 64 && !(elem == sizeof(float) && tsqr_tc_supported(s, 256)) && !panels)
+    if (s > 64 && !panels)
       return fail(ctx, QRKIT_EUNSUPPORTED,
-                  "dense shared block: s <= 64, or (float) s a multiple of 32 up to 512 for the tensor-core tiles");
+                  "dense shared block: s <= 64, or (float) s a multiple of 32 up to 512");
     const int64_t M0 = C.red_rows + (C.damp ? s : 0);
     if (M0 < s) return fail(ctx, QRKIT_EINVAL, "reduced shared block has fewer rows than columns");
     C.tile_rows = 256;

@@ -317,19 +317,18 @@ qrkit_status reduced_row_sort(qrkit_ctx* ctx, const RowSortTables& t, int64_t ns
                               const int64_t* Xstart, const void* Xw, int w, int* hist, int64_t* spos,
                               int64_t* order, int64_t* Xstart_s, void* Xw_s);
 qrkit_status window_start_copy(qrkit_ctx* ctx, const int32_t* in);
-// TSQR tile factor with tcgen05 trailing updates (float, 256-row tiles, 64 < s <= 128, s % 32 == 0).
+// TSQR tile factor with tcgen05 trailing updates (float, 256-row tiles, s % 32 == 0, s <= 128).
 // Tout (optional): each tile's T factors, (s / 32) blocks of 32 x 32 per tile.
-bool tsqr_tc_supported(int s, int tile_rows);
 qrkit_status tsqr_tile_tc(qrkit_ctx* ctx, float* X, int64_t ld, int64_t M, int s, float* taus, float* Xn,
                           int64_t ldn, int64_t tiles, float* Tout = nullptr);
-// Column-panel TSQR (float): the Q^T of every 256-row tile of a factored 128-column panel
+// Column-panel TSQR (float): the Q^T of every 256-row tile of a factored panel
 // (reflectors in X's first pw columns, T factors from tsqr_tile_tc) applied to the n trailing
 // columns X[:, pw .. pw + n); the tile's top pw rows go to `up` (row tile * pw), the rest to
 // `down` (row down0 + tile * (256 - pw)).  ld, ldu and ldd are multiples of 4.
 qrkit_status tsqr_panel_apply(qrkit_ctx* ctx, const float* X, int64_t ld, int64_t M, int pw, const float* T,
                               int n, float* up, int64_t ldu, float* down, int64_t ldd, int64_t down0,
                               int64_t tiles);
-constexpr int kPanelCols = 128;   // column panel width of a dense reduced block wider than that
+constexpr int kPanelCols = 32;    // column panel width of a (float) dense reduced block wider than that
 constexpr int kMaxDenseS = 512;   // widest dense reduced block (float, column panels)
 qrkit_status reduced_rhs_sort(qrkit_ctx* ctx, const int64_t* spos, const void* rhs, void* rhs_s, int64_t rows);
 void release_band(Band& B);

@@ -1,5 +1,9 @@
 // TSQR tile factor of the dense reduced shared block with the trailing updates on the
-// 5th-generation tensor cores (float, s in {96, 128}, 256-row tiles).
+// 5th-generation tensor cores (float, s a multiple of 32 up to 128, 256-row tiles), and the
+// column-panel update that carries a factored panel's tile reflectors to the later columns.
+// The dense reduced block is factored by panels of 32 columns: each tile then holds one panel
+// of 32 (steps 1-2 below, T exported), and the trailing columns are updated by
+// tsqr_panel_apply_kernel (W = Y^T C, Z = T^T W, C -= Y Z on the tensor cores).
 //
 // One CTA factors one 256 x s row tile held in shared memory by blocked Householder QR
 // (Sec. 2, compact WY): for each panel of 32 columns,
@@ -695,12 +699,10 @@ size_t tsqr_tc_smem(int s) {
          (size_t)kNb * kNb * 4;
 }
 
-bool tsqr_tc_supported(int s, int tile_rows) {
-  return tile_rows == kRows && s > 64 && s <= kMaxS && s % kNb == 0;
-}
-
 qrkit_status tsqr_tile_tc(qrkit_ctx* ctx, float* X, int64_t ld, int64_t M, int s, float* taus, float* Xn,
                           int64_t ldn, int64_t tiles, float* Tout) {
+  if (s % kNb != 0 || s <= 0 || s > kMaxS)
+    return fail(ctx, QRKIT_EINVAL, "tensor-core tile kernel: s a multiple of 32 up to 128");
   const size_t smem = tsqr_tc_smem(s);
   if (smem > ctx->max_smem_optin)
     return fail(ctx, QRKIT_EUNSUPPORTED, "not enough shared memory for the tensor-core tile kernel");

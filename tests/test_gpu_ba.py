@@ -40,8 +40,9 @@ def run(d, precision, refine_steps):
 
 @pytest.mark.parametrize("P,C,s_pad,precision,steps,tol", [
     (300, 7, None, "fp64", 0, 1e-10),          # 63 camera columns, CUDA-core TSQR tiles
-    (1500, 14, 128, "fp32_refined", 2, 1e-5),  # 126 camera columns padded to 128: tensor-core tiles
+    (1500, 14, 128, "fp32_refined", 2, 1e-5),  # 126 camera columns padded to 128: column panels
     (800, 10, 96, "fp32_refined", 2, 1e-5),
+    (1200, 30, 288, "fp32_refined", 2, 1e-5),  # 270 camera columns: nine panels of 32
 ])
 def test_ba_system_matches_oracle(P, C, s_pad, precision, steps, tol):
     d = ba_system(P=P, C=C, s_pad=s_pad, dtype=np.float64 if precision == "fp64" else np.float32)

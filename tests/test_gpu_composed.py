@@ -111,8 +111,8 @@ def test_dense_hcat_many_tsqr_levels():
 
 @pytest.mark.parametrize("s,K", [(128, 300), (96, 257), (128, 2000)])
 def test_dense_tensor_core_tiles_fp32_refined(s, K):
-    """Shared block of 96 / 128 columns: the reduced block's tile QR runs its trailing updates
-    on the tensor cores (3xTF32); ragged tiles at every TSQR level.  Refined float result vs the
+    """Shared block of 96 / 128 columns: column panels of 32, whose Q^T reaches the later
+    columns on the tensor cores (3xTF32); ragged tiles at every TSQR level.  Refined float result vs the
     float64 oracle of the float-rounded problem <= 1e-5."""
     d = block_angular_dense(K=K, n=4, m=2, s=s, scale_decades=2.0, seed_offset=s)
     d32 = dict(d)
@@ -128,10 +128,9 @@ def test_dense_tensor_core_tiles_fp32_refined(s, K):
 
 @pytest.mark.parametrize("s,K", [(160, 400), (224, 300), (256, 1029), (512, 700)])
 def test_dense_column_panels_fp32_refined(s, K):
-    """Shared blocks wider than one tile (Sec. 2, blocked Householder by column panels): each
-    128-column panel is a TSQR over the rows the earlier panels left, its tiles' Q^T applied to
-    the trailing columns on the tensor cores; a last panel of 96 columns uses the tensor-core
-    tile, one of 32 the CUDA-core tile.  Several levels and ragged tiles per panel.  The refined
+    """Wider shared blocks (Sec. 2, blocked Householder by column panels): each 32-column panel
+    is a TSQR over the rows the earlier panels left, its tiles' Q^T applied to the trailing
+    columns on the tensor cores; up to 16 panels, several levels and ragged tiles per panel.  The refined
     float solution within 1e-5 of the float64 oracle of the float-rounded problem, plain float
     within 1e-3, and R_S^T R_S (free of the rows' signs) within 1e-5 of the oracle's."""
     torch = cuda_or_skip()
