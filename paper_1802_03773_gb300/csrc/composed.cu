@@ -553,41 +553,71 @@ __global__ void block_apply_qt_kernel(ComposedView<T> V, FactorOut<T> O, const T
     for (int r = m; r < na; ++r) rhs0[O.red_off[i] + (r - m)] = y[r];
 }
 
-// R_S x = c (upper triangular, column-major with ld) by one warp; optionally x += result.
+// The s x s triangle R_S is solved by one CTA with a thread per row (s <= kTriMax).
+constexpr int kTriMax = 1024;
+static inline unsigned tri_threads(int s) { return (unsigned)(s <= 32 ? 32 : (s + 31) / 32 * 32); }
+
 template <typename T>
-__global__ void dense_backsub_kernel(const T* R, int64_t ld, int s, const T* c, T* x, int accumulate,
-                                     int* status) {
-  const int lane = threadIdx.x & 31;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* xs = reinterpret_cast<T*>(smem_raw);
-  for (int k = s - 1; k >= 0; --k) {
-    T part = 0;
-    for (int j = k + 1 + lane; j < s; j += 32) part += R[(int64_t)j * ld + k] * xs[j];
-    for (int d = 16; d >= 1; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
-    if (lane == 0) {
-      const T rkk = R[(int64_t)k * ld + k];
-      if (rkk == T(0)) record(status, QRKIT_ESINGULAR);
-      xs[k] = (c[k] - part) / rkk;
-    }
-    __syncwarp();
-  }
-  for (int k = lane; k < s; k += 32) x[k] = accumulate ? x[k] + xs[k] : xs[k];
+__device__ __forceinline__ T block_warp_sum(T v) {
+  for (int d = 16; d >= 1; d >>= 1) v += __shfl_xor_sync(0xffffffffu, v, d);
+  return v;
 }
 
-// R_S^T h = g (forward substitution), g given in double.
+// R_S x = c (upper triangular, column-major with ld), optionally x += result (x may be c).
+// Columns are eliminated from the last: once x_k is known, every row above subtracts R_ik x_k,
+// so each column is read once, coalesced, and the next one is loaded a step ahead.
 template <typename T>
-__global__ void dense_fwdsub_rt_kernel(const T* R, int64_t ld, int s, const double* g, T* h) {
-  const int lane = threadIdx.x & 31;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  T* hs = reinterpret_cast<T*>(smem_raw);
-  for (int k = 0; k < s; ++k) {
-    T part = 0;
-    for (int i = lane; i < k; i += 32) part += R[(int64_t)k * ld + i] * hs[i];
-    for (int d = 16; d >= 1; d >>= 1) part += __shfl_xor_sync(0xffffffffu, part, d);
-    if (lane == 0) hs[k] = ((T)g[k] - part) / R[(int64_t)k * ld + k];
-    __syncwarp();
+__global__ void __launch_bounds__(kTriMax) dense_backsub_kernel(const T* R, int64_t ld, int s, const T* c, T* x,
+                                                                int accumulate, int* status) {
+  __shared__ T xs[2];
+  const int i = threadIdx.x;
+  T yi = i < s ? c[i] : T(0);
+  T rcur = i < s ? R[(int64_t)(s - 1) * ld + i] : T(0);   // column s - 1
+  for (int k = s - 1; k >= 0; --k) {
+    const T rnext = i < k ? R[(int64_t)(k - 1) * ld + i] : T(0);
+    if (i == k) {
+      if (rcur == T(0)) record(status, QRKIT_ESINGULAR);
+      xs[k & 1] = yi / rcur;
+    }
+    __syncthreads();
+    const T xk = xs[k & 1];
+    if (i < k) yi -= rcur * xk;
+    else if (i == k) yi = xk;
+    rcur = rnext;
   }
-  for (int k = lane; k < s; k += 32) h[k] = hs[k];
+  if (i < s) x[i] = accumulate ? x[i] + yi : yi;
+}
+
+// R_S^T h = g (forward substitution), g given in double: h_k = (g_k - sum_{i<k} R_ik h_i) / R_kk,
+// the sum over column k of R (coalesced, loaded a step ahead) reduced over the CTA.
+template <typename T>
+__global__ void __launch_bounds__(kTriMax) dense_fwdsub_rt_kernel(const T* R, int64_t ld, int s, const double* g,
+                                                                  T* h) {
+  __shared__ T part_s[2][32];
+  __shared__ T hs[2];
+  const int i = threadIdx.x, lane = i & 31, warp = i >> 5, nw = (int)(blockDim.x >> 5);
+  T hi = T(0);
+  T rcur = i < 1 && s > 0 ? R[0] : T(0);                          // column 0
+  T dnext = s > 0 && i == 0 ? R[0] : T(0), gnext = s > 0 && i == 0 ? (T)g[0] : T(0);
+  for (int k = 0; k < s; ++k) {
+    const T rnext = (k + 1 < s && i <= k + 1) ? R[(int64_t)(k + 1) * ld + i] : T(0);
+    const T dk = dnext, gk = gnext;   // thread 0: R_kk and g_k
+    if (i == 0 && k + 1 < s) {
+      dnext = R[(int64_t)(k + 1) * ld + k + 1];
+      gnext = (T)g[k + 1];
+    }
+    const T p = block_warp_sum<T>(i < k ? rcur * hi : T(0));
+    if (lane == 0) part_s[k & 1][warp] = p;
+    __syncthreads();
+    if (warp == 0) {
+      const T q = block_warp_sum<T>(lane < nw ? part_s[k & 1][lane] : T(0));
+      if (lane == 0) hs[k & 1] = (gk - q) / dk;
+    }
+    __syncthreads();
+    if (i == k) hi = hs[k & 1];
+    rcur = rnext;
+  }
+  if (i < s) h[i] = hi;
 }
 
 // Per-block R_i x_i = rhs_i - R12_i x_S; rhs from ctop (T) or from a double vector.  NA > 0:
@@ -1363,7 +1393,7 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
   const T* RS = pan ? (const T*)C.Rs.ptr : (top ? (const T*)top->X.ptr : nullptr);
   const int64_t ldRS = pan ? s : (top ? top->ld : 0);
   if (V.coupled == QRKIT_COUPLED_DENSE) {
-    LAUNCH(ctx, dense_backsub_kernel<T><<<1, 32, (size_t)s * sizeof(T), st>>>(
+    LAUNCH(ctx, dense_backsub_kernel<T><<<1, tri_threads(s), 0, st>>>(
                     RS, ldRS, s, pan ? (const T*)C.cs.ptr : (const T*)top->rhs.ptr, x + nb, 0, ctx->d_status));
   } else if (V.coupled == QRKIT_COUPLED_WINDOW) {
     // reduced banded block of every segment (Sec. 4.4), rows in P_r order, the shared
@@ -1424,9 +1454,9 @@ static qrkit_status solve_typed(qrkit_ctx* ctx, const void* J, const void* S, co
     }
     if (V.coupled == QRKIT_COUPLED_DENSE) {
       // h_S = R_S^{-T} (g_S - R12^T h_B), then dp_S = R_S^{-1} h_S in place
-      LAUNCH(ctx, dense_fwdsub_rt_kernel<T><<<1, 32, (size_t)s * sizeof(T), st>>>(RS, ldRS, s, gS, h + nb));
-      LAUNCH(ctx, dense_backsub_kernel<T><<<1, 32, (size_t)s * sizeof(T), st>>>(RS, ldRS, s, h + nb, h + nb, 0,
-                                                                                 ctx->d_status));
+      LAUNCH(ctx, dense_fwdsub_rt_kernel<T><<<1, tri_threads(s), 0, st>>>(RS, ldRS, s, gS, h + nb));
+      LAUNCH(ctx, dense_backsub_kernel<T><<<1, tri_threads(s), 0, st>>>(RS, ldRS, s, h + nb, h + nb, 0,
+                                                                         ctx->d_status));
       LAUNCH(ctx, axpy_kernel<T><<<blocks_for(s, 128), 128, 0, st>>>(x + nb, h + nb, s));
     }
     // dp_B = R_B^{-1} (h_B - R12 dp_S), accumulated into p
@@ -1722,7 +1752,7 @@ static qrkit_status solve_r_typed(qrkit_ctx* ctx, const void* qtb, void* p) {
   if (V.coupled == QRKIT_COUPLED_DENSE) {
     const TsqrLevel& top = C.levels.back();
     const bool pan = !C.panels.empty();
-    LAUNCH(ctx, dense_backsub_kernel<T><<<1, 32, (size_t)s * sizeof(T), st>>>(
+    LAUNCH(ctx, dense_backsub_kernel<T><<<1, tri_threads(s), 0, st>>>(
                     pan ? (const T*)C.Rs.ptr : (const T*)top.X.ptr, pan ? s : top.ld, s, c + P.cols, x + P.cols, 0,
                     ctx->d_status));
   }

@@ -161,6 +161,57 @@ def test_dense_column_panels_fp32_refined(s, K):
     assert np.abs(G - Gr).max() <= 1e-5 * np.abs(Gr).max()
 
 
+@pytest.mark.parametrize("s", [128, 512])
+def test_dense_column_panels_full_size(s):
+    """The timed shapes at full size (100,000 blocks 4x2, S 400,000 x s, FP32 refined, one
+    refinement step as in the bench): the solution against an FP64 solve of the same damped
+    least-squares problem by its normal equations, eliminated block by block (the Schur
+    complement on the shared columns), in plain float64 PyTorch on the device.  At these
+    condition numbers (columns scaled over two decades) that reference is accurate to about
+    1e-9, far inside the 1e-5 asked of the float path."""
+    torch = cuda_or_skip()
+    from paper_1802_03773_gb300 import Context, qrkit
+    K, n, m = 100_000, 4, 2
+    d = block_angular_dense(K=K, n=n, m=m, s=s, scale_decades=2.0, dtype=np.float32)
+    lam = float(d["lam"])
+    Jb = torch.from_numpy(np.ascontiguousarray(np.asarray(d["blocks"], np.float32))).cuda()   # K x n x m
+    S32 = torch.from_numpy(np.ascontiguousarray(np.asarray(d["S"], np.float32))).cuda()        # K n x s
+    b32 = torch.from_numpy(np.asarray(d["b"], np.float32)).cuda()
+    del d
+    ctx = Context(0, precision="fp32_refined")
+    ctx.plan_blocks(np.full(K, n), np.full(K, m), qrkit.COUPLED_DENSE, shared_cols=s)
+    J = Jb.transpose(1, 2).contiguous().reshape(-1)      # per block column-major
+    Sc = S32.t().contiguous().reshape(-1)                # column-major
+    ctx.factor(J, Sc, None, lam)
+    p = torch.empty(K * m + s, device="cuda", dtype=torch.float32)
+    ctx.solve(b32, p, refine_steps=1)
+    ctx.sync_status()
+    ctx.close()
+    del J, Sc
+    # reference: min ||[J; lam^(1/2) D] p - [b; 0]||, D = column norms of J (zero -> 1)
+    A = Jb.double()
+    S = S32.double()
+    b = b32.double()
+    del Jb, S32
+    Db = A.pow(2).sum(1).sqrt()                          # K x m
+    Ds = S.pow(2).sum(0).sqrt()
+    Db = torch.where(Db == 0, torch.ones_like(Db), Db)
+    Ds = torch.where(Ds == 0, torch.ones_like(Ds), Ds)
+    Sb = S.reshape(K, n, s)
+    bb = b.reshape(K, n, 1)
+    Ai = A.transpose(1, 2) @ A + lam * torch.diag_embed(Db.pow(2))   # K x m x m
+    Ci = A.transpose(1, 2) @ Sb                                       # K x m x s
+    gi = A.transpose(1, 2) @ bb                                       # K x m x 1
+    AiC = torch.linalg.solve(Ai, Ci)
+    Aig = torch.linalg.solve(Ai, gi)
+    schur = S.t() @ S + lam * torch.diag(Ds.pow(2)) - Ci.reshape(K * m, s).t() @ AiC.reshape(K * m, s)
+    rhs = S.t() @ b - Ci.reshape(K * m, s).t() @ Aig.reshape(K * m)
+    pS = torch.linalg.solve(schur, rhs)
+    pB = (Aig - AiC @ pS.reshape(1, s, 1)).reshape(K * m)
+    p_ref = torch.cat([pB, pS]).cpu().numpy()
+    assert_close(p.cpu().numpy(), p_ref, 1e-5)
+
+
 @pytest.mark.parametrize("precision,tol", [("fp64", 1e-12), ("fp32_refined", 1e-5)])
 def test_dense_hcat_solve_replays_in_cuda_graph(precision, tol):
     """factor + solve of the 200-block workload, captured once in a CUDA graph after a warm-up
