@@ -70,9 +70,10 @@ def measured_peaks():
     return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0}, "fallback"
 
 
-def recorded_traffic():
-    """DRAM bytes of one solve (the launches of its kernels) from the committed ncu summary,
-    if it was taken on the current kernel source (else None)."""
+def recorded_traffic(mapping=None):
+    """DRAM bytes of one solve (the launches of its kernels) under the given block mapping (the
+    autotuner's text form) from the committed ncu summary, if it was taken on the current kernel
+    source and that mapping (else None)."""
     p = os.path.join(ROOT, "profiles", "block_task_kernel_1m_blocks.json")
     if not os.path.exists(p):
         return None
@@ -84,8 +85,8 @@ def recorded_traffic():
     h = sha.hexdigest()
     if rec.get("kernel_source_sha256") != h:
         return None
-    v = rec.get("dram_bytes_per_launch")
-    return sum(v.values()) if isinstance(v, dict) else v
+    v = rec.get("dram_bytes_per_launch", {}).get(mapping)
+    return sum(v.values()) if isinstance(v, dict) else None
 
 
 class ClockSampler:
@@ -926,7 +927,7 @@ def run_ours(args):
     alg = algorithmic_bytes(d)
     kavg = sum(kern_ms) / len(kern_ms)
     achieved = alg / (kavg * 1e-3) / 1e9
-    traffic = recorded_traffic()
+    traffic = recorded_traffic(tuned)
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True,
