@@ -1253,14 +1253,15 @@ static qrkit_status factor_panels(qrkit_ctx* ctx, int s) {
     const int c0 = j * kPanelCols;
     const int pw = std::min(kPanelCols, s - c0);
     const int n = s - c0 - pw;   // trailing columns
+    if (pw != kPanelCols) return fail(ctx, QRKIT_EINVAL, "column panels: s must be a multiple of 32");
     for (size_t l = 0; l < LV.size(); ++l) {
       TsqrLevel& L = LV[l];
       const bool top = l + 1 == LV.size();
       float* X = (float*)L.X.ptr;
       float* Xn = top ? Rs + (int64_t)c0 * s + c0 : (float*)LV[l + 1].X.ptr;
       const int64_t ldn = top ? s : LV[l + 1].ld;
-      qrkit_status rc =
-          tsqr_tile_tc(ctx, X, L.ld, L.M, pw, (float*)L.tau.ptr, Xn, ldn, L.tiles, n > 0 ? (float*)L.T.ptr : nullptr);
+      qrkit_status rc = tsqr_panel_tile(ctx, X, L.ld, L.M, (float*)L.tau.ptr, Xn, ldn, L.tiles,
+                                        n > 0 ? (float*)L.T.ptr : nullptr);
       if (rc != QRKIT_OK) return rc;
       if (n > 0) {
         float* upp = top ? Rs + (int64_t)(c0 + pw) * s + c0 : (float*)LV[l + 1].X.ptr + (int64_t)pw * LV[l + 1].ld;

@@ -317,12 +317,12 @@ qrkit_status reduced_row_sort(qrkit_ctx* ctx, const RowSortTables& t, int64_t ns
                               const int64_t* Xstart, const void* Xw, int w, int* hist, int64_t* spos,
                               int64_t* order, int64_t* Xstart_s, void* Xw_s);
 qrkit_status window_start_copy(qrkit_ctx* ctx, const int32_t* in);
-// TSQR tile factor with tcgen05 trailing updates (float, 256-row tiles, s % 32 == 0, s <= 128).
-// Tout (optional): each tile's T factors, (s / 32) blocks of 32 x 32 per tile.
-qrkit_status tsqr_tile_tc(qrkit_ctx* ctx, float* X, int64_t ld, int64_t M, int s, float* taus, float* Xn,
-                          int64_t ldn, int64_t tiles, float* Tout = nullptr);
+// One TSQR level of a 32-column panel (float, 256-row tiles, columns in registers): reflectors
+// and R in place, tau per column, each tile's 32 x 32 T (Tout, optional), the R rows to Xn.
+qrkit_status tsqr_panel_tile(qrkit_ctx* ctx, float* X, int64_t ld, int64_t M, float* taus, float* Xn, int64_t ldn,
+                             int64_t tiles, float* Tout);
 // Column-panel TSQR (float): the Q^T of every 256-row tile of a factored panel
-// (reflectors in X's first pw columns, T factors from tsqr_tile_tc) applied to the n trailing
+// (reflectors in X's first pw columns, T factors from tsqr_panel_tile) applied to the n trailing
 // columns X[:, pw .. pw + n); the tile's top pw rows go to `up` (row tile * pw), the rest to
 // `down` (row down0 + tile * (256 - pw)).  ld, ldu and ldd are multiples of 4.
 qrkit_status tsqr_panel_apply(qrkit_ctx* ctx, const float* X, int64_t ld, int64_t M, int pw, const float* T,

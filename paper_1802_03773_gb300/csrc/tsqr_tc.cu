@@ -1,24 +1,18 @@
-// TSQR tile factor of the dense reduced shared block with the trailing updates on the
-// 5th-generation tensor cores (float, s a multiple of 32 up to 128, 256-row tiles), and the
-// column-panel update that carries a factored panel's tile reflectors to the later columns.
-// The dense reduced block is factored by panels of 32 columns: each tile then holds one panel
-// of 32 (steps 1-2 below, T exported), and the trailing columns are updated by
-// tsqr_panel_apply_kernel (W = Y^T C, Z = T^T W, C -= Y Z on the tensor cores).
-//
-// One CTA factors one 256 x s row tile held in shared memory by blocked Householder QR
-// (Sec. 2, compact WY): for each panel of 32 columns,
-//   1. the panel is factored column by column on the CUDA cores (reflectors H = I - tau v v^T,
-//      v[0] = 1, stored below the diagonal as in the unblocked kernel);
-//   2. T (32 x 32 upper) of Q_panel = H_0 .. H_31 = I - Y T Y^T is built forward from Y^T Y;
-//   3. W = Y^T C for the trailing columns C, then Z = T^T W (CUDA cores);
-//   4. C -= Y Z on the tensor cores: tcgen05.mma kind::tf32 with the 3xTF32 split
+// Column-panel TSQR of the dense reduced shared block (float, s a multiple of 32, 256-row tiles).
+// The reduced block is factored by panels of 32 columns (Sec. 2, compact WY): each panel is a
+// TSQR whose tiles are factored by tsqr_panel_tile_kernel (Householder QR with the columns in
+// registers, then the panel's T), and after every TSQR level tsqr_panel_apply_kernel applies the
+// tiles' Q^T = I - Y T^T Y^T to the later columns:
+//   1. W = Y^T C for the trailing columns C, then Z = T^T W (CUDA cores);
+//   2. C -= Y Z on the tensor cores: tcgen05.mma kind::tf32 with the 3xTF32 split
 //      (Y = Y_hi + Y_lo, Z = Z_hi + Z_lo, Y Z ~ Y_hi Z_hi + Y_hi Z_lo + Y_lo Z_hi), FP32
 //      accumulation in TMEM, M = 128 rows per half tile, K = 32, N = trailing columns; the
 //      product is read back with tcgen05.ld and subtracted in shared memory.
 // Operands are staged in shared memory in the canonical K-major no-swizzle layout (8-row x
-// 16-byte core matrices) and described by tcgen05 shared-memory descriptors.  The outputs
-// follow the unblocked tile kernel exactly (V below / R on and above the diagonal, tau per
-// column, the tile's R rows to the next TSQR level), so Q^T b and the solves are unchanged.
+// 16-byte core matrices) and described by tcgen05 shared-memory descriptors.  Tiles arrive by
+// bulk copies (TMA).  The outputs follow the unblocked tile kernel (V below / R on and above the
+// diagonal, tau per column, the tile's R rows to the next TSQR level), so Q^T b and the solves
+// are those of any TSQR.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -31,9 +25,7 @@ namespace {
 
 constexpr int kRows = 256;      // tile rows (two MMA halves of 128)
 constexpr int kNb = 32;         // panel width = MMA K
-constexpr int kThr = 512;     // 16 warps: more of them to hide the panel's latency
-constexpr int kMaxS = 128;
-constexpr int kTmemCols = 256;  // D of half h at columns [128 h, 128 h + n)
+constexpr int kThr = 512;       // threads of the panel update (16 warps)
 constexpr uint32_t kWaitLimit = 1u << 26;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
@@ -86,28 +78,6 @@ __device__ __forceinline__ float transpose_reduce(float (&v)[32], int lane) {
   return v[0];
 }
 
-// Row i of the panel's Y (Y[i][l] = 1 at i = p0 + l, the stored v below, 0 above and for
-// l >= nk) against a column x of the tile: acc[l] += Y[i][l] x[i] for the lane's rows
-// i = p0 + lane, p0 + lane + 32, ... (the first pass holds the triangle, the others are full).
-__device__ __forceinline__ void accumulate_yt(const float* A, int p0, int nk, const float* x, float (&acc)[32],
-                                              int lane) {
-  {
-    const int i = p0 + lane;
-    const float xv = i < kRows ? x[i] : 0.f;
-#pragma unroll
-    for (int l = 0; l < kNb; ++l) {
-      const int d = p0 + l;
-      const float y = (l < nk && i < kRows) ? (i > d ? A[d * kRows + i] : (i == d ? 1.f : 0.f)) : 0.f;
-      acc[l] += y * xv;
-    }
-  }
-  for (int i = p0 + 32 + lane; i < kRows; i += 32) {
-    const float xv = x[i];
-#pragma unroll
-    for (int l = 0; l < kNb; ++l) acc[l] += (l < nk ? A[(p0 + l) * kRows + i] : 0.f) * xv;
-  }
-}
-
 __device__ __forceinline__ void tc_record(int* status, int code) {
   if (status) atomicCAS(status, 0, code);
 }
@@ -130,347 +100,187 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity) {
   return false;
 }
 
-__global__ void __launch_bounds__(kThr, 1)
-tsqr_tile_tc_kernel(float* X, int64_t ld, int64_t M, int s, float* taus, float* Xn, int64_t ldn, float* Tout,
-                    int* status) {
+// ---- Column-panel TSQR: the QR of one 256-row tile of a 32-column panel ----
+//
+// Householder QR (Sec. 2) of a 256 x 32 tile with its columns in registers: column j lives on
+// warp j % 16, row i = lane + 32 u (u < 8) of it on the lane.  At step k the reflector of column
+// k goes through shared memory (two alternating slots), every warp applies it to its columns
+// after k (a dot product by one warp reduction, then an axpy, all in registers), and the warp
+// that holds column k + 1 forms the next reflector right after updating it.  Then G = Y^T Y
+// (strict upper triangle) and the compact-WY T (T[k][k] = tau_k, column k of the strict upper
+// part = -tau_k T[:, :k] G[:k, k]) for the panel update.  Outputs as the general tile kernel:
+// reflectors below / R on and above the diagonal in place, tau per column, T, the R rows to the
+// next level.
+constexpr int kPT = 512;        // threads of a panel tile (16 warps, two columns each)
+constexpr int kPad = kNb + 1;   // row stride of G and T in shared memory (conflict-free rows)
+
+size_t panel_tile_smem() {
+  return (size_t)kRows * kNb * 4 + 2 * (size_t)kRows * 4 + 2 * (size_t)kNb * kPad * 4;
+}
+
+__global__ void __launch_bounds__(kPT, 1)
+tsqr_panel_tile_kernel(float* X, int64_t ld, int64_t M, float* taus, float* Xn, int64_t ldn, float* Tout,
+                       int* status) {
   extern __shared__ __align__(1024) unsigned char smem_raw[];
-  float* A = reinterpret_cast<float*>(smem_raw);                       // 256 x s, column-major
-  unsigned char* Yhi = smem_raw + (size_t)kRows * s * 4;               // 256 x 32 operand
-  unsigned char* Ylo = Yhi + kRows * kNb * 4;
-  unsigned char* Zhi = Ylo + kRows * kNb * 4;                          // n x 32 operand (n <= 96)
-  unsigned char* Zlo = Zhi + (kMaxS - kNb) * kNb * 4;                  // also W / Z in float
-  float* Tm = reinterpret_cast<float*>(Zlo + (kMaxS - kNb) * kNb * 4);  // 32 x 32 (row l, col k)
-  float* W = reinterpret_cast<float*>(Zlo);                            // 32 x n, row-major
-  __shared__ float sh2[2][2];   // reflector slots: tau, beta
+  float* A = reinterpret_cast<float*>(smem_raw);   // 256 x 32, column-major
+  float* V = A + kRows * kNb;                      // two reflector slots of 256
+  float* Gs = V + 2 * kRows;                       // 32 x 33: G[m][k] at m * kPad + k
+  float* Tm = Gs + kNb * kPad;                     // 32 x 33: T[l][k] at l * kPad + k
+  __shared__ float tslot[2];
   __shared__ float tau_s[kNb];
-  __shared__ uint32_t tmem_slot;
-  __shared__ __align__(8) uint64_t mbar;
   __shared__ __align__(8) uint64_t mbar_ld;
-  __shared__ int abort_s;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t r0 = (int64_t)blockIdx.x * kRows;
   const int r = (int)(M - r0 < (int64_t)kRows ? M - r0 : (int64_t)kRows);
-  const int kmax = r < s ? r : s;
-  // the tile's columns by bulk copies when every column starts on a 16-byte boundary
+  const int kmax = r < kNb ? r : kNb;
   const bool bulk = (ld & 3) == 0 && (reinterpret_cast<uintptr_t>(X) & 15) == 0;
 
-  if (warp == 0) {
-    asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(su32(&tmem_slot)),
-                 "r"(kTmemCols));
-    asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;");
-  }
   if (tid == 0) {
-    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar)), "r"(1));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar_ld)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
-    abort_s = 0;
     if (bulk) {
-      dev::mbar_expect_tx(&mbar_ld, column_bytes(r) * (uint32_t)s);
-      stage_columns(A, X, ld, r0, r, s, &mbar_ld);
+      dev::mbar_expect_tx(&mbar_ld, column_bytes(r) * (uint32_t)kNb);
+      stage_columns(A, X, ld, r0, r, kNb, &mbar_ld);
     }
   }
   if (!bulk)
-    for (int e = tid; e < kRows * s; e += kThr) {
+    for (int e = tid; e < kRows * kNb; e += kPT) {
       const int c = e / kRows, i = e % kRows;
       A[e] = i < r ? X[(int64_t)c * ld + r0 + i] : 0.f;
     }
-  asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
-  asm volatile("tcgen05.fence::after_thread_sync;");
-  const uint32_t tmem = tmem_slot;
-  uint32_t phase = 0;
   if (bulk) {
     const bool ok = wait_phase(&mbar_ld, 0u);
     if (__syncthreads_or(!ok)) {
       // the copies may still be in flight: one more bounded wait before the CTA exits
       if (tid == 0) tc_record(status, QRKIT_ETIMEOUT);
       wait_phase(&mbar_ld, 0u);
-      __syncthreads();
-      if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
       return;
     }
-    for (int e = tid; e < (kRows - r) * s; e += kThr) {   // rows past the tile's end
+    for (int e = tid; e < (kRows - r) * kNb; e += kPT) {   // rows past the tile's end
       const int c = e / (kRows - r), i = r + e % (kRows - r);
       A[c * kRows + i] = 0.f;
     }
     __syncthreads();
   }
-
-  for (int p0 = 0; p0 < kmax; p0 += kNb) {
-    const int kend = p0 + kNb < kmax ? p0 + kNb : kmax;
-    const int pend = p0 + kNb < s ? p0 + kNb : s;   // panel columns
-    // 1. panel factorization.  The reflector of column k is formed by warp 0 (norm of the
-    // column below k, tau, beta, the column scaled to v with v_k = 1) before the barrier that
-    // opens step k; the trailing panel columns are then updated up to four per warp at once
-    // (one pass over the rows for their dot products), and warp 0, which holds column k + 1,
-    // forms the next reflector right after updating it (the reflectors alternate between two
-    // slots, so a warp still reading the current one is never overtaken).
-    auto reflector = [&](int k, int slot) {   // warp 0 only
-      float* x = A + k * kRows;
-      float sq = 0.f;
+  // the warp's two columns in registers
+  float a0[kRows / 32], a1[kRows / 32];
 #pragma unroll
-      for (int u = 0; u < kRows / 32; ++u) {   // rows k + 1 + lane + 32 u below r: loads in flight together
-        const int i = k + 1 + lane + 32 * u;
-        if (i < r) sq += x[i] * x[i];
-      }
-      sq = warp_sum(sq);
-      const float alpha = x[k];
-      const float norm = sqrtf(alpha * alpha + sq);
-      float beta = 0.f, t = 0.f, scale = 0.f;
-      if (norm != 0.f) {
-        beta = alpha >= 0.f ? -norm : norm;
-        t = (beta - alpha) / beta;
-        scale = 1.f / (alpha - beta);
-      }
-#pragma unroll
-      for (int u = 0; u < kRows / 32; ++u) {
-        const int i = k + 1 + lane + 32 * u;
-        if (i < r) x[i] *= scale;
-      }
-      if (lane == 0) {
-        sh2[slot][0] = t;
-        sh2[slot][1] = beta;
-      }
-    };
-    if (warp == 0 && p0 < kend) reflector(p0, p0 & 1);
-    for (int k = p0; k < kend; ++k) {
-      __syncthreads();   // reflector k formed and its column scaled; column k + 1 updated
-      const float* x = A + k * kRows;
-      const float t = sh2[k & 1][0];
-      // warp w takes columns k + 1 + w + 8 q (warp 0 first column k + 1)
-      constexpr int kQ = 4;
-      float* yq[kQ];
-      float w[kQ] = {0.f, 0.f, 0.f, 0.f};
-      const int jstep = kThr / 32;
-#pragma unroll
-      for (int q = 0; q < kQ; ++q) {
-        const int j = k + 1 + warp + q * jstep;
-        yq[q] = A + (j < pend ? j : k) * kRows;   // past the panel: a harmless stand-in, unused
-      }
-      const int left = pend - (k + 1 + warp);
-      const int cnt = left > 0 ? (left + jstep - 1) / jstep : 0;
-      if (cnt > 0) {
-        float xr[kRows / 32];   // the reflector's rows of this lane, kept for the update
-#pragma unroll
-        for (int u = 0; u < kRows / 32; ++u) {
-          const int i = k + 1 + lane + 32 * u;
-          xr[u] = i < r ? x[i] : 0.f;
-#pragma unroll
-          for (int q = 0; q < kQ; ++q)
-            if (q < cnt && i < r) w[q] += xr[u] * yq[q][i];
-        }
-#pragma unroll
-        for (int q = 0; q < kQ; ++q)
-          if (q < cnt) w[q] = (warp_sum(w[q]) + yq[q][k]) * t;
-        __syncwarp();   // every lane has read row k of its columns
-        if (lane == 0) {
-#pragma unroll
-          for (int q = 0; q < kQ; ++q)
-            if (q < cnt) yq[q][k] -= w[q];
-        }
-#pragma unroll
-        for (int u = 0; u < kRows / 32; ++u) {
-          const int i = k + 1 + lane + 32 * u;
-#pragma unroll
-          for (int q = 0; q < kQ; ++q)
-            if (q < cnt && i < r) yq[q][i] -= w[q] * xr[u];
-        }
-      }
-      if (warp == 0 && k + 1 < kend) {
-        __syncwarp();   // column k + 1 (this warp's first) is fully updated
-        reflector(k + 1, (k + 1) & 1);
-      }
-      if (tid == 0) {
-        A[k * kRows + k] = sh2[k & 1][1];
-        taus[(int64_t)blockIdx.x * s + k] = t;
-        tau_s[k - p0] = t;
-      }
-    }
-    __syncthreads();
-    const int n = s - pend;   // trailing columns
-    if (n <= 0 && !Tout) break;
-    const int nk = kend - p0;
-    // Y (256 x 32): Y[i][l] = 1 at i = p0 + l, the stored v below, 0 above (and 0 for l >= nk)
-    auto yval = [&](int i, int l) -> float {
-      if (l >= nk) return 0.f;
-      const int d = p0 + l;
-      return i < d ? 0.f : (i == d ? 1.f : A[d * kRows + i]);
-    };
-    // 2. T: G = Y^T Y (G[l][k], l < k) into W's space first (one warp per column k of Y, lanes
-    // over rows, the 32 sums of a column reduced together), then the forward recurrence
-    for (int k = warp; k < kNb; k += kThr / 32) {
-      float acc[32];
-#pragma unroll
-      for (int l = 0; l < 32; ++l) acc[l] = 0.f;
-      if (k < nk) {
-        // column k of Y as a vector: y_k[i] = 1 at p0 + k, A below, 0 above
-        const float* yk = A + (p0 + k) * kRows;
-        const int d = p0 + k;
-        {
-          const int i = p0 + lane;
-          const float xv = i < kRows ? (i > d ? yk[i] : (i == d ? 1.f : 0.f)) : 0.f;
-#pragma unroll
-          for (int l = 0; l < kNb; ++l) {
-            const int dl = p0 + l;
-            const float y = (l < nk && i < kRows) ? (i > dl ? A[dl * kRows + i] : (i == dl ? 1.f : 0.f)) : 0.f;
-            acc[l] += y * xv;
-          }
-        }
-        for (int i = p0 + 32 + lane; i < kRows; i += 32) {
-          const float xv = yk[i];
-#pragma unroll
-          for (int l = 0; l < kNb; ++l) acc[l] += (l < nk ? A[(p0 + l) * kRows + i] : 0.f) * xv;
-        }
-      }
-      const float g = transpose_reduce(acc, lane);
-      W[lane * kNb + k] = (lane < k && k < nk) ? g : 0.f;
-    }
-    __syncthreads();
-    if (warp == 0) {
-      for (int k = 0; k < kNb; ++k) {
-        const float tk = k < nk ? tau_s[k] : 0.f;
-        // T[l][k] = -tau_k sum_{m=l}^{k-1} T[l][m] G[m][k] for l < k, T[k][k] = tau_k
-        float v = 0.f;
-        if (lane < k) {
-          for (int m = lane; m < k; ++m) v += Tm[lane * kNb + m] * W[m * kNb + k];
-          v *= -tk;
-        }
-        __syncwarp();
-        if (lane < k) Tm[lane * kNb + k] = v;
-        if (lane == k) Tm[k * kNb + k] = tk;
-        if (lane > k) Tm[lane * kNb + k] = 0.f;
-        __syncwarp();
-      }
-    }
-    __syncthreads();
-    if (Tout)
-      for (int e = tid; e < kNb * kNb; e += kThr)
-        Tout[((int64_t)blockIdx.x * (s / kNb) + p0 / kNb) * (kNb * kNb) + e] = Tm[e];
-    if (n <= 0) break;
-    // 3. W = Y^T C (32 x n, row-major; one warp per trailing column, lanes over rows, the 32
-    // sums of a column reduced together), then Z = T^T W
-    for (int j = warp; j < n; j += kThr / 32) {
-      float acc[32];
-#pragma unroll
-      for (int l = 0; l < 32; ++l) acc[l] = 0.f;
-      accumulate_yt(A, p0, nk, A + (pend + j) * kRows, acc, lane);
-      const float w = transpose_reduce(acc, lane);
-      W[lane * n + j] = lane < nk ? w : 0.f;
-    }
-    __syncthreads();
-    for (int j = tid; j < n; j += kThr)
-      for (int i = kNb - 1; i >= 0; --i) {
-        float z = 0.f;
-        for (int l = 0; l <= i; ++l) z += Tm[l * kNb + i] * W[l * n + j];
-        W[i * n + j] = z;
-      }
-    __syncthreads();
-    // 4. operands: Z (n x 32, K-major) hi/lo; Y (256 x 32) hi/lo
-    {
-      float zv[(kMaxS - kNb) * kNb / kThr];
-      int cnt = 0;
-      for (int e = tid; e < kNb * n; e += kThr) zv[cnt++] = W[e];
-      __syncthreads();
-      cnt = 0;
-      for (int e = tid; e < kNb * n; e += kThr) {
-        const int i = e / n, j = e % n;
-        const float v = zv[cnt++], h = to_tf32(v);
-        *reinterpret_cast<float*>(Zhi + koff(j, i)) = h;
-        *reinterpret_cast<float*>(Zlo + koff(j, i)) = to_tf32(v - h);
-      }
-    }
-    const int h0 = p0 >= 128 ? 1 : 0;   // rows of the first half are zero in Y below p0
-    for (int e = tid + h0 * 128; e < kRows * kNb; e += kThr) {
-      const int l = e / kRows, i = e % kRows;
-      if (i < h0 * 128) continue;
-      const float v = yval(i, l), h = to_tf32(v);
-      const uint32_t o = (uint32_t)(i >> 7) * (128 * kNb * 4) + koff(i & 127, l);
-      *reinterpret_cast<float*>(Yhi + o) = h;
-      *reinterpret_cast<float*>(Ylo + o) = to_tf32(v - h);
-    }
-    asm volatile("fence.proxy.async.shared::cta;");
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    if (tid == 0) {
-      const uint32_t id = idesc_tf32(128, n);
-      for (int h = h0; h < 2; ++h) {
-        const uint32_t yo = (uint32_t)h * (128 * kNb * 4);
-        int first = 1;
-        for (int ks = 0; ks < kNb / 8; ++ks) {
-          const uint32_t ko = (uint32_t)ks * 256;
-          for (int sp = 0; sp < 3; ++sp) {
-            const unsigned char* ya = sp == 2 ? Ylo : Yhi;
-            const unsigned char* zb = sp == 1 ? Zlo : Zhi;
-            const uint64_t ad = smem_desc(su32(ya) + yo + ko), bd = smem_desc(su32(zb) + ko);
-            const uint32_t acc = first ? 0u : 1u;
-            asm volatile(
-                "{\n.reg .pred p;\nsetp.ne.b32 p, %4, 0;\n"
-                "tcgen05.mma.cta_group::1.kind::tf32 [%0], %1, %2, %3, p;\n}" ::"r"(tmem + (uint32_t)h * 128),
-                "l"(ad), "l"(bd), "r"(id), "r"(acc));
-            first = 0;
-          }
-        }
-      }
-      asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(
-          su32(&mbar)));
-    }
-    // wait for the MMAs (bounded)
-    uint32_t done = 0;
-    for (uint32_t it = 0; it < kWaitLimit && !done; ++it)
-      asm volatile(
-          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-          : "=r"(done)
-          : "r"(su32(&mbar)), "r"(phase));
-    phase ^= 1u;
-    if (!done) abort_s = 1;
-    asm volatile("tcgen05.fence::after_thread_sync;");
-    __syncthreads();
-    if (abort_s) break;
-    // C -= D: warp w reads TMEM lanes 32 (w % 4) .. of half (w / 4) % 2, columns 8-wide groups
-    // (w / 8), (w / 8) + 2, ... (the lane quarter a warp may read is fixed by w % 4)
-    {
-      const int qd = warp & 3, h = (warp >> 2) & 1, part = warp >> 3;
-      if (h >= h0) {
-        const int row = h * 128 + qd * 32 + lane;
-        for (int c0 = part * 8; c0 < n; c0 += 8 * (kThr / 256)) {
-          uint32_t v[8];
-          const uint32_t ta = tmem + ((uint32_t)(qd * 32) << 16) + (uint32_t)(h * 128 + c0);
-          asm volatile("tcgen05.ld.sync.aligned.32x32b.x8.b32 {%0,%1,%2,%3,%4,%5,%6,%7}, [%8];"
-                       : "=r"(v[0]), "=r"(v[1]), "=r"(v[2]), "=r"(v[3]), "=r"(v[4]), "=r"(v[5]), "=r"(v[6]),
-                         "=r"(v[7])
-                       : "r"(ta));
-          asm volatile("tcgen05.wait::ld.sync.aligned;");
-#pragma unroll
-          for (int j = 0; j < 8; ++j) A[(pend + c0 + j) * kRows + row] -= __uint_as_float(v[j]);
-        }
-      }
-    }
-    asm volatile("tcgen05.fence::before_thread_sync;");
-    __syncthreads();
+  for (int u = 0; u < kRows / 32; ++u) {
+    a0[u] = A[warp * kRows + lane + 32 * u];
+    a1[u] = A[(warp + 16) * kRows + lane + 32 * u];
   }
-  if (abort_s) {
-    if (tid == 0) tc_record(status, QRKIT_ETIMEOUT);
-    // the MMAs of this CTA may still be running: wait once more (bounded) before freeing TMEM
-    uint32_t done = 0;
-    for (uint32_t it = 0; it < kWaitLimit && !done; ++it)
-      asm volatile(
-          "{\n.reg .pred p;\nmbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\nselp.u32 %0, 1, 0, p;\n}"
-          : "=r"(done)
-          : "r"(su32(&mbar)), "r"(phase ^ 1u));
+  // the reflector of column k from its register column a (its owner warp): the column below k
+  // scaled to v (v_k = 1, stored implicitly), beta on the diagonal, v written to slot `slot`
+  auto form = [&](int k, float (&a)[kRows / 32], int slot) {
+    float sq = 0.f, ak = 0.f;
+#pragma unroll
+    for (int u = 0; u < kRows / 32; ++u) {
+      const int i = lane + 32 * u;
+      if (i > k) sq += a[u] * a[u];
+      if (u == (k >> 5)) ak = a[u];
+    }
+    sq = warp_sum(sq);
+    const float alpha = __shfl_sync(0xffffffffu, ak, k & 31);
+    const float norm = sqrtf(alpha * alpha + sq);
+    float beta = 0.f, t = 0.f, scale = 0.f;
+    if (norm != 0.f) {
+      beta = alpha >= 0.f ? -norm : norm;
+      t = (beta - alpha) / beta;
+      scale = 1.f / (alpha - beta);
+    }
+#pragma unroll
+    for (int u = 0; u < kRows / 32; ++u) {
+      const int i = lane + 32 * u;
+      if (i > k) a[u] *= scale;
+      else if (i == k) a[u] = beta;
+      V[slot * kRows + i] = i > k ? a[u] : (i == k ? 1.f : 0.f);
+    }
+    if (lane == 0) {
+      tslot[slot] = t;
+      tau_s[k] = t;
+      taus[(int64_t)blockIdx.x * kNb + k] = t;
+    }
+  };
+  // a column after k updated with reflector k: a -= t (v^T a) v
+  auto update = [&](float (&a)[kRows / 32], const float (&v)[kRows / 32], float t) {
+    float d = 0.f;
+#pragma unroll
+    for (int u = 0; u < kRows / 32; ++u) d += v[u] * a[u];
+    const float w = warp_sum(d) * t;
+#pragma unroll
+    for (int u = 0; u < kRows / 32; ++u) a[u] -= w * v[u];
+  };
+  if (warp == 0 && kmax > 0) form(0, a0, 0);
+  for (int k = 0; k < kmax; ++k) {
+    __syncthreads();   // reflector k in slot k & 1; column k + 1 not yet updated
+    const int slot = k & 1;
+    float v[kRows / 32];
+#pragma unroll
+    for (int u = 0; u < kRows / 32; ++u) v[u] = V[slot * kRows + lane + 32 * u];
+    const float t = tslot[slot];
+    if (warp > k) update(a0, v, t);
+    if (warp + 16 > k) update(a1, v, t);
+    if (k + 1 < kmax && ((k + 1) & 15) == warp) {
+      if (k + 1 < 16) form(k + 1, a0, slot ^ 1);
+      else form(k + 1, a1, slot ^ 1);
+    }
   }
-  asm volatile("tcgen05.fence::before_thread_sync;");
+#pragma unroll
+  for (int u = 0; u < kRows / 32; ++u) {
+    A[warp * kRows + lane + 32 * u] = a0[u];
+    A[(warp + 16) * kRows + lane + 32 * u] = a1[u];
+  }
+  for (int e = tid; e < kNb * kPad; e += kPT) Tm[e] = 0.f;
   __syncthreads();
-  if (warp == 0) asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(tmem), "r"(kTmemCols));
-  if (abort_s) return;
-  for (int e = tid; e < r * s; e += kThr) {
+  // G = Y^T Y, strict upper triangle (Y[i][l] = 1 at i = l, the stored v below, 0 above and for
+  // l >= kmax): one warp per column k of Y, lanes over rows, the 32 sums reduced together
+  for (int k = warp; k < kNb; k += kPT / 32) {
+    float acc[32];
+#pragma unroll
+    for (int l = 0; l < 32; ++l) acc[l] = 0.f;
+    if (k < kmax) {
+      const float* yk = A + k * kRows;
+      for (int i = lane; i < kRows; i += 32) {
+        const float xv = i > k ? yk[i] : (i == k ? 1.f : 0.f);
+#pragma unroll
+        for (int l = 0; l < kNb; ++l) {
+          const float y = (l < kmax && l < k) ? (i > l ? A[l * kRows + i] : (i == l ? 1.f : 0.f)) : 0.f;
+          acc[l] += y * xv;
+        }
+      }
+    }
+    const float g = transpose_reduce(acc, lane);
+    Gs[lane * kPad + k] = (lane < k && k < kmax) ? g : 0.f;
+  }
+  __syncthreads();
+  // T, column by column on warp 0 (lane l holds row l)
+  if (warp == 0) {
+    for (int k = 0; k < kNb; ++k) {
+      const float tk = k < kmax ? tau_s[k] : 0.f;
+      float v = 0.f;
+      if (lane < k) {
+        for (int m = lane; m < k; ++m) v += Tm[lane * kPad + m] * Gs[m * kPad + k];
+        v *= -tk;
+      }
+      __syncwarp();
+      if (lane < k) Tm[lane * kPad + k] = v;
+      if (lane == k) Tm[k * kPad + k] = tk;
+      __syncwarp();
+    }
+  }
+  __syncthreads();
+  if (Tout)
+    for (int e = tid; e < kNb * kNb; e += kPT)
+      Tout[(int64_t)blockIdx.x * (kNb * kNb) + e] = Tm[(e / kNb) * kPad + e % kNb];
+  for (int e = tid; e < r * kNb; e += kPT) {
     const int c = e / r, i = e % r;
     X[(int64_t)c * ld + r0 + i] = A[c * kRows + i];
   }
   if (Xn) {
-    const int64_t n0 = (int64_t)blockIdx.x * s;
-    for (int e = tid; e < kmax * s; e += kThr) {
+    const int64_t n0 = (int64_t)blockIdx.x * kNb;
+    for (int e = tid; e < kmax * kNb; e += kPT) {
       const int c = e / kmax, i = e % kmax;
       Xn[(int64_t)c * ldn + n0 + i] = (c >= i) ? A[c * kRows + i] : 0.f;
     }
@@ -510,7 +320,6 @@ tsqr_panel_apply_kernel(const float* X, int64_t ld, int64_t M, int pw, const flo
   float* W = Tm + kNb * kNb;                                               // 32 x kCw, row-major
   __shared__ uint32_t tmem_slot;
   __shared__ __align__(8) uint64_t mbar_ld, mbar_mma;
-  __shared__ int abort_s;
 
   const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
   const int64_t tile = blockIdx.x;
@@ -530,7 +339,6 @@ tsqr_panel_apply_kernel(const float* X, int64_t ld, int64_t M, int pw, const flo
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar_ld)), "r"(1));
     asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(su32(&mbar_mma)), "r"(1));
     asm volatile("fence.mbarrier_init.release.cluster;");
-    abort_s = 0;
   }
   asm volatile("tcgen05.fence::before_thread_sync;");
   __syncthreads();
@@ -694,30 +502,6 @@ tsqr_panel_apply_kernel(const float* X, int64_t ld, int64_t M, int pw, const flo
 
 }  // namespace
 
-size_t tsqr_tc_smem(int s) {
-  return (size_t)kRows * s * 4 + 2 * (size_t)kRows * kNb * 4 + 2 * (size_t)(kMaxS - kNb) * kNb * 4 +
-         (size_t)kNb * kNb * 4;
-}
-
-qrkit_status tsqr_tile_tc(qrkit_ctx* ctx, float* X, int64_t ld, int64_t M, int s, float* taus, float* Xn,
-                          int64_t ldn, int64_t tiles, float* Tout) {
-  if (s % kNb != 0 || s <= 0 || s > kMaxS)
-    return fail(ctx, QRKIT_EINVAL, "tensor-core tile kernel: s a multiple of 32 up to 128");
-  const size_t smem = tsqr_tc_smem(s);
-  if (smem > ctx->max_smem_optin)
-    return fail(ctx, QRKIT_EUNSUPPORTED, "not enough shared memory for the tensor-core tile kernel");
-  if (ctx->smem_attr[7] < smem) {
-    QRKIT_CUDA_TRY(ctx, cudaFuncSetAttribute(tsqr_tile_tc_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                             (int)smem));
-    ctx->smem_attr[7] = smem;
-  }
-  tsqr_tile_tc_kernel<<<(unsigned)tiles, kThr, smem, ctx->stream>>>(X, ld, M, s, taus, Xn, ldn, Tout,
-                                                                    ctx->d_status);
-  ctx->launches += 1;
-  QRKIT_CUDA_TRY(ctx, cudaGetLastError());
-  return QRKIT_OK;
-}
-
 qrkit_status tsqr_panel_apply(qrkit_ctx* ctx, const float* X, int64_t ld, int64_t M, int pw, const float* T,
                               int n, float* up, int64_t ldu, float* down, int64_t ldd, int64_t down0,
                               int64_t tiles) {
@@ -736,6 +520,22 @@ qrkit_status tsqr_panel_apply(qrkit_ctx* ctx, const float* X, int64_t ld, int64_
   const dim3 grid((unsigned)tiles, (unsigned)((n + kCw - 1) / kCw));
   tsqr_panel_apply_kernel<<<grid, kThr, smem, ctx->stream>>>(X, ld, M, pw, T, n, up, ldu, down, ldd, down0,
                                                              ctx->d_status);
+  ctx->launches += 1;
+  QRKIT_CUDA_TRY(ctx, cudaGetLastError());
+  return QRKIT_OK;
+}
+
+qrkit_status tsqr_panel_tile(qrkit_ctx* ctx, float* X, int64_t ld, int64_t M, float* taus, float* Xn, int64_t ldn,
+                             int64_t tiles, float* Tout) {
+  const size_t smem = panel_tile_smem();
+  if (smem > ctx->max_smem_optin)
+    return fail(ctx, QRKIT_EUNSUPPORTED, "not enough shared memory for the panel tile kernel");
+  if (ctx->smem_attr[13] < smem) {
+    QRKIT_CUDA_TRY(ctx, cudaFuncSetAttribute(tsqr_panel_tile_kernel, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                             (int)smem));
+    ctx->smem_attr[13] = smem;
+  }
+  tsqr_panel_tile_kernel<<<(unsigned)tiles, kPT, smem, ctx->stream>>>(X, ld, M, taus, Xn, ldn, Tout, ctx->d_status);
   ctx->launches += 1;
   QRKIT_CUDA_TRY(ctx, cudaGetLastError());
   return QRKIT_OK;
