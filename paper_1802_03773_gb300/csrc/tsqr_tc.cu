@@ -103,14 +103,14 @@ __device__ __forceinline__ bool wait_phase(uint64_t* bar, uint32_t parity) {
 // ---- Column-panel TSQR: the QR of one 256-row tile of a 32-column panel ----
 //
 // Householder QR (Sec. 2) of a 256 x 32 tile with its columns in registers: column j lives on
-// warp j % 16, row i = lane + 32 u (u < 8) of it on the lane.  At step k the reflector of column
-// k goes through shared memory (two alternating slots), every warp applies it to its columns
-// after k (a dot product by one warp reduction, then an axpy, all in registers), and the warp
-// that holds column k + 1 forms the next reflector right after updating it.  Then G = Y^T Y
-// (strict upper triangle) and the compact-WY T (T[k][k] = tau_k, column k of the strict upper
-// part = -tau_k T[:, :k] G[:k, k]) for the panel update.  Outputs as the general tile kernel:
-// reflectors below / R on and above the diagonal in place, tau per column, T, the R rows to the
-// next level.
+// warp j % 16, row i = lane + 32 u (u < 8) of it on the lane.  At step k the reflector v_k of
+// column k goes through shared memory (two alternating slots); every warp applies it to its
+// columns after k (a dot product, then an axpy, in registers) and takes the products
+// G[c][k] = v_c^T v_k of its columns c before k, its two reductions interleaved; the warp that
+// holds column k + 1 forms the next reflector right after updating it.  Then the compact-WY T
+// (T[k][k] = tau_k, column k of the strict upper part = -tau_k T[:, :k] G[:k, k]) for the panel
+// update.  Outputs as any TSQR tile: reflectors below / R on and above the diagonal in place,
+// tau per column, T, the R rows to the next level.
 constexpr int kPT = 512;        // threads of a panel tile (16 warps, two columns each)
 constexpr int kPad = kNb + 1;   // row stride of G and T in shared memory (conflict-free rows)
 
@@ -203,25 +203,44 @@ tsqr_panel_tile_kernel(float* X, int64_t ld, int64_t M, float* taus, float* Xn, 
       taus[(int64_t)blockIdx.x * kNb + k] = t;
     }
   };
-  // a column after k updated with reflector k: a -= t (v^T a) v
-  auto update = [&](float (&a)[kRows / 32], const float (&v)[kRows / 32], float t) {
-    float d = 0.f;
-#pragma unroll
-    for (int u = 0; u < kRows / 32; ++u) d += v[u] * a[u];
-    const float w = warp_sum(d) * t;
-#pragma unroll
-    for (int u = 0; u < kRows / 32; ++u) a[u] -= w * v[u];
-  };
+  for (int e = tid; e < kNb * kPad; e += kPT) Gs[e] = 0.f;
   if (warp == 0 && kmax > 0) form(0, a0, 0);
+  const int c0 = warp, c1 = warp + 16;   // the warp's columns (a0, a1)
   for (int k = 0; k < kmax; ++k) {
     __syncthreads();   // reflector k in slot k & 1; column k + 1 not yet updated
     const int slot = k & 1;
-    float v[kRows / 32];
-#pragma unroll
-    for (int u = 0; u < kRows / 32; ++u) v[u] = V[slot * kRows + lane + 32 * u];
     const float t = tslot[slot];
-    if (warp > k) update(a0, v, t);
-    if (warp + 16 > k) update(a1, v, t);
+    // v_k against each own column: the column itself if it is after k (to update it: a -= t
+    // (v^T a) v), its reflector y_c (1 at row c, v_c below, 0 above) if it is before k (G[c][k])
+    float v[kRows / 32], p0 = 0.f, p1 = 0.f;
+#pragma unroll
+    for (int u = 0; u < kRows / 32; ++u) {
+      const int i = lane + 32 * u;
+      v[u] = V[slot * kRows + i];
+      const float y0 = c0 > k ? a0[u] : (i > c0 ? a0[u] : (i == c0 ? 1.f : 0.f));
+      const float y1 = c1 > k ? a1[u] : (i > c1 ? a1[u] : (i == c1 ? 1.f : 0.f));
+      p0 += v[u] * y0;
+      p1 += v[u] * y1;
+    }
+#pragma unroll
+    for (int d = 16; d >= 1; d >>= 1) {
+      p0 += __shfl_xor_sync(0xffffffffu, p0, d);
+      p1 += __shfl_xor_sync(0xffffffffu, p1, d);
+    }
+    if (c0 > k) {
+      const float w = p0 * t;
+#pragma unroll
+      for (int u = 0; u < kRows / 32; ++u) a0[u] -= w * v[u];
+    } else if (c0 < k && lane == 0) {
+      Gs[c0 * kPad + k] = p0;
+    }
+    if (c1 > k) {
+      const float w = p1 * t;
+#pragma unroll
+      for (int u = 0; u < kRows / 32; ++u) a1[u] -= w * v[u];
+    } else if (c1 < k && lane == 0) {
+      Gs[c1 * kPad + k] = p1;
+    }
     if (k + 1 < kmax && ((k + 1) & 15) == warp) {
       if (k + 1 < 16) form(k + 1, a0, slot ^ 1);
       else form(k + 1, a1, slot ^ 1);
@@ -234,36 +253,15 @@ tsqr_panel_tile_kernel(float* X, int64_t ld, int64_t M, float* taus, float* Xn, 
   }
   for (int e = tid; e < kNb * kPad; e += kPT) Tm[e] = 0.f;
   __syncthreads();
-  // G = Y^T Y, strict upper triangle (Y[i][l] = 1 at i = l, the stored v below, 0 above and for
-  // l >= kmax): one warp per column k of Y, lanes over rows, the 32 sums reduced together
-  for (int k = warp; k < kNb; k += kPT / 32) {
-    float acc[32];
-#pragma unroll
-    for (int l = 0; l < 32; ++l) acc[l] = 0.f;
-    if (k < kmax) {
-      const float* yk = A + k * kRows;
-      for (int i = lane; i < kRows; i += 32) {
-        const float xv = i > k ? yk[i] : (i == k ? 1.f : 0.f);
-#pragma unroll
-        for (int l = 0; l < kNb; ++l) {
-          const float y = (l < kmax && l < k) ? (i > l ? A[l * kRows + i] : (i == l ? 1.f : 0.f)) : 0.f;
-          acc[l] += y * xv;
-        }
-      }
-    }
-    const float g = transpose_reduce(acc, lane);
-    Gs[lane * kPad + k] = (lane < k && k < kmax) ? g : 0.f;
-  }
-  __syncthreads();
-  // T, column by column on warp 0 (lane l holds row l)
+  // T, column by column on warp 0 (lane l holds row l).  The sum runs over all 32 m: T[l][m]
+  // is still zero for m >= k and below the diagonal, and G[m][k] for m >= k.
   if (warp == 0) {
     for (int k = 0; k < kNb; ++k) {
       const float tk = k < kmax ? tau_s[k] : 0.f;
-      float v = 0.f;
-      if (lane < k) {
-        for (int m = lane; m < k; ++m) v += Tm[lane * kPad + m] * Gs[m * kPad + k];
-        v *= -tk;
-      }
+      float q[4] = {0.f, 0.f, 0.f, 0.f};
+#pragma unroll
+      for (int m = 0; m < kNb; ++m) q[m & 3] += Tm[lane * kPad + m] * Gs[m * kPad + k];
+      const float v = -((q[0] + q[1]) + (q[2] + q[3])) * tk;
       __syncwarp();
       if (lane < k) Tm[lane * kPad + k] = v;
       if (lane == k) Tm[k * kPad + k] = tk;
