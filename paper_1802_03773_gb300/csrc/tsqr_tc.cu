@@ -10,9 +10,9 @@
 //      product is read back with tcgen05.ld and subtracted in shared memory.
 // Operands are staged in shared memory in the canonical K-major no-swizzle layout (8-row x
 // 16-byte core matrices) and described by tcgen05 shared-memory descriptors.  Tiles arrive by
-// bulk copies (TMA).  The outputs follow the unblocked tile kernel (V below / R on and above the
-// diagonal, tau per column, the tile's R rows to the next TSQR level), so Q^T b and the solves
-// are those of any TSQR.
+// bulk copies (TMA).  The outputs are those of any Householder TSQR (V below / R on and above
+// the diagonal, tau per column, the tile's R rows to the next TSQR level), so Q^T b and the
+// solves apply it reflector by reflector.
 #include <cuda_runtime.h>
 #include <math.h>
 #include <stdint.h>
@@ -288,9 +288,9 @@ tsqr_panel_tile_kernel(float* X, int64_t ld, int64_t M, float* taus, float* Xn, 
 // ---- Column-panel TSQR: a factored panel's tile reflectors applied to the columns after it ----
 //
 // One CTA takes one 256-row tile of a TSQR level and kCw of the trailing columns C (staged by
-// bulk copies).  For each group of 32 reflectors of the tile's panel (Y, with the tile kernel's T),
-// Q_group^T C = C - Y (T^T (Y^T C)): W = Y^T C and Z = T^T W on the CUDA cores, C -= Y Z on the
-// tensor cores (kind::tf32, 3xTF32, FP32 accumulation in TMEM), as in the tile kernel.  The
+// bulk copies).  For each group of 32 reflectors of the tile's panel (Y, with the panel tile's
+// T), Q_group^T C = C - Y (T^T (Y^T C)): W = Y^T C and Z = T^T W on the CUDA cores, C -= Y Z on
+// the tensor cores (kind::tf32, 3xTF32, FP32 accumulation in TMEM).  The
 // transformed tile's top rows (R rows of the panel) go up to the next level, the others down to
 // the next panel.  Y arrives column by column in the space of its low operand half and is kept
 // row-major (rows padded to kYr floats), so that a lane reads four reflectors of its row in one
