@@ -161,6 +161,25 @@ def test_dense_column_panels_fp32_refined(s, K):
     assert np.abs(G - Gr).max() <= 1e-5 * np.abs(Gr).max()
 
 
+@pytest.mark.parametrize("K,s,lam", [(8, 64, None), (50, 64, 0.0), (20, 96, None), (150, 160, 0.0)])
+def test_dense_column_panels_small(K, s, lam):
+    """Column panels on small problems: every panel's TSQR is one tile (fewer than 256 rows), the
+    last panel may hold exactly its 32 rows, with and without the damping rows.  Refined float
+    result within 1e-5 of the float64 oracle of the float-rounded problem."""
+    d = block_angular_dense(K=K, n=4, m=2, s=s, scale_decades=1.0, seed_offset=3 * s + K)
+    d32 = dict(d)
+    d32["blocks"] = np.asarray(d["blocks"], np.float32).astype(np.float64)
+    d32["S"] = np.asarray(d["S"], np.float32).astype(np.float64)
+    d32["b"] = np.asarray(d["b"], np.float32).astype(np.float64)
+    P = problem_from(d32)
+    if lam is not None:
+        P.lam = lam
+        d32["lam"] = lam
+    p_ref, _ = st.factor_and_solve(P)
+    out = run(d32, "fp32_refined", refine_steps=2)
+    assert_close(out["p"], p_ref, 1e-5)
+
+
 @pytest.mark.parametrize("s", [128, 512])
 def test_dense_column_panels_full_size(s):
     """The timed shapes at full size (100,000 blocks 4x2, S 400,000 x s, FP32 refined, one
